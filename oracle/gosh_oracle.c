@@ -1,0 +1,400 @@
+/*
+ * gosh_oracle.c -- plain, slow, single-threaded FP64 CPU oracle for the GOSH
+ * per-level embedding step (arxiv 2110.10049).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA library; the only thing
+ * the two sides have in common is the seeded input graph that the tests hand
+ * to both.
+ *
+ * Every function follows one passage of the paper, cited next to it:
+ *   Alg. 1  UPDATEEMBED                (Sec. 2)
+ *   Alg. 3  TRAININGPU epoch loop      (Sec. 3.1)
+ *   Alg. 4  MULTIEDGECOLLAPSE          (Sec. 4)
+ *   Sec. 3  EXPANDEMBEDDING (copy projection), epoch split, lr decay
+ *   Sec. 6.1 link-prediction AUC protocol
+ * Where the paper is silent the reading used is written beside the code.
+ *
+ * Compiled with -ffp-contract=off so that every a*b+c is two rounded
+ * operations, exactly as written.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11).  Counter-based: out = f_key(counter).           */
+/* ------------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2E7470EE14C6C93ULL
+#define PHILOX_M1 0xCA5A826395121157ULL
+#define PHILOX_W0 0x9E3779B97F4A7C15ULL /* golden ratio */
+#define PHILOX_W1 0xBB67AE8584CAA73BULL /* sqrt(3) - 1 */
+
+static void mul128(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+    uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        uint64_t hi0, lo0, hi1, lo1;
+        mul128(PHILOX_M0, c0, &hi0, &lo0);
+        mul128(PHILOX_M1, c2, &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        uint64_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform integer in [0, n) from a 64-bit word: floor(w * n / 2^64). */
+static uint64_t uniform_below(uint64_t w, uint64_t n) {
+    uint64_t hi, lo;
+    mul128(w, n, &hi, &lo);
+    return hi;
+}
+
+/* Stream tags: which use a Philox block serves (fourth counter word). */
+enum { TAG_SAMPLE = 0, TAG_INIT = 1 };
+
+/* The words used by source v in epoch `epoch` of level `level`:
+ * counter (v, blk, level<<32 | epoch, TAG_SAMPLE), key (seed, graph). */
+static void sample_words(uint64_t seed, uint64_t graph, int level, int epoch,
+                         int64_t v, int nwords, uint64_t *w) {
+    uint64_t key[2] = {seed, graph};
+    for (int blk = 0; blk * 4 < nwords; ++blk) {
+        uint64_t ctr[4] = {(uint64_t)v, (uint64_t)blk,
+                           ((uint64_t)(uint32_t)level << 32) | (uint32_t)epoch, TAG_SAMPLE};
+        uint64_t o[4];
+        orc_philox4x64(ctr, key, o);
+        for (int j = 0; j < 4 && blk * 4 + j < nwords; ++j) w[blk * 4 + j] = o[j];
+    }
+}
+
+/*
+ * The k+1 sample vertices of source v (Alg. 3, Sec. 3.1): word 0 draws the
+ * positive uniformly from Gamma(v) (adjacency similarity, Q(u,v)=1 iff
+ * (u,v) in E), words 1..k draw negatives uniformly over V_i.
+ * Reading: a source without neighbours has no positive (u[0] = -1); a
+ * negative equal to the source is skipped (u[t] = -1).  Neighbours are not
+ * rejected as negatives (uniform noise).
+ */
+void orc_draw_samples(int64_t n, const int64_t *rowptr, const int32_t *col, int k,
+                      int level, int epoch, uint64_t seed, uint64_t graph,
+                      int64_t v, int32_t *u) {
+    uint64_t w[64];
+    sample_words(seed, graph, level, epoch, v, k + 1, w);
+    int64_t deg = rowptr[v + 1] - rowptr[v];
+    u[0] = deg > 0 ? col[rowptr[v] + (int64_t)uniform_below(w[0], (uint64_t)deg)] : -1;
+    for (int t = 1; t <= k; ++t) {
+        int64_t x = (int64_t)uniform_below(w[t], (uint64_t)n);
+        u[t] = (x == v) ? -1 : (int32_t)x;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 1 UPDATEEMBED and the NCE loss (Sec. 2).                              */
+/* ------------------------------------------------------------------------ */
+static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+/* softplus(z) = log(1 + e^z), evaluated without overflow. */
+static double softplus(double z) { return (z > 0 ? z : 0.0) + log1p(exp(-fabs(z))); }
+
+/* Negative log-likelihood of one sample (Sec. 2): -log sigma(x) for a
+ * positive (b = 1), -log sigma(-x) = -log(1 - sigma(x)) for a negative. */
+double orc_sample_loss(double x, int b) { return b ? softplus(-x) : softplus(x); }
+
+static double dot(const double *a, const double *b, int d) {
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s += a[j] * b[j];
+    return s;
+}
+
+/*
+ * One UPDATEEMBED (Alg. 1).  Reading of the first line: score = (b - sigma(x)) * lr
+ * (the printed precedence would make the step ~1 regardless of lr).  The
+ * second line updates M[v]; the third updates M[sample] with the UPDATED M[v],
+ * literally in that order.  Returns x, the dot product before the update.
+ */
+double orc_update_embed(double *mv, double *mu, int d, int b, double lr) {
+    double x = dot(mv, mu, d);
+    double score = ((double)b - sigmoid(x)) * lr;
+    for (int j = 0; j < d; ++j) {
+        double step = mu[j] * score;
+        mv[j] = mv[j] + step;
+    }
+    for (int j = 0; j < d; ++j) {
+        double step = mv[j] * score;
+        mu[j] = mu[j] + step;
+    }
+    return x;
+}
+
+/* lr' = lr * max(1 - j/e_i, floor) (Sec. 3, Alg. 3). */
+double orc_epoch_lr(double lr, double lr_floor, int j, int e_i) {
+    double f = 1.0 - (double)j / (double)e_i;
+    return lr * (f > lr_floor ? f : lr_floor);
+}
+
+/*
+ * TRAININGPU (Alg. 3) executed sequentially: for each epoch j, for each source
+ * v in id order, one positive update (b = 1) then k negative updates (b = 0),
+ * each an UPDATEEMBED on the current M.  M is |V| x d row-major FP64.
+ * loss_per_epoch[j] (nullable) sums the NLL of every applied update, taken
+ * from the pre-update dot product.  n_updates (nullable) counts applied
+ * updates.
+ */
+void orc_train_sequential(int64_t n, const int64_t *rowptr, const int32_t *col,
+                          double *M, int d, int k, int level, int epochs,
+                          double lr, double lr_floor, uint64_t seed, uint64_t graph,
+                          double *loss_per_epoch, int64_t *n_updates) {
+    int32_t u[64];
+    int64_t applied = 0;
+    for (int j = 0; j < epochs; ++j) {
+        double lrj = orc_epoch_lr(lr, lr_floor, j, epochs);
+        double loss = 0.0;
+        for (int64_t v = 0; v < n; ++v) {
+            orc_draw_samples(n, rowptr, col, k, level, j, seed, graph, v, u);
+            for (int t = 0; t <= k; ++t) {
+                if (u[t] < 0) continue;
+                double x = orc_update_embed(M + v * d, M + (int64_t)u[t] * d, d, t == 0, lrj);
+                loss += orc_sample_loss(x, t == 0);
+                ++applied;
+            }
+        }
+        if (loss_per_epoch) loss_per_epoch[j] = loss;
+    }
+    if (n_updates) *n_updates = applied;
+}
+
+/*
+ * Deterministic (snapshot) mode.  Not in the paper: it is the reproducible
+ * counterpart of the lock-free epoch.  Sources are taken in batches of m
+ * consecutive ids; S is M at the start of the batch.  Each source v of the
+ * batch runs its k+1 UPDATEEMBEDs on private copies: r starts at S[v]; the
+ * sample row starts at S[u] (or at this source's own updated copy of it when
+ * the same u was already drawn earlier by v, so that m = 1 is exactly the
+ * sequential epoch); the change of the sample row, c = score * r_new, is
+ * recorded.  At the end of the batch every row x becomes
+ *     base(x) + c_1 + c_2 + ...     (summed left to right)
+ * with base(x) = r_x if x is a source of the batch, else S[x], and the
+ * contributions to x taken in order of (source ascending, sample ascending).
+ */
+void orc_train_deterministic(int64_t n, const int64_t *rowptr, const int32_t *col,
+                             double *M, int d, int k, int level, int epochs,
+                             double lr, double lr_floor, uint64_t seed, uint64_t graph,
+                             int64_t m, double *loss_per_epoch, int64_t *n_updates) {
+    int32_t u[64];
+    int64_t applied = 0;
+    /* M itself is the snapshot S: nothing writes M until the batch ends. */
+    double *R = (double *)malloc(sizeof(double) * (size_t)m * d);            /* r of each source */
+    double *C = (double *)malloc(sizeof(double) * (size_t)m * (k + 1) * d);  /* contributions */
+    int32_t *tgt = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * (k + 1));
+    double *rows = (double *)malloc(sizeof(double) * (size_t)(k + 1) * d);   /* private sample rows */
+    for (int j = 0; j < epochs; ++j) {
+        double lrj = orc_epoch_lr(lr, lr_floor, j, epochs);
+        double loss = 0.0;
+        for (int64_t b0 = 0; b0 < n; b0 += m) {
+            int64_t b1 = b0 + m < n ? b0 + m : n;
+            for (int64_t v = b0; v < b1; ++v) {
+                double *r = R + (v - b0) * d;
+                memcpy(r, M + v * d, sizeof(double) * d);
+                orc_draw_samples(n, rowptr, col, k, level, j, seed, graph, v, u);
+                for (int t = 0; t <= k; ++t) {
+                    int64_t slot = (v - b0) * (k + 1) + t;
+                    tgt[slot] = u[t];
+                    if (u[t] < 0) continue;
+                    double *row = rows + t * d;
+                    int prev = -1;
+                    for (int s = 0; s < t; ++s) if (u[s] == u[t]) prev = s;
+                    memcpy(row, prev >= 0 ? rows + prev * d : M + (int64_t)u[t] * d, sizeof(double) * d);
+                    double x = orc_update_embed(r, row, d, t == 0, lrj);
+                    /* the sample row received row + r_new * score: record r_new * score */
+                    double score = ((double)(t == 0) - sigmoid(x)) * lrj;
+                    double *c = C + slot * d;
+                    for (int q = 0; q < d; ++q) c[q] = r[q] * score;
+                    loss += orc_sample_loss(x, t == 0);
+                    ++applied;
+                }
+            }
+            /* write back: bases of the sources first, then contributions in order */
+            for (int64_t v = b0; v < b1; ++v) memcpy(M + v * d, R + (v - b0) * d, sizeof(double) * d);
+            for (int64_t i = 0; i < (b1 - b0) * (k + 1); ++i) {
+                int32_t x = tgt[i];
+                if (x < 0) continue;
+                const double *c = C + i * d;
+                for (int q = 0; q < d; ++q) M[(int64_t)x * d + q] = M[(int64_t)x * d + q] + c[q];
+            }
+        }
+        if (loss_per_epoch) loss_per_epoch[j] = loss;
+    }
+    free(R); free(C); free(tgt); free(rows);
+    if (n_updates) *n_updates = applied;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Random initialisation of M_{D-1} (Alg. 2, "Randomly initialize"):         */
+/* U(-0.5/d, 0.5/d) from Philox.  Element c of row v takes word c%4 of the   */
+/* block with counter (v, c/4, level, TAG_INIT), key (seed, graph):          */
+/*   x = ((w >> 11) * 2^-53 - 0.5) / d        (exact except the division)   */
+/* ------------------------------------------------------------------------ */
+void orc_init_uniform(int64_t n, int d, int level, uint64_t seed, uint64_t graph, double *M) {
+    uint64_t key[2] = {seed, graph};
+    for (int64_t v = 0; v < n; ++v) {
+        for (int c0 = 0; c0 < d; c0 += 4) {
+            uint64_t ctr[4] = {(uint64_t)v, (uint64_t)(c0 / 4), (uint64_t)(uint32_t)level, TAG_INIT};
+            uint64_t o[4];
+            orc_philox4x64(ctr, key, o);
+            for (int j = 0; j < 4 && c0 + j < d; ++j) {
+                double unit = (double)(o[j] >> 11) * 0x1.0p-53;
+                M[v * d + c0 + j] = (unit - 0.5) / (double)d;
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 4 MULTIEDGECOLLAPSE, one level: SORT (ordering heuristic), then the */
+/* greedy mapping with the hub^2 restriction.                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * SORT: counting sort by degree, larger neighbourhoods first.  Reading: the
+ * sort is stable, so vertices of equal degree keep ascending id order.
+ */
+void orc_degree_order(int64_t n, const int64_t *rowptr, int32_t *order) {
+    int64_t maxdeg = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t dv = rowptr[v + 1] - rowptr[v];
+        if (dv > maxdeg) maxdeg = dv;
+    }
+    int64_t *start = (int64_t *)calloc((size_t)maxdeg + 2, sizeof(int64_t));
+    for (int64_t v = 0; v < n; ++v) start[rowptr[v + 1] - rowptr[v]]++;
+    /* exclusive positions, highest degree first */
+    int64_t pos = 0;
+    for (int64_t dd = maxdeg; dd >= 0; --dd) {
+        int64_t c = start[dd];
+        start[dd] = pos;
+        pos += c;
+    }
+    for (int64_t v = 0; v < n; ++v) order[start[rowptr[v + 1] - rowptr[v]]++] = (int32_t)v;
+    free(start);
+}
+
+/*
+ * The mapping loop of Alg. 4.  delta = |E_i| / |V_i| where |E_i| is the number
+ * of CSR entries (both directions of each undirected edge), i.e. the average
+ * degree.  "|Gamma(x)| <= delta" is evaluated exactly as deg(x) * |V_i| <= nnz_i.
+ * Clusters are numbered by a counter in discovery order.
+ * Returns |V_{i+1}|.
+ */
+int64_t orc_mec_map(int64_t n, const int64_t *rowptr, const int32_t *col, int32_t *map) {
+    int64_t nnz = rowptr[n];
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    orc_degree_order(n, rowptr, order);
+    for (int64_t v = 0; v < n; ++v) map[v] = -1;
+    int64_t cluster = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t v = order[i];
+        if (map[v] != -1) continue;
+        map[v] = (int32_t)cluster++;
+        int64_t dv = rowptr[v + 1] - rowptr[v];
+        int v_small = dv * n <= nnz;
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            int32_t u = col[e];
+            int64_t du = rowptr[u + 1] - rowptr[u];
+            int u_small = du * n <= nnz;
+            if (v_small || u_small) {
+                if (map[u] == -1) map[u] = map[v];
+            }
+        }
+    }
+    free(order);
+    return cluster;
+}
+
+static int cmp_u64(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/*
+ * COARSEN(G_i, map_i) (Alg. 4): G_{i+1} has an edge (map u, map v) for every
+ * edge (u, v) of G_i with map u != map v; duplicates collapse (the coarse
+ * graph is simple and unweighted).  Output CSR rows hold neighbours in
+ * ascending order.  col_out must hold nnz_i entries.  Returns nnz_{i+1}.
+ */
+int64_t orc_coarsen(int64_t n, const int64_t *rowptr, const int32_t *col,
+                    const int32_t *map, int64_t nc, int64_t *rowptr_out, int32_t *col_out) {
+    int64_t nnz = rowptr[n];
+    uint64_t *pairs = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t m = 0;
+    for (int64_t v = 0; v < n; ++v)
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            uint32_t a = (uint32_t)map[v], b = (uint32_t)map[col[e]];
+            if (a != b) pairs[m++] = ((uint64_t)a << 32) | b;
+        }
+    qsort(pairs, (size_t)m, sizeof(uint64_t), cmp_u64);
+    int64_t w = 0;
+    for (int64_t i = 0; i < m; ++i)
+        if (i == 0 || pairs[i] != pairs[i - 1]) pairs[w++] = pairs[i];
+    for (int64_t c = 0; c <= nc; ++c) rowptr_out[c] = 0;
+    for (int64_t i = 0; i < w; ++i) {
+        rowptr_out[(pairs[i] >> 32) + 1]++;
+        col_out[i] = (int32_t)(pairs[i] & 0xffffffffu);
+    }
+    for (int64_t c = 0; c < nc; ++c) rowptr_out[c + 1] += rowptr_out[c];
+    free(pairs);
+    return w;
+}
+
+/* EXPANDEMBEDDING (Alg. 2, Sec. 3): M_i[v] = M_{i+1}[map_i[v]]. */
+void orc_project_copy(int64_t n_fine, const int32_t *map, const double *Mc, double *Mf, int d) {
+    for (int64_t v = 0; v < n_fine; ++v)
+        memcpy(Mf + v * d, Mc + (int64_t)map[v] * d, sizeof(double) * d);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Link-prediction scores and AUCROC (Sec. 6.1).  Reading: the score of a    */
+/* pair is the dot product M[u].M[v]; the AUC is the Mann-Whitney statistic */
+/* U / (n+ n-), a tie counting one half.                                      */
+/* ------------------------------------------------------------------------ */
+void orc_pair_scores(const double *M, int d, int64_t npairs, const int32_t *pairs, double *out) {
+    for (int64_t i = 0; i < npairs; ++i)
+        out[i] = dot(M + (int64_t)pairs[2 * i] * d, M + (int64_t)pairs[2 * i + 1] * d, d);
+}
+
+typedef struct { double s; int pos; } scored;
+static int cmp_scored(const void *a, const void *b) {
+    double x = ((const scored *)a)->s, y = ((const scored *)b)->s;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+double orc_auc(int64_t npos, const double *pos, int64_t nneg, const double *neg) {
+    int64_t tot = npos + nneg;
+    scored *a = (scored *)malloc(sizeof(scored) * (size_t)(tot > 0 ? tot : 1));
+    for (int64_t i = 0; i < npos; ++i) { a[i].s = pos[i]; a[i].pos = 1; }
+    for (int64_t i = 0; i < nneg; ++i) { a[npos + i].s = neg[i]; a[npos + i].pos = 0; }
+    qsort(a, (size_t)tot, sizeof(scored), cmp_scored);
+    /* walk tie groups: each positive gains (#neg strictly below) + 0.5 (#neg tied) */
+    double U = 0.0;
+    int64_t neg_below = 0;
+    for (int64_t i = 0; i < tot;) {
+        int64_t j = i, gp = 0, gn = 0;
+        while (j < tot && a[j].s == a[i].s) { if (a[j].pos) ++gp; else ++gn; ++j; }
+        U += (double)gp * ((double)neg_below + 0.5 * (double)gn);
+        neg_below += gn;
+        i = j;
+    }
+    free(a);
+    return U / ((double)npos * (double)nneg);
+}

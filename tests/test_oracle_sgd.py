@@ -1,0 +1,132 @@
+"""Pins for the oracle's training loop (Alg. 3), deterministic mode, init,
+epoch split, projection and AUC.
+
+- deterministic mode with batch m = 1 is exactly the sequential epoch
+  (including repeated samples within a source);
+- training lowers the per-epoch loss and fits the training edges; on a
+  planted-partition graph it predicts held-out edges;
+- epoch split closed forms (Sec. 3);
+- copy projection preserves every coarse dot product on the fine pairs;
+- AUC equals the O(n+ n-) pair count and sklearn's roc_auc_score.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+
+def small_graph():
+    return synth.rmat_graph(7, 6, 11)
+
+
+def test_det_m1_equals_sequential_bitwise(orc):
+    g = small_graph()
+    M0 = orc.init_uniform(g.n, 16, 0, 3).astype(np.float32).astype(np.float64) * 40
+    A, B = M0.copy(), M0.copy()
+    la, na = orc.train_sequential(g.rowptr, g.col, A, 5, 0, 6, 0.05, 1e-4, 77)
+    lb, nb = orc.train_deterministic(g.rowptr, g.col, B, 5, 0, 6, 0.05, 1e-4, 77, 1)
+    assert na == nb
+    np.testing.assert_array_equal(A, B)
+    np.testing.assert_array_equal(la, lb)
+
+
+def test_det_repeated_samples_within_a_source(orc):
+    # 3 vertices, k = 7: repeated negatives are certain; m = 1 must still match
+    g = synth.csr_from_edges(3, np.array([0, 1]), np.array([1, 2]), compact=False)
+    M0 = orc.init_uniform(3, 8, 0, 5) * 50
+    A, B = M0.copy(), M0.copy()
+    orc.train_sequential(g.rowptr, g.col, A, 7, 0, 4, 0.3, 1e-4, 1)
+    orc.train_deterministic(g.rowptr, g.col, B, 7, 0, 4, 0.3, 1e-4, 1, 1)
+    np.testing.assert_array_equal(A, B)
+
+
+def test_det_large_batch_differs_but_converges_similarly(orc):
+    g = small_graph()
+    M0 = orc.init_uniform(g.n, 16, 0, 3) * 30
+    A, B = M0.copy(), M0.copy()
+    la, _ = orc.train_sequential(g.rowptr, g.col, A, 3, 0, 100, 0.045, 1e-4, 5)
+    lb, _ = orc.train_deterministic(g.rowptr, g.col, B, 3, 0, 100, 0.045, 1e-4, 5, 32)
+    assert not np.array_equal(A, B)
+    assert lb[-1] < lb[0] and la[-1] < la[0]
+    assert abs(la[-1] - lb[-1]) / la[-1] < 0.05
+
+
+def test_training_fits_and_loss_falls(orc):
+    g = synth.rmat_graph(9, 8, 21)
+    M = orc.init_uniform(g.n, 32, 0, 1)
+    loss, nup = orc.train_sequential(g.rowptr, g.col, M, 3, 0, 300, 0.1, 1e-4, 9)
+    assert loss[-1] < 0.95 * loss[0]
+    assert nup <= 4 * g.n * 300
+    src = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    edges = np.stack([src, g.col], 1)
+    rng = np.random.default_rng(0)
+    rnd = np.stack([rng.integers(0, g.n, 20000), rng.integers(0, g.n, 20000)], 1)
+    assert orc.link_auc(M, edges, rnd) > 0.9
+
+
+def sbm(n=384, blocks=6, pin=0.2, pout=0.005, seed=1):
+    rng = np.random.default_rng(seed)
+    blk = np.arange(n) // (n // blocks)
+    iu, ju = np.triu_indices(n, 1)
+    keep = rng.random(len(iu)) < np.where(blk[iu] == blk[ju], pin, pout)
+    return synth.csr_from_edges(n, iu[keep], ju[keep])
+
+
+def test_heldout_auc_on_planted_partition(orc):
+    sp = synth.link_split(sbm(), 2)
+    t = sp.train
+    M, info = orc.embed(t.rowptr, t.col, 32, 3, 0.045, 300, 0.3, seed=4, coarsening=False)
+    assert orc.link_auc(M, sp.test_pos, sp.test_neg) > 0.8
+
+
+def test_init_range_and_uniformity(orc):
+    d = 32
+    M = orc.init_uniform(2000, d, 4, 123)
+    assert M.min() >= -0.5 / d and M.max() < 0.5 / d
+    from scipy import stats
+    assert stats.kstest((M.ravel() * d) + 0.5, "uniform").pvalue > 1e-4
+    np.testing.assert_array_equal(M, orc.init_uniform(2000, d, 4, 123))
+    assert not np.array_equal(M, orc.init_uniform(2000, d, 3, 123))
+
+
+@pytest.mark.parametrize("e,p,D", [(200, 0.3, 8), (600, 0.1, 10), (1400, 0.5, 5),
+                                   (1000, 0.3, 1), (7, 0.3, 4), (200, 1.0, 6), (200, 0.0, 6)])
+def test_epoch_split(orc, e, p, D):
+    ep = orc.epoch_split(e, p, D)
+    assert len(ep) == D and sum(ep) == e and min(ep) >= 0
+    if D == 1:
+        assert ep == [e]
+        return
+    uni = p * e / D
+    geo = [x - uni for x in ep]
+    # geometric part: each coarser level takes twice the finer one (floors aside)
+    for i in range(1, D - 1):
+        assert abs(geo[i + 1] - 2 * geo[i]) <= 3
+    if p == 1.0:
+        assert max(ep[1:]) - min(ep[1:]) <= 1
+
+
+def test_projection_preserves_dots(orc):
+    rng = np.random.default_rng(3)
+    nc, nf, d = 20, 100, 8
+    mp = rng.integers(0, nc, nf).astype(np.int32)
+    Mc = rng.normal(size=(nc, d))
+    Mf = orc.project_copy(mp, Mc)
+    np.testing.assert_array_equal(Mf, Mc[mp])
+    pairs = rng.integers(0, nf, (50, 2))
+    np.testing.assert_array_equal(orc.pair_scores(Mf, pairs),
+                                  orc.pair_scores(Mc, mp[pairs]))
+
+
+def test_auc_brute_force_and_ties(orc):
+    rng = np.random.default_rng(8)
+    for trial in range(30):
+        npos, nneg = rng.integers(1, 40, 2)
+        pos = np.round(rng.normal(0.5, 1, npos), 1)  # rounding forces ties
+        neg = np.round(rng.normal(0, 1, nneg), 1)
+        brute = sum((p > q) + 0.5 * (p == q) for p in pos for q in neg) / (npos * nneg)
+        assert orc.auc(pos, neg) == pytest.approx(brute, abs=1e-12)
+    skm = pytest.importorskip("sklearn.metrics")
+    pos, neg = rng.normal(1, 1, 500), rng.normal(0, 1, 700)
+    y = np.r_[np.ones(500), np.zeros(700)]
+    assert orc.auc(pos, neg) == pytest.approx(skm.roc_auc_score(y, np.r_[pos, neg]), abs=1e-12)
