@@ -1,0 +1,210 @@
+/*
+ * gosh.h -- C ABI of libgosh, a GB300 (sm_103a) implementation of the
+ * multi-level graph embedding of GOSH ("Boosting Graph Embedding on a Single
+ * GPU", arxiv 2110.10049).
+ *
+ * Conventions for every entry point
+ *  - Graphs are CSR: row pointer int64[n+1] (rowptr[0] = 0, rowptr[n] = nnz),
+ *    neighbour ids int32[nnz], strictly ascending inside each row, no
+ *    self-loops, symmetric (undirected graph stored in both directions).
+ *  - Embedding matrices are row-major n x d, element type given by gosh_dtype,
+ *    row stride d elements, base address 16-byte aligned.  d is 32, 64 or 128
+ *    (96 for FP32 only).
+ *  - Every pointer is a device pointer unless its comment says otherwise.  The
+ *    caller owns every buffer it passes; the library owns hierarchy handles.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Entry points are asynchronous on that stream unless marked
+ *    "synchronous".  Temporary device memory is taken with cudaMallocAsync on
+ *    the same stream and released before return.
+ *  - No exception crosses the ABI.  Each call returns a gosh_status; on error
+ *    gosh_last_error() (thread-local) holds a one-line message.  Argument
+ *    errors are detected before any kernel is launched.
+ */
+#ifndef GOSH_H
+#define GOSH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gosh_status {
+    GOSH_OK = 0,
+    GOSH_ERR_INVALID_ARG = 1,  /* bad pointer, size, layout or CSR */
+    GOSH_ERR_OOM = 2,          /* device or pinned allocation failed */
+    GOSH_ERR_BUDGET = 3,       /* the work does not fit the device budget */
+    GOSH_ERR_CUDA = 4,         /* a CUDA call failed */
+    GOSH_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    GOSH_ERR_UNSUPPORTED = 6   /* valid request this build does not serve */
+} gosh_status;
+
+typedef enum gosh_dtype { GOSH_F32 = 0, GOSH_BF16 = 1, GOSH_F16 = 2 } gosh_dtype;
+
+/* GOSH_HOGWILD: the lock-free epoch of Sec. 3.1 (concurrent sources race on
+ * shared sample rows).  GOSH_DETERMINISTIC: sources in batches of det_batch
+ * consecutive ids read a snapshot of M taken at the batch start; the row
+ * changes are summed in a fixed order (source, then sample) at the batch end,
+ * so results do not depend on scheduling.  det_batch = 1 is the sequential
+ * epoch of Alg. 3. */
+typedef enum gosh_mode { GOSH_HOGWILD = 0, GOSH_DETERMINISTIC = 1 } gosh_mode;
+
+typedef struct gosh_csr {
+    int64_t n;              /* |V| */
+    const int64_t *rowptr;  /* [n+1] */
+    const int32_t *col;     /* [rowptr[n]] */
+    int on_device;          /* 1: device pointers; 0: host pointers (gosh_embed copies them in) */
+} gosh_csr;
+
+typedef struct gosh_params {
+    int d;                  /* embedding dimension */
+    int k;                  /* negatives per positive, n_s (1..15) */
+    double lr;              /* initial learning rate of every level */
+    double lr_floor;        /* lr' = lr * max(1 - j/e_i, lr_floor); paper: 1e-4 */
+    int epochs;             /* e: total epochs over all levels (one epoch = one pass over V_i) */
+    double p;               /* smoothing ratio of the epoch split */
+    int threshold;          /* coarsening stops once |V_i| <= threshold (paper: 100) */
+    double shrink;          /* ... or once |V_{i+1}| > shrink * |V_i| (paper: 0.8) */
+    int max_levels;         /* cap on the number of graphs; 1 = no coarsening */
+    gosh_dtype dtype;       /* storage type of M */
+    gosh_mode mode;
+    int64_t det_batch;      /* sources per snapshot batch (GOSH_DETERMINISTIC) */
+    uint64_t seed;          /* Philox key word 0 */
+    uint64_t graph_id;      /* Philox key word 1 (distinguishes graphs of a batch) */
+    int lanes_per_row;      /* lanes that share one source row; 0 = automatic */
+    int samples_per_pass;   /* sample rows gathered at once per source; 0 = automatic */
+    int64_t device_budget_bytes; /* 0 = unlimited */
+    int validate;           /* 1: check the CSR before use (costs one pass) */
+} gosh_params;
+
+#define GOSH_MAX_LEVELS 64
+
+typedef struct gosh_stats {
+    int levels;                           /* D */
+    int64_t n[GOSH_MAX_LEVELS];           /* |V_i| */
+    int64_t nnz[GOSH_MAX_LEVELS];         /* CSR entries of G_i */
+    int epochs[GOSH_MAX_LEVELS];          /* e_i */
+    double train_ms[GOSH_MAX_LEVELS];     /* device time of level i's training */
+    double coarsen_ms;                    /* device time of the whole coarsening */
+    double project_ms;                    /* device time of all projections */
+    double total_ms;                      /* wall time of gosh_embed */
+    unsigned long long updates;           /* UPDATEEMBED applications */
+} gosh_stats;
+
+typedef struct gosh_hierarchy gosh_hierarchy;
+
+/* Fills *p with the paper's defaults: d 128, k 3, lr 0.035, lr_floor 1e-4,
+ * e 200, p 0.3 (the "normal" row of the configuration table, Sec. 7),
+ * threshold 100 and shrink 0.8 (Sec. 4), FP32 Hogwild, det_batch 4096. */
+gosh_status gosh_params_default(gosh_params *p);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char *gosh_last_error(void);
+
+/* Checks a device CSR against the layout above (row pointer monotone,
+ * neighbour ids in range, ascending, no self-loop, symmetric).  Synchronous.
+ * Returns GOSH_ERR_INVALID_ARG with a message naming the first violation. */
+gosh_status gosh_validate_csr(const gosh_csr *g, void *stream);
+
+/*
+ * MULTIEDGECOLLAPSE (Alg. 4, Sec. 4).  Builds G_1, G_2, ... from the device
+ * CSR g0: per level, vertices are ordered by degree (descending, ties by
+ * ascending id); in that order each unmapped vertex opens a new cluster and
+ * absorbs its unmapped neighbours u for which deg(v) <= delta or deg(u) <= delta
+ * (hub^2 restriction, delta = nnz_i / |V_i|); G_{i+1} is the image of E_i
+ * without self-loops and duplicates.  Continues while |V_{i+1}| > threshold
+ * and |V_{i+1}| <= floor(shrink * |V_i|); the last graph built is kept; the
+ * body always runs once.  max_levels caps the number of graphs (>= 2).
+ * The maps are identical to the sequential algorithm's (cluster ids in
+ * discovery order).  Synchronous (reads level sizes back).
+ * *out receives a library-owned handle; level 0 aliases g0 (not copied), so
+ * g0 must outlive the handle.
+ */
+gosh_status gosh_coarsen(const gosh_csr *g0, int threshold, double shrink, int max_levels,
+                         void *stream, gosh_hierarchy **out);
+
+/* Number of graphs D in the hierarchy (G_0 .. G_{D-1}). */
+int gosh_hierarchy_levels(const gosh_hierarchy *h);
+
+/* Level i of the hierarchy: g_i (device CSR, library-owned) and map_i, the
+ * device int32[|V_i|] fine-to-coarse map from G_i to G_{i+1} (NULL for the
+ * last level). */
+gosh_status gosh_hierarchy_level(const gosh_hierarchy *h, int i, gosh_csr *g_i,
+                                 const int32_t **map_i);
+
+/* Sizes of level i: *n = |V_i|, *nnz = CSR entries of G_i (either may be NULL). */
+gosh_status gosh_hierarchy_sizes(const gosh_hierarchy *h, int i, int64_t *n, int64_t *nnz);
+
+/* Copies level i to host memory: rowptr int64[n+1], col int32[nnz], map
+ * int32[n] (any may be NULL; map is left untouched for the last level).
+ * Synchronous on `stream`. */
+gosh_status gosh_hierarchy_copy_level(const gosh_hierarchy *h, int i, int64_t *rowptr, int32_t *col,
+                                      int32_t *map, void *stream);
+
+void gosh_hierarchy_free(gosh_hierarchy *h);
+
+/* Random initialisation of M_{D-1} (Alg. 2): M[v][c] = ((w >> 11) * 2^-53 - 0.5) / d
+ * rounded to the storage type, with w word c%4 of Philox4x64-10 at counter
+ * (v, c/4, level, 1) and key (seed, graph_id): uniform on [-0.5/d, 0.5/d). */
+gosh_status gosh_init_embedding(void *M, int64_t n, int d, gosh_dtype dtype, int level,
+                                uint64_t seed, uint64_t graph_id, void *stream);
+
+/*
+ * TRAININGPU (Alg. 3) for one level: `epochs` epochs over the sources of g;
+ * in epoch j every source v draws one positive (uniform over Gamma(v)) and k
+ * negatives (uniform over V) and applies UPDATEEMBED (Alg. 1) to M[v] and each
+ * sample row in turn with lr' = lr * max(1 - j/epochs, lr_floor) and
+ * score = (b - sigmoid(M[v].M[u])) * lr'.  Epochs are serialised (Sec. 3.1).
+ * Draws: Philox4x64-10 at counter (v, blk, level << 32 | j, 0) with key
+ * (seed, graph_id); word 0 picks the positive as col[rowptr[v] + floor(w * deg / 2^64)],
+ * word t picks negative t as floor(w * n / 2^64).  A source without
+ * neighbours skips its positive; a negative equal to the source is skipped.
+ * M: device n x d, updated in place.
+ * loss_per_epoch: device double[epochs] or NULL; receives the summed NLL of
+ *   every applied update (pre-update dot), accumulated in FP64.
+ * n_updates: device uint64 or NULL; incremented by the number of applied updates.
+ * Uses params->{d,k,lr,lr_floor,dtype,mode,det_batch,seed,graph_id,
+ * lanes_per_row,samples_per_pass}.
+ */
+gosh_status gosh_train_level(const gosh_csr *g, void *M, int level, int epochs,
+                             const gosh_params *params, void *stream,
+                             double *loss_per_epoch, unsigned long long *n_updates);
+
+/* EXPANDEMBEDDING (Alg. 2, Sec. 3): M_fine[v] = M_coarse[map[v]] for v < n_fine.
+ * map: device int32[n_fine] with values in [0, n_coarse). */
+gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *map,
+                         void *M_fine, int64_t n_fine, int d, gosh_dtype dtype, void *stream);
+
+/*
+ * GOSH (Alg. 2) end to end: coarsen g0 (unless params->max_levels == 1),
+ * initialise M_{D-1}, then for i = D-1 .. 0 train level i for e_i epochs and,
+ * for i > 0, project onto level i-1.  The epoch split gives a fraction p of
+ * `epochs` uniformly to the D levels and the rest geometrically (each level
+ * twice its finer neighbour): e_i = floor(p*e/D + (1-p)*e*2^i/(2^D-1)) for
+ * i >= 1, e_0 = e - sum of the others.  Every level, level 0 included, is
+ * trained.
+ * g0: device CSR (on_device = 1) or host CSR (on_device = 0, copied in).
+ * M0_out: n x d of params->dtype; device or host memory (host: copied out).
+ * stats: host pointer or NULL.  Synchronous.
+ */
+gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_out,
+                       void *stream, gosh_stats *stats);
+
+/* Scores of vertex pairs, out[i] = M[pairs[2i]] . M[pairs[2i+1]] in FP32.
+ * pairs: device int32[2*npairs]; out: device float[npairs]. */
+gosh_status gosh_pair_scores(const void *M, int d, gosh_dtype dtype, const int32_t *pairs,
+                             int64_t npairs, float *out, void *stream);
+
+/* Link-prediction AUCROC (Sec. 6.1) with dot-product scores: the Mann-Whitney
+ * statistic over the positive and negative pairs, a tie counting 1/2, summed
+ * in FP64.  pos/neg: device int32[2*npos] / [2*nneg].  auc: host double.
+ * Synchronous. */
+gosh_status gosh_link_auc(const void *M, int d, gosh_dtype dtype, const int32_t *pos,
+                          int64_t npos, const int32_t *neg, int64_t nneg, void *stream,
+                          double *auc);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GOSH_H */

@@ -1,0 +1,343 @@
+// MULTIEDGECOLLAPSE (Alg. 4) on the GPU, with maps identical to the
+// sequential greedy algorithm.
+//
+// The greedy walk in degree order makes v a cluster root ("hub") exactly when
+// no earlier-ranked eligible neighbour of v is a hub, i.e. the hubs are the
+// lexicographically-first maximal independent set, in rank order, of the
+// graph of eligible edges (hub^2 restriction: deg(u) <= delta or deg(v) <=
+// delta).  A non-hub is absorbed by the first hub that reaches it, which is
+// its earliest-ranked eligible hub neighbour.  Cluster ids follow hub rank.
+// So one level is:
+//   1. order = stable sort by descending degree (radix sort), rank = order^-1;
+//   2. rounds of the MIS rule until every vertex is decided (each round
+//      decides at least the lowest-ranked undecided vertex; decisions made
+//      earlier in the same round are visible, which usually settles long
+//      dependency chains in a handful of rounds);
+//   3. each non-hub takes its earliest-ranked eligible hub neighbour;
+//      cluster id = number of hubs ranked before the hub (prefix sum);
+//   4. COARSEN: key (map v, map u) per CSR entry, self-loops dropped, radix
+//      sort, unique, CSR of G_{i+1}.
+#include <cmath>
+#include <vector>
+
+#include "hierarchy.cuh"
+
+namespace gosh {
+namespace {
+
+enum : uint8_t { kUndecided = 0, kHub = 1, kNonHub = 2 };
+
+__device__ __forceinline__ bool small_deg(int64_t deg, int64_t n, int64_t nnz) { return deg * n <= nnz; }
+
+__global__ void degree_keys(const int64_t *__restrict__ rowptr, int64_t n, uint32_t *__restrict__ key,
+                            uint32_t *__restrict__ val) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t deg = rowptr[v + 1] - rowptr[v];
+        key[v] = 0xffffffffu - (uint32_t)deg;
+        val[v] = (uint32_t)v;
+    }
+}
+
+__global__ void invert_order(const uint32_t *__restrict__ order, int64_t n, int32_t *__restrict__ rank) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rank[order[i]] = (int32_t)i;
+}
+
+// One MIS round: warp w takes 32 consecutive positions of `order`; the
+// undecided vertices among them are examined one at a time by the whole warp.
+__global__ void __launch_bounds__(256) mis_round(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                 int64_t n, const uint32_t *__restrict__ order,
+                                                 const int32_t *__restrict__ rank, uint8_t *state,
+                                                 unsigned long long *__restrict__ undecided) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nnz = rowptr[n];
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    volatile uint8_t *vstate = state;
+    unsigned long long left = 0;
+    for (int64_t base = wid * 32; base < n; base += wstride * 32) {
+        const int64_t i = base + lane;
+        const int32_t my_v = i < n ? (int32_t)order[i] : -1;
+        const bool mine = my_v >= 0 && vstate[my_v] == kUndecided;
+        uint32_t todo = __ballot_sync(0xffffffffu, mine);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int32_t v = __shfl_sync(0xffffffffu, my_v, src);
+            const int32_t rv = (int32_t)(base + src);
+            const int64_t b = rowptr[v], e = rowptr[v + 1];
+            const bool v_small = small_deg(e - b, n, nnz);
+            bool hub_seen = false, open_seen = false;
+            for (int64_t p = b + lane; p < e; p += 32) {
+                const int32_t u = col[p];
+                if (rank[u] >= rv) continue;
+                if (!(v_small || small_deg(rowptr[u + 1] - rowptr[u], n, nnz))) continue;
+                const uint8_t su = vstate[u];
+                hub_seen |= su == kHub;
+                open_seen |= su == kUndecided;
+            }
+            const bool any_hub = __any_sync(0xffffffffu, hub_seen);
+            const bool any_open = __any_sync(0xffffffffu, open_seen);
+            if (lane == src) {
+                if (any_hub) vstate[v] = kNonHub;
+                else if (!any_open) vstate[v] = kHub;
+                else ++left;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) left += __shfl_xor_sync(0xffffffffu, left, o);
+    if (lane == 0 && left) atomicAdd(undecided, left);
+}
+
+// hub_rank[v] = rank of v for hubs; earliest-ranked eligible hub neighbour for non-hubs.
+__global__ void __launch_bounds__(256) attach_to_hub(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                     int64_t n, const int32_t *__restrict__ rank,
+                                                     const uint8_t *__restrict__ state, int32_t *__restrict__ hub_rank) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nnz = rowptr[n];
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = wid; v < n; v += wstride) {
+        if (state[v] == kHub) {
+            if (lane == 0) hub_rank[v] = rank[v];
+            continue;
+        }
+        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        const bool v_small = small_deg(e - b, n, nnz);
+        int32_t best = 0x7fffffff;
+        for (int64_t p = b + lane; p < e; p += 32) {
+            const int32_t u = col[p];
+            if (state[u] != kHub) continue;
+            if (!(v_small || small_deg(rowptr[u + 1] - rowptr[u], n, nnz))) continue;
+            best = min(best, rank[u]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) hub_rank[v] = best;
+    }
+}
+
+__global__ void hub_flags_by_rank(const uint32_t *__restrict__ order, const uint8_t *__restrict__ state, int64_t n,
+                                  uint8_t *__restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = state[order[i]] == kHub ? 1 : 0;
+}
+
+// A non-hub always has an earlier eligible hub neighbour (maximality); a
+// vertex without one would be a logic error: it is flagged, not followed.
+__global__ void assign_map(const int32_t *__restrict__ hub_rank, const int64_t *__restrict__ cid_of_rank, int64_t n,
+                           int32_t *__restrict__ map, unsigned long long *__restrict__ orphan) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t hr = hub_rank[v];
+        if (hr >= 0 && hr < n) {
+            map[v] = (int32_t)cid_of_rank[hr];
+        } else {
+            map[v] = 0;
+            atomicAdd(orphan, 1ull);
+        }
+    }
+}
+
+// key of every CSR entry: (map v) << 32 | map u, or the sentinel nc << 32 for a self-loop.
+__global__ void __launch_bounds__(256) edge_image(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                  int64_t n, const int32_t *__restrict__ map, uint64_t sentinel,
+                                                  uint64_t *__restrict__ keys) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = wid; v < n; v += wstride) {
+        const uint32_t a = (uint32_t)map[v];
+        for (int64_t p = rowptr[v] + lane; p < rowptr[v + 1]; p += 32) {
+            const uint32_t b = (uint32_t)map[col[p]];
+            keys[p] = a != b ? (((uint64_t)a << 32) | b) : sentinel;
+        }
+    }
+}
+
+__global__ void unique_flags(const uint64_t *__restrict__ keys, int64_t m, uint64_t sentinel, uint8_t *__restrict__ f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = keys[i] != sentinel && (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ f,
+                             const int64_t *__restrict__ pos, int64_t m, int32_t *__restrict__ col_out,
+                             unsigned long long *__restrict__ row_count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        if (f[i]) {
+            col_out[pos[i]] = (int32_t)(keys[i] & 0xffffffffu);
+            atomicAdd(&row_count[keys[i] >> 32], 1ull);
+        }
+}
+
+int grid_1d(int64_t n, int threads = 256) {
+    const int64_t cap = (int64_t)num_sms() * 16;
+    const int64_t g = ceil_div(n > 0 ? n : 1, threads);
+    return (int)(g < cap ? g : cap);
+}
+
+int grid_warps(int64_t nwarps) {
+    const int64_t cap = (int64_t)num_sms() * 8;
+    const int64_t g = ceil_div(nwarps > 0 ? nwarps : 1, 8);
+    return (int)(g < cap ? g : cap);
+}
+
+int bits_for(uint64_t x) {
+    int b = 0;
+    while (b < 64 && (uint64_t(1) << b) <= x) ++b;
+    return b < 1 ? 1 : b;
+}
+
+}  // namespace
+
+// One level: map (device, caller-allocated int32[n]); the coarse CSR is
+// allocated with cudaMalloc into *rp_out / *col_out.  Synchronous.
+gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int64_t nnz, int32_t *map,
+                      int64_t *nc_out, int64_t **rp_out, int32_t **col_out, int64_t *nnz_out, int *rounds_out,
+                      cudaStream_t s) {
+    Scratch keys, vals, rank, state, hub_rank, flags, cid, counter;
+    GOSH_TRY(keys.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(vals.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(rank.alloc(sizeof(int32_t) * n, s));
+    GOSH_TRY(state.alloc(n, s));
+    GOSH_TRY(hub_rank.alloc(sizeof(int32_t) * n, s));
+    GOSH_TRY(flags.alloc(n, s));
+    GOSH_TRY(cid.alloc(sizeof(int64_t) * (n + 1), s));
+    GOSH_TRY(counter.alloc(sizeof(unsigned long long) * 2, s));
+
+    // 1. degree order
+    degree_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>());
+    GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), vals.as<uint32_t>(), n, 0, 32, s));
+    const uint32_t *order = vals.as<uint32_t>();
+    invert_order<<<grid_1d(n), 256, 0, s>>>(order, n, rank.as<int32_t>());
+    GOSH_TRY_CUDA(cudaMemsetAsync(state.ptr, 0, n, s));
+
+    // 2. MIS rounds
+    unsigned long long left = 1;
+    int rounds = 0;
+    while (left > 0) {
+        if (rounds > n + 1) {
+            set_error("coarsening did not settle after %d rounds", rounds);
+            return GOSH_ERR_CUDA;
+        }
+        GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
+        mis_round<<<grid_warps(ceil_div(n, 32)), 256, 0, s>>>(rowptr, col, n, order, rank.as<int32_t>(),
+                                                               state.as<uint8_t>(), counter.as<unsigned long long>());
+        GOSH_TRY_CUDA(cudaMemcpyAsync(&left, counter.ptr, sizeof(left), cudaMemcpyDeviceToHost, s));
+        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+        ++rounds;
+    }
+    if (rounds_out) *rounds_out = rounds;
+
+    // 3. attach non-hubs, number the clusters by hub rank
+    attach_to_hub<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
+                                                 hub_rank.as<int32_t>());
+    hub_flags_by_rank<<<grid_1d(n), 256, 0, s>>>(order, state.as<uint8_t>(), n, flags.as<uint8_t>());
+    GOSH_TRY(scan_exclusive_u8_to_i64(flags.as<uint8_t>(), cid.as<int64_t>(), n, cid.as<int64_t>() + n, s));
+    GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
+    assign_map<<<grid_1d(n), 256, 0, s>>>(hub_rank.as<int32_t>(), cid.as<int64_t>(), n, map,
+                                          counter.as<unsigned long long>());
+    int64_t nc = 0;
+    unsigned long long orphans = 0;
+    GOSH_TRY_CUDA(cudaMemcpyAsync(&nc, cid.as<int64_t>() + n, sizeof(nc), cudaMemcpyDeviceToHost, s));
+    GOSH_TRY_CUDA(cudaMemcpyAsync(&orphans, counter.ptr, sizeof(orphans), cudaMemcpyDeviceToHost, s));
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    if (orphans) {
+        set_error("coarsening: %llu vertices without a cluster root", orphans);
+        return GOSH_ERR_CUDA;
+    }
+    keys.release();
+    vals.release();
+    rank.release();
+    state.release();
+    hub_rank.release();
+    flags.release();
+    cid.release();
+
+    // 4. COARSEN
+    int64_t *rp = nullptr;
+    int32_t *co = nullptr;
+    GOSH_TRY_CUDA(cudaMalloc(&rp, sizeof(int64_t) * (nc + 1)));
+    int64_t m = 0;
+    if (nnz > 0) {
+        Scratch ek, fl, pos, cnt;
+        GOSH_TRY(ek.alloc(sizeof(uint64_t) * nnz, s));
+        GOSH_TRY(fl.alloc(nnz, s));
+        GOSH_TRY(pos.alloc(sizeof(int64_t) * (nnz + 1), s));
+        GOSH_TRY(cnt.alloc(sizeof(unsigned long long) * nc, s));
+        const uint64_t sentinel = (uint64_t)nc << 32;
+        edge_image<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, map, sentinel, ek.as<uint64_t>());
+        int shifts[8];
+        int nd = 0;
+        const int bb = bits_for((uint64_t)(nc > 0 ? nc - 1 : 0)), ba = bits_for((uint64_t)nc);
+        for (int b = 0; b < bb; b += 8) shifts[nd++] = b;
+        for (int b = 0; b < ba; b += 8) shifts[nd++] = 32 + b;
+        GOSH_TRY(radix_sort_u64(ek.as<uint64_t>(), nullptr, nnz, shifts, nd, s));
+        unique_flags<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), nnz, sentinel, fl.as<uint8_t>());
+        GOSH_TRY(scan_exclusive_u8_to_i64(fl.as<uint8_t>(), pos.as<int64_t>(), nnz, pos.as<int64_t>() + nnz, s));
+        GOSH_TRY_CUDA(cudaMemcpyAsync(&m, pos.as<int64_t>() + nnz, sizeof(m), cudaMemcpyDeviceToHost, s));
+        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+        GOSH_TRY_CUDA(cudaMalloc(&co, sizeof(int32_t) * (m > 0 ? m : 1)));
+        GOSH_TRY_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(unsigned long long) * nc, s));
+        write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz, co,
+                                                  cnt.as<unsigned long long>());
+        GOSH_TRY(scan_exclusive_i64(reinterpret_cast<const int64_t *>(cnt.ptr), rp, nc, rp + nc, s));
+        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    } else {
+        GOSH_TRY_CUDA(cudaMalloc(&co, sizeof(int32_t)));
+        GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
+        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    *nc_out = nc;
+    *rp_out = rp;
+    *col_out = co;
+    *nnz_out = m;
+    return GOSH_OK;
+}
+
+gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int max_levels, cudaStream_t s,
+                         gosh_hierarchy **out) {
+    gosh_hierarchy *h = new gosh_hierarchy();
+    int64_t nnz0 = 0;
+    cudaError_t e = cudaMemcpyAsync(&nnz0, g0->rowptr + g0->n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete h;
+        set_error("reading rowptr[n]: %s", cudaGetErrorString(e));
+        return GOSH_ERR_CUDA;
+    }
+    h->n.push_back(g0->n);
+    h->nnz.push_back(nnz0);
+    h->rowptr.push_back(const_cast<int64_t *>(g0->rowptr));
+    h->col.push_back(const_cast<int32_t *>(g0->col));
+    if (max_levels < 2) max_levels = 2;
+    while (true) {
+        const size_t i = h->n.size() - 1;
+        const int64_t n = h->n[i];
+        int32_t *map = nullptr;
+        if (cudaMalloc(&map, sizeof(int32_t) * (n > 0 ? n : 1)) != cudaSuccess) {
+            delete h;
+            set_error("cudaMalloc of map_%zu failed", i);
+            return GOSH_ERR_OOM;
+        }
+        h->map.push_back(map);
+        int64_t nc = 0, m = 0;
+        int64_t *rp = nullptr;
+        int32_t *co = nullptr;
+        gosh_status st = mec_level(n, h->rowptr[i], h->col[i], h->nnz[i], map, &nc, &rp, &co, &m, nullptr, s);
+        if (st != GOSH_OK) {
+            delete h;
+            return st;
+        }
+        h->n.push_back(nc);
+        h->nnz.push_back(m);
+        h->rowptr.push_back(rp);
+        h->col.push_back(co);
+        const bool more = nc > threshold && (double)nc <= std::floor(shrink * (double)n);
+        if (!more || (int)h->n.size() >= max_levels) break;
+    }
+    *out = h;
+    return GOSH_OK;
+}
+
+}  // namespace gosh

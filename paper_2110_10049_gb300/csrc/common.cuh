@@ -1,0 +1,256 @@
+// Shared device/host helpers of libgosh: error reporting, storage-type
+// conversion with stochastic rounding, a device Philox4x64-10, and a
+// stream-ordered scratch buffer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "gosh.h"
+
+namespace gosh {
+
+// ---------------------------------------------------------------------------
+// Errors: a thread-local message plus the status code returned through the ABI.
+// ---------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define GOSH_TRY_CUDA(expr)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::gosh::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr,                 \
+                              cudaGetErrorString(e_));                                   \
+            return e_ == cudaErrorMemoryAllocation ? GOSH_ERR_OOM : GOSH_ERR_CUDA;       \
+        }                                                                                \
+    } while (0)
+
+#define GOSH_TRY(expr)                                                                   \
+    do {                                                                                 \
+        gosh_status s_ = (expr);                                                         \
+        if (s_ != GOSH_OK) return s_;                                                    \
+    } while (0)
+
+#define GOSH_CHECK_ARG(cond, ...)                                                        \
+    do {                                                                                 \
+        if (!(cond)) {                                                                   \
+            ::gosh::set_error(__VA_ARGS__);                                              \
+            return GOSH_ERR_INVALID_ARG;                                                 \
+        }                                                                                \
+    } while (0)
+
+// Stream-ordered device scratch, released on the same stream when it leaves scope.
+struct Scratch {
+    void *ptr = nullptr;
+    cudaStream_t stream = nullptr;
+    Scratch() = default;
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    ~Scratch() { release(); }
+    gosh_status alloc(size_t bytes, cudaStream_t s) {
+        release();
+        stream = s;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            set_error("cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+            return GOSH_ERR_OOM;
+        }
+        return GOSH_OK;
+    }
+    void release() {
+        if (ptr) cudaFreeAsync(ptr, stream);
+        ptr = nullptr;
+    }
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+inline int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+inline size_t dtype_size(gosh_dtype t) { return t == GOSH_F32 ? 4 : 2; }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11): ten rounds of two 64x64->128-bit
+// multiplies; the key is bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct Philox4 {
+    uint64_t w[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                                 uint64_t c3, uint64_t k0, uint64_t k1) {
+    const uint64_t kMul0 = 0xD2E7470EE14C6C93ull, kMul1 = 0xCA5A826395121157ull;
+    const uint64_t kWeyl0 = 0x9E3779B97F4A7C15ull, kWeyl1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0hi = __umul64hi(kMul0, c0), p0lo = kMul0 * c0;
+        const uint64_t p1hi = __umul64hi(kMul1, c2), p1lo = kMul1 * c2;
+        const uint64_t n0 = p1hi ^ c1 ^ k0;
+        const uint64_t n2 = p0hi ^ c3 ^ k1;
+        c0 = n0;
+        c1 = p1lo;
+        c2 = n2;
+        c3 = p0lo;
+        k0 += kWeyl0;
+        k1 += kWeyl1;
+    }
+    Philox4 o;
+    o.w[0] = c0;
+    o.w[1] = c1;
+    o.w[2] = c2;
+    o.w[3] = c3;
+    return o;
+}
+
+// Uniform integer in [0, n): floor(w * n / 2^64).
+__device__ __forceinline__ uint64_t uniform_index(uint64_t w, uint64_t n) { return __umul64hi(w, n); }
+
+enum : uint64_t { kTagSample = 0, kTagInit = 1 };
+
+// 32-bit integer finaliser "lowbias32" (C. Wellons, hash-prospector, public
+// domain): used as a counter-based source of stochastic-rounding bits.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Storage types: 16-byte vectors of T unpacked to / packed from FP32.
+// ---------------------------------------------------------------------------
+template <typename T> struct Store;
+
+template <> struct Store<float> {
+    static constexpr int kPerVec = 4;
+    __device__ __forceinline__ static void unpack(const uint4 &v, float *f) {
+        f[0] = __uint_as_float(v.x);
+        f[1] = __uint_as_float(v.y);
+        f[2] = __uint_as_float(v.z);
+        f[3] = __uint_as_float(v.w);
+    }
+    // Exact store; `f` already holds the stored values.
+    __device__ __forceinline__ static uint4 pack(float *f, uint32_t /*rnd_seed*/, uint32_t /*base*/) {
+        return make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]),
+                          __float_as_uint(f[3]));
+    }
+    __device__ __forceinline__ static float round_nearest(float x) { return x; }
+};
+
+// BF16 stochastic rounding: add 16 random bits below the BF16 mantissa of the
+// FP32 pattern, then truncate.  Rounds |x| up with probability equal to its
+// distance from the lower neighbour (unbiased); NaN/Inf are truncated.
+__device__ __forceinline__ uint32_t bf16_sr_bits(float x, uint32_t r16) {
+    uint32_t b = __float_as_uint(x);
+    if ((b & 0x7f800000u) != 0x7f800000u) b += (r16 & 0xffffu);
+    return b >> 16;
+}
+
+template <> struct Store<__nv_bfloat16> {
+    static constexpr int kPerVec = 8;
+    __device__ __forceinline__ static void unpack(const uint4 &v, float *f) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            f[2 * i] = __uint_as_float(w[i] << 16);
+            f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+    // Stochastic rounding with bits mix32(seed + base + i/2) (two 16-bit halves
+    // per word); `f` is overwritten with the stored values.
+    __device__ __forceinline__ static uint4 pack(float *f, uint32_t seed, uint32_t base) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t r = mix32(seed + base + (uint32_t)i);
+            const uint32_t lo = bf16_sr_bits(f[2 * i], r & 0xffffu);
+            const uint32_t hi = bf16_sr_bits(f[2 * i + 1], r >> 16);
+            w[i] = lo | (hi << 16);
+            f[2 * i] = __uint_as_float(lo << 16);
+            f[2 * i + 1] = __uint_as_float(hi << 16);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __device__ __forceinline__ static float round_nearest(float x) {
+        return __bfloat162float(__float2bfloat16_rn(x));
+    }
+};
+
+// FP16 stochastic rounding: between the toward-zero neighbour and the next
+// value away from zero, pick the upper one with probability proportional to
+// the distance (16-bit resolution).
+__device__ __forceinline__ uint32_t f16_sr_bits(float x, uint32_t r16) {
+    const __half t = __float2half_rz(x);
+    const uint16_t tb = __half_as_ushort(t);
+    if ((tb & 0x7c00u) == 0x7c00u) return tb;  // inf / nan
+    const float lo = __half2float(t);
+    const __half u = __ushort_as_half((uint16_t)(tb + 1));
+    const float hi = __half2float(u);
+    const float frac = (fabsf(x) - fabsf(lo)) / (fabsf(hi) - fabsf(lo));
+    return ((float)(r16 & 0xffffu) * (1.0f / 65536.0f) < frac) ? (uint32_t)(tb + 1) : (uint32_t)tb;
+}
+
+template <> struct Store<__half> {
+    static constexpr int kPerVec = 8;
+    __device__ __forceinline__ static void unpack(const uint4 &v, float *f) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            f[2 * i] = __half2float(__ushort_as_half((uint16_t)(w[i] & 0xffffu)));
+            f[2 * i + 1] = __half2float(__ushort_as_half((uint16_t)(w[i] >> 16)));
+        }
+    }
+    __device__ __forceinline__ static uint4 pack(float *f, uint32_t seed, uint32_t base) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t r = mix32(seed + base + (uint32_t)i);
+            const uint32_t lo = f16_sr_bits(f[2 * i], r & 0xffffu);
+            const uint32_t hi = f16_sr_bits(f[2 * i + 1], r >> 16);
+            w[i] = lo | (hi << 16);
+            f[2 * i] = __half2float(__ushort_as_half((uint16_t)lo));
+            f[2 * i + 1] = __half2float(__ushort_as_half((uint16_t)hi));
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __device__ __forceinline__ static float round_nearest(float x) {
+        return __half2float(__float2half_rn(x));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Device primitives (primitives.cu).
+// ---------------------------------------------------------------------------
+// Exclusive prefix sum of n values; `total` (device, nullable) receives the sum.
+gosh_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
+                               cudaStream_t s);
+gosh_status scan_exclusive_u8_to_i64(const uint8_t *in, int64_t *out, int64_t n,
+                                     int64_t *total, cudaStream_t s);
+gosh_status scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n,
+                                      int64_t *total, cudaStream_t s);
+
+// Stable LSD radix sort on the bit ranges [lo_bits[i], hi_bits[i]) of the key.
+// keys/vals are sorted in place (vals may be null); scratch is taken internally.
+gosh_status radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit,
+                           cudaStream_t s);
+gosh_status radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, const int *digit_bits,
+                           int ndigits, cudaStream_t s);
+
+}  // namespace gosh

@@ -1,0 +1,21 @@
+// The coarsening hierarchy behind the opaque gosh_hierarchy handle.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+// Level 0 aliases the caller's CSR; levels >= 1 and every map are owned.
+struct gosh_hierarchy {
+    std::vector<int64_t> n, nnz;
+    std::vector<int64_t *> rowptr;
+    std::vector<int32_t *> col;
+    std::vector<int32_t *> map;  // map[i]: G_i -> G_{i+1}
+    ~gosh_hierarchy() {
+        for (size_t i = 1; i < rowptr.size(); ++i) {
+            cudaFree(rowptr[i]);
+            cudaFree(col[i]);
+        }
+        for (int32_t *m : map) cudaFree(m);
+    }
+};

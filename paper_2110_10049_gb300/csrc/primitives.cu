@@ -1,0 +1,250 @@
+// Device primitives of libgosh: exclusive prefix sums and a stable LSD radix
+// sort.  Both are deterministic (no atomics decide any output position), which
+// the bit-exact coarsening and the fixed-order reduction of the deterministic
+// training mode rely on.
+#include "common.cuh"
+
+namespace gosh {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Block-wide exclusive scan of one int64 per thread; returns the block total.
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t *smem_warp, int64_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) smem_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int64_t w = lane < nw ? smem_warp[lane] : 0;
+        int64_t winc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, winc, o);
+            if (lane >= o) winc += y;
+        }
+        if (lane < nw) smem_warp[lane] = winc - w;
+        if (lane == 31) smem_warp[32] = winc;
+    }
+    __syncthreads();
+    const int64_t excl = smem_warp[warp] + inc - x;
+    total = smem_warp[32];
+    return excl;
+}
+
+template <typename In>
+__global__ void scan_tile_sums(const In *__restrict__ in, int64_t n, int64_t *__restrict__ sums) {
+    __shared__ int64_t sw[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < n) s += (int64_t)in[base + j];
+    int64_t total;
+    block_exclusive_scan(s, sw, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+template <typename In>
+__global__ void scan_tile_apply(const In *__restrict__ in, int64_t *__restrict__ out, int64_t n,
+                                const int64_t *__restrict__ tile_offsets) {
+    __shared__ int64_t sw[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = base + j < n ? (int64_t)in[base + j] : 0;
+        s += v[j];
+    }
+    int64_t total;
+    int64_t run = block_exclusive_scan(s, sw, total) + (tile_offsets ? tile_offsets[blockIdx.x] : 0);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += v[j];
+    }
+}
+
+template <typename In>
+__global__ void write_total_t(const In *__restrict__ in, const int64_t *__restrict__ out, int64_t n,
+                              int64_t *__restrict__ total) {
+    *total = n > 0 ? out[n - 1] + (int64_t)in[n - 1] : 0;
+}
+
+template <typename In>
+gosh_status scan_exclusive(const In *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s) {
+    if (n <= 0) {
+        if (total) GOSH_TRY_CUDA(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
+        return GOSH_OK;
+    }
+    const int64_t tiles = ceil_div(n, kScanTile);
+    if (tiles == 1) {
+        scan_tile_apply<In><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    } else {
+        Scratch sums, offs;
+        GOSH_TRY(sums.alloc(sizeof(int64_t) * tiles, s));
+        GOSH_TRY(offs.alloc(sizeof(int64_t) * tiles, s));
+        scan_tile_sums<In><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>());
+        GOSH_TRY(scan_exclusive<int64_t>(sums.as<int64_t>(), offs.as<int64_t>(), tiles, nullptr, s));
+        scan_tile_apply<In><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, offs.as<int64_t>());
+    }
+    if (total) write_total_t<In><<<1, 1, 0, s>>>(in, out, n, total);
+    GOSH_TRY_CUDA(cudaGetLastError());
+    return GOSH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort: 8-bit digits, 256 threads x 8 keys per tile.  Warp w of a tile
+// owns keys [w*256, w*256+256) of the tile, taken 32 at a time in index order,
+// so (warp, step, lane) order is index order and the scatter is stable.
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortWarps = kSortThreads / 32;
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) radix_hist(const K *__restrict__ keys, int64_t n,
+                                                           int shift, int64_t *__restrict__ counts,
+                                                           int64_t nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + warp * 256 + lane;
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + i * 32;
+        if (idx < n) atomicAdd(&h[(uint32_t)(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename K, bool kVals>
+__global__ void __launch_bounds__(kSortThreads) radix_scatter(
+    const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t n, int shift, const int64_t *__restrict__ offsets,
+    int64_t nblocks) {
+    __shared__ uint32_t wcnt[kSortWarps][256];
+    __shared__ int64_t gbase[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) wcnt[w][threadIdx.x] = 0;
+    gbase[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    __syncthreads();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + warp * 256 + lane;
+    K key[kSortItems];
+    uint32_t val[kSortItems];
+    uint32_t rank[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + i * 32;
+        const bool ok = idx < n;
+        key[i] = ok ? kin[idx] : K(0);
+        if (kVals) val[i] = ok ? vin[idx] : 0u;
+        const uint32_t digit = ok ? ((uint32_t)(key[i] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        uint32_t pre = 0;
+        if (ok) pre = wcnt[warp][digit];
+        __syncwarp();
+        if (ok && (peers & lt_mask) == 0) wcnt[warp][digit] = pre + __popc(peers);
+        __syncwarp();
+        rank[i] = pre + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + i * 32;
+        if (idx < n) {
+            const uint32_t digit = (uint32_t)(key[i] >> shift) & 255u;
+            const int64_t pos = gbase[digit] + wcnt[warp][digit] + rank[i];
+            kout[pos] = key[i];
+            if (kVals) vout[pos] = val[i];
+        }
+    }
+}
+
+template <typename K>
+gosh_status radix_sort(K *keys, uint32_t *vals, int64_t n, const int *shifts, int ndigits,
+                       cudaStream_t s) {
+    if (n <= 1 || ndigits == 0) return GOSH_OK;
+    const int64_t nblocks = ceil_div(n, kSortTile);
+    Scratch kalt, valt, counts, offs;
+    GOSH_TRY(kalt.alloc(sizeof(K) * n, s));
+    if (vals) GOSH_TRY(valt.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(counts.alloc(sizeof(int64_t) * 256 * nblocks, s));
+    GOSH_TRY(offs.alloc(sizeof(int64_t) * 256 * nblocks, s));
+    K *ka = keys, *kb = kalt.as<K>();
+    uint32_t *va = vals, *vb = valt.as<uint32_t>();
+    for (int d = 0; d < ndigits; ++d) {
+        radix_hist<K><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, n, shifts[d], counts.as<int64_t>(),
+                                                                  nblocks);
+        GOSH_TRY(scan_exclusive<int64_t>(counts.as<int64_t>(), offs.as<int64_t>(), 256 * nblocks,
+                                         nullptr, s));
+        if (vals)
+            radix_scatter<K, true><<<(unsigned)nblocks, kSortThreads, 0, s>>>(
+                ka, va, kb, vb, n, shifts[d], offs.as<int64_t>(), nblocks);
+        else
+            radix_scatter<K, false><<<(unsigned)nblocks, kSortThreads, 0, s>>>(
+                ka, nullptr, kb, nullptr, n, shifts[d], offs.as<int64_t>(), nblocks);
+        GOSH_TRY_CUDA(cudaGetLastError());
+        K *kt = ka; ka = kb; kb = kt;
+        uint32_t *vt = va; va = vb; vb = vt;
+    }
+    if (ka != keys) {
+        GOSH_TRY_CUDA(cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
+        if (vals) GOSH_TRY_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return GOSH_OK;
+}
+
+}  // namespace
+
+gosh_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
+                               cudaStream_t s) {
+    return scan_exclusive<int64_t>(in, out, n, total, s);
+}
+gosh_status scan_exclusive_u8_to_i64(const uint8_t *in, int64_t *out, int64_t n, int64_t *total,
+                                     cudaStream_t s) {
+    return scan_exclusive<uint8_t>(in, out, n, total, s);
+}
+gosh_status scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *total,
+                                      cudaStream_t s) {
+    return scan_exclusive<int32_t>(in, out, n, total, s);
+}
+
+gosh_status radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit,
+                           cudaStream_t s) {
+    int shifts[4];
+    int nd = 0;
+    for (int b = begin_bit; b < end_bit && nd < 4; b += 8) shifts[nd++] = b;
+    return radix_sort<uint32_t>(keys, vals, n, shifts, nd, s);
+}
+
+gosh_status radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, const int *shifts,
+                           int ndigits, cudaStream_t s) {
+    return radix_sort<uint64_t>(keys, vals, n, shifts, ndigits, s);
+}
+
+}  // namespace gosh

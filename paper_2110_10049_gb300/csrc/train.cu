@@ -1,0 +1,216 @@
+// Host side of the training step: variant registry, the epoch loop of Alg. 3
+// (one launch per epoch, so epochs are serialised as Sec. 3.1 requires) and the
+// batch loop of the deterministic mode.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "train.cuh"
+
+namespace gosh {
+namespace {
+
+struct Registry {
+    std::vector<TrainEntry> entries;
+    std::vector<TrainKernel> made;
+    std::vector<bool> ready;
+    std::mutex mu;
+    Registry() {
+        int c = 0;
+        const TrainEntry *e = train_entries_f32(&c);
+        entries.insert(entries.end(), e, e + c);
+        e = train_entries_bf16(&c);
+        entries.insert(entries.end(), e, e + c);
+        e = train_entries_f16(&c);
+        entries.insert(entries.end(), e, e + c);
+        made.resize(entries.size());
+        ready.assign(entries.size(), false);
+    }
+};
+
+Registry &registry() {
+    static Registry r;
+    return r;
+}
+
+__global__ void loss_finalize(const double *__restrict__ parts, int nparts, double *__restrict__ out,
+                              int accumulate) {
+    __shared__ double s[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 256) t += parts[i];
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = accumulate ? *out + s[0] : s[0];
+}
+
+__global__ void iota_u32(uint32_t *__restrict__ p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (uint32_t)i;
+}
+
+int bits_for(int64_t x) {  // bits needed to hold values 0..x
+    int b = 0;
+    while (b < 63 && (int64_t(1) << b) <= x) ++b;
+    return b < 1 ? 1 : b;
+}
+
+void det_apply(gosh_dtype dtype, int d, const uint32_t *skeys, const uint32_t *sidx, int64_t nslots,
+               const float *C, const float *R, void *M, int64_t n, int64_t b0, int64_t b1,
+               uint8_t *src_done, uint32_t sr_seed, cudaStream_t s) {
+    if (dtype == GOSH_F32) det_apply_f32(d, skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s);
+    else if (dtype == GOSH_BF16) det_apply_bf16(d, skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s);
+    else det_apply_f16(d, skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s);
+}
+
+}  // namespace
+
+const TrainKernel *find_train_kernel(gosh_dtype dtype, int d, int lanes, int pass, bool det) {
+    Registry &r = registry();
+    std::lock_guard<std::mutex> lock(r.mu);
+    for (size_t i = 0; i < r.entries.size(); ++i) {
+        const TrainEntry &e = r.entries[i];
+        if (e.dtype == dtype && e.d == d && e.lanes == lanes && e.pass == pass && e.det == det) {
+            if (!r.ready[i]) {
+                r.made[i] = e.make();
+                r.ready[i] = true;
+            }
+            return &r.made[i];
+        }
+    }
+    return nullptr;
+}
+
+int list_train_variants(gosh_dtype dtype, int d, bool det, int *lanes, int *pass, int cap) {
+    Registry &r = registry();
+    int c = 0;
+    for (const TrainEntry &e : r.entries)
+        if (e.dtype == dtype && e.d == d && e.det == det && c < cap) {
+            lanes[c] = e.lanes;
+            pass[c] = e.pass;
+            ++c;
+        }
+    return c;
+}
+
+// Natural lanes per row: one 16-byte vector per lane.
+int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) / 16; }
+
+gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, bool det, int lanes, int pass,
+                              const TrainKernel **out) {
+    const int ns = k + 1;
+    if (lanes <= 0) lanes = natural_lanes(dtype, d);
+    if (pass <= 0) pass = det ? (ns <= 4 ? 4 : 8) : (ns <= 2 ? 2 : 4);
+    if (det && pass < ns) {
+        set_error("deterministic mode gathers all k+1 samples in one pass: samples_per_pass %d < k+1 = %d",
+                  pass, ns);
+        return GOSH_ERR_UNSUPPORTED;
+    }
+    const TrainKernel *kern = find_train_kernel(dtype, d, lanes, pass, det);
+    if (!kern) {
+        set_error("no training kernel for dtype %d, d %d, lanes_per_row %d, samples_per_pass %d, %s",
+                  (int)dtype, d, lanes, pass, det ? "deterministic" : "hogwild");
+        return GOSH_ERR_UNSUPPORTED;
+    }
+    *out = kern;
+    return GOSH_OK;
+}
+
+gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, const gosh_params *p,
+                             cudaStream_t s, double *loss_per_epoch, unsigned long long *n_updates) {
+    const bool det = p->mode == GOSH_DETERMINISTIC;
+    if (p->k > 7 && det) {
+        set_error("deterministic mode supports k <= 7 (got %d)", p->k);
+        return GOSH_ERR_UNSUPPORTED;
+    }
+    const TrainKernel *kern = nullptr;
+    GOSH_TRY(pick_train_kernel(p->dtype, p->d, p->k, det, p->lanes_per_row, p->samples_per_pass, &kern));
+    const int64_t n = g->n;
+    if (epochs <= 0 || n <= 0) return GOSH_OK;
+    const int ns = p->k + 1;
+    const int cap_blocks = num_sms() * kern->blocks_per_sm;
+
+    TrainArgs a{};
+    a.rowptr = g->rowptr;
+    a.col = g->col;
+    a.M = M;
+    a.n = n;
+    a.k = p->k;
+    a.seed = p->seed;
+    a.graph = p->graph_id;
+    a.level = (uint32_t)level;
+    a.n_updates = n_updates;
+
+    auto grid_for = [&](int64_t nsrc) {
+        const int64_t tiles = ceil_div(nsrc, 32);
+        const int64_t want = ceil_div(tiles, kTrainWarps);
+        return (int)(want < cap_blocks ? (want > 0 ? want : 1) : cap_blocks);
+    };
+
+    Scratch parts;
+    if (loss_per_epoch) GOSH_TRY(parts.alloc(sizeof(double) * cap_blocks, s));
+    a.loss_partials = loss_per_epoch ? parts.as<double>() : nullptr;
+
+    if (!det) {
+        const int grid = grid_for(n);
+        a.src_begin = 0;
+        a.src_end = n;
+        for (int j = 0; j < epochs; ++j) {
+            const double f = 1.0 - (double)j / (double)epochs;
+            a.lr = (float)(p->lr * (f > p->lr_floor ? f : p->lr_floor));
+            a.epoch = (uint32_t)j;
+            kern->launch(a, grid, s);
+            if (loss_per_epoch)
+                loss_finalize<<<1, 256, 0, s>>>(parts.as<double>(), grid, loss_per_epoch + j, 0);
+        }
+        GOSH_TRY_CUDA(cudaGetLastError());
+        return GOSH_OK;
+    }
+
+    // deterministic: snapshot batches of m consecutive sources
+    const int64_t m = p->det_batch > 0 ? (p->det_batch < n ? p->det_batch : n) : n;
+    const int64_t slots = m * ns;
+    if (slots >= (int64_t(1) << 32)) {
+        set_error("det_batch * (k+1) must stay below 2^32");
+        return GOSH_ERR_INVALID_ARG;
+    }
+    Scratch R, C, keys, idx, done;
+    GOSH_TRY(R.alloc(sizeof(float) * m * p->d, s));
+    GOSH_TRY(C.alloc(sizeof(float) * slots * p->d, s));
+    GOSH_TRY(keys.alloc(sizeof(uint32_t) * slots, s));
+    GOSH_TRY(idx.alloc(sizeof(uint32_t) * slots, s));
+    GOSH_TRY(done.alloc(m, s));
+    a.R = R.as<float>();
+    a.C = C.as<float>();
+    a.keys = keys.as<uint32_t>();
+    const int kbits = bits_for(n);
+    for (int j = 0; j < epochs; ++j) {
+        const double f = 1.0 - (double)j / (double)epochs;
+        a.lr = (float)(p->lr * (f > p->lr_floor ? f : p->lr_floor));
+        a.epoch = (uint32_t)j;
+        for (int64_t b0 = 0; b0 < n; b0 += m) {
+            const int64_t b1 = b0 + m < n ? b0 + m : n;
+            const int64_t nsl = (b1 - b0) * ns;
+            a.src_begin = b0;
+            a.src_end = b1;
+            const int grid = grid_for(b1 - b0);
+            kern->launch(a, grid, s);
+            if (loss_per_epoch)
+                loss_finalize<<<1, 256, 0, s>>>(parts.as<double>(), grid, loss_per_epoch + j, b0 > 0);
+            iota_u32<<<(int)std::min<int64_t>(ceil_div(nsl, 256), 4096), 256, 0, s>>>(idx.as<uint32_t>(), nsl);
+            GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), idx.as<uint32_t>(), nsl, 0, kbits, s));
+            GOSH_TRY_CUDA(cudaMemsetAsync(done.ptr, 0, (size_t)(b1 - b0), s));
+            const uint32_t sr = mix32((uint32_t)p->seed ^ mix32((uint32_t)(level << 20) ^ (uint32_t)j)) ^
+                                mix32((uint32_t)(b0 >> 5));
+            det_apply(p->dtype, p->d, keys.as<uint32_t>(), idx.as<uint32_t>(), nsl, C.as<float>(), R.as<float>(),
+                      M, n, b0, b1, done.as<uint8_t>(), sr, s);
+        }
+    }
+    GOSH_TRY_CUDA(cudaGetLastError());
+    return GOSH_OK;
+}
+
+}  // namespace gosh

@@ -1,0 +1,83 @@
+// Training-step kernels of libgosh (Alg. 1 inside the epoch loop of Alg. 3).
+//
+// Mapping (GB300): a warp takes a tile of 32 consecutive sources.  First each
+// lane draws the samples of one source of the tile (one Philox4x64-10 block
+// per four samples, computed once per source instead of once per lane of the
+// row) and parks the sample ids in shared memory.  Then the warp walks the
+// tile in rounds: L lanes share one source (G = 32/L sources per round); each
+// lane owns E = D/L contiguous elements of every row and moves them with
+// 16-byte loads/stores.  The source row stays in registers across its k+1
+// updates (the paper stages it in shared memory); the sample rows of one pass
+// (P of them) are gathered together before any arithmetic so that their loads
+// overlap; dot products are reduced with xor-shuffles inside the L-lane group.
+#pragma once
+
+#include "common.cuh"
+
+namespace gosh {
+
+constexpr int kMaxK = 15;        // negatives per positive
+constexpr int kTrainWarps = 8;   // warps per block
+constexpr int kSlotStride = kMaxK + 2;  // padded per-source sample-id slots in smem
+
+struct TrainArgs {
+    const int64_t *rowptr;
+    const int32_t *col;
+    void *M;
+    int64_t n;                 // |V_i|
+    int k;                     // negatives per positive
+    uint64_t seed, graph;      // Philox key
+    uint32_t level, epoch;     // Philox counter word 2 = level << 32 | epoch
+    float lr;                  // lr' of this epoch
+    int64_t src_begin, src_end;
+    // deterministic mode (snapshot batch [src_begin, src_end))
+    float *R;                  // [(src_end-src_begin) x D]  final source rows
+    float *C;                  // [(src_end-src_begin)*(k+1) x D] sample-row changes
+    uint32_t *keys;            // [(src_end-src_begin)*(k+1)] target row or n (skipped)
+    // monitors
+    double *loss_partials;     // [gridDim.x] or null
+    unsigned long long *n_updates;  // or null
+};
+
+// Host-side launcher for one epoch (Hogwild) or one snapshot batch (deterministic).
+struct TrainKernel {
+    void (*launch)(const TrainArgs &, int grid, cudaStream_t);
+    int blocks_per_sm;
+    int lanes;     // L
+    int pass;      // P
+};
+
+// One compiled variant: its key and a factory (the factory queries occupancy,
+// so it runs lazily once a device is current).
+struct TrainEntry {
+    gosh_dtype dtype;
+    int d, lanes, pass;
+    bool det;
+    TrainKernel (*make)();
+};
+const TrainEntry *train_entries_f32(int *count);
+const TrainEntry *train_entries_bf16(int *count);
+const TrainEntry *train_entries_f16(int *count);
+void det_apply_f32(int d, const uint32_t *skeys, const uint32_t *sidx, int64_t nslots, const float *C,
+                   const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
+                   uint32_t sr_seed, cudaStream_t s);
+void det_apply_bf16(int d, const uint32_t *skeys, const uint32_t *sidx, int64_t nslots, const float *C,
+                    const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
+                    uint32_t sr_seed, cudaStream_t s);
+void det_apply_f16(int d, const uint32_t *skeys, const uint32_t *sidx, int64_t nslots, const float *C,
+                   const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
+                   uint32_t sr_seed, cudaStream_t s);
+
+// Looks up the kernel for (dtype, d, lanes-per-row, samples-per-pass, det).
+// Returns nullptr if that combination is not compiled.
+const TrainKernel *find_train_kernel(gosh_dtype dtype, int d, int lanes, int pass, bool det);
+
+// Lists the lanes-per-row and samples-per-pass variants compiled for (dtype, d, det).
+int list_train_variants(gosh_dtype dtype, int d, bool det, int *lanes, int *pass, int cap);
+
+// Deterministic-mode end-of-batch kernels.
+void launch_det_apply(gosh_dtype dtype, int d, const uint32_t *skeys, const uint32_t *sidx,
+                      int64_t nslots, const float *C, const float *R, void *M, int64_t n,
+                      int64_t b0, int64_t b1, uint8_t *src_done, uint32_t sr_seed, cudaStream_t s);
+
+}  // namespace gosh

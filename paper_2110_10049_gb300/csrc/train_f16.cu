@@ -1,0 +1,38 @@
+// Training-step kernel instantiations for f16 storage.
+#include "train_kernels.cuh"
+
+namespace gosh {
+namespace {
+using T = __half;
+constexpr int L32 = 32 * (int)sizeof(T) / 16;
+constexpr int L64 = 64 * (int)sizeof(T) / 16;
+constexpr int L128 = 128 * (int)sizeof(T) / 16;
+constexpr gosh_dtype kType = GOSH_F16;
+
+#define GOSH_V(D, L, P, DET) {kType, D, L, P, DET, &make_train_kernel<T, D, L, P, DET>}
+#define GOSH_VD(D, L0)                                                                     \
+    GOSH_V(D, L0, 2, false), GOSH_V(D, L0, 4, false), GOSH_V(D, (L0 > 1 ? L0 / 2 : 1), 2, false), \
+        GOSH_V(D, (L0 > 1 ? L0 / 2 : 1), 4, false), GOSH_V(D, L0, 4, true), GOSH_V(D, L0, 8, true)
+
+const TrainEntry kEntries[] = {GOSH_VD(32, L32), GOSH_VD(64, L64), GOSH_VD(128, L128)};
+#undef GOSH_VD
+#undef GOSH_V
+}  // namespace
+
+const TrainEntry *train_entries_f16(int *count) {
+    *count = (int)(sizeof(kEntries) / sizeof(kEntries[0]));
+    return kEntries;
+}
+
+void det_apply_f16(int d, const uint32_t *skeys, const uint32_t *sidx, int64_t nslots, const float *C,
+                  const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
+                  uint32_t sr_seed, cudaStream_t s) {
+    switch (d) {
+    case 32: launch_det_apply_t<T, 32>(skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s); break;
+    case 64: launch_det_apply_t<T, 64>(skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s); break;
+    case 128: launch_det_apply_t<T, 128>(skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s); break;
+    default: break;
+    }
+}
+
+}  // namespace gosh

@@ -1,0 +1,333 @@
+// Kernel templates of the training step; instantiated per storage type in
+// train_f32.cu, train_bf16.cu and train_f16.cu.
+#pragma once
+
+#include <type_traits>
+
+#include "train.cuh"
+
+namespace gosh {
+
+// Stochastic-rounding seed of one source in one epoch.
+__device__ __forceinline__ uint32_t sr_source_seed(uint64_t seed, uint64_t graph, uint32_t level,
+                                                   uint32_t epoch, int64_t v) {
+    uint32_t h = mix32((uint32_t)v ^ mix32((uint32_t)((uint64_t)v >> 32)));
+    h = mix32(h ^ (level << 20) ^ epoch);
+    h = mix32(h ^ (uint32_t)graph ^ mix32((uint32_t)(graph >> 32)));
+    h = mix32(h ^ (uint32_t)seed ^ mix32((uint32_t)(seed >> 32)));
+    return h;
+}
+
+__device__ __forceinline__ float softplus_f(float z) {
+    return fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)));
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void load_row(const T *__restrict__ p, float *f) {
+    constexpr int PV = Store<T>::kPerVec;
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int v = 0; v < E / PV; ++v) Store<T>::unpack(__ldcg(q + v), f + v * PV);
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void load_row_snapshot(const T *__restrict__ p, float *f) {
+    constexpr int PV = Store<T>::kPerVec;
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+    for (int v = 0; v < E / PV; ++v) Store<T>::unpack(__ldg(q + v), f + v * PV);
+}
+
+// Stores E elements starting at element `elem0` of row-slot `slot`; f is
+// replaced by the stored (rounded) values.
+template <typename T, int D, int E>
+__device__ __forceinline__ void store_row(T *__restrict__ p, float *f, uint32_t sr, int slot, int elem0) {
+    constexpr int PV = Store<T>::kPerVec;
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+    for (int v = 0; v < E / PV; ++v) {
+        const uint32_t base = (uint32_t)((slot * D + elem0 + v * PV) >> 1);
+        q[v] = Store<T>::pack(f + v * PV, sr, base);
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void store_f32(float *__restrict__ p, const float *f) {
+    float4 *q = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int v = 0; v < E / 4; ++v) q[v] = make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+}
+
+template <int L>
+__device__ __forceinline__ float group_sum(float x) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+/*
+ * One epoch (Hogwild) or one snapshot batch (DET) over sources
+ * [src_begin, src_end).  Template: storage T, dimension D, L lanes per source,
+ * P sample rows gathered per pass.  DET requires P >= k+1 (one pass).
+ */
+template <typename T, int D, int L, int P, bool DET>
+__global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
+    constexpr int E = D / L;
+    constexpr int PV = Store<T>::kPerVec;
+    constexpr int G = 32 / L;
+    static_assert(E % PV == 0, "lane slice must be whole 16-byte vectors");
+    static_assert(32 % L == 0, "L must divide the warp");
+    static_assert(!DET || E % 4 == 0, "float4 stores of the change buffers");
+
+    __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
+    __shared__ uint32_t s_sr[kTrainWarps][32];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / L, gl = lane % L;
+    const int ns = a.k + 1;
+    const int64_t nsrc = a.src_end - a.src_begin;
+    const int64_t ntiles = (nsrc + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * kTrainWarps;
+    T *__restrict__ M = static_cast<T *>(a.M);
+    const uint64_t ctr2 = ((uint64_t)a.level << 32) | a.epoch;
+    const bool want_loss = a.loss_partials != nullptr;
+    double loss_acc = 0.0;
+    unsigned long long applied = 0;
+
+    for (int64_t tile = (int64_t)blockIdx.x * kTrainWarps + warp; tile < ntiles; tile += wstride) {
+        const int64_t v0 = a.src_begin + tile * 32;
+        // ---- draws: lane j -> source v0 + j ----
+        {
+            const int64_t v = v0 + lane;
+            if (v < a.src_end) {
+                const int64_t off = a.rowptr[v];
+                const int64_t deg = a.rowptr[v + 1] - off;
+                for (int blk = 0; blk * 4 < ns; ++blk) {
+                    const Philox4 w = philox4x64_10((uint64_t)v, (uint64_t)blk, ctr2, kTagSample, a.seed, a.graph);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int t = blk * 4 + j;
+                        if (t < ns) {
+                            int32_t u;
+                            if (t == 0) {
+                                u = deg > 0 ? __ldg(a.col + off + (int64_t)uniform_index(w.w[0], (uint64_t)deg)) : -1;
+                            } else {
+                                const int64_t x = (int64_t)uniform_index(w.w[j], (uint64_t)a.n);
+                                u = x == v ? -1 : (int32_t)x;
+                            }
+                            s_u[warp][lane * kSlotStride + t] = u;
+                        }
+                    }
+                }
+                if (!std::is_same<T, float>::value)
+                    s_sr[warp][lane] = sr_source_seed(a.seed, a.graph, a.level, a.epoch, v);
+            }
+        }
+        __syncwarp();
+        // ---- rounds: G sources at a time, L lanes each ----
+#pragma unroll 1
+        for (int q = 0; q < L; ++q) {
+            const int j = q * G + grp;
+            const int64_t v = v0 + j;
+            const bool active = v < a.src_end;
+            const uint32_t sr = std::is_same<T, float>::value ? 0u : s_sr[warp][j];
+            float r[E];
+            if (active) {
+                if (DET) load_row_snapshot<T, E>(M + v * D + gl * E, r);
+                else load_row<T, E>(M + v * D + gl * E, r);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) r[e] = 0.0f;
+            }
+#pragma unroll 1
+            for (int p0 = 0; p0 < ns; p0 += P) {
+                int32_t us[P];
+                float row[P][E];
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    const int t = p0 + s;
+                    us[s] = (active && t < ns) ? s_u[warp][j * kSlotStride + t] : -1;
+                }
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    if (us[s] >= 0) {
+                        if (DET) load_row_snapshot<T, E>(M + (int64_t)us[s] * D + gl * E, row[s]);
+                        else load_row<T, E>(M + (int64_t)us[s] * D + gl * E, row[s]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) row[s][e] = 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    const int t = p0 + s;
+                    const bool ok = us[s] >= 0;
+                    float part = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) part = fmaf(r[e], row[s][e], part);
+                    const float x = group_sum<L>(part);
+                    const float b = t == 0 ? 1.0f : 0.0f;
+                    const float sig = __frcp_rn(1.0f + __expf(-x));
+                    const float score = ok ? (b - sig) * a.lr : 0.0f;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) r[e] = fmaf(row[s][e], score, r[e]);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) row[s][e] = fmaf(r[e], score, row[s][e]);
+                    if (ok) {
+                        if (DET) {
+                            const int64_t slot = (v - a.src_begin) * ns + t;
+                            float c[E];
+#pragma unroll
+                            for (int e = 0; e < E; ++e) c[e] = r[e] * score;
+                            store_f32<E>(a.C + slot * D + gl * E, c);
+                            if (gl == 0) a.keys[slot] = (uint32_t)us[s];
+                        } else {
+                            store_row<T, D, E>(M + (int64_t)us[s] * D + gl * E, row[s], sr, t, gl * E);
+                        }
+                        if (gl == 0) {
+                            ++applied;
+                            if (want_loss) loss_acc += (double)softplus_f(t == 0 ? -x : x);
+                        }
+                    } else if (DET && active && t < ns && gl == 0) {
+                        a.keys[(v - a.src_begin) * ns + t] = (uint32_t)a.n;
+                    }
+                    // a later sample of this pass with the same id continues from this row
+#pragma unroll
+                    for (int s2 = s + 1; s2 < P; ++s2) {
+                        if (ok && us[s2] == us[s]) {
+#pragma unroll
+                            for (int e = 0; e < E; ++e) row[s2][e] = row[s][e];
+                        }
+                    }
+                }
+            }
+            if (active) {
+                if (DET) store_f32<E>(a.R + (v - a.src_begin) * D + gl * E, r);
+                else store_row<T, D, E>(M + v * D + gl * E, r, sr, ns, gl * E);
+            }
+        }
+        __syncwarp();
+    }
+
+    // ---- monitors ----
+    if (a.n_updates) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) applied += __shfl_xor_sync(0xffffffffu, applied, o);
+        if (lane == 0 && applied) atomicAdd(a.n_updates, applied);
+    }
+    if (want_loss) {
+        __shared__ double s_loss[kTrainWarps];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+        if (lane == 0) s_loss[warp] = loss_acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kTrainWarps; ++w) t += s_loss[w];
+            a.loss_partials[blockIdx.x] = t;
+        }
+    }
+}
+
+template <typename T, int D, int L, int P, bool DET>
+void launch_train(const TrainArgs &a, int grid, cudaStream_t s) {
+    train_kernel<T, D, L, P, DET><<<grid, kTrainWarps * 32, 0, s>>>(a);
+}
+
+template <typename T, int D, int L, int P, bool DET>
+TrainKernel make_train_kernel() {
+    TrainKernel k;
+    k.launch = &launch_train<T, D, L, P, DET>;
+    k.blocks_per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.blocks_per_sm, train_kernel<T, D, L, P, DET>,
+                                                  kTrainWarps * 32, 0);
+    if (k.blocks_per_sm < 1) k.blocks_per_sm = 1;
+    k.lanes = L;
+    k.pass = P;
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic mode, end of batch.  Sorted (target row, slot) pairs group the
+// sample-row changes of each row in slot order = (source, sample) order.
+// One L-lane group per sorted position; a group that starts a segment sums it.
+// ---------------------------------------------------------------------------
+template <typename T, int D, int L>
+__global__ void __launch_bounds__(256) det_apply_segments(const uint32_t *__restrict__ skeys,
+                                                          const uint32_t *__restrict__ sidx, int64_t nslots,
+                                                          const float *__restrict__ C, const float *__restrict__ R,
+                                                          T *__restrict__ M, int64_t n, int64_t b0, int64_t b1,
+                                                          uint8_t *__restrict__ src_done, uint32_t sr_seed) {
+    constexpr int E = D / L;
+    const int gl = threadIdx.x % L;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x / L;
+    for (int64_t i = gid; i < nslots; i += gstride) {
+        const uint32_t key = skeys[i];
+        if ((int64_t)key >= n) continue;
+        if (i > 0 && skeys[i - 1] == key) continue;
+        const int64_t x = key;
+        float acc[E];
+        if (x >= b0 && x < b1) {
+            const float4 *q = reinterpret_cast<const float4 *>(R + (x - b0) * D + gl * E);
+#pragma unroll
+            for (int v = 0; v < E / 4; ++v) {
+                const float4 f = q[v];
+                acc[4 * v] = f.x; acc[4 * v + 1] = f.y; acc[4 * v + 2] = f.z; acc[4 * v + 3] = f.w;
+            }
+            if (gl == 0) src_done[x - b0] = 1;
+        } else {
+            load_row_snapshot<T, E>(M + x * D + gl * E, acc);
+        }
+        for (int64_t jj = i; jj < nslots && skeys[jj] == key; ++jj) {
+            const float4 *q = reinterpret_cast<const float4 *>(C + (int64_t)sidx[jj] * D + gl * E);
+#pragma unroll
+            for (int v = 0; v < E / 4; ++v) {
+                const float4 f = q[v];
+                acc[4 * v] += f.x; acc[4 * v + 1] += f.y; acc[4 * v + 2] += f.z; acc[4 * v + 3] += f.w;
+            }
+        }
+        store_row<T, D, E>(M + x * D + gl * E, acc, mix32(sr_seed ^ (uint32_t)x), 0, gl * E);
+    }
+}
+
+template <typename T, int D, int L>
+__global__ void __launch_bounds__(256) det_apply_sources(const float *__restrict__ R, T *__restrict__ M,
+                                                         int64_t b0, int64_t b1,
+                                                         const uint8_t *__restrict__ src_done, uint32_t sr_seed) {
+    constexpr int E = D / L;
+    const int gl = threadIdx.x % L;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x / L;
+    for (int64_t i = gid; i < b1 - b0; i += gstride) {
+        if (src_done[i]) continue;
+        float acc[E];
+        const float4 *q = reinterpret_cast<const float4 *>(R + i * D + gl * E);
+#pragma unroll
+        for (int v = 0; v < E / 4; ++v) {
+            const float4 f = q[v];
+            acc[4 * v] = f.x; acc[4 * v + 1] = f.y; acc[4 * v + 2] = f.z; acc[4 * v + 3] = f.w;
+        }
+        store_row<T, D, E>(M + (b0 + i) * D + gl * E, acc, mix32(sr_seed ^ (uint32_t)(b0 + i)), 0, gl * E);
+    }
+}
+
+template <typename T, int D>
+void launch_det_apply_t(const uint32_t *skeys, const uint32_t *sidx, int64_t nslots, const float *C,
+                        const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
+                        uint32_t sr_seed, cudaStream_t s) {
+    constexpr int L = (D * (int)sizeof(T) / 16) < 1 ? 1 : (D * (int)sizeof(T) / 16);
+    constexpr int LL = (D / L) % 4 == 0 ? L : L / 2;  // float4 slices of the FP32 buffers
+    const int64_t groups_per_block = 256 / LL;
+    const int64_t g1 = ceil_div(nslots, groups_per_block);
+    const int64_t g2 = ceil_div(b1 - b0, groups_per_block);
+    const int cap = num_sms() * 8;
+    if (nslots > 0)
+        det_apply_segments<T, D, LL><<<(int)(g1 < cap ? (g1 > 0 ? g1 : 1) : cap), 256, 0, s>>>(
+            skeys, sidx, nslots, C, R, static_cast<T *>(M), n, b0, b1, src_done, sr_seed);
+    if (b1 > b0)
+        det_apply_sources<T, D, LL><<<(int)(g2 < cap ? (g2 > 0 ? g2 : 1) : cap), 256, 0, s>>>(
+            R, static_cast<T *>(M), b0, b1, src_done, sr_seed ^ 0x9e3779b9u);
+}
+
+}  // namespace gosh

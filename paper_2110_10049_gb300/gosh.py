@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libgosh (include/gosh.h).
+
+Argument marshalling only: every function forwards torch tensors' device
+pointers and the current CUDA stream to the C entry point of the same name and
+raises GoshError on a non-zero status.  There is no fallback: if libgosh.so is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgosh.so")
+
+GOSH_F32, GOSH_BF16, GOSH_F16 = 0, 1, 2
+GOSH_HOGWILD, GOSH_DETERMINISTIC = 0, 1
+MAX_LEVELS = 64
+
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "BUDGET", 4: "CUDA", 5: "TIMEOUT", 6: "UNSUPPORTED"}
+
+
+class GoshError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__("%s -> GOSH_ERR_%s: %s" % (fn, _STATUS.get(status, status), msg))
+        self.status = status
+
+
+class gosh_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p), ("on_device", C.c_int)]
+
+
+class gosh_params(C.Structure):
+    _fields_ = [("d", C.c_int), ("k", C.c_int), ("lr", C.c_double), ("lr_floor", C.c_double),
+                ("epochs", C.c_int), ("p", C.c_double), ("threshold", C.c_int), ("shrink", C.c_double),
+                ("max_levels", C.c_int), ("dtype", C.c_int), ("mode", C.c_int), ("det_batch", C.c_int64),
+                ("seed", C.c_uint64), ("graph_id", C.c_uint64), ("lanes_per_row", C.c_int),
+                ("samples_per_pass", C.c_int), ("device_budget_bytes", C.c_int64), ("validate", C.c_int)]
+
+
+class gosh_stats(C.Structure):
+    _fields_ = [("levels", C.c_int), ("n", C.c_int64 * MAX_LEVELS), ("nnz", C.c_int64 * MAX_LEVELS),
+                ("epochs", C.c_int * MAX_LEVELS), ("train_ms", C.c_double * MAX_LEVELS),
+                ("coarsen_ms", C.c_double), ("project_ms", C.c_double), ("total_ms", C.c_double),
+                ("updates", C.c_ulonglong)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Loads libgosh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgosh.so is not built: run __graft_entry__.build() "
+                               "(or python -m paper_2110_10049_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, u64, f64 = C.c_void_p, C.c_int64, C.c_int, C.c_uint64, C.c_double
+        P = C.POINTER
+        sig = {
+            "gosh_params_default": [P(gosh_params)],
+            "gosh_validate_csr": [P(gosh_csr), vp],
+            "gosh_coarsen": [P(gosh_csr), i32, f64, i32, vp, P(vp)],
+            "gosh_hierarchy_level": [vp, i32, P(gosh_csr), P(vp)],
+            "gosh_hierarchy_sizes": [vp, i32, P(C.c_int64), P(C.c_int64)],
+            "gosh_hierarchy_copy_level": [vp, i32, vp, vp, vp, vp],
+            "gosh_init_embedding": [vp, i64, i32, i32, i32, u64, u64, vp],
+            "gosh_train_level": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, vp, vp],
+            "gosh_project": [vp, i64, vp, vp, i64, i32, i32, vp],
+            "gosh_embed": [P(gosh_csr), P(gosh_params), vp, vp, P(gosh_stats)],
+            "gosh_pair_scores": [vp, i32, i32, vp, i64, vp, vp],
+            "gosh_link_auc": [vp, i32, i32, vp, i64, vp, i64, vp, P(C.c_double)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.gosh_last_error.restype = C.c_char_p
+        L.gosh_last_error.argtypes = []
+        L.gosh_hierarchy_levels.restype = C.c_int
+        L.gosh_hierarchy_levels.argtypes = [vp]
+        L.gosh_hierarchy_free.restype = None
+        L.gosh_hierarchy_free.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _check(fn: str, status: int):
+    if status != 0:
+        raise GoshError(fn, status, lib().gosh_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+_DT = {"f32": GOSH_F32, "bf16": GOSH_BF16, "f16": GOSH_F16}
+
+
+def dtype_code(t) -> int:
+    import torch
+    if isinstance(t, int):
+        return t
+    if isinstance(t, str):
+        return _DT[t]
+    return {torch.float32: GOSH_F32, torch.bfloat16: GOSH_BF16, torch.float16: GOSH_F16}[t]
+
+
+def torch_dtype(code: int):
+    import torch
+    return {GOSH_F32: torch.float32, GOSH_BF16: torch.bfloat16, GOSH_F16: torch.float16}[code]
+
+
+def default_params(**kw) -> gosh_params:
+    p = gosh_params()
+    _check("gosh_params_default", lib().gosh_params_default(C.byref(p)))
+    for k, v in kw.items():
+        if k == "dtype":
+            v = dtype_code(v)
+        if k == "mode" and isinstance(v, str):
+            v = {"hogwild": GOSH_HOGWILD, "deterministic": GOSH_DETERMINISTIC}[v]
+        setattr(p, k, v)
+    return p
+
+
+@dataclass
+class Csr:
+    """Device CSR kept alive alongside its ctypes view."""
+    rowptr: object  # torch.int64 [n+1]
+    col: object     # torch.int32 [nnz]
+
+    @property
+    def n(self) -> int:
+        return self.rowptr.numel() - 1
+
+    def c(self) -> gosh_csr:
+        return gosh_csr(self.n, self.rowptr.data_ptr(), self.col.data_ptr(), 1)
+
+
+def to_device_csr(rowptr, col, device="cuda") -> Csr:
+    import torch
+    rp = torch.as_tensor(np.ascontiguousarray(rowptr, dtype=np.int64)).to(device)
+    co = torch.as_tensor(np.ascontiguousarray(col, dtype=np.int32))
+    if co.numel() == 0:
+        co = torch.zeros(1, dtype=torch.int32)
+    return Csr(rp, co.to(device))
+
+
+def gosh_validate_csr(g: Csr, stream=None):
+    cg = g.c()
+    _check("gosh_validate_csr", lib().gosh_validate_csr(C.byref(cg), _stream(stream)))
+
+
+class Hierarchy:
+    """Owns a gosh_hierarchy handle (level 0 aliases the input CSR)."""
+
+    def __init__(self, handle, g0: Csr):
+        self.handle = handle
+        self._g0 = g0
+
+    def __len__(self):
+        return lib().gosh_hierarchy_levels(self.handle)
+
+    def level(self, i: int):
+        """(n, rowptr ptr, col ptr, map ptr or None) of level i (device pointers)."""
+        cg = gosh_csr()
+        mp = C.c_void_p()
+        _check("gosh_hierarchy_level", lib().gosh_hierarchy_level(self.handle, i, C.byref(cg), C.byref(mp)))
+        return cg, mp.value
+
+    def sizes(self, i: int):
+        n, nnz = C.c_int64(), C.c_int64()
+        _check("gosh_hierarchy_sizes", lib().gosh_hierarchy_sizes(self.handle, i, C.byref(n), C.byref(nnz)))
+        return n.value, nnz.value
+
+    def level_arrays(self, i: int, stream=None):
+        """Copies level i's CSR and map (None for the last level) to host numpy arrays."""
+        n, nnz = self.sizes(i)
+        rp = np.zeros(n + 1, dtype=np.int64)
+        col = np.zeros(max(nnz, 1), dtype=np.int32)
+        m = np.zeros(max(n, 1), dtype=np.int32)
+        last = i == len(self) - 1
+        _check("gosh_hierarchy_copy_level", lib().gosh_hierarchy_copy_level(
+            self.handle, i, rp.ctypes.data_as(C.c_void_p), col.ctypes.data_as(C.c_void_p),
+            None if last else m.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return rp, col[:nnz], (None if last else m[:n])
+
+    def close(self):
+        if self.handle:
+            lib().gosh_hierarchy_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gosh_coarsen(g: Csr, threshold=100, shrink=0.8, max_levels=MAX_LEVELS, stream=None) -> Hierarchy:
+    cg = g.c()
+    h = C.c_void_p()
+    _check("gosh_coarsen", lib().gosh_coarsen(C.byref(cg), threshold, shrink, max_levels, _stream(stream),
+                                              C.byref(h)))
+    return Hierarchy(h.value, g)
+
+
+def gosh_init_embedding(M, level=0, seed=0, graph_id=0, stream=None):
+    n, d = M.shape
+    _check("gosh_init_embedding", lib().gosh_init_embedding(_ptr(M), n, d, dtype_code(M.dtype), level, seed,
+                                                            graph_id, _stream(stream)))
+
+
+def gosh_train_level(g, M, level, epochs, params: gosh_params, loss=None, n_updates=None, stream=None):
+    """g: Csr or gosh_csr (device).  loss: torch.float64[epochs] (device) or None.
+    n_updates: torch.int64[1] (device) or None (incremented)."""
+    cg = g.c() if isinstance(g, Csr) else g
+    _check("gosh_train_level", lib().gosh_train_level(C.byref(cg), _ptr(M), level, epochs, C.byref(params),
+                                                      _stream(stream), _ptr(loss), _ptr(n_updates)))
+
+
+def gosh_project(Mc, map_ptr, Mf, stream=None):
+    """map_ptr: a torch.int32 tensor or a raw device pointer."""
+    mp = C.c_void_p(map_ptr.data_ptr()) if hasattr(map_ptr, "data_ptr") else C.c_void_p(map_ptr)
+    _check("gosh_project", lib().gosh_project(_ptr(Mc), Mc.shape[0], mp, _ptr(Mf), Mf.shape[0], Mc.shape[1],
+                                              dtype_code(Mc.dtype), _stream(stream)))
+
+
+def gosh_embed(rowptr, col, params: gosh_params, out=None, stream=None):
+    """Alg. 2 end to end.  rowptr/col: torch device tensors (device path) or
+    numpy arrays (host path; out must then be a host tensor or None).
+    Returns (M0, stats)."""
+    import torch
+    on_dev = hasattr(rowptr, "is_cuda") and rowptr.is_cuda
+    if on_dev:
+        cg = gosh_csr(rowptr.numel() - 1, rowptr.data_ptr(), col.data_ptr(), 1)
+        n = rowptr.numel() - 1
+    else:
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        cg = gosh_csr(len(rowptr) - 1, rowptr.ctypes.data, col.ctypes.data, 0)
+        n = len(rowptr) - 1
+    if out is None:
+        out = torch.empty((n, params.d), dtype=torch_dtype(params.dtype),
+                          device="cuda" if on_dev else "cpu")
+    st = gosh_stats()
+    _check("gosh_embed", lib().gosh_embed(C.byref(cg), C.byref(params), _ptr(out), _stream(stream),
+                                          C.byref(st)))
+    return out, st
+
+
+def gosh_pair_scores(M, pairs, out=None, stream=None):
+    import torch
+    npairs = pairs.shape[0]
+    if out is None:
+        out = torch.empty(npairs, dtype=torch.float32, device=M.device)
+    _check("gosh_pair_scores", lib().gosh_pair_scores(_ptr(M), M.shape[1], dtype_code(M.dtype), _ptr(pairs),
+                                                      npairs, _ptr(out), _stream(stream)))
+    return out
+
+
+def gosh_link_auc(M, pos, neg, stream=None) -> float:
+    a = C.c_double()
+    _check("gosh_link_auc", lib().gosh_link_auc(_ptr(M), M.shape[1], dtype_code(M.dtype), _ptr(pos),
+                                                pos.shape[0], _ptr(neg), neg.shape[0], _stream(stream),
+                                                C.byref(a)))
+    return a.value
+
+
+def stats_dict(st: gosh_stats) -> dict:
+    D = st.levels
+    return {"levels": D, "n": list(st.n[:D]), "nnz": list(st.nnz[:D]), "epochs": list(st.epochs[:D]),
+            "train_ms": list(st.train_ms[:D]), "coarsen_ms": st.coarsen_ms, "project_ms": st.project_ms,
+            "total_ms": st.total_ms, "updates": int(st.updates)}

@@ -1,0 +1,252 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Bars (see the tolerance derivation next to each test):
+  - integer work (coarsening maps, coarse CSRs), initialisation and copy
+    projection: bit-exact;
+  - deterministic-mode training (FP32 tables) vs the FP64 oracle running the
+    same snapshot batches: relative Frobenius error <= 1e-5;
+  - Hogwild on a graph small enough to occupy one warp with one source per
+    round is sequential, so it meets the same 1e-5 bar against the sequential
+    oracle; larger graphs are judged by link-prediction AUC within 0.005.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import bf16_round_np, gosh, needs_gpu, rel_fro, torch
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+DET_TOL = 1e-5  # relative Frobenius, deterministic FP32 vs FP64 oracle
+
+
+@pytest.fixture(scope="module")
+def g():
+    return gosh()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return synth.workload("rmat12")
+
+
+def dev(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# ----------------------------------------------------------------- init
+@pytest.mark.parametrize("d", [32, 64, 128])
+@pytest.mark.parametrize("n", [1, 33, 1000])
+def test_init_bit_exact(g, d, n):
+    M = torch.empty((n, d), dtype=torch.float32, device="cuda")
+    g.gosh_init_embedding(M, level=5, seed=123, graph_id=7)
+    ref = oracle.init_uniform(n, d, 5, 123, 7).astype(np.float32)
+    np.testing.assert_array_equal(M.cpu().numpy(), ref)
+    Mb = torch.empty((n, d), dtype=torch.bfloat16, device="cuda")
+    g.gosh_init_embedding(Mb, level=5, seed=123, graph_id=7)
+    np.testing.assert_array_equal(Mb.float().cpu().numpy(), bf16_round_np(ref))
+
+
+# ----------------------------------------------------------------- coarsening
+def check_hierarchy(g, rowptr, col, threshold=100, shrink=0.8):
+    graphs, maps = oracle.mec_hierarchy(rowptr, col, threshold, shrink)
+    csr = g.to_device_csr(rowptr, col)
+    h = g.gosh_coarsen(csr, threshold, shrink)
+    assert len(h) == len(graphs)
+    for i in range(len(graphs)):
+        rp, co, mp = h.level_arrays(i)
+        np.testing.assert_array_equal(rp, graphs[i][0])
+        np.testing.assert_array_equal(co, graphs[i][1])
+        if i < len(maps):
+            np.testing.assert_array_equal(mp, maps[i])
+    h.close()
+    return len(graphs)
+
+
+def test_coarsen_rmat12_bit_exact(g, c1):
+    D = check_hierarchy(g, c1.train.rowptr, c1.train.col)
+    assert D >= 3
+
+
+@pytest.mark.parametrize("scale,ef,seed", [(14, 4, 1), (15, 16, 2), (10, 32, 3)])
+def test_coarsen_rmat_bit_exact(g, scale, ef, seed):
+    gr = synth.rmat_graph(scale, ef, seed)
+    check_hierarchy(g, gr.rowptr, gr.col)
+
+
+def test_coarsen_edge_cases(g):
+    # no edges at all: every vertex is its own cluster, one level added
+    check_hierarchy(g, np.zeros(6, dtype=np.int64), np.zeros(0, dtype=np.int32))
+    # single vertex
+    check_hierarchy(g, np.zeros(2, dtype=np.int64), np.zeros(0, dtype=np.int32))
+    # isolated vertices mixed with a star and a path; threshold 1 forces depth
+    s = np.array([0, 0, 0, 0, 5, 6, 7])
+    t = np.array([1, 2, 3, 4, 6, 7, 8])
+    gr = synth.csr_from_edges(12, s, t, compact=False)
+    check_hierarchy(g, gr.rowptr, gr.col, threshold=1)
+    # random small graphs of every density
+    rng = np.random.default_rng(0)
+    for trial in range(40):
+        n = int(rng.integers(2, 200))
+        gr = synth.random_graph(n, float(rng.uniform(0.0, 0.5)), int(rng.integers(1 << 30)))
+        check_hierarchy(g, gr.rowptr, gr.col, threshold=int(rng.integers(1, 20)))
+
+
+# ----------------------------------------------------------------- projection
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+def test_project_copy_exact(g, dtype):
+    rng = np.random.default_rng(1)
+    nc, nf, d = 300, 5000, 64
+    mp = rng.integers(0, nc, nf).astype(np.int32)
+    Mc = torch.randn(nc, d, generator=torch.Generator().manual_seed(0)).to(dtype)
+    ref = oracle.project_copy(mp, Mc.double().numpy())
+    Mf = torch.empty((nf, d), dtype=dtype, device="cuda")
+    g.gosh_project(Mc.cuda(), dev(mp), Mf)
+    np.testing.assert_array_equal(Mf.double().cpu().numpy(), ref)
+
+
+# ----------------------------------------------------------------- training
+def train_gpu(g, gr, M0, k, level, epochs, lr, seed, mode, m=1, dtype=torch.float32, d=None, lanes=0, pas=0):
+    csr = g.to_device_csr(gr.rowptr, gr.col)
+    M = dev(M0, dtype)
+    p = g.default_params(d=M0.shape[1], k=k, lr=lr, dtype=dtype, mode=mode, det_batch=m, seed=seed,
+                         lanes_per_row=lanes, samples_per_pass=pas)
+    loss = torch.zeros(max(epochs, 1), dtype=torch.float64, device="cuda")
+    nup = torch.zeros(1, dtype=torch.int64, device="cuda")
+    g.gosh_train_level(csr, M, level, epochs, p, loss=loss, n_updates=nup)
+    torch.cuda.synchronize()
+    return M.double().cpu().numpy(), loss.cpu().numpy()[:epochs], int(nup.item())
+
+
+@pytest.mark.parametrize("d", [32, 64, 128])
+@pytest.mark.parametrize("k,m", [(3, 64), (3, 1), (5, 257), (1, 10 ** 6)])
+def test_deterministic_matches_oracle(g, c1, d, k, m):
+    gr = c1.train
+    epochs = 3 if m == 1 else 8
+    M0 = oracle.init_uniform(gr.n, d, 2, 99).astype(np.float32).astype(np.float64) * 30
+    Mo = M0.copy()
+    lo, no = oracle.train_deterministic(gr.rowptr, gr.col, Mo, k, 2, epochs, 0.045, 1e-4, 4242, m)
+    Mg, lg, ng = train_gpu(g, gr, M0, k, 2, epochs, 0.045, 4242, "deterministic", m=m)
+    assert ng == no
+    assert rel_fro(Mg, Mo) <= DET_TOL
+    np.testing.assert_allclose(lg, lo, rtol=1e-5)
+
+
+def test_deterministic_is_run_to_run_identical(g, c1):
+    gr = c1.train
+    M0 = oracle.init_uniform(gr.n, 64, 0, 5).astype(np.float32).astype(np.float64) * 30
+    a = train_gpu(g, gr, M0, 3, 0, 4, 0.045, 1, "deterministic", m=500)[0]
+    b = train_gpu(g, gr, M0, 3, 0, 4, 0.045, 1, "deterministic", m=500)[0]
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_hogwild_single_warp_is_sequential(g, k):
+    # n <= 32 and 32 lanes per source (FP32, d=128): one warp, one source per
+    # round, so the lock-free epoch runs the sources in id order.
+    gr = synth.random_graph(30, 0.2, 17)
+    M0 = oracle.init_uniform(gr.n, 128, 0, 3).astype(np.float32).astype(np.float64) * 60
+    Mo = M0.copy()
+    lo, no = oracle.train_sequential(gr.rowptr, gr.col, Mo, k, 0, 20, 0.05, 1e-4, 8)
+    for pas in (2, 4):
+        Mg, lg, ng = train_gpu(g, gr, M0, k, 0, 20, 0.05, 8, "hogwild", lanes=32, pas=pas)
+        assert ng == no
+        assert rel_fro(Mg, Mo) <= DET_TOL
+        np.testing.assert_allclose(lg, lo, rtol=1e-5)
+
+
+def heldout_and_fit_auc(M, sp, seed=0):
+    gr = sp.train
+    src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
+    rng = np.random.default_rng(seed)
+    rnd = np.stack([rng.integers(0, gr.n, 20000), rng.integers(0, gr.n, 20000)], 1)
+    fit = oracle.link_auc(M, np.stack([src, gr.col], 1), rnd)
+    return oracle.link_auc(M, sp.test_pos, sp.test_neg), fit
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_hogwild_auc_matches_oracle(g, c1, dtype):
+    """Hogwild on R-MAT scale 12, d=32, k=3, 200 epochs over the full
+    hierarchy: held-out and training-edge AUC within 0.005 of the sequential
+    oracle, each averaged over 3 seeds."""
+    sp = c1
+    res_o, res_g = [], []
+    for seed in (1, 2, 3):
+        Mo, _ = oracle.embed(sp.train.rowptr, sp.train.col, 32, 3, 0.045, 200, 0.3, seed=seed)
+        p = g.default_params(d=32, k=3, lr=0.045, epochs=200, p=0.3, seed=seed, dtype=dtype)
+        Mg, st = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
+        res_o.append(heldout_and_fit_auc(Mo, sp))
+        res_g.append(heldout_and_fit_auc(Mg.double().cpu().numpy(), sp))
+    o, gg = np.mean(res_o, 0), np.mean(res_g, 0)
+    assert abs(o[0] - gg[0]) <= 0.005, (o, gg)
+    assert abs(o[1] - gg[1]) <= 0.005, (o, gg)
+
+
+def test_embed_deterministic_matches_oracle(g, c1):
+    sp = c1
+    m = 128
+    Mo, info = oracle.embed(sp.train.rowptr, sp.train.col, 64, 3, 0.045, 60, 0.3, seed=11,
+                            mode="deterministic", det_batch=m)
+    p = g.default_params(d=64, k=3, lr=0.045, epochs=60, p=0.3, seed=11, mode="deterministic", det_batch=m)
+    Mg, st = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
+    s = g.stats_dict(st)
+    assert s["levels"] == info["levels"] and s["epochs"] == info["epochs"]
+    assert s["updates"] == info["updates"]
+    assert rel_fro(Mg.double().cpu().numpy(), Mo) <= DET_TOL
+
+
+def test_embed_host_buffers_equal_device_buffers(g, c1):
+    sp = c1
+    p = g.default_params(d=32, k=3, lr=0.045, epochs=30, p=0.3, seed=3, mode="deterministic", det_batch=256)
+    Md, _ = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
+    Mh, _ = g.gosh_embed(sp.train.rowptr, sp.train.col, p)
+    assert not Mh.is_cuda
+    np.testing.assert_array_equal(Md.cpu().numpy(), Mh.numpy())
+
+
+# ----------------------------------------------------------------- AUC
+def test_auc_matches_oracle(g, c1):
+    sp = c1
+    rng = np.random.default_rng(5)
+    M = rng.normal(size=(sp.train.n, 32)).astype(np.float32)
+    Md = dev(M)
+    pos, neg = dev(sp.test_pos), dev(sp.test_neg)
+    sc_pos = g.gosh_pair_scores(Md, pos).cpu().numpy().astype(np.float64)
+    sc_neg = g.gosh_pair_scores(Md, neg).cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(sc_pos, oracle.pair_scores(M, sp.test_pos), rtol=1e-5, atol=1e-5)
+    a = g.gosh_link_auc(Md, pos, neg)
+    # same float32 scores on both sides: the AUC must agree to rounding
+    assert abs(a - oracle.auc(sc_pos, sc_neg)) < 1e-12
+    # ties: all-equal scores give exactly 1/2
+    z = torch.zeros((sp.train.n, 32), device="cuda")
+    assert g.gosh_link_auc(z, pos, neg) == 0.5
+
+
+# ----------------------------------------------------------------- errors
+def test_invalid_arguments_rejected_before_launch(g, c1):
+    gr = c1.train
+    csr = g.to_device_csr(gr.rowptr, gr.col)
+    M = torch.zeros((gr.n, 48), device="cuda")
+    p = g.default_params(d=48)
+    with pytest.raises(g.GoshError) as e:
+        g.gosh_train_level(csr, M, 0, 1, p)
+    assert e.value.status == 1
+    # unsorted row / self loop / asymmetric CSR caught by validation
+    bad_col = gr.col.copy()
+    r0, r1 = gr.rowptr[5], gr.rowptr[6]
+    assert r1 - r0 >= 2
+    bad_col[r0], bad_col[r0 + 1] = bad_col[r0 + 1], bad_col[r0]
+    with pytest.raises(g.GoshError, match="ascending"):
+        g.gosh_validate_csr(g.to_device_csr(gr.rowptr, bad_col))
+    asym = synth.Graph(np.array([0, 1, 1], dtype=np.int64), np.array([1], dtype=np.int32))
+    with pytest.raises(g.GoshError, match="symmetric"):
+        g.gosh_validate_csr(g.to_device_csr(asym.rowptr, asym.col))
+    g.gosh_validate_csr(csr)
+    # deterministic mode needs all samples in one pass
+    p = g.default_params(d=32, k=9, mode="deterministic")
+    with pytest.raises(g.GoshError):
+        g.gosh_train_level(csr, torch.zeros((gr.n, 32), device="cuda"), 0, 1, p)
