@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GOSH embedding step on one GB300 (or N replicas).
+
+One step = one gosh_embed (Alg. 2) of the R-MAT scale-20 workload (edge factor
+16, 80% training split, d = 128, k = 3, e = 200, p = 0.3, lr = 0.045): GPU
+coarsening (Alg. 4), every level's training epochs (Alg. 3) and the copy
+projections, with BF16 tables (FP32 arithmetic, stochastic rounding).  The
+CSR is resident in HBM when the timed region starts; the L2 is flushed
+between steps.  value = applied sample updates (UPDATEEMBED calls) per second
+of step time, summed over ranks.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+The reference arm (--impl reference) times the CPU oracle (plain FP64 C, one
+core) on level-0 epochs of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sample-updates/s and time-to-embed vs plain FP32 at equal link-pred AUC"
+UNIT = "sample-updates/s"
+WL = dict(name="rmat20", scale=20, edge_factor=16, d=128, k=3, epochs=200, p=0.3, lr=0.045)
+
+
+def workload_name(tables):
+    return "R-MAT scale 20, ef 16, 80/20 split, d=128, k=3, e=200, p=0.3, %s tables" % tables
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(rank):
+    import synth
+    seed = 20211021 + 1000 * rank
+    g = synth.rmat_graph(WL["scale"], WL["edge_factor"], seed)
+    return synth.link_split(g, seed)
+
+
+def cpu_oracle_sample(sp, budget_s=12.0):
+    """The oracle as it stands, level-0 epochs of the same graph on one core,
+    until budget_s of CPU time; returns (updates/s, description)."""
+    import oracle
+    gr = sp.train
+    M = oracle.init_uniform(gr.n, WL["d"], 0, 1) * 30
+    t0 = time.perf_counter()
+    upd, ep = 0, 0
+    while True:
+        _, nu = oracle.train_sequential(gr.rowptr, gr.col, M, WL["k"], 0, 1, WL["lr"], 1e-4, 7 + ep)
+        upd += nu
+        ep += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return upd / dt, "%d level-0 epoch(s) of the FP64 sequential oracle (%d sources, %d updates, %.1f s)" % (
+        ep, gr.n, upd, dt)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sp = make_inputs(0)
+    gr = sp.train
+    M = oracle.init_uniform(gr.n, WL["d"], 0, 1) * 30
+    for w in range(args.warmup):
+        oracle.train_sequential(gr.rowptr, gr.col, M, WL["k"], 0, 1, WL["lr"], 1e-4, 100 + w)
+    t0 = time.perf_counter()
+    upd = 0
+    for s in range(args.steps):
+        _, nu = oracle.train_sequential(gr.rowptr, gr.col, M, WL["k"], 0, 1, WL["lr"], 1e-4, 200 + s)
+        upd += nu
+    dt = time.perf_counter() - t0
+    val = upd / dt
+    sample = "one level-0 epoch per step (%d sources, FP64 sequential Alg. 3)" % gr.n
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name("f64 (oracle)")},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gosh", choices=["gosh", "reference"])
+    ap.add_argument("--tables", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 / AUC comparison")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2110_10049_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2110_10049_gb300 import gosh
+
+    sp = make_inputs(rank)
+    gr = sp.train
+    rp = torch.from_numpy(gr.rowptr).cuda()
+    co = torch.from_numpy(gr.col).cuda()
+    dt_code = gosh.GOSH_BF16 if args.tables == "bf16" else gosh.GOSH_F32
+    params = gosh.default_params(d=WL["d"], k=WL["k"], lr=WL["lr"], epochs=WL["epochs"], p=WL["p"],
+                                 dtype=dt_code, seed=11 + rank)
+    out = torch.empty((gr.n, WL["d"]), dtype=gosh.torch_dtype(dt_code), device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        gosh.gosh_embed(rp, co, params, out=out)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    l0 = gosh.lib()
+    l0.gosh_kernel_launches.restype = __import__("ctypes").c_ulonglong
+    launches0 = l0.gosh_kernel_launches()
+    total_ms, updates, stats = 0.0, 0, []
+    with ClockSampler(local) as clocks:
+        for s in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = gosh.gosh_embed(rp, co, params, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            sd = gosh.stats_dict(st)
+            updates += sd["updates"]
+            stats.append(sd)
+    launches = l0.gosh_kernel_launches() - launches0
+    barrier()
+    # max time over ranks, sum of work
+    t = torch.tensor([total_ms, float(updates)], dtype=torch.float64, device="cuda")
+    if dist:
+        tt = t.clone()
+        dist.all_reduce(tt[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
+        t = tt
+    max_ms, all_updates = float(t[0]), float(t[1])
+    value = all_updates / (max_ms / 1000.0)
+    ms_per_step = max_ms / args.steps
+
+    # dominant kernel: level-0 training epochs (one launch per epoch)
+    last = stats[-1]
+    e0n = last["epochs"][0]
+    row = WL["d"] * (2 if dt_code == gosh.GOSH_BF16 else 4)
+    bytes_per_src = 2 * row * (WL["k"] + 2) + 12
+    alg_bytes = gr.n * bytes_per_src
+    l0_ms = np.median([s["train_ms"][0] for s in stats]) / max(e0n, 1)
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (l0_ms / 1000.0) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                tr = json.load(f)
+            traffic = tr.get("%s_level0_bytes_per_launch" % args.tables)
+        except Exception:
+            traffic = None
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(args.tables), "vertices": gr.n, "csr_entries": gr.nnz,
+                   "levels": last["levels"], "level_sizes": last["n"], "epochs_per_level": last["epochs"],
+                   "tables": args.tables, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": "replicas x%d" % world},
+        "time_to_embed_ms": ms_per_step,
+        "breakdown_ms": {"coarsen": last["coarsen_ms"], "train": sum(last["train_ms"]),
+                         "project": last["project_ms"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "train_kernel (level 0, one launch per epoch)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": l0_ms,
+                     "peak_kind": peak_kind + " copy bandwidth"},
+        "clocks": clocks.summary(),
+        "gpu_launches": int(launches),
+    }
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    if rank == 0 or True:
+        prp = torch.from_numpy(gr.rowptr).pin_memory()
+        pco = torch.from_numpy(gr.col).pin_memory()
+        hout = torch.empty((gr.n, WL["d"]), dtype=gosh.torch_dtype(dt_code)).pin_memory()
+        hrp = prp.numpy()
+        hco = pco.numpy()
+        gosh.gosh_embed(hrp, hco, params, out=hout)
+        torch.cuda.synchronize()
+        ne = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        upd_e = 0
+        for _ in range(ne):
+            _, st = gosh.gosh_embed(hrp, hco, params, out=hout)
+            upd_e += int(st.updates)
+        torch.cuda.synchronize()
+        dte = time.perf_counter() - t0
+        result["e2e"] = {"value": upd_e / dte * world, "unit": UNIT,
+                         "h2d_bytes_per_step": int(gr.rowptr.nbytes + gr.col.nbytes),
+                         "d2h_bytes_per_step": int(hout.numel() * hout.element_size())}
+
+    if not args.no_compare and rank == 0:
+        pos = torch.from_numpy(sp.test_pos).cuda()
+        neg = torch.from_numpy(sp.test_neg).cuda()
+        cmp = {}
+        for tname, code in (("bf16", gosh.GOSH_BF16), ("f32", gosh.GOSH_F32)):
+            pr = gosh.default_params(d=WL["d"], k=WL["k"], lr=WL["lr"], epochs=WL["epochs"], p=WL["p"],
+                                     dtype=code, seed=11)
+            M, _ = gosh.gosh_embed(rp, co, pr)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M, st = gosh.gosh_embed(rp, co, pr)
+            e1.record(stream)
+            e1.synchronize()
+            cmp[tname] = {"time_to_embed_ms": e0.elapsed_time(e1), "heldout_auc": gosh.gosh_link_auc(M, pos, neg),
+                          "updates": int(st.updates)}
+        result["tables_compare"] = cmp
+
+    if not args.no_cpu_baseline and rank == 0:
+        v, desc = cpu_oracle_sample(sp)
+        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+if __name__ == "__main__":
+    main()

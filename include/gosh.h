@@ -75,6 +75,11 @@ typedef struct gosh_params {
     int samples_per_pass;   /* sample rows gathered at once per source; 0 = automatic */
     int64_t device_budget_bytes; /* 0 = unlimited */
     int validate;           /* 1: check the CSR before use (costs one pass) */
+    int plain_stores;       /* GOSH_HOGWILD with FP32 tables: 0 (default) applies every row
+                               change as an atomic vector addition, so concurrent updates of
+                               one row are never lost; 1 writes rows back with plain stores
+                               as the paper does (a racing writer may overwrite an update).
+                               16-bit tables always use plain stores with stochastic rounding. */
 } gosh_params;
 
 #define GOSH_MAX_LEVELS 64
@@ -100,6 +105,10 @@ gosh_status gosh_params_default(gosh_params *p);
 
 /* Thread-local message of the last failed call ("" if none). */
 const char *gosh_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all devices).  A diagnostic for profiling and benchmarking. */
+unsigned long long gosh_kernel_launches(void);
 
 /* Checks a device CSR against the layout above (row pointer monotone,
  * neighbour ids in range, ascending, no self-loop, symmetric).  Synchronous.

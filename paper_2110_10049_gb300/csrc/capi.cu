@@ -1,6 +1,7 @@
 // The C ABI of libgosh (include/gosh.h): argument checks, the small kernels
 // around the training step (initialisation, copy projection, CSR validation,
 // pair scores and AUC) and the end-to-end driver of Alg. 2.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -22,6 +23,9 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 void clear_error() { g_error[0] = 0; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, const gosh_params *p,
                              cudaStream_t s, double *loss_per_epoch, unsigned long long *n_updates);
@@ -155,7 +159,7 @@ void launch_pair_scores(const void *M, int d, const int32_t *pairs, int64_t np, 
     int64_t g = ceil_div(groups * L, 256);
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    pair_scores_kernel<T, L><<<(int)g, 256, 0, s>>>(static_cast<const T *>(M), d, pairs, np, out);
+    (pair_scores_kernel<T, L><<<(int)g, 256, 0, s>>>(static_cast<const T *>(M), d, pairs, np, out), note_launch());
 }
 
 __global__ void score_keys(const float *__restrict__ score, int64_t n, uint32_t *__restrict__ key,
@@ -287,6 +291,25 @@ struct EventTimer {
     }
 };
 
+// A fixed set of events recorded on a stream and read after a synchronize.
+struct EventList {
+    std::vector<cudaEvent_t> e;
+    explicit EventList(int n) : e(n, nullptr) {
+        for (auto &x : e) cudaEventCreate(&x);
+    }
+    void record(int i, cudaStream_t s) {
+        if (i < (int)e.size()) cudaEventRecord(e[i], s);
+    }
+    double elapsed(int a, int b) const {
+        float ms = 0.f;
+        if (a < (int)e.size() && b < (int)e.size()) cudaEventElapsedTime(&ms, e[a], e[b]);
+        return ms;
+    }
+    ~EventList() {
+        for (auto &x : e) cudaEventDestroy(x);
+    }
+};
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -325,6 +348,8 @@ gosh_status gosh_params_default(gosh_params *p) {
 
 const char *gosh_last_error(void) { return g_error; }
 
+unsigned long long gosh_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
 gosh_status gosh_validate_csr(const gosh_csr *g, void *stream) {
     clear_error();
     GOSH_TRY(check_csr(g));
@@ -336,7 +361,7 @@ gosh_status gosh_validate_csr(const gosh_csr *g, void *stream) {
     unsigned long long *first = reinterpret_cast<unsigned long long *>(buf.as<char>() + 8);
     GOSH_TRY_CUDA(cudaMemsetAsync(flags, 0, 4, s));
     GOSH_TRY_CUDA(cudaMemsetAsync(first, 0xff, 8, s));
-    validate_kernel<<<grid_for(g->n), 256, 0, s>>>(g->rowptr, g->col, g->n, flags, first);
+    (validate_kernel<<<grid_for(g->n), 256, 0, s>>>(g->rowptr, g->col, g->n, flags, first), note_launch());
     unsigned hf = 0;
     unsigned long long hv = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&hf, flags, 4, cudaMemcpyDeviceToHost, s));
@@ -410,7 +435,7 @@ gosh_status gosh_init_embedding(void *M, int64_t n, int d, gosh_dtype dtype, int
     const int64_t work = n * ((d + 3) / 4);
     GOSH_TRY(by_dtype(dtype, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        init_kernel<T><<<grid_for(work), 256, 0, s>>>(static_cast<T *>(M), n, d, (uint32_t)level, seed, graph_id);
+        (init_kernel<T><<<grid_for(work), 256, 0, s>>>(static_cast<T *>(M), n, d, (uint32_t)level, seed, graph_id), note_launch());
     }));
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
@@ -436,8 +461,8 @@ gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *
     GOSH_CHECK_ARG(dtype_ok(dtype) && dim_ok(d, dtype), "bad d / dtype");
     cudaStream_t s = (cudaStream_t)stream;
     const int vecs = (int)(d * dtype_size(dtype) / 16);
-    project_copy_kernel<<<grid_for(n_fine * vecs), 256, 0, s>>>(static_cast<const uint4 *>(M_coarse), map,
-                                                                static_cast<uint4 *>(M_fine), n_fine, vecs);
+    (project_copy_kernel<<<grid_for(n_fine * vecs), 256, 0, s>>>(static_cast<const uint4 *>(M_coarse), map,
+                                                                static_cast<uint4 *>(M_fine), n_fine, vecs), note_launch());
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
 }
@@ -476,13 +501,13 @@ gosh_status gosh_link_auc(const void *M, int d, gosh_dtype dtype, const int32_t 
     GOSH_TRY(out.alloc(sizeof(double), s));
     GOSH_TRY(gosh_pair_scores(M, d, dtype, pos, npos, score.as<float>(), stream));
     GOSH_TRY(gosh_pair_scores(M, d, dtype, neg, nneg, score.as<float>() + npos, stream));
-    score_keys<<<grid, 256, 0, s>>>(score.as<float>(), n, key.as<uint32_t>(), idx.as<uint32_t>());
+    (score_keys<<<grid, 256, 0, s>>>(score.as<float>(), n, key.as<uint32_t>(), idx.as<uint32_t>()), note_launch());
     GOSH_TRY(radix_sort_u32(key.as<uint32_t>(), idx.as<uint32_t>(), n, 0, 32, s));
-    neg_flags<<<grid, 256, 0, s>>>(idx.as<uint32_t>(), n, npos, flag.as<uint8_t>());
+    (neg_flags<<<grid, 256, 0, s>>>(idx.as<uint32_t>(), n, npos, flag.as<uint8_t>()), note_launch());
     GOSH_TRY(scan_exclusive_u8_to_i64(flag.as<uint8_t>(), before.as<int64_t>(), n, before.as<int64_t>() + n, s));
-    auc_partials<<<grid, 256, 0, s>>>(key.as<uint32_t>(), idx.as<uint32_t>(), before.as<int64_t>(), n, npos,
-                                      parts.as<double>());
-    sum_partials<<<1, 256, 0, s>>>(parts.as<double>(), grid, out.as<double>());
+    (auc_partials<<<grid, 256, 0, s>>>(key.as<uint32_t>(), idx.as<uint32_t>(), before.as<int64_t>(), n, npos,
+                                      parts.as<double>()), note_launch());
+    (sum_partials<<<1, 256, 0, s>>>(parts.as<double>(), grid, out.as<double>()), note_launch());
     double U = 0.0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&U, out.ptr, sizeof(double), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
@@ -558,27 +583,28 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
     GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
 
     GOSH_TRY(gosh_init_embedding(buf(D - 1), h->n[D - 1], p.d, p.dtype, D - 1, p.seed, p.graph_id, stream));
-    double project_ms = 0.0;
-    std::vector<double> train_ms(D, 0.0);
+    // per-level events, read once at the end so that no level waits for the host
+    EventList ev(stats ? 2 * D + 1 : 0);
     for (int i = D - 1; i >= 0; --i) {
         gosh_csr gi{h->n[i], h->rowptr[i], h->col[i], 1};
-        {
-            EventTimer t(s);
-            GOSH_TRY(train_level_impl(&gi, buf(i), i, ep[i], &p, s, nullptr, counter.as<unsigned long long>()));
-            train_ms[i] = stats ? t.stop() : 0.0;
-        }
-        if (i > 0) {
-            EventTimer t(s);
+        ev.record(2 * i + 1, s);
+        GOSH_TRY(train_level_impl(&gi, buf(i), i, ep[i], &p, s, nullptr, counter.as<unsigned long long>()));
+        ev.record(2 * i, s);
+        if (i > 0)
             GOSH_TRY(gosh_project(buf(i), h->n[i], h->map[i - 1], buf(i - 1), h->n[i - 1], p.d, p.dtype, stream));
-            if (stats) project_ms += t.stop();
-        }
     }
+    std::vector<double> train_ms(D, 0.0);
+    double project_ms = 0.0;
     if (!out_dev)
         GOSH_TRY_CUDA(cudaMemcpyAsync(M0_out, even, row_bytes * g.n, cudaMemcpyDeviceToHost, s));
     unsigned long long updates = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&updates, counter.ptr, sizeof(updates), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     if (stats) {
+        for (int i = 0; i < D; ++i) {
+            train_ms[i] = ev.elapsed(2 * i + 1, 2 * i);
+            if (i > 0) project_ms += ev.elapsed(2 * i, 2 * i - 1);
+        }
         memset(stats, 0, sizeof(*stats));
         stats->levels = D;
         for (int i = 0; i < D && i < GOSH_MAX_LEVELS; ++i) {

@@ -206,10 +206,10 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     GOSH_TRY(counter.alloc(sizeof(unsigned long long) * 2, s));
 
     // 1. degree order
-    degree_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>());
+    (degree_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>()), note_launch());
     GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), vals.as<uint32_t>(), n, 0, 32, s));
     const uint32_t *order = vals.as<uint32_t>();
-    invert_order<<<grid_1d(n), 256, 0, s>>>(order, n, rank.as<int32_t>());
+    (invert_order<<<grid_1d(n), 256, 0, s>>>(order, n, rank.as<int32_t>()), note_launch());
     GOSH_TRY_CUDA(cudaMemsetAsync(state.ptr, 0, n, s));
 
     // 2. MIS rounds
@@ -221,8 +221,8 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
             return GOSH_ERR_CUDA;
         }
         GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
-        mis_round<<<grid_warps(ceil_div(n, 32)), 256, 0, s>>>(rowptr, col, n, order, rank.as<int32_t>(),
-                                                               state.as<uint8_t>(), counter.as<unsigned long long>());
+        (mis_round<<<grid_warps(ceil_div(n, 32)), 256, 0, s>>>(rowptr, col, n, order, rank.as<int32_t>(),
+                                                               state.as<uint8_t>(), counter.as<unsigned long long>()), note_launch());
         GOSH_TRY_CUDA(cudaMemcpyAsync(&left, counter.ptr, sizeof(left), cudaMemcpyDeviceToHost, s));
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
         ++rounds;
@@ -230,13 +230,13 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     if (rounds_out) *rounds_out = rounds;
 
     // 3. attach non-hubs, number the clusters by hub rank
-    attach_to_hub<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
-                                                 hub_rank.as<int32_t>());
-    hub_flags_by_rank<<<grid_1d(n), 256, 0, s>>>(order, state.as<uint8_t>(), n, flags.as<uint8_t>());
+    (attach_to_hub<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
+                                                 hub_rank.as<int32_t>()), note_launch());
+    (hub_flags_by_rank<<<grid_1d(n), 256, 0, s>>>(order, state.as<uint8_t>(), n, flags.as<uint8_t>()), note_launch());
     GOSH_TRY(scan_exclusive_u8_to_i64(flags.as<uint8_t>(), cid.as<int64_t>(), n, cid.as<int64_t>() + n, s));
     GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
-    assign_map<<<grid_1d(n), 256, 0, s>>>(hub_rank.as<int32_t>(), cid.as<int64_t>(), n, map,
-                                          counter.as<unsigned long long>());
+    (assign_map<<<grid_1d(n), 256, 0, s>>>(hub_rank.as<int32_t>(), cid.as<int64_t>(), n, map,
+                                          counter.as<unsigned long long>()), note_launch());
     int64_t nc = 0;
     unsigned long long orphans = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&nc, cid.as<int64_t>() + n, sizeof(nc), cudaMemcpyDeviceToHost, s));
@@ -266,21 +266,21 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
         GOSH_TRY(pos.alloc(sizeof(int64_t) * (nnz + 1), s));
         GOSH_TRY(cnt.alloc(sizeof(unsigned long long) * nc, s));
         const uint64_t sentinel = (uint64_t)nc << 32;
-        edge_image<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, map, sentinel, ek.as<uint64_t>());
+        (edge_image<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, map, sentinel, ek.as<uint64_t>()), note_launch());
         int shifts[8];
         int nd = 0;
         const int bb = bits_for((uint64_t)(nc > 0 ? nc - 1 : 0)), ba = bits_for((uint64_t)nc);
         for (int b = 0; b < bb; b += 8) shifts[nd++] = b;
         for (int b = 0; b < ba; b += 8) shifts[nd++] = 32 + b;
         GOSH_TRY(radix_sort_u64(ek.as<uint64_t>(), nullptr, nnz, shifts, nd, s));
-        unique_flags<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), nnz, sentinel, fl.as<uint8_t>());
+        (unique_flags<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), nnz, sentinel, fl.as<uint8_t>()), note_launch());
         GOSH_TRY(scan_exclusive_u8_to_i64(fl.as<uint8_t>(), pos.as<int64_t>(), nnz, pos.as<int64_t>() + nnz, s));
         GOSH_TRY_CUDA(cudaMemcpyAsync(&m, pos.as<int64_t>() + nnz, sizeof(m), cudaMemcpyDeviceToHost, s));
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
         GOSH_TRY_CUDA(cudaMalloc(&co, sizeof(int32_t) * (m > 0 ? m : 1)));
         GOSH_TRY_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(unsigned long long) * nc, s));
-        write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz, co,
-                                                  cnt.as<unsigned long long>());
+        (write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz, co,
+                                                  cnt.as<unsigned long long>()), note_launch());
         GOSH_TRY(scan_exclusive_i64(reinterpret_cast<const int64_t *>(cnt.ptr), rp, nc, rp + nc, s));
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     } else {

@@ -18,6 +18,9 @@ namespace gosh {
 void set_error(const char *fmt, ...);
 void clear_error();
 
+// Process-wide count of kernel launches made by this library (diagnostics).
+void note_launch();
+
 #define GOSH_TRY_CUDA(expr)                                                              \
     do {                                                                                 \
         cudaError_t e_ = (expr);                                                         \

@@ -88,16 +88,16 @@ gosh_status scan_exclusive(const In *in, int64_t *out, int64_t n, int64_t *total
     }
     const int64_t tiles = ceil_div(n, kScanTile);
     if (tiles == 1) {
-        scan_tile_apply<In><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        (scan_tile_apply<In><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr), note_launch());
     } else {
         Scratch sums, offs;
         GOSH_TRY(sums.alloc(sizeof(int64_t) * tiles, s));
         GOSH_TRY(offs.alloc(sizeof(int64_t) * tiles, s));
-        scan_tile_sums<In><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>());
+        (scan_tile_sums<In><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>()), note_launch());
         GOSH_TRY(scan_exclusive<int64_t>(sums.as<int64_t>(), offs.as<int64_t>(), tiles, nullptr, s));
-        scan_tile_apply<In><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, offs.as<int64_t>());
+        (scan_tile_apply<In><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, offs.as<int64_t>()), note_launch());
     }
-    if (total) write_total_t<In><<<1, 1, 0, s>>>(in, out, n, total);
+    if (total) (write_total_t<In><<<1, 1, 0, s>>>(in, out, n, total), note_launch());
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
 }
@@ -198,16 +198,16 @@ gosh_status radix_sort(K *keys, uint32_t *vals, int64_t n, const int *shifts, in
     K *ka = keys, *kb = kalt.as<K>();
     uint32_t *va = vals, *vb = valt.as<uint32_t>();
     for (int d = 0; d < ndigits; ++d) {
-        radix_hist<K><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, n, shifts[d], counts.as<int64_t>(),
-                                                                  nblocks);
+        (radix_hist<K><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, n, shifts[d], counts.as<int64_t>(),
+                                                                  nblocks), note_launch());
         GOSH_TRY(scan_exclusive<int64_t>(counts.as<int64_t>(), offs.as<int64_t>(), 256 * nblocks,
                                          nullptr, s));
         if (vals)
-            radix_scatter<K, true><<<(unsigned)nblocks, kSortThreads, 0, s>>>(
-                ka, va, kb, vb, n, shifts[d], offs.as<int64_t>(), nblocks);
+            (radix_scatter<K, true><<<(unsigned)nblocks, kSortThreads, 0, s>>>(
+                ka, va, kb, vb, n, shifts[d], offs.as<int64_t>(), nblocks), note_launch());
         else
-            radix_scatter<K, false><<<(unsigned)nblocks, kSortThreads, 0, s>>>(
-                ka, nullptr, kb, nullptr, n, shifts[d], offs.as<int64_t>(), nblocks);
+            (radix_scatter<K, false><<<(unsigned)nblocks, kSortThreads, 0, s>>>(
+                ka, nullptr, kb, nullptr, n, shifts[d], offs.as<int64_t>(), nblocks), note_launch());
         GOSH_TRY_CUDA(cudaGetLastError());
         K *kt = ka; ka = kb; kb = kt;
         uint32_t *vt = va; va = vb; vb = vt;

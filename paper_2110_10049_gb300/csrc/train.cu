@@ -68,12 +68,12 @@ void det_apply(gosh_dtype dtype, int d, const uint32_t *skeys, const uint32_t *s
 
 }  // namespace
 
-const TrainKernel *find_train_kernel(gosh_dtype dtype, int d, int lanes, int pass, bool det) {
+const TrainKernel *find_train_kernel(gosh_dtype dtype, int d, int lanes, int pass, int mode) {
     Registry &r = registry();
     std::lock_guard<std::mutex> lock(r.mu);
     for (size_t i = 0; i < r.entries.size(); ++i) {
         const TrainEntry &e = r.entries[i];
-        if (e.dtype == dtype && e.d == d && e.lanes == lanes && e.pass == pass && e.det == det) {
+        if (e.dtype == dtype && e.d == d && e.lanes == lanes && e.pass == pass && e.mode == mode) {
             if (!r.ready[i]) {
                 r.made[i] = e.make();
                 r.ready[i] = true;
@@ -84,11 +84,11 @@ const TrainKernel *find_train_kernel(gosh_dtype dtype, int d, int lanes, int pas
     return nullptr;
 }
 
-int list_train_variants(gosh_dtype dtype, int d, bool det, int *lanes, int *pass, int cap) {
+int list_train_variants(gosh_dtype dtype, int d, int mode, int *lanes, int *pass, int cap) {
     Registry &r = registry();
     int c = 0;
     for (const TrainEntry &e : r.entries)
-        if (e.dtype == dtype && e.d == d && e.det == det && c < cap) {
+        if (e.dtype == dtype && e.d == d && e.mode == mode && c < cap) {
             lanes[c] = e.lanes;
             pass[c] = e.pass;
             ++c;
@@ -99,8 +99,17 @@ int list_train_variants(gosh_dtype dtype, int d, bool det, int *lanes, int *pass
 // Natural lanes per row: one 16-byte vector per lane.
 int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) / 16; }
 
-gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, bool det, int lanes, int pass,
+// Kernel mode for the parameters: deterministic batches, or the lock-free
+// epoch with atomic FP32 row changes unless plain stores are requested (and
+// always plain stores with stochastic rounding for 16-bit tables).
+int train_mode(const gosh_params *p) {
+    if (p->mode == GOSH_DETERMINISTIC) return kModeDet;
+    return (p->dtype == GOSH_F32 && !p->plain_stores) ? kModeRed : kModeStore;
+}
+
+gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lanes, int pass,
                               const TrainKernel **out) {
+    const bool det = mode == kModeDet;
     const int ns = k + 1;
     if (lanes <= 0) lanes = natural_lanes(dtype, d);
     if (pass <= 0) pass = det ? (ns <= 4 ? 4 : 8) : (ns <= 2 ? 2 : 4);
@@ -109,10 +118,10 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, bool det, int lane
                   pass, ns);
         return GOSH_ERR_UNSUPPORTED;
     }
-    const TrainKernel *kern = find_train_kernel(dtype, d, lanes, pass, det);
+    const TrainKernel *kern = find_train_kernel(dtype, d, lanes, pass, mode);
     if (!kern) {
-        set_error("no training kernel for dtype %d, d %d, lanes_per_row %d, samples_per_pass %d, %s",
-                  (int)dtype, d, lanes, pass, det ? "deterministic" : "hogwild");
+        set_error("no training kernel for dtype %d, d %d, lanes_per_row %d, samples_per_pass %d, mode %d",
+                  (int)dtype, d, lanes, pass, mode);
         return GOSH_ERR_UNSUPPORTED;
     }
     *out = kern;
@@ -127,7 +136,7 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
         return GOSH_ERR_UNSUPPORTED;
     }
     const TrainKernel *kern = nullptr;
-    GOSH_TRY(pick_train_kernel(p->dtype, p->d, p->k, det, p->lanes_per_row, p->samples_per_pass, &kern));
+    GOSH_TRY(pick_train_kernel(p->dtype, p->d, p->k, train_mode(p), p->lanes_per_row, p->samples_per_pass, &kern));
     const int64_t n = g->n;
     if (epochs <= 0 || n <= 0) return GOSH_OK;
     const int ns = p->k + 1;
@@ -164,7 +173,7 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
             a.epoch = (uint32_t)j;
             kern->launch(a, grid, s);
             if (loss_per_epoch)
-                loss_finalize<<<1, 256, 0, s>>>(parts.as<double>(), grid, loss_per_epoch + j, 0);
+                (loss_finalize<<<1, 256, 0, s>>>(parts.as<double>(), grid, loss_per_epoch + j, 0), note_launch());
         }
         GOSH_TRY_CUDA(cudaGetLastError());
         return GOSH_OK;
@@ -199,8 +208,8 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
             const int grid = grid_for(b1 - b0);
             kern->launch(a, grid, s);
             if (loss_per_epoch)
-                loss_finalize<<<1, 256, 0, s>>>(parts.as<double>(), grid, loss_per_epoch + j, b0 > 0);
-            iota_u32<<<(int)std::min<int64_t>(ceil_div(nsl, 256), 4096), 256, 0, s>>>(idx.as<uint32_t>(), nsl);
+                (loss_finalize<<<1, 256, 0, s>>>(parts.as<double>(), grid, loss_per_epoch + j, b0 > 0), note_launch());
+            (iota_u32<<<(int)std::min<int64_t>(ceil_div(nsl, 256), 4096), 256, 0, s>>>(idx.as<uint32_t>(), nsl), note_launch());
             GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), idx.as<uint32_t>(), nsl, 0, kbits, s));
             GOSH_TRY_CUDA(cudaMemsetAsync(done.ptr, 0, (size_t)(b1 - b0), s));
             const uint32_t sr = mix32((uint32_t)p->seed ^ mix32((uint32_t)(level << 20) ^ (uint32_t)j)) ^

@@ -20,6 +20,9 @@ constexpr int kMaxK = 15;        // negatives per positive
 constexpr int kTrainWarps = 8;   // warps per block
 constexpr int kSlotStride = kMaxK + 2;  // padded per-source sample-id slots in smem
 
+// How a kernel writes its row changes (see train_kernels.cuh).
+enum : int { kModeStore = 0, kModeRed = 1, kModeDet = 2 };
+
 struct TrainArgs {
     const int64_t *rowptr;
     const int32_t *col;
@@ -52,7 +55,7 @@ struct TrainKernel {
 struct TrainEntry {
     gosh_dtype dtype;
     int d, lanes, pass;
-    bool det;
+    int mode;
     TrainKernel (*make)();
 };
 const TrainEntry *train_entries_f32(int *count);
@@ -68,12 +71,12 @@ void det_apply_f16(int d, const uint32_t *skeys, const uint32_t *sidx, int64_t n
                    const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
                    uint32_t sr_seed, cudaStream_t s);
 
-// Looks up the kernel for (dtype, d, lanes-per-row, samples-per-pass, det).
+// Looks up the kernel for (dtype, d, lanes-per-row, samples-per-pass, mode).
 // Returns nullptr if that combination is not compiled.
-const TrainKernel *find_train_kernel(gosh_dtype dtype, int d, int lanes, int pass, bool det);
+const TrainKernel *find_train_kernel(gosh_dtype dtype, int d, int lanes, int pass, int mode);
 
-// Lists the lanes-per-row and samples-per-pass variants compiled for (dtype, d, det).
-int list_train_variants(gosh_dtype dtype, int d, bool det, int *lanes, int *pass, int cap);
+// Lists the lanes-per-row and samples-per-pass variants compiled for (dtype, d, mode).
+int list_train_variants(gosh_dtype dtype, int d, int mode, int *lanes, int *pass, int cap);
 
 // Deterministic-mode end-of-batch kernels.
 void launch_det_apply(gosh_dtype dtype, int d, const uint32_t *skeys, const uint32_t *sidx,

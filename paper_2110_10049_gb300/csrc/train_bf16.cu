@@ -9,10 +9,10 @@ constexpr int L64 = 64 * (int)sizeof(T) / 16;
 constexpr int L128 = 128 * (int)sizeof(T) / 16;
 constexpr gosh_dtype kType = GOSH_BF16;
 
-#define GOSH_V(D, L, P, DET) {kType, D, L, P, DET, &make_train_kernel<T, D, L, P, DET>}
-#define GOSH_VD(D, L0)                                                                     \
-    GOSH_V(D, L0, 2, false), GOSH_V(D, L0, 4, false), GOSH_V(D, (L0 > 1 ? L0 / 2 : 1), 2, false), \
-        GOSH_V(D, (L0 > 1 ? L0 / 2 : 1), 4, false), GOSH_V(D, L0, 4, true), GOSH_V(D, L0, 8, true)
+#define GOSH_V(D, L, P, MODE) {kType, D, L, P, MODE, &make_train_kernel<T, D, L, P, MODE>}
+#define GOSH_VD(D, L0)                                                                               \
+    GOSH_V(D, L0, 2, kModeStore), GOSH_V(D, L0, 4, kModeStore), GOSH_V(D, L0 / 2, 2, kModeStore),    \
+        GOSH_V(D, L0 / 2, 4, kModeStore), GOSH_V(D, L0, 4, kModeDet), GOSH_V(D, L0, 8, kModeDet)
 
 const TrainEntry kEntries[] = {GOSH_VD(32, L32), GOSH_VD(64, L64), GOSH_VD(128, L128)};
 #undef GOSH_VD

@@ -58,6 +58,18 @@ __device__ __forceinline__ void store_f32(float *__restrict__ p, const float *f)
     for (int v = 0; v < E / 4; ++v) q[v] = make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
 }
 
+// Atomic vector addition at L2 (fire-and-forget): M[p..p+3] += f[0..3].
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+template <int E>
+__device__ __forceinline__ void red_row(float *p, const float *f) {
+#pragma unroll
+    for (int v = 0; v < E / 4; ++v) red_add_v4(p + 4 * v, f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+}
+
 template <int L>
 __device__ __forceinline__ float group_sum(float x) {
 #pragma unroll
@@ -66,12 +78,21 @@ __device__ __forceinline__ float group_sum(float x) {
 }
 
 /*
- * One epoch (Hogwild) or one snapshot batch (DET) over sources
+ * One epoch (Hogwild) or one snapshot batch (deterministic) over sources
  * [src_begin, src_end).  Template: storage T, dimension D, L lanes per source,
- * P sample rows gathered per pass.  DET requires P >= k+1 (one pass).
+ * P sample rows gathered per pass, MODE:
+ *   kModeStore  lock-free epoch, rows written back with plain stores (the
+ *               paper's scheme; concurrent writers to one row may lose updates);
+ *   kModeRed    lock-free epoch, FP32 rows changed by atomic vector additions
+ *               of the update (M[u] += score * M[v]; M[v] += its net change),
+ *               so concurrent updates are never lost, only read stale;
+ *   kModeDet    snapshot batch, changes written to R/C/keys (needs P >= k+1).
  */
-template <typename T, int D, int L, int P, bool DET>
+template <typename T, int D, int L, int P, int MODE>
 __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
+    constexpr bool DET = MODE == kModeDet;
+    constexpr bool RED = MODE == kModeRed;
+    static_assert(!RED || std::is_same<T, float>::value, "atomic row updates need FP32 tables");
     constexpr int E = D / L;
     constexpr int PV = Store<T>::kPerVec;
     constexpr int G = 32 / L;
@@ -139,6 +160,11 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[e] = 0.0f;
             }
+            float r0[RED ? E : 1];
+            if (RED) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) r0[e] = r[e];
+            }
 #pragma unroll 1
             for (int p0 = 0; p0 < ns; p0 += P) {
                 int32_t us[P];
@@ -181,6 +207,11 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
                             for (int e = 0; e < E; ++e) c[e] = r[e] * score;
                             store_f32<E>(a.C + slot * D + gl * E, c);
                             if (gl == 0) a.keys[slot] = (uint32_t)us[s];
+                        } else if (RED) {
+                            float c[E];
+#pragma unroll
+                            for (int e = 0; e < E; ++e) c[e] = r[e] * score;
+                            red_row<E>(reinterpret_cast<float *>(M) + (int64_t)us[s] * D + gl * E, c);
                         } else {
                             store_row<T, D, E>(M + (int64_t)us[s] * D + gl * E, row[s], sr, t, gl * E);
                         }
@@ -202,8 +233,16 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
                 }
             }
             if (active) {
-                if (DET) store_f32<E>(a.R + (v - a.src_begin) * D + gl * E, r);
-                else store_row<T, D, E>(M + v * D + gl * E, r, sr, ns, gl * E);
+                if (DET) {
+                    store_f32<E>(a.R + (v - a.src_begin) * D + gl * E, r);
+                } else if (RED) {
+                    float dr[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) dr[e] = r[e] - r0[RED ? e : 0];
+                    red_row<E>(reinterpret_cast<float *>(M) + v * D + gl * E, dr);
+                } else {
+                    store_row<T, D, E>(M + v * D + gl * E, r, sr, ns, gl * E);
+                }
             }
         }
         __syncwarp();
@@ -229,17 +268,17 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
     }
 }
 
-template <typename T, int D, int L, int P, bool DET>
+template <typename T, int D, int L, int P, int MODE>
 void launch_train(const TrainArgs &a, int grid, cudaStream_t s) {
-    train_kernel<T, D, L, P, DET><<<grid, kTrainWarps * 32, 0, s>>>(a);
+    (train_kernel<T, D, L, P, MODE><<<grid, kTrainWarps * 32, 0, s>>>(a), note_launch());
 }
 
-template <typename T, int D, int L, int P, bool DET>
+template <typename T, int D, int L, int P, int MODE>
 TrainKernel make_train_kernel() {
     TrainKernel k;
-    k.launch = &launch_train<T, D, L, P, DET>;
+    k.launch = &launch_train<T, D, L, P, MODE>;
     k.blocks_per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.blocks_per_sm, train_kernel<T, D, L, P, DET>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.blocks_per_sm, train_kernel<T, D, L, P, MODE>,
                                                   kTrainWarps * 32, 0);
     if (k.blocks_per_sm < 1) k.blocks_per_sm = 1;
     k.lanes = L;
@@ -323,11 +362,11 @@ void launch_det_apply_t(const uint32_t *skeys, const uint32_t *sidx, int64_t nsl
     const int64_t g2 = ceil_div(b1 - b0, groups_per_block);
     const int cap = num_sms() * 8;
     if (nslots > 0)
-        det_apply_segments<T, D, LL><<<(int)(g1 < cap ? (g1 > 0 ? g1 : 1) : cap), 256, 0, s>>>(
-            skeys, sidx, nslots, C, R, static_cast<T *>(M), n, b0, b1, src_done, sr_seed);
+        (det_apply_segments<T, D, LL><<<(int)(g1 < cap ? (g1 > 0 ? g1 : 1) : cap), 256, 0, s>>>(
+            skeys, sidx, nslots, C, R, static_cast<T *>(M), n, b0, b1, src_done, sr_seed), note_launch());
     if (b1 > b0)
-        det_apply_sources<T, D, LL><<<(int)(g2 < cap ? (g2 > 0 ? g2 : 1) : cap), 256, 0, s>>>(
-            R, static_cast<T *>(M), b0, b1, src_done, sr_seed ^ 0x9e3779b9u);
+        (det_apply_sources<T, D, LL><<<(int)(g2 < cap ? (g2 > 0 ? g2 : 1) : cap), 256, 0, s>>>(
+            R, static_cast<T *>(M), b0, b1, src_done, sr_seed ^ 0x9e3779b9u), note_launch());
 }
 
 }  // namespace gosh

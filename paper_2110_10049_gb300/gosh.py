@@ -38,7 +38,8 @@ class gosh_params(C.Structure):
                 ("epochs", C.c_int), ("p", C.c_double), ("threshold", C.c_int), ("shrink", C.c_double),
                 ("max_levels", C.c_int), ("dtype", C.c_int), ("mode", C.c_int), ("det_batch", C.c_int64),
                 ("seed", C.c_uint64), ("graph_id", C.c_uint64), ("lanes_per_row", C.c_int),
-                ("samples_per_pass", C.c_int), ("device_budget_bytes", C.c_int64), ("validate", C.c_int)]
+                ("samples_per_pass", C.c_int), ("device_budget_bytes", C.c_int64), ("validate", C.c_int),
+                ("plain_stores", C.c_int)]
 
 
 class gosh_stats(C.Structure):

@@ -43,26 +43,60 @@ class LinkSplit:
     test_neg: np.ndarray  # int32 [m, 2] in train ids
 
 
-def rmat_edges(scale: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19,
-               chunk: int = 1 << 24) -> tuple[np.ndarray, np.ndarray]:
-    """Directed R-MAT draws (step 1 and 2 of the recipe)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
+_LIB = None
+
+
+def _clib():
+    """Builds and loads synth/librmatgen.so (gcc, OpenMP)."""
+    global _LIB
+    if _LIB is None:
+        import ctypes as C
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src, so = os.path.join(here, "rmatgen.c"), os.path.join(here, "librmatgen.so")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            tmp = so + ".tmp%d" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src])
+            os.replace(tmp, so)
+        L = C.CDLL(so)
+        vp, i64, u64, f64, i32 = C.c_void_p, C.c_int64, C.c_uint64, C.c_double, C.c_int
+        L.rmat_edges.argtypes = [i32, i64, u64, f64, f64, f64, vp, vp]
+        L.rmat_edges.restype = None
+        L.csr_build.argtypes = [i64, i64, vp, vp, i32, vp, vp, vp, vp, vp]
+        L.csr_build.restype = i64
+        L.link_split.argtypes = [i64, vp, vp, u64, f64, vp, vp, vp, vp, vp, vp, vp]
+        L.link_split.restype = i64
+        _LIB = L
+    return _LIB
+
+
+def _p(a):
+    import ctypes as C
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def rmat_edges(scale: int, edge_factor: int, seed: int, a=0.57, b=0.19, c=0.19):
+    """Directed R-MAT draws followed by a seeded relabelling (steps 1-2)."""
     m = edge_factor << scale
-    src = np.zeros(m, dtype=np.uint32)
-    dst = np.zeros(m, dtype=np.uint32)
-    ab, abc = a + b, a + b + c
-    for s0 in range(0, m, chunk):
-        s1 = min(m, s0 + chunk)
-        u = np.zeros(s1 - s0, dtype=np.uint32)
-        v = np.zeros(s1 - s0, dtype=np.uint32)
-        for _ in range(scale):
-            r = rng.random(s1 - s0, dtype=np.float32)
-            u = (u << 1) | (r >= ab).astype(np.uint32)
-            v = (v << 1) | (((r >= a) & (r < ab)) | (r >= abc)).astype(np.uint32)
-        src[s0:s1] = u
-        dst[s0:s1] = v
-    perm = rng.permutation(1 << scale).astype(np.uint32)
-    return perm[src], perm[dst]
+    src = np.empty(m, dtype=np.uint32)
+    dst = np.empty(m, dtype=np.uint32)
+    _clib().rmat_edges(scale, m, seed, a, b, c, _p(src), _p(dst))
+    return src, dst
+
+
+def _csr_c(n: int, src: np.ndarray, dst: np.ndarray, compact: bool) -> Graph:
+    import ctypes as C
+    src = np.ascontiguousarray(src, dtype=np.uint32)
+    dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    m = len(src)
+    work = np.empty(max(4 * m, 2), dtype=np.uint64)
+    nn = C.c_int64()
+    nnz = _clib().csr_build(n, m, _p(src), _p(dst), int(compact), _p(work), C.byref(nn), None, None, None)
+    rowptr = np.zeros(nn.value + 1, dtype=np.int64)
+    col = np.empty(max(nnz, 1), dtype=np.int32)
+    _clib().csr_build(n, m, _p(src), _p(dst), int(compact), _p(work), C.byref(nn), _p(rowptr), _p(col), None)
+    return Graph(rowptr, col[:nnz])
 
 
 def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, compact: bool = True) -> Graph:
@@ -93,7 +127,7 @@ def to_csr(n, src, dst, compact=True) -> Graph:
 
 def rmat_graph(scale: int, edge_factor: int, seed: int, **kw) -> Graph:
     s, d = rmat_edges(scale, edge_factor, seed, **kw)
-    return csr_from_edges(1 << scale, s, d)
+    return _csr_c(1 << scale, s, d, compact=True)
 
 
 def random_graph(n: int, p: float, seed: int, compact: bool = False) -> Graph:
@@ -105,49 +139,23 @@ def random_graph(n: int, p: float, seed: int, compact: bool = False) -> Graph:
 
 
 def link_split(g: Graph, seed: int, test_frac: float = 0.2) -> LinkSplit:
-    rng = np.random.Generator(np.random.PCG64(seed ^ 0x5EED))
-    n = g.n
-    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.rowptr))
-    dst = g.col.astype(np.int64)
-    und = src < dst
-    eu, ev = src[und], dst[und]
-    order = rng.permutation(len(eu))
-    ntest = int(round(test_frac * len(eu)))
-    test_idx, train_idx = order[:ntest], order[ntest:]
-    tr = csr_from_edges(n, eu[train_idx], ev[train_idx], compact=False)
-    deg = np.diff(tr.rowptr)
-    present = deg > 0
-    newid = np.cumsum(present, dtype=np.int64) - 1
-    # compact the training graph
-    tsrc = np.repeat(np.arange(n, dtype=np.int64), deg)
-    keep_rows = present[tsrc]
-    rowptr = np.zeros(int(present.sum()) + 1, dtype=np.int64)
-    np.cumsum(deg[present], out=rowptr[1:])
-    train = Graph(rowptr, newid[tr.col.astype(np.int64)][keep_rows].astype(np.int32))
-    tu, tv = eu[test_idx], ev[test_idx]
-    ok = present[tu] & present[tv]
-    test_pos = np.stack([newid[tu[ok]], newid[tv[ok]]], axis=1).astype(np.int32)
-    # negatives: uniform pairs over V_train, not an edge of the full graph
-    nt = train.n
-    full_keys = set()
-    if nt > 0:
-        fk = (newid[src[present[src] & present[dst]]] * nt + newid[dst[present[src] & present[dst]]])
-        full_keys = np.unique(fk)
-    negs = []
-    need = len(test_pos)
-    while need > 0 and nt > 1:
-        cu = rng.integers(0, nt, size=2 * need + 16)
-        cv = rng.integers(0, nt, size=2 * need + 16)
-        ok = cu != cv
-        cu, cv = cu[ok], cv[ok]
-        hit = np.isin(cu * nt + cv, full_keys)
-        cu, cv = cu[~hit], cv[~hit]
-        take = min(need, len(cu))
-        negs.append(np.stack([cu[:take], cv[:take]], axis=1))
-        need -= take
-    test_neg = (np.concatenate(negs).astype(np.int32) if negs
-                else np.zeros((0, 2), dtype=np.int32))
-    return LinkSplit(train, test_pos, test_neg)
+    import ctypes as C
+    n, nnz = g.n, g.nnz
+    ne = nnz // 2
+    work = np.empty(ne + (4 * n + ne) // 8 + 2, dtype=np.uint64)
+    ntr, nte = C.c_int64(), C.c_int64()
+    rp, co = np.ascontiguousarray(g.rowptr, np.int64), np.ascontiguousarray(g.col, np.int32)
+    if co.size == 0:
+        co = np.zeros(1, dtype=np.int32)
+    m2 = _clib().link_split(n, _p(rp), _p(co), seed, test_frac, _p(work), C.byref(ntr), C.byref(nte),
+                            None, None, None, None)
+    trp = np.zeros(ntr.value + 1, dtype=np.int64)
+    tco = np.empty(max(m2, 1), dtype=np.int32)
+    pos = np.empty((max(nte.value, 1), 2), dtype=np.int32)
+    neg = np.empty((max(nte.value, 1), 2), dtype=np.int32)
+    _clib().link_split(n, _p(rp), _p(co), seed, test_frac, _p(work), C.byref(ntr), C.byref(nte),
+                       _p(trp), _p(tco), _p(pos), _p(neg))
+    return LinkSplit(Graph(trp, tco[:m2]), pos[:nte.value], neg[:nte.value])
 
 
 # Named workloads: R-MAT parameters of the benchmark configurations.
