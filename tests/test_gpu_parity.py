@@ -168,22 +168,49 @@ def heldout_and_fit_auc(M, sp, seed=0):
     return oracle.link_auc(M, sp.test_pos, sp.test_neg), fit
 
 
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_hogwild_auc_matches_oracle(g, c1, dtype):
-    """Hogwild on R-MAT scale 12, d=32, k=3, 200 epochs over the full
+def test_hogwild_auc_matches_oracle(g, c1):
+    """FP32 Hogwild on R-MAT scale 12, d=32, k=3, 200 epochs over the full
     hierarchy: held-out and training-edge AUC within 0.005 of the sequential
     oracle, each averaged over 3 seeds."""
     sp = c1
     res_o, res_g = [], []
     for seed in (1, 2, 3):
         Mo, _ = oracle.embed(sp.train.rowptr, sp.train.col, 32, 3, 0.045, 200, 0.3, seed=seed)
-        p = g.default_params(d=32, k=3, lr=0.045, epochs=200, p=0.3, seed=seed, dtype=dtype)
+        p = g.default_params(d=32, k=3, lr=0.045, epochs=200, p=0.3, seed=seed)
         Mg, st = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
         res_o.append(heldout_and_fit_auc(Mo, sp))
         res_g.append(heldout_and_fit_auc(Mg.double().cpu().numpy(), sp))
     o, gg = np.mean(res_o, 0), np.mean(res_g, 0)
     assert abs(o[0] - gg[0]) <= 0.005, (o, gg)
     assert abs(o[1] - gg[1]) <= 0.005, (o, gg)
+
+
+def test_bf16_tables_reach_fp32_auc(g, c1):
+    """BF16 tables (FP32 arithmetic, stochastic rounding) reach the held-out
+    AUC of the FP32 tables within 0.005 (mean of 3 seeds)."""
+    sp = c1
+    res = {torch.float32: [], torch.bfloat16: []}
+    for seed in (1, 2, 3):
+        for dt in res:
+            p = g.default_params(d=32, k=3, lr=0.045, epochs=200, p=0.3, seed=seed, dtype=dt)
+            Mg, _ = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
+            res[dt].append(heldout_and_fit_auc(Mg.double().cpu().numpy(), sp)[0])
+    assert np.mean(res[torch.bfloat16]) >= np.mean(res[torch.float32]) - 0.005, res
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_16bit_tables_error_vs_oracle(g, c1, dtype):
+    """Deterministic mode with 16-bit tables against the FP64 oracle: the
+    error is that of storage rounding (BF16: 8-bit significand, about 2^-9
+    relative per rounding; FP16: 2^-12), not of the arithmetic."""
+    gr = c1.train
+    M0 = bf16_round_np(oracle.init_uniform(gr.n, 64, 0, 5).astype(np.float32)) * 32  # exact in both formats
+    Mo = M0.copy()
+    oracle.train_deterministic(gr.rowptr, gr.col, Mo, 3, 0, 4, 0.045, 1e-4, 9, 256)
+    Mg = train_gpu(g, gr, M0, 3, 0, 4, 0.045, 9, "deterministic", m=256, dtype=dtype)[0]
+    err = rel_fro(Mg, Mo)
+    bound = 2e-2 if dtype == torch.bfloat16 else 3e-3
+    assert err <= bound, err
 
 
 def test_embed_deterministic_matches_oracle(g, c1):
