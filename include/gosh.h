@@ -179,6 +179,34 @@ gosh_status gosh_train_level(const gosh_csr *g, void *M, int level, int epochs,
                              const gosh_params *params, void *stream,
                              double *loss_per_epoch, unsigned long long *n_updates);
 
+/*
+ * gosh_train_level for callers that cannot allocate device memory (the paper
+ * has no counterpart; this is a deployment variant).  Callers that run inside
+ * a framework or server owning all device memory through its own arena, or
+ * that must never let a library call cudaMalloc/cudaFree (which can
+ * synchronise the device), use this entry point: it allocates nothing.  The
+ * caller still passes the graph, M, loss_per_epoch and n_updates buffers,
+ * with the same meaning, layout and results as gosh_train_level.
+ * Limits and behaviour:
+ *  - GOSH_HOGWILD only; GOSH_DETERMINISTIC returns GOSH_ERR_UNSUPPORTED (its
+ *    scratch grows with det_batch).
+ *  - The per-block loss partial sums live in one static device array of 4096
+ *    FP64 values (32 KB), held by every GPU that loads the library until the
+ *    process exits.  A launch needing more blocks than that returns
+ *    GOSH_ERR_INVALID_ARG before any kernel runs (a GB300 launch uses at most
+ *    152 SMs x 8 blocks = 1216).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture starts.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents (each launch overwrites the slots it reads, so nothing needs
+ *    clearing).  Calls whose work overlaps on the GPU (different streams or
+ *    threads at the same time) race on it: serialise them.
+ */
+gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int level, int epochs,
+                                     const gosh_params *params, void *stream,
+                                     double *loss_per_epoch, unsigned long long *n_updates);
+
 /* EXPANDEMBEDDING (Alg. 2, Sec. 3): M_fine[v] = M_coarse[map[v]] for v < n_fine.
  * map: device int32[n_fine] with values in [0, n_coarse). */
 gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *map,

@@ -71,6 +71,7 @@ def lib() -> C.CDLL:
             "gosh_hierarchy_copy_level": [vp, i32, vp, vp, vp, vp],
             "gosh_init_embedding": [vp, i64, i32, i32, i32, u64, u64, vp],
             "gosh_train_level": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, vp, vp],
+            "gosh_train_level_noalloc": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, vp, vp],
             "gosh_project": [vp, i64, vp, vp, i64, i32, i32, vp],
             "gosh_embed": [P(gosh_csr), P(gosh_params), vp, vp, P(gosh_stats)],
             "gosh_pair_scores": [vp, i32, i32, vp, i64, vp, vp],
@@ -228,6 +229,14 @@ def gosh_train_level(g, M, level, epochs, params: gosh_params, loss=None, n_upda
     cg = g.c() if isinstance(g, Csr) else g
     _check("gosh_train_level", lib().gosh_train_level(C.byref(cg), _ptr(M), level, epochs, C.byref(params),
                                                       _stream(stream), _ptr(loss), _ptr(n_updates)))
+
+
+def gosh_train_level_noalloc(g, M, level, epochs, params: gosh_params, loss=None, n_updates=None, stream=None):
+    """gosh_train_level without any device allocation by the library (lock-free
+    mode only; see include/gosh.h for the limits)."""
+    cg = g.c() if isinstance(g, Csr) else g
+    _check("gosh_train_level_noalloc", lib().gosh_train_level_noalloc(
+        C.byref(cg), _ptr(M), level, epochs, C.byref(params), _stream(stream), _ptr(loss), _ptr(n_updates)))
 
 
 def gosh_project(Mc, map_ptr, Mf, stream=None):
