@@ -227,6 +227,17 @@ gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *
 gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_out,
                        void *stream, gosh_stats *stats);
 
+/* The tensor-core (tcgen05) GEMM behind the learned projection, exported so
+ * it can be verified on its own: C[m][n] = sum_k A[m][k] * B[n][k] for
+ * m < M, n < N, with A (M x K) and B (N x K) BF16 row-major (row strides lda,
+ * ldb elements, K contiguous) and C FP32 row-major (stride ldc).  K must be a
+ * multiple of 16; strides keep rows 16-byte aligned.  splits > 1 splits K
+ * over that many thread blocks per tile and ADDS into C (which must hold the
+ * addend, e.g. zeros).  Synchronous; GOSH_ERR_TIMEOUT if an MMA completion
+ * wait gave up. */
+gosh_status gosh_tc_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, float *C, int64_t ldc,
+                              int M, int N, int K, int splits, void *stream);
+
 /* Scores of vertex pairs, out[i] = M[pairs[2i]] . M[pairs[2i+1]] in FP32.
  * pairs: device int32[2*npairs]; out: device float[npairs]. */
 gosh_status gosh_pair_scores(const void *M, int d, gosh_dtype dtype, const int32_t *pairs,

@@ -43,78 +43,68 @@ __global__ void invert_order(const uint32_t *__restrict__ order, int64_t n, int3
         rank[order[i]] = (int32_t)i;
 }
 
-// One MIS round: warp w takes 32 consecutive positions of `order`; the
-// undecided vertices among them are examined one at a time by the whole warp.
+// A vertex above the density (deg * n > nnz) has no eligible earlier-ranked
+// neighbour: eligibility needs the other end at or below the density, and an
+// earlier rank needs a degree at least as large.  Such vertices are cluster
+// roots from the start; only vertices at or below the density (whose every
+// edge is eligible and whose rows are at most the average degree long) go
+// through the rounds.
+__global__ void mis_init(const int64_t *__restrict__ rowptr, int64_t n, uint8_t *__restrict__ state) {
+    const int64_t nnz = rowptr[n];
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        state[v] = small_deg(rowptr[v + 1] - rowptr[v], n, nnz) ? kUndecided : kHub;
+}
+
+// One round of the MIS rule, one thread per rank position (so a warp holds
+// vertices of nearly equal degree): v becomes a non-hub if an earlier-ranked
+// neighbour is a hub, a hub if every earlier-ranked neighbour is a non-hub,
+// and stays undecided otherwise.  Decisions are final, so reading states that
+// other threads set during the same round is safe and speeds convergence.
 __global__ void __launch_bounds__(256) mis_round(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                                  int64_t n, const uint32_t *__restrict__ order,
                                                  const int32_t *__restrict__ rank, uint8_t *state,
                                                  unsigned long long *__restrict__ undecided) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nnz = rowptr[n];
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     volatile uint8_t *vstate = state;
     unsigned long long left = 0;
-    for (int64_t base = wid * 32; base < n; base += wstride * 32) {
-        const int64_t i = base + lane;
-        const int32_t my_v = i < n ? (int32_t)order[i] : -1;
-        const bool mine = my_v >= 0 && vstate[my_v] == kUndecided;
-        uint32_t todo = __ballot_sync(0xffffffffu, mine);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int32_t v = __shfl_sync(0xffffffffu, my_v, src);
-            const int32_t rv = (int32_t)(base + src);
-            const int64_t b = rowptr[v], e = rowptr[v + 1];
-            const bool v_small = small_deg(e - b, n, nnz);
-            bool hub_seen = false, open_seen = false;
-            for (int64_t p = b + lane; p < e; p += 32) {
-                const int32_t u = col[p];
-                if (rank[u] >= rv) continue;
-                if (!(v_small || small_deg(rowptr[u + 1] - rowptr[u], n, nnz))) continue;
-                const uint8_t su = vstate[u];
-                hub_seen |= su == kHub;
-                open_seen |= su == kUndecided;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)order[i];
+        if (vstate[v] != kUndecided) continue;
+        bool hub_seen = false, open_seen = false;
+        for (int64_t p = rowptr[v], e = rowptr[v + 1]; p < e; ++p) {
+            const int32_t u = __ldg(col + p);
+            if (__ldg(rank + u) >= (int32_t)i) continue;
+            const uint8_t su = vstate[u];
+            if (su == kHub) {
+                hub_seen = true;
+                break;
             }
-            const bool any_hub = __any_sync(0xffffffffu, hub_seen);
-            const bool any_open = __any_sync(0xffffffffu, open_seen);
-            if (lane == src) {
-                if (any_hub) vstate[v] = kNonHub;
-                else if (!any_open) vstate[v] = kHub;
-                else ++left;
-            }
+            open_seen |= su == kUndecided;
         }
+        if (hub_seen) vstate[v] = kNonHub;
+        else if (!open_seen) vstate[v] = kHub;
+        else ++left;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) left += __shfl_xor_sync(0xffffffffu, left, o);
-    if (lane == 0 && left) atomicAdd(undecided, left);
+    if ((threadIdx.x & 31) == 0 && left) atomicAdd(undecided, left);
 }
 
-// hub_rank[v] = rank of v for hubs; earliest-ranked eligible hub neighbour for non-hubs.
-__global__ void __launch_bounds__(256) attach_to_hub(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                                     int64_t n, const int32_t *__restrict__ rank,
-                                                     const uint8_t *__restrict__ state, int32_t *__restrict__ hub_rank) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nnz = rowptr[n];
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = wid; v < n; v += wstride) {
+// hub_rank[v] = rank of v for hubs; for a non-hub (always at or below the
+// density, so all its edges are eligible) the earliest-ranked hub neighbour.
+__global__ void attach_to_hub(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, int64_t n,
+                              const int32_t *__restrict__ rank, const uint8_t *__restrict__ state,
+                              int32_t *__restrict__ hub_rank) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         if (state[v] == kHub) {
-            if (lane == 0) hub_rank[v] = rank[v];
+            hub_rank[v] = rank[v];
             continue;
         }
-        const int64_t b = rowptr[v], e = rowptr[v + 1];
-        const bool v_small = small_deg(e - b, n, nnz);
         int32_t best = 0x7fffffff;
-        for (int64_t p = b + lane; p < e; p += 32) {
-            const int32_t u = col[p];
-            if (state[u] != kHub) continue;
-            if (!(v_small || small_deg(rowptr[u + 1] - rowptr[u], n, nnz))) continue;
-            best = min(best, rank[u]);
+        for (int64_t p = rowptr[v], e = rowptr[v + 1]; p < e; ++p) {
+            const int32_t u = __ldg(col + p);
+            if (state[u] == kHub) best = min(best, __ldg(rank + u));
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-        if (lane == 0) hub_rank[v] = best;
+        hub_rank[v] = best;
     }
 }
 
@@ -160,14 +150,23 @@ __global__ void unique_flags(const uint64_t *__restrict__ keys, int64_t m, uint6
         f[i] = keys[i] != sentinel && (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
 }
 
+// Sorted unique keys -> coarse CSR.  The first entry of each row writes the
+// row pointers of that row and of the empty rows before it; the last valid
+// entry closes the empty rows after it.  No atomics.
 __global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ f,
-                             const int64_t *__restrict__ pos, int64_t m, int32_t *__restrict__ col_out,
-                             unsigned long long *__restrict__ row_count) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-        if (f[i]) {
-            col_out[pos[i]] = (int32_t)(keys[i] & 0xffffffffu);
-            atomicAdd(&row_count[keys[i] >> 32], 1ull);
-        }
+                             const int64_t *__restrict__ pos, int64_t nnz, uint64_t sentinel, int64_t nc,
+                             int32_t *__restrict__ col_out, int64_t *__restrict__ rowptr) {
+    const int64_t m = pos[nnz];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = keys[i];
+        if (key == sentinel) continue;
+        if (f[i]) col_out[pos[i]] = (int32_t)(key & 0xffffffffu);
+        const int64_t r = (int64_t)(key >> 32);
+        const int64_t rprev = i == 0 ? -1 : (int64_t)(keys[i - 1] >> 32);
+        for (int64_t c = rprev + 1; c <= r; ++c) rowptr[c] = pos[i];
+        if (i + 1 == nnz || keys[i + 1] == sentinel)
+            for (int64_t c = r + 1; c <= nc; ++c) rowptr[c] = m;
+    }
 }
 
 int grid_1d(int64_t n, int threads = 256) {
@@ -210,7 +209,7 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), vals.as<uint32_t>(), n, 0, 32, s));
     const uint32_t *order = vals.as<uint32_t>();
     (invert_order<<<grid_1d(n), 256, 0, s>>>(order, n, rank.as<int32_t>()), note_launch());
-    GOSH_TRY_CUDA(cudaMemsetAsync(state.ptr, 0, n, s));
+    (mis_init<<<grid_1d(n), 256, 0, s>>>(rowptr, n, state.as<uint8_t>()), note_launch());
 
     // 2. MIS rounds
     unsigned long long left = 1;
@@ -221,7 +220,7 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
             return GOSH_ERR_CUDA;
         }
         GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
-        (mis_round<<<grid_warps(ceil_div(n, 32)), 256, 0, s>>>(rowptr, col, n, order, rank.as<int32_t>(),
+        (mis_round<<<grid_1d(n), 256, 0, s>>>(rowptr, col, n, order, rank.as<int32_t>(),
                                                                state.as<uint8_t>(), counter.as<unsigned long long>()), note_launch());
         GOSH_TRY_CUDA(cudaMemcpyAsync(&left, counter.ptr, sizeof(left), cudaMemcpyDeviceToHost, s));
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
@@ -230,7 +229,7 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     if (rounds_out) *rounds_out = rounds;
 
     // 3. attach non-hubs, number the clusters by hub rank
-    (attach_to_hub<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
+    (attach_to_hub<<<grid_1d(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
                                                  hub_rank.as<int32_t>()), note_launch());
     (hub_flags_by_rank<<<grid_1d(n), 256, 0, s>>>(order, state.as<uint8_t>(), n, flags.as<uint8_t>()), note_launch());
     GOSH_TRY(scan_exclusive_u8_to_i64(flags.as<uint8_t>(), cid.as<int64_t>(), n, cid.as<int64_t>() + n, s));
@@ -260,11 +259,10 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     GOSH_TRY_CUDA(cudaMalloc(&rp, sizeof(int64_t) * (nc + 1)));
     int64_t m = 0;
     if (nnz > 0) {
-        Scratch ek, fl, pos, cnt;
+        Scratch ek, fl, pos;
         GOSH_TRY(ek.alloc(sizeof(uint64_t) * nnz, s));
         GOSH_TRY(fl.alloc(nnz, s));
         GOSH_TRY(pos.alloc(sizeof(int64_t) * (nnz + 1), s));
-        GOSH_TRY(cnt.alloc(sizeof(unsigned long long) * nc, s));
         const uint64_t sentinel = (uint64_t)nc << 32;
         (edge_image<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, map, sentinel, ek.as<uint64_t>()), note_launch());
         int shifts[8];
@@ -278,10 +276,9 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
         GOSH_TRY_CUDA(cudaMemcpyAsync(&m, pos.as<int64_t>() + nnz, sizeof(m), cudaMemcpyDeviceToHost, s));
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
         GOSH_TRY_CUDA(cudaMalloc(&co, sizeof(int32_t) * (m > 0 ? m : 1)));
-        GOSH_TRY_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(unsigned long long) * nc, s));
-        (write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz, co,
-                                                  cnt.as<unsigned long long>()), note_launch());
-        GOSH_TRY(scan_exclusive_i64(reinterpret_cast<const int64_t *>(cnt.ptr), rp, nc, rp + nc, s));
+        GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
+        (write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz,
+                                                   sentinel, nc, co, rp), note_launch());
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     } else {
         GOSH_TRY_CUDA(cudaMalloc(&co, sizeof(int32_t)));

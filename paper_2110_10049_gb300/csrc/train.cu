@@ -111,8 +111,14 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
                               const TrainKernel **out) {
     const bool det = mode == kModeDet;
     const int ns = k + 1;
-    if (lanes <= 0) lanes = natural_lanes(dtype, d);
-    if (pass <= 0) pass = det ? (ns <= 4 ? 4 : 8) : (ns <= 2 ? 2 : 4);
+    // Defaults from the lanes/pass sweep on R-MAT 20 (d = 128, k = 3): 16-bit
+    // tables do best with two 16-byte vectors per lane (more sources in flight
+    // per warp), FP32 with one; two sample rows per pass keep registers low.
+    if (lanes <= 0) {
+        const int nat = natural_lanes(dtype, d);
+        lanes = (!det && dtype != GOSH_F32 && nat >= 4) ? nat / 2 : nat;
+    }
+    if (pass <= 0) pass = det ? (ns <= 4 ? 4 : 8) : 2;
     if (det && pass < ns) {
         set_error("deterministic mode gathers all k+1 samples in one pass: samples_per_pass %d < k+1 = %d",
                   pass, ns);
