@@ -80,6 +80,13 @@ typedef struct gosh_params {
                                one row are never lost; 1 writes rows back with plain stores
                                as the paper does (a racing writer may overwrite an update).
                                16-bit tables always use plain stores with stochastic rounding. */
+    int projection;         /* gosh_embed between levels: 0 = copy (EXPANDEMBEDDING, Alg. 2),
+                               1 = learned residual MLP (gosh_project_learned), trained after
+                               every level on that level's (coarse, fine) pairs */
+    int mlp_hidden;         /* hidden width of the projection MLP (default 256) */
+    int mlp_epochs;         /* passes over a level's vertices per MLP training (default 4) */
+    double mlp_lr;          /* Adam step size (default 1e-3) */
+    int mlp_batch;          /* vertices per MLP training step (default 4096) */
 } gosh_params;
 
 #define GOSH_MAX_LEVELS 64
@@ -211,6 +218,57 @@ gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int level, int 
  * map: device int32[n_fine] with values in [0, n_coarse). */
 gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *map,
                          void *M_fine, int64_t n_fine, int d, gosh_dtype dtype, void *stream);
+
+/*
+ * Learned coarse-to-fine projection (not in the paper, whose projection is the
+ * copy of Alg. 2; MILE's learned projection is the paper's point of
+ * comparison, Sec. 7).  A residual two-layer MLP on per-vertex features
+ *   f(v) = [ M_c[map v] | log(1 + deg v) | mean_{w in Gamma(v)} M_c[map w] ]  (2d+1 values)
+ *   M_f[v] = M_c[map v] + W2 relu(W1 f(v) + b1) + b2
+ * with BF16 weights/activations for the tensor-core GEMMs, FP32 accumulation
+ * and FP32 master weights with Adam.  W2 = b2 = 0 at creation, so an
+ * untrained network is exactly the copy projection.
+ */
+typedef struct gosh_mlp gosh_mlp;
+
+/* Creates a network for dimension d (32, 64, 128) with `hidden` units (a
+ * multiple of 16); W1 is Glorot-uniform from Philox (key seed). */
+gosh_status gosh_mlp_create(int d, int hidden, uint64_t seed, gosh_mlp **out);
+void gosh_mlp_free(gosh_mlp *m);
+
+/* Row stride (BF16 elements) of a feature matrix: 2d+1 rounded up to 16. */
+int gosh_mlp_feature_stride(int d);
+
+/* Host copies of the FP32 master weights: W1 hidden x (2d+1), b1 hidden,
+ * W2 d x hidden, b2 d (row-major).  Any pointer may be NULL (get). */
+gosh_status gosh_mlp_get_weights(const gosh_mlp *m, float *W1, float *b1, float *W2, float *b2);
+gosh_status gosh_mlp_set_weights(gosh_mlp *m, const float *W1, const float *b1, const float *W2, const float *b2);
+
+/* Feature rows of every vertex of g_fine (device CSR) from M_coarse through
+ * map (device int32[n_fine]); X: device BF16 n_fine x gosh_mlp_feature_stride(d). */
+gosh_status gosh_mlp_features(const gosh_csr *g_fine, const int32_t *map, const void *M_coarse, int d,
+                              gosh_dtype dtype, void *X, void *stream);
+
+/* Mean-squared-error loss L = (1/n) sum_v |Y(v) - R(v)|^2 and its gradients
+ * for one batch of n rows (16 <= n <= 2^20): X device BF16 features, R device
+ * FP32 n x d residual targets; gradients to host buffers (shapes as in
+ * gosh_mlp_get_weights), loss to *loss (host).  No update.  Synchronous. */
+gosh_status gosh_mlp_grads(gosh_mlp *m, const void *X, const float *R, int64_t n, float *dW1, float *db1,
+                           float *dW2, float *db2, double *loss, void *stream);
+
+/* Trains on the pairs of one level: inputs f(v) from M_coarse, targets
+ * M_fine[v] - M_coarse[map v], `epochs` passes in batches of `batch` vertices
+ * with Adam (step size lr).  final_loss (host, nullable): mean squared error
+ * per vertex over the last pass.  Synchronous. */
+gosh_status gosh_mlp_train(gosh_mlp *m, const gosh_csr *g_fine, const int32_t *map, const void *M_coarse,
+                           const void *M_fine, int d, gosh_dtype dtype, int epochs, double lr, int batch,
+                           void *stream, double *final_loss);
+
+/* M_fine[v] = M_coarse[map v] + MLP(f(v)) for every vertex of g_fine,
+ * rounded to nearest in the storage type.  Synchronous. */
+gosh_status gosh_project_learned(gosh_mlp *m, const void *M_coarse, const int32_t *map,
+                                 const gosh_csr *g_fine, void *M_fine, int d, gosh_dtype dtype,
+                                 void *stream);
 
 /*
  * GOSH (Alg. 2) end to end: coarsen g0 (unless params->max_levels == 1),

@@ -343,6 +343,11 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->det_batch = 4096;
     p->seed = 20211020;
     p->validate = 0;
+    p->projection = 0;
+    p->mlp_hidden = 256;
+    p->mlp_epochs = 4;
+    p->mlp_lr = 1e-3;
+    p->mlp_batch = 4096;
     return GOSH_OK;
 }
 
@@ -585,13 +590,31 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
     GOSH_TRY(gosh_init_embedding(buf(D - 1), h->n[D - 1], p.d, p.dtype, D - 1, p.seed, p.graph_id, stream));
     // per-level events, read once at the end so that no level waits for the host
     EventList ev(stats ? 2 * D + 1 : 0);
+    // learned projection: one network for the whole run, trained after each
+    // level i < D-1 on (features from M_{i+1}, trained M_i) before M_{i+1}'s
+    // buffer is reused for M_{i-1}
+    struct MlpGuard {
+        gosh_mlp *m = nullptr;
+        ~MlpGuard() { gosh_mlp_free(m); }
+    } mlp;
+    if (p.projection == 1 && D > 1)
+        GOSH_TRY(gosh_mlp_create(p.d, p.mlp_hidden > 0 ? p.mlp_hidden : 256, p.seed ^ 0x6d6c70ull, &mlp.m));
     for (int i = D - 1; i >= 0; --i) {
         gosh_csr gi{h->n[i], h->rowptr[i], h->col[i], 1};
         ev.record(2 * i + 1, s);
         GOSH_TRY(train_level_impl(&gi, buf(i), i, ep[i], &p, s, nullptr, counter.as<unsigned long long>()));
         ev.record(2 * i, s);
-        if (i > 0)
-            GOSH_TRY(gosh_project(buf(i), h->n[i], h->map[i - 1], buf(i - 1), h->n[i - 1], p.d, p.dtype, stream));
+        if (mlp.m && i <= D - 2 && i > 0)
+            GOSH_TRY(gosh_mlp_train(mlp.m, &gi, h->map[i], buf(i + 1), buf(i), p.d, p.dtype,
+                                    p.mlp_epochs > 0 ? p.mlp_epochs : 4, p.mlp_lr > 0 ? p.mlp_lr : 1e-3,
+                                    p.mlp_batch > 0 ? p.mlp_batch : 4096, stream, nullptr));
+        if (i > 0) {
+            gosh_csr gf{h->n[i - 1], h->rowptr[i - 1], h->col[i - 1], 1};
+            if (mlp.m && i <= D - 2)
+                GOSH_TRY(gosh_project_learned(mlp.m, buf(i), h->map[i - 1], &gf, buf(i - 1), p.d, p.dtype, stream));
+            else
+                GOSH_TRY(gosh_project(buf(i), h->n[i], h->map[i - 1], buf(i - 1), h->n[i - 1], p.d, p.dtype, stream));
+        }
     }
     std::vector<double> train_ms(D, 0.0);
     double project_ms = 0.0;

@@ -39,7 +39,8 @@ class gosh_params(C.Structure):
                 ("max_levels", C.c_int), ("dtype", C.c_int), ("mode", C.c_int), ("det_batch", C.c_int64),
                 ("seed", C.c_uint64), ("graph_id", C.c_uint64), ("lanes_per_row", C.c_int),
                 ("samples_per_pass", C.c_int), ("device_budget_bytes", C.c_int64), ("validate", C.c_int),
-                ("plain_stores", C.c_int)]
+                ("plain_stores", C.c_int), ("projection", C.c_int), ("mlp_hidden", C.c_int),
+                ("mlp_epochs", C.c_int), ("mlp_lr", C.c_double), ("mlp_batch", C.c_int)]
 
 
 class gosh_stats(C.Structure):
@@ -76,7 +77,21 @@ def lib() -> C.CDLL:
             "gosh_embed": [P(gosh_csr), P(gosh_params), vp, vp, P(gosh_stats)],
             "gosh_pair_scores": [vp, i32, i32, vp, i64, vp, vp],
             "gosh_link_auc": [vp, i32, i32, vp, i64, vp, i64, vp, P(C.c_double)],
+            "gosh_tc_gemm_bf16": [vp, i64, vp, i64, vp, i64, i32, i32, i32, i32, vp],
+            "gosh_mlp_create": [i32, i32, u64, P(vp)],
+            "gosh_mlp_get_weights": [vp, vp, vp, vp, vp],
+            "gosh_mlp_set_weights": [vp, vp, vp, vp, vp],
+            "gosh_mlp_features": [P(gosh_csr), vp, vp, i32, i32, vp, vp],
+            "gosh_mlp_grads": [vp, vp, vp, i64, vp, vp, vp, vp, P(C.c_double), vp],
+            "gosh_mlp_train": [vp, P(gosh_csr), vp, vp, vp, i32, i32, i32, f64, i32, vp, P(C.c_double)],
+            "gosh_project_learned": [vp, vp, vp, P(gosh_csr), vp, i32, i32, vp],
         }
+        L.gosh_mlp_free.restype = None
+        L.gosh_mlp_free.argtypes = [vp]
+        L.gosh_mlp_feature_stride.restype = C.c_int
+        L.gosh_mlp_feature_stride.argtypes = [C.c_int]
+        L.gosh_kernel_launches.restype = C.c_ulonglong
+        L.gosh_kernel_launches.argtypes = []
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
@@ -267,6 +282,79 @@ def gosh_embed(rowptr, col, params: gosh_params, out=None, stream=None):
     _check("gosh_embed", lib().gosh_embed(C.byref(cg), C.byref(params), _ptr(out), _stream(stream),
                                           C.byref(st)))
     return out, st
+
+
+class Mlp:
+    """Owns a gosh_mlp handle (learned projection network)."""
+
+    def __init__(self, d, hidden=256, seed=0):
+        h = C.c_void_p()
+        _check("gosh_mlp_create", lib().gosh_mlp_create(d, hidden, seed, C.byref(h)))
+        self.handle, self.d, self.hidden = h.value, d, hidden
+
+    @property
+    def stride(self) -> int:
+        return lib().gosh_mlp_feature_stride(self.d)
+
+    def get_weights(self):
+        din = 2 * self.d + 1
+        W1 = np.zeros((self.hidden, din), np.float32)
+        b1 = np.zeros(self.hidden, np.float32)
+        W2 = np.zeros((self.d, self.hidden), np.float32)
+        b2 = np.zeros(self.d, np.float32)
+        _check("gosh_mlp_get_weights", lib().gosh_mlp_get_weights(
+            self.handle, W1.ctypes.data, b1.ctypes.data, W2.ctypes.data, b2.ctypes.data))
+        return W1, b1, W2, b2
+
+    def set_weights(self, W1, b1, W2, b2):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (W1, b1, W2, b2)]
+        _check("gosh_mlp_set_weights", lib().gosh_mlp_set_weights(self.handle, *[a.ctypes.data for a in arrs]))
+
+    def features(self, g, map_ptr, Mc, stream=None):
+        """Device BF16 feature matrix (n_fine x stride) of g's vertices."""
+        import torch
+        cg = g.c() if isinstance(g, Csr) else g
+        X = torch.empty((cg.n, self.stride), dtype=torch.bfloat16, device="cuda")
+        mp = map_ptr.data_ptr() if hasattr(map_ptr, "data_ptr") else map_ptr
+        _check("gosh_mlp_features", lib().gosh_mlp_features(C.byref(cg), C.c_void_p(mp), _ptr(Mc), self.d,
+                                                            dtype_code(Mc.dtype), _ptr(X), _stream(stream)))
+        return X
+
+    def grads(self, X, R, stream=None):
+        din = 2 * self.d + 1
+        out = [np.zeros((self.hidden, din), np.float32), np.zeros(self.hidden, np.float32),
+               np.zeros((self.d, self.hidden), np.float32), np.zeros(self.d, np.float32)]
+        loss = C.c_double()
+        _check("gosh_mlp_grads", lib().gosh_mlp_grads(self.handle, _ptr(X), _ptr(R), X.shape[0],
+                                                      *[a.ctypes.data for a in out], C.byref(loss), _stream(stream)))
+        return loss.value, out
+
+    def train(self, g, map_ptr, Mc, Mf, epochs=4, lr=1e-3, batch=4096, stream=None):
+        cg = g.c() if isinstance(g, Csr) else g
+        mp = map_ptr.data_ptr() if hasattr(map_ptr, "data_ptr") else map_ptr
+        loss = C.c_double()
+        _check("gosh_mlp_train", lib().gosh_mlp_train(self.handle, C.byref(cg), C.c_void_p(mp), _ptr(Mc), _ptr(Mf),
+                                                      self.d, dtype_code(Mc.dtype), epochs, lr, batch,
+                                                      _stream(stream), C.byref(loss)))
+        return loss.value
+
+    def project(self, Mc, map_ptr, g, Mf, stream=None):
+        cg = g.c() if isinstance(g, Csr) else g
+        mp = map_ptr.data_ptr() if hasattr(map_ptr, "data_ptr") else map_ptr
+        _check("gosh_project_learned", lib().gosh_project_learned(self.handle, _ptr(Mc), C.c_void_p(mp),
+                                                                  C.byref(cg), _ptr(Mf), self.d,
+                                                                  dtype_code(Mc.dtype), _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            lib().gosh_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gosh_pair_scores(M, pairs, out=None, stream=None):
