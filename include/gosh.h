@@ -296,6 +296,41 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
 gosh_status gosh_tc_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, float *C, int64_t ldc,
                               int M, int N, int K, int splits, void *stream);
 
+typedef struct gosh_batch_stats {
+    int graphs;                 /* graphs in the batch */
+    int64_t phases;             /* scheduled phases (inits, epochs, projections) */
+    int64_t level0_vertices;    /* sum of |V_0| */
+    int lanes_per_row;          /* variant used (autotuned when params asked for 0) */
+    int samples_per_pass;
+    int sources_per_item;       /* sources (rows) per work item of a warp */
+    int autotuned;              /* 1 if this call ran the autotuner */
+    double coarsen_ms;          /* host wall time of the per-graph coarsening */
+    double train_ms;            /* device time of the persistent launch */
+    double total_ms;            /* wall time of the call */
+    unsigned long long updates; /* UPDATEEMBED applications */
+} gosh_batch_stats;
+
+/*
+ * Many independent graphs embedded at once (GOSH, Alg. 2, per graph): every
+ * graph is coarsened (gosh_coarsen), then ALL graphs' levels are trained in
+ * one persistent kernel launch, captured in a CUDA graph.  Each graph follows
+ * its own schedule -- initialise M_{D-1}, the epochs of each level in order
+ * (epochs serialised, Sec. 3.1), copy projection between levels -- while
+ * different graphs proceed concurrently; warps take work items (chunks of
+ * sources or rows) from whichever graph has work.  Graph g draws its samples
+ * with Philox key (seed, graph_id + g), so its random stream is that of a
+ * standalone gosh_embed with graph_id + g.
+ * graphs: n_graphs device CSRs; M_out[g]: device n_g x d of params->dtype
+ * (FP32 or BF16).  Lock-free mode only (GOSH_HOGWILD), copy projection.
+ * params->lanes_per_row / samples_per_pass = 0 ask the autotuner to time the
+ * compiled (lanes per row, samples per pass, sources per item) variants on
+ * this batch once per (dtype, d, k) and keep the fastest (cached per
+ * process).  A warp that finds no work for 4 s stops the launch with
+ * GOSH_ERR_TIMEOUT.  stats: host pointer or NULL.  Synchronous.
+ */
+gosh_status gosh_embed_batch(int n_graphs, const gosh_csr *graphs, const gosh_params *params,
+                             void *const *M_out, void *stream, gosh_batch_stats *stats);
+
 /* Scores of vertex pairs, out[i] = M[pairs[2i]] . M[pairs[2i+1]] in FP32.
  * pairs: device int32[2*npairs]; out: device float[npairs]. */
 gosh_status gosh_pair_scores(const void *M, int d, gosh_dtype dtype, const int32_t *pairs,

@@ -89,7 +89,8 @@ __device__ __forceinline__ float group_sum(float x) {
  *   kModeDet    snapshot batch, changes written to R/C/keys (needs P >= k+1).
  */
 template <typename T, int D, int L, int P, int MODE>
-__global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
+__device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0, int32_t *s_u_w, uint32_t *s_sr_w,
+                                           double &loss_acc, unsigned long long &applied) {
     constexpr bool DET = MODE == kModeDet;
     constexpr bool RED = MODE == kModeRed;
     static_assert(!RED || std::is_same<T, float>::value, "atomic row updates need FP32 tables");
@@ -100,23 +101,13 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
     static_assert(32 % L == 0, "L must divide the warp");
     static_assert(!DET || E % 4 == 0, "float4 stores of the change buffers");
 
-    __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
-    __shared__ uint32_t s_sr[kTrainWarps][32];
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int grp = lane / L, gl = lane % L;
     const int ns = a.k + 1;
-    const int64_t nsrc = a.src_end - a.src_begin;
-    const int64_t ntiles = (nsrc + 31) / 32;
-    const int64_t wstride = (int64_t)gridDim.x * kTrainWarps;
     T *__restrict__ M = static_cast<T *>(a.M);
     const uint64_t ctr2 = ((uint64_t)a.level << 32) | a.epoch;
     const bool want_loss = a.loss_partials != nullptr;
-    double loss_acc = 0.0;
-    unsigned long long applied = 0;
-
-    for (int64_t tile = (int64_t)blockIdx.x * kTrainWarps + warp; tile < ntiles; tile += wstride) {
-        const int64_t v0 = a.src_begin + tile * 32;
+    {
         // ---- draws: lane j -> source v0 + j ----
         {
             const int64_t v = v0 + lane;
@@ -136,12 +127,12 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
                                 const int64_t x = (int64_t)uniform_index(w.w[j], (uint64_t)a.n);
                                 u = x == v ? -1 : (int32_t)x;
                             }
-                            s_u[warp][lane * kSlotStride + t] = u;
+                            s_u_w[lane * kSlotStride + t] = u;
                         }
                     }
                 }
                 if (!std::is_same<T, float>::value)
-                    s_sr[warp][lane] = sr_source_seed(a.seed, a.graph, a.level, a.epoch, v);
+                    s_sr_w[lane] = sr_source_seed(a.seed, a.graph, a.level, a.epoch, v);
             }
         }
         __syncwarp();
@@ -151,7 +142,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
             const int j = q * G + grp;
             const int64_t v = v0 + j;
             const bool active = v < a.src_end;
-            const uint32_t sr = std::is_same<T, float>::value ? 0u : s_sr[warp][j];
+            const uint32_t sr = std::is_same<T, float>::value ? 0u : s_sr_w[j];
             float r[E];
             if (active) {
                 if (DET) load_row_snapshot<T, E>(M + v * D + gl * E, r);
@@ -172,7 +163,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
 #pragma unroll
                 for (int s = 0; s < P; ++s) {
                     const int t = p0 + s;
-                    us[s] = (active && t < ns) ? s_u[warp][j * kSlotStride + t] : -1;
+                    us[s] = (active && t < ns) ? s_u_w[j * kSlotStride + t] : -1;
                 }
 #pragma unroll
                 for (int s = 0; s < P; ++s) {
@@ -247,6 +238,24 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
         }
         __syncwarp();
     }
+}
+
+/*
+ * One epoch (Hogwild) or one snapshot batch (deterministic): the warps of the
+ * grid take tiles of 32 consecutive sources of [src_begin, src_end) in turn.
+ */
+template <typename T, int D, int L, int P, int MODE>
+__global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
+    __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
+    __shared__ uint32_t s_sr[kTrainWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t ntiles = (a.src_end - a.src_begin + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * kTrainWarps;
+    const bool want_loss = a.loss_partials != nullptr;
+    double loss_acc = 0.0;
+    unsigned long long applied = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * kTrainWarps + warp; tile < ntiles; tile += wstride)
+        train_tile<T, D, L, P, MODE>(a, a.src_begin + tile * 32, s_u[warp], s_sr[warp], loss_acc, applied);
 
     // ---- monitors ----
     if (a.n_updates) {

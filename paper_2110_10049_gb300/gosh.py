@@ -50,6 +50,13 @@ class gosh_stats(C.Structure):
                 ("updates", C.c_ulonglong)]
 
 
+class gosh_batch_stats(C.Structure):
+    _fields_ = [("graphs", C.c_int), ("phases", C.c_int64), ("level0_vertices", C.c_int64),
+                ("lanes_per_row", C.c_int), ("samples_per_pass", C.c_int), ("sources_per_item", C.c_int),
+                ("autotuned", C.c_int), ("coarsen_ms", C.c_double), ("train_ms", C.c_double),
+                ("total_ms", C.c_double), ("updates", C.c_ulonglong)]
+
+
 _lib = None
 
 
@@ -78,6 +85,7 @@ def lib() -> C.CDLL:
             "gosh_pair_scores": [vp, i32, i32, vp, i64, vp, vp],
             "gosh_link_auc": [vp, i32, i32, vp, i64, vp, i64, vp, P(C.c_double)],
             "gosh_tc_gemm_bf16": [vp, i64, vp, i64, vp, i64, i32, i32, i32, i32, vp],
+            "gosh_embed_batch": [i32, vp, P(gosh_params), vp, vp, P(gosh_batch_stats)],
             "gosh_mlp_create": [i32, i32, u64, P(vp)],
             "gosh_mlp_get_weights": [vp, vp, vp, vp, vp],
             "gosh_mlp_set_weights": [vp, vp, vp, vp, vp],
@@ -282,6 +290,22 @@ def gosh_embed(rowptr, col, params: gosh_params, out=None, stream=None):
     _check("gosh_embed", lib().gosh_embed(C.byref(cg), C.byref(params), _ptr(out), _stream(stream),
                                           C.byref(st)))
     return out, st
+
+
+def gosh_embed_batch(graphs, params: gosh_params, outs=None, stream=None):
+    """Embeds a list of device CSRs (Csr) in one persistent launch.
+    Returns (list of M tensors, stats dict)."""
+    import torch
+    G = len(graphs)
+    arr = (gosh_csr * G)(*[g.c() for g in graphs])
+    if outs is None:
+        outs = [torch.empty((g.n, params.d), dtype=torch_dtype(params.dtype), device="cuda") for g in graphs]
+    ptrs = (C.c_void_p * G)(*[o.data_ptr() for o in outs])
+    st = gosh_batch_stats()
+    _check("gosh_embed_batch", lib().gosh_embed_batch(G, C.cast(arr, C.c_void_p), C.byref(params),
+                                                      C.cast(ptrs, C.c_void_p), _stream(stream), C.byref(st)))
+    stats = {f: getattr(st, f) for f, _ in gosh_batch_stats._fields_}
+    return outs, stats
 
 
 class Mlp:

@@ -1,0 +1,76 @@
+"""Batched persistent launch (many graphs and their levels in one kernel).
+
+- graphs small enough that every level is a single work item of one warp
+  with one source per round (FP32, d = 128, 32 lanes per source) are trained
+  sequentially both in the batch and standalone: the batch must reproduce the
+  standalone gosh_embed of each graph (same Philox stream: graph_id + g) to
+  the deterministic-mode tolerance 1e-5;
+- a batch of R-MAT graphs reaches the standalone training-edge AUC (within
+  0.01, mean over the batch; lock-free runs are not bit-reproducible);
+- the autotuner runs once per (dtype, d, k) and its choice is reused.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import gosh, needs_gpu, rel_fro, torch
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+
+def dev_csr(g, gr):
+    return g.to_device_csr(gr.rowptr, gr.col)
+
+
+def test_batch_equals_standalone_on_single_warp_graphs():
+    g = gosh()
+    graphs = [synth.random_graph(int(n), 0.25, int(s)) for n, s in zip(range(18, 32, 2), range(7))]
+    csrs = [dev_csr(g, gr) for gr in graphs]
+    p = g.default_params(d=128, k=3, lr=0.05, epochs=30, p=0.3, seed=5, graph_id=100,
+                         lanes_per_row=32, samples_per_pass=2, threshold=4)
+    outs, st = g.gosh_embed_batch(csrs, p)
+    assert st["graphs"] == len(graphs)
+    for i, gr in enumerate(graphs):
+        q = g.default_params(d=128, k=3, lr=0.05, epochs=30, p=0.3, seed=5, graph_id=100 + i,
+                             lanes_per_row=32, samples_per_pass=2, threshold=4)
+        M, _ = g.gosh_embed(csrs[i].rowptr, csrs[i].col, q)
+        assert rel_fro(outs[i].double().cpu().numpy(), M.double().cpu().numpy()) <= 1e-5
+
+
+def fit_auc(M, gr, seed=0):
+    src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
+    rng = np.random.default_rng(seed)
+    rnd = np.stack([rng.integers(0, gr.n, 20000), rng.integers(0, gr.n, 20000)], 1)
+    return oracle.link_auc(M, np.stack([src, gr.col], 1), rnd)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_batch_matches_standalone_quality(dtype):
+    g = gosh()
+    rng = np.random.default_rng(3)
+    graphs = [synth.rmat_graph(int(rng.integers(8, 12)), int(rng.integers(4, 17)), 50 + i) for i in range(12)]
+    csrs = [dev_csr(g, gr) for gr in graphs]
+    p = g.default_params(d=64, k=5, lr=0.045, epochs=200, p=0.3, seed=9, dtype=dtype)
+    outs, st = g.gosh_embed_batch(csrs, p)
+    a_batch = [fit_auc(o.double().cpu().numpy(), gr) for o, gr in zip(outs, graphs)]
+    a_alone = []
+    for i, gr in enumerate(graphs):
+        q = g.default_params(d=64, k=5, lr=0.045, epochs=200, p=0.3, seed=9, graph_id=i, dtype=dtype)
+        M, _ = g.gosh_embed(csrs[i].rowptr, csrs[i].col, q)
+        a_alone.append(fit_auc(M.double().cpu().numpy(), gr))
+    assert abs(np.mean(a_batch) - np.mean(a_alone)) <= 0.01, (np.mean(a_batch), np.mean(a_alone))
+    assert st["updates"] > 0
+
+
+def test_autotuner_runs_once_and_is_reused():
+    g = gosh()
+    graphs = [synth.rmat_graph(9, 8, 70 + i) for i in range(6)]
+    csrs = [dev_csr(g, gr) for gr in graphs]
+    p = g.default_params(d=32, k=2, lr=0.045, epochs=20, p=0.3, seed=1, dtype=torch.bfloat16)
+    _, st1 = g.gosh_embed_batch(csrs, p)
+    _, st2 = g.gosh_embed_batch(csrs, p)
+    assert st1["autotuned"] == 1 and st2["autotuned"] == 0
+    assert (st1["lanes_per_row"], st1["samples_per_pass"], st1["sources_per_item"]) == \
+           (st2["lanes_per_row"], st2["samples_per_pass"], st2["sources_per_item"])
+    assert st1["lanes_per_row"] in (2, 4) and st1["samples_per_pass"] in (2, 4)
