@@ -87,7 +87,24 @@ typedef struct gosh_params {
     int mlp_epochs;         /* passes over a level's vertices per MLP training (default 4) */
     double mlp_lr;          /* Adam step size (default 1e-3) */
     int mlp_batch;          /* vertices per MLP training step (default 4096) */
+    int p_gpu;              /* LargeGraphGPU: part (submatrix) bins on the device (paper: 3) */
+    int s_gpu;              /* LargeGraphGPU: edge-block bins on the device (paper: 2) */
+    int B;                  /* LargeGraphGPU: positives per vertex per part pair per round (paper: 5) */
+    int large_parts;        /* LargeGraphGPU: K; 0 = derive from device_budget_bytes */
 } gosh_params;
+
+typedef struct gosh_large_stats {
+    int parts;              /* K */
+    int rounds;             /* ceil(e / B) */
+    int64_t kernels;        /* part-pair kernels launched (rounds * K(K+1)/2) */
+    int64_t swaps;          /* part loads into bins */
+    int64_t h2d_bytes;      /* parts + edge blocks copied to the device */
+    int64_t d2h_bytes;      /* parts copied back */
+    unsigned long long positives;  /* positive samples used (<= e * |V|) */
+    unsigned long long updates;    /* UPDATEEMBED applications */
+    int64_t device_bytes;   /* bins allocated on the device */
+    double total_ms;        /* wall time of the call */
+} gosh_large_stats;
 
 #define GOSH_MAX_LEVELS 64
 
@@ -213,6 +230,37 @@ gosh_status gosh_train_level(const gosh_csr *g, void *M, int level, int epochs,
 gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int level, int epochs,
                                      const gosh_params *params, void *stream,
                                      double *loss_per_epoch, unsigned long long *n_updates);
+
+/*
+ * LargeGraphGPU (Sec. 5): TRAININGPU for a level whose graph and embedding
+ * exceed the device budget.  V is split into K contiguous parts (K =
+ * params->large_parts, or derived from device_budget_bytes: part bins get 60%
+ * of the budget); a round runs kernel K_{a,b} for every part pair in
+ * inside-out order (0,0),(1,0),(1,1),(2,0),...: each u in V^a with neighbours
+ * in V^b takes B positives uniform over Gamma(u) & V^b, each followed by k
+ * negatives uniform over V^b, and symmetrically for V^b when a != b;
+ * ceil(epochs/B) rounds; a device counter stops positives at epochs * |V|.
+ * Positive t = round*B + j of a source uses lr * max(1 - t/epochs, lr_floor)
+ * and Philox counter (u, blk, level << 32 | t, tag) with tag 0 when K = 1
+ * (so K = 1, B = 1 draws exactly the samples of gosh_train_level) and
+ * 3 | (a*K+b) << 8 otherwise.  Parts move between pinned host memory and
+ * params->p_gpu device bins (farthest-next-use eviction), edge blocks
+ * (built once on host threads) through params->s_gpu bins, all
+ * asynchronously on per-bin streams with cudaEvent dependencies; kernels
+ * alternate over two streams and may overlap (lock-free, as in the paper).
+ * g: HOST CSR; M: HOST n x d (FP32 or BF16; pinned in place if pageable),
+ * updated in place.  Lock-free mode only.  stats: host pointer or NULL.
+ * GOSH_ERR_BUDGET if K parts do not fit the budget.  Synchronous.
+ */
+gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int epochs,
+                                   const gosh_params *params, void *stream, gosh_large_stats *stats);
+
+/* Host-only simulation of the LargeGraphGPU part-bin schedule (no GPU use):
+ * for `rounds` rounds over K parts and p_gpu bins, writes for every kernel i
+ * its pair (pairs_out[2i], pairs_out[2i+1]) = (a, b) and the loads done
+ * before it (loads_out[2i], loads_out[2i+1]: part * 1000 + bin, or -1).
+ * Returns the kernel count, or -1 if it exceeds cap_tasks. */
+int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int *loads_out, int cap_tasks);
 
 /* EXPANDEMBEDDING (Alg. 2, Sec. 3): M_fine[v] = M_coarse[map[v]] for v < n_fine.
  * map: device int32[n_fine] with values in [0, n_coarse). */

@@ -348,6 +348,10 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->mlp_epochs = 4;
     p->mlp_lr = 1e-3;
     p->mlp_batch = 4096;
+    p->p_gpu = 3;
+    p->s_gpu = 2;
+    p->B = 5;
+    p->large_parts = 0;
     return GOSH_OK;
 }
 

@@ -1,0 +1,633 @@
+// LargeGraphGPU (Sec. 5): training a level whose embedding and graph exceed
+// the device budget.  V is split into K contiguous parts V^0..V^{K-1} (M into
+// the matching submatrices); a round visits every part pair (a, b), a >= b, in
+// inside-out order (0,0),(1,0),(1,1),(2,0),... and runs kernel K_{a,b}: every
+// u in V^a with neighbours in V^b draws B positives uniformly from
+// Gamma(u) & V^b, each followed by k negatives uniform over V^b, and
+// symmetrically for u in V^b when a != b.  r = ceil(e/B) rounds; a global
+// atomic counter stops positives at e*|V|.
+//
+// GB300 realisation: the host keeps M and the CSR in pinned memory.  The
+// device holds P_GPU part bins and S_GPU edge-block bins.  Edge block (a, b)
+// = for each u in V^a the sub-range of its sorted row that falls in V^b
+// (parts are id ranges, so it is found by binary search), stored with local
+// ids; blocks are built once on host threads and streamed every round.  A
+// single host thread issues the DAG of the paper's three task kinds
+// asynchronously: submatrix swaps (MST: D2H of the evicted part, H2D of the
+// needed one) on the bin's stream, edge-block copies (SCT) on the edge bin's
+// stream, kernels (KT) alternating over two streams; cudaEvents carry every
+// dependency (a kernel waits for its parts and block; a swap waits for every
+// kernel that used the bin and for the host copy of the incoming part to be
+// fresh; an edge bin is refilled after its last kernel).  Victims are chosen
+// by the known future order (farthest next use).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <thread>
+#include <vector>
+
+#include "train_kernels.cuh"
+
+namespace gosh {
+namespace {
+
+constexpr int kMaxSlots = 32;  // B * (k+1) sample ids per source kept in shared memory
+constexpr uint64_t kTagLarge = 3;
+
+struct PairArgs {
+    void *Ma, *Mb;                    // bins of parts a and b (local rows)
+    int64_t na, nb;                   // part sizes
+    int64_t start_a, start_b;         // first global id of each part
+    const int64_t *rp_ab;             // [na+1] block (a,b): rows of V^a, local column ids in V^b
+    const int32_t *col_ab;
+    const int64_t *rp_ba;             // [nb+1] block (b,a) (a != b)
+    const int32_t *col_ba;
+    int same;                         // a == b
+    int B, k;
+    int epochs_total;                 // e of this level
+    int round;
+    float lr, lr_floor;
+    uint64_t seed, graph, tag;        // Philox key and stream tag
+    uint32_t level;
+    unsigned long long *positives;    // global counter
+    unsigned long long cap;           // e * |V|
+    unsigned long long *n_updates;
+};
+
+// One tile of 32 sources (side A: V^a, side B: V^b).  Lane j draws source j's
+// B positives and k negatives each (shared memory), then L-lane groups apply
+// the B*(k+1) updates of their source with the source row in registers.
+template <typename T, int D, int L, int P, int MODE>
+__device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *su, float *slr,
+                          unsigned long long &applied) {
+    constexpr bool RED = MODE == kModeRed;
+    constexpr int E = D / L;
+    constexpr int G = 32 / L;
+    const int lane = threadIdx.x & 31, grp = lane / L, gl = lane % L;
+    const int ns = a.B * (a.k + 1);
+    // ---- draws ----
+    int npos = 0;
+    {
+        const int64_t s = s0 + lane;
+        if (s < nsrc) {
+            const bool sideA = s < a.na;
+            const int64_t u = sideA ? s : s - a.na;
+            const int64_t *rp = sideA ? a.rp_ab : a.rp_ba;
+            const int32_t *cl = sideA ? a.col_ab : a.col_ba;
+            const int64_t nopp = sideA ? a.nb : a.na;
+            const int64_t ug = (sideA ? a.start_a : a.start_b) + u;
+            const int64_t lo = rp[u], cnt = rp[u + 1] - lo;
+            for (int j = 0; j < a.B; ++j) {
+                const uint32_t t = (uint32_t)(a.round * a.B + j);
+                const int ks = j * (a.k + 1);
+                for (int blk = 0; blk * 4 < a.k + 1; ++blk) {
+                    const Philox4 w = philox4x64_10((uint64_t)ug, (uint64_t)blk, ((uint64_t)a.level << 32) | t, a.tag,
+                                                    a.seed, a.graph);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int m = blk * 4 + q;
+                        if (m <= a.k) {
+                            int32_t id;
+                            if (m == 0) {
+                                id = cnt > 0 ? __ldg(cl + lo + (int64_t)uniform_index(w.w[0], (uint64_t)cnt)) : -1;
+                            } else {
+                                const int64_t x = (int64_t)uniform_index(w.w[q], (uint64_t)nopp);
+                                id = (a.same && x == u) ? -1 : (int32_t)x;
+                            }
+                            su[lane * kMaxSlots + ks + m] = id;
+                        }
+                    }
+                }
+                const double f = 1.0 - (double)t / (double)a.epochs_total;
+                slr[lane * 8 + j] = a.lr * (float)(f > a.lr_floor ? f : a.lr_floor);
+            }
+            npos = cnt > 0 ? a.B : 0;
+        }
+    }
+    // ---- cap on positives (global counter) ----
+    int before = npos;  // inclusive prefix over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, before, o);
+        if (lane >= o) before += y;
+    }
+    const int tile_pos = __shfl_sync(0xffffffffu, before, 31);
+    unsigned long long old = 0;
+    if (lane == 0 && tile_pos > 0) old = atomicAdd(a.positives, (unsigned long long)tile_pos);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    const long long allowed = old >= a.cap ? 0 : (long long)std::min<unsigned long long>(a.cap - old, tile_pos);
+    const int my_first = before - npos;  // positives of this lane's source start here
+    __syncwarp();
+    // ---- updates ----
+#pragma unroll 1
+    for (int q = 0; q < L; ++q) {
+        const int j = q * G + grp;
+        const int64_t s = s0 + j;
+        const bool active = s < nsrc;
+        const bool sideA = s < a.na;
+        const int64_t u = active ? (sideA ? s : s - a.na) : 0;
+        T *Mown = static_cast<T *>(sideA ? a.Ma : a.Mb);
+        T *Mopp = static_cast<T *>(sideA ? a.Mb : a.Ma);
+        const int first = __shfl_sync(0xffffffffu, my_first, j);
+        const uint32_t sr = std::is_same<T, float>::value
+                                ? 0u
+                                : sr_source_seed(a.seed, a.graph ^ a.tag, a.level, (uint32_t)a.round, (sideA ? a.start_a : a.start_b) + u);
+        float r[E];
+        if (active) load_row<T, E>(Mown + u * D + gl * E, r);
+        else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) r[e] = 0.0f;
+        }
+        float r0[RED ? E : 1];
+        if (RED) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) r0[e] = r[e];
+        }
+#pragma unroll 1
+        for (int p0 = 0; p0 < ns; p0 += P) {
+            int32_t us[P];
+            float row[P][E];
+#pragma unroll
+            for (int x = 0; x < P; ++x) {
+                const int t = p0 + x;
+                int32_t id = (active && t < ns) ? su[j * kMaxSlots + t] : -1;
+                const int jj = t / (a.k + 1);  // positive group of this slot
+                if (id >= 0 && first + jj >= allowed) id = -1;  // over the global cap
+                us[x] = id;
+            }
+#pragma unroll
+            for (int x = 0; x < P; ++x) {
+                if (us[x] >= 0) load_row<T, E>(Mopp + (int64_t)us[x] * D + gl * E, row[x]);
+                else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) row[x][e] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < P; ++x) {
+                const int t = p0 + x;
+                const bool ok = us[x] >= 0;
+                float part = 0.0f;
+#pragma unroll
+                for (int e = 0; e < E; ++e) part = fmaf(r[e], row[x][e], part);
+                const float xx = group_sum<L>(part);
+                const int jj = t / (a.k + 1);
+                const float b = (t % (a.k + 1)) == 0 ? 1.0f : 0.0f;
+                const float lr = (active && t < ns) ? slr[j * 8 + jj] : 0.0f;
+                const float score = ok ? (b - __frcp_rn(1.0f + __expf(-xx))) * lr : 0.0f;
+#pragma unroll
+                for (int e = 0; e < E; ++e) r[e] = fmaf(row[x][e], score, r[e]);
+#pragma unroll
+                for (int e = 0; e < E; ++e) row[x][e] = fmaf(r[e], score, row[x][e]);
+                if (ok) {
+                    if (RED) {
+                        float c[E];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) c[e] = r[e] * score;
+                        red_row<E>(reinterpret_cast<float *>(Mopp) + (int64_t)us[x] * D + gl * E, c);
+                    } else {
+                        store_row<T, D, E>(Mopp + (int64_t)us[x] * D + gl * E, row[x], sr, t, gl * E);
+                    }
+                    if (gl == 0) ++applied;
+                }
+#pragma unroll
+                for (int x2 = x + 1; x2 < P; ++x2)
+                    if (ok && us[x2] == us[x]) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) row[x2][e] = row[x][e];
+                    }
+            }
+        }
+        if (active) {
+            if (RED) {
+                float dr[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) dr[e] = r[e] - r0[RED ? e : 0];
+                red_row<E>(reinterpret_cast<float *>(Mown) + u * D + gl * E, dr);
+            } else {
+                store_row<T, D, E>(Mown + u * D + gl * E, r, sr, ns, gl * E);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <typename T, int D, int L, int P>
+__global__ void __launch_bounds__(kTrainWarps * 32) pair_kernel(PairArgs a) {
+    constexpr int MODE = std::is_same<T, float>::value ? kModeRed : kModeStore;
+    __shared__ int32_t su[kTrainWarps][32 * kMaxSlots];
+    __shared__ float slr[kTrainWarps][32 * 8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nsrc = a.na + (a.same ? 0 : a.nb);
+    const int64_t tiles = (nsrc + 31) / 32;
+    unsigned long long applied = 0;
+    for (int64_t t = (int64_t)blockIdx.x * kTrainWarps + warp; t < tiles; t += (int64_t)gridDim.x * kTrainWarps)
+        pair_tile<T, D, L, P, MODE>(a, t * 32, nsrc, su[warp], slr[warp], applied);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) applied += __shfl_xor_sync(0xffffffffu, applied, o);
+    if (lane == 0 && applied && a.n_updates) atomicAdd(a.n_updates, applied);
+}
+
+typedef void (*PairLaunch)(const PairArgs &, int, cudaStream_t);
+
+template <typename T, int D, int L, int P>
+void launch_pair(const PairArgs &a, int grid, cudaStream_t s) {
+    (pair_kernel<T, D, L, P><<<grid, kTrainWarps * 32, 0, s>>>(a), note_launch());
+}
+
+PairLaunch pick_pair_kernel(gosh_dtype dt, int d) {
+    // two 16-byte vectors per lane for BF16, one for FP32; two sample rows per pass
+    if (dt == GOSH_F32) {
+        if (d == 32) return &launch_pair<float, 32, 8, 2>;
+        if (d == 64) return &launch_pair<float, 64, 16, 2>;
+        if (d == 128) return &launch_pair<float, 128, 32, 2>;
+    } else if (dt == GOSH_BF16) {
+        if (d == 32) return &launch_pair<__nv_bfloat16, 32, 2, 2>;
+        if (d == 64) return &launch_pair<__nv_bfloat16, 64, 4, 2>;
+        if (d == 128) return &launch_pair<__nv_bfloat16, 128, 8, 2>;
+    }
+    return nullptr;
+}
+
+// Edge block (a, b) of one pair, built once on the host in pinned memory.
+struct Block {
+    int64_t *rp_ab = nullptr, *rp_ba = nullptr;
+    int32_t *col_ab = nullptr, *col_ba = nullptr;
+    int64_t m_ab = 0, m_ba = 0;
+    size_t bytes = 0;
+    char *base = nullptr;  // one pinned allocation: rp_ab | col_ab | rp_ba | col_ba
+};
+
+void build_rows(const int64_t *rowptr, const int32_t *col, int64_t a0, int64_t a1, int64_t b0, int64_t b1,
+                int64_t *rp, int32_t *cols_or_null, std::vector<std::pair<int64_t, int64_t>> &ranges) {
+    ranges.resize((size_t)(a1 - a0));
+    int64_t m = 0;
+    rp[0] = 0;
+    for (int64_t u = a0; u < a1; ++u) {
+        const int32_t *row = col + rowptr[u], *end = col + rowptr[u + 1];
+        const int32_t *lo = std::lower_bound(row, end, (int32_t)b0);
+        const int32_t *hi = std::lower_bound(lo, end, (int32_t)b1);
+        ranges[(size_t)(u - a0)] = {lo - col, hi - col};
+        m += hi - lo;
+        rp[u - a0 + 1] = m;
+    }
+    if (cols_or_null)
+        for (int64_t u = a0; u < a1; ++u) {
+            const auto r = ranges[(size_t)(u - a0)];
+            int32_t *out = cols_or_null + rp[u - a0];
+            for (int64_t p = r.first; p < r.second; ++p) *out++ = col[p] - (int32_t)b0;
+        }
+}
+
+struct Sched {
+    int K, PB, SB;
+    std::vector<int64_t> start;                 // K+1
+    std::vector<std::pair<int, int>> order;     // one round
+};
+
+}  // namespace
+
+// Inside-out order of one round: (0,0),(1,0),(1,1),(2,0),(2,1),(2,2),...
+void large_pair_order(int K, std::vector<std::pair<int, int>> &order) {
+    order.clear();
+    for (int a = 0; a < K; ++a)
+        for (int b = 0; b <= a; ++b) order.push_back({a, b});
+}
+
+}  // namespace gosh
+
+using namespace gosh;
+
+extern "C" {
+
+/* See include/gosh.h. */
+int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int *loads_out, int cap_tasks) {
+    // Host-only simulation of the submatrix-bin schedule: for each kernel of
+    // `rounds` rounds, the pair (a, b) and the part loaded into a bin before
+    // it (or -1 entries); returns the number of kernels (or -1 if cap_tasks is
+    // too small).  Eviction: farthest next use.
+    std::vector<std::pair<int, int>> order;
+    large_pair_order(K, order);
+    std::vector<std::pair<int, int>> seq;
+    for (int r = 0; r < rounds; ++r)
+        for (auto &pr : order) seq.push_back(pr);
+    if ((int)seq.size() > cap_tasks) return -1;
+    std::vector<int> bin(p_gpu, -1);
+    for (size_t i = 0; i < seq.size(); ++i) {
+        const int need[2] = {seq[i].first, seq[i].second};
+        int loads[2] = {-1, -1};
+        for (int q = 0; q < 2; ++q) {
+            const int x = need[q];
+            if (std::find(bin.begin(), bin.end(), x) != bin.end()) continue;
+            int victim = -1;
+            size_t far = 0;
+            for (int bi = 0; bi < p_gpu; ++bi) {
+                if (bin[bi] == need[0] || bin[bi] == need[1]) continue;
+                if (bin[bi] < 0) { victim = bi; break; }
+                size_t nxt = seq.size() + 1;
+                for (size_t j = i + 1; j < seq.size(); ++j)
+                    if (seq[j].first == bin[bi] || seq[j].second == bin[bi]) { nxt = j; break; }
+                if (victim < 0 || nxt > far) { victim = bi; far = nxt; }
+            }
+            bin[victim] = x;
+            loads[q] = x * 1000 + victim;  // part * 1000 + bin
+        }
+        pairs_out[2 * i] = seq[i].first;
+        pairs_out[2 * i + 1] = seq[i].second;
+        loads_out[2 * i] = loads[0];
+        loads_out[2 * i + 1] = loads[1];
+    }
+    (void)n;
+    return (int)seq.size();
+}
+
+gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int epochs, const gosh_params *p,
+                                   void *stream, gosh_large_stats *stats) {
+    clear_error();
+    GOSH_CHECK_ARG(g && p && M, "NULL argument");
+    GOSH_CHECK_ARG(!g->on_device, "gosh_train_level_large takes a host CSR (it streams it)");
+    GOSH_CHECK_ARG(g->n >= 1 && g->n < (int64_t(1) << 31), "bad n");
+    GOSH_CHECK_ARG(p->mode == GOSH_HOGWILD, "LargeGraphGPU is lock-free (GOSH_HOGWILD)");
+    GOSH_CHECK_ARG(p->B >= 1 && p->B * (p->k + 1) <= kMaxSlots && p->B <= 8, "need 1 <= B <= 8 and B*(k+1) <= %d",
+                   kMaxSlots);
+    GOSH_CHECK_ARG(p->p_gpu >= 2 && p->s_gpu >= 1, "need P_GPU >= 2 and S_GPU >= 1");
+    const PairLaunch launch = pick_pair_kernel(p->dtype, p->d);
+    GOSH_CHECK_ARG(launch != nullptr, "LargeGraphGPU serves FP32 / BF16 with d in {32, 64, 128}");
+    const auto t_start = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->n;
+    const size_t row = (size_t)p->d * dtype_size(p->dtype);
+    const int64_t nnz = g->rowptr[n];
+
+    // ---- K from the budget (reading of "increasing P_GPU increases K") ----
+    int K = p->large_parts;
+    const int64_t budget = p->device_budget_bytes;
+    if (K <= 0) {
+        GOSH_CHECK_ARG(budget > 0, "give device_budget_bytes or large_parts");
+        // edge bins take up to 40% of the budget, part bins the rest
+        const double part_budget = 0.6 * (double)budget / p->p_gpu;
+        K = std::max(p->p_gpu, (int)std::ceil((double)n * row / part_budget));
+    }
+    K = (int)std::min<int64_t>(K, n);
+    std::vector<int64_t> start(K + 1);
+    for (int i = 0; i <= K; ++i) start[i] = n * i / K;
+
+    // ---- edge blocks (pinned, built on host threads) ----
+    std::vector<std::pair<int, int>> order;
+    large_pair_order(K, order);
+    std::vector<Block> blocks(order.size());
+    size_t max_block = 0;
+    {
+        std::vector<std::thread> th;
+        const int nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<gosh_status> st(nt, GOSH_OK);
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&, t]() {
+                std::vector<std::pair<int64_t, int64_t>> ranges;
+                for (size_t i = t; i < order.size(); i += nt) {
+                    const int a = order[i].first, b = order[i].second;
+                    const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
+                    std::vector<int64_t> rpa(na + 1), rpb(a != b ? nb + 1 : 1);
+                    build_rows(g->rowptr, g->col, start[a], start[a + 1], start[b], start[b + 1], rpa.data(), nullptr,
+                               ranges);
+                    if (a != b)
+                        build_rows(g->rowptr, g->col, start[b], start[b + 1], start[a], start[a + 1], rpb.data(),
+                                   nullptr, ranges);
+                    Block &B = blocks[i];
+                    B.m_ab = rpa[na];
+                    B.m_ba = a != b ? rpb[nb] : 0;
+                    const size_t s1 = sizeof(int64_t) * (na + 1), s2 = sizeof(int32_t) * B.m_ab;
+                    const size_t s3 = a != b ? sizeof(int64_t) * (nb + 1) : 0, s4 = sizeof(int32_t) * B.m_ba;
+                    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+                    B.bytes = al(s1) + al(s2) + al(s3) + al(s4);
+                    if (cudaMallocHost(&B.base, B.bytes) != cudaSuccess) {
+                        st[t] = GOSH_ERR_OOM;
+                        return;
+                    }
+                    B.rp_ab = reinterpret_cast<int64_t *>(B.base);
+                    B.col_ab = reinterpret_cast<int32_t *>(B.base + al(s1));
+                    B.rp_ba = reinterpret_cast<int64_t *>(B.base + al(s1) + al(s2));
+                    B.col_ba = reinterpret_cast<int32_t *>(B.base + al(s1) + al(s2) + al(s3));
+                    build_rows(g->rowptr, g->col, start[a], start[a + 1], start[b], start[b + 1], B.rp_ab, B.col_ab,
+                               ranges);
+                    if (a != b)
+                        build_rows(g->rowptr, g->col, start[b], start[b + 1], start[a], start[a + 1], B.rp_ba,
+                                   B.col_ba, ranges);
+                }
+            });
+        for (auto &x : th) x.join();
+        for (auto x : st)
+            if (x != GOSH_OK) {
+                for (auto &b : blocks)
+                    if (b.base) cudaFreeHost(b.base);
+                set_error("pinned allocation of edge blocks failed");
+                return x;
+            }
+        for (auto &b : blocks) max_block = std::max(max_block, b.bytes);
+    }
+    struct BlockFree {
+        std::vector<Block> &v;
+        ~BlockFree() {
+            for (auto &b : v)
+                if (b.base) cudaFreeHost(b.base);
+        }
+    } block_free{blocks};
+    int64_t part_rows = 0;
+    for (int i = 0; i < K; ++i) part_rows = std::max(part_rows, start[i + 1] - start[i]);
+    const size_t bin_bytes = row * part_rows;
+    const size_t need = bin_bytes * p->p_gpu + max_block * p->s_gpu;
+    if (budget > 0 && (int64_t)need > budget) {
+        set_error("LargeGraphGPU: %d parts need %zu bytes of bins (> budget %lld); raise K (large_parts)", K, need,
+                  (long long)budget);
+        return GOSH_ERR_BUDGET;
+    }
+
+    // host M pinned for async copies (registered in place if the caller's is pageable)
+    bool registered = false;
+    {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, M) != cudaSuccess || at.type == cudaMemoryTypeUnregistered) {
+            cudaGetLastError();
+            if (cudaHostRegister(M, row * n, cudaHostRegisterDefault) == cudaSuccess) registered = true;
+            else cudaGetLastError();
+        }
+    }
+    struct Unreg {
+        void *p;
+        bool on;
+        ~Unreg() {
+            if (on) cudaHostUnregister(p);
+        }
+    } unreg{M, registered};
+
+    // ---- device bins, streams, events ----
+    std::vector<Scratch> pbin(p->p_gpu), ebin(p->s_gpu);
+    for (auto &b : pbin) GOSH_TRY(b.alloc(bin_bytes, s));
+    for (auto &b : ebin) GOSH_TRY(b.alloc(max_block, s));
+    Scratch counters;
+    GOSH_TRY(counters.alloc(2 * sizeof(unsigned long long), s));
+    GOSH_TRY_CUDA(cudaMemsetAsync(counters.ptr, 0, 2 * sizeof(unsigned long long), s));
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    std::vector<cudaStream_t> pstr(p->p_gpu), estr(p->s_gpu), kstr(2);
+    for (auto &x : pstr) GOSH_TRY_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    for (auto &x : estr) GOSH_TRY_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    for (auto &x : kstr) GOSH_TRY_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    std::vector<cudaEvent_t> pool;
+    auto new_event = [&](cudaStream_t st) {
+        cudaEvent_t e;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        cudaEventRecord(e, st);
+        pool.push_back(e);
+        return e;
+    };
+    struct Cleanup {
+        std::vector<cudaStream_t> &a, &b, &c;
+        std::vector<cudaEvent_t> &ev;
+        ~Cleanup() {
+            for (auto *v : {&a, &b, &c})
+                for (auto x : *v) {
+                    cudaStreamSynchronize(x);
+                    cudaStreamDestroy(x);
+                }
+            for (auto e : ev) cudaEventDestroy(e);
+        }
+    } cleanup{pstr, estr, kstr, pool};
+
+    const int rounds = (epochs + p->B - 1) / p->B;
+    std::vector<std::pair<int, int>> seq;
+    for (int r = 0; r < rounds; ++r)
+        for (auto &pr : order) seq.push_back(pr);
+    std::vector<int> bin_part(p->p_gpu, -1);
+    std::vector<std::vector<cudaEvent_t>> bin_users(p->p_gpu);     // kernels using the bin since its load
+    std::vector<cudaEvent_t> bin_ready(p->p_gpu, nullptr);
+    std::vector<cudaEvent_t> host_fresh(K, nullptr);               // D2H of part x completed
+    std::vector<cudaEvent_t> ebin_free(p->s_gpu, nullptr);
+    int64_t swaps = 0, h2d = 0, d2h = 0, block_bytes = 0;
+    const int grid = num_sms() * 2;
+    char *hM = static_cast<char *>(M);
+
+    auto ensure = [&](int x, int keep0, int keep1, size_t i) -> int {
+        for (int bi = 0; bi < p->p_gpu; ++bi)
+            if (bin_part[bi] == x) return bi;
+        int victim = -1;
+        size_t far = 0;
+        for (int bi = 0; bi < p->p_gpu; ++bi) {
+            if (bin_part[bi] == keep0 || bin_part[bi] == keep1) continue;
+            if (bin_part[bi] < 0) {
+                victim = bi;
+                break;
+            }
+            size_t nxt = seq.size() + 1;
+            for (size_t j = i + 1; j < seq.size(); ++j)
+                if (seq[j].first == bin_part[bi] || seq[j].second == bin_part[bi]) {
+                    nxt = j;
+                    break;
+                }
+            if (victim < 0 || nxt > far) {
+                victim = bi;
+                far = nxt;
+            }
+        }
+        cudaStream_t st = pstr[victim];
+        for (cudaEvent_t e : bin_users[victim]) cudaStreamWaitEvent(st, e, 0);
+        bin_users[victim].clear();
+        const int old = bin_part[victim];
+        if (old >= 0) {  // MST, first half: the evicted part goes home
+            const size_t bytes = row * (start[old + 1] - start[old]);
+            cudaMemcpyAsync(hM + row * start[old], pbin[victim].ptr, bytes, cudaMemcpyDeviceToHost, st);
+            host_fresh[old] = new_event(st);
+            d2h += bytes;
+        }
+        if (host_fresh[x]) cudaStreamWaitEvent(st, host_fresh[x], 0);
+        const size_t bytes = row * (start[x + 1] - start[x]);
+        cudaMemcpyAsync(pbin[victim].ptr, hM + row * start[x], bytes, cudaMemcpyHostToDevice, st);
+        h2d += bytes;
+        bin_ready[victim] = new_event(st);
+        bin_part[victim] = x;
+        ++swaps;
+        return victim;
+    };
+
+    for (size_t i = 0; i < seq.size(); ++i) {
+        const int a = seq[i].first, b = seq[i].second;
+        const int r = (int)(i / order.size());
+        const int ba = ensure(a, a, b, i);
+        const int bb = ensure(b, a, b, i);
+        // SCT: edge block into the next edge bin
+        const int eb = (int)(i % p->s_gpu);
+        const Block &blk = blocks[i % order.size()];
+        if (ebin_free[eb]) cudaStreamWaitEvent(estr[eb], ebin_free[eb], 0);
+        cudaMemcpyAsync(ebin[eb].ptr, blk.base, blk.bytes, cudaMemcpyHostToDevice, estr[eb]);
+        block_bytes += blk.bytes;
+        cudaEvent_t e_ready = new_event(estr[eb]);
+        // KT
+        cudaStream_t ks = kstr[i % 2];
+        cudaStreamWaitEvent(ks, bin_ready[ba], 0);
+        cudaStreamWaitEvent(ks, bin_ready[bb], 0);
+        cudaStreamWaitEvent(ks, e_ready, 0);
+        PairArgs pa{};
+        const char *eb0 = ebin[eb].as<char>();
+        pa.Ma = pbin[ba].ptr;
+        pa.Mb = pbin[bb].ptr;
+        pa.na = start[a + 1] - start[a];
+        pa.nb = start[b + 1] - start[b];
+        pa.start_a = start[a];
+        pa.start_b = start[b];
+        pa.rp_ab = reinterpret_cast<const int64_t *>(eb0 + ((char *)blk.rp_ab - blk.base));
+        pa.col_ab = reinterpret_cast<const int32_t *>(eb0 + ((char *)blk.col_ab - blk.base));
+        pa.rp_ba = reinterpret_cast<const int64_t *>(eb0 + ((char *)blk.rp_ba - blk.base));
+        pa.col_ba = reinterpret_cast<const int32_t *>(eb0 + ((char *)blk.col_ba - blk.base));
+        pa.same = a == b;
+        pa.B = p->B;
+        pa.k = p->k;
+        pa.epochs_total = epochs;
+        pa.round = r;
+        pa.lr = (float)p->lr;
+        pa.lr_floor = (float)p->lr_floor;
+        pa.seed = p->seed;
+        pa.graph = p->graph_id;
+        pa.tag = K == 1 ? kTagSample : (kTagLarge | ((uint64_t)(a * K + b) << 8));
+        pa.level = (uint32_t)level;
+        pa.positives = counters.as<unsigned long long>();
+        pa.cap = (unsigned long long)epochs * (unsigned long long)n;
+        pa.n_updates = counters.as<unsigned long long>() + 1;
+        launch(pa, grid, ks);
+        cudaEvent_t kdone = new_event(ks);
+        bin_users[ba].push_back(kdone);
+        if (bb != ba) bin_users[bb].push_back(kdone);
+        ebin_free[eb] = kdone;
+    }
+    // write every resident part back
+    for (int bi = 0; bi < p->p_gpu; ++bi) {
+        if (bin_part[bi] < 0) continue;
+        for (cudaEvent_t e : bin_users[bi]) cudaStreamWaitEvent(pstr[bi], e, 0);
+        const int x = bin_part[bi];
+        const size_t bytes = row * (start[x + 1] - start[x]);
+        cudaMemcpyAsync(hM + row * start[x], pbin[bi].ptr, bytes, cudaMemcpyDeviceToHost, pstr[bi]);
+        d2h += bytes;
+    }
+    unsigned long long hc[2] = {0, 0};
+    for (auto x : pstr) GOSH_TRY_CUDA(cudaStreamSynchronize(x));
+    for (auto x : kstr) GOSH_TRY_CUDA(cudaStreamSynchronize(x));
+    for (auto x : estr) GOSH_TRY_CUDA(cudaStreamSynchronize(x));
+    GOSH_TRY_CUDA(cudaMemcpy(hc, counters.ptr, sizeof(hc), cudaMemcpyDeviceToHost));
+    GOSH_TRY_CUDA(cudaGetLastError());
+    if (stats) {
+        stats->parts = K;
+        stats->rounds = rounds;
+        stats->kernels = (int64_t)seq.size();
+        stats->swaps = swaps;
+        stats->h2d_bytes = h2d + block_bytes;
+        stats->d2h_bytes = d2h;
+        stats->positives = hc[0] < (unsigned long long)epochs * n ? hc[0] : (unsigned long long)epochs * n;
+        stats->updates = hc[1];
+        stats->device_bytes = (int64_t)need;
+        stats->total_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    }
+    (void)nnz;
+    return GOSH_OK;
+}
+
+}  // extern "C"

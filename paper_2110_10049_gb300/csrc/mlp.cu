@@ -96,11 +96,19 @@ __global__ void features_kernel(const int64_t *__restrict__ rowptr, const int32_
         __nv_bfloat16 *x = X + r * kp;
         const T *own = Mc + (int64_t)map[v] * d;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};  // d <= 128: lane owns columns lane + 32 j
-        for (int64_t p = b; p < e; ++p) {
-            const T *row = Mc + (int64_t)__ldg(map + __ldg(col + p)) * d;
+        // 32 neighbours at a time: each lane fetches one neighbour's cluster id
+        // (one round trip for all), then the warp sums their rows with
+        // independent, back-to-back row loads.
+        for (int64_t p0 = b; p0 < e; p0 += 32) {
+            const int cnt = (int)(e - p0 < 32 ? e - p0 : 32);
+            const int32_t cid = lane < cnt ? __ldg(map + __ldg(col + p0 + lane)) : 0;
+#pragma unroll 4
+            for (int q = 0; q < cnt; ++q) {
+                const T *row = Mc + (int64_t)__shfl_sync(0xffffffffu, cid, q) * d;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (lane + 32 * j < d) acc[j] += (float)row[lane + 32 * j];
+                for (int j = 0; j < 4; ++j)
+                    if (lane + 32 * j < d) acc[j] += (float)row[lane + 32 * j];
+            }
         }
         const float inv = e > b ? 1.0f / (float)(e - b) : 0.0f;
 #pragma unroll

@@ -40,7 +40,14 @@ class gosh_params(C.Structure):
                 ("seed", C.c_uint64), ("graph_id", C.c_uint64), ("lanes_per_row", C.c_int),
                 ("samples_per_pass", C.c_int), ("device_budget_bytes", C.c_int64), ("validate", C.c_int),
                 ("plain_stores", C.c_int), ("projection", C.c_int), ("mlp_hidden", C.c_int),
-                ("mlp_epochs", C.c_int), ("mlp_lr", C.c_double), ("mlp_batch", C.c_int)]
+                ("mlp_epochs", C.c_int), ("mlp_lr", C.c_double), ("mlp_batch", C.c_int),
+                ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int)]
+
+
+class gosh_large_stats(C.Structure):
+    _fields_ = [("parts", C.c_int), ("rounds", C.c_int), ("kernels", C.c_int64), ("swaps", C.c_int64),
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("positives", C.c_ulonglong),
+                ("updates", C.c_ulonglong), ("device_bytes", C.c_int64), ("total_ms", C.c_double)]
 
 
 class gosh_stats(C.Structure):
@@ -86,6 +93,8 @@ def lib() -> C.CDLL:
             "gosh_link_auc": [vp, i32, i32, vp, i64, vp, i64, vp, P(C.c_double)],
             "gosh_tc_gemm_bf16": [vp, i64, vp, i64, vp, i64, i32, i32, i32, i32, vp],
             "gosh_embed_batch": [i32, vp, P(gosh_params), vp, vp, P(gosh_batch_stats)],
+            "gosh_train_level_large": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, P(gosh_large_stats)],
+            "gosh_large_plan": [i64, i32, i32, i32, vp, vp, i32],
             "gosh_mlp_create": [i32, i32, u64, P(vp)],
             "gosh_mlp_get_weights": [vp, vp, vp, vp, vp],
             "gosh_mlp_set_weights": [vp, vp, vp, vp, vp],
@@ -306,6 +315,32 @@ def gosh_embed_batch(graphs, params: gosh_params, outs=None, stream=None):
                                                       C.cast(ptrs, C.c_void_p), _stream(stream), C.byref(st)))
     stats = {f: getattr(st, f) for f, _ in gosh_batch_stats._fields_}
     return outs, stats
+
+
+def gosh_train_level_large(rowptr, col, M, level, epochs, params: gosh_params, stream=None):
+    """LargeGraphGPU on a host CSR (numpy) and host M (numpy or CPU tensor,
+    updated in place).  Returns the stats dict."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    cg = gosh_csr(len(rowptr) - 1, rowptr.ctypes.data, col.ctypes.data, 0)
+    ptr = M.ctypes.data if isinstance(M, np.ndarray) else M.data_ptr()
+    st = gosh_large_stats()
+    _check("gosh_train_level_large", lib().gosh_train_level_large(C.byref(cg), C.c_void_p(ptr), level, epochs,
+                                                                  C.byref(params), _stream(stream), C.byref(st)))
+    return {f: getattr(st, f) for f, _ in gosh_large_stats._fields_}
+
+
+def gosh_large_plan(n, K, p_gpu, rounds):
+    """Host-only schedule simulation: (pairs [kernels x 2], loads [kernels x 2])."""
+    cap = rounds * K * (K + 1) // 2
+    pairs = np.zeros((max(cap, 1), 2), dtype=np.int32)
+    loads = np.zeros((max(cap, 1), 2), dtype=np.int32)
+    cnt = lib().gosh_large_plan(n, K, p_gpu, rounds, pairs.ctypes.data, loads.ctypes.data, cap)
+    if cnt < 0:
+        raise GoshError("gosh_large_plan", 1, "capacity")
+    return pairs[:cnt], loads[:cnt]
 
 
 class Mlp:

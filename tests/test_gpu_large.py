@@ -1,0 +1,66 @@
+"""LargeGraphGPU (Sec. 5) on the GPU.
+
+- K = 1, B = 1 draws exactly the samples of the resident step (same Philox
+  counters, one part pair per round = one epoch); on a graph that fits one
+  warp with one source per round both are sequential, so they agree to the
+  deterministic-mode tolerance 1e-5;
+- with K = 4 parts and 3 bins the step loses no training-edge AUC against
+  the resident step (at most 0.02 below it; parity beyond this is unpinned:
+  part pairs reorder the updates), launches rounds * K(K+1)/2 kernels, and
+  the global counter caps positives at e * |V|;
+- BF16 tables run through the same path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import gosh, needs_gpu, rel_fro, torch
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+
+def test_single_part_equals_resident_step():
+    g = gosh()
+    gr = synth.random_graph(30, 0.2, 17)
+    M0 = (oracle.init_uniform(gr.n, 128, 0, 3) * 60).astype(np.float32)
+    p = g.default_params(d=128, k=3, lr=0.05, seed=8, B=1, large_parts=1, p_gpu=2, s_gpu=1)
+    Mh = M0.copy()
+    st = g.gosh_train_level_large(gr.rowptr, gr.col, Mh, 0, 12, p)
+    assert st["parts"] == 1 and st["rounds"] == 12 and st["kernels"] == 12
+    csr = g.to_device_csr(gr.rowptr, gr.col)
+    Md = torch.from_numpy(M0.copy()).cuda()
+    nup = torch.zeros(1, dtype=torch.int64, device="cuda")
+    g.gosh_train_level(csr, Md, 0, 12, g.default_params(d=128, k=3, lr=0.05, seed=8), n_updates=nup)
+    assert st["updates"] == int(nup.item())
+    assert rel_fro(Mh, Md.cpu().numpy()) <= 1e-5
+
+
+def fit_auc(M, gr, seed=0):
+    src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
+    rng = np.random.default_rng(seed)
+    rnd = np.stack([rng.integers(0, gr.n, 20000), rng.integers(0, gr.n, 20000)], 1)
+    return oracle.link_auc(M, np.stack([src, gr.col], 1), rnd)
+
+
+@pytest.mark.parametrize("dtype,npdt", [(torch.float32, np.float32), (torch.bfloat16, None)])
+def test_parts_reach_resident_quality(dtype, npdt):
+    g = gosh()
+    gr = synth.rmat_graph(12, 8, 31)
+    e = 60
+    M0 = oracle.init_uniform(gr.n, 32, 0, 2).astype(np.float32) * 20
+    # resident
+    csr = g.to_device_csr(gr.rowptr, gr.col)
+    Md = torch.from_numpy(M0).to(dtype).cuda()
+    g.gosh_train_level(csr, Md, 0, e, g.default_params(d=32, k=3, lr=0.045, seed=4, dtype=dtype))
+    a_res = fit_auc(Md.double().cpu().numpy(), gr)
+    # LargeGraphGPU, 4 parts, 3 bins, B = 2
+    Mh = torch.from_numpy(M0).to(dtype).contiguous()
+    p = g.default_params(d=32, k=3, lr=0.045, seed=4, dtype=dtype, B=2, large_parts=4, p_gpu=3, s_gpu=2)
+    st = g.gosh_train_level_large(gr.rowptr, gr.col, Mh, 0, e, p)
+    assert st["parts"] == 4 and st["rounds"] == 30 and st["kernels"] == 30 * 10
+    assert st["positives"] == e * gr.n      # B * (parts with neighbours) > B per round: the cap binds
+    a_large = fit_auc(Mh.double().numpy(), gr)
+    # the part-pair order changes the dynamics (measured: 0.63 vs 0.59 resident
+    # at this short schedule); the bar is that splitting into parts costs no quality
+    assert a_large >= a_res - 0.02, (a_large, a_res)
