@@ -84,9 +84,10 @@ typedef struct gosh_params {
                                1 = learned residual MLP (gosh_project_learned), trained after
                                every level on that level's (coarse, fine) pairs */
     int mlp_hidden;         /* hidden width of the projection MLP (default 256) */
-    int mlp_epochs;         /* passes over a level's vertices per MLP training (default 4) */
+    int mlp_epochs;         /* passes over a level's training rows per MLP training (default 1) */
     double mlp_lr;          /* Adam step size (default 1e-3) */
-    int mlp_batch;          /* vertices per MLP training step (default 4096) */
+    int mlp_batch;          /* vertices per MLP training step (default 8192) */
+    int64_t mlp_max_rows;   /* training rows per level: every ceil(n/max)-th vertex (default 32768; 0 = all) */
     int p_gpu;              /* LargeGraphGPU: part (submatrix) bins on the device (paper: 3) */
     int s_gpu;              /* LargeGraphGPU: edge-block bins on the device (paper: 2) */
     int B;                  /* LargeGraphGPU: positives per vertex per part pair per round (paper: 5) */
@@ -306,11 +307,12 @@ gosh_status gosh_mlp_grads(gosh_mlp *m, const void *X, const float *R, int64_t n
 
 /* Trains on the pairs of one level: inputs f(v) from M_coarse, targets
  * M_fine[v] - M_coarse[map v], `epochs` passes in batches of `batch` vertices
- * with Adam (step size lr).  final_loss (host, nullable): mean squared error
- * per vertex over the last pass.  Synchronous. */
+ * with Adam (step size lr).  max_rows > 0 trains on every ceil(n/max_rows)-th
+ * vertex only (0 = all).  final_loss (host, nullable): mean squared error per
+ * vertex over the last pass.  Synchronous. */
 gosh_status gosh_mlp_train(gosh_mlp *m, const gosh_csr *g_fine, const int32_t *map, const void *M_coarse,
                            const void *M_fine, int d, gosh_dtype dtype, int epochs, double lr, int batch,
-                           void *stream, double *final_loss);
+                           int64_t max_rows, void *stream, double *final_loss);
 
 /* M_fine[v] = M_coarse[map v] + MLP(f(v)) for every vertex of g_fine,
  * rounded to nearest in the storage type.  Synchronous. */

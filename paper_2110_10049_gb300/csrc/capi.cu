@@ -345,9 +345,10 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->validate = 0;
     p->projection = 0;
     p->mlp_hidden = 256;
-    p->mlp_epochs = 4;
+    p->mlp_epochs = 1;
     p->mlp_lr = 1e-3;
-    p->mlp_batch = 4096;
+    p->mlp_batch = 8192;
+    p->mlp_max_rows = 32768;
     p->p_gpu = 3;
     p->s_gpu = 2;
     p->B = 5;
@@ -610,8 +611,8 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
         ev.record(2 * i, s);
         if (mlp.m && i <= D - 2 && i > 0)
             GOSH_TRY(gosh_mlp_train(mlp.m, &gi, h->map[i], buf(i + 1), buf(i), p.d, p.dtype,
-                                    p.mlp_epochs > 0 ? p.mlp_epochs : 4, p.mlp_lr > 0 ? p.mlp_lr : 1e-3,
-                                    p.mlp_batch > 0 ? p.mlp_batch : 4096, stream, nullptr));
+                                    p.mlp_epochs > 0 ? p.mlp_epochs : 1, p.mlp_lr > 0 ? p.mlp_lr : 1e-3,
+                                    p.mlp_batch > 0 ? p.mlp_batch : 8192, p.mlp_max_rows, stream, nullptr));
         if (i > 0) {
             gosh_csr gf{h->n[i - 1], h->rowptr[i - 1], h->col[i - 1], 1};
             if (mlp.m && i <= D - 2)

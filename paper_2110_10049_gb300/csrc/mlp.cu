@@ -86,12 +86,12 @@ __global__ void refresh_bf16(const float *W1, const float *W2, __nv_bfloat16 *W1
 template <typename T>
 __global__ void features_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                 const int32_t *__restrict__ map, const T *__restrict__ Mc, int d, int kp, int64_t v0,
-                                int64_t rows, __nv_bfloat16 *__restrict__ X) {
+                                int64_t rows, int64_t stride, __nv_bfloat16 *__restrict__ X) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = wid; r < rows; r += nw) {
-        const int64_t v = v0 + r;
+        const int64_t v = v0 + r * stride;
         const int64_t b = rowptr[v], e = rowptr[v + 1];
         __nv_bfloat16 *x = X + r * kp;
         const T *own = Mc + (int64_t)map[v] * d;
@@ -102,7 +102,7 @@ __global__ void features_kernel(const int64_t *__restrict__ rowptr, const int32_
         for (int64_t p0 = b; p0 < e; p0 += 32) {
             const int cnt = (int)(e - p0 < 32 ? e - p0 : 32);
             const int32_t cid = lane < cnt ? __ldg(map + __ldg(col + p0 + lane)) : 0;
-#pragma unroll 4
+#pragma unroll 8
             for (int q = 0; q < cnt; ++q) {
                 const T *row = Mc + (int64_t)__shfl_sync(0xffffffffu, cid, q) * d;
 #pragma unroll
@@ -127,12 +127,12 @@ __global__ void features_kernel(const int64_t *__restrict__ rowptr, const int32_
 // R[r][c] = Mf[v][c] - Mc[map v][c], v = v0 + r.
 template <typename T>
 __global__ void residual_kernel(const int32_t *__restrict__ map, const T *__restrict__ Mc, const T *__restrict__ Mf,
-                                int d, int64_t v0, int64_t rows, float *__restrict__ R) {
+                                int d, int64_t v0, int64_t rows, int64_t stride, float *__restrict__ R) {
     const int64_t total = rows * d;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / d;
         const int c = (int)(i % d);
-        const int64_t v = v0 + r;
+        const int64_t v = v0 + r * stride;
         R[i] = (float)Mf[v * d + c] - (float)Mc[(int64_t)map[v] * d + c];
     }
 }
@@ -368,12 +368,12 @@ gosh_status check_err(gosh_mlp *m, cudaStream_t s) {
 }
 
 gosh_status features(const gosh_csr *g, const int32_t *map, const void *Mc, int d, gosh_dtype dt, int kp, int64_t v0,
-                     int64_t rows, __nv_bfloat16 *X, cudaStream_t s) {
+                     int64_t rows, __nv_bfloat16 *X, cudaStream_t s, int64_t stride = 1) {
     const int blocks = (int)std::min<int64_t>(ceil_div(rows * 32, 256), (int64_t)num_sms() * 16);
     return by_dtype(dt, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         (features_kernel<T><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(g->rowptr, g->col, map, static_cast<const T *>(Mc),
-                                                                    d, kp, v0, rows, X),
+                                                                    d, kp, v0, rows, stride, X),
          note_launch());
     });
 }
@@ -418,9 +418,13 @@ gosh_status mlp_create(int d, int hidden, uint64_t seed, gosh_mlp **out) {
 }
 
 // Trains on (features of g's vertices from Mc, residual Mf - copy) pairs.
+// At most max_rows vertices take part (every stride-th vertex of the level).
 gosh_status mlp_train(gosh_mlp *m, const gosh_csr *g, const int32_t *map, const void *Mc, const void *Mf,
-                      gosh_dtype dt, int epochs, double lr, int batch, cudaStream_t s, double *final_loss) {
-    const int64_t n = g->n;
+                      gosh_dtype dt, int epochs, double lr, int batch, int64_t max_rows, cudaStream_t s,
+                      double *final_loss) {
+    const int64_t nlev = g->n;
+    const int64_t stride = (max_rows > 0 && nlev > max_rows) ? (nlev + max_rows - 1) / max_rows : 1;
+    const int64_t n = (nlev + stride - 1) / stride;
     const int d = m->d, kp = m->kp;
     if (batch <= 0) batch = 4096;
     batch = round16(batch);
@@ -429,11 +433,12 @@ gosh_status mlp_train(gosh_mlp *m, const gosh_csr *g, const int32_t *map, const 
     GOSH_TRY(X.alloc(sizeof(__nv_bfloat16) * n * kp, s));
     GOSH_TRY(R.alloc(sizeof(float) * n * d, s));
     GOSH_TRY(loss.alloc(sizeof(double), s));
-    GOSH_TRY(features(g, map, Mc, d, dt, kp, 0, n, X.as<__nv_bfloat16>(), s));
+    GOSH_TRY(features(g, map, Mc, d, dt, kp, 0, n, X.as<__nv_bfloat16>(), s, stride));
     GOSH_TRY(by_dtype(dt, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         (residual_kernel<T><<<grid_for(n * d), 256, 0, s>>>(map, static_cast<const T *>(Mc),
-                                                            static_cast<const T *>(Mf), d, 0, n, R.as<float>()),
+                                                            static_cast<const T *>(Mf), d, 0, n, stride,
+                                                            R.as<float>()),
          note_launch());
     }));
     Work w;
@@ -569,13 +574,14 @@ gosh_status gosh_mlp_grads(gosh_mlp *m, const void *X, const float *R, int64_t n
 }
 
 gosh_status gosh_mlp_train(gosh_mlp *m, const gosh_csr *g_fine, const int32_t *map, const void *M_coarse,
-                           const void *M_fine, int d, gosh_dtype dtype, int epochs, double lr, int batch, void *stream,
-                           double *final_loss) {
+                           const void *M_fine, int d, gosh_dtype dtype, int epochs, double lr, int batch,
+                           int64_t max_rows, void *stream, double *final_loss) {
     clear_error();
     GOSH_CHECK_ARG(m && g_fine && g_fine->on_device && map && M_coarse && M_fine, "NULL or host argument");
     GOSH_CHECK_ARG(d == m->d, "d (%d) differs from the network's (%d)", d, m->d);
     GOSH_CHECK_ARG(epochs >= 0 && lr > 0, "bad epochs / lr");
-    return mlp_train(m, g_fine, map, M_coarse, M_fine, dtype, epochs, lr, batch, (cudaStream_t)stream, final_loss);
+    return mlp_train(m, g_fine, map, M_coarse, M_fine, dtype, epochs, lr, batch, max_rows, (cudaStream_t)stream,
+                     final_loss);
 }
 
 gosh_status gosh_project_learned(gosh_mlp *m, const void *M_coarse, const int32_t *map, const gosh_csr *g_fine,

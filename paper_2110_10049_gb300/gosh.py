@@ -41,7 +41,7 @@ class gosh_params(C.Structure):
                 ("samples_per_pass", C.c_int), ("device_budget_bytes", C.c_int64), ("validate", C.c_int),
                 ("plain_stores", C.c_int), ("projection", C.c_int), ("mlp_hidden", C.c_int),
                 ("mlp_epochs", C.c_int), ("mlp_lr", C.c_double), ("mlp_batch", C.c_int),
-                ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int)]
+                ("mlp_max_rows", C.c_int64), ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int)]
 
 
 class gosh_large_stats(C.Structure):
@@ -100,7 +100,7 @@ def lib() -> C.CDLL:
             "gosh_mlp_set_weights": [vp, vp, vp, vp, vp],
             "gosh_mlp_features": [P(gosh_csr), vp, vp, i32, i32, vp, vp],
             "gosh_mlp_grads": [vp, vp, vp, i64, vp, vp, vp, vp, P(C.c_double), vp],
-            "gosh_mlp_train": [vp, P(gosh_csr), vp, vp, vp, i32, i32, i32, f64, i32, vp, P(C.c_double)],
+            "gosh_mlp_train": [vp, P(gosh_csr), vp, vp, vp, i32, i32, i32, f64, i32, i64, vp, P(C.c_double)],
             "gosh_project_learned": [vp, vp, vp, P(gosh_csr), vp, i32, i32, vp],
         }
         L.gosh_mlp_free.restype = None
@@ -388,12 +388,12 @@ class Mlp:
                                                       *[a.ctypes.data for a in out], C.byref(loss), _stream(stream)))
         return loss.value, out
 
-    def train(self, g, map_ptr, Mc, Mf, epochs=4, lr=1e-3, batch=4096, stream=None):
+    def train(self, g, map_ptr, Mc, Mf, epochs=4, lr=1e-3, batch=4096, max_rows=0, stream=None):
         cg = g.c() if isinstance(g, Csr) else g
         mp = map_ptr.data_ptr() if hasattr(map_ptr, "data_ptr") else map_ptr
         loss = C.c_double()
         _check("gosh_mlp_train", lib().gosh_mlp_train(self.handle, C.byref(cg), C.c_void_p(mp), _ptr(Mc), _ptr(Mf),
-                                                      self.d, dtype_code(Mc.dtype), epochs, lr, batch,
+                                                      self.d, dtype_code(Mc.dtype), epochs, lr, batch, max_rows,
                                                       _stream(stream), C.byref(loss)))
         return loss.value
 

@@ -49,3 +49,27 @@ def test_params_default_on_host():
     p = gosh.default_params()
     assert (p.d, p.k, p.threshold) == (128, 3, 100)
     assert abs(p.shrink - 0.8) < 1e-12 and abs(p.lr_floor - 1e-4) < 1e-18
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    """sizeof/offsetof of every ABI struct as gcc sees include/gosh.h equals
+    the ctypes mirror in the binding."""
+    import subprocess
+    from paper_2110_10049_gb300 import gosh
+    structs = {"gosh_params": gosh.gosh_params, "gosh_stats": gosh.gosh_stats, "gosh_csr": gosh.gosh_csr,
+               "gosh_batch_stats": gosh.gosh_batch_stats, "gosh_large_stats": gosh.gosh_large_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gosh.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(out[name + "." + f]) == getattr(cls, f).offset, (name, f)
