@@ -131,6 +131,12 @@ gosh_status gosh_params_default(gosh_params *p);
 /* Thread-local message of the last failed call ("" if none). */
 const char *gosh_last_error(void);
 
+/* Synchronises `stream`, then reads and clears the current device's error
+ * word, which a kernel raises when one of its bounded waits (TMA copy or MMA
+ * completion) gave up.  GOSH_ERR_TIMEOUT if it was raised since the last
+ * check.  gosh_embed checks it before returning. */
+gosh_status gosh_device_check(void *stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads, all devices).  A diagnostic for profiling and benchmarking. */
 unsigned long long gosh_kernel_launches(void);

@@ -3,6 +3,7 @@
 // pair scores and AUC) and the end-to-end driver of Alg. 2.
 #include <atomic>
 #include <chrono>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -26,6 +27,21 @@ void clear_error() { g_error[0] = 0; }
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int *device_error_word() {
+    static std::mutex mu;
+    static int *words[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!words[dev]) {
+        if (cudaMalloc(&words[dev], sizeof(int)) != cudaSuccess || cudaMemset(words[dev], 0, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            words[dev] = nullptr;
+        }
+    }
+    return words[dev];
+}
 
 gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, const gosh_params *p,
                              cudaStream_t s, double *loss_per_epoch, unsigned long long *n_updates);
@@ -360,6 +376,22 @@ const char *gosh_last_error(void) { return g_error; }
 
 unsigned long long gosh_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+gosh_status gosh_device_check(void *stream) {
+    clear_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    int *w = device_error_word();
+    if (!w) return GOSH_OK;
+    int h = 0;
+    GOSH_TRY_CUDA(cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        GOSH_TRY_CUDA(cudaMemset(w, 0, sizeof(int)));
+        set_error("a bounded device-side wait timed out in an earlier asynchronous call");
+        return GOSH_ERR_TIMEOUT;
+    }
+    return GOSH_OK;
+}
+
 gosh_status gosh_validate_csr(const gosh_csr *g, void *stream) {
     clear_error();
     GOSH_TRY(check_csr(g));
@@ -628,6 +660,7 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
     unsigned long long updates = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&updates, counter.ptr, sizeof(updates), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    GOSH_TRY(gosh_device_check(stream));
     if (stats) {
         for (int i = 0; i < D; ++i) {
             train_ms[i] = ev.elapsed(2 * i + 1, 2 * i);

@@ -101,7 +101,7 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;
     const int cap_blocks = num_sms() * kern->blocks_per_sm;
-    const int64_t want = ceil_div(ceil_div(n, 32), kTrainWarps);
+    const int64_t want = ceil_div(ceil_div(n, 32), kern->warps);
     const int grid = (int)(want < cap_blocks ? (want > 0 ? want : 1) : cap_blocks);
     double *partials = nullptr;
     if (loss_per_epoch) {

@@ -23,6 +23,10 @@ struct Registry {
         entries.insert(entries.end(), e, e + c);
         e = train_entries_f16(&c);
         entries.insert(entries.end(), e, e + c);
+        e = train_tma_entries_f32(&c);
+        entries.insert(entries.end(), e, e + c);
+        e = train_tma_entries_bf16(&c);
+        entries.insert(entries.end(), e, e + c);
         made.resize(entries.size());
         ready.assign(entries.size(), false);
     }
@@ -111,14 +115,23 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
                               const TrainKernel **out) {
     const bool det = mode == kModeDet;
     const int ns = k + 1;
-    // Defaults from the lanes/pass sweep on R-MAT 20 (d = 128, k = 3): 16-bit
-    // tables do best with two 16-byte vectors per lane (more sources in flight
-    // per warp), FP32 with one; two sample rows per pass keep registers low.
+    // Defaults from the lanes/pass sweeps on R-MAT 20 (d = 128, k = 3):
+    // FP32 lock-free runs best with every row staged by TMA (one 16-byte
+    // vector per lane); 16-bit tables do best in registers with two vectors
+    // per lane (more sources in flight per warp) and two sample rows per pass.
+    if (lanes <= 0 && pass == 0 && mode == kModeRed && ns <= 6) {
+        lanes = natural_lanes(dtype, d);
+        pass = ns <= 4 ? -4 : -6;
+    }
     if (lanes <= 0) {
         const int nat = natural_lanes(dtype, d);
         lanes = (!det && dtype != GOSH_F32 && nat >= 4) ? nat / 2 : nat;
     }
-    if (pass <= 0) pass = det ? (ns <= 4 ? 4 : 8) : 2;
+    if (pass == 0) pass = det ? (ns <= 4 ? 4 : 8) : 2;
+    if (pass < 0 && (det || ns > -pass)) {
+        set_error("TMA-staged kernels (samples_per_pass = -S) serve the lock-free mode with k+1 <= S (k+1 = %d)", ns);
+        return GOSH_ERR_UNSUPPORTED;
+    }
     if (det && pass < ns) {
         set_error("deterministic mode gathers all k+1 samples in one pass: samples_per_pass %d < k+1 = %d",
                   pass, ns);
@@ -158,10 +171,11 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
     a.graph = p->graph_id;
     a.level = (uint32_t)level;
     a.n_updates = n_updates;
+    a.err = device_error_word();
 
     auto grid_for = [&](int64_t nsrc) {
         const int64_t tiles = ceil_div(nsrc, 32);
-        const int64_t want = ceil_div(tiles, kTrainWarps);
+        const int64_t want = ceil_div(tiles, kern->warps);
         return (int)(want < cap_blocks ? (want > 0 ? want : 1) : cap_blocks);
     };
 

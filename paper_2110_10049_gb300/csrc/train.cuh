@@ -40,14 +40,20 @@ struct TrainArgs {
     // monitors
     double *loss_partials;     // [gridDim.x] or null
     unsigned long long *n_updates;  // or null
+    int *err;                  // device error word raised by a timed-out wait, or null
 };
+
+// Per-device error word of the library (lazily allocated; read and cleared
+// by gosh_device_check).
+int *device_error_word();
 
 // Host-side launcher for one epoch (Hogwild) or one snapshot batch (deterministic).
 struct TrainKernel {
     void (*launch)(const TrainArgs &, int grid, cudaStream_t);
     int blocks_per_sm;
     int lanes;     // L
-    int pass;      // P
+    int pass;      // P (negative: all of up to -P samples staged by TMA)
+    int warps;     // warps per block
 };
 
 // One compiled variant: its key and a factory (the factory queries occupancy,
@@ -61,6 +67,8 @@ struct TrainEntry {
 const TrainEntry *train_entries_f32(int *count);
 const TrainEntry *train_entries_bf16(int *count);
 const TrainEntry *train_entries_f16(int *count);
+const TrainEntry *train_tma_entries_f32(int *count);
+const TrainEntry *train_tma_entries_bf16(int *count);
 void det_apply_f32(int d, const uint32_t *skeys, const uint32_t *sidx, int64_t nslots, const float *C,
                    const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
                    uint32_t sr_seed, cudaStream_t s);

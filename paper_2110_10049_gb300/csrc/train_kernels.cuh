@@ -292,6 +292,7 @@ TrainKernel make_train_kernel() {
     if (k.blocks_per_sm < 1) k.blocks_per_sm = 1;
     k.lanes = L;
     k.pass = P;
+    k.warps = kTrainWarps;
     return k;
 }
 

@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
             "gosh_link_auc": [vp, i32, i32, vp, i64, vp, i64, vp, P(C.c_double)],
             "gosh_tc_gemm_bf16": [vp, i64, vp, i64, vp, i64, i32, i32, i32, i32, vp],
             "gosh_embed_batch": [i32, vp, P(gosh_params), vp, vp, P(gosh_batch_stats)],
+            "gosh_device_check": [vp],
             "gosh_train_level_large": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, P(gosh_large_stats)],
             "gosh_large_plan": [i64, i32, i32, i32, vp, vp, i32],
             "gosh_mlp_create": [i32, i32, u64, P(vp)],

@@ -31,7 +31,9 @@ def test_single_part_equals_resident_step():
     csr = g.to_device_csr(gr.rowptr, gr.col)
     Md = torch.from_numpy(M0.copy()).cuda()
     nup = torch.zeros(1, dtype=torch.int64, device="cuda")
-    g.gosh_train_level(csr, Md, 0, 12, g.default_params(d=128, k=3, lr=0.05, seed=8), n_updates=nup)
+    # register kernel, 32 lanes: one warp takes the sources strictly in order
+    g.gosh_train_level(csr, Md, 0, 12, g.default_params(d=128, k=3, lr=0.05, seed=8, lanes_per_row=32,
+                                                        samples_per_pass=2), n_updates=nup)
     assert st["updates"] == int(nup.item())
     assert rel_fro(Mh, Md.cpu().numpy()) <= 1e-5
 
