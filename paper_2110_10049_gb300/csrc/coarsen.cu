@@ -129,18 +129,39 @@ __global__ void assign_map(const int32_t *__restrict__ hub_rank, const int64_t *
     }
 }
 
-// key of every CSR entry: (map v) << 32 | map u, or the sentinel nc << 32 for a self-loop.
+// Key of every CSR entry (v, u): map v * nc + map u, or the sentinel nc * nc for
+// a self-loop (packed so the sort needs only ceil(log2(nc^2) / 8) passes).
+// Balanced over entries: each warp takes 1024 consecutive entries; a lane finds
+// the row of its first entry by binary search and then walks forward.
+constexpr int kEntriesPerWarp = 1024;
 __global__ void __launch_bounds__(256) edge_image(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                                  int64_t n, const int32_t *__restrict__ map, uint64_t sentinel,
+                                                  int64_t n, const int32_t *__restrict__ map, uint64_t nc,
                                                   uint64_t *__restrict__ keys) {
     const int lane = threadIdx.x & 31;
+    const int64_t nnz = rowptr[n];
+    const int64_t sentinel = (int64_t)(nc * nc);
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = wid; v < n; v += wstride) {
-        const uint32_t a = (uint32_t)map[v];
-        for (int64_t p = rowptr[v] + lane; p < rowptr[v + 1]; p += 32) {
-            const uint32_t b = (uint32_t)map[col[p]];
-            keys[p] = a != b ? (((uint64_t)a << 32) | b) : sentinel;
+    for (int64_t base = wid * kEntriesPerWarp; base < nnz; base += wstride * kEntriesPerWarp) {
+        int64_t p = base + lane;
+        if (p >= nnz) continue;
+        int64_t lo = 0, hi = n;  // last row with rowptr[row] <= p
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(rowptr + mid) <= p) lo = mid; else hi = mid;
+        }
+        int64_t r = lo;
+        int64_t rend = __ldg(rowptr + r + 1);
+        uint64_t a = (uint64_t)__ldg(map + r);
+        const int64_t end = base + kEntriesPerWarp < nnz ? base + kEntriesPerWarp : nnz;
+        for (; p < end; p += 32) {
+            while (rend <= p) {
+                ++r;
+                rend = __ldg(rowptr + r + 1);
+                a = (uint64_t)__ldg(map + r);
+            }
+            const uint64_t b = (uint64_t)__ldg(map + __ldg(col + p));
+            keys[p] = a != b ? a * nc + b : (uint64_t)sentinel;
         }
     }
 }
@@ -157,12 +178,13 @@ __global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *_
                              const int64_t *__restrict__ pos, int64_t nnz, uint64_t sentinel, int64_t nc,
                              int32_t *__restrict__ col_out, int64_t *__restrict__ rowptr) {
     const int64_t m = pos[nnz];
+    const uint64_t unc = (uint64_t)nc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = keys[i];
         if (key == sentinel) continue;
-        if (f[i]) col_out[pos[i]] = (int32_t)(key & 0xffffffffu);
-        const int64_t r = (int64_t)(key >> 32);
-        const int64_t rprev = i == 0 ? -1 : (int64_t)(keys[i - 1] >> 32);
+        const int64_t r = (int64_t)(key / unc);
+        if (f[i]) col_out[pos[i]] = (int32_t)(key - (uint64_t)r * unc);
+        const int64_t rprev = i == 0 ? -1 : (int64_t)(keys[i - 1] / unc);
         for (int64_t c = rprev + 1; c <= r; ++c) rowptr[c] = pos[i];
         if (i + 1 == nnz || keys[i + 1] == sentinel)
             for (int64_t c = r + 1; c <= nc; ++c) rowptr[c] = m;
@@ -256,34 +278,35 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     // 4. COARSEN
     int64_t *rp = nullptr;
     int32_t *co = nullptr;
-    GOSH_TRY_CUDA(cudaMalloc(&rp, sizeof(int64_t) * (nc + 1)));
+    // hierarchy buffers come from the stream-ordered pool (no device-wide sync)
+    GOSH_TRY_CUDA(cudaMallocAsync(&rp, sizeof(int64_t) * (nc + 1), s));
     int64_t m = 0;
     if (nnz > 0) {
         Scratch ek, fl, pos;
         GOSH_TRY(ek.alloc(sizeof(uint64_t) * nnz, s));
         GOSH_TRY(fl.alloc(nnz, s));
         GOSH_TRY(pos.alloc(sizeof(int64_t) * (nnz + 1), s));
-        const uint64_t sentinel = (uint64_t)nc << 32;
-        (edge_image<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, map, sentinel, ek.as<uint64_t>()), note_launch());
+        const uint64_t unc = (uint64_t)nc;
+        const uint64_t sentinel = unc * unc;
+        (edge_image<<<grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s>>>(rowptr, col, n, map, unc,
+                                                                                 ek.as<uint64_t>()),
+         note_launch());
         int shifts[8];
         int nd = 0;
-        const int bb = bits_for((uint64_t)(nc > 0 ? nc - 1 : 0)), ba = bits_for((uint64_t)nc);
-        for (int b = 0; b < bb; b += 8) shifts[nd++] = b;
-        for (int b = 0; b < ba; b += 8) shifts[nd++] = 32 + b;
+        const int kb = bits_for(sentinel);
+        for (int b = 0; b < kb && nd < 8; b += 8) shifts[nd++] = b;
         GOSH_TRY(radix_sort_u64(ek.as<uint64_t>(), nullptr, nnz, shifts, nd, s));
         (unique_flags<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), nnz, sentinel, fl.as<uint8_t>()), note_launch());
         GOSH_TRY(scan_exclusive_u8_to_i64(fl.as<uint8_t>(), pos.as<int64_t>(), nnz, pos.as<int64_t>() + nnz, s));
         GOSH_TRY_CUDA(cudaMemcpyAsync(&m, pos.as<int64_t>() + nnz, sizeof(m), cudaMemcpyDeviceToHost, s));
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
-        GOSH_TRY_CUDA(cudaMalloc(&co, sizeof(int32_t) * (m > 0 ? m : 1)));
+        GOSH_TRY_CUDA(cudaMallocAsync(&co, sizeof(int32_t) * (m > 0 ? m : 1), s));
         GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
         (write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz,
                                                    sentinel, nc, co, rp), note_launch());
-        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     } else {
-        GOSH_TRY_CUDA(cudaMalloc(&co, sizeof(int32_t)));
+        GOSH_TRY_CUDA(cudaMallocAsync(&co, sizeof(int32_t), s));
         GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
-        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     }
     *nc_out = nc;
     *rp_out = rp;
@@ -294,6 +317,7 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
 
 gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int max_levels, cudaStream_t s,
                          gosh_hierarchy **out) {
+    keep_pool_memory();
     gosh_hierarchy *h = new gosh_hierarchy();
     int64_t nnz0 = 0;
     cudaError_t e = cudaMemcpyAsync(&nnz0, g0->rowptr + g0->n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -312,9 +336,9 @@ gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int m
         const size_t i = h->n.size() - 1;
         const int64_t n = h->n[i];
         int32_t *map = nullptr;
-        if (cudaMalloc(&map, sizeof(int32_t) * (n > 0 ? n : 1)) != cudaSuccess) {
+        if (cudaMallocAsync(&map, sizeof(int32_t) * (n > 0 ? n : 1), s) != cudaSuccess) {
             delete h;
-            set_error("cudaMalloc of map_%zu failed", i);
+            set_error("allocation of map_%zu failed", i);
             return GOSH_ERR_OOM;
         }
         h->map.push_back(map);
@@ -332,6 +356,12 @@ gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int m
         h->col.push_back(co);
         const bool more = nc > threshold && (double)nc <= std::floor(shrink * (double)n);
         if (!more || (int)h->n.size() >= max_levels) break;
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e2 != cudaSuccess) {
+        delete h;
+        set_error("coarsening: %s", cudaGetErrorString(e2));
+        return GOSH_ERR_CUDA;
     }
     *out = h;
     return GOSH_OK;

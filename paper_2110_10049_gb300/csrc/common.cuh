@@ -45,6 +45,11 @@ void note_launch();
         }                                                                                \
     } while (0)
 
+// Keeps freed stream-ordered memory cached in the device's default pool
+// (release threshold = unlimited) so repeated calls do not re-map physical
+// pages for their scratch; done once per device.
+void keep_pool_memory();
+
 // Stream-ordered device scratch, released on the same stream when it leaves scope.
 struct Scratch {
     void *ptr = nullptr;
@@ -57,6 +62,7 @@ struct Scratch {
         release();
         stream = s;
         if (bytes == 0) bytes = 16;
+        keep_pool_memory();
         cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
         if (e != cudaSuccess) {
             ptr = nullptr;
