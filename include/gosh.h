@@ -92,6 +92,12 @@ typedef struct gosh_params {
     int s_gpu;              /* LargeGraphGPU: edge-block bins on the device (paper: 2) */
     int B;                  /* LargeGraphGPU: positives per vertex per part pair per round (paper: 5) */
     int large_parts;        /* LargeGraphGPU: K; 0 = derive from device_budget_bytes */
+    int persistent_small_levels; /* gosh_embed, lock-free with copy projection and automatic
+                               kernels: 1 trains every level with |V_i| <= 2^17 in one
+                               persistent launch (as gosh_embed_batch does); 0 (default)
+                               launches every epoch separately */
+    int vertices_per_warp;  /* sources a warp takes per tile (<= 32, rounded to a multiple
+                               of 32/lanes_per_row); 0 = by level size (8 / 16 / 32) */
 } gosh_params;
 
 typedef struct gosh_large_stats {

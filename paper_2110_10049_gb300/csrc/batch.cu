@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32) batch_kernel(BatchArgs b) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int g = (int)(((int64_t)blockIdx.x * kTrainWarps + warp) % b.G);
     int misses = 0;
+    unsigned backoff = 32;
     unsigned long long idle_since = 0;
     double loss = 0.0;
     unsigned long long applied = 0;
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32) batch_kernel(BatchArgs b) {
                     a.lr = P_.lr;
                     a.src_begin = r0;
                     a.src_end = r1;
+                    a.tile = 32;
                     for (int64_t v0 = r0; v0 < r1; v0 += 32)
                         train_tile<T, D, L, P, MODE>(a, v0, s_u[warp], s_sr[warp], loss, applied);
                 } else if (P_.type == kPhaseInit) {
@@ -186,10 +188,11 @@ __global__ void __launch_bounds__(kTrainWarps * 32) batch_kernel(BatchArgs b) {
         if (worked) {
             misses = 0;
             idle_since = 0;
+            backoff = 32;
             continue;
         }
         g = g + 1 == b.G ? 0 : g + 1;
-        if (++misses >= b.G) {  // a full sweep found nothing: back off, bounded
+        if (++misses >= b.G) {  // a full sweep found nothing: back off (exponentially), bounded
             misses = 0;
             const unsigned long long now = global_ns();
             if (idle_since == 0) idle_since = now;
@@ -197,7 +200,8 @@ __global__ void __launch_bounds__(kTrainWarps * 32) batch_kernel(BatchArgs b) {
                 if (lane == 0) atomicExch(b.err, 1);
                 break;
             }
-            __nanosleep(200);
+            __nanosleep(backoff);
+            backoff = backoff < 2048 ? backoff * 2 : 2048;
         }
     }
 #pragma unroll
@@ -284,8 +288,10 @@ struct Plan {
     Scratch d_phases, d_first, d_count, d_ctl, d_done, d_err;
 };
 
+// Phases of levels D-1 .. lowest of every graph (projections between them).
 gosh_status build_plan(const std::vector<gosh_hierarchy *> &hs, const std::vector<std::vector<void *>> &bufs,
-                       const gosh_params &p, int epochs, int rows_per_item, Plan &plan, cudaStream_t s) {
+                       const gosh_params &p, int epochs, int rows_per_item, Plan &plan, cudaStream_t s,
+                       int lowest = 0) {
     plan.phases.clear();
     plan.first.clear();
     plan.count.clear();
@@ -303,7 +309,7 @@ gosh_status build_plan(const std::vector<gosh_hierarchy *> &hs, const std::vecto
         init.items = items(init.n);
         init.M = bufs[gi][D - 1];
         plan.phases.push_back(init);
-        for (int i = D - 1; i >= 0; --i) {
+        for (int i = D - 1; i >= lowest; --i) {
             for (int j = 0; j < ep[i]; ++j) {
                 Phase t{};
                 t.type = kPhaseTrain;
@@ -318,7 +324,7 @@ gosh_status build_plan(const std::vector<gosh_hierarchy *> &hs, const std::vecto
                 t.M = bufs[gi][i];
                 plan.phases.push_back(t);
             }
-            if (i > 0) {
+            if (i > lowest) {
                 Phase pr{};
                 pr.type = kPhaseProject;
                 pr.level = i - 1;
@@ -365,7 +371,12 @@ gosh_status run_plan(Plan &plan, const BatchKernel *kern, const gosh_params &p, 
     b.graphs_done = plan.d_done.as<unsigned long long>();
     b.err = plan.d_err.as<int>();
     b.n_updates = n_updates;
-    const int grid = num_sms() * kern->blocks_per_sm;
+    // no more warps than the widest moment of the schedule can use: with G
+    // graphs at most G phases run at once, each with at most max-items items
+    int64_t max_items = 1;
+    for (const Phase &ph : plan.phases) max_items = std::max<int64_t>(max_items, ph.items);
+    const int64_t useful = std::max<int64_t>(1, ceil_div(max_items * G, kTrainWarps));
+    const int grid = (int)std::min<int64_t>((int64_t)num_sms() * kern->blocks_per_sm, useful);
 
     cudaStream_t cs;
     GOSH_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -409,6 +420,33 @@ gosh_status run_plan(Plan &plan, const BatchKernel *kern, const gosh_params &p, 
 }
 
 }  // namespace
+
+// Trains levels D-1 .. lowest of one hierarchy in one persistent launch: the
+// initialisation of M_{D-1}, every epoch of those levels and the copy
+// projections between them, with no host round trip between epochs (the
+// small levels of a hierarchy are otherwise bound by launch latency).
+// bufs[i] holds M_i.  Same Philox streams as the per-epoch launches.
+gosh_status persistent_levels(gosh_hierarchy *h, const std::vector<void *> &bufs, int lowest, const gosh_params &p,
+                              unsigned long long *n_updates, cudaStream_t s) {
+    const int L0 = p.d * (int)dtype_size(p.dtype) / 16;
+    int lanes = p.dtype == GOSH_F32 ? L0 : L0 / 2, pass = 2, rpi = 64;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        auto it = g_tuned.find(std::make_tuple((int)p.dtype, p.d, p.k));
+        if (it != g_tuned.end()) std::tie(lanes, pass, rpi) = it->second;
+    }
+    const BatchKernel *kern = find_batch(p.dtype, p.d, lanes, pass);
+    if (!kern) {
+        set_error("no persistent kernel for dtype %d, d %d", (int)p.dtype, p.d);
+        return GOSH_ERR_UNSUPPORTED;
+    }
+    std::vector<gosh_hierarchy *> hs{h};
+    std::vector<std::vector<void *>> bv{bufs};
+    Plan plan;
+    GOSH_TRY(build_plan(hs, bv, p, p.epochs, rpi, plan, s, lowest));
+    return run_plan(plan, kern, p, rpi, n_updates, s, nullptr);
+}
+
 }  // namespace gosh
 
 using namespace gosh;

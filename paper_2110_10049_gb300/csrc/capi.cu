@@ -62,6 +62,8 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
                              cudaStream_t s, double *loss_per_epoch, unsigned long long *n_updates);
 gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int max_levels, cudaStream_t s,
                          gosh_hierarchy **out);
+gosh_status persistent_levels(gosh_hierarchy *h, const std::vector<void *> &bufs, int lowest, const gosh_params &p,
+                              unsigned long long *n_updates, cudaStream_t s);
 
 namespace {
 
@@ -325,15 +327,21 @@ struct EventTimer {
 // A fixed set of events recorded on a stream and read after a synchronize.
 struct EventList {
     std::vector<cudaEvent_t> e;
-    explicit EventList(int n) : e(n, nullptr) {
+    std::vector<bool> rec;
+    explicit EventList(int n) : e(n, nullptr), rec(n, false) {
         for (auto &x : e) cudaEventCreate(&x);
     }
     void record(int i, cudaStream_t s) {
-        if (i < (int)e.size()) cudaEventRecord(e[i], s);
+        if (i < (int)e.size() && cudaEventRecord(e[i], s) == cudaSuccess) rec[i] = true;
     }
+    // 0 unless both events were recorded
     double elapsed(int a, int b) const {
         float ms = 0.f;
-        if (a < (int)e.size() && b < (int)e.size()) cudaEventElapsedTime(&ms, e[a], e[b]);
+        if (a < (int)e.size() && b < (int)e.size() && rec[a] && rec[b] &&
+            cudaEventElapsedTime(&ms, e[a], e[b]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
         return ms;
     }
     ~EventList() {
@@ -384,6 +392,8 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->s_gpu = 2;
     p->B = 5;
     p->large_parts = 0;
+    p->persistent_small_levels = 0;
+    p->vertices_per_warp = 0;
     return GOSH_OK;
 }
 
@@ -639,9 +649,30 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
     GOSH_TRY(counter.alloc(sizeof(unsigned long long), s));
     GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
 
-    GOSH_TRY(gosh_init_embedding(buf(D - 1), h->n[D - 1], p.d, p.dtype, D - 1, p.seed, p.graph_id, stream));
     // per-level events, read once at the end so that no level waits for the host
     EventList ev(stats ? 2 * D + 1 : 0);
+    // The small levels (|V_i| <= 2^17) of a lock-free, copy-projection run go
+    // through one persistent launch (epochs would otherwise be launch-bound);
+    // the large levels keep one launch per epoch with the best kernel.
+    int top = D - 1;  // highest level still to train below
+    const bool persist = p.persistent_small_levels && p.mode == GOSH_HOGWILD && p.projection == 0 && D > 1 &&
+                         (p.dtype == GOSH_F32 || p.dtype == GOSH_BF16) && p.lanes_per_row == 0 &&
+                         p.samples_per_pass == 0;
+    int lowest = D;
+    if (persist)
+        while (lowest > 1 && h->n[lowest - 1] <= (int64_t(1) << 17)) --lowest;
+    if (persist && lowest <= D - 1) {
+        std::vector<void *> bufs(D);
+        for (int i = 0; i < D; ++i) bufs[i] = buf(i);
+        ev.record(2 * (D - 1) + 1, s);
+        GOSH_TRY(persistent_levels(h, bufs, lowest, p, counter.as<unsigned long long>(), s));
+        ev.record(2 * lowest, s);
+        GOSH_TRY(gosh_project(buf(lowest), h->n[lowest], h->map[lowest - 1], buf(lowest - 1), h->n[lowest - 1], p.d,
+                              p.dtype, stream));
+        top = lowest - 1;
+    } else {
+        GOSH_TRY(gosh_init_embedding(buf(D - 1), h->n[D - 1], p.d, p.dtype, D - 1, p.seed, p.graph_id, stream));
+    }
     // learned projection: one network for the whole run, trained after each
     // level i < D-1 on (features from M_{i+1}, trained M_i) before M_{i+1}'s
     // buffer is reused for M_{i-1}
@@ -651,7 +682,7 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
     } mlp;
     if (p.projection == 1 && D > 1)
         GOSH_TRY(gosh_mlp_create(p.d, p.mlp_hidden > 0 ? p.mlp_hidden : 256, p.seed ^ 0x6d6c70ull, &mlp.m));
-    for (int i = D - 1; i >= 0; --i) {
+    for (int i = top; i >= 0; --i) {
         gosh_csr gi{h->n[i], h->rowptr[i], h->col[i], 1};
         ev.record(2 * i + 1, s);
         GOSH_TRY(train_level_impl(&gi, buf(i), i, ep[i], &p, s, nullptr, counter.as<unsigned long long>()));

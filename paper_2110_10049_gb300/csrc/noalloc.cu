@@ -18,6 +18,7 @@ namespace gosh {
 gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lanes, int pass,
                               const TrainKernel **out);
 int train_mode(const gosh_params *p);
+int tile_vertices(const gosh_params *p, int64_t n, int lanes);
 
 namespace {
 
@@ -101,7 +102,7 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;
     const int cap_blocks = num_sms() * kern->blocks_per_sm;
-    const int64_t want = ceil_div(ceil_div(n, 32), kern->warps);
+    const int64_t want = ceil_div(ceil_div(n, tile_vertices(p, n, kern->lanes)), kern->warps);
     const int grid = (int)(want < cap_blocks ? (want > 0 ? want : 1) : cap_blocks);
     double *partials = nullptr;
     if (loss_per_epoch) {
@@ -125,6 +126,7 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
     a.loss_partials = partials;
     a.src_begin = 0;
     a.src_end = n;
+    a.tile = tile_vertices(p, n, kern->lanes);
     for (int j = 0; j < epochs; ++j) {
         const double f = 1.0 - (double)j / (double)epochs;
         a.lr = (float)(p->lr * (f > p->lr_floor ? f : p->lr_floor));

@@ -103,6 +103,18 @@ int list_train_variants(gosh_dtype dtype, int d, int mode, int *lanes, int *pass
 // Natural lanes per row: one 16-byte vector per lane.
 int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) / 16; }
 
+// Sources per warp tile.  A warp walks its tile in tile / (32/L) dependent
+// rounds, so small levels (few tiles, far fewer than the GPU's warps) take
+// short tiles; large levels take 32 to amortise the draws.  A multiple of
+// 32/L in [32/L, 32]; params->vertices_per_warp overrides.
+int tile_vertices(const gosh_params *p, int64_t n, int lanes) {
+    const int G = 32 / lanes;
+    int t = p->vertices_per_warp;
+    if (t <= 0) t = n >= (int64_t(1) << 19) ? 32 : (n >= (int64_t(1) << 16) ? 16 : 8);
+    t = t < G ? G : (t > 32 ? 32 : t);
+    return t / G * G;
+}
+
 // Kernel mode for the parameters: deterministic batches, or the lock-free
 // epoch with atomic FP32 row changes unless plain stores are requested (and
 // always plain stores with stochastic rounding for 16-bit tables).
@@ -172,9 +184,10 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
     a.level = (uint32_t)level;
     a.n_updates = n_updates;
     a.err = device_error_word();
+    a.tile = tile_vertices(p, n, kern->lanes);
 
     auto grid_for = [&](int64_t nsrc) {
-        const int64_t tiles = ceil_div(nsrc, 32);
+        const int64_t tiles = ceil_div(nsrc, a.tile);
         const int64_t want = ceil_div(tiles, kern->warps);
         return (int)(want < cap_blocks ? (want > 0 ? want : 1) : cap_blocks);
     };

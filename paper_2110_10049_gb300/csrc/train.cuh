@@ -33,6 +33,7 @@ struct TrainArgs {
     uint32_t level, epoch;     // Philox counter word 2 = level << 32 | epoch
     float lr;                  // lr' of this epoch
     int64_t src_begin, src_end;
+    int tile;                  // sources per warp tile (a multiple of 32/L, <= 32)
     // deterministic mode (snapshot batch [src_begin, src_end))
     float *R;                  // [(src_end-src_begin) x D]  final source rows
     float *C;                  // [(src_end-src_begin)*(k+1) x D] sample-row changes

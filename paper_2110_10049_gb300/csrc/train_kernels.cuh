@@ -111,7 +111,7 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
         // ---- draws: lane j -> source v0 + j ----
         {
             const int64_t v = v0 + lane;
-            if (v < a.src_end) {
+            if (lane < a.tile && v < a.src_end) {
                 const int64_t off = a.rowptr[v];
                 const int64_t deg = a.rowptr[v + 1] - off;
                 for (int blk = 0; blk * 4 < ns; ++blk) {
@@ -136,9 +136,10 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
             }
         }
         __syncwarp();
-        // ---- rounds: G sources at a time, L lanes each ----
+        // ---- rounds: G sources at a time, L lanes each (tile / G rounds) ----
+        const int rounds = a.tile / G;
 #pragma unroll 1
-        for (int q = 0; q < L; ++q) {
+        for (int q = 0; q < rounds; ++q) {
             const int j = q * G + grp;
             const int64_t v = v0 + j;
             const bool active = v < a.src_end;
@@ -249,13 +250,13 @@ __global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
     __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
     __shared__ uint32_t s_sr[kTrainWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t ntiles = (a.src_end - a.src_begin + 31) / 32;
+    const int64_t ntiles = (a.src_end - a.src_begin + a.tile - 1) / a.tile;
     const int64_t wstride = (int64_t)gridDim.x * kTrainWarps;
     const bool want_loss = a.loss_partials != nullptr;
     double loss_acc = 0.0;
     unsigned long long applied = 0;
     for (int64_t tile = (int64_t)blockIdx.x * kTrainWarps + warp; tile < ntiles; tile += wstride)
-        train_tile<T, D, L, P, MODE>(a, a.src_begin + tile * 32, s_u[warp], s_sr[warp], loss_acc, applied);
+        train_tile<T, D, L, P, MODE>(a, a.src_begin + tile * a.tile, s_u[warp], s_sr[warp], loss_acc, applied);
 
     // ---- monitors ----
     if (a.n_updates) {

@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
     unsigned long long applied = 0;
     double loss_acc = 0.0;
     const bool want_loss = a.loss_partials != nullptr;
-    const int64_t ntiles = (a.src_end - a.src_begin + 31) / 32;
+    const int64_t ntiles = (a.src_end - a.src_begin + a.tile - 1) / a.tile;
+    const int rounds = a.tile / G;
     bool failed = false;
 
     // issues the copies of round q of the tile starting at v0 into stage st
@@ -122,12 +123,12 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
 
     for (int64_t tile = (int64_t)blockIdx.x * kTmaWarps + warp; tile < ntiles && !failed;
          tile += (int64_t)gridDim.x * kTmaWarps) {
-        const int64_t v0 = a.src_begin + tile * 32;
+        const int64_t v0 = a.src_begin + tile * a.tile;
         // ---- draws (as in train_tile) ----
         {
             const uint64_t ctr2 = ((uint64_t)a.level << 32) | a.epoch;
             const int64_t v = v0 + lane;
-            if (v < a.src_end) {
+            if (lane < a.tile && v < a.src_end) {
                 const int64_t off = a.rowptr[v];
                 const int64_t deg = a.rowptr[v + 1] - off;
                 for (int blk = 0; blk * 4 < ns; ++blk) {
@@ -154,14 +155,14 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
         __syncwarp();
         issue(v0, 0, 0);
 #pragma unroll 1
-        for (int q = 0; q < L; ++q) {
+        for (int q = 0; q < rounds; ++q) {
             const int st = q & 1;
-            if (q + 1 < L) issue(v0, q + 1, st ^ 1);
+            if (q + 1 < rounds) issue(v0, q + 1, st ^ 1);
             if (!mbar_try(st ? bar1 : bar0, phase[st], kTmaWaitPolls)) {
                 failed = true;
                 if (lane == 0 && a.err) atomicExch(a.err, 1);
                 mbar_try(st ? bar1 : bar0, phase[st], kTmaWaitPolls);
-                if (q + 1 < L) mbar_try(st ? bar0 : bar1, phase[st ^ 1], kTmaWaitPolls);
+                if (q + 1 < rounds) mbar_try(st ? bar0 : bar1, phase[st ^ 1], kTmaWaitPolls);
                 break;
             }
             phase[st] ^= 1;

@@ -41,7 +41,8 @@ class gosh_params(C.Structure):
                 ("samples_per_pass", C.c_int), ("device_budget_bytes", C.c_int64), ("validate", C.c_int),
                 ("plain_stores", C.c_int), ("projection", C.c_int), ("mlp_hidden", C.c_int),
                 ("mlp_epochs", C.c_int), ("mlp_lr", C.c_double), ("mlp_batch", C.c_int),
-                ("mlp_max_rows", C.c_int64), ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int)]
+                ("mlp_max_rows", C.c_int64), ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int),
+                ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int)]
 
 
 class gosh_large_stats(C.Structure):

@@ -28,12 +28,12 @@ def test_batch_equals_standalone_on_single_warp_graphs():
     graphs = [synth.random_graph(int(n), 0.25, int(s)) for n, s in zip(range(18, 32, 2), range(7))]
     csrs = [dev_csr(g, gr) for gr in graphs]
     p = g.default_params(d=128, k=3, lr=0.05, epochs=30, p=0.3, seed=5, graph_id=100,
-                         lanes_per_row=32, samples_per_pass=2, threshold=4)
+                         lanes_per_row=32, samples_per_pass=2, threshold=4, vertices_per_warp=32)
     outs, st = g.gosh_embed_batch(csrs, p)
     assert st["graphs"] == len(graphs)
     for i, gr in enumerate(graphs):
         q = g.default_params(d=128, k=3, lr=0.05, epochs=30, p=0.3, seed=5, graph_id=100 + i,
-                             lanes_per_row=32, samples_per_pass=2, threshold=4)
+                             lanes_per_row=32, samples_per_pass=2, threshold=4, vertices_per_warp=32)
         M, _ = g.gosh_embed(csrs[i].rowptr, csrs[i].col, q)
         assert rel_fro(outs[i].double().cpu().numpy(), M.double().cpu().numpy()) <= 1e-5
 

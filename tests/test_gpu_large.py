@@ -33,7 +33,7 @@ def test_single_part_equals_resident_step():
     nup = torch.zeros(1, dtype=torch.int64, device="cuda")
     # register kernel, 32 lanes: one warp takes the sources strictly in order
     g.gosh_train_level(csr, Md, 0, 12, g.default_params(d=128, k=3, lr=0.05, seed=8, lanes_per_row=32,
-                                                        samples_per_pass=2), n_updates=nup)
+                                                        samples_per_pass=2, vertices_per_warp=32), n_updates=nup)
     assert st["updates"] == int(nup.item())
     assert rel_fro(Mh, Md.cpu().numpy()) <= 1e-5
 

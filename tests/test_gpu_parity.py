@@ -114,7 +114,7 @@ def train_gpu(g, gr, M0, k, level, epochs, lr, seed, mode, m=1, dtype=torch.floa
     csr = g.to_device_csr(gr.rowptr, gr.col)
     M = dev(M0, dtype)
     p = g.default_params(d=M0.shape[1], k=k, lr=lr, dtype=dtype, mode=mode, det_batch=m, seed=seed,
-                         lanes_per_row=lanes, samples_per_pass=pas)
+                         lanes_per_row=lanes, samples_per_pass=pas, vertices_per_warp=32 if lanes == 32 else 0)
     loss = torch.zeros(max(epochs, 1), dtype=torch.float64, device="cuda")
     nup = torch.zeros(1, dtype=torch.int64, device="cuda")
     g.gosh_train_level(csr, M, level, epochs, p, loss=loss, n_updates=nup)

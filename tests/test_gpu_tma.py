@@ -31,7 +31,7 @@ def test_staged_single_warp_matches_sequential():
     csr = g.to_device_csr(gr.rowptr, gr.col)
     M = torch.from_numpy(M0.astype(np.float32)).cuda()
     nup = torch.zeros(1, dtype=torch.int64, device="cuda")
-    p = g.default_params(d=128, k=0, lr=0.05, seed=8, lanes_per_row=32, samples_per_pass=-4)
+    p = g.default_params(d=128, k=0, lr=0.05, seed=8, lanes_per_row=32, samples_per_pass=-4, vertices_per_warp=32)
     g.gosh_train_level(csr, M, 0, 10, p, n_updates=nup)
     torch.cuda.synchronize()
     assert int(nup.item()) == no

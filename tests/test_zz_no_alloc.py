@@ -28,7 +28,7 @@ def test_noalloc_matches_train_level_on_two_calls():
     csr = g.to_device_csr(gr.rowptr, gr.col)
     rng = np.random.default_rng(4)
     M0 = torch.from_numpy(rng.uniform(-0.3, 0.3, (gr.n, 128)).astype(np.float32)).cuda()
-    p = g.default_params(d=128, k=5, lr=0.05, seed=8, lanes_per_row=32)
+    p = g.default_params(d=128, k=5, lr=0.05, seed=8, lanes_per_row=32, vertices_per_warp=32)
     Ma, Mb = M0.clone(), M0.clone()
     for call in range(2):
         epochs = 7 + call
