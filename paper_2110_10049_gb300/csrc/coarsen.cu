@@ -15,9 +15,13 @@
 //      dependency chains in a handful of rounds);
 //   3. each non-hub takes its earliest-ranked eligible hub neighbour;
 //      cluster id = number of hubs ranked before the hub (prefix sum);
-//   4. COARSEN: key (map v, map u) per CSR entry, self-loops dropped, radix
-//      sort, unique, CSR of G_{i+1}.
+//   4. COARSEN: coarse row c = the set of map[u] over the edges (v, u) of
+//      the members v of cluster c, minus c: built in a shared-memory bitmap
+//      over the coarse ids and read back in ascending order (sorted, unique);
+//      above 2^19 coarse vertices, by a radix sort of packed (map v, map u)
+//      keys instead.
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "hierarchy.cuh"
@@ -191,6 +195,217 @@ __global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *_
     }
 }
 
+// ---- COARSEN through per-row bitmaps ----------------------------------------
+// Coarse row c is the union of map[N(x)] over the members x of cluster c,
+// minus c itself.  The members that have neighbours are grouped by cluster
+// and their CSR rows, laid end to end, are the "virtual entries" of row c,
+// cut into chunks of kChunk entries.  A block takes one chunk and sets bit
+// map[y] of a shared-memory bitmap over the nc coarse ids for each entry
+// (plus one summary bit per nonzero 32-bit word), then reads the set bits
+// back in ascending order: the row comes out sorted and deduplicated without
+// a global sort, and only the words the chunk touched are visited.  Rows of
+// more than one chunk OR their chunk bitmaps into a global bitmap that a
+// second kernel reads back.  The member order inside a cluster (atomics)
+// does not matter: a bitmap is a set.
+constexpr int kChunk = 4096;
+constexpr int kRowThreads = 128;
+constexpr int kListCap = 4096;  // nonzero words per summary group of kRowThreads words
+constexpr int64_t kBitmapMaxDefault = int64_t(1) << 19;
+
+__global__ void cluster_sizes(const int64_t *__restrict__ rowptr, int64_t n, const int32_t *__restrict__ map,
+                              int32_t *__restrict__ csize) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (rowptr[v + 1] > rowptr[v]) atomicAdd(csize + map[v], 1);
+}
+
+__global__ void place_members(const int64_t *__restrict__ rowptr, int64_t n, const int32_t *__restrict__ map,
+                              const int64_t *__restrict__ cstart, int32_t *__restrict__ fill,
+                              int64_t *__restrict__ mrow, int64_t *__restrict__ mdeg) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t deg = rowptr[v + 1] - rowptr[v];
+        if (deg == 0) continue;
+        const int32_t c = map[v];
+        const int64_t j = cstart[c] + atomicAdd(fill + c, 1);
+        mrow[j] = rowptr[v];
+        mdeg[j] = deg;
+    }
+}
+
+__global__ void row_chunks(const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff, int64_t nc,
+                           int32_t *__restrict__ nchunk, uint8_t *__restrict__ multi) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = moff[cstart[c + 1]] - moff[cstart[c]];
+        const int64_t k = (len + kChunk - 1) / kChunk;
+        nchunk[c] = (int32_t)k;
+        multi[c] = k > 1 ? 1 : 0;
+    }
+}
+
+__global__ void chunk_rows(const int64_t *__restrict__ chunk_start, const uint8_t *__restrict__ multi,
+                           const int64_t *__restrict__ slot, int64_t nc, int32_t *__restrict__ chunk_row,
+                           int32_t *__restrict__ slot_row) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t t = chunk_start[c]; t < chunk_start[c + 1]; ++t) chunk_row[t] = (int32_t)c;
+        if (multi[c]) slot_row[slot[c]] = (int32_t)c;
+    }
+}
+
+// Exclusive prefix sum over the block (kRowThreads threads); every thread
+// gets the block total.  wsum: kRowThreads / 32 shared ints.
+__device__ __forceinline__ int block_scan(int x, int *wsum, int &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int off = 0;
+    total = 0;
+#pragma unroll
+    for (int i = 0; i < kRowThreads / 32; ++i) {
+        const int t = wsum[i];
+        off += i < w ? t : 0;
+        total += t;
+    }
+    __syncthreads();
+    return off + incl - x;
+}
+
+// Writes the set bits of bm (its nonzero words flagged in sum, n0 summary
+// words) in ascending order to out and returns their number (in every
+// thread).  kClear: zero the visited words (shared-memory bitmaps are reused).
+template <bool kClear>
+__device__ int read_bits(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int *wsum, int32_t *__restrict__ out) {
+    int nout = 0;
+    for (int s0 = 0; s0 < n0; s0 += kRowThreads) {
+        const int s = s0 + threadIdx.x;
+        uint32_t sw = s < n0 ? sum[s] : 0u;
+        if (kClear && s < n0) sum[s] = 0;
+        int nlist;
+        int k = block_scan(__popc(sw), wsum, nlist);
+        while (sw) {
+            list[k++] = s * 32 + (__ffs(sw) - 1);
+            sw &= sw - 1;
+        }
+        __syncthreads();
+        for (int i0 = 0; i0 < nlist; i0 += kRowThreads) {
+            const int i = i0 + threadIdx.x;
+            int w = 0;
+            uint32_t bits = 0;
+            if (i < nlist) {
+                w = list[i];
+                bits = bm[w];
+                if (kClear) bm[w] = 0;
+            }
+            int tot;
+            int at = nout + block_scan(__popc(bits), wsum, tot);
+            while (bits) {
+                out[at++] = w * 32 + (__ffs(bits) - 1);
+                bits &= bits - 1;
+            }
+            nout += tot;
+        }
+    }
+    return nout;
+}
+
+// Last member j in [lo, hi) with moff[j] <= p (moff ascending, moff[lo] <= p).
+__device__ __forceinline__ int64_t member_of(const int64_t *__restrict__ moff, int64_t lo, int64_t hi, int64_t p) {
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(moff + mid) <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kRowThreads) coarse_rows(
+    const int32_t *__restrict__ col, const int32_t *__restrict__ map, const int64_t *__restrict__ cstart,
+    const int64_t *__restrict__ mrow, const int64_t *__restrict__ moff, const int64_t *__restrict__ chunk_start,
+    const int32_t *__restrict__ chunk_row, const uint8_t *__restrict__ multi, const int64_t *__restrict__ slot,
+    int64_t nchunks, int words, int n0, int list_cap, uint32_t *__restrict__ gbm, uint32_t *__restrict__ gsum,
+    int32_t *__restrict__ scratch, int32_t *__restrict__ count) {
+    extern __shared__ uint32_t smem[];
+    uint32_t *bm = smem;
+    uint32_t *sum = bm + words;
+    int32_t *list = reinterpret_cast<int32_t *>(sum + n0);
+    int *wsum = reinterpret_cast<int *>(list + list_cap);
+    for (int i = threadIdx.x; i < words + n0; i += kRowThreads) smem[i] = 0;
+    __syncthreads();
+    for (int64_t t = blockIdx.x; t < nchunks; t += gridDim.x) {
+        const int32_t c = chunk_row[t];
+        const int64_t jlo = cstart[c], jhi = cstart[c + 1];
+        const int64_t rb = moff[jlo], re = moff[jhi];
+        const int64_t e0 = rb + (t - chunk_start[c]) * kChunk;
+        const int64_t e1 = e0 + kChunk < re ? e0 + kChunk : re;
+        int64_t j = -1;
+        for (int64_t p = e0 + threadIdx.x; p < e1; p += kRowThreads) {
+            if (j < 0) j = member_of(moff, jlo, jhi, p);
+            else if (__ldg(moff + j + 1) <= p) j = member_of(moff, j + 1, jhi, p);
+            const int32_t y = __ldg(col + __ldg(mrow + j) + (p - __ldg(moff + j)));
+            const int32_t b = __ldg(map + y);
+            if (b == c) continue;
+            const uint32_t old = atomicOr(bm + (b >> 5), 1u << (b & 31));
+            if (old == 0) atomicOr(sum + (b >> 10), 1u << ((b >> 5) & 31));
+        }
+        __syncthreads();
+        if (!multi[c]) {
+            const int m = read_bits<true>(bm, sum, n0, list, wsum, scratch + rb);
+            if (threadIdx.x == 0) count[c] = m;
+        } else {
+            // OR the touched words into row c's global bitmap and clear them here
+            const int64_t g = slot[c];
+            uint32_t *gb = gbm + g * words;
+            uint32_t *gs = gsum + g * n0;
+            for (int s = threadIdx.x; s < n0; s += kRowThreads) {
+                uint32_t sw = sum[s];
+                if (!sw) continue;
+                atomicOr(gs + s, sw);
+                sum[s] = 0;
+                while (sw) {
+                    const int w = s * 32 + (__ffs(sw) - 1);
+                    sw &= sw - 1;
+                    atomicOr(gb + w, bm[w]);
+                    bm[w] = 0;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Rows of more than one chunk: read their global bitmaps back.
+__global__ void __launch_bounds__(kRowThreads) coarse_rows_multi(
+    const int32_t *__restrict__ slot_row, int64_t nslots, const int64_t *__restrict__ cstart,
+    const int64_t *__restrict__ moff, int words, int n0, uint32_t *gbm, uint32_t *gsum,
+    int32_t *__restrict__ scratch, int32_t *__restrict__ count) {
+    __shared__ int32_t list[kListCap];
+    __shared__ int wsum[kRowThreads / 32];
+    for (int64_t g = blockIdx.x; g < nslots; g += gridDim.x) {
+        const int32_t c = slot_row[g];
+        const int m = read_bits<false>(gbm + g * words, gsum + g * n0, n0, list, wsum, scratch + moff[cstart[c]]);
+        if (threadIdx.x == 0) count[c] = m;
+        __syncthreads();
+    }
+}
+
+// Row c of the coarse CSR from its sorted ids in scratch; one warp per row.
+__global__ void compact_rows(const int32_t *__restrict__ scratch, const int64_t *__restrict__ cstart,
+                             const int64_t *__restrict__ moff, const int64_t *__restrict__ rowptr, int64_t nc,
+                             int32_t *__restrict__ col_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = wid; c < nc; c += wstride) {
+        const int32_t *src = scratch + moff[cstart[c]];
+        int32_t *dst = col_out + rowptr[c];
+        const int64_t len = rowptr[c + 1] - rowptr[c];
+        for (int64_t i = lane; i < len; i += 32) dst[i] = src[i];
+    }
+}
+
 int grid_1d(int64_t n, int threads = 256) {
     const int64_t cap = (int64_t)num_sms() * 16;
     const int64_t g = ceil_div(n > 0 ? n : 1, threads);
@@ -207,6 +422,129 @@ int bits_for(uint64_t x) {
     int b = 0;
     while (b < 64 && (uint64_t(1) << b) <= x) ++b;
     return b < 1 ? 1 : b;
+}
+
+// Largest coarse vertex count for the bitmap construction (its shared-memory
+// bitmap has nc bits); GOSH_COARSEN_BITMAP_MAX overrides it (0: always sort).
+int64_t bitmap_limit() {
+    const char *e = getenv("GOSH_COARSEN_BITMAP_MAX");
+    if (e && *e) {
+        const long long v = atoll(e);
+        return v < kBitmapMaxDefault ? (int64_t)v : kBitmapMaxDefault;
+    }
+    return kBitmapMaxDefault;
+}
+
+// Coarse CSR by sorting the packed edge keys (map v * nc + map u) of all entries.
+gosh_status coarse_graph_sorted(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *map, int64_t nc,
+                                int64_t nnz, int64_t *rp, int32_t **co_out, int64_t *m_out, cudaStream_t s) {
+    Scratch ek, fl, pos;
+    GOSH_TRY(ek.alloc(sizeof(uint64_t) * nnz, s));
+    GOSH_TRY(fl.alloc(nnz, s));
+    GOSH_TRY(pos.alloc(sizeof(int64_t) * (nnz + 1), s));
+    const uint64_t unc = (uint64_t)nc;
+    const uint64_t sentinel = unc * unc;
+    (edge_image<<<grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s>>>(rowptr, col, n, map, unc,
+                                                                             ek.as<uint64_t>()),
+     note_launch());
+    int shifts[8];
+    int nd = 0;
+    const int kb = bits_for(sentinel);
+    for (int b = 0; b < kb && nd < 8; b += 8) shifts[nd++] = b;
+    GOSH_TRY(radix_sort_u64(ek.as<uint64_t>(), nullptr, nnz, shifts, nd, s));
+    (unique_flags<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), nnz, sentinel, fl.as<uint8_t>()), note_launch());
+    GOSH_TRY(scan_exclusive_u8_to_i64(fl.as<uint8_t>(), pos.as<int64_t>(), nnz, pos.as<int64_t>() + nnz, s));
+    int64_t m = 0;
+    GOSH_TRY_CUDA(cudaMemcpyAsync(&m, pos.as<int64_t>() + nnz, sizeof(m), cudaMemcpyDeviceToHost, s));
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
+    GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
+    (write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz,
+                                               sentinel, nc, *co_out, rp), note_launch());
+    *m_out = m;
+    return GOSH_OK;
+}
+
+// Coarse CSR through per-row bitmaps (coarse_rows); nc <= bitmap_limit().
+gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *map, int64_t nc,
+                                int64_t nnz, int64_t *rp, int32_t **co_out, int64_t *m_out, cudaStream_t s) {
+    const int words = (int)ceil_div(nc, 32);
+    const int n0 = (int)ceil_div(words, 32);
+    const int list_cap = words < kListCap ? words : kListCap;
+    Scratch csize, cstart, fill, mrow, mdeg, moff, nchunk, multi, cstart_k, slot;
+    GOSH_TRY(csize.alloc(sizeof(int32_t) * nc, s));
+    GOSH_TRY(cstart.alloc(sizeof(int64_t) * (nc + 1), s));
+    GOSH_TRY(fill.alloc(sizeof(int32_t) * nc, s));
+    GOSH_TRY(mrow.alloc(sizeof(int64_t) * n, s));
+    GOSH_TRY(mdeg.alloc(sizeof(int64_t) * n, s));
+    GOSH_TRY(moff.alloc(sizeof(int64_t) * (n + 1), s));
+    GOSH_TRY(nchunk.alloc(sizeof(int32_t) * nc, s));
+    GOSH_TRY(multi.alloc(nc, s));
+    GOSH_TRY(cstart_k.alloc(sizeof(int64_t) * (nc + 1), s));
+    GOSH_TRY(slot.alloc(sizeof(int64_t) * (nc + 1), s));
+    GOSH_TRY_CUDA(cudaMemsetAsync(csize.ptr, 0, sizeof(int32_t) * nc, s));
+    GOSH_TRY_CUDA(cudaMemsetAsync(fill.ptr, 0, sizeof(int32_t) * nc, s));
+    GOSH_TRY_CUDA(cudaMemsetAsync(mdeg.ptr, 0, sizeof(int64_t) * n, s));
+    (cluster_sizes<<<grid_1d(n), 256, 0, s>>>(rowptr, n, map, csize.as<int32_t>()), note_launch());
+    GOSH_TRY(scan_exclusive_i32_to_i64(csize.as<int32_t>(), cstart.as<int64_t>(), nc, cstart.as<int64_t>() + nc, s));
+    (place_members<<<grid_1d(n), 256, 0, s>>>(rowptr, n, map, cstart.as<int64_t>(), fill.as<int32_t>(),
+                                              mrow.as<int64_t>(), mdeg.as<int64_t>()), note_launch());
+    GOSH_TRY(scan_exclusive_i64(mdeg.as<int64_t>(), moff.as<int64_t>(), n, moff.as<int64_t>() + n, s));
+    (row_chunks<<<grid_1d(nc), 256, 0, s>>>(cstart.as<int64_t>(), moff.as<int64_t>(), nc, nchunk.as<int32_t>(),
+                                           multi.as<uint8_t>()), note_launch());
+    GOSH_TRY(scan_exclusive_i32_to_i64(nchunk.as<int32_t>(), cstart_k.as<int64_t>(), nc, cstart_k.as<int64_t>() + nc, s));
+    GOSH_TRY(scan_exclusive_u8_to_i64(multi.as<uint8_t>(), slot.as<int64_t>(), nc, slot.as<int64_t>() + nc, s));
+    int64_t totals[2] = {0, 0};
+    GOSH_TRY_CUDA(cudaMemcpyAsync(totals, cstart_k.as<int64_t>() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GOSH_TRY_CUDA(cudaMemcpyAsync(totals + 1, slot.as<int64_t>() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t nchunks = totals[0], nslots = totals[1];
+    Scratch chunk_row, slot_row, gbm, gsum, scratch, count;
+    GOSH_TRY(chunk_row.alloc(sizeof(int32_t) * nchunks, s));
+    GOSH_TRY(slot_row.alloc(sizeof(int32_t) * nslots, s));
+    GOSH_TRY(gbm.alloc(sizeof(uint32_t) * nslots * words, s));
+    GOSH_TRY(gsum.alloc(sizeof(uint32_t) * nslots * n0, s));
+    GOSH_TRY(scratch.alloc(sizeof(int32_t) * nnz, s));
+    GOSH_TRY(count.alloc(sizeof(int32_t) * nc, s));
+    if (nslots > 0) {
+        GOSH_TRY_CUDA(cudaMemsetAsync(gbm.ptr, 0, sizeof(uint32_t) * nslots * words, s));
+        GOSH_TRY_CUDA(cudaMemsetAsync(gsum.ptr, 0, sizeof(uint32_t) * nslots * n0, s));
+    }
+    GOSH_TRY_CUDA(cudaMemsetAsync(count.ptr, 0, sizeof(int32_t) * nc, s));
+    (chunk_rows<<<grid_1d(nc), 256, 0, s>>>(cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nc,
+                                           chunk_row.as<int32_t>(), slot_row.as<int32_t>()), note_launch());
+    if (nchunks > 0) {
+        const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap) + sizeof(int) * (kRowThreads / 32);
+        GOSH_TRY_CUDA(cudaFuncSetAttribute(coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        GOSH_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_rows, kRowThreads, smem));
+        if (per_sm < 1) per_sm = 1;
+        const int64_t cap = (int64_t)num_sms() * per_sm;
+        const int grid = (int)(nchunks < cap ? nchunks : cap);
+        (coarse_rows<<<grid, kRowThreads, smem, s>>>(col, map, cstart.as<int64_t>(), mrow.as<int64_t>(),
+                                                    moff.as<int64_t>(), cstart_k.as<int64_t>(),
+                                                    chunk_row.as<int32_t>(), multi.as<uint8_t>(),
+                                                    slot.as<int64_t>(), nchunks, words, n0, list_cap,
+                                                    gbm.as<uint32_t>(), gsum.as<uint32_t>(), scratch.as<int32_t>(),
+                                                    count.as<int32_t>()),
+         note_launch());
+    }
+    if (nslots > 0) {
+        const int64_t cap = (int64_t)num_sms() * 8;
+        (coarse_rows_multi<<<(int)(nslots < cap ? nslots : cap), kRowThreads, 0, s>>>(
+             slot_row.as<int32_t>(), nslots, cstart.as<int64_t>(), moff.as<int64_t>(), words, n0,
+             gbm.as<uint32_t>(), gsum.as<uint32_t>(), scratch.as<int32_t>(), count.as<int32_t>()),
+         note_launch());
+    }
+    GOSH_TRY(scan_exclusive_i32_to_i64(count.as<int32_t>(), rp, nc, rp + nc, s));
+    int64_t m = 0;
+    GOSH_TRY_CUDA(cudaMemcpyAsync(&m, rp + nc, sizeof(m), cudaMemcpyDeviceToHost, s));
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
+    (compact_rows<<<grid_warps(nc), 256, 0, s>>>(scratch.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(), rp,
+                                                 nc, *co_out), note_launch());
+    *m_out = m;
+    return GOSH_OK;
 }
 
 }  // namespace
@@ -281,29 +619,10 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     // hierarchy buffers come from the stream-ordered pool (no device-wide sync)
     GOSH_TRY_CUDA(cudaMallocAsync(&rp, sizeof(int64_t) * (nc + 1), s));
     int64_t m = 0;
-    if (nnz > 0) {
-        Scratch ek, fl, pos;
-        GOSH_TRY(ek.alloc(sizeof(uint64_t) * nnz, s));
-        GOSH_TRY(fl.alloc(nnz, s));
-        GOSH_TRY(pos.alloc(sizeof(int64_t) * (nnz + 1), s));
-        const uint64_t unc = (uint64_t)nc;
-        const uint64_t sentinel = unc * unc;
-        (edge_image<<<grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s>>>(rowptr, col, n, map, unc,
-                                                                                 ek.as<uint64_t>()),
-         note_launch());
-        int shifts[8];
-        int nd = 0;
-        const int kb = bits_for(sentinel);
-        for (int b = 0; b < kb && nd < 8; b += 8) shifts[nd++] = b;
-        GOSH_TRY(radix_sort_u64(ek.as<uint64_t>(), nullptr, nnz, shifts, nd, s));
-        (unique_flags<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), nnz, sentinel, fl.as<uint8_t>()), note_launch());
-        GOSH_TRY(scan_exclusive_u8_to_i64(fl.as<uint8_t>(), pos.as<int64_t>(), nnz, pos.as<int64_t>() + nnz, s));
-        GOSH_TRY_CUDA(cudaMemcpyAsync(&m, pos.as<int64_t>() + nnz, sizeof(m), cudaMemcpyDeviceToHost, s));
-        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
-        GOSH_TRY_CUDA(cudaMallocAsync(&co, sizeof(int32_t) * (m > 0 ? m : 1), s));
-        GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
-        (write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz,
-                                                   sentinel, nc, co, rp), note_launch());
+    if (nnz > 0 && nc <= bitmap_limit()) {
+        GOSH_TRY(coarse_graph_bitmap(n, rowptr, col, map, nc, nnz, rp, &co, &m, s));
+    } else if (nnz > 0) {
+        GOSH_TRY(coarse_graph_sorted(n, rowptr, col, map, nc, nnz, rp, &co, &m, s));
     } else {
         GOSH_TRY_CUDA(cudaMallocAsync(&co, sizeof(int32_t), s));
         GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));

@@ -78,6 +78,29 @@ def test_coarsen_rmat_bit_exact(g, scale, ef, seed):
     check_hierarchy(g, gr.rowptr, gr.col)
 
 
+@pytest.mark.parametrize("bitmap_max", ["0", "2000"])
+def test_coarsen_sorted_path_bit_exact(g, monkeypatch, bitmap_max):
+    # coarse graphs with more vertices than the bitmap limit are built by a
+    # radix sort of packed edge keys; lowering the limit runs that path on
+    # every level ("0") or on the wide first levels only ("2000")
+    monkeypatch.setenv("GOSH_COARSEN_BITMAP_MAX", bitmap_max)
+    gr = synth.rmat_graph(14, 8, 5)
+    assert check_hierarchy(g, gr.rowptr, gr.col) >= 3
+
+
+def test_coarsen_multi_chunk_rows(g):
+    # two hubs with 6000 leaves each plus leaf-leaf edges across them: each
+    # hub's cluster row spans several 4096-entry chunks (global bitmap path)
+    rng = np.random.default_rng(9)
+    leaves = 6000
+    a = np.arange(2, 2 + leaves)
+    b = np.arange(2 + leaves, 2 + 2 * leaves)
+    s = np.concatenate([np.zeros(leaves, np.int64), np.ones(leaves, np.int64), rng.choice(a, 3000)])
+    t = np.concatenate([a, b, rng.choice(b, 3000)])
+    gr = synth.csr_from_edges(2 + 2 * leaves, s, t, compact=False)
+    check_hierarchy(g, gr.rowptr, gr.col, threshold=1)
+
+
 def test_coarsen_edge_cases(g):
     # no edges at all: every vertex is its own cluster, one level added
     check_hierarchy(g, np.zeros(6, dtype=np.int64), np.zeros(0, dtype=np.int32))
