@@ -33,11 +33,13 @@ enum : uint8_t { kUndecided = 0, kHub = 1, kNonHub = 2 };
 
 __device__ __forceinline__ bool small_deg(int64_t deg, int64_t n, int64_t nnz) { return deg * n <= nnz; }
 
+// Key (n - 1) - deg (a simple graph has deg <= n - 1): ascending keys are
+// descending degrees, and the sort needs only the bits of n - 1.
 __global__ void degree_keys(const int64_t *__restrict__ rowptr, int64_t n, uint32_t *__restrict__ key,
                             uint32_t *__restrict__ val) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t deg = rowptr[v + 1] - rowptr[v];
-        key[v] = 0xffffffffu - (uint32_t)deg;
+        key[v] = deg < n ? (uint32_t)(n - 1 - deg) : 0u;
         val[v] = (uint32_t)v;
     }
 }
@@ -109,6 +111,31 @@ __global__ void attach_to_hub(const int64_t *__restrict__ rowptr, const int32_t 
             if (state[u] == kHub) best = min(best, __ldg(rank + u));
         }
         hub_rank[v] = best;
+    }
+}
+
+// The same with one warp per vertex, for dense levels (non-hub rows are up to
+// the average degree long, hundreds of entries on the small levels).
+__global__ void __launch_bounds__(256) attach_to_hub_warp(const int64_t *__restrict__ rowptr,
+                                                          const int32_t *__restrict__ col, int64_t n,
+                                                          const int32_t *__restrict__ rank,
+                                                          const uint8_t *__restrict__ state,
+                                                          int32_t *__restrict__ hub_rank) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = wid; v < n; v += wstride) {
+        if (state[v] == kHub) {
+            if (lane == 0) hub_rank[v] = rank[v];
+            continue;
+        }
+        int32_t best = 0x7fffffff;
+        for (int64_t p = rowptr[v] + lane, e = rowptr[v + 1]; p < e; p += 32) {
+            const int32_t u = __ldg(col + p);
+            if (state[u] == kHub) best = min(best, __ldg(rank + u));
+        }
+        best = __reduce_min_sync(0xffffffffu, best);
+        if (lane == 0) hub_rank[v] = best;
     }
 }
 
@@ -209,32 +236,46 @@ __global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *_
 // does not matter: a bitmap is a set.
 constexpr int kChunk = 4096;
 constexpr int kRowThreads = 128;
-constexpr int kListCap = 4096;  // nonzero words per summary group of kRowThreads words
+constexpr int kRowWarps = kRowThreads / 32;
+constexpr int kSumGroup = 32;                // summary words read back per step
+constexpr int kListCap = kSumGroup * 32;     // nonzero bitmap words per step
 constexpr int64_t kBitmapMaxDefault = int64_t(1) << 19;
 
-__global__ void cluster_sizes(const int64_t *__restrict__ rowptr, int64_t n, const int32_t *__restrict__ map,
-                              int32_t *__restrict__ csize) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        if (rowptr[v + 1] > rowptr[v]) atomicAdd(csize + map[v], 1);
+// Sort key of vertex v for grouping the members by cluster: map[v], or nc for
+// a vertex without neighbours (it adds no entries and sorts past every cluster).
+__global__ void member_keys(const int64_t *__restrict__ rowptr, int64_t n, const int32_t *__restrict__ map,
+                            uint32_t nc, uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        key[v] = rowptr[v + 1] > rowptr[v] ? (uint32_t)map[v] : nc;
+        val[v] = (uint32_t)v;
+    }
 }
 
-__global__ void place_members(const int64_t *__restrict__ rowptr, int64_t n, const int32_t *__restrict__ map,
-                              const int64_t *__restrict__ cstart, int32_t *__restrict__ fill,
-                              int64_t *__restrict__ mrow, int64_t *__restrict__ mdeg) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t deg = rowptr[v + 1] - rowptr[v];
-        if (deg == 0) continue;
-        const int32_t c = map[v];
-        const int64_t j = cstart[c] + atomicAdd(fill + c, 1);
-        mrow[j] = rowptr[v];
-        mdeg[j] = deg;
+// From the members sorted by cluster: cstart[c] = first member of cluster c
+// (cstart[nc] = number of members with neighbours), each member's row start
+// and degree.  A position whose key differs from its predecessor's writes the
+// starts of every cluster in between (clusters without such members are empty).
+__global__ void member_layout(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
+                              const int64_t *__restrict__ rowptr, int64_t n, uint32_t nc,
+                              int64_t *__restrict__ cstart, int64_t *__restrict__ mrow, int64_t *__restrict__ mdeg) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = val[i];
+        const int64_t k = key[i];
+        mrow[i] = rowptr[v];
+        mdeg[i] = rowptr[v + 1] - rowptr[v];
+        const int64_t kp = i == 0 ? -1 : (int64_t)key[i - 1];
+        for (int64_t c = kp + 1; c <= k; ++c) cstart[c] = i;
+        if (i == n - 1)
+            for (int64_t c = k + 1; c <= (int64_t)nc; ++c) cstart[c] = n;
     }
 }
 
 __global__ void row_chunks(const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff, int64_t nc,
-                           int32_t *__restrict__ nchunk, uint8_t *__restrict__ multi) {
+                           int32_t *__restrict__ nchunk, uint8_t *__restrict__ multi, int64_t *__restrict__ rbase) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t len = moff[cstart[c + 1]] - moff[cstart[c]];
+        const int64_t rb = moff[cstart[c]];
+        rbase[c] = rb;
+        const int64_t len = moff[cstart[c + 1]] - rb;
         const int64_t k = (len + kChunk - 1) / kChunk;
         nchunk[c] = (int32_t)k;
         multi[c] = k > 1 ? 1 : 0;
@@ -280,10 +321,11 @@ __device__ __forceinline__ int block_scan(int x, int *wsum, int &total) {
 template <bool kClear>
 __device__ int read_bits(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int *wsum, int32_t *__restrict__ out) {
     int nout = 0;
-    for (int s0 = 0; s0 < n0; s0 += kRowThreads) {
+    for (int s0 = 0; s0 < n0; s0 += kSumGroup) {
         const int s = s0 + threadIdx.x;
-        uint32_t sw = s < n0 ? sum[s] : 0u;
-        if (kClear && s < n0) sum[s] = 0;
+        const bool mine = threadIdx.x < kSumGroup && s < n0;
+        uint32_t sw = mine ? sum[s] : 0u;
+        if (kClear && mine) sum[s] = 0;
         int nlist;
         int k = block_scan(__popc(sw), wsum, nlist);
         while (sw) {
@@ -312,6 +354,8 @@ __device__ int read_bits(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int
     return nout;
 }
 
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
 // Last member j in [lo, hi) with moff[j] <= p (moff ascending, moff[lo] <= p).
 __device__ __forceinline__ int64_t member_of(const int64_t *__restrict__ moff, int64_t lo, int64_t hi, int64_t p) {
     while (hi - lo > 1) {
@@ -332,6 +376,7 @@ __global__ void __launch_bounds__(kRowThreads) coarse_rows(
     uint32_t *sum = bm + words;
     int32_t *list = reinterpret_cast<int32_t *>(sum + n0);
     int *wsum = reinterpret_cast<int *>(list + list_cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < words + n0; i += kRowThreads) smem[i] = 0;
     __syncthreads();
     for (int64_t t = blockIdx.x; t < nchunks; t += gridDim.x) {
@@ -340,15 +385,33 @@ __global__ void __launch_bounds__(kRowThreads) coarse_rows(
         const int64_t rb = moff[jlo], re = moff[jhi];
         const int64_t e0 = rb + (t - chunk_start[c]) * kChunk;
         const int64_t e1 = e0 + kChunk < re ? e0 + kChunk : re;
-        int64_t j = -1;
-        for (int64_t p = e0 + threadIdx.x; p < e1; p += kRowThreads) {
-            if (j < 0) j = member_of(moff, jlo, jhi, p);
-            else if (__ldg(moff + j + 1) <= p) j = member_of(moff, j + 1, jhi, p);
-            const int32_t y = __ldg(col + __ldg(mrow + j) + (p - __ldg(moff + j)));
-            const int32_t b = __ldg(map + y);
-            if (b == c) continue;
-            const uint32_t old = atomicOr(bm + (b >> 5), 1u << (b & 31));
-            if (old == 0) atomicOr(sum + (b >> 10), 1u << ((b >> 5) & 31));
+        // Warp w takes a contiguous quarter of the chunk, 32 entries per step.
+        // The members of a step's entries follow from the next 32 member
+        // boundaries (one coalesced load; boundaries are distinct because
+        // every member has an entry): lane L's entry lies in member
+        // j0 + #{boundaries <= base + L}.
+        const int64_t per = ceil_div_dev(e1 - e0, (int64_t)kRowWarps * 32) * 32;
+        int64_t base = e0 + warp * per;
+        const int64_t wend = base + per < e1 ? base + per : e1;
+        if (base < wend) {
+            int64_t j0 = member_of(moff, jlo, jhi, base);
+            for (; base < wend; base += 32) {
+                const int64_t jb = j0 + 1 + lane;
+                const int64_t r = jb <= jhi ? __ldg(moff + jb) - base : 64;
+                const uint32_t starts = __reduce_or_sync(0xffffffffu, r < 32 ? 1u << r : 0u);
+                const bool next32 = __any_sync(0xffffffffu, r == 32);
+                const int64_t p = base + lane;
+                if (p < wend) {
+                    const int64_t j = j0 + __popc(starts & ((2u << lane) - 1u));
+                    const int32_t y = __ldg(col + __ldg(mrow + j) + (p - __ldg(moff + j)));
+                    const int32_t b = __ldg(map + y);
+                    if (b != c) {
+                        const uint32_t old = atomicOr(bm + (b >> 5), 1u << (b & 31));
+                        if (old == 0) atomicOr(sum + (b >> 10), 1u << ((b >> 5) & 31));
+                    }
+                }
+                j0 += __popc(starts) + (next32 ? 1 : 0);
+            }
         }
         __syncthreads();
         if (!multi[c]) {
@@ -378,31 +441,61 @@ __global__ void __launch_bounds__(kRowThreads) coarse_rows(
 
 // Rows of more than one chunk: read their global bitmaps back.
 __global__ void __launch_bounds__(kRowThreads) coarse_rows_multi(
-    const int32_t *__restrict__ slot_row, int64_t nslots, const int64_t *__restrict__ cstart,
-    const int64_t *__restrict__ moff, int words, int n0, uint32_t *gbm, uint32_t *gsum,
-    int32_t *__restrict__ scratch, int32_t *__restrict__ count) {
+    const int32_t *__restrict__ slot_row, int64_t nslots, const int64_t *__restrict__ rbase, int words, int n0,
+    uint32_t *gbm, uint32_t *gsum, int32_t *__restrict__ scratch, int32_t *__restrict__ count) {
     __shared__ int32_t list[kListCap];
     __shared__ int wsum[kRowThreads / 32];
     for (int64_t g = blockIdx.x; g < nslots; g += gridDim.x) {
         const int32_t c = slot_row[g];
-        const int m = read_bits<false>(gbm + g * words, gsum + g * n0, n0, list, wsum, scratch + moff[cstart[c]]);
+        const int m = read_bits<false>(gbm + g * words, gsum + g * n0, n0, list, wsum, scratch + rbase[c]);
         if (threadIdx.x == 0) count[c] = m;
         __syncthreads();
     }
 }
 
-// Row c of the coarse CSR from its sorted ids in scratch; one warp per row.
-__global__ void compact_rows(const int32_t *__restrict__ scratch, const int64_t *__restrict__ cstart,
-                             const int64_t *__restrict__ moff, const int64_t *__restrict__ rowptr, int64_t nc,
-                             int32_t *__restrict__ col_out) {
+// Coarse CSR entry q of row r is scratch[rbase[r] + q - rowptr[r]].  Balanced
+// over entries: each warp takes 1024 consecutive entries; a lane finds the
+// row of its first entry by binary search and then walks forward.
+__global__ void __launch_bounds__(256) compact_rows(const int32_t *__restrict__ scratch,
+                                                    const int64_t *__restrict__ rbase,
+                                                    const int64_t *__restrict__ rowptr, int64_t nc,
+                                                    int32_t *__restrict__ col_out) {
     const int lane = threadIdx.x & 31;
+    const int64_t m = rowptr[nc];
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = wid; c < nc; c += wstride) {
-        const int32_t *src = scratch + moff[cstart[c]];
-        int32_t *dst = col_out + rowptr[c];
-        const int64_t len = rowptr[c + 1] - rowptr[c];
-        for (int64_t i = lane; i < len; i += 32) dst[i] = src[i];
+    for (int64_t base = wid * kEntriesPerWarp; base < m; base += wstride * kEntriesPerWarp) {
+        int64_t q = base + lane;
+        if (q >= m) continue;
+        int64_t lo = 0, hi = nc;  // last row with rowptr[row] <= q
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(rowptr + mid) <= q) lo = mid; else hi = mid;
+        }
+        int64_t r = lo;
+        int64_t rend = __ldg(rowptr + r + 1);
+        int64_t shift = __ldg(rbase + r) - __ldg(rowptr + r);
+        const int64_t end = base + kEntriesPerWarp < m ? base + kEntriesPerWarp : m;
+        // four entries per lane per step, their loads issued together
+        for (; q < end; q += 128) {
+            int64_t src[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t qu = q + 32 * u;
+                while (qu < end && rend <= qu) {
+                    ++r;
+                    rend = __ldg(rowptr + r + 1);
+                    shift = __ldg(rbase + r) - __ldg(rowptr + r);
+                }
+                src[u] = qu + shift;
+            }
+            int32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = q + 32 * u < end ? __ldg(scratch + src[u]) : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q + 32 * u < end) col_out[q + 32 * u] = v[u];
+        }
     }
 }
 
@@ -471,27 +564,28 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     const int words = (int)ceil_div(nc, 32);
     const int n0 = (int)ceil_div(words, 32);
     const int list_cap = words < kListCap ? words : kListCap;
-    Scratch csize, cstart, fill, mrow, mdeg, moff, nchunk, multi, cstart_k, slot;
-    GOSH_TRY(csize.alloc(sizeof(int32_t) * nc, s));
+    Scratch mkey, mval, cstart, mrow, mdeg, moff, nchunk, multi, rbase, cstart_k, slot;
+    GOSH_TRY(mkey.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(mval.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(cstart.alloc(sizeof(int64_t) * (nc + 1), s));
-    GOSH_TRY(fill.alloc(sizeof(int32_t) * nc, s));
     GOSH_TRY(mrow.alloc(sizeof(int64_t) * n, s));
     GOSH_TRY(mdeg.alloc(sizeof(int64_t) * n, s));
     GOSH_TRY(moff.alloc(sizeof(int64_t) * (n + 1), s));
     GOSH_TRY(nchunk.alloc(sizeof(int32_t) * nc, s));
     GOSH_TRY(multi.alloc(nc, s));
+    GOSH_TRY(rbase.alloc(sizeof(int64_t) * nc, s));
     GOSH_TRY(cstart_k.alloc(sizeof(int64_t) * (nc + 1), s));
     GOSH_TRY(slot.alloc(sizeof(int64_t) * (nc + 1), s));
-    GOSH_TRY_CUDA(cudaMemsetAsync(csize.ptr, 0, sizeof(int32_t) * nc, s));
-    GOSH_TRY_CUDA(cudaMemsetAsync(fill.ptr, 0, sizeof(int32_t) * nc, s));
-    GOSH_TRY_CUDA(cudaMemsetAsync(mdeg.ptr, 0, sizeof(int64_t) * n, s));
-    (cluster_sizes<<<grid_1d(n), 256, 0, s>>>(rowptr, n, map, csize.as<int32_t>()), note_launch());
-    GOSH_TRY(scan_exclusive_i32_to_i64(csize.as<int32_t>(), cstart.as<int64_t>(), nc, cstart.as<int64_t>() + nc, s));
-    (place_members<<<grid_1d(n), 256, 0, s>>>(rowptr, n, map, cstart.as<int64_t>(), fill.as<int32_t>(),
-                                              mrow.as<int64_t>(), mdeg.as<int64_t>()), note_launch());
+    // members grouped by cluster (stable: ascending ids inside a cluster)
+    (member_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, map, (uint32_t)nc, mkey.as<uint32_t>(), mval.as<uint32_t>()),
+     note_launch());
+    GOSH_TRY(radix_sort_u32(mkey.as<uint32_t>(), mval.as<uint32_t>(), n, 0, bits_for((uint64_t)nc), s));
+    (member_layout<<<grid_1d(n), 256, 0, s>>>(mkey.as<uint32_t>(), mval.as<uint32_t>(), rowptr, n, (uint32_t)nc,
+                                              cstart.as<int64_t>(), mrow.as<int64_t>(), mdeg.as<int64_t>()),
+     note_launch());
     GOSH_TRY(scan_exclusive_i64(mdeg.as<int64_t>(), moff.as<int64_t>(), n, moff.as<int64_t>() + n, s));
     (row_chunks<<<grid_1d(nc), 256, 0, s>>>(cstart.as<int64_t>(), moff.as<int64_t>(), nc, nchunk.as<int32_t>(),
-                                           multi.as<uint8_t>()), note_launch());
+                                           multi.as<uint8_t>(), rbase.as<int64_t>()), note_launch());
     GOSH_TRY(scan_exclusive_i32_to_i64(nchunk.as<int32_t>(), cstart_k.as<int64_t>(), nc, cstart_k.as<int64_t>() + nc, s));
     GOSH_TRY(scan_exclusive_u8_to_i64(multi.as<uint8_t>(), slot.as<int64_t>(), nc, slot.as<int64_t>() + nc, s));
     int64_t totals[2] = {0, 0};
@@ -514,7 +608,7 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     (chunk_rows<<<grid_1d(nc), 256, 0, s>>>(cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nc,
                                            chunk_row.as<int32_t>(), slot_row.as<int32_t>()), note_launch());
     if (nchunks > 0) {
-        const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap) + sizeof(int) * (kRowThreads / 32);
+        const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap) + sizeof(int) * kRowWarps;
         GOSH_TRY_CUDA(cudaFuncSetAttribute(coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         GOSH_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_rows, kRowThreads, smem));
@@ -532,8 +626,8 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     if (nslots > 0) {
         const int64_t cap = (int64_t)num_sms() * 8;
         (coarse_rows_multi<<<(int)(nslots < cap ? nslots : cap), kRowThreads, 0, s>>>(
-             slot_row.as<int32_t>(), nslots, cstart.as<int64_t>(), moff.as<int64_t>(), words, n0,
-             gbm.as<uint32_t>(), gsum.as<uint32_t>(), scratch.as<int32_t>(), count.as<int32_t>()),
+             slot_row.as<int32_t>(), nslots, rbase.as<int64_t>(), words, n0, gbm.as<uint32_t>(),
+             gsum.as<uint32_t>(), scratch.as<int32_t>(), count.as<int32_t>()),
          note_launch());
     }
     GOSH_TRY(scan_exclusive_i32_to_i64(count.as<int32_t>(), rp, nc, rp + nc, s));
@@ -541,8 +635,8 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY_CUDA(cudaMemcpyAsync(&m, rp + nc, sizeof(m), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
-    (compact_rows<<<grid_warps(nc), 256, 0, s>>>(scratch.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(), rp,
-                                                 nc, *co_out), note_launch());
+    (compact_rows<<<grid_warps(ceil_div(m, kEntriesPerWarp)), 256, 0, s>>>(scratch.as<int32_t>(), rbase.as<int64_t>(),
+                                                                             rp, nc, *co_out), note_launch());
     *m_out = m;
     return GOSH_OK;
 }
@@ -566,7 +660,7 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
 
     // 1. degree order
     (degree_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>()), note_launch());
-    GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), vals.as<uint32_t>(), n, 0, 32, s));
+    GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), vals.as<uint32_t>(), n, 0, bits_for((uint64_t)(n - 1)), s));
     const uint32_t *order = vals.as<uint32_t>();
     (invert_order<<<grid_1d(n), 256, 0, s>>>(order, n, rank.as<int32_t>()), note_launch());
     (mis_init<<<grid_1d(n), 256, 0, s>>>(rowptr, n, state.as<uint8_t>()), note_launch());
@@ -589,8 +683,12 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     if (rounds_out) *rounds_out = rounds;
 
     // 3. attach non-hubs, number the clusters by hub rank
-    (attach_to_hub<<<grid_1d(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
-                                                 hub_rank.as<int32_t>()), note_launch());
+    if (nnz > 64 * n)
+        (attach_to_hub_warp<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
+                                                          hub_rank.as<int32_t>()), note_launch());
+    else
+        (attach_to_hub<<<grid_1d(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
+                                                     hub_rank.as<int32_t>()), note_launch());
     (hub_flags_by_rank<<<grid_1d(n), 256, 0, s>>>(order, state.as<uint8_t>(), n, flags.as<uint8_t>()), note_launch());
     GOSH_TRY(scan_exclusive_u8_to_i64(flags.as<uint8_t>(), cid.as<int64_t>(), n, cid.as<int64_t>() + n, s));
     GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));

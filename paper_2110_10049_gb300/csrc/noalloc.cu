@@ -15,7 +15,7 @@
 
 namespace gosh {
 
-gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lanes, int pass,
+gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lanes, int pass, int64_t n,
                               const TrainKernel **out);
 int train_mode(const gosh_params *p);
 int tile_vertices(const gosh_params *p, int64_t n, int lanes);
@@ -97,7 +97,8 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
         return GOSH_ERR_UNSUPPORTED;
     }
     const TrainKernel *kern = nullptr;
-    GOSH_TRY(pick_train_kernel(p->dtype, p->d, p->k, train_mode(p), p->lanes_per_row, p->samples_per_pass, &kern));
+    GOSH_TRY(pick_train_kernel(p->dtype, p->d, p->k, train_mode(p), p->lanes_per_row, p->samples_per_pass, g->n,
+                               &kern));
     if (epochs == 0) return GOSH_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;

@@ -105,12 +105,13 @@ int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) /
 
 // Sources per warp tile.  A warp walks its tile in tile / (32/L) dependent
 // rounds, so small levels (few tiles, far fewer than the GPU's warps) take
-// short tiles; large levels take 32 to amortise the draws.  A multiple of
-// 32/L in [32/L, 32]; params->vertices_per_warp overrides.
+// short tiles (4 below 2^16 rows, 16 below 2^19); large levels take 32 to
+// amortise the draws.  A multiple of 32/L in [32/L, 32];
+// params->vertices_per_warp overrides.
 int tile_vertices(const gosh_params *p, int64_t n, int lanes) {
     const int G = 32 / lanes;
     int t = p->vertices_per_warp;
-    if (t <= 0) t = n >= (int64_t(1) << 19) ? 32 : (n >= (int64_t(1) << 16) ? 16 : 8);
+    if (t <= 0) t = n >= (int64_t(1) << 19) ? 32 : (n >= (int64_t(1) << 16) ? 16 : 4);
     t = t < G ? G : (t > 32 ? 32 : t);
     return t / G * G;
 }
@@ -123,22 +124,39 @@ int train_mode(const gosh_params *p) {
     return (p->dtype == GOSH_F32 && !p->plain_stores) ? kModeRed : kModeStore;
 }
 
-gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lanes, int pass,
+gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lanes, int pass, int64_t n,
                               const TrainKernel **out) {
     const bool det = mode == kModeDet;
     const int ns = k + 1;
-    // Defaults from the lanes/pass sweeps on R-MAT 20 (d = 128, k = 3):
-    // FP32 lock-free runs best with every row staged by TMA (one 16-byte
-    // vector per lane); 16-bit tables do best in registers with two vectors
-    // per lane (more sources in flight per warp) and two sample rows per pass.
-    if (lanes <= 0 && pass == 0 && mode == kModeRed && ns <= 6) {
-        lanes = natural_lanes(dtype, d);
-        pass = ns <= 4 ? -4 : -6;
+    const int nat = natural_lanes(dtype, d);
+    // Defaults by level size, from per-level sweeps of lanes per row L,
+    // samples per pass P and tile on the R-MAT 20 hierarchy (d = 128, k = 3;
+    // L0 = one 16-byte vector per lane):
+    //  - FP32 lock-free: above 2^19 rows every row staged by TMA (L0); from
+    //    2^14 rows, registers with L0 lanes and P = 2; below, L0/2 lanes and
+    //    P = 4 (shorter dependency chains on the latency-bound small levels);
+    //  - 16-bit tables: registers with P = 4; L0/2 lanes (two vectors per
+    //    lane, more sources in flight) except from 2^16 to 2^19 rows, where
+    //    L0 lanes keep more warps resident.
+    if (!det && lanes <= 0 && pass == 0) {
+        if (mode == kModeRed) {
+            if (n >= (int64_t(1) << 19) && ns <= 6) {
+                lanes = nat;
+                pass = ns <= 4 ? -4 : -6;
+            } else if (n >= (int64_t(1) << 14)) {
+                lanes = nat;
+                pass = 2;
+            } else {
+                lanes = nat >= 2 ? nat / 2 : nat;
+                pass = 4;
+            }
+        } else if (dtype != GOSH_F32) {
+            const bool mid = n >= (int64_t(1) << 16) && n < (int64_t(1) << 19);
+            lanes = (mid || nat < 4) ? nat : nat / 2;
+            pass = 4;
+        }
     }
-    if (lanes <= 0) {
-        const int nat = natural_lanes(dtype, d);
-        lanes = (!det && dtype != GOSH_F32 && nat >= 4) ? nat / 2 : nat;
-    }
+    if (lanes <= 0) lanes = (!det && dtype != GOSH_F32 && nat >= 4) ? nat / 2 : nat;
     if (pass == 0) pass = det ? (ns <= 4 ? 4 : 8) : 2;
     if (pass < 0 && (det || ns > -pass)) {
         set_error("TMA-staged kernels (samples_per_pass = -S) serve the lock-free mode with k+1 <= S (k+1 = %d)", ns);
@@ -167,7 +185,8 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
         return GOSH_ERR_UNSUPPORTED;
     }
     const TrainKernel *kern = nullptr;
-    GOSH_TRY(pick_train_kernel(p->dtype, p->d, p->k, train_mode(p), p->lanes_per_row, p->samples_per_pass, &kern));
+    GOSH_TRY(pick_train_kernel(p->dtype, p->d, p->k, train_mode(p), p->lanes_per_row, p->samples_per_pass, g->n,
+                               &kern));
     const int64_t n = g->n;
     if (epochs <= 0 || n <= 0) return GOSH_OK;
     const int ns = p->k + 1;
