@@ -75,11 +75,15 @@ typedef struct gosh_params {
     int samples_per_pass;   /* sample rows gathered at once per source; 0 = automatic */
     int64_t device_budget_bytes; /* 0 = unlimited */
     int validate;           /* 1: check the CSR before use (costs one pass) */
-    int plain_stores;       /* GOSH_HOGWILD with FP32 tables: 0 (default) applies every row
-                               change as an atomic vector addition, so concurrent updates of
-                               one row are never lost; 1 writes rows back with plain stores
-                               as the paper does (a racing writer may overwrite an update).
-                               16-bit tables always use plain stores with stochastic rounding. */
+    int plain_stores;       /* GOSH_HOGWILD: 0 (default) applies every row change as an atomic
+                               vector addition at L2 (16-bit tables: the stochastically
+                               rounded new row minus the row read, rounded to nearest; without
+                               a racing writer this leaves exactly the rounded row whenever the
+                               change fits the 16-bit significand, e.g. any change below 256
+                               ulps, else within one ulp), so concurrent updates of one row are
+                               never lost; 1 writes rows back with plain (16-bit:
+                               stochastically rounded) stores as the paper does (a racing
+                               writer may overwrite an update). */
     int projection;         /* gosh_embed between levels: 0 = copy (EXPANDEMBEDDING, Alg. 2),
                                1 = learned residual MLP (gosh_project_learned), trained after
                                every level on that level's (coarse, fine) pairs */

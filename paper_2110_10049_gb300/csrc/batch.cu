@@ -116,7 +116,7 @@ __device__ void project_rows(const Phase &ph, int64_t r0, int64_t r1, int lane) 
 
 template <typename T, int D, int L, int P>
 __global__ void __launch_bounds__(kTrainWarps * 32) batch_kernel(BatchArgs b) {
-    constexpr int MODE = std::is_same<T, float>::value ? kModeRed : kModeStore;
+    constexpr int MODE = kModeRed;  // atomic row changes (16-bit: stochastically rounded)
     __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
     __shared__ uint32_t s_sr[kTrainWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -200,6 +200,23 @@ template <> struct Store<__nv_bfloat16> {
     __device__ __forceinline__ static float round_nearest(float x) {
         return __bfloat162float(__float2bfloat16_rn(x));
     }
+    // Differences nw - old of 8 values, rounded to nearest and packed (exact
+    // when they need at most 8 significant bits, e.g. a few ulps).
+    __device__ __forceinline__ static uint4 pack_diff(const float *nw, const float *old) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(nw[2 * i] - old[2 * i], nw[2 * i + 1] - old[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    // Atomic addition of 8 packed values at L2 (no flush to zero).
+    __device__ __forceinline__ static void red_add(__nv_bfloat16 *p, const uint4 &d) {
+        asm volatile("red.global.add.noftz.v4.bf16x2 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(d.x), "r"(d.y),
+                     "r"(d.z), "r"(d.w)
+                     : "memory");
+    }
 };
 
 // FP16 stochastic rounding: between the toward-zero neighbour and the next
@@ -241,6 +258,20 @@ template <> struct Store<__half> {
     }
     __device__ __forceinline__ static float round_nearest(float x) {
         return __half2float(__float2half_rn(x));
+    }
+    __device__ __forceinline__ static uint4 pack_diff(const float *nw, const float *old) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 h = __floats2half2_rn(nw[2 * i] - old[2 * i], nw[2 * i + 1] - old[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __device__ __forceinline__ static void red_add(__half *p, const uint4 &d) {
+        asm volatile("red.global.add.noftz.v4.f16x2 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(d.x), "r"(d.y),
+                     "r"(d.z), "r"(d.w)
+                     : "memory");
     }
 };
 

@@ -62,6 +62,7 @@ template <typename T, int D, int L, int P, int MODE>
 __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *su, float *slr,
                           unsigned long long &applied) {
     constexpr bool RED = MODE == kModeRed;
+    constexpr bool RED16 = RED && !std::is_same<T, float>::value;
     constexpr int E = D / L;
     constexpr int G = 32 / L;
     const int lane = threadIdx.x & 31, grp = lane / L, gl = lane % L;
@@ -178,10 +179,17 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
                 const float score = ok ? (b - __frcp_rn(1.0f + __expf(-xx))) * lr : 0.0f;
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[e] = fmaf(row[x][e], score, r[e]);
+                float old16[RED16 ? E : 1];
+                if (RED16) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) old16[e] = row[x][e];
+                }
 #pragma unroll
                 for (int e = 0; e < E; ++e) row[x][e] = fmaf(r[e], score, row[x][e]);
                 if (ok) {
-                    if (RED) {
+                    if constexpr (RED16) {
+                        red_row16<T, D, E>(Mopp + (int64_t)us[x] * D + gl * E, row[x], old16, sr, t, gl * E);
+                    } else if (RED) {
                         float c[E];
 #pragma unroll
                         for (int e = 0; e < E; ++e) c[e] = r[e] * score;
@@ -200,7 +208,9 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
             }
         }
         if (active) {
-            if (RED) {
+            if constexpr (RED16) {
+                red_row16<T, D, E>(Mown + u * D + gl * E, r, r0, sr, ns, gl * E);
+            } else if (RED) {
                 float dr[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) dr[e] = r[e] - r0[RED ? e : 0];
@@ -215,7 +225,7 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
 
 template <typename T, int D, int L, int P>
 __global__ void __launch_bounds__(kTrainWarps * 32) pair_kernel(PairArgs a) {
-    constexpr int MODE = std::is_same<T, float>::value ? kModeRed : kModeStore;
+    constexpr int MODE = kModeRed;  // atomic row changes (16-bit: stochastically rounded)
     __shared__ int32_t su[kTrainWarps][32 * kMaxSlots];
     __shared__ float slr[kTrainWarps][32 * 8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -105,23 +105,24 @@ int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) /
 
 // Sources per warp tile.  A warp walks its tile in tile / (32/L) dependent
 // rounds, so small levels (few tiles, far fewer than the GPU's warps) take
-// short tiles (4 below 2^16 rows, 16 below 2^19); large levels take 32 to
-// amortise the draws.  A multiple of 32/L in [32/L, 32];
-// params->vertices_per_warp overrides.
+// short tiles (4 below 2^16 rows; below 2^19, 16, or 8 for 16-bit tables);
+// large levels take 32 to amortise the draws.  A multiple of 32/L in
+// [32/L, 32]; params->vertices_per_warp overrides.
 int tile_vertices(const gosh_params *p, int64_t n, int lanes) {
     const int G = 32 / lanes;
     int t = p->vertices_per_warp;
-    if (t <= 0) t = n >= (int64_t(1) << 19) ? 32 : (n >= (int64_t(1) << 16) ? 16 : 4);
+    const int mid = (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC) ? 8 : 16;
+    if (t <= 0) t = n >= (int64_t(1) << 19) ? 32 : (n >= (int64_t(1) << 16) ? mid : 4);
     t = t < G ? G : (t > 32 ? 32 : t);
     return t / G * G;
 }
 
 // Kernel mode for the parameters: deterministic batches, or the lock-free
-// epoch with atomic FP32 row changes unless plain stores are requested (and
-// always plain stores with stochastic rounding for 16-bit tables).
+// epoch with atomic row changes (16-bit tables: the stochastically rounded
+// change) unless plain stores are requested.
 int train_mode(const gosh_params *p) {
     if (p->mode == GOSH_DETERMINISTIC) return kModeDet;
-    return (p->dtype == GOSH_F32 && !p->plain_stores) ? kModeRed : kModeStore;
+    return p->plain_stores ? kModeStore : kModeRed;
 }
 
 gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lanes, int pass, int64_t n,
@@ -135,11 +136,11 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
     //  - FP32 lock-free: above 2^19 rows every row staged by TMA (L0); from
     //    2^14 rows, registers with L0 lanes and P = 2; below, L0/2 lanes and
     //    P = 4 (shorter dependency chains on the latency-bound small levels);
-    //  - 16-bit tables: registers with P = 4; L0/2 lanes (two vectors per
-    //    lane, more sources in flight) except from 2^16 to 2^19 rows, where
-    //    L0 lanes keep more warps resident.
+    //  - 16-bit tables: registers; L0/2 lanes (two vectors per lane, more
+    //    sources in flight) and P = 2 (P = 4 with plain stores), except from
+    //    2^16 to 2^19 rows, where L0 lanes and P = 4 keep more warps resident.
     if (!det && lanes <= 0 && pass == 0) {
-        if (mode == kModeRed) {
+        if (dtype == GOSH_F32 && mode == kModeRed) {
             if (n >= (int64_t(1) << 19) && ns <= 6) {
                 lanes = nat;
                 pass = ns <= 4 ? -4 : -6;
@@ -153,7 +154,7 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
         } else if (dtype != GOSH_F32) {
             const bool mid = n >= (int64_t(1) << 16) && n < (int64_t(1) << 19);
             lanes = (mid || nat < 4) ? nat : nat / 2;
-            pass = 4;
+            pass = (mode == kModeStore || mid) ? 4 : 2;
         }
     }
     if (lanes <= 0) lanes = (!det && dtype != GOSH_F32 && nat >= 4) ? nat / 2 : nat;

@@ -11,8 +11,10 @@ constexpr gosh_dtype kType = GOSH_F16;
 
 #define GOSH_V(D, L, P, MODE) {kType, D, L, P, MODE, &make_train_kernel<T, D, L, P, MODE>}
 #define GOSH_VD(D, L0)                                                                               \
-    GOSH_V(D, L0, 2, kModeStore), GOSH_V(D, L0, 4, kModeStore), GOSH_V(D, L0 / 2, 2, kModeStore),    \
-        GOSH_V(D, L0 / 2, 4, kModeStore), GOSH_V(D, L0, 4, kModeDet), GOSH_V(D, L0, 8, kModeDet)
+    GOSH_V(D, L0, 2, kModeRed), GOSH_V(D, L0, 4, kModeRed), GOSH_V(D, L0 / 2, 2, kModeRed),          \
+        GOSH_V(D, L0 / 2, 4, kModeRed), GOSH_V(D, L0, 2, kModeStore), GOSH_V(D, L0, 4, kModeStore),   \
+        GOSH_V(D, L0 / 2, 2, kModeStore), GOSH_V(D, L0 / 2, 4, kModeStore), GOSH_V(D, L0, 4, kModeDet), \
+        GOSH_V(D, L0, 8, kModeDet)
 
 const TrainEntry kEntries[] = {GOSH_VD(32, L32), GOSH_VD(64, L64), GOSH_VD(128, L128)};
 #undef GOSH_VD

@@ -64,6 +64,25 @@ __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, 
                  : "memory");
 }
 
+// 16-bit tables, atomic mode: the new values f are stochastically rounded in
+// place and new - old, rounded to nearest, is added to the stored row at L2.
+// Without a concurrent writer the stored old value becomes exactly the rounded
+// new one whenever new - old fits the 16-bit significand (always when the
+// change is below 256 ulps of the value, which covers the small updates that
+// stochastic rounding exists for), else within one ulp of it; with a
+// concurrent writer both changes are kept instead of one overwriting the other.
+template <typename T, int D, int E>
+__device__ __forceinline__ void red_row16(T *__restrict__ p, float *f, const float *old, uint32_t sr, int slot,
+                                          int elem0) {
+    constexpr int PV = Store<T>::kPerVec;
+#pragma unroll
+    for (int v = 0; v < E / PV; ++v) {
+        const uint32_t base = (uint32_t)((slot * D + elem0 + v * PV) >> 1);
+        Store<T>::pack(f + v * PV, sr, base);
+        Store<T>::red_add(p + v * PV, Store<T>::pack_diff(f + v * PV, old + v * PV));
+    }
+}
+
 template <int E>
 __device__ __forceinline__ void red_row(float *p, const float *f) {
 #pragma unroll
@@ -83,9 +102,11 @@ __device__ __forceinline__ float group_sum(float x) {
  * P sample rows gathered per pass, MODE:
  *   kModeStore  lock-free epoch, rows written back with plain stores (the
  *               paper's scheme; concurrent writers to one row may lose updates);
- *   kModeRed    lock-free epoch, FP32 rows changed by atomic vector additions
- *               of the update (M[u] += score * M[v]; M[v] += its net change),
- *               so concurrent updates are never lost, only read stale;
+ *   kModeRed    lock-free epoch, rows changed by atomic vector additions of
+ *               the update (M[u] += score * M[v]; M[v] += its net change;
+ *               16-bit tables add the difference of the stochastically
+ *               rounded new row and the row read), so concurrent updates are
+ *               kept, only read stale;
  *   kModeDet    snapshot batch, changes written to R/C/keys (needs P >= k+1).
  */
 template <typename T, int D, int L, int P, int MODE>
@@ -93,7 +114,7 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
                                            double &loss_acc, unsigned long long &applied) {
     constexpr bool DET = MODE == kModeDet;
     constexpr bool RED = MODE == kModeRed;
-    static_assert(!RED || std::is_same<T, float>::value, "atomic row updates need FP32 tables");
+    constexpr bool RED16 = RED && !std::is_same<T, float>::value;
     constexpr int E = D / L;
     constexpr int PV = Store<T>::kPerVec;
     constexpr int G = 32 / L;
@@ -189,10 +210,17 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
                     const float score = ok ? (b - sig) * a.lr : 0.0f;
 #pragma unroll
                     for (int e = 0; e < E; ++e) r[e] = fmaf(row[s][e], score, r[e]);
+                    float old16[RED16 ? E : 1];
+                    if (RED16) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) old16[e] = row[s][e];
+                    }
 #pragma unroll
                     for (int e = 0; e < E; ++e) row[s][e] = fmaf(r[e], score, row[s][e]);
                     if (ok) {
-                        if (DET) {
+                        if constexpr (RED16) {
+                            red_row16<T, D, E>(M + (int64_t)us[s] * D + gl * E, row[s], old16, sr, t, gl * E);
+                        } else if (DET) {
                             const int64_t slot = (v - a.src_begin) * ns + t;
                             float c[E];
 #pragma unroll
@@ -225,7 +253,9 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
                 }
             }
             if (active) {
-                if (DET) {
+                if constexpr (RED16) {
+                    red_row16<T, D, E>(M + v * D + gl * E, r, r0, sr, ns, gl * E);
+                } else if (DET) {
                     store_f32<E>(a.R + (v - a.src_begin) * D + gl * E, r);
                 } else if (RED) {
                     float dr[E];

@@ -9,8 +9,9 @@
 // round therefore exposes no load latency once the pipeline is full, and the
 // registers hold only the source row and the current sample row (the paper
 // stages the source row in shared memory; here every row is staged).
-// Sample-row changes go straight to global memory (FP32: atomic vector
-// additions; 16-bit: stochastic-rounding stores); a later draw of the same
+// Sample-row changes go straight to global memory as atomic vector additions
+// (16-bit tables: of the stochastically rounded new row minus the staged
+// one), or as plain stores in the store mode; a later draw of the same
 // row by the same source continues from the staged copy, which the lanes
 // overwrite with the updated values.  Every mbarrier wait is bounded: on
 // time-out the warp raises the error word, waits (bounded) for its copies
@@ -60,8 +61,8 @@ constexpr int tma_stage_bytes() {
 template <typename T, int D, int L, int KS, int MODE>
 __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) {
     constexpr bool RED = MODE == kModeRed;
+    constexpr bool RED16 = RED && !std::is_same<T, float>::value;
     static_assert(MODE == kModeRed || MODE == kModeStore, "lock-free modes only");
-    static_assert(!RED || std::is_same<T, float>::value, "atomic row updates need FP32 tables");
     constexpr int E = D / L;
     constexpr int PV = Store<T>::kPerVec;
     constexpr int G = 32 / L;
@@ -205,10 +206,17 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
                 const float score = ok ? (b - __frcp_rn(1.0f + __expf(-x))) * a.lr : 0.0f;
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[e] = fmaf(row[e], score, r[e]);
+                float old16[RED16 ? E : 1];
+                if (RED16) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) old16[e] = row[e];
+                }
 #pragma unroll
                 for (int e = 0; e < E; ++e) row[e] = fmaf(r[e], score, row[e]);
                 if (ok) {
-                    if (RED) {
+                    if constexpr (RED16) {
+                        red_row16<T, D, E>(M + (int64_t)uid * D + gl * E, row, old16, sr, t, gl * E);
+                    } else if (RED) {
                         float c[E];
 #pragma unroll
                         for (int e = 0; e < E; ++e) c[e] = r[e] * score;
@@ -235,7 +243,9 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
                 }
             }
             if (active) {
-                if (RED) {
+                if constexpr (RED16) {
+                    red_row16<T, D, E>(M + v * D + gl * E, r, r0, sr, ns, gl * E);
+                } else if (RED) {
                     float dr[E];
 #pragma unroll
                     for (int e = 0; e < E; ++e) dr[e] = r[e] - r0[RED ? e : 0];

@@ -6,7 +6,7 @@ namespace {
 using T = __nv_bfloat16;
 constexpr gosh_dtype kType = GOSH_BF16;
 
-#define GOSH_TV(D, L, KS) {kType, D, L, -(KS), kModeStore, &make_train_tma_kernel<T, D, L, KS, kModeStore>}
+#define GOSH_TV(D, L, KS) {kType, D, L, -(KS), kModeRed, &make_train_tma_kernel<T, D, L, KS, kModeRed>}
 #define GOSH_TVL(D, L) GOSH_TV(D, L, 4), GOSH_TV(D, L, 6)
 #define GOSH_TVD(D, L0a, L0b) GOSH_TVL(D, L0a), GOSH_TVL(D, L0b)
 constexpr int L032 = 32 * (int)sizeof(T) / 16, L064 = 64 * (int)sizeof(T) / 16, L0128 = 128 * (int)sizeof(T) / 16;

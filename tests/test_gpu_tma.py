@@ -8,7 +8,8 @@ shared-memory ring) against the oracle.
   excluded by k = 0) the result is still the sequential epoch: within 1e-5
   of the oracle;
 - on R-MAT scale 12 the staged kernel reaches the oracle's training-edge AUC
-  within 0.01 (FP32 and BF16), and draws exactly the oracle's update count.
+  within 0.01 (FP32 and BF16, both with atomic row changes), and draws
+  exactly the oracle's update count.
 """
 import numpy as np
 import pytest
@@ -62,12 +63,7 @@ def test_staged_kernel_quality_and_counts(dtype, lanes, ks):
     assert g.lib().gosh_device_check(None) == 0
     assert int(nup.item()) == no
     a_o, a_g = fit_auc(Mo, gr), fit_auc(M.double().cpu().numpy(), gr)
-    if dtype == torch.float32:
-        assert abs(a_o - a_g) <= 0.01, (a_o, a_g)
-    else:
-        # 16-bit tables write whole rows back (stochastic rounding cannot be
-        # applied by an atomic add), and rows staged a round ahead widen the
-        # window in which a racing writer's update is overwritten: measured
-        # 0.61 vs 0.72; the library therefore keeps the register kernel as the
-        # 16-bit default.  Here: the staged path trains (well above chance).
-        assert torch.isfinite(M.float()).all() and a_g > 0.55, (a_o, a_g)
+    # FP32 and 16-bit rows both change by atomic additions at L2 (16-bit: the
+    # stochastically rounded change), so rows staged a round ahead are read
+    # stale but no update is overwritten
+    assert abs(a_o - a_g) <= 0.01, (a_o, a_g)
