@@ -64,6 +64,11 @@ gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int m
                          gosh_hierarchy **out);
 gosh_status persistent_levels(gosh_hierarchy *h, const std::vector<void *> &bufs, int lowest, const gosh_params &p,
                               unsigned long long *n_updates, cudaStream_t s);
+gosh_status mlp_train(gosh_mlp *m, const gosh_csr *g, const int32_t *map, const void *Mc, const void *Mf,
+                      gosh_dtype dt, int epochs, double lr, int batch, int64_t max_rows, cudaStream_t s,
+                      double *final_loss, bool use_kept);
+gosh_status mlp_project(gosh_mlp *m, const void *Mc, const int32_t *map, const gosh_csr *g, void *Mf, gosh_dtype dt,
+                        cudaStream_t s, int64_t keep_rows_of);
 
 namespace {
 
@@ -688,13 +693,16 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
         GOSH_TRY(train_level_impl(&gi, buf(i), i, ep[i], &p, s, nullptr, counter.as<unsigned long long>()));
         ev.record(2 * i, s);
         if (mlp.m && i <= D - 2 && i > 0)
-            GOSH_TRY(gosh_mlp_train(mlp.m, &gi, h->map[i], buf(i + 1), buf(i), p.d, p.dtype,
-                                    p.mlp_epochs > 0 ? p.mlp_epochs : 1, p.mlp_lr > 0 ? p.mlp_lr : 1e-3,
-                                    p.mlp_batch > 0 ? p.mlp_batch : 8192, p.mlp_max_rows, stream, nullptr));
+            GOSH_TRY(mlp_train(mlp.m, &gi, h->map[i], buf(i + 1), buf(i), p.dtype, p.mlp_epochs > 0 ? p.mlp_epochs : 1,
+                               p.mlp_lr > 0 ? p.mlp_lr : 1e-3, p.mlp_batch > 0 ? p.mlp_batch : 8192, p.mlp_max_rows,
+                               s, nullptr, true));
         if (i > 0) {
             gosh_csr gf{h->n[i - 1], h->rowptr[i - 1], h->col[i - 1], 1};
+            // the projection keeps the feature rows level i-1's training will use
+            // (same table M_i, still unchanged then)
             if (mlp.m && i <= D - 2)
-                GOSH_TRY(gosh_project_learned(mlp.m, buf(i), h->map[i - 1], &gf, buf(i - 1), p.d, p.dtype, stream));
+                GOSH_TRY(mlp_project(mlp.m, buf(i), h->map[i - 1], &gf, buf(i - 1), p.dtype, s,
+                                     i - 1 > 0 ? (p.mlp_max_rows > 0 ? p.mlp_max_rows : -1) : 0));
             else
                 GOSH_TRY(gosh_project(buf(i), h->n[i], h->map[i - 1], buf(i - 1), h->n[i - 1], p.d, p.dtype, stream));
         }

@@ -6,9 +6,11 @@
 //   f(v) = [ Mc[map v] | log(1 + deg v) | mean_{w in Gamma(v)} Mc[map w] | 0 pad ]   (kp = round16(2d+1))
 //   Z1 = f W1^T + b1,  H = relu(Z1),  Y = H W2^T + b2,  Mf[v] = Mc[map v] + Y
 //
-// All four contractions of a training step (Z1, Y, dW2 = dY^T H, dH = dY W2,
-// dW1 = dZ1^T f) run on the tcgen05 GEMM with BF16 operands and FP32
-// accumulation; masters and Adam moments are FP32.  W2 = b2 = 0 at creation,
+// All contractions of a training step (Z1, Y, dW2 = dY^T H, dH = dY W2,
+// dW1 = dZ1^T f) and of the projection run on the TMA-fed tcgen05 GEMM with
+// BF16 operands and FP32 accumulation; bias + ReLU is fused into the first
+// layer's epilogue and the residual update of the fine table into the second
+// layer's; masters and Adam moments are FP32.  W2 = b2 = 0 at creation,
 // so an untrained network is exactly the copy projection.
 #include <algorithm>
 #include <cmath>
@@ -20,6 +22,12 @@
 namespace gosh {
 gosh_status tc_gemm(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, float *C, int64_t ldc,
                     int M, int N, int K, int splits, int *err, cudaStream_t s);
+gosh_status tc_gemm_bias_relu(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
+                              const float *bias, __nv_bfloat16 *H, int64_t ldh, int M, int N, int K, int *err,
+                              cudaStream_t s);
+gosh_status tc_gemm_residual(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
+                             const float *bias, const int32_t *map, const void *Mc, void *Mf, int64_t v0, int d,
+                             gosh_dtype dt, int M, int K, int *err, cudaStream_t s);
 }
 
 struct gosh_mlp {
@@ -29,8 +37,17 @@ struct gosh_mlp {
     __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2tb = nullptr;
     int *err = nullptr;
     int64_t t = 0;
+    // Feature rows kept by a projection for the next training on the same
+    // level (gosh_embed only): rows v = j * stride of the graph with row
+    // pointer `key_rowptr`, features from the table `key_Mc` through `key_map`.
+    __nv_bfloat16 *Xc = nullptr;
+    int64_t Xc_cap = 0;
+    const void *key_Mc = nullptr;
+    const int64_t *key_rowptr = nullptr;
+    const int32_t *key_map = nullptr;
+    int64_t key_n = 0, key_stride = 0;
     ~gosh_mlp() {
-        void *ps[] = {W1, b1, W2, b2, mo[0], mo[1], mo[2], mo[3], ve[0], ve[1], ve[2], ve[3], W1b, W2b, W2tb, err};
+        void *ps[] = {W1, b1, W2, b2, mo[0], mo[1], mo[2], mo[3], ve[0], ve[1], ve[2], ve[3], W1b, W2b, W2tb, err, Xc};
         for (void *p : ps)
             if (p) cudaFree(p);
     }
@@ -82,45 +99,149 @@ __global__ void refresh_bf16(const float *W1, const float *W2, __nv_bfloat16 *W1
     }
 }
 
-// f(v) for fine vertices [v0, v0 + rows): one warp per vertex.
+// f(v) for the selected fine vertices v_r = v0 + r * stride, r < rows.
+//
+// The neighbour mean is an entry-balanced gather: the selected rows' CSR
+// entries are laid end to end (voff = prefix sum of their degrees) and cut
+// into spans of kFeatSpan entries, one warp per span, so a hub's row is
+// spread over many warps instead of holding one.  A warp walks the row
+// segments of its span; rows read as 16-byte vectors (V = d * sizeof(T) / 16
+// per row, 32 / V neighbours per step, four steps in flight), FP32 sums,
+// lanes holding the same vector added in a fixed order.  A row inside one
+// span is written at once; a row crossing spans leaves its partial sums in
+// the span's slots (0: the span's first row, 1: its last row) and
+// feat_fixup adds them in span order.  Deterministic throughout.
+constexpr int kFeatSpan = 1024;
+
+__global__ void feat_degrees(const int64_t *__restrict__ rowptr, int64_t v0, int64_t rows, int64_t stride,
+                             int64_t *__restrict__ deg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = v0 + r * stride;
+        deg[r] = rowptr[v + 1] - rowptr[v];
+    }
+}
+
+// Own row, log-degree and padding of every selected row; the mean part is
+// zero for a row without neighbours (the spans never visit it).
 template <typename T>
-__global__ void features_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                const int32_t *__restrict__ map, const T *__restrict__ Mc, int d, int kp, int64_t v0,
-                                int64_t rows, int64_t stride, __nv_bfloat16 *__restrict__ X) {
+__global__ void __launch_bounds__(256) feat_own(const int32_t *__restrict__ map, const T *__restrict__ Mc,
+                                                const int64_t *__restrict__ voff, int d, int kp, int64_t v0,
+                                                int64_t rows, int64_t stride, __nv_bfloat16 *__restrict__ X) {
+    constexpr int PV = Store<T>::kPerVec;
     const int lane = threadIdx.x & 31;
+    const int V = d / PV;
+    const uint4 *M4 = reinterpret_cast<const uint4 *>(Mc);
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = wid; r < rows; r += nw) {
         const int64_t v = v0 + r * stride;
-        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        const int64_t deg = voff[r + 1] - voff[r];
         __nv_bfloat16 *x = X + r * kp;
-        const T *own = Mc + (int64_t)map[v] * d;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};  // d <= 128: lane owns columns lane + 32 j
-        // 32 neighbours at a time: each lane fetches one neighbour's cluster id
-        // (one round trip for all), then the warp sums their rows with
-        // independent, back-to-back row loads.
-        for (int64_t p0 = b; p0 < e; p0 += 32) {
-            const int cnt = (int)(e - p0 < 32 ? e - p0 : 32);
-            const int32_t cid = lane < cnt ? __ldg(map + __ldg(col + p0 + lane)) : 0;
-#pragma unroll 8
-            for (int q = 0; q < cnt; ++q) {
-                const T *row = Mc + (int64_t)__shfl_sync(0xffffffffu, cid, q) * d;
+        if (lane < V) {
+            float own[PV];
+            Store<T>::unpack(__ldg(M4 + (int64_t)__ldg(map + v) * V + lane), own);
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (lane + 32 * j < d) acc[j] += (float)row[lane + 32 * j];
+            for (int i = 0; i < PV; ++i) {
+                x[lane * PV + i] = __float2bfloat16_rn(own[i]);
+                if (deg == 0) x[d + 1 + lane * PV + i] = __float2bfloat16_rn(0.0f);
             }
         }
-        const float inv = e > b ? 1.0f / (float)(e - b) : 0.0f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = lane + 32 * j;
-            if (c < d) {
-                x[c] = __float2bfloat16_rn((float)own[c]);
-                x[d + 1 + c] = __float2bfloat16_rn(acc[j] * inv);
-            }
-        }
-        if (lane == 0) x[d] = __float2bfloat16_rn(log1pf((float)(e - b)));
+        if (lane == 0) x[d] = __float2bfloat16_rn(log1pf((float)deg));
         for (int c = 2 * d + 1 + lane; c < kp; c += 32) x[c] = __float2bfloat16_rn(0.0f);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) feat_spans(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                                  const int32_t *__restrict__ map, const T *__restrict__ Mc,
+                                                  const int64_t *__restrict__ voff, int d, int kp, int64_t v0,
+                                                  int64_t rows, int64_t stride, __nv_bfloat16 *__restrict__ X,
+                                                  float *__restrict__ slots) {
+    constexpr int PV = Store<T>::kPerVec;
+    const int lane = threadIdx.x & 31;
+    const int V = d / PV;
+    const int R = 32 / V;
+    const int sub = lane / V, vec = lane % V;
+    const uint4 *M4 = reinterpret_cast<const uint4 *>(Mc);
+    const int64_t total = voff[rows];
+    const int64_t nspans = (total + kFeatSpan - 1) / kFeatSpan;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sp = wid; sp < nspans; sp += nw) {
+        const int64_t lo = sp * kFeatSpan, hi = lo + kFeatSpan < total ? lo + kFeatSpan : total;
+        int64_t a = 0, b = rows;  // last row with voff[row] <= lo
+        while (b - a > 1) {
+            const int64_t mid = (a + b) >> 1;
+            if (__ldg(voff + mid) <= lo) a = mid; else b = mid;
+        }
+        const int64_t first = a;
+        for (int64_t r = first; r < rows && __ldg(voff + r) < hi; ++r) {
+            const int64_t rb = __ldg(voff + r), re = __ldg(voff + r + 1);
+            if (re == rb) continue;
+            const int64_t sb = rb > lo ? rb : lo, se = re < hi ? re : hi;
+            const int64_t cbase = __ldg(rowptr + v0 + r * stride) - rb;  // CSR index of virtual entry p: cbase + p
+            float acc[PV];
+#pragma unroll
+            for (int i = 0; i < PV; ++i) acc[i] = 0.0f;
+            for (int64_t p0 = sb; p0 < se; p0 += 32) {
+                const int cnt = (int)(se - p0 < 32 ? se - p0 : 32);
+                const int32_t cid = lane < cnt ? __ldg(map + __ldg(col + cbase + p0 + lane)) : 0;
+                for (int q0 = 0; q0 < cnt; q0 += 4 * R) {
+                    uint4 w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + u * R + sub;
+                        const int32_t c = __shfl_sync(0xffffffffu, cid, q & 31);
+                        w[u] = q < cnt ? __ldg(M4 + (int64_t)c * V + vec) : make_uint4(0, 0, 0, 0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float f[PV];
+                        Store<T>::unpack(w[u], f);
+#pragma unroll
+                        for (int i = 0; i < PV; ++i) acc[i] += f[i];
+                    }
+                }
+            }
+            for (int o = V; o < 32; o <<= 1)
+#pragma unroll
+                for (int i = 0; i < PV; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+            if (lane < V) {
+                if (rb >= lo && re <= hi) {
+                    const float inv = 1.0f / (float)(re - rb);
+                    __nv_bfloat16 *x = X + r * kp + d + 1 + vec * PV;
+#pragma unroll
+                    for (int i = 0; i < PV; ++i) x[i] = __float2bfloat16_rn(acc[i] * inv);
+                } else {
+                    float *sl = slots + (sp * 2 + (r == first ? 0 : 1)) * d + vec * PV;
+#pragma unroll
+                    for (int i = 0; i < PV; ++i) sl[i] = acc[i];
+                }
+            }
+        }
+    }
+}
+
+// Rows whose entries cross span boundaries: add the span partials in order.
+__global__ void __launch_bounds__(256) feat_fixup(const int64_t *__restrict__ voff, int d, int kp, int64_t rows,
+                                                  const float *__restrict__ slots, __nv_bfloat16 *__restrict__ X) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = wid; r < rows; r += nw) {
+        const int64_t rb = voff[r], re = voff[r + 1];
+        if (re == rb) continue;
+        const int64_t s0 = rb / kFeatSpan, s1 = (re - 1) / kFeatSpan;
+        if (s0 == s1) continue;
+        const float inv = 1.0f / (float)(re - rb);
+        for (int c = lane; c < d; c += 32) {
+            float t = 0.0f;
+            for (int64_t sp = s0; sp <= s1; ++sp) {
+                const int slot = (sp == s0 && rb != sp * kFeatSpan) ? 1 : 0;
+                t += slots[(sp * 2 + slot) * d + c];
+            }
+            X[r * kp + d + 1 + c] = __float2bfloat16_rn(t * inv);
+        }
     }
 }
 
@@ -135,14 +256,6 @@ __global__ void residual_kernel(const int32_t *__restrict__ map, const T *__rest
         const int64_t v = v0 + r * stride;
         R[i] = (float)Mf[v * d + c] - (float)Mc[(int64_t)map[v] * d + c];
     }
-}
-
-// H = relu(Z1 + b1) in BF16 (rows x hid).
-__global__ void bias_relu_kernel(const float *__restrict__ Z1, const float *__restrict__ b1, int64_t rows, int hid,
-                                 __nv_bfloat16 *__restrict__ H) {
-    const int64_t total = rows * hid;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-        H[i] = __float2bfloat16_rn(fmaxf(Z1[i] + b1[i % hid], 0.0f));
 }
 
 // Y = Yacc + b2; diff = Y - R; G = 2 diff / B (FP32 and BF16); per-block loss sums.
@@ -178,12 +291,35 @@ __global__ void relu_grad_kernel(const float *__restrict__ dH, const __nv_bfloat
     }
 }
 
-// out[c] = sum over rows of G[r][c] (fixed order per column).
-__global__ void colsum_kernel(const float *__restrict__ G, int64_t rows, int cols, float *__restrict__ out) {
+// Column sums out[c] = sum over rows of G[r][c] in two fixed-order passes:
+// block (x, y) of 32 x 32 threads sums rows y*kColRows .. of 32 columns
+// (thread row ty takes rows ty, ty + 32, ...; then the 32 partials in order)
+// into part[y][c]; colsum_finish adds the row blocks' partials in order.
+constexpr int kColRows = 512;
+
+__global__ void __launch_bounds__(1024) colsum_kernel(const float *__restrict__ G, int64_t rows, int cols,
+                                                      float *__restrict__ part) {
+    __shared__ float p[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    const int64_t r0 = (int64_t)blockIdx.y * kColRows, r1 = r0 + kColRows < rows ? r0 + kColRows : rows;
+    float s = 0.0f;
+    if (c < cols)
+        for (int64_t r = r0 + ty; r < r1; r += 32) s += G[r * cols + c];
+    p[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && c < cols) {
+        float t = 0.0f;
+        for (int i = 0; i < 32; ++i) t += p[i][tx];
+        part[(int64_t)blockIdx.y * cols + c] = t;
+    }
+}
+
+__global__ void colsum_finish(const float *__restrict__ part, int nparts, int cols, float *__restrict__ out) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
-        float s = 0.0f;
-        for (int64_t r = 0; r < rows; ++r) s += G[r * cols + c];
-        out[c] = s;
+        float t = 0.0f;
+        for (int i = 0; i < nparts; ++i) t += part[(int64_t)i * cols + c];
+        out[c] = t;
     }
 }
 
@@ -219,18 +355,17 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     }
 }
 
-// Mf[v] = Mc[map v] + Yacc[r] + b2 (round to nearest in the storage type).
-template <typename T>
-__global__ void apply_residual_kernel(const int32_t *__restrict__ map, const T *__restrict__ Mc,
-                                      const float *__restrict__ Yacc, const float *__restrict__ b2, int d, int64_t v0,
-                                      int64_t rows, T *__restrict__ Mf) {
-    const int64_t total = rows * d;
+// Copies the chunk rows v = j * stride (v in [v0, v0 + rows)) of X into row j
+// of Xc (16-byte vectors; kp * 2 bytes is a multiple of 16).
+__global__ void keep_rows(const __nv_bfloat16 *__restrict__ X, int kp, int64_t v0, int64_t rows, int64_t stride,
+                          __nv_bfloat16 *__restrict__ Xc) {
+    const int vpr = kp * 2 / 16;
+    const int64_t j0 = (v0 + stride - 1) / stride, j1 = (v0 + rows + stride - 1) / stride;
+    const int64_t total = (j1 - j0) * vpr;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / d;
-        const int c = (int)(i % d);
-        const int64_t v = v0 + r;
-        const float x = (float)Mc[(int64_t)map[v] * d + c] + Yacc[i] + b2[c];
-        Mf[v * d + c] = (T)x;
+        const int64_t j = j0 + i / vpr;
+        const int q = (int)(i % vpr);
+        reinterpret_cast<uint4 *>(Xc + j * kp)[q] = reinterpret_cast<const uint4 *>(X + (j * stride - v0) * kp)[q];
     }
 }
 
@@ -257,14 +392,23 @@ gosh_status gemm(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, in
     return GOSH_OK;
 }
 
+// H = relu(A . B^T + bias) in BF16, over N in chunks of 256 columns.
+gosh_status gemm_bias_relu(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, const float *bias,
+                           __nv_bfloat16 *H, int64_t ldh, int M, int N, int K, int *err, cudaStream_t s) {
+    for (int n0 = 0; n0 < N; n0 += 256) {
+        const int nn = N - n0 < 256 ? N - n0 : 256;
+        GOSH_TRY(tc_gemm_bias_relu(A, lda, B + (int64_t)n0 * ldb, ldb, bias + n0, H + n0, ldh, M, nn, K, err, s));
+    }
+    return GOSH_OK;
+}
+
 // Workspace of one training batch of up to B rows.
 struct Work {
-    Scratch Z1, H, Y, G, Gb, Gt, Ht, dH, dZ, dZb, dZt, Xt, dW1, db1, dW2, db2, parts, loss;
+    Scratch H, Y, G, Gb, Gt, Ht, dH, dZ, dZb, dZt, Xt, dW1, db1, dW2, db2, parts, loss, cpart;
     int B = 0;
     gosh_status alloc(const gosh_mlp *m, int B_, cudaStream_t s) {
         B = B_;
         const int64_t Bp = round16(B);
-        GOSH_TRY(Z1.alloc(sizeof(float) * B * m->hid, s));
         GOSH_TRY(H.alloc(sizeof(__nv_bfloat16) * B * m->hid, s));
         GOSH_TRY(Y.alloc(sizeof(float) * B * m->d, s));
         GOSH_TRY(G.alloc(sizeof(float) * B * m->d, s));
@@ -282,9 +426,17 @@ struct Work {
         GOSH_TRY(db2.alloc(sizeof(float) * m->d, s));
         GOSH_TRY(parts.alloc(sizeof(double) * num_sms() * 16, s));
         GOSH_TRY(loss.alloc(sizeof(double), s));
+        GOSH_TRY(cpart.alloc(sizeof(float) * ceil_div(B, kColRows) * std::max(m->d, m->hid), s));
         return GOSH_OK;
     }
 };
+
+void colsum(const float *G, int64_t rows, int cols, float *part, float *out, cudaStream_t s) {
+    const int nparts = (int)ceil_div(rows, kColRows);
+    dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)nparts);
+    (colsum_kernel<<<grid, 1024, 0, s>>>(G, rows, cols, part), note_launch());
+    (colsum_finish<<<(int)ceil_div(cols, 256), 256, 0, s>>>(part, nparts, cols, out), note_launch());
+}
 
 void transpose(const __nv_bfloat16 *in, int64_t rows, int cols, int64_t ldo, __nv_bfloat16 *out, cudaStream_t s) {
     dim3 grid((unsigned)ceil_div(ldo, 32), (unsigned)ceil_div(cols, 32));
@@ -313,9 +465,8 @@ gosh_status batch_grads(gosh_mlp *m, const __nv_bfloat16 *X, const float *R, int
     const int Kb = round16(rows);
     const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(32, Kb / 256));
     const int g = grid_for((int64_t)rows * hid);
-    // forward
-    GOSH_TRY(gemm(X, kp, m->W1b, kp, w.Z1.as<float>(), hid, rows, hid, kp, 1, m->err, s));
-    (bias_relu_kernel<<<g, 256, 0, s>>>(w.Z1.as<float>(), m->b1, rows, hid, w.H.as<__nv_bfloat16>()), note_launch());
+    // forward (bias and ReLU fused into the first GEMM's epilogue)
+    GOSH_TRY(gemm_bias_relu(X, kp, m->W1b, kp, m->b1, w.H.as<__nv_bfloat16>(), hid, rows, hid, kp, m->err, s));
     GOSH_TRY(gemm(w.H.as<__nv_bfloat16>(), hid, m->W2b, hid, w.Y.as<float>(), d, rows, d, hid, 1, m->err, s));
     const int go = grid_for((int64_t)rows * d);
     (out_grad_kernel<<<go, 256, 0, s>>>(w.Y.as<float>(), m->b2, R, rows, d, 2.0f / (float)rows, w.G.as<float>(),
@@ -328,13 +479,12 @@ gosh_status batch_grads(gosh_mlp *m, const __nv_bfloat16 *X, const float *R, int
     GOSH_TRY_CUDA(cudaMemsetAsync(w.dW2.ptr, 0, sizeof(float) * d * hid, s));
     GOSH_TRY(gemm(w.Gt.as<__nv_bfloat16>(), Kb, w.Ht.as<__nv_bfloat16>(), Kb, w.dW2.as<float>(), hid, d, hid, Kb,
                   splits, m->err, s));
-    (colsum_kernel<<<(int)ceil_div(d, 128), 128, 0, s>>>(w.G.as<float>(), rows, d, w.db2.as<float>()), note_launch());
+    colsum(w.G.as<float>(), rows, d, w.cpart.as<float>(), w.db2.as<float>(), s);
     GOSH_TRY(gemm(w.Gb.as<__nv_bfloat16>(), d, m->W2tb, d, w.dH.as<float>(), hid, rows, hid, d, 1, m->err, s));
     (relu_grad_kernel<<<g, 256, 0, s>>>(w.dH.as<float>(), w.H.as<__nv_bfloat16>(), (int64_t)rows * hid,
                                         w.dZ.as<float>(), w.dZb.as<__nv_bfloat16>()),
      note_launch());
-    (colsum_kernel<<<(int)ceil_div(hid, 128), 128, 0, s>>>(w.dZ.as<float>(), rows, hid, w.db1.as<float>()),
-     note_launch());
+    colsum(w.dZ.as<float>(), rows, hid, w.cpart.as<float>(), w.db1.as<float>(), s);
     transpose(w.dZb.as<__nv_bfloat16>(), rows, hid, Kb, w.dZt.as<__nv_bfloat16>(), s);
     transpose(X, rows, kp, Kb, w.Xt.as<__nv_bfloat16>(), s);
     GOSH_TRY_CUDA(cudaMemsetAsync(w.dW1.ptr, 0, sizeof(float) * hid * kp, s));
@@ -369,12 +519,31 @@ gosh_status check_err(gosh_mlp *m, cudaStream_t s) {
 
 gosh_status features(const gosh_csr *g, const int32_t *map, const void *Mc, int d, gosh_dtype dt, int kp, int64_t v0,
                      int64_t rows, __nv_bfloat16 *X, cudaStream_t s, int64_t stride = 1) {
-    const int blocks = (int)std::min<int64_t>(ceil_div(rows * 32, 256), (int64_t)num_sms() * 16);
+    if (rows <= 0) return GOSH_OK;
+    Scratch deg, voff;
+    GOSH_TRY(deg.alloc(sizeof(int64_t) * rows, s));
+    GOSH_TRY(voff.alloc(sizeof(int64_t) * (rows + 1), s));
+    (feat_degrees<<<grid_for(rows), 256, 0, s>>>(g->rowptr, v0, rows, stride, deg.as<int64_t>()), note_launch());
+    GOSH_TRY(scan_exclusive_i64(deg.as<int64_t>(), voff.as<int64_t>(), rows, voff.as<int64_t>() + rows, s));
+    int64_t total = 0;
+    GOSH_TRY_CUDA(cudaMemcpyAsync(&total, voff.as<int64_t>() + rows, sizeof(total), cudaMemcpyDeviceToHost, s));
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t nspans = ceil_div(total, kFeatSpan);
+    Scratch slots;
+    GOSH_TRY(slots.alloc(sizeof(float) * 2 * d * (nspans > 0 ? nspans : 1), s));
+    const int64_t cap = (int64_t)num_sms() * 8;
+    const int own_blocks = (int)std::min<int64_t>(ceil_div(rows * 32, 256), cap);
+    const int span_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nspans * 32, 256), cap));
     return by_dtype(dt, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        (features_kernel<T><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(g->rowptr, g->col, map, static_cast<const T *>(Mc),
-                                                                    d, kp, v0, rows, stride, X),
-         note_launch());
+        const T *M = static_cast<const T *>(Mc);
+        (feat_own<T><<<own_blocks, 256, 0, s>>>(map, M, voff.as<int64_t>(), d, kp, v0, rows, stride, X), note_launch());
+        if (nspans > 0) {
+            (feat_spans<T><<<span_blocks, 256, 0, s>>>(g->rowptr, g->col, map, M, voff.as<int64_t>(), d, kp, v0, rows,
+                                                      stride, X, slots.as<float>()),
+             note_launch());
+            (feat_fixup<<<own_blocks, 256, 0, s>>>(voff.as<int64_t>(), d, kp, rows, slots.as<float>(), X), note_launch());
+        }
     });
 }
 
@@ -419,21 +588,35 @@ gosh_status mlp_create(int d, int hidden, uint64_t seed, gosh_mlp **out) {
 
 // Trains on (features of g's vertices from Mc, residual Mf - copy) pairs.
 // At most max_rows vertices take part (every stride-th vertex of the level).
+int64_t train_stride(int64_t nlev, int64_t max_rows) {
+    return (max_rows > 0 && nlev > max_rows) ? (nlev + max_rows - 1) / max_rows : 1;
+}
+
+// use_kept: take the feature rows a preceding projection kept for this level
+// (same graph, map, source table and stride) instead of gathering them again.
 gosh_status mlp_train(gosh_mlp *m, const gosh_csr *g, const int32_t *map, const void *Mc, const void *Mf,
                       gosh_dtype dt, int epochs, double lr, int batch, int64_t max_rows, cudaStream_t s,
-                      double *final_loss) {
+                      double *final_loss, bool use_kept) {
     const int64_t nlev = g->n;
-    const int64_t stride = (max_rows > 0 && nlev > max_rows) ? (nlev + max_rows - 1) / max_rows : 1;
+    const int64_t stride = train_stride(nlev, max_rows);
     const int64_t n = (nlev + stride - 1) / stride;
     const int d = m->d, kp = m->kp;
     if (batch <= 0) batch = 4096;
     batch = round16(batch);
     if (batch > n) batch = (int)round16((int)n);
-    Scratch X, R, loss;
-    GOSH_TRY(X.alloc(sizeof(__nv_bfloat16) * n * kp, s));
+    Scratch Xs, R, loss;
     GOSH_TRY(R.alloc(sizeof(float) * n * d, s));
     GOSH_TRY(loss.alloc(sizeof(double), s));
-    GOSH_TRY(features(g, map, Mc, d, dt, kp, 0, n, X.as<__nv_bfloat16>(), s, stride));
+    const __nv_bfloat16 *X = nullptr;
+    if (use_kept && m->Xc && m->key_Mc == Mc && m->key_rowptr == g->rowptr && m->key_map == map &&
+        m->key_n == nlev && m->key_stride == stride) {
+        X = m->Xc;
+    } else {
+        GOSH_TRY(Xs.alloc(sizeof(__nv_bfloat16) * n * kp, s));
+        GOSH_TRY(features(g, map, Mc, d, dt, kp, 0, n, Xs.as<__nv_bfloat16>(), s, stride));
+        X = Xs.as<__nv_bfloat16>();
+    }
+    m->key_Mc = nullptr;  // the kept rows serve one training
     GOSH_TRY(by_dtype(dt, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         (residual_kernel<T><<<grid_for(n * d), 256, 0, s>>>(map, static_cast<const T *>(Mc),
@@ -448,8 +631,8 @@ gosh_status mlp_train(gosh_mlp *m, const gosh_csr *g, const int32_t *map, const 
         for (int64_t r0 = 0; r0 < n; r0 += batch) {
             const int rows = (int)std::min<int64_t>(batch, n - r0);
             if (rows < 16) continue;  // a sliver batch adds noise, not signal
-            GOSH_TRY(batch_grads(m, X.as<__nv_bfloat16>() + r0 * kp, R.as<float>() + r0 * d, rows, w,
-                                 last ? loss.as<double>() : nullptr, r0 > 0, s));
+            GOSH_TRY(batch_grads(m, X + r0 * kp, R.as<float>() + r0 * d, rows, w, last ? loss.as<double>() : nullptr,
+                                 r0 > 0, s));
             adam_all(m, w, (float)lr, s);
         }
     }
@@ -463,30 +646,46 @@ gosh_status mlp_train(gosh_mlp *m, const gosh_csr *g, const int32_t *map, const 
 }
 
 // Mf = copy + MLP(features), in chunks of kRowsPerChunk fine vertices.
+// keep_rows_of > 0: keep the feature rows a training with max_rows =
+// keep_rows_of will use on this level (gosh_embed only).
 gosh_status mlp_project(gosh_mlp *m, const void *Mc, const int32_t *map, const gosh_csr *g, void *Mf, gosh_dtype dt,
-                        cudaStream_t s) {
+                        cudaStream_t s, int64_t keep_rows_of) {
     const int64_t n = g->n;
     const int d = m->d, kp = m->kp, hid = m->hid;
     const int64_t chunk = std::min<int64_t>(n, kRowsPerChunk);
-    Scratch X, Z1, H, Y;
+    const int64_t stride = train_stride(n, keep_rows_of);
+    const int64_t nkeep = (n + stride - 1) / stride;
+    m->key_Mc = nullptr;
+    if (keep_rows_of != 0 && nkeep > m->Xc_cap) {
+        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+        if (m->Xc) cudaFree(m->Xc);
+        m->Xc = nullptr;
+        m->Xc_cap = 0;
+        GOSH_TRY_CUDA(cudaMalloc(&m->Xc, sizeof(__nv_bfloat16) * nkeep * kp));
+        m->Xc_cap = nkeep;
+    }
+    Scratch X, H;
     GOSH_TRY(X.alloc(sizeof(__nv_bfloat16) * chunk * kp, s));
-    GOSH_TRY(Z1.alloc(sizeof(float) * chunk * hid, s));
     GOSH_TRY(H.alloc(sizeof(__nv_bfloat16) * chunk * hid, s));
-    GOSH_TRY(Y.alloc(sizeof(float) * chunk * d, s));
     for (int64_t v0 = 0; v0 < n; v0 += chunk) {
         const int rows = (int)std::min<int64_t>(chunk, n - v0);
         GOSH_TRY(features(g, map, Mc, d, dt, kp, v0, rows, X.as<__nv_bfloat16>(), s));
-        GOSH_TRY(gemm(X.as<__nv_bfloat16>(), kp, m->W1b, kp, Z1.as<float>(), hid, rows, hid, kp, 1, m->err, s));
-        (bias_relu_kernel<<<grid_for((int64_t)rows * hid), 256, 0, s>>>(Z1.as<float>(), m->b1, rows, hid,
-                                                                        H.as<__nv_bfloat16>()),
-         note_launch());
-        GOSH_TRY(gemm(H.as<__nv_bfloat16>(), hid, m->W2b, hid, Y.as<float>(), d, rows, d, hid, 1, m->err, s));
-        GOSH_TRY(by_dtype(dt, [&](auto *tp) {
-            using T = std::remove_pointer_t<decltype(tp)>;
-            (apply_residual_kernel<T><<<grid_for((int64_t)rows * d), 256, 0, s>>>(
-                 map, static_cast<const T *>(Mc), Y.as<float>(), m->b2, d, v0, rows, static_cast<T *>(Mf)),
+        if (keep_rows_of != 0)
+            (keep_rows<<<grid_for(ceil_div(rows, stride) * (kp / 8)), 256, 0, s>>>(X.as<__nv_bfloat16>(), kp, v0, rows,
+                                                                                  stride, m->Xc),
              note_launch());
-        }));
+        GOSH_TRY(gemm_bias_relu(X.as<__nv_bfloat16>(), kp, m->W1b, kp, m->b1, H.as<__nv_bfloat16>(), hid, rows, hid, kp,
+                                m->err, s));
+        // Mf[v] = Mc[map v] + H W2^T + b2, written by the second GEMM's epilogue
+        GOSH_TRY(tc_gemm_residual(H.as<__nv_bfloat16>(), hid, m->W2b, hid, m->b2, map, Mc, Mf, v0, d, dt, rows, hid,
+                                  m->err, s));
+    }
+    if (keep_rows_of != 0) {
+        m->key_Mc = Mc;
+        m->key_rowptr = g->rowptr;
+        m->key_map = map;
+        m->key_n = n;
+        m->key_stride = stride;
     }
     return check_err(m, s);
 }
@@ -581,7 +780,7 @@ gosh_status gosh_mlp_train(gosh_mlp *m, const gosh_csr *g_fine, const int32_t *m
     GOSH_CHECK_ARG(d == m->d, "d (%d) differs from the network's (%d)", d, m->d);
     GOSH_CHECK_ARG(epochs >= 0 && lr > 0, "bad epochs / lr");
     return mlp_train(m, g_fine, map, M_coarse, M_fine, dtype, epochs, lr, batch, max_rows, (cudaStream_t)stream,
-                     final_loss);
+                     final_loss, false);
 }
 
 gosh_status gosh_project_learned(gosh_mlp *m, const void *M_coarse, const int32_t *map, const gosh_csr *g_fine,
@@ -589,7 +788,7 @@ gosh_status gosh_project_learned(gosh_mlp *m, const void *M_coarse, const int32_
     clear_error();
     GOSH_CHECK_ARG(m && g_fine && g_fine->on_device && map && M_coarse && M_fine, "NULL or host argument");
     GOSH_CHECK_ARG(d == m->d, "d (%d) differs from the network's (%d)", d, m->d);
-    return mlp_project(m, M_coarse, map, g_fine, M_fine, dtype, (cudaStream_t)stream);
+    return mlp_project(m, M_coarse, map, g_fine, M_fine, dtype, (cudaStream_t)stream, 0);
 }
 
 }  // extern "C"

@@ -1,98 +1,191 @@
-// BF16 GEMM on the tcgen05 tensor cores: C[m][n] = sum_k A[m][k] * B[n][k]
-// (A and B row-major with K contiguous, FP32 accumulation in tensor memory).
+// BF16 GEMM on the tcgen05 tensor cores: acc[m][n] = sum_k A[m][k] * B[n][k]
+// (A and B row-major with K contiguous, FP32 accumulation in tensor memory),
+// with the epilogue fused: FP32 store, FP32 atomic addition (split-K),
+// bias + ReLU to BF16, or the learned projection's residual update of an
+// embedding table.
 //
-// One CTA (4 warps) computes a 128 x NT tile over a K range: 64-wide K chunks
-// of A and B are copied into shared memory in the canonical no-swizzle K-major
-// layout, one thread issues the K/16 MMAs, tcgen05.commit signals an mbarrier
-// and the four warps read their 32 accumulator lanes back with tcgen05.ld.
-// Split-K launches add their partial tiles into C with vector atomics.
-// Every wait is bounded: on time-out the CTA raises *err, waits (bounded) for
-// its MMAs, frees its tensor memory and leaves C unwritten.
+// One CTA (4 warps) computes a 128 x NT tile.  Operands arrive by TMA: each
+// stage holds 64 K-columns of the A and B tiles, loaded as eight 2-D boxes
+// of {8 columns, rows} placed side by side, which is the tensor cores'
+// canonical K-major layout without swizzle (8-row x 16-byte core matrices;
+// K-adjacent ones rows * 16 bytes apart, row groups 128 bytes apart).  Thread
+// 0 of warp 0 runs the TMA producer over a ring of S stages (full/empty
+// mbarriers), thread 0 of warp 1 issues the MMAs (one elected thread) and
+// frees each stage with tcgen05.commit; after the last commit all four warps
+// read their 32 accumulator lanes back with tcgen05.ld and apply the
+// epilogue.  Every wait is bounded: on time-out the CTA raises *err, waits
+// (bounded) for its MMAs and copies, frees its tensor memory and leaves the
+// output unwritten.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "tcgen05.cuh"
 
 namespace gosh {
 
 constexpr int kGemmThreads = 128;
-constexpr int kGemmKChunk = 64;
+constexpr int kGemmKStage = 64;  // K columns per pipeline stage
 constexpr uint32_t kGemmWaitPolls = 1u << 22;
 
+enum : int { kEpiStore = 0, kEpiAtomic = 1, kEpiBiasRelu = 2, kEpiResidual = 3 };
+
+// Epilogue operands (unused fields stay null).
+struct GemmEpi {
+    float *C = nullptr;               // kEpiStore / kEpiAtomic: C[m][n], row stride ldc
+    int64_t ldc = 0;
+    const float *bias = nullptr;      // kEpiBiasRelu / kEpiResidual: bias[n]
+    __nv_bfloat16 *H = nullptr;       // kEpiBiasRelu: H[m][n] = relu(acc + bias), row stride ldh
+    int64_t ldh = 0;
+    const int32_t *map = nullptr;     // kEpiResidual: Mf[v][n] = Mc[map v][n] + acc + bias, v = v0 + m
+    const void *Mc = nullptr;
+    void *Mf = nullptr;
+    int64_t v0 = 0;
+    int d = 0;                        // kEpiResidual: row length of Mc / Mf
+};
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ float to_f(T x) { return (float)x; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ float to_f<__half>(__half x) { return __half2float(x); }
+template <typename T>
+__device__ __forceinline__ T from_f(float x) { return (T)x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half from_f<__half>(float x) { return __float2half_rn(x); }
+
+// Pipeline stages: as many 64-column stages (2..4) as fit in 96 KB, so two
+// CTAs share an SM (two 256-column accumulators fill its tensor memory).
 template <int NT>
-__global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __nv_bfloat16 *__restrict__ A, int64_t lda,
-                                                               const __nv_bfloat16 *__restrict__ B, int64_t ldb,
-                                                               float *__restrict__ C, int64_t ldc, int M, int N,
-                                                               int K, int k_per_split, int atomic_add,
-                                                               int *__restrict__ err) {
+struct GemmShape {
+    static constexpr int kStageBytes = (128 + NT) * kGemmKStage * 2;
+    static constexpr int kFit = 98304 / kStageBytes;
+    static constexpr int kStages = kFit < 2 ? 2 : (kFit > 4 ? 4 : kFit);
+    static constexpr size_t kSmem = (size_t)kStages * kStageBytes;
+};
+
+template <int NT, int EPI, typename T>
+__global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB, GemmEpi ep,
+                                                                int M, int N, int K, int k_per_split,
+                                                                int *__restrict__ err) {
     static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "M = 128 needs N in [16, 256], multiple of 16");
+    constexpr int S = GemmShape<NT>::kStages;
     constexpr uint32_t kCols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t mbar;
+    constexpr int A_BYTES = 128 * kGemmKStage * 2, B_BYTES = NT * kGemmKStage * 2;
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
     __shared__ uint32_t tmem_base;
-    uint8_t *sA = smem;                  // 128 rows x 64 K x 2 B = 16 KB
-    uint8_t *sB = smem + 128 * 128;      // NT rows x 64 K x 2 B
+    __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
     const int kb = blockIdx.z * k_per_split;
     const int ke = min(K, kb + k_per_split);
+    const int nk = (ke - kb + kGemmKStage - 1) / kGemmKStage;
 
     if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
-    if (tid == 0) tc::mbar_init(&mbar, 1);
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&done, 1);
+        s_fail = 0;
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = tc::make_idesc_bf16(128, NT);
+    int issued[S];  // loads issued per stage (producer thread)
+#pragma unroll
+    for (int s = 0; s < S; ++s) issued[s] = 0;
 
-    uint32_t phase = 0;
-    int ok = 1, issued = 0;
-    for (int k0 = kb; k0 < ke && ok; k0 += kGemmKChunk) {
-        const int kc = min(kGemmKChunk, ke - k0);  // multiple of 16
-        const int nv = kc / 8;                       // core matrices along K
-        for (int i = tid; i < 128 * nv; i += kGemmThreads) {
-            const int r = i / nv, c = i % nv;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(A + (int64_t)(m0 + r) * lda + k0 + c * 8);
-            *reinterpret_cast<uint4 *>(sA + (r >> 3) * (nv * 128) + c * 128 + (r & 7) * 16) = v;
-        }
-        for (int i = tid; i < NT * nv; i += kGemmThreads) {
-            const int r = i / nv, c = i % nv;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (n0 + r < N) v = *reinterpret_cast<const uint4 *>(B + (int64_t)(n0 + r) * ldb + k0 + c * 8);
-            *reinterpret_cast<uint4 *>(sB + (r >> 3) * (nv * 128) + c * 128 + (r & 7) * 16) = v;
-        }
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            for (int s = 0; s < kc / 16; ++s) {
-                const uint64_t ad = tc::make_desc(tc::smem_addr(sA) + s * 256, 128, nv * 128);
-                const uint64_t bd = tc::make_desc(tc::smem_addr(sB) + s * 256, 128, nv * 128);
-                tc::mma_bf16(tmem, ad, bd, idesc, (k0 > kb || s > 0) ? 1u : 0u);
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer ----
+        for (int k = 0; k < nk; ++k) {
+            const int st = k % S;
+            if (k >= S && !tc::mbar_wait(&empty[st], ((k / S) - 1) & 1, kGemmWaitPolls)) {
+                atomicExch(&s_fail, 1);
+                break;
             }
-            tc::mma_commit(&mbar);
+            const int k0 = kb + k * kGemmKStage;
+            const int nc = min(kGemmKStage, ke - k0) / 8;  // 8-column boxes inside this split
+            mbar_arrive_expect_tx(&full[st], (uint32_t)nc * (128 + NT) * 16);
+            const uint32_t sa = tc::smem_addr(smem + (size_t)st * (A_BYTES + B_BYTES));
+            const uint32_t sb = sa + A_BYTES;
+            for (int c = 0; c < nc; ++c) {
+                tma_load_2d(sa + c * 128 * 16, &tmA, k0 + 8 * c, m0, tc::smem_addr(&full[st]));
+                tma_load_2d(sb + c * NT * 16, &tmB, k0 + 8 * c, n0, tc::smem_addr(&full[st]));
+            }
+            ++issued[st];
         }
-        issued = 1;
-        const bool done = tc::mbar_wait(&mbar, phase, kGemmWaitPolls);
-        ok = __syncthreads_and(done ? 1 : 0);
-        phase ^= 1;
-        tc::fence_after_sync();
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = tc::make_idesc_bf16(128, NT);
+        bool ok = true;
+        for (int k = 0; k < nk && ok; ++k) {
+            const int st = k % S;
+            if (!tc::mbar_wait(&full[st], (k / S) & 1, kGemmWaitPolls) || *(volatile int *)&s_fail) {
+                atomicExch(&s_fail, 1);
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const int k0 = kb + k * kGemmKStage;
+            const int steps = min(kGemmKStage, ke - k0) / 16;
+            const uint32_t sa = tc::smem_addr(smem + (size_t)st * (A_BYTES + B_BYTES));
+            const uint32_t sb = sa + A_BYTES;
+            for (int j = 0; j < steps; ++j) {
+                const uint64_t ad = tc::make_desc(sa + 2 * j * 128 * 16, 128 * 16, 128);
+                const uint64_t bd = tc::make_desc(sb + 2 * j * NT * 16, NT * 16, 128);
+                tc::mma_bf16(tmem, ad, bd, idesc, (k > 0 || j > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&empty[st]);
+        }
+        tc::mma_commit(&done);  // arrives once every MMA issued above has completed
     }
+    __syncwarp();
+    const bool finished = tc::mbar_wait(&done, 0, kGemmWaitPolls);
+    const int ok = __syncthreads_and(finished && !s_fail ? 1 : 0);
+    tc::fence_after_sync();
     if (!ok) {
-        // the last commit never arrived: give the MMAs one more bounded wait
-        tc::mbar_wait(&mbar, phase ^ 1, kGemmWaitPolls);
-        if (tid == 0) atomicExch(err, 1);
-    } else if (issued) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // Let copies still in flight land before the CTA's shared memory
+            // goes away.  A stage is refilled only after its previous load was
+            // consumed, so at most its last load (phase issued - 1) is pending.
+            for (int s = 0; s < S; ++s)
+                if (issued[s] > 0) tc::mbar_wait(&full[s], (uint32_t)(issued[s] - 1) & 1u, kGemmWaitPolls);
+        }
+    } else if (nk > 0) {
         const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
         for (int c = 0; c < NT; c += 16) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (row < M) {
-                float *out = C + (int64_t)row * ldc + n0 + c;
+            if (row >= M) continue;
+            const int col0 = n0 + c;
+            if (EPI == kEpiStore || EPI == kEpiAtomic) {
+                float *out = ep.C + (int64_t)row * ep.ldc + col0;
 #pragma unroll
                 for (int j = 0; j < 16; j += 4) {
-                    if (n0 + c + j + 3 < N) {
-                        if (atomic_add) {
+                    if (col0 + j + 3 < N) {
+                        if (EPI == kEpiAtomic) {
                             asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(out + j), "f"(v[j]),
                                          "f"(v[j + 1]), "f"(v[j + 2]), "f"(v[j + 3])
                                          : "memory");
@@ -101,11 +194,46 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __nv_bfloat
                         }
                     } else {
                         for (int q = j; q < j + 4; ++q)
-                            if (n0 + c + q < N) {
-                                if (atomic_add) atomicAdd(out + q, v[q]);
+                            if (col0 + q < N) {
+                                if (EPI == kEpiAtomic) atomicAdd(out + q, v[q]);
                                 else out[q] = v[q];
                             }
                     }
+                }
+            } else if (EPI == kEpiBiasRelu) {
+                __nv_bfloat16 *out = ep.H + (int64_t)row * ep.ldh + col0;
+                if (col0 + 15 < N) {
+                    uint32_t w[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(v[2 * j] + ep.bias[col0 + 2 * j], 0.0f),
+                                                                       fmaxf(v[2 * j + 1] + ep.bias[col0 + 2 * j + 1], 0.0f));
+                        w[j] = *reinterpret_cast<const uint32_t *>(&h);
+                    }
+                    uint4 *o4 = reinterpret_cast<uint4 *>(out);
+                    o4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    o4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                } else {
+                    for (int q = 0; q < 16; ++q)
+                        if (col0 + q < N) out[q] = __float2bfloat16_rn(fmaxf(v[q] + ep.bias[col0 + q], 0.0f));
+                }
+            } else {  // kEpiResidual: N == d, a multiple of 16 (16 values = whole 16-byte vectors)
+                constexpr int PV = 16 / (int)sizeof(T);
+                const int64_t vv = ep.v0 + row;
+                const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const T *>(ep.Mc) +
+                                                                   (int64_t)__ldg(ep.map + vv) * ep.d + col0);
+                uint4 *dst = reinterpret_cast<uint4 *>(static_cast<T *>(ep.Mf) + vv * ep.d + col0);
+#pragma unroll
+                for (int x = 0; x < 16 / PV; ++x) {
+                    union {
+                        uint4 u;
+                        T t[PV];
+                    } pk;
+                    pk.u = __ldg(src + x);
+#pragma unroll
+                    for (int q = 0; q < PV; ++q)
+                        pk.t[q] = from_f<T>(to_f<T>(pk.t[q]) + v[x * PV + q] + __ldg(ep.bias + col0 + x * PV + q));
+                    dst[x] = pk.u;
                 }
             }
         }
@@ -115,40 +243,140 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __nv_bfloat
     if (warp == 0) tc::tmem_dealloc(tmem, kCols);
 }
 
-template <int NT>
-gosh_status launch_tc_gemm_nt(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, float *C,
-                              int64_t ldc, int M, int N, int K, int splits, int *err, cudaStream_t s) {
-    const size_t smem = 128 * 128 + NT * 128;
+namespace {
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+gosh_status encoder(EncodeTiled *out) {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return GOSH_ERR_CUDA;
+        }
+        fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    *out = fn;
+    return GOSH_OK;
+}
+
+// Row-major BF16 matrix (rows x cols, row stride ld elements) read in boxes of
+// {8 columns, box_rows rows}; out-of-range rows and columns read as zero.
+gosh_status make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    EncodeTiled enc = nullptr;
+    GOSH_TRY(encoder(&enc));
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld operand, stride %lld", (int)r, (long long)rows,
+                  (long long)cols, (long long)ld);
+        return GOSH_ERR_CUDA;
+    }
+    return GOSH_OK;
+}
+
+template <int NT, int EPI, typename T>
+gosh_status launch_nt(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, const GemmEpi &ep,
+                      int M, int N, int K, int splits, int *err, cudaStream_t s) {
+    constexpr size_t smem = GemmShape<NT>::kSmem;
     static bool attr = false;
     if (!attr) {
-        GOSH_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GOSH_TRY_CUDA(cudaFuncSetAttribute(tma_gemm_kernel<NT, EPI, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
         attr = true;
     }
+    CUtensorMap ma, mb;
+    GOSH_TRY(make_map(&ma, A, M, K, lda, 128));
+    GOSH_TRY(make_map(&mb, B, N, K, ldb, NT));
     int kps = (int)ceil_div(K, splits);
     kps = (int)ceil_div(kps, 16) * 16;
     const int zs = (int)ceil_div(K, kps);
     dim3 grid((unsigned)ceil_div(M, 128), (unsigned)ceil_div(N, NT), (unsigned)zs);
-    (tc_gemm_kernel<NT><<<grid, kGemmThreads, smem, s>>>(A, lda, B, ldb, C, ldc, M, N, K, kps, splits > 1 ? 1 : 0,
-                                                         err),
-     note_launch());
+    (tma_gemm_kernel<NT, EPI, T><<<grid, kGemmThreads, smem, s>>>(ma, mb, ep, M, N, K, kps, err), note_launch());
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
 }
 
+template <int EPI, typename T>
+gosh_status launch(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, const GemmEpi &ep, int M,
+                   int N, int K, int splits, int *err, cudaStream_t s) {
+    if (N <= 16) return launch_nt<16, EPI, T>(A, lda, B, ldb, ep, M, N, K, splits, err, s);
+    if (N <= 32) return launch_nt<32, EPI, T>(A, lda, B, ldb, ep, M, N, K, splits, err, s);
+    if (N <= 64) return launch_nt<64, EPI, T>(A, lda, B, ldb, ep, M, N, K, splits, err, s);
+    if (N <= 128) return launch_nt<128, EPI, T>(A, lda, B, ldb, ep, M, N, K, splits, err, s);
+    return launch_nt<256, EPI, T>(A, lda, B, ldb, ep, M, N, K, splits, err, s);
+}
+
+gosh_status check_operands(const void *A, int64_t lda, const void *B, int64_t ldb, int M, int N, int K) {
+    GOSH_CHECK_ARG(M > 0 && N > 0 && N <= 256 && K > 0 && K % 16 == 0,
+                   "GEMM needs M > 0, 0 < N <= 256 and K a positive multiple of 16");
+    GOSH_CHECK_ARG(lda % 8 == 0 && ldb % 8 == 0 && lda >= K && ldb >= K, "row strides must be >= K and keep 16-byte alignment");
+    GOSH_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0, "GEMM operands must be 16-byte aligned");
+    return GOSH_OK;
+}
+
+}  // namespace
+
 // C (M x N, FP32, row stride ldc) = A (M x K) . B (N x K)^T, or += when splits > 1
-// (split-K over `splits` CTAs per tile, C must then hold the addend).
+// (split-K over `splits` CTAs per tile, C must then hold the addend).  N <= 256.
 gosh_status tc_gemm(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb, float *C, int64_t ldc,
                     int M, int N, int K, int splits, int *err, cudaStream_t s) {
-    GOSH_CHECK_ARG(M > 0 && N > 0 && K > 0 && K % 16 == 0, "GEMM needs M, N > 0 and K a positive multiple of 16");
-    GOSH_CHECK_ARG(lda % 8 == 0 && ldb % 8 == 0 && ldc % 4 == 0, "row strides must keep 16-byte alignment");
-    GOSH_CHECK_ARG(((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0 && ((uintptr_t)C & 15) == 0,
-                   "GEMM operands must be 16-byte aligned");
+    GOSH_TRY(check_operands(A, lda, B, ldb, M, N, K));
+    GOSH_CHECK_ARG(ldc % 4 == 0 && ((uintptr_t)C & 15) == 0, "C must keep 16-byte alignment");
     if (splits < 1) splits = 1;
-    if (N <= 16) return launch_tc_gemm_nt<16>(A, lda, B, ldb, C, ldc, M, N, K, splits, err, s);
-    if (N <= 32) return launch_tc_gemm_nt<32>(A, lda, B, ldb, C, ldc, M, N, K, splits, err, s);
-    if (N <= 64) return launch_tc_gemm_nt<64>(A, lda, B, ldb, C, ldc, M, N, K, splits, err, s);
-    if (N <= 128) return launch_tc_gemm_nt<128>(A, lda, B, ldb, C, ldc, M, N, K, splits, err, s);
-    return launch_tc_gemm_nt<256>(A, lda, B, ldb, C, ldc, M, N, K, splits, err, s);
+    GemmEpi ep;
+    ep.C = C;
+    ep.ldc = ldc;
+    if (splits > 1) return launch<kEpiAtomic, float>(A, lda, B, ldb, ep, M, N, K, splits, err, s);
+    return launch<kEpiStore, float>(A, lda, B, ldb, ep, M, N, K, 1, err, s);
+}
+
+// H (M x N, BF16, row stride ldh) = relu(A . B^T + bias).  N <= 256.
+gosh_status tc_gemm_bias_relu(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
+                              const float *bias, __nv_bfloat16 *H, int64_t ldh, int M, int N, int K, int *err,
+                              cudaStream_t s) {
+    GOSH_TRY(check_operands(A, lda, B, ldb, M, N, K));
+    GOSH_CHECK_ARG(ldh % 8 == 0 && ((uintptr_t)H & 15) == 0, "H must keep 16-byte alignment");
+    GemmEpi ep;
+    ep.bias = bias;
+    ep.H = H;
+    ep.ldh = ldh;
+    return launch<kEpiBiasRelu, float>(A, lda, B, ldb, ep, M, N, K, 1, err, s);
+}
+
+// Mf[v0 + m][n] = Mc[map[v0 + m]][n] + (A . B^T)[m][n] + bias[n] for m < M,
+// n < d (storage type of Mc/Mf: dt; d a multiple of 16, at most 256; rows
+// 16-byte aligned).
+gosh_status tc_gemm_residual(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
+                             const float *bias, const int32_t *map, const void *Mc, void *Mf, int64_t v0, int d,
+                             gosh_dtype dt, int M, int K, int *err, cudaStream_t s) {
+    GOSH_TRY(check_operands(A, lda, B, ldb, M, d, K));
+    GOSH_CHECK_ARG(d % 16 == 0 && ((uintptr_t)Mc & 15) == 0 && ((uintptr_t)Mf & 15) == 0,
+                   "residual epilogue needs d a multiple of 16 and 16-byte aligned tables");
+    GemmEpi ep;
+    ep.bias = bias;
+    ep.map = map;
+    ep.Mc = Mc;
+    ep.Mf = Mf;
+    ep.v0 = v0;
+    ep.d = d;
+    switch (dt) {
+    case GOSH_F32: return launch<kEpiResidual, float>(A, lda, B, ldb, ep, M, d, K, 1, err, s);
+    case GOSH_BF16: return launch<kEpiResidual, __nv_bfloat16>(A, lda, B, ldb, ep, M, d, K, 1, err, s);
+    case GOSH_F16: return launch<kEpiResidual, __half>(A, lda, B, ldb, ep, M, d, K, 1, err, s);
+    }
+    set_error("unknown dtype");
+    return GOSH_ERR_INVALID_ARG;
 }
 
 }  // namespace gosh
@@ -174,7 +402,7 @@ extern "C" gosh_status gosh_tc_gemm_bf16(const void *A, int64_t lda, const void 
     GOSH_TRY_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     if (herr) {
-        set_error("tensor-core GEMM: an MMA completion wait timed out");
+        set_error("tensor-core GEMM: an MMA or copy completion wait timed out");
         return GOSH_ERR_TIMEOUT;
     }
     return GOSH_OK;

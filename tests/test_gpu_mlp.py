@@ -117,3 +117,53 @@ def test_learned_projection_gains_over_copy():
             M, _ = g.gosh_embed(rp, co, p)
             auc[proj].append(g.gosh_link_auc(M, pos, neg))
     assert np.mean(auc[1]) > np.mean(auc[0]) + 0.05, auc
+
+
+def test_features_hubs_and_isolated_vertices():
+    """Rows longer than one gather span (a 5000-leaf star and a 2500-entry
+    hub) are summed from span partials; vertices without neighbours get a zero
+    mean; both against the oracle's definition."""
+    g = gosh()
+    rng = np.random.default_rng(5)
+    n = 9000
+    s = np.concatenate([np.zeros(5000, np.int64), np.full(2500, 6000), rng.integers(7000, 8000, 3000)])
+    t = np.concatenate([np.arange(1, 5001), rng.choice(np.arange(6001, 9000), 2500, replace=False),
+                        rng.integers(7000, 8000, 3000)])
+    keep = s != t
+    gr = synth.csr_from_edges(n, s[keep], t[keep], compact=False)
+    assert np.diff(gr.rowptr).max() >= 5000 and (np.diff(gr.rowptr) == 0).any()
+    nc, d = 300, 128
+    mp = rng.integers(0, nc, n).astype(np.int32)
+    Mc = bf16_round_np(rng.normal(size=(nc, d)))
+    m = g.Mlp(d, 64)
+    csr = g.to_device_csr(gr.rowptr, gr.col)
+    X = m.features(csr, torch.from_numpy(mp).cuda(), torch.from_numpy(Mc).to(torch.bfloat16).cuda())
+    ref = omlp.features(gr.rowptr, gr.col, mp, Mc)
+    np.testing.assert_allclose(X.float().cpu().numpy()[:, :2 * d + 1], ref, rtol=2 ** -7, atol=1e-6)
+
+
+@pytest.mark.parametrize("d,hidden", [(32, 64), (128, 256), (64, 512)])
+def test_projection_matches_oracle_forward(d, hidden):
+    """gosh_project_learned with random weights: Mf - copy equals the oracle's
+    forward pass on the BF16-rounded weights and features (the GPU also rounds
+    the hidden layer to BF16: tolerance 3e-2 norm-wise)."""
+    g = gosh()
+    gr = synth.rmat_graph(11, 8, 9)
+    rng = np.random.default_rng(d + hidden)
+    nc = 500
+    din = 2 * d + 1
+    mp = rng.integers(0, nc, gr.n).astype(np.int32)
+    Mc = bf16_round_np(rng.normal(size=(nc, d)) * 0.5)
+    W1 = bf16_round_np(rng.normal(size=(hidden, din)) * 0.2)
+    b1 = rng.normal(size=hidden).astype(np.float32) * 0.1
+    W2 = bf16_round_np(rng.normal(size=(d, hidden)) * 0.2)
+    b2 = rng.normal(size=d).astype(np.float32) * 0.1
+    m = g.Mlp(d, hidden, seed=1)
+    m.set_weights(W1, b1, W2, b2)
+    csr = g.to_device_csr(gr.rowptr, gr.col)
+    Mf = torch.empty((gr.n, d), device="cuda")
+    m.project(torch.from_numpy(Mc.astype(np.float32)).cuda(), torch.from_numpy(mp).cuda(), csr, Mf)
+    X = bf16_round_np(omlp.features(gr.rowptr, gr.col, mp, Mc)).astype(np.float64)
+    Y, _ = omlp.forward(W1, b1.astype(np.float64), W2, b2.astype(np.float64), X)
+    got = Mf.double().cpu().numpy() - Mc[mp]
+    assert rel(got, Y) < TOL, rel(got, Y)
