@@ -22,6 +22,7 @@
 //      keys instead.
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "hierarchy.cuh"
@@ -609,7 +610,18 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
                                            chunk_row.as<int32_t>(), slot_row.as<int32_t>()), note_launch());
     if (nchunks > 0) {
         const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap) + sizeof(int) * kRowWarps;
-        GOSH_TRY_CUDA(cudaFuncSetAttribute(coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // The attribute is process-wide state of the kernel: set it once to the
+        // largest size any level can ask for, so concurrent coarsenings (the
+        // batched entry runs several host threads) never lower it under one
+        // another's launch.
+        static std::once_flag attr_once;
+        static cudaError_t attr_err = cudaSuccess;
+        std::call_once(attr_once, [] {
+            constexpr int64_t w = kBitmapMaxDefault / 32;
+            const size_t most = sizeof(uint32_t) * (size_t)(w + ceil_div(w, 32) + kListCap) + sizeof(int) * kRowWarps;
+            attr_err = cudaFuncSetAttribute(coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        });
+        GOSH_TRY_CUDA(attr_err);
         int per_sm = 0;
         GOSH_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_rows, kRowThreads, smem));
         if (per_sm < 1) per_sm = 1;
