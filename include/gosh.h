@@ -279,6 +279,17 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
  * Returns the kernel count, or -1 if it exceeds cap_tasks. */
 int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int *loads_out, int cap_tasks);
 
+/* Stochastic rounding of FP32 values to a 16-bit table type (dtype GOSH_BF16
+ * or GOSH_F16), exactly as the training kernels round every value they write
+ * (the benchmark spec's 16-bit tables; the paper trains in FP32): value i is rounded
+ * away from zero with probability equal to its distance from the value toward
+ * zero divided by the gap between the two, using 16 random bits from a 32-bit
+ * hash of (seed, i / 2); infinities and NaNs pass unchanged.
+ * x: device float[n]; out: device 16-bit[n]; both 4-byte aligned.
+ * Asynchronous on `stream`.  No counterpart in the paper. */
+gosh_status gosh_round_stochastic(const float *x, void *out, int64_t n, gosh_dtype dtype, uint64_t seed,
+                                  void *stream);
+
 /* EXPANDEMBEDDING (Alg. 2, Sec. 3): M_fine[v] = M_coarse[map[v]] for v < n_fine.
  * map: device int32[n_fine] with values in [0, n_coarse). */
 gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *map,

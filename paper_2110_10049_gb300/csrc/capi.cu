@@ -524,6 +524,39 @@ gosh_status gosh_train_level(const gosh_csr *g, void *M, int level, int epochs, 
     return train_level_impl(g, M, level, epochs, params, (cudaStream_t)stream, loss_per_epoch, n_updates);
 }
 
+}  // extern "C"
+
+namespace gosh {
+namespace {
+// Element i takes the half (i & 1) of the 32-bit hash of pair i / 2, the
+// assignment Store<T>::pack uses for a row's 16-byte vectors.
+__global__ void round_sr_kernel(const float *__restrict__ x, uint16_t *__restrict__ out, int64_t n, uint32_t seed,
+                                int half) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = mix32(seed + (uint32_t)(i >> 1));
+        const uint32_t r16 = (i & 1) ? (r >> 16) : (r & 0xffffu);
+        out[i] = (uint16_t)(half ? f16_sr_bits(x[i], r16) : bf16_sr_bits(x[i], r16));
+    }
+}
+}  // namespace
+}  // namespace gosh
+
+extern "C" {
+
+gosh_status gosh_round_stochastic(const float *x, void *out, int64_t n, gosh_dtype dtype, uint64_t seed,
+                                  void *stream) {
+    clear_error();
+    GOSH_CHECK_ARG(x && out && n >= 0, "NULL pointer or negative n");
+    GOSH_CHECK_ARG(dtype == GOSH_BF16 || dtype == GOSH_F16, "dtype must be GOSH_BF16 or GOSH_F16");
+    if (n == 0) return GOSH_OK;
+    const uint32_t s32 = (uint32_t)seed ^ mix32((uint32_t)(seed >> 32));
+    (round_sr_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(x, static_cast<uint16_t *>(out), n, s32,
+                                                                    dtype == GOSH_F16 ? 1 : 0),
+     note_launch());
+    GOSH_TRY_CUDA(cudaGetLastError());
+    return GOSH_OK;
+}
+
 gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *map, void *M_fine, int64_t n_fine,
                          int d, gosh_dtype dtype, void *stream) {
     clear_error();

@@ -104,6 +104,7 @@ def lib() -> C.CDLL:
             "gosh_mlp_grads": [vp, vp, vp, i64, vp, vp, vp, vp, P(C.c_double), vp],
             "gosh_mlp_train": [vp, P(gosh_csr), vp, vp, vp, i32, i32, i32, f64, i32, i64, vp, P(C.c_double)],
             "gosh_project_learned": [vp, vp, vp, P(gosh_csr), vp, i32, i32, vp],
+            "gosh_round_stochastic": [vp, vp, i64, i32, u64, vp],
         }
         L.gosh_mlp_free.restype = None
         L.gosh_mlp_free.argtypes = [vp]
@@ -271,6 +272,17 @@ def gosh_train_level_noalloc(g, M, level, epochs, params: gosh_params, loss=None
     cg = g.c() if isinstance(g, Csr) else g
     _check("gosh_train_level_noalloc", lib().gosh_train_level_noalloc(
         C.byref(cg), _ptr(M), level, epochs, C.byref(params), _stream(stream), _ptr(loss), _ptr(n_updates)))
+
+
+def gosh_round_stochastic(x, dtype, seed=0, stream=None):
+    """x: torch.float32 device tensor; dtype: torch.bfloat16 / torch.float16 or
+    a GOSH_* code.  Returns the stochastically rounded tensor."""
+    import torch
+    code = dtype if isinstance(dtype, int) else dtype_code(dtype)
+    out = torch.empty(x.shape, dtype=torch_dtype(code), device=x.device)
+    _check("gosh_round_stochastic", lib().gosh_round_stochastic(_ptr(x), _ptr(out), x.numel(), code, seed,
+                                                                _stream(stream)))
+    return out
 
 
 def gosh_project(Mc, map_ptr, Mf, stream=None):
