@@ -115,6 +115,7 @@ typedef struct gosh_large_stats {
     unsigned long long updates;    /* UPDATEEMBED applications */
     int64_t device_bytes;   /* bins allocated on the device */
     double total_ms;        /* wall time of the call */
+    double setup_ms;        /* of which: edge blocks built (host threads, pinned) and bins allocated */
 } gosh_large_stats;
 
 #define GOSH_MAX_LEVELS 64

@@ -21,9 +21,12 @@
 // fresh; an edge bin is refilled after its last kernel).  Victims are chosen
 // by the known future order (farthest next use).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <cstring>
 #include <cmath>
 #include <deque>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -261,34 +264,67 @@ PairLaunch pick_pair_kernel(gosh_dtype dt, int d) {
 }
 
 // Edge block (a, b) of one pair, built once on the host in pinned memory.
+// Pinned host memory for edge blocks, kept across calls (grow-only).  A call
+// that finds it in use by another call takes a private region instead.
+struct PinnedArena {
+    std::mutex mu;
+    char *ptr = nullptr;
+    size_t cap = 0;
+    bool busy = false;
+};
+PinnedArena g_pinned;
+
+struct PinnedLease {
+    char *ptr = nullptr;
+    bool shared = false;
+    gosh_status acquire(size_t bytes) {
+        if (bytes == 0) bytes = 256;
+        {
+            std::lock_guard<std::mutex> lock(g_pinned.mu);
+            if (!g_pinned.busy) {
+                if (g_pinned.cap < bytes) {
+                    if (g_pinned.ptr) cudaFreeHost(g_pinned.ptr);
+                    g_pinned.ptr = nullptr;
+                    g_pinned.cap = 0;
+                    if (cudaMallocHost(&g_pinned.ptr, bytes) != cudaSuccess) {
+                        g_pinned.ptr = nullptr;
+                        cudaGetLastError();
+                        set_error("pinned allocation of %zu bytes of edge blocks failed", bytes);
+                        return GOSH_ERR_OOM;
+                    }
+                    g_pinned.cap = bytes;
+                }
+                g_pinned.busy = true;
+                shared = true;
+                ptr = g_pinned.ptr;
+                return GOSH_OK;
+            }
+        }
+        if (cudaMallocHost(&ptr, bytes) != cudaSuccess) {
+            ptr = nullptr;
+            cudaGetLastError();
+            set_error("pinned allocation of %zu bytes of edge blocks failed", bytes);
+            return GOSH_ERR_OOM;
+        }
+        return GOSH_OK;
+    }
+    ~PinnedLease() {
+        if (shared) {
+            std::lock_guard<std::mutex> lock(g_pinned.mu);
+            g_pinned.busy = false;
+        } else if (ptr) {
+            cudaFreeHost(ptr);
+        }
+    }
+};
+
 struct Block {
     int64_t *rp_ab = nullptr, *rp_ba = nullptr;
     int32_t *col_ab = nullptr, *col_ba = nullptr;
     int64_t m_ab = 0, m_ba = 0;
     size_t bytes = 0;
-    char *base = nullptr;  // one pinned allocation: rp_ab | col_ab | rp_ba | col_ba
+    char *base = nullptr;  // inside the pinned region: rp_ab | col_ab | rp_ba | col_ba
 };
-
-void build_rows(const int64_t *rowptr, const int32_t *col, int64_t a0, int64_t a1, int64_t b0, int64_t b1,
-                int64_t *rp, int32_t *cols_or_null, std::vector<std::pair<int64_t, int64_t>> &ranges) {
-    ranges.resize((size_t)(a1 - a0));
-    int64_t m = 0;
-    rp[0] = 0;
-    for (int64_t u = a0; u < a1; ++u) {
-        const int32_t *row = col + rowptr[u], *end = col + rowptr[u + 1];
-        const int32_t *lo = std::lower_bound(row, end, (int32_t)b0);
-        const int32_t *hi = std::lower_bound(lo, end, (int32_t)b1);
-        ranges[(size_t)(u - a0)] = {lo - col, hi - col};
-        m += hi - lo;
-        rp[u - a0 + 1] = m;
-    }
-    if (cols_or_null)
-        for (int64_t u = a0; u < a1; ++u) {
-            const auto r = ranges[(size_t)(u - a0)];
-            int32_t *out = cols_or_null + rp[u - a0];
-            for (int64_t p = r.first; p < r.second; ++p) *out++ = col[p] - (int32_t)b0;
-        }
-}
 
 struct Sched {
     int K, PB, SB;
@@ -384,65 +420,106 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     for (int i = 0; i <= K; ++i) start[i] = n * i / K;
 
     // ---- edge blocks (pinned, built on host threads) ----
+    // A block side (u in V^a, entries in V^b) is built in row chunks spread
+    // over every host thread: per row the sub-range of its sorted row that
+    // falls in V^b (two binary searches), a prefix sum of the counts, then the
+    // entries with local ids.  All blocks share one pinned region, kept across
+    // calls (grow-only: pinning host memory costs far more than building).
     std::vector<std::pair<int, int>> order;
     large_pair_order(K, order);
     std::vector<Block> blocks(order.size());
     size_t max_block = 0;
-    {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    struct Side {
+        int blk;
+        bool ab;
+        int64_t a0, a1, b0, b1;
+        std::vector<int64_t> lo, rp;  // per row: first entry in V^b; prefix of the counts
+    };
+    std::vector<Side> sides;
+    for (size_t i = 0; i < order.size(); ++i) {
+        const int a = order[i].first, b = order[i].second;
+        sides.push_back({(int)i, true, start[a], start[a + 1], start[b], start[b + 1], {}, {}});
+        if (a != b) sides.push_back({(int)i, false, start[b], start[b + 1], start[a], start[a + 1], {}, {}});
+    }
+    constexpr int64_t kChunkRows = 32768;
+    std::vector<std::pair<int, int64_t>> items;  // (side, first row offset)
+    for (size_t j = 0; j < sides.size(); ++j) {
+        Side &sd = sides[j];
+        sd.lo.resize((size_t)(sd.a1 - sd.a0));
+        sd.rp.assign((size_t)(sd.a1 - sd.a0 + 1), 0);
+        for (int64_t r = 0; r < sd.a1 - sd.a0; r += kChunkRows) items.push_back({(int)j, r});
+    }
+    const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    auto parallel_items = [&](auto &&body) {
+        std::atomic<size_t> next{0};
         std::vector<std::thread> th;
-        const int nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        std::vector<gosh_status> st(nt, GOSH_OK);
         for (int t = 0; t < nt; ++t)
-            th.emplace_back([&, t]() {
-                std::vector<std::pair<int64_t, int64_t>> ranges;
-                for (size_t i = t; i < order.size(); i += nt) {
-                    const int a = order[i].first, b = order[i].second;
-                    const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
-                    std::vector<int64_t> rpa(na + 1), rpb(a != b ? nb + 1 : 1);
-                    build_rows(g->rowptr, g->col, start[a], start[a + 1], start[b], start[b + 1], rpa.data(), nullptr,
-                               ranges);
-                    if (a != b)
-                        build_rows(g->rowptr, g->col, start[b], start[b + 1], start[a], start[a + 1], rpb.data(),
-                                   nullptr, ranges);
-                    Block &B = blocks[i];
-                    B.m_ab = rpa[na];
-                    B.m_ba = a != b ? rpb[nb] : 0;
-                    const size_t s1 = sizeof(int64_t) * (na + 1), s2 = sizeof(int32_t) * B.m_ab;
-                    const size_t s3 = a != b ? sizeof(int64_t) * (nb + 1) : 0, s4 = sizeof(int32_t) * B.m_ba;
-                    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-                    B.bytes = al(s1) + al(s2) + al(s3) + al(s4);
-                    if (cudaMallocHost(&B.base, B.bytes) != cudaSuccess) {
-                        st[t] = GOSH_ERR_OOM;
-                        return;
-                    }
-                    B.rp_ab = reinterpret_cast<int64_t *>(B.base);
-                    B.col_ab = reinterpret_cast<int32_t *>(B.base + al(s1));
-                    B.rp_ba = reinterpret_cast<int64_t *>(B.base + al(s1) + al(s2));
-                    B.col_ba = reinterpret_cast<int32_t *>(B.base + al(s1) + al(s2) + al(s3));
-                    build_rows(g->rowptr, g->col, start[a], start[a + 1], start[b], start[b + 1], B.rp_ab, B.col_ab,
-                               ranges);
-                    if (a != b)
-                        build_rows(g->rowptr, g->col, start[b], start[b + 1], start[a], start[a + 1], B.rp_ba,
-                                   B.col_ba, ranges);
-                }
+            th.emplace_back([&]() {
+                for (size_t it = next.fetch_add(1); it < items.size(); it = next.fetch_add(1)) body(items[it]);
             });
         for (auto &x : th) x.join();
-        for (auto x : st)
-            if (x != GOSH_OK) {
-                for (auto &b : blocks)
-                    if (b.base) cudaFreeHost(b.base);
-                set_error("pinned allocation of edge blocks failed");
-                return x;
-            }
-        for (auto &b : blocks) max_block = std::max(max_block, b.bytes);
-    }
-    struct BlockFree {
-        std::vector<Block> &v;
-        ~BlockFree() {
-            for (auto &b : v)
-                if (b.base) cudaFreeHost(b.base);
+    };
+    parallel_items([&](const std::pair<int, int64_t> &it) {
+        Side &sd = sides[it.first];
+        const int64_t r1 = std::min(it.second + kChunkRows, sd.a1 - sd.a0);
+        for (int64_t r = it.second; r < r1; ++r) {
+            const int64_t u = sd.a0 + r;
+            const int32_t *row = g->col + g->rowptr[u], *end = g->col + g->rowptr[u + 1];
+            const int32_t *lo = std::lower_bound(row, end, (int32_t)sd.b0);
+            const int32_t *hi = std::lower_bound(lo, end, (int32_t)sd.b1);
+            sd.lo[(size_t)r] = lo - g->col;
+            sd.rp[(size_t)r + 1] = hi - lo;
         }
-    } block_free{blocks};
+    });
+    for (Side &sd : sides)
+        for (size_t r = 1; r < sd.rp.size(); ++r) sd.rp[r] += sd.rp[r - 1];
+    size_t total_bytes = 0;
+    for (size_t i = 0; i < blocks.size(); ++i) {
+        Block &B = blocks[i];
+        const int a = order[i].first, b = order[i].second;
+        const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
+        for (const Side &sd : sides)
+            if (sd.blk == (int)i) (sd.ab ? B.m_ab : B.m_ba) = sd.rp.back();
+        B.bytes = al(sizeof(int64_t) * (na + 1)) + al(sizeof(int32_t) * B.m_ab) +
+                  al(a != b ? sizeof(int64_t) * (nb + 1) : 0) + al(sizeof(int32_t) * B.m_ba);
+        max_block = std::max(max_block, B.bytes);
+        total_bytes += B.bytes;
+    }
+    PinnedLease lease;
+    GOSH_TRY(lease.acquire(total_bytes));
+    {
+        size_t off = 0;
+        for (size_t i = 0; i < blocks.size(); ++i) {
+            Block &B = blocks[i];
+            const int a = order[i].first, b = order[i].second;
+            const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
+            B.base = lease.ptr + off;
+            off += B.bytes;
+            B.rp_ab = reinterpret_cast<int64_t *>(B.base);
+            B.col_ab = reinterpret_cast<int32_t *>(B.base + al(sizeof(int64_t) * (na + 1)));
+            B.rp_ba = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(B.col_ab) + al(sizeof(int32_t) * B.m_ab));
+            B.col_ba = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(B.rp_ba) +
+                                                   al(a != b ? sizeof(int64_t) * (nb + 1) : 0));
+        }
+        for (const Side &sd : sides) {
+            Block &B = blocks[sd.blk];
+            std::memcpy(sd.ab ? B.rp_ab : B.rp_ba, sd.rp.data(), sizeof(int64_t) * sd.rp.size());
+        }
+    }
+    parallel_items([&](const std::pair<int, int64_t> &it) {
+        const Side &sd = sides[it.first];
+        Block &B = blocks[sd.blk];
+        int32_t *out = sd.ab ? B.col_ab : B.col_ba;
+        const int64_t r1 = std::min(it.second + kChunkRows, sd.a1 - sd.a0);
+        const int32_t b0 = (int32_t)sd.b0;
+        for (int64_t r = it.second; r < r1; ++r) {
+            const int32_t *src = g->col + sd.lo[(size_t)r];
+            int32_t *dst = out + sd.rp[(size_t)r];
+            const int64_t cnt = sd.rp[(size_t)r + 1] - sd.rp[(size_t)r];
+            for (int64_t q = 0; q < cnt; ++q) dst[q] = src[q] - b0;
+        }
+    });
     int64_t part_rows = 0;
     for (int i = 0; i < K; ++i) part_rows = std::max(part_rows, start[i + 1] - start[i]);
     const size_t bin_bytes = row * part_rows;
@@ -513,6 +590,7 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     std::vector<cudaEvent_t> bin_ready(p->p_gpu, nullptr);
     std::vector<cudaEvent_t> host_fresh(K, nullptr);               // D2H of part x completed
     std::vector<cudaEvent_t> ebin_free(p->s_gpu, nullptr);
+    const auto t_setup = std::chrono::steady_clock::now();
     int64_t swaps = 0, h2d = 0, d2h = 0, block_bytes = 0;
     const int grid = num_sms() * 2;
     char *hM = static_cast<char *>(M);
@@ -635,6 +713,7 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
         stats->device_bytes = (int64_t)need;
         stats->total_ms =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        stats->setup_ms = std::chrono::duration<double, std::milli>(t_setup - t_start).count();
     }
     (void)nnz;
     return GOSH_OK;

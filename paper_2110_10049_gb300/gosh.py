@@ -48,7 +48,8 @@ class gosh_params(C.Structure):
 class gosh_large_stats(C.Structure):
     _fields_ = [("parts", C.c_int), ("rounds", C.c_int), ("kernels", C.c_int64), ("swaps", C.c_int64),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("positives", C.c_ulonglong),
-                ("updates", C.c_ulonglong), ("device_bytes", C.c_int64), ("total_ms", C.c_double)]
+                ("updates", C.c_ulonglong), ("device_bytes", C.c_int64), ("total_ms", C.c_double),
+                ("setup_ms", C.c_double)]
 
 
 class gosh_stats(C.Structure):
