@@ -533,7 +533,7 @@ namespace {
 __global__ void round_sr_kernel(const float *__restrict__ x, uint16_t *__restrict__ out, int64_t n, uint32_t seed,
                                 int half) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = mix32(seed + (uint32_t)(i >> 1));
+        const uint32_t r = sr_pair_bits(seed + (uint32_t)(i >> 1));
         const uint32_t r16 = (i & 1) ? (r >> 16) : (r & 0xffffu);
         out[i] = (uint16_t)(half ? f16_sr_bits(x[i], r16) : bf16_sr_bits(x[i], r16));
     }

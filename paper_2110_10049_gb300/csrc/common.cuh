@@ -165,11 +165,20 @@ template <> struct Store<float> {
 
 // BF16 stochastic rounding: add 16 random bits below the BF16 mantissa of the
 // FP32 pattern, then truncate.  Rounds |x| up with probability equal to its
-// distance from the lower neighbour (unbiased); NaN/Inf are truncated.
+// distance from the lower neighbour (unbiased).  An infinity's low half is
+// zero, so the addition cannot carry out of it, and a NaN keeps its exponent
+// and a nonzero mantissa: specials pass unchanged without a test; the largest
+// finite value may round up to infinity, as rounding away from zero must.
 __device__ __forceinline__ uint32_t bf16_sr_bits(float x, uint32_t r16) {
-    uint32_t b = __float_as_uint(x);
-    if ((b & 0x7f800000u) != 0x7f800000u) b += (r16 & 0xffffu);
-    return b >> 16;
+    return (__float_as_uint(x) + (r16 & 0xffffu)) >> 16;
+}
+
+// 32 random bits for the pair of values with counter c (seed-relative): an
+// odd multiply and an xorshift, both bijections, so every 16-bit half is
+// uniform when the seed is (the per-source seed is a full hash).
+__device__ __forceinline__ uint32_t sr_pair_bits(uint32_t c) {
+    c *= 0x9e3779b1u;
+    return c ^ (c >> 15);
 }
 
 template <> struct Store<__nv_bfloat16> {
@@ -182,32 +191,38 @@ template <> struct Store<__nv_bfloat16> {
             f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
         }
     }
-    // Stochastic rounding with bits mix32(seed + base + i/2) (two 16-bit halves
-    // per word); `f` is overwritten with the stored values.
+    // Stochastic rounding with bits sr_pair_bits(seed + base + i/2) (two 16-bit
+    // halves per word, as bf16_sr_bits); one byte permute keeps the upper
+    // halves of both sums.  `f` is overwritten with the stored values.
     __device__ __forceinline__ static uint4 pack(float *f, uint32_t seed, uint32_t base) {
         uint32_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const uint32_t r = mix32(seed + base + (uint32_t)i);
-            const uint32_t lo = bf16_sr_bits(f[2 * i], r & 0xffffu);
-            const uint32_t hi = bf16_sr_bits(f[2 * i + 1], r >> 16);
-            w[i] = lo | (hi << 16);
-            f[2 * i] = __uint_as_float(lo << 16);
-            f[2 * i + 1] = __uint_as_float(hi << 16);
+            const uint32_t r = sr_pair_bits(seed + base + (uint32_t)i);
+            const uint32_t a = __float_as_uint(f[2 * i]) + (r & 0xffffu);
+            const uint32_t b = __float_as_uint(f[2 * i + 1]) + (r >> 16);
+            w[i] = __byte_perm(a, b, 0x7632);
+            f[2 * i] = __uint_as_float(w[i] << 16);
+            f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
         }
         return make_uint4(w[0], w[1], w[2], w[3]);
     }
     __device__ __forceinline__ static float round_nearest(float x) {
         return __bfloat162float(__float2bfloat16_rn(x));
     }
-    // Differences nw - old of 8 values, rounded to nearest and packed (exact
-    // when they need at most 8 significant bits, e.g. a few ulps).
-    __device__ __forceinline__ static uint4 pack_diff(const float *nw, const float *old) {
+    // Packed differences nw - old of 8 values (nw packed; old exact BF16
+    // values as floats, packed losslessly by one byte permute per pair), by a
+    // packed BF16 subtraction rounded to nearest: exact when a difference
+    // needs at most 8 significant bits, e.g. a few ulps.
+    __device__ __forceinline__ static uint4 change(const uint4 &nw, const float *old) {
+        const uint32_t n4[4] = {nw.x, nw.y, nw.z, nw.w};
         uint32_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(nw[2 * i] - old[2 * i], nw[2 * i + 1] - old[2 * i + 1]);
-            w[i] = *reinterpret_cast<const uint32_t *>(&h);
+            const uint32_t o = __byte_perm(__float_as_uint(old[2 * i]), __float_as_uint(old[2 * i + 1]), 0x7632);
+            const __nv_bfloat162 d = __hsub2(*reinterpret_cast<const __nv_bfloat162 *>(&n4[i]),
+                                             *reinterpret_cast<const __nv_bfloat162 *>(&o));
+            w[i] = *reinterpret_cast<const uint32_t *>(&d);
         }
         return make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -247,7 +262,7 @@ template <> struct Store<__half> {
         uint32_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const uint32_t r = mix32(seed + base + (uint32_t)i);
+            const uint32_t r = sr_pair_bits(seed + base + (uint32_t)i);
             const uint32_t lo = f16_sr_bits(f[2 * i], r & 0xffffu);
             const uint32_t hi = f16_sr_bits(f[2 * i + 1], r >> 16);
             w[i] = lo | (hi << 16);
@@ -259,12 +274,16 @@ template <> struct Store<__half> {
     __device__ __forceinline__ static float round_nearest(float x) {
         return __half2float(__float2half_rn(x));
     }
-    __device__ __forceinline__ static uint4 pack_diff(const float *nw, const float *old) {
+    // Packed differences nw - old (old exact FP16 values as floats), by a packed
+    // FP16 subtraction rounded to nearest.
+    __device__ __forceinline__ static uint4 change(const uint4 &nw, const float *old) {
+        const uint32_t n4[4] = {nw.x, nw.y, nw.z, nw.w};
         uint32_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const __half2 h = __floats2half2_rn(nw[2 * i] - old[2 * i], nw[2 * i + 1] - old[2 * i + 1]);
-            w[i] = *reinterpret_cast<const uint32_t *>(&h);
+            const __half2 o = __floats2half2_rn(old[2 * i], old[2 * i + 1]);
+            const __half2 d = __hsub2(*reinterpret_cast<const __half2 *>(&n4[i]), o);
+            w[i] = *reinterpret_cast<const uint32_t *>(&d);
         }
         return make_uint4(w[0], w[1], w[2], w[3]);
     }

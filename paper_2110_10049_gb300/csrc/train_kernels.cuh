@@ -78,8 +78,8 @@ __device__ __forceinline__ void red_row16(T *__restrict__ p, float *f, const flo
 #pragma unroll
     for (int v = 0; v < E / PV; ++v) {
         const uint32_t base = (uint32_t)((slot * D + elem0 + v * PV) >> 1);
-        Store<T>::pack(f + v * PV, sr, base);
-        Store<T>::red_add(p + v * PV, Store<T>::pack_diff(f + v * PV, old + v * PV));
+        const uint4 nw = Store<T>::pack(f + v * PV, sr, base);
+        Store<T>::red_add(p + v * PV, Store<T>::change(nw, old + v * PV));
     }
 }
 
