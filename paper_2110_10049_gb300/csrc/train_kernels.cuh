@@ -89,6 +89,32 @@ __device__ __forceinline__ void red_row(float *p, const float *f) {
     for (int v = 0; v < E / 4; ++v) red_add_v4(p + 4 * v, f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
 }
 
+// d = a * b + c on two FP32 lanes at once (fma.rn.f32x2, sm_100 and later).
+__device__ __forceinline__ void ffma2(float &d0, float &d1, float a0, float a1, float b0, float b1, float c0, float c1) {
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
+
+// sum over e of x[e] * y[e] (E even): two interleaved partial sums.
+template <int E>
+__device__ __forceinline__ float dot2(const float *x, const float *y) {
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < E; e += 2) ffma2(s0, s1, x[e], x[e + 1], y[e], y[e + 1], s0, s1);
+    return s0 + s1;
+}
+
+// y[e] += a * x[e] (E even).
+template <int E>
+__device__ __forceinline__ void axpy2(float *y, const float *x, float a) {
+#pragma unroll
+    for (int e = 0; e < E; e += 2) ffma2(y[e], y[e + 1], x[e], x[e + 1], a, a, y[e], y[e + 1]);
+}
+
 template <int L>
 __device__ __forceinline__ float group_sum(float x) {
 #pragma unroll
@@ -201,22 +227,18 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
                 for (int s = 0; s < P; ++s) {
                     const int t = p0 + s;
                     const bool ok = us[s] >= 0;
-                    float part = 0.0f;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) part = fmaf(r[e], row[s][e], part);
+                    const float part = dot2<E>(r, row[s]);
                     const float x = group_sum<L>(part);
                     const float b = t == 0 ? 1.0f : 0.0f;
                     const float sig = __frcp_rn(1.0f + __expf(-x));
                     const float score = ok ? (b - sig) * a.lr : 0.0f;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) r[e] = fmaf(row[s][e], score, r[e]);
+                    axpy2<E>(r, row[s], score);
                     float old16[RED16 ? E : 1];
                     if (RED16) {
 #pragma unroll
                         for (int e = 0; e < E; ++e) old16[e] = row[s][e];
                     }
-#pragma unroll
-                    for (int e = 0; e < E; ++e) row[s][e] = fmaf(r[e], score, row[s][e]);
+                    axpy2<E>(row[s], r, score);
                     if (ok) {
                         if constexpr (RED16) {
                             red_row16<T, D, E>(M + (int64_t)us[s] * D + gl * E, row[s], old16, sr, t, gl * E);

@@ -198,21 +198,17 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
 #pragma unroll
                     for (int e = 0; e < E; ++e) row[e] = 0.0f;
                 }
-                float part = 0.0f;
-#pragma unroll
-                for (int e = 0; e < E; ++e) part = fmaf(r[e], row[e], part);
+                const float part = dot2<E>(r, row);
                 const float x = group_sum<L>(part);
                 const float b = t == 0 ? 1.0f : 0.0f;
                 const float score = ok ? (b - __frcp_rn(1.0f + __expf(-x))) * a.lr : 0.0f;
-#pragma unroll
-                for (int e = 0; e < E; ++e) r[e] = fmaf(row[e], score, r[e]);
+                axpy2<E>(r, row, score);
                 float old16[RED16 ? E : 1];
                 if (RED16) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) old16[e] = row[e];
                 }
-#pragma unroll
-                for (int e = 0; e < E; ++e) row[e] = fmaf(r[e], score, row[e]);
+                axpy2<E>(row, r, score);
                 if (ok) {
                     if constexpr (RED16) {
                         red_row16<T, D, E>(M + (int64_t)uid * D + gl * E, row, old16, sr, t, gl * E);
