@@ -105,13 +105,16 @@ int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) /
 
 // Sources per warp tile.  A warp walks its tile in tile / (32/L) dependent
 // rounds, so small levels (few tiles, far fewer than the GPU's warps) take
-// short tiles (4 below 2^16 rows; below 2^19, 16, or 8 for 16-bit tables);
+// short tiles (4 below 2^16 rows; below 2^19, 32 for lock-free atomic changes,
+// 8 for 16-bit plain stores, 16 in the deterministic mode);
 // large levels take 32 to amortise the draws.  A multiple of 32/L in
 // [32/L, 32]; params->vertices_per_warp overrides.
 int tile_vertices(const gosh_params *p, int64_t n, int lanes) {
     const int G = 32 / lanes;
     int t = p->vertices_per_warp;
-    const int mid = (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC) ? 8 : 16;
+    const bool red16 = p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC && !p->plain_stores;
+    const bool f32_lockfree = p->dtype == GOSH_F32 && p->mode != GOSH_DETERMINISTIC;
+    const int mid = (red16 || f32_lockfree) ? 32 : (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC ? 8 : 16);
     if (t <= 0) t = n >= (int64_t(1) << 19) ? 32 : (n >= (int64_t(1) << 16) ? mid : 4);
     t = t < G ? G : (t > 32 ? 32 : t);
     return t / G * G;
@@ -133,12 +136,14 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
     // Defaults by level size, from per-level sweeps of lanes per row L,
     // samples per pass P and tile on the R-MAT 20 hierarchy (d = 128, k = 3;
     // L0 = one 16-byte vector per lane):
-    //  - FP32 lock-free: above 2^19 rows every row staged by TMA (L0); from
-    //    2^14 rows, registers with L0 lanes and P = 2; below, L0/2 lanes and
-    //    P = 4 (shorter dependency chains on the latency-bound small levels);
-    //  - 16-bit tables: registers; L0/2 lanes (two vectors per lane, more
-    //    sources in flight) and P = 2 (P = 4 with plain stores), except from
-    //    2^16 to 2^19 rows, where L0 lanes and P = 4 keep more warps resident.
+    //  - FP32 lock-free: above 2^19 rows every row staged by TMA (L0); below,
+    //    registers with P = 4 and L0 lanes from 2^14 rows, L0/2 lanes under
+    //    (shorter dependency chains on the latency-bound small levels);
+    //  - 16-bit tables (atomic changes): registers; above 2^19 rows L0/2
+    //    lanes (two vectors per lane, more sources in flight) and P = 2;
+    //    below, L0 lanes (one vector per lane: 80 registers, 24 warps per
+    //    SM) with P = 2, or P = 4 under 2^14 rows; with plain stores, L0/2
+    //    lanes and P = 4 except L0 lanes from 2^16 to 2^19 rows.
     if (!det && lanes <= 0 && pass == 0) {
         if (dtype == GOSH_F32 && mode == kModeRed) {
             if (n >= (int64_t(1) << 19) && ns <= 6) {
@@ -146,15 +151,19 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
                 pass = ns <= 4 ? -4 : -6;
             } else if (n >= (int64_t(1) << 14)) {
                 lanes = nat;
-                pass = 2;
+                pass = 4;
             } else {
                 lanes = nat >= 2 ? nat / 2 : nat;
                 pass = 4;
             }
+        } else if (dtype != GOSH_F32 && mode == kModeRed) {
+            const bool large = n >= (int64_t(1) << 19);
+            lanes = (large && nat >= 4) ? nat / 2 : nat;
+            pass = (large || n >= (int64_t(1) << 14)) ? 2 : 4;
         } else if (dtype != GOSH_F32) {
             const bool mid = n >= (int64_t(1) << 16) && n < (int64_t(1) << 19);
             lanes = (mid || nat < 4) ? nat : nat / 2;
-            pass = (mode == kModeStore || mid) ? 4 : 2;
+            pass = 4;
         }
     }
     if (lanes <= 0) lanes = (!det && dtype != GOSH_F32 && nat >= 4) ? nat / 2 : nat;

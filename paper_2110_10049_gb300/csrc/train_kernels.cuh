@@ -293,12 +293,20 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
     }
 }
 
+// Resident blocks the register allocation must allow: three (80 registers,
+// 24 warps per SM) for lock-free variants whose lanes hold at most 8 values of
+// a row, two (128 registers) otherwise: longer slices and the deterministic
+// mode's larger passes would spill under three.
+constexpr int train_min_blocks(int values_per_lane, int mode) {
+    return (mode != kModeDet && values_per_lane <= 8) ? 3 : 2;
+}
+
 /*
  * One epoch (Hogwild) or one snapshot batch (deterministic): the warps of the
- * grid take tiles of 32 consecutive sources of [src_begin, src_end) in turn.
+ * grid take tiles of consecutive sources of [src_begin, src_end) in turn.
  */
 template <typename T, int D, int L, int P, int MODE>
-__global__ void __launch_bounds__(kTrainWarps * 32) train_kernel(TrainArgs a) {
+__global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, MODE)) train_kernel(TrainArgs a) {
     __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
     __shared__ uint32_t s_sr[kTrainWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
