@@ -237,7 +237,6 @@ __global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *_
 // does not matter: a bitmap is a set.
 constexpr int kChunk = 4096;
 constexpr int kRowThreads = 128;
-constexpr int kRowWarps = kRowThreads / 32;
 constexpr int kSumGroup = 32;                // summary words read back per step
 constexpr int kListCap = kSumGroup * 32;     // nonzero bitmap words per step
 constexpr int64_t kBitmapMaxDefault = int64_t(1) << 19;
@@ -253,16 +252,17 @@ __global__ void member_keys(const int64_t *__restrict__ rowptr, int64_t n, const
 }
 
 // From the members sorted by cluster: cstart[c] = first member of cluster c
-// (cstart[nc] = number of members with neighbours), each member's row start
-// and degree.  A position whose key differs from its predecessor's writes the
-// starts of every cluster in between (clusters without such members are empty).
+// (cstart[nc] = number of members with neighbours), each member's degree and
+// each vertex's member position inv[v].  A position whose key differs from its
+// predecessor's writes the starts of every cluster in between (clusters
+// without such members are empty).
 __global__ void member_layout(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
                               const int64_t *__restrict__ rowptr, int64_t n, uint32_t nc,
-                              int64_t *__restrict__ cstart, int64_t *__restrict__ mrow, int64_t *__restrict__ mdeg) {
+                              int64_t *__restrict__ cstart, int32_t *__restrict__ inv, int64_t *__restrict__ mdeg) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = val[i];
         const int64_t k = key[i];
-        mrow[i] = rowptr[v];
+        inv[v] = (int32_t)i;
         mdeg[i] = rowptr[v + 1] - rowptr[v];
         const int64_t kp = i == 0 ? -1 : (int64_t)key[i - 1];
         for (int64_t c = kp + 1; c <= k; ++c) cstart[c] = i;
@@ -271,12 +271,61 @@ __global__ void member_layout(const uint32_t *__restrict__ key, const uint32_t *
     }
 }
 
+// Cluster id of every CSR entry, written in member order: entry p of row r
+// goes to vb[moff[inv r] + p - rowptr[r]], so the entries of cluster c's
+// members are vb[moff[cstart c] .. moff[cstart c+1]).  Balanced over entries:
+// each warp takes kEntriesPerWarp consecutive entries; a lane finds the row of
+// its first entry by binary search and then walks forward.
+__global__ void __launch_bounds__(256) member_entries(const int64_t *__restrict__ rowptr,
+                                                      const int32_t *__restrict__ col, int64_t n,
+                                                      const int32_t *__restrict__ map,
+                                                      const int32_t *__restrict__ inv,
+                                                      const int64_t *__restrict__ moff, int32_t *__restrict__ vb) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nnz = rowptr[n];
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = wid * kEntriesPerWarp; base < nnz; base += wstride * kEntriesPerWarp) {
+        int64_t p = base + lane;
+        if (p >= nnz) continue;
+        int64_t lo = 0, hi = n;  // last row with rowptr[row] <= p
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(rowptr + mid) <= p) lo = mid; else hi = mid;
+        }
+        int64_t r = lo;
+        int64_t rend = __ldg(rowptr + r + 1);
+        int64_t shift = __ldg(moff + __ldg(inv + r)) - __ldg(rowptr + r);
+        const int64_t end = base + kEntriesPerWarp < nnz ? base + kEntriesPerWarp : nnz;
+        // four entries per lane per step, their loads issued together
+        for (; p < end; p += 128) {
+            int64_t dst[4];
+            int32_t y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t pu = p + 32 * u;
+                while (pu < end && rend <= pu) {
+                    ++r;
+                    rend = __ldg(rowptr + r + 1);
+                    if (rend > pu) shift = __ldg(moff + __ldg(inv + r)) - __ldg(rowptr + r);
+                }
+                dst[u] = pu + shift;
+                y[u] = pu < end ? __ldg(col + pu) : 0;
+            }
+            int32_t b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = __ldg(map + y[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (p + 32 * u < end) vb[dst[u]] = b[u];
+        }
+    }
+}
+
 __global__ void row_chunks(const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff, int64_t nc,
-                           int32_t *__restrict__ nchunk, uint8_t *__restrict__ multi, int64_t *__restrict__ rbase) {
+                           int32_t *__restrict__ nchunk, uint8_t *__restrict__ multi) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rb = moff[cstart[c]];
-        rbase[c] = rb;
-        const int64_t len = moff[cstart[c + 1]] - rb;
+        const int64_t len = moff[cstart[c + 1]] - moff[cstart[c]];
         const int64_t k = (len + kChunk - 1) / kChunk;
         nchunk[c] = (int32_t)k;
         multi[c] = k > 1 ? 1 : 0;
@@ -355,81 +404,141 @@ __device__ int read_bits(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int
     return nout;
 }
 
-__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
-
-// Last member j in [lo, hi) with moff[j] <= p (moff ascending, moff[lo] <= p).
-__device__ __forceinline__ int64_t member_of(const int64_t *__restrict__ moff, int64_t lo, int64_t hi, int64_t p) {
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (__ldg(moff + mid) <= p) lo = mid; else hi = mid;
+// The same read-back by one warp (shuffle scans, no block barrier): the
+// chunk's words are few, so a single warp walks them faster than the block's
+// barrier-separated scans.
+__device__ __forceinline__ int warp_incl_scan(int x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    return lo;
+    return x;
 }
 
+template <bool kClear>
+__device__ int read_bits_warp(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int32_t *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    int nout = 0;
+    for (int s0 = 0; s0 < n0; s0 += 32) {
+        const int s = s0 + lane;
+        uint32_t sw = s < n0 ? sum[s] : 0u;
+        if (kClear && s < n0 && sw) sum[s] = 0;
+        const int c = __popc(sw);
+        const int incl = warp_incl_scan(c);
+        const int nlist = __shfl_sync(0xffffffffu, incl, 31);
+        int k = incl - c;
+        while (sw) {
+            list[k++] = s * 32 + (__ffs(sw) - 1);
+            sw &= sw - 1;
+        }
+        __syncwarp();
+        for (int i0 = 0; i0 < nlist; i0 += 32) {
+            const int i = i0 + lane;
+            int w = 0;
+            uint32_t bits = 0;
+            if (i < nlist) {
+                w = list[i];
+                bits = bm[w];
+                if (kClear) bm[w] = 0;
+            }
+            const int cb = __popc(bits);
+            const int ib = warp_incl_scan(cb);
+            int at = nout + ib - cb;
+            while (bits) {
+                out[at++] = w * 32 + (__ffs(bits) - 1);
+                bits &= bits - 1;
+            }
+            nout += __shfl_sync(0xffffffffu, ib, 31);
+        }
+        __syncwarp();
+    }
+    return nout;
+}
+
+// Set bits of a shared-memory bitmap counted (and cleared) by one warp.
+__device__ __forceinline__ int count_bits_warp(uint32_t *bm, uint32_t *sum, int n0) {
+    const int lane = threadIdx.x & 31;
+    int total = 0;
+    for (int s0 = 0; s0 < n0; s0 += 32) {
+        const int s = s0 + lane;
+        uint32_t sw = s < n0 ? sum[s] : 0u;
+        int c = 0;
+        if (sw) sum[s] = 0;
+        while (sw) {
+            const int w = s * 32 + (__ffs(sw) - 1);
+            sw &= sw - 1;
+            c += __popc(bm[w]);
+            bm[w] = 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        total += c;
+    }
+    return total;
+}
+
+// One pass over the chunks of the coarse rows (cluster ids of their member
+// entries in vb).  kWrite = false: single-chunk rows count their distinct ids
+// into count[c]; rows of several chunks OR their chunk bitmaps into their
+// global bitmap.  kWrite = true: single-chunk rows rebuild the bitmap and read
+// it back, sorted, into col_out at rowptr[c] (multi-chunk rows are left to
+// coarse_rows_multi).
+template <bool kWrite>
 __global__ void __launch_bounds__(kRowThreads) coarse_rows(
-    const int32_t *__restrict__ col, const int32_t *__restrict__ map, const int64_t *__restrict__ cstart,
-    const int64_t *__restrict__ mrow, const int64_t *__restrict__ moff, const int64_t *__restrict__ chunk_start,
-    const int32_t *__restrict__ chunk_row, const uint8_t *__restrict__ multi, const int64_t *__restrict__ slot,
-    int64_t nchunks, int words, int n0, int list_cap, uint32_t *__restrict__ gbm, uint32_t *__restrict__ gsum,
-    int32_t *__restrict__ scratch, int32_t *__restrict__ count) {
+    const int32_t *__restrict__ vb, const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff,
+    const int64_t *__restrict__ chunk_start, const int32_t *__restrict__ chunk_row, const uint8_t *__restrict__ multi,
+    const int64_t *__restrict__ slot, int64_t nchunks, int words, int n0, int list_cap, uint32_t *__restrict__ gbm,
+    uint32_t *__restrict__ gsum, int32_t *__restrict__ count, const int64_t *__restrict__ rowptr,
+    int32_t *__restrict__ col_out) {
     extern __shared__ uint32_t smem[];
     uint32_t *bm = smem;
     uint32_t *sum = bm + words;
     int32_t *list = reinterpret_cast<int32_t *>(sum + n0);
-    int *wsum = reinterpret_cast<int *>(list + list_cap);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    (void)list_cap;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < words + n0; i += kRowThreads) smem[i] = 0;
     __syncthreads();
     for (int64_t t = blockIdx.x; t < nchunks; t += gridDim.x) {
         const int32_t c = chunk_row[t];
-        const int64_t jlo = cstart[c], jhi = cstart[c + 1];
-        const int64_t rb = moff[jlo], re = moff[jhi];
+        const bool many = multi[c] != 0;
+        if (kWrite && many) continue;  // the same for every thread of the block
+        const int64_t rb = moff[cstart[c]], re = moff[cstart[c + 1]];
         const int64_t e0 = rb + (t - chunk_start[c]) * kChunk;
         const int64_t e1 = e0 + kChunk < re ? e0 + kChunk : re;
-        // Warp w takes a contiguous quarter of the chunk, 32 entries per step.
-        // The members of a step's entries follow from the next 32 member
-        // boundaries (one coalesced load; boundaries are distinct because
-        // every member has an entry): lane L's entry lies in member
-        // j0 + #{boundaries <= base + L}.
-        const int64_t per = ceil_div_dev(e1 - e0, (int64_t)kRowWarps * 32) * 32;
-        int64_t base = e0 + warp * per;
-        const int64_t wend = base + per < e1 ? base + per : e1;
-        if (base < wend) {
-            int64_t j0 = member_of(moff, jlo, jhi, base);
-            for (; base < wend; base += 32) {
-                const int64_t jb = j0 + 1 + lane;
-                const int64_t r = jb <= jhi ? __ldg(moff + jb) - base : 64;
-                const uint32_t starts = __reduce_or_sync(0xffffffffu, r < 32 ? 1u << r : 0u);
-                const bool next32 = __any_sync(0xffffffffu, r == 32);
-                const int64_t p = base + lane;
-                if (p < wend) {
-                    const int64_t j = j0 + __popc(starts & ((2u << lane) - 1u));
-                    const int32_t y = __ldg(col + __ldg(mrow + j) + (p - __ldg(moff + j)));
-                    const int32_t b = __ldg(map + y);
-                    if (b != c) {
-                        const uint32_t old = atomicOr(bm + (b >> 5), 1u << (b & 31));
-                        if (old == 0) atomicOr(sum + (b >> 10), 1u << ((b >> 5) & 31));
-                    }
-                }
-                j0 += __popc(starts) + (next32 ? 1 : 0);
-            }
+        // Entries crowd onto the hubs' clusters, so most bits are already set:
+        // a plain read first turns those into broadcast loads instead of
+        // atomics serialised on one word.
+        for (int64_t p = e0 + threadIdx.x; p < e1; p += kRowThreads) {
+            const int32_t b = __ldg(vb + p);
+            const uint32_t bit = 1u << (b & 31);
+            if (b == c || (bm[b >> 5] & bit)) continue;
+            const uint32_t old = atomicOr(bm + (b >> 5), bit);
+            if (old == 0) atomicOr(sum + (b >> 10), 1u << ((b >> 5) & 31));
         }
         __syncthreads();
-        if (!multi[c]) {
-            const int m = read_bits<true>(bm, sum, n0, list, wsum, scratch + rb);
-            if (threadIdx.x == 0) count[c] = m;
+        if (!many) {
+            if (warp == 0) {
+                if (kWrite) {
+                    read_bits_warp<true>(bm, sum, n0, list, col_out + rowptr[c]);
+                } else {
+                    const int m = count_bits_warp(bm, sum, n0);
+                    if (lane == 0) count[c] = m;
+                }
+            }
         } else {
             // OR the touched words into row c's global bitmap and clear them here
             const int64_t g = slot[c];
             uint32_t *gb = gbm + g * words;
             uint32_t *gs = gsum + g * n0;
-            for (int s = threadIdx.x; s < n0; s += kRowThreads) {
-                uint32_t sw = sum[s];
+            for (int si = threadIdx.x; si < n0; si += kRowThreads) {
+                uint32_t sw = sum[si];
                 if (!sw) continue;
-                atomicOr(gs + s, sw);
-                sum[s] = 0;
+                atomicOr(gs + si, sw);
+                sum[si] = 0;
                 while (sw) {
-                    const int w = s * 32 + (__ffs(sw) - 1);
+                    const int w = si * 32 + (__ffs(sw) - 1);
                     sw &= sw - 1;
                     atomicOr(gb + w, bm[w]);
                     bm[w] = 0;
@@ -440,63 +549,34 @@ __global__ void __launch_bounds__(kRowThreads) coarse_rows(
     }
 }
 
-// Rows of more than one chunk: read their global bitmaps back.
+// Rows of more than one chunk, from their global bitmaps: count (kWrite =
+// false) or read back into col_out at rowptr[c].
+template <bool kWrite>
 __global__ void __launch_bounds__(kRowThreads) coarse_rows_multi(
-    const int32_t *__restrict__ slot_row, int64_t nslots, const int64_t *__restrict__ rbase, int words, int n0,
-    uint32_t *gbm, uint32_t *gsum, int32_t *__restrict__ scratch, int32_t *__restrict__ count) {
+    const int32_t *__restrict__ slot_row, int64_t nslots, int words, int n0, uint32_t *gbm, uint32_t *gsum,
+    int32_t *__restrict__ count, const int64_t *__restrict__ rowptr, int32_t *__restrict__ col_out) {
     __shared__ int32_t list[kListCap];
     __shared__ int wsum[kRowThreads / 32];
     for (int64_t g = blockIdx.x; g < nslots; g += gridDim.x) {
         const int32_t c = slot_row[g];
-        const int m = read_bits<false>(gbm + g * words, gsum + g * n0, n0, list, wsum, scratch + rbase[c]);
-        if (threadIdx.x == 0) count[c] = m;
-        __syncthreads();
-    }
-}
-
-// Coarse CSR entry q of row r is scratch[rbase[r] + q - rowptr[r]].  Balanced
-// over entries: each warp takes 1024 consecutive entries; a lane finds the
-// row of its first entry by binary search and then walks forward.
-__global__ void __launch_bounds__(256) compact_rows(const int32_t *__restrict__ scratch,
-                                                    const int64_t *__restrict__ rbase,
-                                                    const int64_t *__restrict__ rowptr, int64_t nc,
-                                                    int32_t *__restrict__ col_out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t m = rowptr[nc];
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = wid * kEntriesPerWarp; base < m; base += wstride * kEntriesPerWarp) {
-        int64_t q = base + lane;
-        if (q >= m) continue;
-        int64_t lo = 0, hi = nc;  // last row with rowptr[row] <= q
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (__ldg(rowptr + mid) <= q) lo = mid; else hi = mid;
-        }
-        int64_t r = lo;
-        int64_t rend = __ldg(rowptr + r + 1);
-        int64_t shift = __ldg(rbase + r) - __ldg(rowptr + r);
-        const int64_t end = base + kEntriesPerWarp < m ? base + kEntriesPerWarp : m;
-        // four entries per lane per step, their loads issued together
-        for (; q < end; q += 128) {
-            int64_t src[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t qu = q + 32 * u;
-                while (qu < end && rend <= qu) {
-                    ++r;
-                    rend = __ldg(rowptr + r + 1);
-                    shift = __ldg(rbase + r) - __ldg(rowptr + r);
+        uint32_t *gb = gbm + g * words;
+        const uint32_t *gs = gsum + g * n0;
+        if (kWrite) {
+            read_bits<false>(gb, const_cast<uint32_t *>(gs), n0, list, wsum, col_out + rowptr[c]);
+        } else {
+            int cnt = 0;
+            for (int si = threadIdx.x; si < n0; si += kRowThreads) {
+                uint32_t sw = gs[si];
+                while (sw) {
+                    cnt += __popc(gb[si * 32 + (__ffs(sw) - 1)]);
+                    sw &= sw - 1;
                 }
-                src[u] = qu + shift;
             }
-            int32_t v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = q + 32 * u < end ? __ldg(scratch + src[u]) : 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (q + 32 * u < end) col_out[q + 32 * u] = v[u];
+            int tot;
+            block_scan(cnt, wsum, tot);
+            if (threadIdx.x == 0) count[c] = tot;
         }
+        __syncthreads();
     }
 }
 
@@ -565,16 +645,16 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     const int words = (int)ceil_div(nc, 32);
     const int n0 = (int)ceil_div(words, 32);
     const int list_cap = words < kListCap ? words : kListCap;
-    Scratch mkey, mval, cstart, mrow, mdeg, moff, nchunk, multi, rbase, cstart_k, slot;
+    Scratch mkey, mval, cstart, inv, mdeg, moff, vb, nchunk, multi, cstart_k, slot;
     GOSH_TRY(mkey.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(mval.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(cstart.alloc(sizeof(int64_t) * (nc + 1), s));
-    GOSH_TRY(mrow.alloc(sizeof(int64_t) * n, s));
+    GOSH_TRY(inv.alloc(sizeof(int32_t) * n, s));
     GOSH_TRY(mdeg.alloc(sizeof(int64_t) * n, s));
     GOSH_TRY(moff.alloc(sizeof(int64_t) * (n + 1), s));
+    GOSH_TRY(vb.alloc(sizeof(int32_t) * nnz, s));
     GOSH_TRY(nchunk.alloc(sizeof(int32_t) * nc, s));
     GOSH_TRY(multi.alloc(nc, s));
-    GOSH_TRY(rbase.alloc(sizeof(int64_t) * nc, s));
     GOSH_TRY(cstart_k.alloc(sizeof(int64_t) * (nc + 1), s));
     GOSH_TRY(slot.alloc(sizeof(int64_t) * (nc + 1), s));
     // members grouped by cluster (stable: ascending ids inside a cluster)
@@ -582,11 +662,14 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
      note_launch());
     GOSH_TRY(radix_sort_u32(mkey.as<uint32_t>(), mval.as<uint32_t>(), n, 0, bits_for((uint64_t)nc), s));
     (member_layout<<<grid_1d(n), 256, 0, s>>>(mkey.as<uint32_t>(), mval.as<uint32_t>(), rowptr, n, (uint32_t)nc,
-                                              cstart.as<int64_t>(), mrow.as<int64_t>(), mdeg.as<int64_t>()),
+                                              cstart.as<int64_t>(), inv.as<int32_t>(), mdeg.as<int64_t>()),
      note_launch());
     GOSH_TRY(scan_exclusive_i64(mdeg.as<int64_t>(), moff.as<int64_t>(), n, moff.as<int64_t>() + n, s));
+    (member_entries<<<grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s>>>(
+         rowptr, col, n, map, inv.as<int32_t>(), moff.as<int64_t>(), vb.as<int32_t>()),
+     note_launch());
     (row_chunks<<<grid_1d(nc), 256, 0, s>>>(cstart.as<int64_t>(), moff.as<int64_t>(), nc, nchunk.as<int32_t>(),
-                                           multi.as<uint8_t>(), rbase.as<int64_t>()), note_launch());
+                                           multi.as<uint8_t>()), note_launch());
     GOSH_TRY(scan_exclusive_i32_to_i64(nchunk.as<int32_t>(), cstart_k.as<int64_t>(), nc, cstart_k.as<int64_t>() + nc, s));
     GOSH_TRY(scan_exclusive_u8_to_i64(multi.as<uint8_t>(), slot.as<int64_t>(), nc, slot.as<int64_t>() + nc, s));
     int64_t totals[2] = {0, 0};
@@ -594,12 +677,11 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY_CUDA(cudaMemcpyAsync(totals + 1, slot.as<int64_t>() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     const int64_t nchunks = totals[0], nslots = totals[1];
-    Scratch chunk_row, slot_row, gbm, gsum, scratch, count;
+    Scratch chunk_row, slot_row, gbm, gsum, count;
     GOSH_TRY(chunk_row.alloc(sizeof(int32_t) * nchunks, s));
     GOSH_TRY(slot_row.alloc(sizeof(int32_t) * nslots, s));
     GOSH_TRY(gbm.alloc(sizeof(uint32_t) * nslots * words, s));
     GOSH_TRY(gsum.alloc(sizeof(uint32_t) * nslots * n0, s));
-    GOSH_TRY(scratch.alloc(sizeof(int32_t) * nnz, s));
     GOSH_TRY(count.alloc(sizeof(int32_t) * nc, s));
     if (nslots > 0) {
         GOSH_TRY_CUDA(cudaMemsetAsync(gbm.ptr, 0, sizeof(uint32_t) * nslots * words, s));
@@ -608,38 +690,41 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY_CUDA(cudaMemsetAsync(count.ptr, 0, sizeof(int32_t) * nc, s));
     (chunk_rows<<<grid_1d(nc), 256, 0, s>>>(cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nc,
                                            chunk_row.as<int32_t>(), slot_row.as<int32_t>()), note_launch());
+    const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap);
+    int grid = 1, mgrid = 1;
     if (nchunks > 0) {
-        const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap) + sizeof(int) * kRowWarps;
-        // The attribute is process-wide state of the kernel: set it once to the
-        // largest size any level can ask for, so concurrent coarsenings (the
-        // batched entry runs several host threads) never lower it under one
-        // another's launch.
+        // The attribute is process-wide state of the kernels: set it once to
+        // the largest size any level can ask for, so concurrent coarsenings
+        // (the batched entry runs several host threads) never lower it under
+        // one another's launch.
         static std::once_flag attr_once;
         static cudaError_t attr_err = cudaSuccess;
         std::call_once(attr_once, [] {
             constexpr int64_t w = kBitmapMaxDefault / 32;
-            const size_t most = sizeof(uint32_t) * (size_t)(w + ceil_div(w, 32) + kListCap) + sizeof(int) * kRowWarps;
-            attr_err = cudaFuncSetAttribute(coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+            const size_t most = sizeof(uint32_t) * (size_t)(w + ceil_div(w, 32) + kListCap);
+            attr_err = cudaFuncSetAttribute(coarse_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+            if (attr_err == cudaSuccess)
+                attr_err = cudaFuncSetAttribute(coarse_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         });
         GOSH_TRY_CUDA(attr_err);
         int per_sm = 0;
-        GOSH_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_rows, kRowThreads, smem));
+        GOSH_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_rows<false>, kRowThreads, smem));
         if (per_sm < 1) per_sm = 1;
         const int64_t cap = (int64_t)num_sms() * per_sm;
-        const int grid = (int)(nchunks < cap ? nchunks : cap);
-        (coarse_rows<<<grid, kRowThreads, smem, s>>>(col, map, cstart.as<int64_t>(), mrow.as<int64_t>(),
-                                                    moff.as<int64_t>(), cstart_k.as<int64_t>(),
-                                                    chunk_row.as<int32_t>(), multi.as<uint8_t>(),
-                                                    slot.as<int64_t>(), nchunks, words, n0, list_cap,
-                                                    gbm.as<uint32_t>(), gsum.as<uint32_t>(), scratch.as<int32_t>(),
-                                                    count.as<int32_t>()),
+        grid = (int)(nchunks < cap ? nchunks : cap);
+        (coarse_rows<false><<<grid, kRowThreads, smem, s>>>(vb.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(),
+                                                           cstart_k.as<int64_t>(), chunk_row.as<int32_t>(),
+                                                           multi.as<uint8_t>(), slot.as<int64_t>(), nchunks, words,
+                                                           n0, list_cap, gbm.as<uint32_t>(), gsum.as<uint32_t>(),
+                                                           count.as<int32_t>(), nullptr, nullptr),
          note_launch());
     }
     if (nslots > 0) {
         const int64_t cap = (int64_t)num_sms() * 8;
-        (coarse_rows_multi<<<(int)(nslots < cap ? nslots : cap), kRowThreads, 0, s>>>(
-             slot_row.as<int32_t>(), nslots, rbase.as<int64_t>(), words, n0, gbm.as<uint32_t>(),
-             gsum.as<uint32_t>(), scratch.as<int32_t>(), count.as<int32_t>()),
+        mgrid = (int)(nslots < cap ? nslots : cap);
+        (coarse_rows_multi<false><<<mgrid, kRowThreads, 0, s>>>(slot_row.as<int32_t>(), nslots, words, n0,
+                                                               gbm.as<uint32_t>(), gsum.as<uint32_t>(),
+                                                               count.as<int32_t>(), nullptr, nullptr),
          note_launch());
     }
     GOSH_TRY(scan_exclusive_i32_to_i64(count.as<int32_t>(), rp, nc, rp + nc, s));
@@ -647,8 +732,18 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY_CUDA(cudaMemcpyAsync(&m, rp + nc, sizeof(m), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
-    (compact_rows<<<grid_warps(ceil_div(m, kEntriesPerWarp)), 256, 0, s>>>(scratch.as<int32_t>(), rbase.as<int64_t>(),
-                                                                             rp, nc, *co_out), note_launch());
+    if (nchunks > 0)
+        (coarse_rows<true><<<grid, kRowThreads, smem, s>>>(vb.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(),
+                                                          cstart_k.as<int64_t>(), chunk_row.as<int32_t>(),
+                                                          multi.as<uint8_t>(), slot.as<int64_t>(), nchunks, words,
+                                                          n0, list_cap, gbm.as<uint32_t>(), gsum.as<uint32_t>(),
+                                                          nullptr, rp, *co_out),
+         note_launch());
+    if (nslots > 0)
+        (coarse_rows_multi<true><<<mgrid, kRowThreads, 0, s>>>(slot_row.as<int32_t>(), nslots, words, n0,
+                                                              gbm.as<uint32_t>(), gsum.as<uint32_t>(), nullptr, rp,
+                                                              *co_out),
+         note_launch());
     *m_out = m;
     return GOSH_OK;
 }

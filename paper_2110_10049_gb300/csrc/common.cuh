@@ -294,6 +294,9 @@ template <> struct Store<__half> {
     }
 };
 
+// Device word raised by bounded waits that gave up (capi.cu); read by gosh_device_check.
+int *device_error_word();
+
 // ---------------------------------------------------------------------------
 // Device primitives (primitives.cu).
 // ---------------------------------------------------------------------------

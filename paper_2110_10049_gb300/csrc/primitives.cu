@@ -2,14 +2,13 @@
 // sort.  Both are deterministic (no atomics decide any output position), which
 // the bit-exact coarsening and the fixed-order reduction of the deterministic
 // training mode rely on.
+#include <algorithm>
+#include <unordered_map>
+
 #include "common.cuh"
 
 namespace gosh {
 namespace {
-
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Block-wide exclusive scan of one int64 per thread; returns the block total.
 __device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t *smem_warp, int64_t &total) {
@@ -40,44 +39,120 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t *smem
     return excl;
 }
 
-template <typename In>
-__global__ void scan_tile_sums(const In *__restrict__ in, int64_t n, int64_t *__restrict__ sums) {
-    __shared__ int64_t sw[33];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    int64_t s = 0;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j)
-        if (base + j < n) s += (int64_t)in[base + j];
-    int64_t total;
-    block_exclusive_scan(s, sw, total);
-    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+// ---------------------------------------------------------------------------
+// Single-pass exclusive scan with decoupled look-back: each block claims the
+// next tile from an atomic counter (so every tile it waits for belongs to a
+// block that is already running), publishes its tile sum, then walks back
+// over the published words of earlier tiles until it meets an inclusive
+// prefix, and publishes its own.  A status word packs (epoch, flag, value):
+// the epoch of the call, so words left by earlier calls in the per-stream
+// workspace never look ready and no reset is needed; flag 1 = tile sum,
+// 2 = inclusive prefix.  The wait is bounded: after kLookbackPolls fruitless
+// polls the block raises the error word and stops waiting (the output is then
+// wrong, which the error word reports).  Inputs are counts: non-negative,
+// with a total below 2^38.
+// ---------------------------------------------------------------------------
+constexpr int kLbThreads = 256;
+constexpr int kLbItems = 16;
+constexpr int kLbTile = kLbThreads * kLbItems;
+constexpr uint32_t kLookbackPolls = 1u << 22;
+constexpr int kEpochShift = 40, kFlagShift = 38;
+constexpr uint64_t kValueMask = (uint64_t(1) << kFlagShift) - 1;
+
+__device__ __forceinline__ uint64_t lb_word(uint64_t epoch, uint64_t flag, int64_t value) {
+    return (epoch << kEpochShift) | (flag << kFlagShift) | ((uint64_t)value & kValueMask);
 }
 
 template <typename In>
-__global__ void scan_tile_apply(const In *__restrict__ in, int64_t *__restrict__ out, int64_t n,
-                                const int64_t *__restrict__ tile_offsets) {
+__global__ void __launch_bounds__(kLbThreads) scan_lookback(const In *__restrict__ in, int64_t *__restrict__ out,
+                                                            int64_t n, int64_t *__restrict__ total,
+                                                            unsigned long long *status,
+                                                            unsigned long long *counter, unsigned long long base,
+                                                            uint64_t epoch, int *err) {
     __shared__ int64_t sw[33];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    int64_t v[kScanItems];
-    int64_t s = 0;
+    __shared__ int64_t s_tile, s_prefix;
+    if (threadIdx.x == 0) s_tile = (int64_t)(atomicAdd(counter, 1ull) - base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t i0 = tile * kLbTile + (int64_t)threadIdx.x * kLbItems;
+    int64_t v[kLbItems];
+    int64_t sum = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        v[j] = base + j < n ? (int64_t)in[base + j] : 0;
-        s += v[j];
+    for (int j = 0; j < kLbItems; ++j) {
+        v[j] = i0 + j < n ? (int64_t)in[i0 + j] : 0;
+        sum += v[j];
     }
-    int64_t total;
-    int64_t run = block_exclusive_scan(s, sw, total) + (tile_offsets ? tile_offsets[blockIdx.x] : 0);
+    int64_t agg;
+    int64_t run = block_exclusive_scan(sum, sw, agg);
+    if (threadIdx.x == 0) {
+        int64_t prefix = 0;
+        if (tile == 0) {
+            atomicExch(status, lb_word(epoch, 2, agg));
+        } else {
+            atomicExch(status + tile, lb_word(epoch, 1, agg));
+            uint32_t polls = 0;
+            for (int64_t j = tile - 1; j >= 0;) {
+                const uint64_t w = *reinterpret_cast<volatile unsigned long long *>(status + j);
+                if ((w >> kEpochShift) != epoch) {
+                    if (++polls > kLookbackPolls) {
+                        atomicExch(err, 1);
+                        break;
+                    }
+                    continue;
+                }
+                prefix += (int64_t)(w & kValueMask);
+                if (((w >> kFlagShift) & 3) == 2) break;
+                --j;
+            }
+            atomicExch(status + tile, lb_word(epoch, 2, prefix + agg));
+        }
+        s_prefix = prefix;
+    }
+    __syncthreads();
+    run += s_prefix;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-        if (base + j < n) out[base + j] = run;
+    for (int j = 0; j < kLbItems; ++j) {
+        if (i0 + j < n) out[i0 + j] = run;
         run += v[j];
     }
+    if (total && (tile + 1) * kLbTile >= n && threadIdx.x == 0) *total = s_prefix + agg;
 }
 
-template <typename In>
-__global__ void write_total_t(const In *__restrict__ in, const int64_t *__restrict__ out, int64_t n,
-                              int64_t *__restrict__ total) {
-    *total = n > 0 ? out[n - 1] + (int64_t)in[n - 1] : 0;
+// Per host thread and stream: the tile status words (zeroed once, then only
+// ever overwritten with later epochs) and the tile counter (monotonic: a call
+// claims tiles base .. base + ntiles - 1).  An event orders a workspace's use
+// after its previous use even if the stream handle was recycled.
+struct LookbackWork {
+    unsigned long long *status = nullptr;
+    unsigned long long *counter = nullptr;
+    int64_t cap = 0;
+    uint64_t epoch = 0;
+    unsigned long long base = 0;
+    cudaEvent_t last = nullptr;
+};
+
+gosh_status lookback_work(cudaStream_t s, int64_t ntiles, LookbackWork **out) {
+    static thread_local std::unordered_map<cudaStream_t, LookbackWork> works;
+    LookbackWork &w = works[s];
+    if (w.last) GOSH_TRY_CUDA(cudaStreamWaitEvent(s, w.last, 0));
+    else GOSH_TRY_CUDA(cudaEventCreateWithFlags(&w.last, cudaEventDisableTiming));
+    if (!w.counter) {
+        GOSH_TRY_CUDA(cudaMallocAsync(&w.counter, sizeof(unsigned long long), s));
+        GOSH_TRY_CUDA(cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), s));
+        w.base = 0;
+    }
+    const uint64_t kMaxEpoch = (uint64_t(1) << (64 - kEpochShift)) - 1;
+    if (w.cap < ntiles || w.epoch >= kMaxEpoch) {
+        if (w.status) GOSH_TRY_CUDA(cudaFreeAsync(w.status, s));
+        const int64_t cap = std::max<int64_t>(ntiles, std::max<int64_t>(256, 2 * w.cap));
+        GOSH_TRY_CUDA(cudaMallocAsync(&w.status, sizeof(unsigned long long) * cap, s));
+        GOSH_TRY_CUDA(cudaMemsetAsync(w.status, 0, sizeof(unsigned long long) * cap, s));
+        w.cap = cap;
+        w.epoch = 0;
+    }
+    ++w.epoch;
+    *out = &w;
+    return GOSH_OK;
 }
 
 template <typename In>
@@ -86,19 +161,15 @@ gosh_status scan_exclusive(const In *in, int64_t *out, int64_t n, int64_t *total
         if (total) GOSH_TRY_CUDA(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
         return GOSH_OK;
     }
-    const int64_t tiles = ceil_div(n, kScanTile);
-    if (tiles == 1) {
-        (scan_tile_apply<In><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr), note_launch());
-    } else {
-        Scratch sums, offs;
-        GOSH_TRY(sums.alloc(sizeof(int64_t) * tiles, s));
-        GOSH_TRY(offs.alloc(sizeof(int64_t) * tiles, s));
-        (scan_tile_sums<In><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>()), note_launch());
-        GOSH_TRY(scan_exclusive<int64_t>(sums.as<int64_t>(), offs.as<int64_t>(), tiles, nullptr, s));
-        (scan_tile_apply<In><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, offs.as<int64_t>()), note_launch());
-    }
-    if (total) (write_total_t<In><<<1, 1, 0, s>>>(in, out, n, total), note_launch());
+    const int64_t tiles = ceil_div(n, kLbTile);
+    LookbackWork *w = nullptr;
+    GOSH_TRY(lookback_work(s, tiles, &w));
+    (scan_lookback<In><<<(unsigned)tiles, kLbThreads, 0, s>>>(in, out, n, total, w->status, w->counter, w->base,
+                                                            w->epoch, device_error_word()),
+     note_launch());
+    w->base += (unsigned long long)tiles;
     GOSH_TRY_CUDA(cudaGetLastError());
+    GOSH_TRY_CUDA(cudaEventRecord(w->last, s));
     return GOSH_OK;
 }
 

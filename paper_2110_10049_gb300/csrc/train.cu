@@ -105,8 +105,8 @@ int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) /
 
 // Sources per warp tile.  A warp walks its tile in tile / (32/L) dependent
 // rounds, so small levels (few tiles, far fewer than the GPU's warps) take
-// short tiles (4 below 2^16 rows; below 2^19, 32 for lock-free atomic changes,
-// 8 for 16-bit plain stores, 16 in the deterministic mode);
+// short tiles (4 below 2^16 rows; below 2^19, 8 for 16-bit tables with plain
+// stores, 16 in the deterministic mode, 32 otherwise);
 // large levels take 32 to amortise the draws.  A multiple of 32/L in
 // [32/L, 32]; params->vertices_per_warp overrides.
 int tile_vertices(const gosh_params *p, int64_t n, int lanes) {
@@ -229,6 +229,20 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
         const int grid = grid_for(n);
         a.src_begin = 0;
         a.src_end = n;
+        // Small levels: every epoch in one cooperative launch (per-epoch
+        // launches cost about as much as the epochs' work).
+        // Only where one wave holds every tile (more would make warps loop).
+        const int coop_cap = num_sms() * kern->epochs_blocks_per_sm;
+        if (kern->launch_epochs && !loss_per_epoch && epochs > 1 && kern->epochs_blocks_per_sm > 0 &&
+            ceil_div(ceil_div(n, a.tile), kern->warps) <= coop_cap) {
+            const int g = grid;
+            Scratch bar;
+            GOSH_TRY(bar.alloc(sizeof(unsigned int), s));
+            GOSH_TRY_CUDA(cudaMemsetAsync(bar.ptr, 0, sizeof(unsigned int), s));
+            const cudaError_t e = kern->launch_epochs(a, g, epochs, p->lr, p->lr_floor, bar.as<unsigned int>(), s);
+            if (e == cudaSuccess) return GOSH_OK;
+            cudaGetLastError();  // not co-resident here: fall back to one launch per epoch
+        }
         for (int j = 0; j < epochs; ++j) {
             const double f = 1.0 - (double)j / (double)epochs;
             a.lr = (float)(p->lr * (f > p->lr_floor ? f : p->lr_floor));

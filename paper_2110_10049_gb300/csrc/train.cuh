@@ -51,6 +51,11 @@ int *device_error_word();
 // Host-side launcher for one epoch (Hogwild) or one snapshot batch (deterministic).
 struct TrainKernel {
     void (*launch)(const TrainArgs &, int grid, cudaStream_t);
+    // all epochs in one cooperative launch with a grid barrier between them
+    // (null where not compiled); returns the launch's error
+    cudaError_t (*launch_epochs)(const TrainArgs &, int grid, int epochs, double lr, double lr_floor,
+                                 unsigned int *barrier, cudaStream_t);
+    int epochs_blocks_per_sm;
     int blocks_per_sm;
     int lanes;     // L
     int pass;      // P (negative: all of up to -P samples staged by TMA)

@@ -343,14 +343,84 @@ void launch_train(const TrainArgs &a, int grid, cudaStream_t s) {
     (train_kernel<T, D, L, P, MODE><<<grid, kTrainWarps * 32, 0, s>>>(a), note_launch());
 }
 
+constexpr uint32_t kEpochBarrierPolls = 1u << 22;
+
+/*
+ * Every epoch of a lock-free level in one cooperative launch: the warps run
+ * their tiles of epoch j (learning rate lr * max(1 - j/epochs, lr_floor), as
+ * the host would pass it), then the blocks meet at a grid barrier (a
+ * monotonic arrival counter: epoch j waits for (j+1) * gridDim.x arrivals)
+ * before epoch j+1, so an epoch sees every update of the previous one (Alg. 3
+ * serialises epochs).  Small levels are bound by launch latency, not work.
+ * The barrier wait is bounded: on time-out the block raises the error word
+ * and goes on.
+ */
+template <typename T, int D, int L, int P, int MODE>
+__global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, MODE))
+    train_epochs_kernel(TrainArgs a, int epochs, double lr, double lr_floor, unsigned int *barrier) {
+    __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
+    __shared__ uint32_t s_sr[kTrainWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t ntiles = (a.src_end - a.src_begin + a.tile - 1) / a.tile;
+    const int64_t wstride = (int64_t)gridDim.x * kTrainWarps;
+    double loss_acc = 0.0;
+    unsigned long long applied = 0;
+    for (int j = 0; j < epochs; ++j) {
+        const double f = 1.0 - (double)j / (double)epochs;
+        a.lr = (float)(lr * (f > lr_floor ? f : lr_floor));
+        a.epoch = (uint32_t)j;
+        for (int64_t tile = (int64_t)blockIdx.x * kTrainWarps + warp; tile < ntiles; tile += wstride)
+            train_tile<T, D, L, P, MODE>(a, a.src_begin + tile * a.tile, s_u[warp], s_sr[warp], loss_acc, applied);
+        if (j + 1 == epochs) break;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(barrier, 1u);
+            const unsigned int target = (unsigned int)(j + 1) * gridDim.x;
+            uint32_t polls = 0;
+            while (*reinterpret_cast<volatile unsigned int *>(barrier) < target) {
+                if (++polls > kEpochBarrierPolls) {
+                    if (a.err) atomicExch(a.err, 1);
+                    break;
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
+    if (a.n_updates) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) applied += __shfl_xor_sync(0xffffffffu, applied, o);
+        if (lane == 0 && applied) atomicAdd(a.n_updates, applied);
+    }
+}
+
+template <typename T, int D, int L, int P, int MODE>
+cudaError_t launch_train_epochs(const TrainArgs &a, int grid, int epochs, double lr, double lr_floor,
+                                unsigned int *barrier, cudaStream_t s) {
+    TrainArgs args = a;
+    void *params[] = {&args, &epochs, &lr, &lr_floor, &barrier};
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void *)train_epochs_kernel<T, D, L, P, MODE>, dim3(grid),
+                                                      dim3(kTrainWarps * 32), params, 0, s);
+    if (e == cudaSuccess) note_launch();
+    return e;
+}
+
 template <typename T, int D, int L, int P, int MODE>
 TrainKernel make_train_kernel() {
     TrainKernel k;
     k.launch = &launch_train<T, D, L, P, MODE>;
+    k.launch_epochs = nullptr;
+    k.epochs_blocks_per_sm = 0;
     k.blocks_per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.blocks_per_sm, train_kernel<T, D, L, P, MODE>,
                                                   kTrainWarps * 32, 0);
     if (k.blocks_per_sm < 1) k.blocks_per_sm = 1;
+    if constexpr (MODE != kModeDet) {
+        k.launch_epochs = &launch_train_epochs<T, D, L, P, MODE>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.epochs_blocks_per_sm, train_epochs_kernel<T, D, L, P, MODE>,
+                                                      kTrainWarps * 32, 0);
+    }
     k.lanes = L;
     k.pass = P;
     k.warps = kTrainWarps;

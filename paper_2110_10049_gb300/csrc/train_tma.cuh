@@ -285,6 +285,8 @@ TrainKernel make_train_tma_kernel() {
     constexpr int smem = kTmaWarps * 2 * tma_stage_bytes<T, D, L, KS>();
     TrainKernel k;
     k.launch = &launch_train_tma<T, D, L, KS, MODE>;
+    k.launch_epochs = nullptr;
+    k.epochs_blocks_per_sm = 0;
     cudaFuncSetAttribute(train_tma_kernel<T, D, L, KS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k.blocks_per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.blocks_per_sm, train_tma_kernel<T, D, L, KS, MODE>,
