@@ -34,32 +34,28 @@ enum : uint8_t { kUndecided = 0, kHub = 1, kNonHub = 2 };
 
 __device__ __forceinline__ bool small_deg(int64_t deg, int64_t n, int64_t nnz) { return deg * n <= nnz; }
 
-// Key (n - 1) - deg (a simple graph has deg <= n - 1): ascending keys are
-// descending degrees, and the sort needs only the bits of n - 1.
-__global__ void degree_keys(const int64_t *__restrict__ rowptr, int64_t n, uint32_t *__restrict__ key,
-                            uint32_t *__restrict__ val) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t deg = rowptr[v + 1] - rowptr[v];
-        key[v] = deg < n ? (uint32_t)(n - 1 - deg) : 0u;
-        val[v] = (uint32_t)v;
-    }
-}
-
 __global__ void invert_order(const uint32_t *__restrict__ order, int64_t n, int32_t *__restrict__ rank) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         rank[order[i]] = (int32_t)i;
 }
 
-// A vertex above the density (deg * n > nnz) has no eligible earlier-ranked
-// neighbour: eligibility needs the other end at or below the density, and an
-// earlier rank needs a degree at least as large.  Such vertices are cluster
-// roots from the start; only vertices at or below the density (whose every
-// edge is eligible and whose rows are at most the average degree long) go
-// through the rounds.
-__global__ void mis_init(const int64_t *__restrict__ rowptr, int64_t n, uint8_t *__restrict__ state) {
+// Sort key (n - 1) - deg (a simple graph has deg <= n - 1): ascending keys
+// are descending degrees, and the sort needs only the bits of n - 1.
+// Initial MIS state: a vertex above the density (deg * n > nnz) has no
+// eligible earlier-ranked neighbour (eligibility needs the other end at or
+// below the density, and an earlier rank needs a degree at least as large),
+// so it is a cluster root from the start; only vertices at or below the
+// density (whose every edge is eligible and whose rows are at most the
+// average degree long) go through the rounds.
+__global__ void degree_keys(const int64_t *__restrict__ rowptr, int64_t n, uint32_t *__restrict__ key,
+                            uint32_t *__restrict__ val, uint8_t *__restrict__ state) {
     const int64_t nnz = rowptr[n];
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        state[v] = small_deg(rowptr[v + 1] - rowptr[v], n, nnz) ? kUndecided : kHub;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t deg = rowptr[v + 1] - rowptr[v];
+        key[v] = deg < n ? (uint32_t)(n - 1 - deg) : 0u;
+        val[v] = (uint32_t)v;
+        state[v] = small_deg(deg, n, nnz) ? kUndecided : kHub;
+    }
 }
 
 // One round of the MIS rule, one thread per rank position (so a warp holds
@@ -323,8 +319,9 @@ __global__ void __launch_bounds__(256) member_entries(const int64_t *__restrict_
 }
 
 __global__ void row_chunks(const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff, int64_t nc,
-                           int32_t *__restrict__ nchunk, uint8_t *__restrict__ multi) {
+                           int32_t *__restrict__ nchunk, uint8_t *__restrict__ multi, int32_t *__restrict__ count) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        count[c] = 0;  // rows without entries keep it
         const int64_t len = moff[cstart[c + 1]] - moff[cstart[c]];
         const int64_t k = (len + kChunk - 1) / kChunk;
         nchunk[c] = (int32_t)k;
@@ -645,9 +642,12 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     const int words = (int)ceil_div(nc, 32);
     const int n0 = (int)ceil_div(words, 32);
     const int list_cap = words < kListCap ? words : kListCap;
-    Scratch mkey, mval, cstart, inv, mdeg, moff, vb, nchunk, multi, cstart_k, slot;
+    Scratch mkey, mval, kalt, valt, cstart, inv, mdeg, moff, vb, nchunk, multi, cstart_k, slot, count;
     GOSH_TRY(mkey.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(mval.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(kalt.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(valt.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(count.alloc(sizeof(int32_t) * nc, s));
     GOSH_TRY(cstart.alloc(sizeof(int64_t) * (nc + 1), s));
     GOSH_TRY(inv.alloc(sizeof(int32_t) * n, s));
     GOSH_TRY(mdeg.alloc(sizeof(int64_t) * n, s));
@@ -660,16 +660,20 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     // members grouped by cluster (stable: ascending ids inside a cluster)
     (member_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, map, (uint32_t)nc, mkey.as<uint32_t>(), mval.as<uint32_t>()),
      note_launch());
-    GOSH_TRY(radix_sort_u32(mkey.as<uint32_t>(), mval.as<uint32_t>(), n, 0, bits_for((uint64_t)nc), s));
-    (member_layout<<<grid_1d(n), 256, 0, s>>>(mkey.as<uint32_t>(), mval.as<uint32_t>(), rowptr, n, (uint32_t)nc,
-                                              cstart.as<int64_t>(), inv.as<int32_t>(), mdeg.as<int64_t>()),
+    bool in_alt = false;
+    GOSH_TRY(radix_sort_u32_pp(mkey.as<uint32_t>(), mval.as<uint32_t>(), kalt.as<uint32_t>(), valt.as<uint32_t>(), n, 0,
+                               bits_for((uint64_t)nc), s, &in_alt));
+    (member_layout<<<grid_1d(n), 256, 0, s>>>(in_alt ? kalt.as<uint32_t>() : mkey.as<uint32_t>(),
+                                              in_alt ? valt.as<uint32_t>() : mval.as<uint32_t>(), rowptr, n,
+                                              (uint32_t)nc, cstart.as<int64_t>(), inv.as<int32_t>(),
+                                              mdeg.as<int64_t>()),
      note_launch());
     GOSH_TRY(scan_exclusive_i64(mdeg.as<int64_t>(), moff.as<int64_t>(), n, moff.as<int64_t>() + n, s));
     (member_entries<<<grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s>>>(
          rowptr, col, n, map, inv.as<int32_t>(), moff.as<int64_t>(), vb.as<int32_t>()),
      note_launch());
     (row_chunks<<<grid_1d(nc), 256, 0, s>>>(cstart.as<int64_t>(), moff.as<int64_t>(), nc, nchunk.as<int32_t>(),
-                                           multi.as<uint8_t>()), note_launch());
+                                           multi.as<uint8_t>(), count.as<int32_t>()), note_launch());
     GOSH_TRY(scan_exclusive_i32_to_i64(nchunk.as<int32_t>(), cstart_k.as<int64_t>(), nc, cstart_k.as<int64_t>() + nc, s));
     GOSH_TRY(scan_exclusive_u8_to_i64(multi.as<uint8_t>(), slot.as<int64_t>(), nc, slot.as<int64_t>() + nc, s));
     int64_t totals[2] = {0, 0};
@@ -677,17 +681,15 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY_CUDA(cudaMemcpyAsync(totals + 1, slot.as<int64_t>() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     const int64_t nchunks = totals[0], nslots = totals[1];
-    Scratch chunk_row, slot_row, gbm, gsum, count;
+    Scratch chunk_row, slot_row, gbm, gsum;
     GOSH_TRY(chunk_row.alloc(sizeof(int32_t) * nchunks, s));
     GOSH_TRY(slot_row.alloc(sizeof(int32_t) * nslots, s));
     GOSH_TRY(gbm.alloc(sizeof(uint32_t) * nslots * words, s));
     GOSH_TRY(gsum.alloc(sizeof(uint32_t) * nslots * n0, s));
-    GOSH_TRY(count.alloc(sizeof(int32_t) * nc, s));
     if (nslots > 0) {
         GOSH_TRY_CUDA(cudaMemsetAsync(gbm.ptr, 0, sizeof(uint32_t) * nslots * words, s));
         GOSH_TRY_CUDA(cudaMemsetAsync(gsum.ptr, 0, sizeof(uint32_t) * nslots * n0, s));
     }
-    GOSH_TRY_CUDA(cudaMemsetAsync(count.ptr, 0, sizeof(int32_t) * nc, s));
     (chunk_rows<<<grid_1d(nc), 256, 0, s>>>(cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nc,
                                            chunk_row.as<int32_t>(), slot_row.as<int32_t>()), note_launch());
     const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap);
@@ -755,9 +757,11 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
 gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int64_t nnz, int32_t *map,
                       int64_t *nc_out, int64_t **rp_out, int32_t **col_out, int64_t *nnz_out, int *rounds_out,
                       cudaStream_t s) {
-    Scratch keys, vals, rank, state, hub_rank, flags, cid, counter;
+    Scratch keys, vals, kalt, valt, rank, state, hub_rank, flags, cid, counter;
     GOSH_TRY(keys.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(vals.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(kalt.alloc(sizeof(uint32_t) * n, s));
+    GOSH_TRY(valt.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(rank.alloc(sizeof(int32_t) * n, s));
     GOSH_TRY(state.alloc(n, s));
     GOSH_TRY(hub_rank.alloc(sizeof(int32_t) * n, s));
@@ -765,27 +769,32 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     GOSH_TRY(cid.alloc(sizeof(int64_t) * (n + 1), s));
     GOSH_TRY(counter.alloc(sizeof(unsigned long long) * 2, s));
 
-    // 1. degree order
-    (degree_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>()), note_launch());
-    GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), vals.as<uint32_t>(), n, 0, bits_for((uint64_t)(n - 1)), s));
-    const uint32_t *order = vals.as<uint32_t>();
+    // 1. degree order (and the initial MIS state)
+    (degree_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>(), state.as<uint8_t>()),
+     note_launch());
+    bool in_alt = false;
+    GOSH_TRY(radix_sort_u32_pp(keys.as<uint32_t>(), vals.as<uint32_t>(), kalt.as<uint32_t>(), valt.as<uint32_t>(), n, 0,
+                               bits_for((uint64_t)(n - 1)), s, &in_alt));
+    const uint32_t *order = in_alt ? valt.as<uint32_t>() : vals.as<uint32_t>();
     (invert_order<<<grid_1d(n), 256, 0, s>>>(order, n, rank.as<int32_t>()), note_launch());
-    (mis_init<<<grid_1d(n), 256, 0, s>>>(rowptr, n, state.as<uint8_t>()), note_launch());
 
-    // 2. MIS rounds
-    unsigned long long left = 1;
+    // 2. MIS rounds, two per check of the undecided count (most levels settle
+    // in two; a round after settling does nothing)
+    unsigned long long left[2] = {1, 1};
     int rounds = 0;
-    while (left > 0) {
+    while (left[1] > 0) {
         if (rounds > n + 1) {
             set_error("coarsening did not settle after %d rounds", rounds);
             return GOSH_ERR_CUDA;
         }
-        GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
-        (mis_round<<<grid_1d(n), 256, 0, s>>>(rowptr, col, n, order, rank.as<int32_t>(),
-                                                               state.as<uint8_t>(), counter.as<unsigned long long>()), note_launch());
-        GOSH_TRY_CUDA(cudaMemcpyAsync(&left, counter.ptr, sizeof(left), cudaMemcpyDeviceToHost, s));
+        GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long) * 2, s));
+        for (int r = 0; r < 2; ++r)
+            (mis_round<<<grid_1d(n), 256, 0, s>>>(rowptr, col, n, order, rank.as<int32_t>(), state.as<uint8_t>(),
+                                                 counter.as<unsigned long long>() + r),
+             note_launch());
+        GOSH_TRY_CUDA(cudaMemcpyAsync(left, counter.ptr, sizeof(left), cudaMemcpyDeviceToHost, s));
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
-        ++rounds;
+        rounds += 2;
     }
     if (rounds_out) *rounds_out = rounds;
 

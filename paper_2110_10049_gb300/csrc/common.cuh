@@ -312,6 +312,10 @@ gosh_status scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n
 // keys/vals are sorted in place (vals may be null); scratch is taken internally.
 gosh_status radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit,
                            cudaStream_t s);
+// The same into caller-provided alternate buffers, without the copy back:
+// *in_alt tells where the sorted data ended.
+gosh_status radix_sort_u32_pp(uint32_t *keys, uint32_t *vals, uint32_t *kalt, uint32_t *valt, int64_t n, int begin_bit,
+                              int end_bit, cudaStream_t s, bool *in_alt);
 gosh_status radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, const int *digit_bits,
                            int ndigits, cudaStream_t s);
 

@@ -183,10 +183,12 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortWarps = kSortThreads / 32;
 
+// Digit histogram of one pass over the current arrangement of the keys:
+// counts[digit * nblocks + block] (each pass needs its own: a block's counts
+// depend on which keys the previous pass placed in it).
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) radix_hist(const K *__restrict__ keys, int64_t n,
-                                                           int shift, int64_t *__restrict__ counts,
-                                                           int64_t nblocks) {
+__global__ void __launch_bounds__(kSortThreads) radix_hist(const K *__restrict__ keys, int64_t n, int shift,
+                                                           int64_t *__restrict__ counts, int64_t nblocks) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -256,36 +258,53 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(
     }
 }
 
+// LSD radix sort over the given digit shifts, ping-ponging between (keys,
+// vals) and (kalt, valt): per pass a histogram of the current arrangement,
+// one scan, one stable scatter.  Returns in *in_alt whether the result ended
+// in the alternate buffers (an odd pass count).
 template <typename K>
-gosh_status radix_sort(K *keys, uint32_t *vals, int64_t n, const int *shifts, int ndigits,
-                       cudaStream_t s) {
+gosh_status radix_sort_pp(K *keys, uint32_t *vals, K *kalt, uint32_t *valt, int64_t n, const int *shifts,
+                          int ndigits, cudaStream_t s, bool *in_alt) {
+    *in_alt = false;
     if (n <= 1 || ndigits == 0) return GOSH_OK;
     const int64_t nblocks = ceil_div(n, kSortTile);
-    Scratch kalt, valt, counts, offs;
-    GOSH_TRY(kalt.alloc(sizeof(K) * n, s));
-    if (vals) GOSH_TRY(valt.alloc(sizeof(uint32_t) * n, s));
+    Scratch counts, offs;
     GOSH_TRY(counts.alloc(sizeof(int64_t) * 256 * nblocks, s));
     GOSH_TRY(offs.alloc(sizeof(int64_t) * 256 * nblocks, s));
-    K *ka = keys, *kb = kalt.as<K>();
-    uint32_t *va = vals, *vb = valt.as<uint32_t>();
+    K *ka = keys, *kb = kalt;
+    uint32_t *va = vals, *vb = valt;
     for (int d = 0; d < ndigits; ++d) {
-        (radix_hist<K><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, n, shifts[d], counts.as<int64_t>(),
-                                                                  nblocks), note_launch());
-        GOSH_TRY(scan_exclusive<int64_t>(counts.as<int64_t>(), offs.as<int64_t>(), 256 * nblocks,
-                                         nullptr, s));
+        (radix_hist<K><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, n, shifts[d], counts.as<int64_t>(), nblocks),
+         note_launch());
+        GOSH_TRY(scan_exclusive<int64_t>(counts.as<int64_t>(), offs.as<int64_t>(), 256 * nblocks, nullptr, s));
         if (vals)
-            (radix_scatter<K, true><<<(unsigned)nblocks, kSortThreads, 0, s>>>(
-                ka, va, kb, vb, n, shifts[d], offs.as<int64_t>(), nblocks), note_launch());
+            (radix_scatter<K, true><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shifts[d],
+                                                                              offs.as<int64_t>(), nblocks),
+             note_launch());
         else
-            (radix_scatter<K, false><<<(unsigned)nblocks, kSortThreads, 0, s>>>(
-                ka, nullptr, kb, nullptr, n, shifts[d], offs.as<int64_t>(), nblocks), note_launch());
+            (radix_scatter<K, false><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, nullptr, kb, nullptr, n, shifts[d],
+                                                                               offs.as<int64_t>(), nblocks),
+             note_launch());
         GOSH_TRY_CUDA(cudaGetLastError());
         K *kt = ka; ka = kb; kb = kt;
         uint32_t *vt = va; va = vb; vb = vt;
     }
-    if (ka != keys) {
-        GOSH_TRY_CUDA(cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
-        if (vals) GOSH_TRY_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    *in_alt = ka != keys;
+    return GOSH_OK;
+}
+
+template <typename K>
+gosh_status radix_sort(K *keys, uint32_t *vals, int64_t n, const int *shifts, int ndigits, cudaStream_t s) {
+    if (n <= 1 || ndigits == 0) return GOSH_OK;
+    Scratch kalt, valt;
+    GOSH_TRY(kalt.alloc(sizeof(K) * n, s));
+    if (vals) GOSH_TRY(valt.alloc(sizeof(uint32_t) * n, s));
+    bool in_alt = false;
+    GOSH_TRY(radix_sort_pp<K>(keys, vals, kalt.as<K>(), valt.as<uint32_t>(), n, shifts, ndigits, s, &in_alt));
+    if (in_alt) {
+        GOSH_TRY_CUDA(cudaMemcpyAsync(keys, kalt.as<K>(), sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
+        if (vals)
+            GOSH_TRY_CUDA(cudaMemcpyAsync(vals, valt.as<uint32_t>(), sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
     }
     return GOSH_OK;
 }
@@ -311,6 +330,14 @@ gosh_status radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_
     int nd = 0;
     for (int b = begin_bit; b < end_bit && nd < 4; b += 8) shifts[nd++] = b;
     return radix_sort<uint32_t>(keys, vals, n, shifts, nd, s);
+}
+
+gosh_status radix_sort_u32_pp(uint32_t *keys, uint32_t *vals, uint32_t *kalt, uint32_t *valt, int64_t n, int begin_bit,
+                              int end_bit, cudaStream_t s, bool *in_alt) {
+    int shifts[4];
+    int nd = 0;
+    for (int b = begin_bit; b < end_bit && nd < 4; b += 8) shifts[nd++] = b;
+    return radix_sort_pp<uint32_t>(keys, vals, kalt, valt, n, shifts, nd, s, in_alt);
 }
 
 gosh_status radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, const int *shifts,
