@@ -35,6 +35,7 @@ enum : uint8_t { kUndecided = 0, kHub = 1, kNonHub = 2 };
 __device__ __forceinline__ bool small_deg(int64_t deg, int64_t n, int64_t nnz) { return deg * n <= nnz; }
 
 __global__ void invert_order(const uint32_t *__restrict__ order, int64_t n, int32_t *__restrict__ rank) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         rank[order[i]] = (int32_t)i;
 }
@@ -49,6 +50,7 @@ __global__ void invert_order(const uint32_t *__restrict__ order, int64_t n, int3
 // average degree long) go through the rounds.
 __global__ void degree_keys(const int64_t *__restrict__ rowptr, int64_t n, uint32_t *__restrict__ key,
                             uint32_t *__restrict__ val, uint8_t *__restrict__ state) {
+    GOSH_DEP_WAIT();
     const int64_t nnz = rowptr[n];
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t deg = rowptr[v + 1] - rowptr[v];
@@ -67,6 +69,7 @@ __global__ void __launch_bounds__(256) mis_round(const int64_t *__restrict__ row
                                                  int64_t n, const uint32_t *__restrict__ order,
                                                  const int32_t *__restrict__ rank, uint8_t *state,
                                                  unsigned long long *__restrict__ undecided) {
+    GOSH_DEP_WAIT();
     volatile uint8_t *vstate = state;
     unsigned long long left = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -97,6 +100,7 @@ __global__ void __launch_bounds__(256) mis_round(const int64_t *__restrict__ row
 __global__ void attach_to_hub(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, int64_t n,
                               const int32_t *__restrict__ rank, const uint8_t *__restrict__ state,
                               int32_t *__restrict__ hub_rank) {
+    GOSH_DEP_WAIT();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         if (state[v] == kHub) {
             hub_rank[v] = rank[v];
@@ -118,6 +122,7 @@ __global__ void __launch_bounds__(256) attach_to_hub_warp(const int64_t *__restr
                                                           const int32_t *__restrict__ rank,
                                                           const uint8_t *__restrict__ state,
                                                           int32_t *__restrict__ hub_rank) {
+    GOSH_DEP_WAIT();
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -138,6 +143,7 @@ __global__ void __launch_bounds__(256) attach_to_hub_warp(const int64_t *__restr
 
 __global__ void hub_flags_by_rank(const uint32_t *__restrict__ order, const uint8_t *__restrict__ state, int64_t n,
                                   uint8_t *__restrict__ flag) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         flag[i] = state[order[i]] == kHub ? 1 : 0;
 }
@@ -146,6 +152,7 @@ __global__ void hub_flags_by_rank(const uint32_t *__restrict__ order, const uint
 // vertex without one would be a logic error: it is flagged, not followed.
 __global__ void assign_map(const int32_t *__restrict__ hub_rank, const int64_t *__restrict__ cid_of_rank, int64_t n,
                            int32_t *__restrict__ map, unsigned long long *__restrict__ orphan) {
+    GOSH_DEP_WAIT();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t hr = hub_rank[v];
         if (hr >= 0 && hr < n) {
@@ -165,6 +172,7 @@ constexpr int kEntriesPerWarp = 1024;
 __global__ void __launch_bounds__(256) edge_image(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                                   int64_t n, const int32_t *__restrict__ map, uint64_t nc,
                                                   uint64_t *__restrict__ keys) {
+    GOSH_DEP_WAIT();
     const int lane = threadIdx.x & 31;
     const int64_t nnz = rowptr[n];
     const int64_t sentinel = (int64_t)(nc * nc);
@@ -195,6 +203,7 @@ __global__ void __launch_bounds__(256) edge_image(const int64_t *__restrict__ ro
 }
 
 __global__ void unique_flags(const uint64_t *__restrict__ keys, int64_t m, uint64_t sentinel, uint8_t *__restrict__ f) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
         f[i] = keys[i] != sentinel && (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
 }
@@ -205,6 +214,7 @@ __global__ void unique_flags(const uint64_t *__restrict__ keys, int64_t m, uint6
 __global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ f,
                              const int64_t *__restrict__ pos, int64_t nnz, uint64_t sentinel, int64_t nc,
                              int32_t *__restrict__ col_out, int64_t *__restrict__ rowptr) {
+    GOSH_DEP_WAIT();
     const int64_t m = pos[nnz];
     const uint64_t unc = (uint64_t)nc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
@@ -241,6 +251,7 @@ constexpr int64_t kBitmapMaxDefault = int64_t(1) << 19;
 // a vertex without neighbours (it adds no entries and sorts past every cluster).
 __global__ void member_keys(const int64_t *__restrict__ rowptr, int64_t n, const int32_t *__restrict__ map,
                             uint32_t nc, uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+    GOSH_DEP_WAIT();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         key[v] = rowptr[v + 1] > rowptr[v] ? (uint32_t)map[v] : nc;
         val[v] = (uint32_t)v;
@@ -255,6 +266,7 @@ __global__ void member_keys(const int64_t *__restrict__ rowptr, int64_t n, const
 __global__ void member_layout(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
                               const int64_t *__restrict__ rowptr, int64_t n, uint32_t nc,
                               int64_t *__restrict__ cstart, int32_t *__restrict__ inv, int64_t *__restrict__ mdeg) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = val[i];
         const int64_t k = key[i];
@@ -277,6 +289,7 @@ __global__ void __launch_bounds__(256) member_entries(const int64_t *__restrict_
                                                       const int32_t *__restrict__ map,
                                                       const int32_t *__restrict__ inv,
                                                       const int64_t *__restrict__ moff, int32_t *__restrict__ vb) {
+    GOSH_DEP_WAIT();
     const int lane = threadIdx.x & 31;
     const int64_t nnz = rowptr[n];
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -320,6 +333,7 @@ __global__ void __launch_bounds__(256) member_entries(const int64_t *__restrict_
 
 __global__ void row_chunks(const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff, int64_t nc,
                            int32_t *__restrict__ nchunk, uint8_t *__restrict__ multi, int32_t *__restrict__ count) {
+    GOSH_DEP_WAIT();
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         count[c] = 0;  // rows without entries keep it
         const int64_t len = moff[cstart[c + 1]] - moff[cstart[c]];
@@ -332,6 +346,7 @@ __global__ void row_chunks(const int64_t *__restrict__ cstart, const int64_t *__
 __global__ void chunk_rows(const int64_t *__restrict__ chunk_start, const uint8_t *__restrict__ multi,
                            const int64_t *__restrict__ slot, int64_t nc, int32_t *__restrict__ chunk_row,
                            int32_t *__restrict__ slot_row) {
+    GOSH_DEP_WAIT();
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         for (int64_t t = chunk_start[c]; t < chunk_start[c + 1]; ++t) chunk_row[t] = (int32_t)c;
         if (multi[c]) slot_row[slot[c]] = (int32_t)c;
@@ -489,6 +504,7 @@ __global__ void __launch_bounds__(kRowThreads) coarse_rows(
     const int64_t *__restrict__ slot, int64_t nchunks, int words, int n0, int list_cap, uint32_t *__restrict__ gbm,
     uint32_t *__restrict__ gsum, int32_t *__restrict__ count, const int64_t *__restrict__ rowptr,
     int32_t *__restrict__ col_out) {
+    GOSH_DEP_WAIT();
     extern __shared__ uint32_t smem[];
     uint32_t *bm = smem;
     uint32_t *sum = bm + words;
@@ -552,6 +568,7 @@ template <bool kWrite>
 __global__ void __launch_bounds__(kRowThreads) coarse_rows_multi(
     const int32_t *__restrict__ slot_row, int64_t nslots, int words, int n0, uint32_t *gbm, uint32_t *gsum,
     int32_t *__restrict__ count, const int64_t *__restrict__ rowptr, int32_t *__restrict__ col_out) {
+    GOSH_DEP_WAIT();
     __shared__ int32_t list[kListCap];
     __shared__ int wsum[kRowThreads / 32];
     for (int64_t g = blockIdx.x; g < nslots; g += gridDim.x) {
@@ -615,23 +632,20 @@ gosh_status coarse_graph_sorted(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY(pos.alloc(sizeof(int64_t) * (nnz + 1), s));
     const uint64_t unc = (uint64_t)nc;
     const uint64_t sentinel = unc * unc;
-    (edge_image<<<grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s>>>(rowptr, col, n, map, unc,
-                                                                             ek.as<uint64_t>()),
-     note_launch());
+    launch_dep(edge_image, grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s, rowptr, col, n, map, unc, ek.as<uint64_t>());
     int shifts[8];
     int nd = 0;
     const int kb = bits_for(sentinel);
     for (int b = 0; b < kb && nd < 8; b += 8) shifts[nd++] = b;
     GOSH_TRY(radix_sort_u64(ek.as<uint64_t>(), nullptr, nnz, shifts, nd, s));
-    (unique_flags<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), nnz, sentinel, fl.as<uint8_t>()), note_launch());
+    launch_dep(unique_flags, grid_1d(nnz), 256, 0, s, ek.as<uint64_t>(), nnz, sentinel, fl.as<uint8_t>());
     GOSH_TRY(scan_exclusive_u8_to_i64(fl.as<uint8_t>(), pos.as<int64_t>(), nnz, pos.as<int64_t>() + nnz, s));
     int64_t m = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&m, pos.as<int64_t>() + nnz, sizeof(m), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
     GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
-    (write_coarse<<<grid_1d(nnz), 256, 0, s>>>(ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz,
-                                               sentinel, nc, *co_out, rp), note_launch());
+    launch_dep(write_coarse, grid_1d(nnz), 256, 0, s, ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz, sentinel, nc, *co_out, rp);
     *m_out = m;
     return GOSH_OK;
 }
@@ -658,22 +672,14 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY(cstart_k.alloc(sizeof(int64_t) * (nc + 1), s));
     GOSH_TRY(slot.alloc(sizeof(int64_t) * (nc + 1), s));
     // members grouped by cluster (stable: ascending ids inside a cluster)
-    (member_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, map, (uint32_t)nc, mkey.as<uint32_t>(), mval.as<uint32_t>()),
-     note_launch());
+    launch_dep(member_keys, grid_1d(n), 256, 0, s, rowptr, n, map, (uint32_t)nc, mkey.as<uint32_t>(), mval.as<uint32_t>());
     bool in_alt = false;
     GOSH_TRY(radix_sort_u32_pp(mkey.as<uint32_t>(), mval.as<uint32_t>(), kalt.as<uint32_t>(), valt.as<uint32_t>(), n, 0,
                                bits_for((uint64_t)nc), s, &in_alt));
-    (member_layout<<<grid_1d(n), 256, 0, s>>>(in_alt ? kalt.as<uint32_t>() : mkey.as<uint32_t>(),
-                                              in_alt ? valt.as<uint32_t>() : mval.as<uint32_t>(), rowptr, n,
-                                              (uint32_t)nc, cstart.as<int64_t>(), inv.as<int32_t>(),
-                                              mdeg.as<int64_t>()),
-     note_launch());
+    launch_dep(member_layout, grid_1d(n), 256, 0, s, in_alt ? kalt.as<uint32_t>() : mkey.as<uint32_t>(), in_alt ? valt.as<uint32_t>() : mval.as<uint32_t>(), rowptr, n, (uint32_t)nc, cstart.as<int64_t>(), inv.as<int32_t>(), mdeg.as<int64_t>());
     GOSH_TRY(scan_exclusive_i64(mdeg.as<int64_t>(), moff.as<int64_t>(), n, moff.as<int64_t>() + n, s));
-    (member_entries<<<grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s>>>(
-         rowptr, col, n, map, inv.as<int32_t>(), moff.as<int64_t>(), vb.as<int32_t>()),
-     note_launch());
-    (row_chunks<<<grid_1d(nc), 256, 0, s>>>(cstart.as<int64_t>(), moff.as<int64_t>(), nc, nchunk.as<int32_t>(),
-                                           multi.as<uint8_t>(), count.as<int32_t>()), note_launch());
+    launch_dep(member_entries, grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s, rowptr, col, n, map, inv.as<int32_t>(), moff.as<int64_t>(), vb.as<int32_t>());
+    launch_dep(row_chunks, grid_1d(nc), 256, 0, s, cstart.as<int64_t>(), moff.as<int64_t>(), nc, nchunk.as<int32_t>(), multi.as<uint8_t>(), count.as<int32_t>());
     GOSH_TRY(scan_exclusive_i32_to_i64(nchunk.as<int32_t>(), cstart_k.as<int64_t>(), nc, cstart_k.as<int64_t>() + nc, s));
     GOSH_TRY(scan_exclusive_u8_to_i64(multi.as<uint8_t>(), slot.as<int64_t>(), nc, slot.as<int64_t>() + nc, s));
     int64_t totals[2] = {0, 0};
@@ -690,8 +696,7 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
         GOSH_TRY_CUDA(cudaMemsetAsync(gbm.ptr, 0, sizeof(uint32_t) * nslots * words, s));
         GOSH_TRY_CUDA(cudaMemsetAsync(gsum.ptr, 0, sizeof(uint32_t) * nslots * n0, s));
     }
-    (chunk_rows<<<grid_1d(nc), 256, 0, s>>>(cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nc,
-                                           chunk_row.as<int32_t>(), slot_row.as<int32_t>()), note_launch());
+    launch_dep(chunk_rows, grid_1d(nc), 256, 0, s, cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nc, chunk_row.as<int32_t>(), slot_row.as<int32_t>());
     const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap);
     int grid = 1, mgrid = 1;
     if (nchunks > 0) {
@@ -714,20 +719,12 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
         if (per_sm < 1) per_sm = 1;
         const int64_t cap = (int64_t)num_sms() * per_sm;
         grid = (int)(nchunks < cap ? nchunks : cap);
-        (coarse_rows<false><<<grid, kRowThreads, smem, s>>>(vb.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(),
-                                                           cstart_k.as<int64_t>(), chunk_row.as<int32_t>(),
-                                                           multi.as<uint8_t>(), slot.as<int64_t>(), nchunks, words,
-                                                           n0, list_cap, gbm.as<uint32_t>(), gsum.as<uint32_t>(),
-                                                           count.as<int32_t>(), nullptr, nullptr),
-         note_launch());
+        launch_dep(coarse_rows<false>, grid, kRowThreads, smem, s, vb.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(), cstart_k.as<int64_t>(), chunk_row.as<int32_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nchunks, words, n0, list_cap, gbm.as<uint32_t>(), gsum.as<uint32_t>(), count.as<int32_t>(), nullptr, nullptr);
     }
     if (nslots > 0) {
         const int64_t cap = (int64_t)num_sms() * 8;
         mgrid = (int)(nslots < cap ? nslots : cap);
-        (coarse_rows_multi<false><<<mgrid, kRowThreads, 0, s>>>(slot_row.as<int32_t>(), nslots, words, n0,
-                                                               gbm.as<uint32_t>(), gsum.as<uint32_t>(),
-                                                               count.as<int32_t>(), nullptr, nullptr),
-         note_launch());
+        launch_dep(coarse_rows_multi<false>, mgrid, kRowThreads, 0, s, slot_row.as<int32_t>(), nslots, words, n0, gbm.as<uint32_t>(), gsum.as<uint32_t>(), count.as<int32_t>(), nullptr, nullptr);
     }
     GOSH_TRY(scan_exclusive_i32_to_i64(count.as<int32_t>(), rp, nc, rp + nc, s));
     int64_t m = 0;
@@ -735,17 +732,9 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
     if (nchunks > 0)
-        (coarse_rows<true><<<grid, kRowThreads, smem, s>>>(vb.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(),
-                                                          cstart_k.as<int64_t>(), chunk_row.as<int32_t>(),
-                                                          multi.as<uint8_t>(), slot.as<int64_t>(), nchunks, words,
-                                                          n0, list_cap, gbm.as<uint32_t>(), gsum.as<uint32_t>(),
-                                                          nullptr, rp, *co_out),
-         note_launch());
+        launch_dep(coarse_rows<true>, grid, kRowThreads, smem, s, vb.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(), cstart_k.as<int64_t>(), chunk_row.as<int32_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nchunks, words, n0, list_cap, gbm.as<uint32_t>(), gsum.as<uint32_t>(), nullptr, rp, *co_out);
     if (nslots > 0)
-        (coarse_rows_multi<true><<<mgrid, kRowThreads, 0, s>>>(slot_row.as<int32_t>(), nslots, words, n0,
-                                                              gbm.as<uint32_t>(), gsum.as<uint32_t>(), nullptr, rp,
-                                                              *co_out),
-         note_launch());
+        launch_dep(coarse_rows_multi<true>, mgrid, kRowThreads, 0, s, slot_row.as<int32_t>(), nslots, words, n0, gbm.as<uint32_t>(), gsum.as<uint32_t>(), nullptr, rp, *co_out);
     *m_out = m;
     return GOSH_OK;
 }
@@ -770,13 +759,12 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     GOSH_TRY(counter.alloc(sizeof(unsigned long long) * 2, s));
 
     // 1. degree order (and the initial MIS state)
-    (degree_keys<<<grid_1d(n), 256, 0, s>>>(rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>(), state.as<uint8_t>()),
-     note_launch());
+    launch_dep(degree_keys, grid_1d(n), 256, 0, s, rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>(), state.as<uint8_t>());
     bool in_alt = false;
     GOSH_TRY(radix_sort_u32_pp(keys.as<uint32_t>(), vals.as<uint32_t>(), kalt.as<uint32_t>(), valt.as<uint32_t>(), n, 0,
                                bits_for((uint64_t)(n - 1)), s, &in_alt));
     const uint32_t *order = in_alt ? valt.as<uint32_t>() : vals.as<uint32_t>();
-    (invert_order<<<grid_1d(n), 256, 0, s>>>(order, n, rank.as<int32_t>()), note_launch());
+    launch_dep(invert_order, grid_1d(n), 256, 0, s, order, n, rank.as<int32_t>());
 
     // 2. MIS rounds, two per check of the undecided count (most levels settle
     // in two; a round after settling does nothing)
@@ -789,9 +777,7 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
         }
         GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long) * 2, s));
         for (int r = 0; r < 2; ++r)
-            (mis_round<<<grid_1d(n), 256, 0, s>>>(rowptr, col, n, order, rank.as<int32_t>(), state.as<uint8_t>(),
-                                                 counter.as<unsigned long long>() + r),
-             note_launch());
+            launch_dep(mis_round, grid_1d(n), 256, 0, s, rowptr, col, n, order, rank.as<int32_t>(), state.as<uint8_t>(), counter.as<unsigned long long>() + r);
         GOSH_TRY_CUDA(cudaMemcpyAsync(left, counter.ptr, sizeof(left), cudaMemcpyDeviceToHost, s));
         GOSH_TRY_CUDA(cudaStreamSynchronize(s));
         rounds += 2;
@@ -800,16 +786,13 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
 
     // 3. attach non-hubs, number the clusters by hub rank
     if (nnz > 64 * n)
-        (attach_to_hub_warp<<<grid_warps(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
-                                                          hub_rank.as<int32_t>()), note_launch());
+        launch_dep(attach_to_hub_warp, grid_warps(n), 256, 0, s, rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(), hub_rank.as<int32_t>());
     else
-        (attach_to_hub<<<grid_1d(n), 256, 0, s>>>(rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(),
-                                                     hub_rank.as<int32_t>()), note_launch());
-    (hub_flags_by_rank<<<grid_1d(n), 256, 0, s>>>(order, state.as<uint8_t>(), n, flags.as<uint8_t>()), note_launch());
+        launch_dep(attach_to_hub, grid_1d(n), 256, 0, s, rowptr, col, n, rank.as<int32_t>(), state.as<uint8_t>(), hub_rank.as<int32_t>());
+    launch_dep(hub_flags_by_rank, grid_1d(n), 256, 0, s, order, state.as<uint8_t>(), n, flags.as<uint8_t>());
     GOSH_TRY(scan_exclusive_u8_to_i64(flags.as<uint8_t>(), cid.as<int64_t>(), n, cid.as<int64_t>() + n, s));
     GOSH_TRY_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned long long), s));
-    (assign_map<<<grid_1d(n), 256, 0, s>>>(hub_rank.as<int32_t>(), cid.as<int64_t>(), n, map,
-                                          counter.as<unsigned long long>()), note_launch());
+    launch_dep(assign_map, grid_1d(n), 256, 0, s, hub_rank.as<int32_t>(), cid.as<int64_t>(), n, map, counter.as<unsigned long long>());
     int64_t nc = 0;
     unsigned long long orphans = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&nc, cid.as<int64_t>() + n, sizeof(nc), cudaMemcpyDeviceToHost, s));

@@ -8,6 +8,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "gosh.h"
 
 namespace gosh {
@@ -77,6 +79,28 @@ struct Scratch {
     }
     template <typename T> T *as() const { return static_cast<T *>(ptr); }
 };
+
+// Programmatic dependent launch: the next kernel in the stream is scheduled
+// while this one drains, and waits at GOSH_DEP_WAIT() for it to finish (its
+// writes visible) before touching anything.  Every kernel started through
+// launch_dep must begin with GOSH_DEP_WAIT(); for a plain launch it is a no-op.
+#define GOSH_DEP_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+
+template <typename... KArgs, typename... Args>
+inline void launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    note_launch();
+}
 
 inline int num_sms() {
     static int sms = 0;

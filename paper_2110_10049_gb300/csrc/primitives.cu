@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(kLbThreads) scan_lookback(const In *__restrict
                                                             unsigned long long *status,
                                                             unsigned long long *counter, unsigned long long base,
                                                             uint64_t epoch, int *err) {
+    GOSH_DEP_WAIT();
     __shared__ int64_t sw[33];
     __shared__ int64_t s_tile, s_prefix;
     if (threadIdx.x == 0) s_tile = (int64_t)(atomicAdd(counter, 1ull) - base);
@@ -164,9 +165,7 @@ gosh_status scan_exclusive(const In *in, int64_t *out, int64_t n, int64_t *total
     const int64_t tiles = ceil_div(n, kLbTile);
     LookbackWork *w = nullptr;
     GOSH_TRY(lookback_work(s, tiles, &w));
-    (scan_lookback<In><<<(unsigned)tiles, kLbThreads, 0, s>>>(in, out, n, total, w->status, w->counter, w->base,
-                                                            w->epoch, device_error_word()),
-     note_launch());
+    launch_dep(scan_lookback<In>, (unsigned)tiles, kLbThreads, 0, s, in, out, n, total, w->status, w->counter, w->base, w->epoch, device_error_word());
     w->base += (unsigned long long)tiles;
     GOSH_TRY_CUDA(cudaGetLastError());
     GOSH_TRY_CUDA(cudaEventRecord(w->last, s));
@@ -189,6 +188,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const K *__restrict__ keys, int64_t n, int shift,
                                                            int64_t *__restrict__ counts, int64_t nblocks) {
+    GOSH_DEP_WAIT();
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, int shift, const int64_t *__restrict__ offsets,
     int64_t nblocks) {
+    GOSH_DEP_WAIT();
     __shared__ uint32_t wcnt[kSortWarps][256];
     __shared__ int64_t gbase[256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -274,17 +275,12 @@ gosh_status radix_sort_pp(K *keys, uint32_t *vals, K *kalt, uint32_t *valt, int6
     K *ka = keys, *kb = kalt;
     uint32_t *va = vals, *vb = valt;
     for (int d = 0; d < ndigits; ++d) {
-        (radix_hist<K><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, n, shifts[d], counts.as<int64_t>(), nblocks),
-         note_launch());
+        launch_dep(radix_hist<K>, (unsigned)nblocks, kSortThreads, 0, s, ka, n, shifts[d], counts.as<int64_t>(), nblocks);
         GOSH_TRY(scan_exclusive<int64_t>(counts.as<int64_t>(), offs.as<int64_t>(), 256 * nblocks, nullptr, s));
         if (vals)
-            (radix_scatter<K, true><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shifts[d],
-                                                                              offs.as<int64_t>(), nblocks),
-             note_launch());
+            launch_dep(radix_scatter<K, true>, (unsigned)nblocks, kSortThreads, 0, s, ka, va, kb, vb, n, shifts[d], offs.as<int64_t>(), nblocks);
         else
-            (radix_scatter<K, false><<<(unsigned)nblocks, kSortThreads, 0, s>>>(ka, nullptr, kb, nullptr, n, shifts[d],
-                                                                               offs.as<int64_t>(), nblocks),
-             note_launch());
+            launch_dep(radix_scatter<K, false>, (unsigned)nblocks, kSortThreads, 0, s, ka, nullptr, kb, nullptr, n, shifts[d], offs.as<int64_t>(), nblocks);
         GOSH_TRY_CUDA(cudaGetLastError());
         K *kt = ka; ka = kb; kb = kt;
         uint32_t *vt = va; va = vb; vb = vt;
