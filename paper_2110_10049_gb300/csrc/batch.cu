@@ -118,6 +118,7 @@ __device__ void project_rows(const Phase &ph, int64_t r0, int64_t r1, int lane) 
 
 template <typename T, int D, int L, int P>
 __global__ void __launch_bounds__(kTrainWarps * 32) batch_kernel(BatchArgs b) {
+    GOSH_DEP_WAIT();
     constexpr int MODE = kModeRed;  // atomic row changes (16-bit: stochastically rounded)
     __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
     __shared__ uint32_t s_sr[kTrainWarps][32];
@@ -219,7 +220,7 @@ struct BatchKernel {
 
 template <typename T, int D, int L, int P>
 void launch_batch(const BatchArgs &b, int grid, cudaStream_t s) {
-    (batch_kernel<T, D, L, P><<<grid, kTrainWarps * 32, 0, s>>>(b), note_launch());
+    launch_dep(batch_kernel<T, D, L, P>, grid, kTrainWarps * 32, 0, s, b);
 }
 
 template <typename T, int D, int L, int P>

@@ -87,6 +87,7 @@ enum : unsigned { kBadRowptr = 1, kBadRange = 2, kUnsorted = 4, kSelfLoop = 8, k
 
 __global__ void validate_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, int64_t n,
                                 unsigned *__restrict__ flags, unsigned long long *__restrict__ first_bad) {
+    GOSH_DEP_WAIT();
     const int64_t nnz = rowptr[n];
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = rowptr[v], e = rowptr[v + 1];
@@ -124,6 +125,7 @@ template <> __device__ __forceinline__ __half from_float<__half>(float x) { retu
 
 template <typename T>
 __global__ void init_kernel(T *__restrict__ M, int64_t n, int d, uint32_t level, uint64_t seed, uint64_t graph) {
+    GOSH_DEP_WAIT();
     const int nq = (d + 3) / 4;
     const int64_t total = n * nq;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -145,6 +147,7 @@ __global__ void init_kernel(T *__restrict__ M, int64_t n, int d, uint32_t level,
 // ---------------------------------------------------------------- projection
 __global__ void project_copy_kernel(const uint4 *__restrict__ Mc, const int32_t *__restrict__ map, uint4 *__restrict__ Mf,
                                     int64_t n_fine, int vecs) {
+    GOSH_DEP_WAIT();
     const int64_t total = n_fine * vecs;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = i / vecs;
@@ -154,6 +157,7 @@ __global__ void project_copy_kernel(const uint4 *__restrict__ Mc, const int32_t 
 }
 
 __global__ void map_range_check(const int32_t *__restrict__ map, int64_t n, int64_t nc, unsigned *__restrict__ bad) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         if (map[i] < 0 || map[i] >= nc) atomicOr(bad, 1u);
 }
@@ -162,6 +166,7 @@ __global__ void map_range_check(const int32_t *__restrict__ map, int64_t n, int6
 template <typename T, int L>
 __global__ void pair_scores_kernel(const T *__restrict__ M, int d, const int32_t *__restrict__ pairs, int64_t np,
                                    float *__restrict__ out) {
+    GOSH_DEP_WAIT();
     constexpr int PV = Store<T>::kPerVec;
     constexpr int G = 32 / L;
     const int lane = threadIdx.x & 31, gl = lane % L;
@@ -197,11 +202,12 @@ void launch_pair_scores(const void *M, int d, const int32_t *pairs, int64_t np, 
     int64_t g = ceil_div(groups * L, 256);
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    (pair_scores_kernel<T, L><<<(int)g, 256, 0, s>>>(static_cast<const T *>(M), d, pairs, np, out), note_launch());
+    launch_dep(pair_scores_kernel<T, L>, (int)g, 256, 0, s, static_cast<const T *>(M), d, pairs, np, out);
 }
 
 __global__ void score_keys(const float *__restrict__ score, int64_t n, uint32_t *__restrict__ key,
                            uint32_t *__restrict__ idx) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float f = score[i];
         if (f == 0.0f) f = 0.0f;  // -0 and +0 tie
@@ -212,6 +218,7 @@ __global__ void score_keys(const float *__restrict__ score, int64_t n, uint32_t 
 }
 
 __global__ void neg_flags(const uint32_t *__restrict__ idx, int64_t n, int64_t npos, uint8_t *__restrict__ f) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         f[i] = idx[i] >= (uint64_t)npos ? 1 : 0;
 }
@@ -219,6 +226,7 @@ __global__ void neg_flags(const uint32_t *__restrict__ idx, int64_t n, int64_t n
 __global__ void auc_partials(const uint32_t *__restrict__ key, const uint32_t *__restrict__ idx,
                              const int64_t *__restrict__ neg_before, int64_t n, int64_t npos,
                              double *__restrict__ parts) {
+    GOSH_DEP_WAIT();
     __shared__ double s[256];
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -248,6 +256,7 @@ __global__ void auc_partials(const uint32_t *__restrict__ key, const uint32_t *_
 }
 
 __global__ void sum_partials(const double *__restrict__ parts, int n, double *__restrict__ out) {
+    GOSH_DEP_WAIT();
     __shared__ double s[256];
     double t = 0.0;
     for (int i = threadIdx.x; i < n; i += 256) t += parts[i];
@@ -507,7 +516,7 @@ gosh_status gosh_init_embedding(void *M, int64_t n, int d, gosh_dtype dtype, int
     const int64_t work = n * ((d + 3) / 4);
     GOSH_TRY(by_dtype(dtype, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        (init_kernel<T><<<grid_for(work), 256, 0, s>>>(static_cast<T *>(M), n, d, (uint32_t)level, seed, graph_id), note_launch());
+        launch_dep(init_kernel<T>, grid_for(work), 256, 0, s, static_cast<T *>(M), n, d, (uint32_t)level, seed, graph_id);
     }));
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
@@ -532,6 +541,7 @@ namespace {
 // assignment Store<T>::pack uses for a row's 16-byte vectors.
 __global__ void round_sr_kernel(const float *__restrict__ x, uint16_t *__restrict__ out, int64_t n, uint32_t seed,
                                 int half) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t r = sr_pair_bits(seed + (uint32_t)(i >> 1));
         const uint32_t r16 = (i & 1) ? (r >> 16) : (r & 0xffffu);
@@ -550,9 +560,8 @@ gosh_status gosh_round_stochastic(const float *x, void *out, int64_t n, gosh_dty
     GOSH_CHECK_ARG(dtype == GOSH_BF16 || dtype == GOSH_F16, "dtype must be GOSH_BF16 or GOSH_F16");
     if (n == 0) return GOSH_OK;
     const uint32_t s32 = (uint32_t)seed ^ mix32((uint32_t)(seed >> 32));
-    (round_sr_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(x, static_cast<uint16_t *>(out), n, s32,
-                                                                    dtype == GOSH_F16 ? 1 : 0),
-     note_launch());
+    launch_dep(round_sr_kernel, grid_for(n), 256, 0, (cudaStream_t)stream, x, static_cast<uint16_t *>(out), n, s32,
+                                                                    dtype == GOSH_F16 ? 1 : 0);
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
 }
@@ -566,8 +575,8 @@ gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *
     GOSH_CHECK_ARG(dtype_ok(dtype) && dim_ok(d, dtype), "bad d / dtype");
     cudaStream_t s = (cudaStream_t)stream;
     const int vecs = (int)(d * dtype_size(dtype) / 16);
-    (project_copy_kernel<<<grid_for(n_fine * vecs), 256, 0, s>>>(static_cast<const uint4 *>(M_coarse), map,
-                                                                static_cast<uint4 *>(M_fine), n_fine, vecs), note_launch());
+    launch_dep(project_copy_kernel, grid_for(n_fine * vecs), 256, 0, s, static_cast<const uint4 *>(M_coarse), map,
+                                                                static_cast<uint4 *>(M_fine), n_fine, vecs);
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
 }
@@ -606,13 +615,13 @@ gosh_status gosh_link_auc(const void *M, int d, gosh_dtype dtype, const int32_t 
     GOSH_TRY(out.alloc(sizeof(double), s));
     GOSH_TRY(gosh_pair_scores(M, d, dtype, pos, npos, score.as<float>(), stream));
     GOSH_TRY(gosh_pair_scores(M, d, dtype, neg, nneg, score.as<float>() + npos, stream));
-    (score_keys<<<grid, 256, 0, s>>>(score.as<float>(), n, key.as<uint32_t>(), idx.as<uint32_t>()), note_launch());
+    launch_dep(score_keys, grid, 256, 0, s, score.as<float>(), n, key.as<uint32_t>(), idx.as<uint32_t>());
     GOSH_TRY(radix_sort_u32(key.as<uint32_t>(), idx.as<uint32_t>(), n, 0, 32, s));
-    (neg_flags<<<grid, 256, 0, s>>>(idx.as<uint32_t>(), n, npos, flag.as<uint8_t>()), note_launch());
+    launch_dep(neg_flags, grid, 256, 0, s, idx.as<uint32_t>(), n, npos, flag.as<uint8_t>());
     GOSH_TRY(scan_exclusive_u8_to_i64(flag.as<uint8_t>(), before.as<int64_t>(), n, before.as<int64_t>() + n, s));
-    (auc_partials<<<grid, 256, 0, s>>>(key.as<uint32_t>(), idx.as<uint32_t>(), before.as<int64_t>(), n, npos,
-                                      parts.as<double>()), note_launch());
-    (sum_partials<<<1, 256, 0, s>>>(parts.as<double>(), grid, out.as<double>()), note_launch());
+    launch_dep(auc_partials, grid, 256, 0, s, key.as<uint32_t>(), idx.as<uint32_t>(), before.as<int64_t>(), n, npos,
+                                      parts.as<double>());
+    launch_dep(sum_partials, 1, 256, 0, s, parts.as<double>(), grid, out.as<double>());
     double U = 0.0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&U, out.ptr, sizeof(double), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));

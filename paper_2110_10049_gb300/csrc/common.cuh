@@ -84,7 +84,14 @@ struct Scratch {
 // while this one drains, and waits at GOSH_DEP_WAIT() for it to finish (its
 // writes visible) before touching anything.  Every kernel started through
 // launch_dep must begin with GOSH_DEP_WAIT(); for a plain launch it is a no-op.
+// The one exception is a training epoch, which may draw its samples first:
+// they read only the CSR, which no kernel of a training run writes.
+// GOSH_DEP_TRIGGER() (after the wait) lets the next kernel start while this
+// one still runs; only training epochs of small levels use it, so at most two
+// grids overlap, and the next one's pre-wait part reads nothing the running
+// one writes.
 #define GOSH_DEP_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+#define GOSH_DEP_TRIGGER() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
 
 template <typename... KArgs, typename... Args>
 inline void launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {

@@ -228,6 +228,7 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
 
 template <typename T, int D, int L, int P>
 __global__ void __launch_bounds__(kTrainWarps * 32) pair_kernel(PairArgs a) {
+    GOSH_DEP_WAIT();
     constexpr int MODE = kModeRed;  // atomic row changes (16-bit: stochastically rounded)
     __shared__ int32_t su[kTrainWarps][32 * kMaxSlots];
     __shared__ float slr[kTrainWarps][32 * 8];
@@ -246,7 +247,7 @@ typedef void (*PairLaunch)(const PairArgs &, int, cudaStream_t);
 
 template <typename T, int D, int L, int P>
 void launch_pair(const PairArgs &a, int grid, cudaStream_t s) {
-    (pair_kernel<T, D, L, P><<<grid, kTrainWarps * 32, 0, s>>>(a), note_launch());
+    launch_dep(pair_kernel<T, D, L, P>, grid, kTrainWarps * 32, 0, s, a);
 }
 
 PairLaunch pick_pair_kernel(gosh_dtype dt, int d) {

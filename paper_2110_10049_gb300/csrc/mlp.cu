@@ -68,6 +68,7 @@ int grid_for(int64_t work) {
 }
 
 __global__ void mlp_init_kernel(float *W1, int hid, int din, int kp, uint64_t seed, float a) {
+    GOSH_DEP_WAIT();
     const int64_t total = (int64_t)hid * kp;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t h = i / kp;
@@ -85,6 +86,7 @@ __global__ void mlp_init_kernel(float *W1, int hid, int din, int kp, uint64_t se
 // BF16 working copies: W1b (hid x kp), W2b (d x hid), W2tb (hid x d).
 __global__ void refresh_bf16(const float *W1, const float *W2, __nv_bfloat16 *W1b, __nv_bfloat16 *W2b,
                              __nv_bfloat16 *W2tb, int hid, int kp, int d) {
+    GOSH_DEP_WAIT();
     const int64_t n1 = (int64_t)hid * kp, n2 = (int64_t)d * hid;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2; i += (int64_t)gridDim.x * blockDim.x) {
         if (i < n1) {
@@ -115,6 +117,7 @@ constexpr int kFeatSpan = 1024;
 
 __global__ void feat_degrees(const int64_t *__restrict__ rowptr, int64_t v0, int64_t rows, int64_t stride,
                              int64_t *__restrict__ deg) {
+    GOSH_DEP_WAIT();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = v0 + r * stride;
         deg[r] = rowptr[v + 1] - rowptr[v];
@@ -127,6 +130,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) feat_own(const int32_t *__restrict__ map, const T *__restrict__ Mc,
                                                 const int64_t *__restrict__ voff, int d, int kp, int64_t v0,
                                                 int64_t rows, int64_t stride, __nv_bfloat16 *__restrict__ X) {
+    GOSH_DEP_WAIT();
     constexpr int PV = Store<T>::kPerVec;
     const int lane = threadIdx.x & 31;
     const int V = d / PV;
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(256) feat_spans(const int64_t *__restrict__ ro
                                                   const int64_t *__restrict__ voff, int d, int kp, int64_t v0,
                                                   int64_t rows, int64_t stride, __nv_bfloat16 *__restrict__ X,
                                                   float *__restrict__ slots) {
+    GOSH_DEP_WAIT();
     constexpr int PV = Store<T>::kPerVec;
     const int lane = threadIdx.x & 31;
     const int V = d / PV;
@@ -225,6 +230,7 @@ __global__ void __launch_bounds__(256) feat_spans(const int64_t *__restrict__ ro
 // Rows whose entries cross span boundaries: add the span partials in order.
 __global__ void __launch_bounds__(256) feat_fixup(const int64_t *__restrict__ voff, int d, int kp, int64_t rows,
                                                   const float *__restrict__ slots, __nv_bfloat16 *__restrict__ X) {
+    GOSH_DEP_WAIT();
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -249,6 +255,7 @@ __global__ void __launch_bounds__(256) feat_fixup(const int64_t *__restrict__ vo
 template <typename T>
 __global__ void residual_kernel(const int32_t *__restrict__ map, const T *__restrict__ Mc, const T *__restrict__ Mf,
                                 int d, int64_t v0, int64_t rows, int64_t stride, float *__restrict__ R) {
+    GOSH_DEP_WAIT();
     const int64_t total = rows * d;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / d;
@@ -262,6 +269,7 @@ __global__ void residual_kernel(const int32_t *__restrict__ map, const T *__rest
 __global__ void out_grad_kernel(const float *__restrict__ Yacc, const float *__restrict__ b2,
                                 const float *__restrict__ R, int64_t rows, int d, float scale,
                                 float *__restrict__ G, __nv_bfloat16 *__restrict__ Gb, double *__restrict__ parts) {
+    GOSH_DEP_WAIT();
     __shared__ double s[256];
     double acc = 0.0;
     const int64_t total = rows * d;
@@ -284,6 +292,7 @@ __global__ void out_grad_kernel(const float *__restrict__ Yacc, const float *__r
 // dZ1 = dH * (H > 0): FP32 (for the bias gradient) and BF16 (for dW1).
 __global__ void relu_grad_kernel(const float *__restrict__ dH, const __nv_bfloat16 *__restrict__ H, int64_t total,
                                  float *__restrict__ dZ, __nv_bfloat16 *__restrict__ dZb) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const float g = __bfloat162float(H[i]) > 0.0f ? dH[i] : 0.0f;
         dZ[i] = g;
@@ -299,6 +308,7 @@ constexpr int kColRows = 512;
 
 __global__ void __launch_bounds__(1024) colsum_kernel(const float *__restrict__ G, int64_t rows, int cols,
                                                       float *__restrict__ part) {
+    GOSH_DEP_WAIT();
     __shared__ float p[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + tx;
@@ -316,6 +326,7 @@ __global__ void __launch_bounds__(1024) colsum_kernel(const float *__restrict__ 
 }
 
 __global__ void colsum_finish(const float *__restrict__ part, int nparts, int cols, float *__restrict__ out) {
+    GOSH_DEP_WAIT();
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
         float t = 0.0f;
         for (int i = 0; i < nparts; ++i) t += part[(int64_t)i * cols + c];
@@ -326,6 +337,7 @@ __global__ void colsum_finish(const float *__restrict__ part, int nparts, int co
 // out (cols x ldo) = in^T for in (rows x cols); columns rows..ldo-1 of out are zero.
 __global__ void transpose_bf16(const __nv_bfloat16 *__restrict__ in, int64_t rows, int cols, int64_t ldo,
                                __nv_bfloat16 *__restrict__ out) {
+    GOSH_DEP_WAIT();
     __shared__ __nv_bfloat16 tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -344,6 +356,7 @@ __global__ void transpose_bf16(const __nv_bfloat16 *__restrict__ in, int64_t row
 
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, int64_t n, float lr, float c1, float c2) {
+    GOSH_DEP_WAIT();
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -359,6 +372,7 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
 // of Xc (16-byte vectors; kp * 2 bytes is a multiple of 16).
 __global__ void keep_rows(const __nv_bfloat16 *__restrict__ X, int kp, int64_t v0, int64_t rows, int64_t stride,
                           __nv_bfloat16 *__restrict__ Xc) {
+    GOSH_DEP_WAIT();
     const int vpr = kp * 2 / 16;
     const int64_t j0 = (v0 + stride - 1) / stride, j1 = (v0 + rows + stride - 1) / stride;
     const int64_t total = (j1 - j0) * vpr;
@@ -434,16 +448,17 @@ struct Work {
 void colsum(const float *G, int64_t rows, int cols, float *part, float *out, cudaStream_t s) {
     const int nparts = (int)ceil_div(rows, kColRows);
     dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)nparts);
-    (colsum_kernel<<<grid, 1024, 0, s>>>(G, rows, cols, part), note_launch());
-    (colsum_finish<<<(int)ceil_div(cols, 256), 256, 0, s>>>(part, nparts, cols, out), note_launch());
+    launch_dep(colsum_kernel, grid, 1024, 0, s, G, rows, cols, part);
+    launch_dep(colsum_finish, (int)ceil_div(cols, 256), 256, 0, s, part, nparts, cols, out);
 }
 
 void transpose(const __nv_bfloat16 *in, int64_t rows, int cols, int64_t ldo, __nv_bfloat16 *out, cudaStream_t s) {
     dim3 grid((unsigned)ceil_div(ldo, 32), (unsigned)ceil_div(cols, 32));
-    (transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, ldo, out), note_launch());
+    launch_dep(transpose_bf16, grid, dim3(32, 8), 0, s, in, rows, cols, ldo, out);
 }
 
 __global__ void sum_parts_kernel(const double *__restrict__ parts, int n, double *__restrict__ out, int accumulate) {
+    GOSH_DEP_WAIT();
     __shared__ double s[256];
     double t = 0.0;
     for (int i = threadIdx.x; i < n; i += 256) t += parts[i];
@@ -469,10 +484,9 @@ gosh_status batch_grads(gosh_mlp *m, const __nv_bfloat16 *X, const float *R, int
     GOSH_TRY(gemm_bias_relu(X, kp, m->W1b, kp, m->b1, w.H.as<__nv_bfloat16>(), hid, rows, hid, kp, m->err, s));
     GOSH_TRY(gemm(w.H.as<__nv_bfloat16>(), hid, m->W2b, hid, w.Y.as<float>(), d, rows, d, hid, 1, m->err, s));
     const int go = grid_for((int64_t)rows * d);
-    (out_grad_kernel<<<go, 256, 0, s>>>(w.Y.as<float>(), m->b2, R, rows, d, 2.0f / (float)rows, w.G.as<float>(),
-                                        w.Gb.as<__nv_bfloat16>(), w.parts.as<double>()),
-     note_launch());
-    if (loss_acc) (sum_parts_kernel<<<1, 256, 0, s>>>(w.parts.as<double>(), go, loss_acc, accumulate_loss), note_launch());
+    launch_dep(out_grad_kernel, go, 256, 0, s, w.Y.as<float>(), m->b2, R, rows, d, 2.0f / (float)rows, w.G.as<float>(),
+                                        w.Gb.as<__nv_bfloat16>(), w.parts.as<double>());
+    if (loss_acc) launch_dep(sum_parts_kernel, 1, 256, 0, s, w.parts.as<double>(), go, loss_acc, accumulate_loss);
     // backward
     transpose(w.Gb.as<__nv_bfloat16>(), rows, d, Kb, w.Gt.as<__nv_bfloat16>(), s);
     transpose(w.H.as<__nv_bfloat16>(), rows, hid, Kb, w.Ht.as<__nv_bfloat16>(), s);
@@ -481,9 +495,8 @@ gosh_status batch_grads(gosh_mlp *m, const __nv_bfloat16 *X, const float *R, int
                   splits, m->err, s));
     colsum(w.G.as<float>(), rows, d, w.cpart.as<float>(), w.db2.as<float>(), s);
     GOSH_TRY(gemm(w.Gb.as<__nv_bfloat16>(), d, m->W2tb, d, w.dH.as<float>(), hid, rows, hid, d, 1, m->err, s));
-    (relu_grad_kernel<<<g, 256, 0, s>>>(w.dH.as<float>(), w.H.as<__nv_bfloat16>(), (int64_t)rows * hid,
-                                        w.dZ.as<float>(), w.dZb.as<__nv_bfloat16>()),
-     note_launch());
+    launch_dep(relu_grad_kernel, g, 256, 0, s, w.dH.as<float>(), w.H.as<__nv_bfloat16>(), (int64_t)rows * hid,
+                                        w.dZ.as<float>(), w.dZb.as<__nv_bfloat16>());
     colsum(w.dZ.as<float>(), rows, hid, w.cpart.as<float>(), w.db1.as<float>(), s);
     transpose(w.dZb.as<__nv_bfloat16>(), rows, hid, Kb, w.dZt.as<__nv_bfloat16>(), s);
     transpose(X, rows, kp, Kb, w.Xt.as<__nv_bfloat16>(), s);
@@ -500,7 +513,7 @@ void adam_all(gosh_mlp *m, Work &w, float lr, cudaStream_t s) {
     float *Gs[4] = {w.dW1.as<float>(), w.db1.as<float>(), w.dW2.as<float>(), w.db2.as<float>()};
     const int64_t N[4] = {(int64_t)m->hid * m->kp, m->hid, (int64_t)m->d * m->hid, m->d};
     for (int i = 0; i < 4; ++i)
-        (adam_kernel<<<grid_for(N[i]), 256, 0, s>>>(P[i], Gs[i], m->mo[i], m->ve[i], N[i], lr, c1, c2), note_launch());
+        launch_dep(adam_kernel, grid_for(N[i]), 256, 0, s, P[i], Gs[i], m->mo[i], m->ve[i], N[i], lr, c1, c2);
     (refresh_bf16<<<grid_for((int64_t)m->hid * m->kp + (int64_t)m->d * m->hid), 256, 0, s>>>(
          m->W1, m->W2, m->W1b, m->W2b, m->W2tb, m->hid, m->kp, m->d),
      note_launch());
@@ -523,7 +536,7 @@ gosh_status features(const gosh_csr *g, const int32_t *map, const void *Mc, int 
     Scratch deg, voff;
     GOSH_TRY(deg.alloc(sizeof(int64_t) * rows, s));
     GOSH_TRY(voff.alloc(sizeof(int64_t) * (rows + 1), s));
-    (feat_degrees<<<grid_for(rows), 256, 0, s>>>(g->rowptr, v0, rows, stride, deg.as<int64_t>()), note_launch());
+    launch_dep(feat_degrees, grid_for(rows), 256, 0, s, g->rowptr, v0, rows, stride, deg.as<int64_t>());
     GOSH_TRY(scan_exclusive_i64(deg.as<int64_t>(), voff.as<int64_t>(), rows, voff.as<int64_t>() + rows, s));
     int64_t total = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&total, voff.as<int64_t>() + rows, sizeof(total), cudaMemcpyDeviceToHost, s));
@@ -537,12 +550,11 @@ gosh_status features(const gosh_csr *g, const int32_t *map, const void *Mc, int 
     return by_dtype(dt, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         const T *M = static_cast<const T *>(Mc);
-        (feat_own<T><<<own_blocks, 256, 0, s>>>(map, M, voff.as<int64_t>(), d, kp, v0, rows, stride, X), note_launch());
+        launch_dep(feat_own<T>, own_blocks, 256, 0, s, map, M, voff.as<int64_t>(), d, kp, v0, rows, stride, X);
         if (nspans > 0) {
-            (feat_spans<T><<<span_blocks, 256, 0, s>>>(g->rowptr, g->col, map, M, voff.as<int64_t>(), d, kp, v0, rows,
-                                                      stride, X, slots.as<float>()),
-             note_launch());
-            (feat_fixup<<<own_blocks, 256, 0, s>>>(voff.as<int64_t>(), d, kp, rows, slots.as<float>(), X), note_launch());
+            launch_dep(feat_spans<T>, span_blocks, 256, 0, s, g->rowptr, g->col, map, M, voff.as<int64_t>(), d, kp, v0, rows,
+                                                      stride, X, slots.as<float>());
+            launch_dep(feat_fixup, own_blocks, 256, 0, s, voff.as<int64_t>(), d, kp, rows, slots.as<float>(), X);
         }
     });
 }
@@ -619,10 +631,9 @@ gosh_status mlp_train(gosh_mlp *m, const gosh_csr *g, const int32_t *map, const 
     m->key_Mc = nullptr;  // the kept rows serve one training
     GOSH_TRY(by_dtype(dt, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
-        (residual_kernel<T><<<grid_for(n * d), 256, 0, s>>>(map, static_cast<const T *>(Mc),
+        launch_dep(residual_kernel<T>, grid_for(n * d), 256, 0, s, map, static_cast<const T *>(Mc),
                                                             static_cast<const T *>(Mf), d, 0, n, stride,
-                                                            R.as<float>()),
-         note_launch());
+                                                            R.as<float>());
     }));
     Work w;
     GOSH_TRY(w.alloc(m, batch, s));
@@ -671,9 +682,8 @@ gosh_status mlp_project(gosh_mlp *m, const void *Mc, const int32_t *map, const g
         const int rows = (int)std::min<int64_t>(chunk, n - v0);
         GOSH_TRY(features(g, map, Mc, d, dt, kp, v0, rows, X.as<__nv_bfloat16>(), s));
         if (keep_rows_of != 0)
-            (keep_rows<<<grid_for(ceil_div(rows, stride) * (kp / 8)), 256, 0, s>>>(X.as<__nv_bfloat16>(), kp, v0, rows,
-                                                                                  stride, m->Xc),
-             note_launch());
+            launch_dep(keep_rows, grid_for(ceil_div(rows, stride) * (kp / 8)), 256, 0, s, X.as<__nv_bfloat16>(), kp, v0, rows,
+                                                                                  stride, m->Xc);
         GOSH_TRY(gemm_bias_relu(X.as<__nv_bfloat16>(), kp, m->W1b, kp, m->b1, H.as<__nv_bfloat16>(), hid, rows, hid, kp,
                                 m->err, s));
         // Mf[v] = Mc[map v] + H W2^T + b2, written by the second GEMM's epilogue

@@ -18,7 +18,7 @@ namespace gosh {
 gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lanes, int pass, int64_t n,
                               const TrainKernel **out);
 int train_mode(const gosh_params *p);
-int tile_vertices(const gosh_params *p, int64_t n, int lanes);
+int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass);
 
 namespace {
 
@@ -63,6 +63,7 @@ gosh_status partials_on_current_device(double **out) {
 
 // Sum of the grid's partials into out (fixed order, one block).
 __global__ void noalloc_loss_finalize(const double *__restrict__ parts, int nparts, double *__restrict__ out) {
+    GOSH_DEP_WAIT();
     __shared__ double s[256];
     double t = 0.0;
     for (int i = threadIdx.x; i < nparts; i += 256) t += parts[i];
@@ -103,7 +104,7 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;
     const int cap_blocks = num_sms() * kern->blocks_per_sm;
-    const int64_t want = ceil_div(ceil_div(n, tile_vertices(p, n, kern->lanes)), kern->warps);
+    const int64_t want = ceil_div(ceil_div(n, tile_vertices(p, n, kern->lanes, kern->pass)), kern->warps);
     const int grid = (int)(want < cap_blocks ? (want > 0 ? want : 1) : cap_blocks);
     double *partials = nullptr;
     if (loss_per_epoch) {
@@ -127,13 +128,13 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
     a.loss_partials = partials;
     a.src_begin = 0;
     a.src_end = n;
-    a.tile = tile_vertices(p, n, kern->lanes);
+    a.tile = tile_vertices(p, n, kern->lanes, kern->pass);
     for (int j = 0; j < epochs; ++j) {
         const double f = 1.0 - (double)j / (double)epochs;
         a.lr = (float)(p->lr * (f > p->lr_floor ? f : p->lr_floor));
         a.epoch = (uint32_t)j;
         kern->launch(a, grid, s);
-        if (loss_per_epoch) (noalloc_loss_finalize<<<1, 256, 0, s>>>(partials, grid, loss_per_epoch + j), note_launch());
+        if (loss_per_epoch) launch_dep(noalloc_loss_finalize, 1, 256, 0, s, partials, grid, loss_per_epoch + j);
     }
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;

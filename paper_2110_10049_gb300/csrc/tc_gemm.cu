@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
                                                                 const __grid_constant__ CUtensorMap tmB, GemmEpi ep,
                                                                 int M, int N, int K, int k_per_split,
                                                                 int *__restrict__ err) {
+    GOSH_DEP_WAIT();
     static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "M = 128 needs N in [16, 256], multiple of 16");
     constexpr int S = GemmShape<NT>::kStages;
     constexpr uint32_t kCols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
@@ -302,7 +303,7 @@ gosh_status launch_nt(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *
     kps = (int)ceil_div(kps, 16) * 16;
     const int zs = (int)ceil_div(K, kps);
     dim3 grid((unsigned)ceil_div(M, 128), (unsigned)ceil_div(N, NT), (unsigned)zs);
-    (tma_gemm_kernel<NT, EPI, T><<<grid, kGemmThreads, smem, s>>>(ma, mb, ep, M, N, K, kps, err), note_launch());
+    launch_dep(tma_gemm_kernel<NT, EPI, T>, grid, kGemmThreads, smem, s, ma, mb, ep, M, N, K, kps, err);
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
 }

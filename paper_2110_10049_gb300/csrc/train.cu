@@ -39,6 +39,7 @@ Registry &registry() {
 
 __global__ void loss_finalize(const double *__restrict__ parts, int nparts, double *__restrict__ out,
                               int accumulate) {
+    GOSH_DEP_WAIT();
     __shared__ double s[256];
     double t = 0.0;
     for (int i = threadIdx.x; i < nparts; i += 256) t += parts[i];
@@ -52,6 +53,7 @@ __global__ void loss_finalize(const double *__restrict__ parts, int nparts, doub
 }
 
 __global__ void iota_u32(uint32_t *__restrict__ p, int64_t n) {
+    GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = (uint32_t)i;
 }
@@ -109,9 +111,14 @@ int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) /
 // stores, 16 in the deterministic mode, 32 otherwise);
 // large levels take 32 to amortise the draws.  A multiple of 32/L in
 // [32/L, 32]; params->vertices_per_warp overrides.
-int tile_vertices(const gosh_params *p, int64_t n, int lanes) {
+int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass) {
     const int G = 32 / lanes;
     int t = p->vertices_per_warp;
+    if (t <= 0 && pass < 0 && n < (int64_t(1) << 14)) {
+        // TMA-staged kernel on a small level: about 2048 warps of single
+        // rounds (G sources each), fewer rounds per warp than a fixed tile
+        t = (int)(ceil_div(n, (int64_t)G * 2048) * G);
+    }
     const bool red16 = p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC && !p->plain_stores;
     const bool f32_lockfree = p->dtype == GOSH_F32 && p->mode != GOSH_DETERMINISTIC;
     const int mid = (red16 || f32_lockfree) ? 32 : (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC ? 8 : 16);
@@ -135,31 +142,48 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
     const int nat = natural_lanes(dtype, d);
     // Defaults by level size, from per-level sweeps of lanes per row L,
     // samples per pass P and tile on the R-MAT 20 hierarchy (d = 128, k = 3;
-    // L0 = one 16-byte vector per lane):
-    //  - FP32 lock-free: above 2^19 rows every row staged by TMA (L0); below,
-    //    registers with P = 4 and L0 lanes from 2^14 rows, L0/2 lanes under
-    //    (shorter dependency chains on the latency-bound small levels);
-    //  - 16-bit tables (atomic changes): registers; above 2^19 rows L0/2
-    //    lanes (two vectors per lane, more sources in flight) and P = 2;
-    //    below, L0 lanes (one vector per lane: 80 registers, 24 warps per
-    //    SM) with P = 2, or P = 4 under 2^14 rows; with plain stores, L0/2
-    //    lanes and P = 4 except L0 lanes from 2^16 to 2^19 rows.
+    // L0 = one 16-byte vector per lane; P < 0: rows staged by TMA):
+    //  - FP32 lock-free: above 2^19 rows TMA-staged with L0 lanes; from 2^14
+    //    rows registers, L0 lanes, P = 4; below, TMA-staged with L0/2 lanes
+    //    (a latency-bound level: every row of a round in flight at once);
+    //  - 16-bit tables (atomic changes): above 2^19 rows registers, L0/2
+    //    lanes (two vectors per lane, more sources in flight), P = 2; from
+    //    2^16 rows L0 lanes (one vector per lane: 80 registers, 24 warps per
+    //    SM), P = 2; from 2^14 rows L0/2 lanes, P = 2; below, BF16 tables
+    //    TMA-staged with L0/2 lanes (FP16 has no staged variant: L0 lanes,
+    //    P = 4); with plain stores, L0/2 lanes and P = 4 except L0 lanes from
+    //    2^16 to 2^19 rows.
     if (!det && lanes <= 0 && pass == 0) {
+        const int staged = ns <= 4 ? -4 : -6;
+        const int half = nat >= 4 ? nat / 2 : nat;
         if (dtype == GOSH_F32 && mode == kModeRed) {
             if (n >= (int64_t(1) << 19) && ns <= 6) {
                 lanes = nat;
-                pass = ns <= 4 ? -4 : -6;
+                pass = staged;
             } else if (n >= (int64_t(1) << 14)) {
                 lanes = nat;
                 pass = 4;
             } else {
-                lanes = nat >= 2 ? nat / 2 : nat;
-                pass = 4;
+                lanes = half;
+                pass = ns <= 6 ? staged : 4;
             }
         } else if (dtype != GOSH_F32 && mode == kModeRed) {
-            const bool large = n >= (int64_t(1) << 19);
-            lanes = (large && nat >= 4) ? nat / 2 : nat;
-            pass = (large || n >= (int64_t(1) << 14)) ? 2 : 4;
+            if (n >= (int64_t(1) << 19)) {
+                lanes = half;
+                pass = 2;
+            } else if (n >= (int64_t(1) << 16)) {
+                lanes = nat;
+                pass = 2;
+            } else if (n >= (int64_t(1) << 14)) {
+                lanes = half;
+                pass = 2;
+            } else if (dtype == GOSH_BF16 && ns <= 6) {
+                lanes = half;
+                pass = staged;
+            } else {
+                lanes = nat;
+                pass = 4;
+            }
         } else if (dtype != GOSH_F32) {
             const bool mid = n >= (int64_t(1) << 16) && n < (int64_t(1) << 19);
             lanes = (mid || nat < 4) ? nat : nat / 2;
@@ -213,7 +237,7 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
     a.level = (uint32_t)level;
     a.n_updates = n_updates;
     a.err = device_error_word();
-    a.tile = tile_vertices(p, n, kern->lanes);
+    a.tile = tile_vertices(p, n, kern->lanes, kern->pass);
 
     auto grid_for = [&](int64_t nsrc) {
         const int64_t tiles = ceil_div(nsrc, a.tile);
@@ -226,13 +250,13 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
     a.loss_partials = loss_per_epoch ? parts.as<double>() : nullptr;
 
     if (!det) {
-        const int grid = grid_for(n);
         a.src_begin = 0;
         a.src_end = n;
         // Small levels: every epoch in one cooperative launch (per-epoch
         // launches cost about as much as the epochs' work).
         // Only where one wave holds every tile (more would make warps loop).
         const int coop_cap = num_sms() * kern->epochs_blocks_per_sm;
+        const int grid = grid_for(n);
         if (kern->launch_epochs && !loss_per_epoch && epochs > 1 && kern->epochs_blocks_per_sm > 0 &&
             ceil_div(ceil_div(n, a.tile), kern->warps) <= coop_cap) {
             const int g = grid;
@@ -249,7 +273,7 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
             a.epoch = (uint32_t)j;
             kern->launch(a, grid, s);
             if (loss_per_epoch)
-                (loss_finalize<<<1, 256, 0, s>>>(parts.as<double>(), grid, loss_per_epoch + j, 0), note_launch());
+                launch_dep(loss_finalize, 1, 256, 0, s, parts.as<double>(), grid, loss_per_epoch + j, 0);
         }
         GOSH_TRY_CUDA(cudaGetLastError());
         return GOSH_OK;
@@ -284,8 +308,8 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
             const int grid = grid_for(b1 - b0);
             kern->launch(a, grid, s);
             if (loss_per_epoch)
-                (loss_finalize<<<1, 256, 0, s>>>(parts.as<double>(), grid, loss_per_epoch + j, b0 > 0), note_launch());
-            (iota_u32<<<(int)std::min<int64_t>(ceil_div(nsl, 256), 4096), 256, 0, s>>>(idx.as<uint32_t>(), nsl), note_launch());
+                launch_dep(loss_finalize, 1, 256, 0, s, parts.as<double>(), grid, loss_per_epoch + j, b0 > 0);
+            launch_dep(iota_u32, (int)std::min<int64_t>(ceil_div(nsl, 256), 4096), 256, 0, s, idx.as<uint32_t>(), nsl);
             GOSH_TRY(radix_sort_u32(keys.as<uint32_t>(), idx.as<uint32_t>(), nsl, 0, kbits, s));
             GOSH_TRY_CUDA(cudaMemsetAsync(done.ptr, 0, (size_t)(b1 - b0), s));
             const uint32_t sr = mix32((uint32_t)p->seed ^ mix32((uint32_t)(level << 20) ^ (uint32_t)j)) ^

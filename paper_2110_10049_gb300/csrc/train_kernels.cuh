@@ -122,6 +122,10 @@ __device__ __forceinline__ float group_sum(float x) {
     return x;
 }
 
+// Phases of a tile: the draws (sample ids and rounding seeds into shared
+// memory; they read only the CSR) and the rounds (the row updates).
+constexpr int kTileDraws = 1, kTileRounds = 2;
+
 /*
  * One epoch (Hogwild) or one snapshot batch (deterministic) over sources
  * [src_begin, src_end).  Template: storage T, dimension D, L lanes per source,
@@ -135,7 +139,7 @@ __device__ __forceinline__ float group_sum(float x) {
  *               kept, only read stale;
  *   kModeDet    snapshot batch, changes written to R/C/keys (needs P >= k+1).
  */
-template <typename T, int D, int L, int P, int MODE>
+template <typename T, int D, int L, int P, int MODE, int PHASES = kTileDraws | kTileRounds>
 __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0, int32_t *s_u_w, uint32_t *s_sr_w,
                                            double &loss_acc, unsigned long long &applied) {
     constexpr bool DET = MODE == kModeDet;
@@ -156,7 +160,7 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
     const bool want_loss = a.loss_partials != nullptr;
     {
         // ---- draws: lane j -> source v0 + j ----
-        {
+        if constexpr ((PHASES & kTileDraws) != 0) {
             const int64_t v = v0 + lane;
             if (lane < a.tile && v < a.src_end) {
                 const int64_t off = a.rowptr[v];
@@ -183,6 +187,7 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
             }
         }
         __syncwarp();
+        if constexpr ((PHASES & kTileRounds) == 0) return;
         // ---- rounds: G sources at a time, L lanes each (tile / G rounds) ----
         const int rounds = a.tile / G;
 #pragma unroll 1
@@ -315,8 +320,22 @@ __global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, MODE
     const bool want_loss = a.loss_partials != nullptr;
     double loss_acc = 0.0;
     unsigned long long applied = 0;
-    for (int64_t tile = (int64_t)blockIdx.x * kTrainWarps + warp; tile < ntiles; tile += wstride)
-        train_tile<T, D, L, P, MODE>(a, a.src_begin + tile * a.tile, s_u[warp], s_sr[warp], loss_acc, applied);
+    // The first tile's draws read only the CSR: taken while the previous
+    // kernel of the stream (the previous epoch) still runs.
+    const int64_t first = (int64_t)blockIdx.x * kTrainWarps + warp;
+    if (first < ntiles)
+        train_tile<T, D, L, P, MODE, kTileDraws>(a, a.src_begin + first * a.tile, s_u[warp], s_sr[warp], loss_acc,
+                                                 applied);
+    GOSH_DEP_WAIT();
+    // the next epoch may start early where every warp owns one tile
+    if (ntiles <= wstride) GOSH_DEP_TRIGGER();
+    for (int64_t tile = first; tile < ntiles; tile += wstride) {
+        if (tile == first)
+            train_tile<T, D, L, P, MODE, kTileRounds>(a, a.src_begin + tile * a.tile, s_u[warp], s_sr[warp], loss_acc,
+                                                      applied);
+        else
+            train_tile<T, D, L, P, MODE>(a, a.src_begin + tile * a.tile, s_u[warp], s_sr[warp], loss_acc, applied);
+    }
 
     // ---- monitors ----
     if (a.n_updates) {
@@ -340,7 +359,7 @@ __global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, MODE
 
 template <typename T, int D, int L, int P, int MODE>
 void launch_train(const TrainArgs &a, int grid, cudaStream_t s) {
-    (train_kernel<T, D, L, P, MODE><<<grid, kTrainWarps * 32, 0, s>>>(a), note_launch());
+    launch_dep(train_kernel<T, D, L, P, MODE>, grid, kTrainWarps * 32, 0, s, a);
 }
 
 constexpr uint32_t kEpochBarrierPolls = 1u << 22;
@@ -358,6 +377,7 @@ constexpr uint32_t kEpochBarrierPolls = 1u << 22;
 template <typename T, int D, int L, int P, int MODE>
 __global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, MODE))
     train_epochs_kernel(TrainArgs a, int epochs, double lr, double lr_floor, unsigned int *barrier) {
+    GOSH_DEP_WAIT();
     __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
     __shared__ uint32_t s_sr[kTrainWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -365,12 +385,30 @@ __global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, MODE
     const int64_t wstride = (int64_t)gridDim.x * kTrainWarps;
     double loss_acc = 0.0;
     unsigned long long applied = 0;
+    // A warp that owns at most one tile draws the samples of epoch j+1 (they
+    // read only the CSR) before the barrier that closes epoch j, so an epoch
+    // after the barrier starts with the row loads.
+    const int64_t my_tile = (int64_t)blockIdx.x * kTrainWarps + warp;
+    const bool one_tile = ntiles <= wstride;
+    const int64_t my_v0 = a.src_begin + my_tile * a.tile;
     for (int j = 0; j < epochs; ++j) {
         const double f = 1.0 - (double)j / (double)epochs;
         a.lr = (float)(lr * (f > lr_floor ? f : lr_floor));
         a.epoch = (uint32_t)j;
-        for (int64_t tile = (int64_t)blockIdx.x * kTrainWarps + warp; tile < ntiles; tile += wstride)
-            train_tile<T, D, L, P, MODE>(a, a.src_begin + tile * a.tile, s_u[warp], s_sr[warp], loss_acc, applied);
+        if (one_tile) {
+            if (my_tile < ntiles) {
+                if (j == 0)
+                    train_tile<T, D, L, P, MODE, kTileDraws>(a, my_v0, s_u[warp], s_sr[warp], loss_acc, applied);
+                train_tile<T, D, L, P, MODE, kTileRounds>(a, my_v0, s_u[warp], s_sr[warp], loss_acc, applied);
+                if (j + 1 < epochs) {
+                    a.epoch = (uint32_t)(j + 1);
+                    train_tile<T, D, L, P, MODE, kTileDraws>(a, my_v0, s_u[warp], s_sr[warp], loss_acc, applied);
+                }
+            }
+        } else {
+            for (int64_t tile = my_tile; tile < ntiles; tile += wstride)
+                train_tile<T, D, L, P, MODE>(a, a.src_begin + tile * a.tile, s_u[warp], s_sr[warp], loss_acc, applied);
+        }
         if (j + 1 == epochs) break;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -438,6 +476,7 @@ __global__ void __launch_bounds__(256) det_apply_segments(const uint32_t *__rest
                                                           const float *__restrict__ C, const float *__restrict__ R,
                                                           T *__restrict__ M, int64_t n, int64_t b0, int64_t b1,
                                                           uint8_t *__restrict__ src_done, uint32_t sr_seed) {
+    GOSH_DEP_WAIT();
     constexpr int E = D / L;
     const int gl = threadIdx.x % L;
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
@@ -475,6 +514,7 @@ template <typename T, int D, int L>
 __global__ void __launch_bounds__(256) det_apply_sources(const float *__restrict__ R, T *__restrict__ M,
                                                          int64_t b0, int64_t b1,
                                                          const uint8_t *__restrict__ src_done, uint32_t sr_seed) {
+    GOSH_DEP_WAIT();
     constexpr int E = D / L;
     const int gl = threadIdx.x % L;
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
@@ -503,11 +543,11 @@ void launch_det_apply_t(const uint32_t *skeys, const uint32_t *sidx, int64_t nsl
     const int64_t g2 = ceil_div(b1 - b0, groups_per_block);
     const int cap = num_sms() * 8;
     if (nslots > 0)
-        (det_apply_segments<T, D, LL><<<(int)(g1 < cap ? (g1 > 0 ? g1 : 1) : cap), 256, 0, s>>>(
-            skeys, sidx, nslots, C, R, static_cast<T *>(M), n, b0, b1, src_done, sr_seed), note_launch());
+        launch_dep(det_apply_segments<T, D, LL>, (int)(g1 < cap ? (g1 > 0 ? g1 : 1) : cap), 256, 0, s,
+            skeys, sidx, nslots, C, R, static_cast<T *>(M), n, b0, b1, src_done, sr_seed);
     if (b1 > b0)
-        (det_apply_sources<T, D, LL><<<(int)(g2 < cap ? (g2 > 0 ? g2 : 1) : cap), 256, 0, s>>>(
-            R, static_cast<T *>(M), b0, b1, src_done, sr_seed ^ 0x9e3779b9u), note_launch());
+        launch_dep(det_apply_sources<T, D, LL>, (int)(g2 < cap ? (g2 > 0 ? g2 : 1) : cap), 256, 0, s,
+            R, static_cast<T *>(M), b0, b1, src_done, sr_seed ^ 0x9e3779b9u);
 }
 
 }  // namespace gosh

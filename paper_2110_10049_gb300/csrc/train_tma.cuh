@@ -122,10 +122,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
         }
     };
 
-    for (int64_t tile = (int64_t)blockIdx.x * kTmaWarps + warp; tile < ntiles && !failed;
-         tile += (int64_t)gridDim.x * kTmaWarps) {
-        const int64_t v0 = a.src_begin + tile * a.tile;
-        // ---- draws (as in train_tile) ----
+    // draws of the tile starting at v0 (as in train_tile); they read only the CSR
+    auto draw = [&](int64_t v0) {
         {
             const uint64_t ctr2 = ((uint64_t)a.level << 32) | a.epoch;
             const int64_t v = v0 + lane;
@@ -154,6 +152,24 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
             }
         }
         __syncwarp();
+    };
+
+    // The first tile's draws are taken while the previous kernel of the
+    // stream (the previous epoch) still runs; the rows only after it ended.
+    // (One call site of the draws: a second copy costs registers.)
+    bool waited = false;
+    for (int64_t tile = (int64_t)blockIdx.x * kTmaWarps + warp;; tile += (int64_t)gridDim.x * kTmaWarps) {
+        const bool more = tile < ntiles && !failed;
+        const int64_t v0 = a.src_begin + tile * a.tile;
+        if (more) draw(v0);
+        if (!waited) {
+            GOSH_DEP_WAIT();
+            // let the next epoch start early only where every warp owns one
+            // tile (small levels); on large grids it cost throughput
+            if (ntiles <= (int64_t)gridDim.x * kTmaWarps) GOSH_DEP_TRIGGER();
+            waited = true;
+        }
+        if (!more) break;
         issue(v0, 0, 0);
 #pragma unroll 1
         for (int q = 0; q < rounds; ++q) {
@@ -277,7 +293,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
 template <typename T, int D, int L, int KS, int MODE>
 void launch_train_tma(const TrainArgs &a, int grid, cudaStream_t s) {
     constexpr int smem = kTmaWarps * 2 * tma_stage_bytes<T, D, L, KS>();
-    (train_tma_kernel<T, D, L, KS, MODE><<<grid, kTmaWarps * 32, smem, s>>>(a), note_launch());
+    launch_dep(train_tma_kernel<T, D, L, KS, MODE>, grid, kTmaWarps * 32, smem, s, a);
 }
 
 template <typename T, int D, int L, int KS, int MODE>
