@@ -242,6 +242,7 @@ __global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *_
 // second kernel reads back.  The member order inside a cluster (atomics)
 // does not matter: a bitmap is a set.
 constexpr int kChunk = 4096;
+constexpr int kBatch = 8;                    // loads in flight per thread
 constexpr int kRowThreads = 128;
 constexpr int kSumGroup = 32;                // summary words read back per step
 constexpr int kListCap = kSumGroup * 32;     // nonzero bitmap words per step
@@ -259,18 +260,16 @@ __global__ void member_keys(const int64_t *__restrict__ rowptr, int64_t n, const
 }
 
 // From the members sorted by cluster: cstart[c] = first member of cluster c
-// (cstart[nc] = number of members with neighbours), each member's degree and
-// each vertex's member position inv[v].  A position whose key differs from its
+// (cstart[nc] = number of members with neighbours) and each member's degree.  A position whose key differs from its
 // predecessor's writes the starts of every cluster in between (clusters
 // without such members are empty).
 __global__ void member_layout(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
                               const int64_t *__restrict__ rowptr, int64_t n, uint32_t nc,
-                              int64_t *__restrict__ cstart, int32_t *__restrict__ inv, int64_t *__restrict__ mdeg) {
+                              int64_t *__restrict__ cstart, int64_t *__restrict__ mdeg) {
     GOSH_DEP_WAIT();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = val[i];
         const int64_t k = key[i];
-        inv[v] = (int32_t)i;
         mdeg[i] = rowptr[v + 1] - rowptr[v];
         const int64_t kp = i == 0 ? -1 : (int64_t)key[i - 1];
         for (int64_t c = kp + 1; c <= k; ++c) cstart[c] = i;
@@ -279,54 +278,85 @@ __global__ void member_layout(const uint32_t *__restrict__ key, const uint32_t *
     }
 }
 
-// Cluster id of every CSR entry, written in member order: entry p of row r
-// goes to vb[moff[inv r] + p - rowptr[r]], so the entries of cluster c's
-// members are vb[moff[cstart c] .. moff[cstart c+1]).  Balanced over entries:
-// each warp takes kEntriesPerWarp consecutive entries; a lane finds the row of
-// its first entry by binary search and then walks forward.
+// Last index i in [0, n) with a[i] <= x (a non-decreasing, a[0] <= x), found
+// by the whole warp: each round probes 32 evenly spaced positions, so the
+// range shrinks 32-fold per dependent load instead of 2-fold.
+__device__ __forceinline__ int64_t warp_last_le(const int64_t *__restrict__ a, int64_t n, int64_t x) {
+    const int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t probe = lo + lane * step;
+        const bool ok = probe < hi && __ldg(a + probe) <= x;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        const int64_t k = 31 - __clz(m);  // lane 0 always holds: a[lo] <= x
+        lo += k * step;
+        hi = lo + step < hi ? lo + step : hi;
+    }
+    return lo;
+}
+
+// Cluster id of every CSR entry, written in member order: the entries of
+// member i (vertex mval[i], members sorted by cluster) go to vb[moff[i] ..
+// moff[i+1]), so the entries of cluster c's members are vb[moff[cstart c] ..
+// moff[cstart c+1]).  Balanced over the output: a warp takes kEntriesPerWarp
+// consecutive positions, finds the member holding the first one (one
+// warp-wide search), and walks batches of 32 members whose offsets sit in
+// its lanes: each position finds its member by a shuffle search among them,
+// so the gathers of col and map carry no dependent index loads.
 __global__ void __launch_bounds__(256) member_entries(const int64_t *__restrict__ rowptr,
                                                       const int32_t *__restrict__ col, int64_t n,
                                                       const int32_t *__restrict__ map,
-                                                      const int32_t *__restrict__ inv,
+                                                      const uint32_t *__restrict__ mval,
                                                       const int64_t *__restrict__ moff, int32_t *__restrict__ vb) {
     GOSH_DEP_WAIT();
+    constexpr int U = 4;  // positions per lane per step
     const int lane = threadIdx.x & 31;
-    const int64_t nnz = rowptr[n];
+    const int64_t total = moff[n];
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = wid * kEntriesPerWarp; base < nnz; base += wstride * kEntriesPerWarp) {
-        int64_t p = base + lane;
-        if (p >= nnz) continue;
-        int64_t lo = 0, hi = n;  // last row with rowptr[row] <= p
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (__ldg(rowptr + mid) <= p) lo = mid; else hi = mid;
-        }
-        int64_t r = lo;
-        int64_t rend = __ldg(rowptr + r + 1);
-        int64_t shift = __ldg(moff + __ldg(inv + r)) - __ldg(rowptr + r);
-        const int64_t end = base + kEntriesPerWarp < nnz ? base + kEntriesPerWarp : nnz;
-        // four entries per lane per step, their loads issued together
-        for (; p < end; p += 128) {
-            int64_t dst[4];
-            int32_t y[4];
+    for (int64_t o0 = wid * kEntriesPerWarp; o0 < total; o0 += wstride * kEntriesPerWarp) {
+        const int64_t o1 = o0 + kEntriesPerWarp < total ? o0 + kEntriesPerWarp : total;
+        int64_t i = warp_last_le(moff, n, o0);
+        while (true) {
+            const int64_t im = i + lane;
+            const bool valid = im < n;
+            const int64_t mo = valid ? __ldg(moff + im) : total;
+            const int64_t me = valid ? __ldg(moff + im + 1) : total;
+            const int64_t rs = valid ? __ldg(rowptr + __ldg(mval + im)) : 0;
+            const int64_t first = __shfl_sync(0xffffffffu, mo, 0);
+            if (i >= n || first >= o1) break;
+            const int64_t lo_pos = first > o0 ? first : o0;
+            const int64_t last = __shfl_sync(0xffffffffu, me, 31);
+            const int64_t hi_pos = last < o1 ? last : o1;
+            for (int64_t base = lo_pos; base < hi_pos; base += 32 * U) {
+                int64_t src[U];
+                int32_t y[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t pu = p + 32 * u;
-                while (pu < end && rend <= pu) {
-                    ++r;
-                    rend = __ldg(rowptr + r + 1);
-                    if (rend > pu) shift = __ldg(moff + __ldg(inv + r)) - __ldg(rowptr + r);
+                for (int u = 0; u < U; ++u) {
+                    const int64_t o = base + u * 32 + lane;
+                    int j = 0;  // last lane whose member starts at or before o
+#pragma unroll
+                    for (int w = 16; w > 0; w >>= 1) {
+                        const int64_t t = __shfl_sync(0xffffffffu, mo, j + w);
+                        if (t <= o) j += w;
+                    }
+                    const int64_t s0 = __shfl_sync(0xffffffffu, rs, j);
+                    const int64_t m0 = __shfl_sync(0xffffffffu, mo, j);
+                    src[u] = s0 + (o - m0);
+                    y[u] = o < hi_pos ? __ldg(col + src[u]) : 0;
                 }
-                dst[u] = pu + shift;
-                y[u] = pu < end ? __ldg(col + pu) : 0;
+                int32_t b[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) b[u] = __ldg(map + y[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t o = base + u * 32 + lane;
+                    if (o < hi_pos) vb[o] = b[u];
+                }
             }
-            int32_t b[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) b[u] = __ldg(map + y[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (p + 32 * u < end) vb[dst[u]] = b[u];
+            if (last >= o1) break;
+            i += 32;
         }
     }
 }
@@ -343,13 +373,51 @@ __global__ void row_chunks(const int64_t *__restrict__ cstart, const int64_t *__
     }
 }
 
+// One chunk of a coarse row: entries [e0, e0 + len) of the member-order vb
+// (the row's entries start at rb), cluster c, and whether the row has more
+// than one chunk.  One 24-byte record per chunk instead of a chain of
+// dependent index loads in the kernels that walk the chunks.
+struct ChunkInfo {
+    int64_t e0;
+    int64_t rb;
+    int32_t len;
+    int32_t c;  // bit 31: the row has several chunks
+};
+
 __global__ void chunk_rows(const int64_t *__restrict__ chunk_start, const uint8_t *__restrict__ multi,
-                           const int64_t *__restrict__ slot, int64_t nc, int32_t *__restrict__ chunk_row,
+                           const int64_t *__restrict__ slot, const int64_t *__restrict__ cstart,
+                           const int64_t *__restrict__ moff, int64_t nc, ChunkInfo *__restrict__ info,
                            int32_t *__restrict__ slot_row) {
     GOSH_DEP_WAIT();
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        for (int64_t t = chunk_start[c]; t < chunk_start[c + 1]; ++t) chunk_row[t] = (int32_t)c;
-        if (multi[c]) slot_row[slot[c]] = (int32_t)c;
+    // a thread per cluster reads its layout; the warp then writes the
+    // clusters' chunk records together (a hub's row has many chunks)
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < nc; c0 += stride) {
+        const int64_t c = c0 + lane;
+        int64_t rb = 0, re = 0, t0 = 0, t1 = 0;
+        bool many = false;
+        if (c < nc) {
+            rb = moff[cstart[c]];
+            re = moff[cstart[c + 1]];
+            t0 = chunk_start[c];
+            t1 = chunk_start[c + 1];
+            many = multi[c] != 0;
+            if (many) slot_row[slot[c]] = (int32_t)c;
+        }
+        for (int j = 0; j < 32; ++j) {
+            const int64_t jt0 = __shfl_sync(0xffffffffu, t0, j), jt1 = __shfl_sync(0xffffffffu, t1, j);
+            const int64_t jrb = __shfl_sync(0xffffffffu, rb, j), jre = __shfl_sync(0xffffffffu, re, j);
+            const bool jmany = __shfl_sync(0xffffffffu, many ? 1 : 0, j) != 0;
+            for (int64_t t = jt0 + lane; t < jt1; t += 32) {
+                ChunkInfo ci;
+                ci.e0 = jrb + (t - jt0) * kChunk;
+                ci.rb = jrb;
+                ci.len = (int32_t)(jre - ci.e0 < kChunk ? jre - ci.e0 : kChunk);
+                ci.c = (int32_t)(c0 + j) | (jmany ? (int32_t)0x80000000 : 0);
+                info[t] = ci;
+            }
+        }
     }
 }
 
@@ -469,128 +537,146 @@ __device__ int read_bits_warp(uint32_t *bm, uint32_t *sum, int n0, int32_t *list
     return nout;
 }
 
-// Set bits of a shared-memory bitmap counted (and cleared) by one warp.
-__device__ __forceinline__ int count_bits_warp(uint32_t *bm, uint32_t *sum, int n0) {
-    const int lane = threadIdx.x & 31;
-    int total = 0;
-    for (int s0 = 0; s0 < n0; s0 += 32) {
-        const int s = s0 + lane;
-        uint32_t sw = s < n0 ? sum[s] : 0u;
-        int c = 0;
-        if (sw) sum[s] = 0;
-        while (sw) {
-            const int w = s * 32 + (__ffs(sw) - 1);
-            sw &= sw - 1;
-            c += __popc(bm[w]);
-            bm[w] = 0;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        total += c;
-    }
-    return total;
-}
-
 // One pass over the chunks of the coarse rows (cluster ids of their member
-// entries in vb).  kWrite = false: single-chunk rows count their distinct ids
-// into count[c]; rows of several chunks OR their chunk bitmaps into their
-// global bitmap.  kWrite = true: single-chunk rows rebuild the bitmap and read
-// it back, sorted, into col_out at rowptr[c] (multi-chunk rows are left to
-// coarse_rows_multi).
-template <bool kWrite>
+// entries in vb).  A single-chunk row reads its bitmap back, sorted, over the
+// front of its own vb range (its entries are all in the bitmap by then and no
+// other block reads them) and writes its length to count[c]; rows of several
+// chunks OR their chunk bitmaps into their global bitmap for
+// coarse_rows_multi.  compact_rows then moves every row to its CSR position.
 __global__ void __launch_bounds__(kRowThreads) coarse_rows(
-    const int32_t *__restrict__ vb, const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff,
-    const int64_t *__restrict__ chunk_start, const int32_t *__restrict__ chunk_row, const uint8_t *__restrict__ multi,
-    const int64_t *__restrict__ slot, int64_t nchunks, int words, int n0, int list_cap, uint32_t *__restrict__ gbm,
-    uint32_t *__restrict__ gsum, int32_t *__restrict__ count, const int64_t *__restrict__ rowptr,
-    int32_t *__restrict__ col_out) {
+    int32_t *vb, const ChunkInfo *__restrict__ info, const int64_t *__restrict__ slot, int64_t nchunks, int words,
+    int n0, uint32_t *__restrict__ gbm, uint32_t *__restrict__ gsum, int32_t *__restrict__ count) {
     GOSH_DEP_WAIT();
     extern __shared__ uint32_t smem[];
     uint32_t *bm = smem;
     uint32_t *sum = bm + words;
     int32_t *list = reinterpret_cast<int32_t *>(sum + n0);
-    (void)list_cap;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < words + n0; i += kRowThreads) smem[i] = 0;
     __syncthreads();
-    for (int64_t t = blockIdx.x; t < nchunks; t += gridDim.x) {
-        const int32_t c = chunk_row[t];
-        const bool many = multi[c] != 0;
-        if (kWrite && many) continue;  // the same for every thread of the block
-        const int64_t rb = moff[cstart[c]], re = moff[cstart[c + 1]];
-        const int64_t e0 = rb + (t - chunk_start[c]) * kChunk;
-        const int64_t e1 = e0 + kChunk < re ? e0 + kChunk : re;
-        // Entries crowd onto the hubs' clusters, so most bits are already set:
-        // a plain read first turns those into broadcast loads instead of
-        // atomics serialised on one word.
-        for (int64_t p = e0 + threadIdx.x; p < e1; p += kRowThreads) {
-            const int32_t b = __ldg(vb + p);
+    // Entries crowd onto the hubs' clusters, so most bits are already set: a
+    // plain read first turns those into broadcast loads instead of atomics
+    // serialised on one word.
+    auto set_bits = [&](const int32_t *bs, int32_t c) {
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int32_t b = bs[u];
             const uint32_t bit = 1u << (b & 31);
             if (b == c || (bm[b >> 5] & bit)) continue;
             const uint32_t old = atomicOr(bm + (b >> 5), bit);
             if (old == 0) atomicOr(sum + (b >> 10), 1u << ((b >> 5) & 31));
         }
+    };
+    // kBatch entries per thread from p0 on (the chunk's own id past its end)
+    auto load_batch = [&](int32_t *bs, int64_t p0, int64_t e1, int32_t c) {
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int64_t p = p0 + (int64_t)u * kRowThreads;
+            bs[u] = p < e1 ? vb[p] : c;
+        }
+    };
+    // The first batch of the next chunk is loaded while this chunk is read
+    // back (its range is another cluster's: the read-back never writes it).
+    ChunkInfo cur;
+    int32_t first[kBatch];
+    if (blockIdx.x < nchunks) {
+        cur = info[blockIdx.x];
+        load_batch(first, cur.e0 + threadIdx.x, cur.e0 + cur.len, cur.c & 0x7fffffff);
+    }
+    for (int64_t t = blockIdx.x; t < nchunks; t += gridDim.x) {
+        // the next chunk's record is loaded while this one is worked on
+        ChunkInfo nxt = cur;
+        const bool has_next = t + gridDim.x < nchunks;
+        if (has_next) nxt = info[t + gridDim.x];
+        const int32_t c = cur.c & 0x7fffffff;
+        const bool many = cur.c < 0;
+        const int64_t e0 = cur.e0, e1 = cur.e0 + cur.len;
+        set_bits(first, c);
+        for (int64_t p0 = e0 + threadIdx.x + kBatch * kRowThreads; p0 < e1; p0 += kBatch * kRowThreads) {
+            int32_t bs[kBatch];
+            load_batch(bs, p0, e1, c);
+            set_bits(bs, c);
+        }
         __syncthreads();
+        if (has_next) load_batch(first, nxt.e0 + threadIdx.x, nxt.e0 + nxt.len, nxt.c & 0x7fffffff);
         if (!many) {
             if (warp == 0) {
-                if (kWrite) {
-                    read_bits_warp<true>(bm, sum, n0, list, col_out + rowptr[c]);
-                } else {
-                    const int m = count_bits_warp(bm, sum, n0);
-                    if (lane == 0) count[c] = m;
-                }
+                const int m = read_bits_warp<true>(bm, sum, n0, list, vb + cur.rb);
+                if (lane == 0) count[c] = m;
             }
         } else {
-            // OR the touched words into row c's global bitmap and clear them here
+            // OR the chunk's bitmap into row c's global bitmap, every thread
+            // on its own words, and clear it here
             const int64_t g = slot[c];
             uint32_t *gb = gbm + g * words;
             uint32_t *gs = gsum + g * n0;
             for (int si = threadIdx.x; si < n0; si += kRowThreads) {
-                uint32_t sw = sum[si];
-                if (!sw) continue;
-                atomicOr(gs + si, sw);
-                sum[si] = 0;
-                while (sw) {
-                    const int w = si * 32 + (__ffs(sw) - 1);
-                    sw &= sw - 1;
-                    atomicOr(gb + w, bm[w]);
+                const uint32_t sw = sum[si];
+                if (sw) {
+                    atomicOr(gs + si, sw);
+                    sum[si] = 0;
+                }
+            }
+            for (int w = threadIdx.x; w < words; w += kRowThreads) {
+                const uint32_t x = bm[w];
+                if (x) {
+                    atomicOr(gb + w, x);
                     bm[w] = 0;
                 }
             }
         }
         __syncthreads();
+        cur = nxt;
     }
 }
 
-// Rows of more than one chunk, from their global bitmaps: count (kWrite =
-// false) or read back into col_out at rowptr[c].
-template <bool kWrite>
+// Rows of more than one chunk, from their global bitmaps: read back, sorted,
+// over the front of the row's vb range, length to count[c].
 __global__ void __launch_bounds__(kRowThreads) coarse_rows_multi(
     const int32_t *__restrict__ slot_row, int64_t nslots, int words, int n0, uint32_t *gbm, uint32_t *gsum,
-    int32_t *__restrict__ count, const int64_t *__restrict__ rowptr, int32_t *__restrict__ col_out) {
+    const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff, int32_t *__restrict__ count,
+    int32_t *__restrict__ vb) {
     GOSH_DEP_WAIT();
     __shared__ int32_t list[kListCap];
     __shared__ int wsum[kRowThreads / 32];
     for (int64_t g = blockIdx.x; g < nslots; g += gridDim.x) {
         const int32_t c = slot_row[g];
-        uint32_t *gb = gbm + g * words;
-        const uint32_t *gs = gsum + g * n0;
-        if (kWrite) {
-            read_bits<false>(gb, const_cast<uint32_t *>(gs), n0, list, wsum, col_out + rowptr[c]);
-        } else {
-            int cnt = 0;
-            for (int si = threadIdx.x; si < n0; si += kRowThreads) {
-                uint32_t sw = gs[si];
-                while (sw) {
-                    cnt += __popc(gb[si * 32 + (__ffs(sw) - 1)]);
-                    sw &= sw - 1;
-                }
-            }
-            int tot;
-            block_scan(cnt, wsum, tot);
-            if (threadIdx.x == 0) count[c] = tot;
-        }
+        const int m = read_bits<false>(gbm + g * words, gsum + g * n0, n0, list, wsum, vb + moff[cstart[c]]);
+        if (threadIdx.x == 0) count[c] = m;
         __syncthreads();
+    }
+}
+
+// Row c of the coarse CSR from the front of its vb range to col_out at
+// rowptr[c], in the row's input chunks (a row is no longer than its entries):
+// one warp per chunk, kBatch loads in flight per lane.
+__global__ void compact_rows(const int32_t *__restrict__ vb, const ChunkInfo *__restrict__ info, int64_t nchunks,
+                             const int64_t *__restrict__ rowptr, int32_t *__restrict__ col_out) {
+    GOSH_DEP_WAIT();
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = wid; t < nchunks; t += wstride) {
+        const ChunkInfo ci = info[t];
+        const int32_t c = ci.c & 0x7fffffff;
+        const int64_t len = rowptr[c + 1] - rowptr[c];
+        const int64_t j0 = ci.e0 - ci.rb;
+        const int64_t j1 = j0 + kChunk < len ? j0 + kChunk : len;
+        const int32_t *src = vb + ci.rb;
+        int32_t *dst = col_out + rowptr[c];
+        for (int64_t j = j0 + lane; j < j1; j += kBatch * 32) {
+            int32_t x[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int64_t i = j + u * 32;
+                x[u] = i < j1 ? src[i] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int64_t i = j + u * 32;
+                if (i < j1) dst[i] = x[u];
+            }
+        }
     }
 }
 
@@ -656,14 +742,13 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     const int words = (int)ceil_div(nc, 32);
     const int n0 = (int)ceil_div(words, 32);
     const int list_cap = words < kListCap ? words : kListCap;
-    Scratch mkey, mval, kalt, valt, cstart, inv, mdeg, moff, vb, nchunk, multi, cstart_k, slot, count;
+    Scratch mkey, mval, kalt, valt, cstart, mdeg, moff, vb, nchunk, multi, cstart_k, slot, count;
     GOSH_TRY(mkey.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(mval.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(kalt.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(valt.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(count.alloc(sizeof(int32_t) * nc, s));
     GOSH_TRY(cstart.alloc(sizeof(int64_t) * (nc + 1), s));
-    GOSH_TRY(inv.alloc(sizeof(int32_t) * n, s));
     GOSH_TRY(mdeg.alloc(sizeof(int64_t) * n, s));
     GOSH_TRY(moff.alloc(sizeof(int64_t) * (n + 1), s));
     GOSH_TRY(vb.alloc(sizeof(int32_t) * nnz, s));
@@ -676,9 +761,13 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     bool in_alt = false;
     GOSH_TRY(radix_sort_u32_pp(mkey.as<uint32_t>(), mval.as<uint32_t>(), kalt.as<uint32_t>(), valt.as<uint32_t>(), n, 0,
                                bits_for((uint64_t)nc), s, &in_alt));
-    launch_dep(member_layout, grid_1d(n), 256, 0, s, in_alt ? kalt.as<uint32_t>() : mkey.as<uint32_t>(), in_alt ? valt.as<uint32_t>() : mval.as<uint32_t>(), rowptr, n, (uint32_t)nc, cstart.as<int64_t>(), inv.as<int32_t>(), mdeg.as<int64_t>());
+    const uint32_t *skey = in_alt ? kalt.as<uint32_t>() : mkey.as<uint32_t>();
+    const uint32_t *sval = in_alt ? valt.as<uint32_t>() : mval.as<uint32_t>();
+    launch_dep(member_layout, grid_1d(n), 256, 0, s, skey, sval, rowptr, n, (uint32_t)nc, cstart.as<int64_t>(),
+               mdeg.as<int64_t>());
     GOSH_TRY(scan_exclusive_i64(mdeg.as<int64_t>(), moff.as<int64_t>(), n, moff.as<int64_t>() + n, s));
-    launch_dep(member_entries, grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s, rowptr, col, n, map, inv.as<int32_t>(), moff.as<int64_t>(), vb.as<int32_t>());
+    launch_dep(member_entries, grid_warps(ceil_div(nnz, kEntriesPerWarp)), 256, 0, s, rowptr, col, n, map, sval,
+               moff.as<int64_t>(), vb.as<int32_t>());
     launch_dep(row_chunks, grid_1d(nc), 256, 0, s, cstart.as<int64_t>(), moff.as<int64_t>(), nc, nchunk.as<int32_t>(), multi.as<uint8_t>(), count.as<int32_t>());
     GOSH_TRY(scan_exclusive_i32_to_i64(nchunk.as<int32_t>(), cstart_k.as<int64_t>(), nc, cstart_k.as<int64_t>() + nc, s));
     GOSH_TRY(scan_exclusive_u8_to_i64(multi.as<uint8_t>(), slot.as<int64_t>(), nc, slot.as<int64_t>() + nc, s));
@@ -687,8 +776,8 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     GOSH_TRY_CUDA(cudaMemcpyAsync(totals + 1, slot.as<int64_t>() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     const int64_t nchunks = totals[0], nslots = totals[1];
-    Scratch chunk_row, slot_row, gbm, gsum;
-    GOSH_TRY(chunk_row.alloc(sizeof(int32_t) * nchunks, s));
+    Scratch chunk_info, slot_row, gbm, gsum;
+    GOSH_TRY(chunk_info.alloc(sizeof(ChunkInfo) * nchunks, s));
     GOSH_TRY(slot_row.alloc(sizeof(int32_t) * nslots, s));
     GOSH_TRY(gbm.alloc(sizeof(uint32_t) * nslots * words, s));
     GOSH_TRY(gsum.alloc(sizeof(uint32_t) * nslots * n0, s));
@@ -696,11 +785,11 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
         GOSH_TRY_CUDA(cudaMemsetAsync(gbm.ptr, 0, sizeof(uint32_t) * nslots * words, s));
         GOSH_TRY_CUDA(cudaMemsetAsync(gsum.ptr, 0, sizeof(uint32_t) * nslots * n0, s));
     }
-    launch_dep(chunk_rows, grid_1d(nc), 256, 0, s, cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nc, chunk_row.as<int32_t>(), slot_row.as<int32_t>());
+    launch_dep(chunk_rows, grid_1d(nc), 256, 0, s, cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(),
+               cstart.as<int64_t>(), moff.as<int64_t>(), nc, chunk_info.as<ChunkInfo>(), slot_row.as<int32_t>());
     const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap);
-    int grid = 1, mgrid = 1;
     if (nchunks > 0) {
-        // The attribute is process-wide state of the kernels: set it once to
+        // The attribute is process-wide state of the kernel: set it once to
         // the largest size any level can ask for, so concurrent coarsenings
         // (the batched entry runs several host threads) never lower it under
         // one another's launch.
@@ -709,32 +798,33 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
         std::call_once(attr_once, [] {
             constexpr int64_t w = kBitmapMaxDefault / 32;
             const size_t most = sizeof(uint32_t) * (size_t)(w + ceil_div(w, 32) + kListCap);
-            attr_err = cudaFuncSetAttribute(coarse_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-            if (attr_err == cudaSuccess)
-                attr_err = cudaFuncSetAttribute(coarse_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+            attr_err = cudaFuncSetAttribute(coarse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         });
         GOSH_TRY_CUDA(attr_err);
         int per_sm = 0;
-        GOSH_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_rows<false>, kRowThreads, smem));
+        GOSH_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_rows, kRowThreads, smem));
         if (per_sm < 1) per_sm = 1;
         const int64_t cap = (int64_t)num_sms() * per_sm;
-        grid = (int)(nchunks < cap ? nchunks : cap);
-        launch_dep(coarse_rows<false>, grid, kRowThreads, smem, s, vb.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(), cstart_k.as<int64_t>(), chunk_row.as<int32_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nchunks, words, n0, list_cap, gbm.as<uint32_t>(), gsum.as<uint32_t>(), count.as<int32_t>(), nullptr, nullptr);
+        const int grid = (int)(nchunks < cap ? nchunks : cap);
+        launch_dep(coarse_rows, grid, kRowThreads, smem, s, vb.as<int32_t>(), chunk_info.as<ChunkInfo>(),
+                   slot.as<int64_t>(), nchunks, words, n0, gbm.as<uint32_t>(), gsum.as<uint32_t>(),
+                   count.as<int32_t>());
     }
     if (nslots > 0) {
         const int64_t cap = (int64_t)num_sms() * 8;
-        mgrid = (int)(nslots < cap ? nslots : cap);
-        launch_dep(coarse_rows_multi<false>, mgrid, kRowThreads, 0, s, slot_row.as<int32_t>(), nslots, words, n0, gbm.as<uint32_t>(), gsum.as<uint32_t>(), count.as<int32_t>(), nullptr, nullptr);
+        const int mgrid = (int)(nslots < cap ? nslots : cap);
+        launch_dep(coarse_rows_multi, mgrid, kRowThreads, 0, s, slot_row.as<int32_t>(), nslots, words, n0,
+                   gbm.as<uint32_t>(), gsum.as<uint32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(),
+                   count.as<int32_t>(), vb.as<int32_t>());
     }
     GOSH_TRY(scan_exclusive_i32_to_i64(count.as<int32_t>(), rp, nc, rp + nc, s));
     int64_t m = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&m, rp + nc, sizeof(m), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
-    if (nchunks > 0)
-        launch_dep(coarse_rows<true>, grid, kRowThreads, smem, s, vb.as<int32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(), cstart_k.as<int64_t>(), chunk_row.as<int32_t>(), multi.as<uint8_t>(), slot.as<int64_t>(), nchunks, words, n0, list_cap, gbm.as<uint32_t>(), gsum.as<uint32_t>(), nullptr, rp, *co_out);
-    if (nslots > 0)
-        launch_dep(coarse_rows_multi<true>, mgrid, kRowThreads, 0, s, slot_row.as<int32_t>(), nslots, words, n0, gbm.as<uint32_t>(), gsum.as<uint32_t>(), nullptr, rp, *co_out);
+    if (m > 0)
+        launch_dep(compact_rows, grid_warps(nchunks), 256, 0, s, vb.as<int32_t>(), chunk_info.as<ChunkInfo>(),
+                   nchunks, rp, *co_out);
     *m_out = m;
     return GOSH_OK;
 }
