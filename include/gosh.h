@@ -174,6 +174,21 @@ gosh_status gosh_validate_csr(const gosh_csr *g, void *stream);
 gosh_status gosh_coarsen(const gosh_csr *g0, int threshold, double shrink, int max_levels,
                          void *stream, gosh_hierarchy **out);
 
+/*
+ * gosh_coarsen for n_graphs independent graphs at once (Alg. 4 per graph):
+ * each level is computed for all graphs still coarsening as one disjoint
+ * union (vertex ids graph after graph; the degree order sorts by graph
+ * first), so one sequence of kernels serves every graph.  out[g] receives a
+ * handle equal, level by level, to gosh_coarsen(&graphs[g], ...): the same
+ * maps and coarse CSRs, bit for bit, and the same stopping rule per graph.
+ * graphs: device CSRs with n >= 1 (each must outlive its handle); out:
+ * n_graphs handles, each freed with gosh_hierarchy_free (levels coarsened
+ * together share device buffers, released with the last handle holding
+ * them).  Synchronous.  On error no handle is returned (all are NULL).
+ */
+gosh_status gosh_coarsen_batch(const gosh_csr *graphs, int n_graphs, int threshold, double shrink,
+                               int max_levels, void *stream, gosh_hierarchy **out);
+
 /* Number of graphs D in the hierarchy (G_0 .. G_{D-1}). */
 int gosh_hierarchy_levels(const gosh_hierarchy *h);
 

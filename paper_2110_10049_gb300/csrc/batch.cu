@@ -36,6 +36,8 @@ namespace gosh {
 
 gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int max_levels, cudaStream_t s,
                          gosh_hierarchy **out);
+gosh_status coarsen_batch_impl(const gosh_csr *graphs, int G, int threshold, double shrink, int max_levels,
+                               cudaStream_t s, std::vector<gosh_hierarchy *> &out);
 
 namespace {
 
@@ -468,13 +470,11 @@ extern "C" gosh_status gosh_embed_batch(int n_graphs, const gosh_csr *graphs, co
     const auto t0 = std::chrono::steady_clock::now();
     const size_t row = (size_t)p.d * dtype_size(p.dtype);
 
-    // coarsen every graph: host threads with a stream each take graphs in
-    // turn, so the launches and size read-backs of independent coarsenings
-    // overlap (each coarsening is a sequence of small, dependent steps)
     for (int gi = 0; gi < n_graphs; ++gi) {
         GOSH_CHECK_ARG(graphs[gi].on_device && graphs[gi].n >= 1, "graph %d: needs a device CSR with n >= 1", gi);
         GOSH_CHECK_ARG(((uintptr_t)M_out[gi] & 15) == 0, "graph %d: M_out must be 16-byte aligned", gi);
     }
+    // coarsen every graph: one union of the graphs still coarsening per level
     std::vector<gosh_hierarchy *> hs(n_graphs, nullptr);
     struct Free {
         std::vector<gosh_hierarchy *> &v;
@@ -482,50 +482,7 @@ extern "C" gosh_status gosh_embed_batch(int n_graphs, const gosh_csr *graphs, co
             for (auto *h : v) delete h;
         }
     } free_hs{hs};
-    {
-        int dev = 0;
-        GOSH_TRY_CUDA(cudaGetDevice(&dev));
-        cudaEvent_t ready;
-        GOSH_TRY_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-        GOSH_TRY_CUDA(cudaEventRecord(ready, s));
-        const int hw = (int)std::thread::hardware_concurrency();
-        const int nt = std::max(1, std::min({n_graphs, 8, hw > 0 ? hw : 1}));
-        std::vector<gosh_status> st(nt, GOSH_OK);
-        std::vector<std::string> msg(nt);
-        auto work = [&](int t) {
-            cudaSetDevice(dev);
-            cudaStream_t ts = nullptr;
-            cudaError_t e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(ts, ready, 0);
-            if (e != cudaSuccess) {
-                st[t] = GOSH_ERR_CUDA;
-                msg[t] = std::string("coarsening stream: ") + cudaGetErrorString(e);
-                if (ts) cudaStreamDestroy(ts);
-                return;
-            }
-            for (int gi = t; gi < n_graphs; gi += nt) {
-                const gosh_status r = coarsen_impl(&graphs[gi], p.threshold, p.shrink,
-                                                   p.max_levels > 0 ? p.max_levels : 64, ts, &hs[gi]);
-                if (r != GOSH_OK) {
-                    st[t] = r;
-                    msg[t] = std::string("graph ") + std::to_string(gi) + ": " + gosh_last_error();
-                    break;
-                }
-            }
-            cudaStreamSynchronize(ts);
-            cudaStreamDestroy(ts);
-        };
-        std::vector<std::thread> pool;
-        for (int t = 1; t < nt; ++t) pool.emplace_back(work, t);
-        work(0);
-        for (auto &th : pool) th.join();
-        cudaEventDestroy(ready);
-        for (int t = 0; t < nt; ++t)
-            if (st[t] != GOSH_OK) {
-                set_error("%s", msg[t].c_str());
-                return st[t];
-            }
-    }
+    GOSH_TRY(coarsen_batch_impl(graphs, n_graphs, p.threshold, p.shrink, p.max_levels > 0 ? p.max_levels : 64, s, hs));
     const double coarsen_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 

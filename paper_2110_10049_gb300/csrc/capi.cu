@@ -62,6 +62,8 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
                              cudaStream_t s, double *loss_per_epoch, unsigned long long *n_updates);
 gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int max_levels, cudaStream_t s,
                          gosh_hierarchy **out);
+gosh_status coarsen_batch_impl(const gosh_csr *graphs, int G, int threshold, double shrink, int max_levels,
+                               cudaStream_t s, std::vector<gosh_hierarchy *> &out);
 gosh_status persistent_levels(gosh_hierarchy *h, const std::vector<void *> &bufs, int lowest, const gosh_params &p,
                               unsigned long long *n_updates, cudaStream_t s);
 gosh_status mlp_train(gosh_mlp *m, const gosh_csr *g, const int32_t *map, const void *Mc, const void *Mf,
@@ -465,6 +467,22 @@ gosh_status gosh_coarsen(const gosh_csr *g0, int threshold, double shrink, int m
     GOSH_CHECK_ARG(g0->on_device, "gosh_coarsen needs a device CSR");
     GOSH_CHECK_ARG(shrink > 0 && shrink <= 1, "shrink must be in (0, 1]");
     return coarsen_impl(g0, threshold, shrink, max_levels, (cudaStream_t)stream, out);
+}
+
+gosh_status gosh_coarsen_batch(const gosh_csr *graphs, int n_graphs, int threshold, double shrink, int max_levels,
+                               void *stream, gosh_hierarchy **out) {
+    clear_error();
+    GOSH_CHECK_ARG(out != nullptr && graphs != nullptr && n_graphs >= 1, "bad graphs / n_graphs / out");
+    for (int g = 0; g < n_graphs; ++g) {
+        out[g] = nullptr;
+        GOSH_TRY(check_csr(&graphs[g]));
+        GOSH_CHECK_ARG(graphs[g].on_device && graphs[g].n >= 1, "graph %d: needs a device CSR with n >= 1", g);
+    }
+    GOSH_CHECK_ARG(shrink > 0 && shrink <= 1, "shrink must be in (0, 1]");
+    std::vector<gosh_hierarchy *> hs;
+    GOSH_TRY(coarsen_batch_impl(graphs, n_graphs, threshold, shrink, max_levels, (cudaStream_t)stream, hs));
+    for (int g = 0; g < n_graphs; ++g) out[g] = hs[g];
+    return GOSH_OK;
 }
 
 int gosh_hierarchy_levels(const gosh_hierarchy *h) { return h ? (int)h->n.size() : 0; }

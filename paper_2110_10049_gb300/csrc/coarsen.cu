@@ -20,8 +20,11 @@
 //      over the coarse ids and read back in ascending order (sorted, unique);
 //      above 2^19 coarse vertices, by a radix sort of packed (map v, map u)
 //      keys instead.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -381,13 +384,15 @@ struct ChunkInfo {
     int64_t e0;
     int64_t rb;
     int32_t len;
-    int32_t c;  // bit 31: the row has several chunks
+    int32_t c;     // bit 31: the row has several chunks
+    int32_t base;  // first coarse id of the row's graph (unions of graphs; else 0)
+    int32_t pad;
 };
 
 __global__ void chunk_rows(const int64_t *__restrict__ chunk_start, const uint8_t *__restrict__ multi,
                            const int64_t *__restrict__ slot, const int64_t *__restrict__ cstart,
-                           const int64_t *__restrict__ moff, int64_t nc, ChunkInfo *__restrict__ info,
-                           int32_t *__restrict__ slot_row) {
+                           const int64_t *__restrict__ moff, const int32_t *__restrict__ cbase, int64_t nc,
+                           ChunkInfo *__restrict__ info, int32_t *__restrict__ slot_row) {
     GOSH_DEP_WAIT();
     // a thread per cluster reads its layout; the warp then writes the
     // clusters' chunk records together (a hub's row has many chunks)
@@ -396,8 +401,10 @@ __global__ void chunk_rows(const int64_t *__restrict__ chunk_start, const uint8_
     for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < nc; c0 += stride) {
         const int64_t c = c0 + lane;
         int64_t rb = 0, re = 0, t0 = 0, t1 = 0;
+        int32_t base = 0;
         bool many = false;
         if (c < nc) {
+            if (cbase) base = cbase[c];
             rb = moff[cstart[c]];
             re = moff[cstart[c + 1]];
             t0 = chunk_start[c];
@@ -409,12 +416,15 @@ __global__ void chunk_rows(const int64_t *__restrict__ chunk_start, const uint8_
             const int64_t jt0 = __shfl_sync(0xffffffffu, t0, j), jt1 = __shfl_sync(0xffffffffu, t1, j);
             const int64_t jrb = __shfl_sync(0xffffffffu, rb, j), jre = __shfl_sync(0xffffffffu, re, j);
             const bool jmany = __shfl_sync(0xffffffffu, many ? 1 : 0, j) != 0;
+            const int32_t jbase = __shfl_sync(0xffffffffu, base, j);
             for (int64_t t = jt0 + lane; t < jt1; t += 32) {
                 ChunkInfo ci;
                 ci.e0 = jrb + (t - jt0) * kChunk;
                 ci.rb = jrb;
                 ci.len = (int32_t)(jre - ci.e0 < kChunk ? jre - ci.e0 : kChunk);
                 ci.c = (int32_t)(c0 + j) | (jmany ? (int32_t)0x80000000 : 0);
+                ci.base = jbase;
+                ci.pad = 0;
                 info[t] = ci;
             }
         }
@@ -445,11 +455,12 @@ __device__ __forceinline__ int block_scan(int x, int *wsum, int &total) {
     return off + incl - x;
 }
 
-// Writes the set bits of bm (its nonzero words flagged in sum, n0 summary
-// words) in ascending order to out and returns their number (in every
+// Writes base + the set bits of bm (its nonzero words flagged in sum, n0
+// summary words) in ascending order to out and returns their number (in every
 // thread).  kClear: zero the visited words (shared-memory bitmaps are reused).
 template <bool kClear>
-__device__ int read_bits(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int *wsum, int32_t *__restrict__ out) {
+__device__ int read_bits(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int *wsum, int32_t *__restrict__ out,
+                         int32_t base) {
     int nout = 0;
     for (int s0 = 0; s0 < n0; s0 += kSumGroup) {
         const int s = s0 + threadIdx.x;
@@ -475,7 +486,7 @@ __device__ int read_bits(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int
             int tot;
             int at = nout + block_scan(__popc(bits), wsum, tot);
             while (bits) {
-                out[at++] = w * 32 + (__ffs(bits) - 1);
+                out[at++] = base + w * 32 + (__ffs(bits) - 1);
                 bits &= bits - 1;
             }
             nout += tot;
@@ -498,7 +509,8 @@ __device__ __forceinline__ int warp_incl_scan(int x) {
 }
 
 template <bool kClear>
-__device__ int read_bits_warp(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int32_t *__restrict__ out) {
+__device__ int read_bits_warp(uint32_t *bm, uint32_t *sum, int n0, int32_t *list, int32_t *__restrict__ out,
+                              int32_t base) {
     const int lane = threadIdx.x & 31;
     int nout = 0;
     for (int s0 = 0; s0 < n0; s0 += 32) {
@@ -527,7 +539,7 @@ __device__ int read_bits_warp(uint32_t *bm, uint32_t *sum, int n0, int32_t *list
             const int ib = warp_incl_scan(cb);
             int at = nout + ib - cb;
             while (bits) {
-                out[at++] = w * 32 + (__ffs(bits) - 1);
+                out[at++] = base + w * 32 + (__ffs(bits) - 1);
                 bits &= bits - 1;
             }
             nout += __shfl_sync(0xffffffffu, ib, 31);
@@ -557,12 +569,13 @@ __global__ void __launch_bounds__(kRowThreads) coarse_rows(
     // Entries crowd onto the hubs' clusters, so most bits are already set: a
     // plain read first turns those into broadcast loads instead of atomics
     // serialised on one word.
-    auto set_bits = [&](const int32_t *bs, int32_t c) {
+    auto set_bits = [&](const int32_t *bs, int32_t c, int32_t base) {
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-            const int32_t b = bs[u];
+            if (bs[u] == c) continue;
+            const int32_t b = bs[u] - base;  // id within the row's graph
             const uint32_t bit = 1u << (b & 31);
-            if (b == c || (bm[b >> 5] & bit)) continue;
+            if (bm[b >> 5] & bit) continue;
             const uint32_t old = atomicOr(bm + (b >> 5), bit);
             if (old == 0) atomicOr(sum + (b >> 10), 1u << ((b >> 5) & 31));
         }
@@ -591,17 +604,17 @@ __global__ void __launch_bounds__(kRowThreads) coarse_rows(
         const int32_t c = cur.c & 0x7fffffff;
         const bool many = cur.c < 0;
         const int64_t e0 = cur.e0, e1 = cur.e0 + cur.len;
-        set_bits(first, c);
+        set_bits(first, c, cur.base);
         for (int64_t p0 = e0 + threadIdx.x + kBatch * kRowThreads; p0 < e1; p0 += kBatch * kRowThreads) {
             int32_t bs[kBatch];
             load_batch(bs, p0, e1, c);
-            set_bits(bs, c);
+            set_bits(bs, c, cur.base);
         }
         __syncthreads();
         if (has_next) load_batch(first, nxt.e0 + threadIdx.x, nxt.e0 + nxt.len, nxt.c & 0x7fffffff);
         if (!many) {
             if (warp == 0) {
-                const int m = read_bits_warp<true>(bm, sum, n0, list, vb + cur.rb);
+                const int m = read_bits_warp<true>(bm, sum, n0, list, vb + cur.rb, cur.base);
                 if (lane == 0) count[c] = m;
             }
         } else {
@@ -634,14 +647,15 @@ __global__ void __launch_bounds__(kRowThreads) coarse_rows(
 // over the front of the row's vb range, length to count[c].
 __global__ void __launch_bounds__(kRowThreads) coarse_rows_multi(
     const int32_t *__restrict__ slot_row, int64_t nslots, int words, int n0, uint32_t *gbm, uint32_t *gsum,
-    const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff, int32_t *__restrict__ count,
-    int32_t *__restrict__ vb) {
+    const int64_t *__restrict__ cstart, const int64_t *__restrict__ moff, const int32_t *__restrict__ cbase,
+    int32_t *__restrict__ count, int32_t *__restrict__ vb) {
     GOSH_DEP_WAIT();
     __shared__ int32_t list[kListCap];
     __shared__ int wsum[kRowThreads / 32];
     for (int64_t g = blockIdx.x; g < nslots; g += gridDim.x) {
         const int32_t c = slot_row[g];
-        const int m = read_bits<false>(gbm + g * words, gsum + g * n0, n0, list, wsum, vb + moff[cstart[c]]);
+        const int m = read_bits<false>(gbm + g * words, gsum + g * n0, n0, list, wsum, vb + moff[cstart[c]],
+                                       cbase ? cbase[c] : 0);
         if (threadIdx.x == 0) count[c] = m;
         __syncthreads();
     }
@@ -737,9 +751,12 @@ gosh_status coarse_graph_sorted(int64_t n, const int64_t *rowptr, const int32_t 
 }
 
 // Coarse CSR through per-row bitmaps (coarse_rows); nc <= bitmap_limit().
+// width: the bitmaps' span of coarse ids (nc; for a union of graphs the most
+// clusters of one graph, with cbase[c] the first coarse id of row c's graph).
 gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *map, int64_t nc,
-                                int64_t nnz, int64_t *rp, int32_t **co_out, int64_t *m_out, cudaStream_t s) {
-    const int words = (int)ceil_div(nc, 32);
+                                int64_t nnz, int64_t width, const int32_t *cbase, int64_t *rp, int32_t **co_out,
+                                int64_t *m_out, cudaStream_t s) {
+    const int words = (int)ceil_div(width, 32);
     const int n0 = (int)ceil_div(words, 32);
     const int list_cap = words < kListCap ? words : kListCap;
     Scratch mkey, mval, kalt, valt, cstart, mdeg, moff, vb, nchunk, multi, cstart_k, slot, count;
@@ -786,7 +803,7 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
         GOSH_TRY_CUDA(cudaMemsetAsync(gsum.ptr, 0, sizeof(uint32_t) * nslots * n0, s));
     }
     launch_dep(chunk_rows, grid_1d(nc), 256, 0, s, cstart_k.as<int64_t>(), multi.as<uint8_t>(), slot.as<int64_t>(),
-               cstart.as<int64_t>(), moff.as<int64_t>(), nc, chunk_info.as<ChunkInfo>(), slot_row.as<int32_t>());
+               cstart.as<int64_t>(), moff.as<int64_t>(), cbase, nc, chunk_info.as<ChunkInfo>(), slot_row.as<int32_t>());
     const size_t smem = sizeof(uint32_t) * ((size_t)words + n0 + list_cap);
     if (nchunks > 0) {
         // The attribute is process-wide state of the kernel: set it once to
@@ -814,7 +831,7 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
         const int64_t cap = (int64_t)num_sms() * 8;
         const int mgrid = (int)(nslots < cap ? nslots : cap);
         launch_dep(coarse_rows_multi, mgrid, kRowThreads, 0, s, slot_row.as<int32_t>(), nslots, words, n0,
-                   gbm.as<uint32_t>(), gsum.as<uint32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(),
+                   gbm.as<uint32_t>(), gsum.as<uint32_t>(), cstart.as<int64_t>(), moff.as<int64_t>(), cbase,
                    count.as<int32_t>(), vb.as<int32_t>());
     }
     GOSH_TRY(scan_exclusive_i32_to_i64(count.as<int32_t>(), rp, nc, rp + nc, s));
@@ -829,13 +846,148 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     return GOSH_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Unions of graphs.  Many graphs are coarsened as one disjoint union: slot j
+// holds the vertices [vo[j], vo[j+1]) (ids graph-major).  The degree order
+// sorts by (slot, descending degree, id), so every graph keeps its own rank
+// order, its hubs are numbered consecutively from the union's count of hubs
+// in earlier slots, and each graph's maps and coarse CSR equal those of
+// coarsening it alone once that first id is subtracted.
+// ---------------------------------------------------------------------------
+
+// Last i in [0, n) with a[i] <= x (a non-decreasing, a[0] <= x).
+__device__ __forceinline__ int last_le(const int64_t *__restrict__ a, int n, int64_t x) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Key (slot << bn) | (nmax - 1 - deg): graph-major, descending degree inside
+// a graph; the density test uses the vertex's own graph.
+__global__ void degree_keys_union(const int64_t *__restrict__ rowptr, int64_t n, const int32_t *__restrict__ vslot,
+                                  const int64_t *__restrict__ slot_n, const int64_t *__restrict__ slot_nnz,
+                                  int64_t nmax, int bn, uint32_t *__restrict__ key, uint32_t *__restrict__ val,
+                                  uint8_t *__restrict__ state) {
+    GOSH_DEP_WAIT();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t deg = rowptr[v + 1] - rowptr[v];
+        const int j = vslot[v];
+        key[v] = ((uint32_t)j << bn) | (deg < nmax ? (uint32_t)(nmax - 1 - deg) : 0u);
+        val[v] = (uint32_t)v;
+        state[v] = small_deg(deg, slot_n[j], slot_nnz[j]) ? kUndecided : kHub;
+    }
+}
+
+// out[j] = src[idx[j]] for j < m
+__global__ void gather_at(const int64_t *__restrict__ src, const int64_t *__restrict__ idx, int m,
+                          int64_t *__restrict__ out) {
+    GOSH_DEP_WAIT();
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) out[j] = src[idx[j]];
+}
+
+// cbase[c] = first coarse id of the slot holding cluster c
+__global__ void fill_cbase(const int64_t *__restrict__ cid_at, int nslots, int64_t nc, int32_t *__restrict__ cbase) {
+    GOSH_DEP_WAIT();
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        cbase[c] = (int32_t)cid_at[last_le(cid_at, nslots, c)];
+}
+
+struct SlotIn {
+    const int64_t *rowptr;
+    const int32_t *col;
+};
+struct SlotOut {
+    int32_t *map;
+    int64_t *rp;
+    int32_t *col;
+};
+
+// union CSR rows (and the slot of every vertex)
+__global__ void union_rows(const SlotIn *__restrict__ in, const int64_t *__restrict__ vo,
+                           const int64_t *__restrict__ eo, int nslots, int64_t n, int64_t nnz,
+                           int64_t *__restrict__ rowptr_u, int32_t *__restrict__ vslot) {
+    GOSH_DEP_WAIT();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= n; r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == n) {
+            rowptr_u[n] = nnz;
+            continue;
+        }
+        const int j = last_le(vo, nslots, r);
+        rowptr_u[r] = eo[j] + in[j].rowptr[r - vo[j]];
+        vslot[r] = j;
+    }
+}
+
+// union CSR entries: neighbour ids shifted by their graph's first vertex
+__global__ void union_cols(const SlotIn *__restrict__ in, const int64_t *__restrict__ vo,
+                           const int64_t *__restrict__ eo, int nslots, int64_t nnz, int32_t *__restrict__ col_u) {
+    GOSH_DEP_WAIT();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = last_le(eo, nslots, e);
+        col_u[e] = in[j].col[e - eo[j]] + (int32_t)vo[j];
+    }
+}
+
+// per-graph maps (cluster ids minus the graph's first cluster id)
+__global__ void split_maps(const int32_t *__restrict__ map_u, const int32_t *__restrict__ vslot,
+                           const int64_t *__restrict__ vo, const int64_t *__restrict__ cid_at, int64_t n,
+                           const SlotOut *__restrict__ out) {
+    GOSH_DEP_WAIT();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int j = vslot[r];
+        out[j].map[r - vo[j]] = map_u[r] - (int32_t)cid_at[j];
+    }
+}
+
+// per-graph coarse row pointers (rows [cid_at[j], cid_at[j+1]) of the union,
+// entries from ceo[j]); thread t < nslots also writes graph t's final pointer
+__global__ void split_rows(const int64_t *__restrict__ rp_u, const int64_t *__restrict__ cid_at,
+                           const int64_t *__restrict__ ceo, int nslots, int64_t nc, const SlotOut *__restrict__ out) {
+    GOSH_DEP_WAIT();
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc + nslots;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (c < nc) {
+            const int j = last_le(cid_at, nslots, c);
+            out[j].rp[c - cid_at[j]] = rp_u[c] - ceo[j];
+        } else {
+            const int j = (int)(c - nc);
+            out[j].rp[cid_at[j + 1] - cid_at[j]] = ceo[j + 1] - ceo[j];
+        }
+    }
+}
+
+// per-graph coarse entries
+__global__ void split_cols(const int32_t *__restrict__ co_u, const int64_t *__restrict__ ceo,
+                           const int64_t *__restrict__ cid_at, int nslots, int64_t m,
+                           const SlotOut *__restrict__ out) {
+    GOSH_DEP_WAIT();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = last_le(ceo, nslots, e);
+        out[j].col[e - ceo[j]] = co_u[e] - (int32_t)cid_at[j];
+    }
+}
+
 }  // namespace
 
 // One level: map (device, caller-allocated int32[n]); the coarse CSR is
 // allocated with cudaMalloc into *rp_out / *col_out.  Synchronous.
+// A union of graphs for mec_level (device arrays; cid_at is returned).
+struct UnionLevel {
+    int nslots = 0;
+    int64_t nmax = 0;                  // most vertices of one graph
+    const int32_t *vslot = nullptr;    // slot of every vertex
+    const int64_t *slot_n = nullptr;   // vertices of every slot
+    const int64_t *slot_nnz = nullptr; // entries of every slot
+    const int64_t *vo = nullptr;       // nslots + 1 first vertices
+    std::vector<int64_t> cid_at;       // out: nslots + 1 first cluster ids
+};
+
 gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int64_t nnz, int32_t *map,
                       int64_t *nc_out, int64_t **rp_out, int32_t **col_out, int64_t *nnz_out, int *rounds_out,
-                      cudaStream_t s) {
+                      cudaStream_t s, UnionLevel *u) {
     Scratch keys, vals, kalt, valt, rank, state, hub_rank, flags, cid, counter;
     GOSH_TRY(keys.alloc(sizeof(uint32_t) * n, s));
     GOSH_TRY(vals.alloc(sizeof(uint32_t) * n, s));
@@ -849,10 +1001,19 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     GOSH_TRY(counter.alloc(sizeof(unsigned long long) * 2, s));
 
     // 1. degree order (and the initial MIS state)
-    launch_dep(degree_keys, grid_1d(n), 256, 0, s, rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>(), state.as<uint8_t>());
+    int key_bits = bits_for((uint64_t)(n - 1));
+    if (u) {
+        const int bn = bits_for((uint64_t)(u->nmax - 1));
+        key_bits = bn + bits_for((uint64_t)(u->nslots - 1));
+        launch_dep(degree_keys_union, grid_1d(n), 256, 0, s, rowptr, n, u->vslot, u->slot_n, u->slot_nnz, u->nmax, bn,
+                   keys.as<uint32_t>(), vals.as<uint32_t>(), state.as<uint8_t>());
+    } else {
+        launch_dep(degree_keys, grid_1d(n), 256, 0, s, rowptr, n, keys.as<uint32_t>(), vals.as<uint32_t>(),
+                   state.as<uint8_t>());
+    }
     bool in_alt = false;
     GOSH_TRY(radix_sort_u32_pp(keys.as<uint32_t>(), vals.as<uint32_t>(), kalt.as<uint32_t>(), valt.as<uint32_t>(), n, 0,
-                               bits_for((uint64_t)(n - 1)), s, &in_alt));
+                               key_bits, s, &in_alt));
     const uint32_t *order = in_alt ? valt.as<uint32_t>() : vals.as<uint32_t>();
     launch_dep(invert_order, grid_1d(n), 256, 0, s, order, n, rank.as<int32_t>());
 
@@ -885,12 +1046,31 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     launch_dep(assign_map, grid_1d(n), 256, 0, s, hub_rank.as<int32_t>(), cid.as<int64_t>(), n, map, counter.as<unsigned long long>());
     int64_t nc = 0;
     unsigned long long orphans = 0;
+    Scratch cid_at;
+    if (u) {
+        // first cluster id of every slot (its hubs come after all earlier slots')
+        GOSH_TRY(cid_at.alloc(sizeof(int64_t) * (u->nslots + 1), s));
+        launch_dep(gather_at, grid_1d(u->nslots + 1), 256, 0, s, cid.as<int64_t>(), u->vo, u->nslots + 1,
+                   cid_at.as<int64_t>());
+        u->cid_at.assign(u->nslots + 1, 0);
+        GOSH_TRY_CUDA(cudaMemcpyAsync(u->cid_at.data(), cid_at.ptr, sizeof(int64_t) * (u->nslots + 1),
+                                      cudaMemcpyDeviceToHost, s));
+    }
     GOSH_TRY_CUDA(cudaMemcpyAsync(&nc, cid.as<int64_t>() + n, sizeof(nc), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaMemcpyAsync(&orphans, counter.ptr, sizeof(orphans), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
     if (orphans) {
         set_error("coarsening: %llu vertices without a cluster root", orphans);
         return GOSH_ERR_CUDA;
+    }
+    // bitmap span: the most clusters of one graph (ids taken from the graph's first)
+    int64_t width = nc;
+    Scratch cbase;
+    if (u) {
+        width = 0;
+        for (int j = 0; j < u->nslots; ++j) width = std::max<int64_t>(width, u->cid_at[j + 1] - u->cid_at[j]);
+        GOSH_TRY(cbase.alloc(sizeof(int32_t) * (nc > 0 ? nc : 1), s));
+        launch_dep(fill_cbase, grid_1d(nc), 256, 0, s, cid_at.as<int64_t>(), u->nslots, nc, cbase.as<int32_t>());
     }
     keys.release();
     vals.release();
@@ -906,8 +1086,9 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     // hierarchy buffers come from the stream-ordered pool (no device-wide sync)
     GOSH_TRY_CUDA(cudaMallocAsync(&rp, sizeof(int64_t) * (nc + 1), s));
     int64_t m = 0;
-    if (nnz > 0 && nc <= bitmap_limit()) {
-        GOSH_TRY(coarse_graph_bitmap(n, rowptr, col, map, nc, nnz, rp, &co, &m, s));
+    if (nnz > 0 && width <= bitmap_limit()) {
+        GOSH_TRY(coarse_graph_bitmap(n, rowptr, col, map, nc, nnz, width, u ? cbase.as<int32_t>() : nullptr, rp, &co,
+                                     &m, s));
     } else if (nnz > 0) {
         GOSH_TRY(coarse_graph_sorted(n, rowptr, col, map, nc, nnz, rp, &co, &m, s));
     } else {
@@ -948,10 +1129,11 @@ gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int m
             return GOSH_ERR_OOM;
         }
         h->map.push_back(map);
+        h->owned.push_back(device_owner(map));
         int64_t nc = 0, m = 0;
         int64_t *rp = nullptr;
         int32_t *co = nullptr;
-        gosh_status st = mec_level(n, h->rowptr[i], h->col[i], h->nnz[i], map, &nc, &rp, &co, &m, nullptr, s);
+        gosh_status st = mec_level(n, h->rowptr[i], h->col[i], h->nnz[i], map, &nc, &rp, &co, &m, nullptr, s, nullptr);
         if (st != GOSH_OK) {
             delete h;
             return st;
@@ -960,6 +1142,8 @@ gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int m
         h->nnz.push_back(m);
         h->rowptr.push_back(rp);
         h->col.push_back(co);
+        h->owned.push_back(device_owner(rp));
+        h->owned.push_back(device_owner(co));
         const bool more = nc > threshold && (double)nc <= std::floor(shrink * (double)n);
         if (!more || (int)h->n.size() >= max_levels) break;
     }
@@ -970,6 +1154,206 @@ gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int m
         return GOSH_ERR_CUDA;
     }
     *out = h;
+    return GOSH_OK;
+}
+
+
+namespace {
+
+// sizes of the G input graphs' CSRs: nnz[g] = rowptr_g[n_g]
+__global__ void input_nnz(const SlotIn *__restrict__ in, const int64_t *__restrict__ n, int G,
+                          int64_t *__restrict__ nnz) {
+    GOSH_DEP_WAIT();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) nnz[g] = in[g].rowptr[n[g]];
+}
+
+// One level of the graphs in `slots` (each at its hierarchy's last level),
+// coarsened as one union; appends the map and the coarse level to each.
+gosh_status union_level(const std::vector<int> &slots, std::vector<gosh_hierarchy *> &hs, cudaStream_t s) {
+    const int A = (int)slots.size();
+    std::vector<int64_t> vo(A + 1, 0), eo(A + 1, 0), sn(A), snnz(A);
+    std::vector<SlotIn> in(A);
+    int64_t nmax = 0;
+    for (int j = 0; j < A; ++j) {
+        const gosh_hierarchy *h = hs[slots[j]];
+        const size_t i = h->n.size() - 1;
+        sn[j] = h->n[i];
+        snnz[j] = h->nnz[i];
+        in[j] = {h->rowptr[i], h->col[i]};
+        vo[j + 1] = vo[j] + sn[j];
+        eo[j + 1] = eo[j] + snnz[j];
+        nmax = std::max(nmax, sn[j]);
+    }
+    const int64_t N = vo[A], E = eo[A];
+    // device tables: SlotIn[A] | vo[A+1] | eo[A+1] | n[A] | nnz[A]
+    const size_t tbytes = sizeof(SlotIn) * A + sizeof(int64_t) * (2 * (A + 1) + 2 * A);
+    std::vector<char> host(tbytes);
+    char *hp = host.data();
+    std::memcpy(hp, in.data(), sizeof(SlotIn) * A);
+    hp += sizeof(SlotIn) * A;
+    for (auto *v : {&vo, &eo, &sn, &snnz}) {
+        std::memcpy(hp, v->data(), sizeof(int64_t) * v->size());
+        hp += sizeof(int64_t) * v->size();
+    }
+    Scratch tab, rowptr_u, col_u, vslot, map_u;
+    GOSH_TRY(tab.alloc(tbytes, s));
+    GOSH_TRY_CUDA(cudaMemcpyAsync(tab.ptr, host.data(), tbytes, cudaMemcpyHostToDevice, s));
+    const SlotIn *d_in = tab.as<SlotIn>();
+    const int64_t *d_vo = reinterpret_cast<const int64_t *>(tab.as<char>() + sizeof(SlotIn) * A);
+    const int64_t *d_eo = d_vo + (A + 1);
+    const int64_t *d_n = d_eo + (A + 1);
+    const int64_t *d_nnz = d_n + A;
+    GOSH_TRY(rowptr_u.alloc(sizeof(int64_t) * (N + 1), s));
+    GOSH_TRY(col_u.alloc(sizeof(int32_t) * (E > 0 ? E : 1), s));
+    GOSH_TRY(vslot.alloc(sizeof(int32_t) * N, s));
+    GOSH_TRY(map_u.alloc(sizeof(int32_t) * N, s));
+    launch_dep(union_rows, grid_1d(N + 1), 256, 0, s, d_in, d_vo, d_eo, A, N, E, rowptr_u.as<int64_t>(),
+               vslot.as<int32_t>());
+    if (E > 0) launch_dep(union_cols, grid_1d(E), 256, 0, s, d_in, d_vo, d_eo, A, E, col_u.as<int32_t>());
+
+    UnionLevel u;
+    u.nslots = A;
+    u.nmax = nmax;
+    u.vslot = vslot.as<int32_t>();
+    u.slot_n = d_n;
+    u.slot_nnz = d_nnz;
+    u.vo = d_vo;
+    int64_t NC = 0, M = 0;
+    int64_t *rp_u = nullptr;
+    int32_t *co_u = nullptr;
+    GOSH_TRY(mec_level(N, rowptr_u.as<int64_t>(), col_u.as<int32_t>(), E, map_u.as<int32_t>(), &NC, &rp_u, &co_u, &M,
+                       nullptr, s, &u));
+    std::shared_ptr<void> rp_own = device_owner(rp_u), co_own = device_owner(co_u);
+    rowptr_u.release();
+    col_u.release();
+
+    // every graph's first coarse entry (ceo) and its first cluster id (cid_at)
+    Scratch at;
+    GOSH_TRY(at.alloc(sizeof(int64_t) * 2 * (A + 1), s));
+    GOSH_TRY_CUDA(cudaMemcpyAsync(at.ptr, u.cid_at.data(), sizeof(int64_t) * (A + 1), cudaMemcpyHostToDevice, s));
+    const int64_t *d_cid = at.as<int64_t>();
+    int64_t *d_ceo = at.as<int64_t>() + (A + 1);
+    launch_dep(gather_at, grid_1d(A + 1), 256, 0, s, static_cast<const int64_t *>(rp_u), d_cid, A + 1, d_ceo);
+    std::vector<int64_t> ceo(A + 1);
+    GOSH_TRY_CUDA(cudaMemcpyAsync(ceo.data(), d_ceo, sizeof(int64_t) * (A + 1), cudaMemcpyDeviceToHost, s));
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+
+    // the graphs' new levels: one buffer each for maps, row pointers and
+    // entries, shared by the hierarchies
+    int32_t *maps = nullptr, *cols = nullptr;
+    int64_t *rps = nullptr;
+    GOSH_TRY_CUDA(cudaMallocAsync(&maps, sizeof(int32_t) * N, s));
+    std::shared_ptr<void> maps_own = device_owner(maps);
+    GOSH_TRY_CUDA(cudaMallocAsync(&rps, sizeof(int64_t) * (NC + A), s));
+    std::shared_ptr<void> rps_own = device_owner(rps);
+    GOSH_TRY_CUDA(cudaMallocAsync(&cols, sizeof(int32_t) * (M > 0 ? M : 1), s));
+    std::shared_ptr<void> cols_own = device_owner(cols);
+    std::vector<SlotOut> out(A);
+    for (int j = 0; j < A; ++j)
+        out[j] = {maps + vo[j], rps + u.cid_at[j] + j, cols + ceo[j]};
+    Scratch otab;
+    GOSH_TRY(otab.alloc(sizeof(SlotOut) * A, s));
+    GOSH_TRY_CUDA(cudaMemcpyAsync(otab.ptr, out.data(), sizeof(SlotOut) * A, cudaMemcpyHostToDevice, s));
+    launch_dep(split_maps, grid_1d(N), 256, 0, s, static_cast<const int32_t *>(map_u.as<int32_t>()),
+               static_cast<const int32_t *>(vslot.as<int32_t>()), d_vo, d_cid, N, otab.as<SlotOut>());
+    launch_dep(split_rows, grid_1d(NC + A), 256, 0, s, static_cast<const int64_t *>(rp_u), d_cid,
+               static_cast<const int64_t *>(d_ceo), A, NC, otab.as<SlotOut>());
+    if (M > 0)
+        launch_dep(split_cols, grid_1d(M), 256, 0, s, static_cast<const int32_t *>(co_u),
+                   static_cast<const int64_t *>(d_ceo), d_cid, A, M, otab.as<SlotOut>());
+    for (int j = 0; j < A; ++j) {
+        gosh_hierarchy *h = hs[slots[j]];
+        h->map.push_back(out[j].map);
+        h->n.push_back(u.cid_at[j + 1] - u.cid_at[j]);
+        h->nnz.push_back(ceo[j + 1] - ceo[j]);
+        h->rowptr.push_back(out[j].rp);
+        h->col.push_back(out[j].col);
+        h->owned.push_back(maps_own);
+        h->owned.push_back(rps_own);
+        h->owned.push_back(cols_own);
+    }
+    return GOSH_OK;
+}
+
+}  // namespace
+
+// Coarsens G graphs (device CSRs) level by level as unions of the graphs
+// still coarsening; each hierarchy equals coarsen_impl's for its graph.
+gosh_status coarsen_batch_impl(const gosh_csr *graphs, int G, int threshold, double shrink, int max_levels,
+                               cudaStream_t s, std::vector<gosh_hierarchy *> &out) {
+    keep_pool_memory();
+    out.assign(G, nullptr);
+    struct Fail {
+        std::vector<gosh_hierarchy *> &v;
+        bool armed = true;
+        ~Fail() {
+            if (!armed) return;
+            for (auto *&h : v) {
+                delete h;
+                h = nullptr;
+            }
+        }
+    } fail{out};
+    for (int g = 0; g < G; ++g) out[g] = new gosh_hierarchy();
+    {
+        // level 0: the callers' CSRs
+        std::vector<SlotIn> in(G);
+        std::vector<int64_t> n(G), nnz(G);
+        for (int g = 0; g < G; ++g) {
+            in[g] = {graphs[g].rowptr, graphs[g].col};
+            n[g] = graphs[g].n;
+        }
+        Scratch tab;
+        const size_t tb = sizeof(SlotIn) * G + sizeof(int64_t) * 2 * G;
+        GOSH_TRY(tab.alloc(tb, s));
+        GOSH_TRY_CUDA(cudaMemcpyAsync(tab.ptr, in.data(), sizeof(SlotIn) * G, cudaMemcpyHostToDevice, s));
+        int64_t *d_n = reinterpret_cast<int64_t *>(tab.as<char>() + sizeof(SlotIn) * G);
+        GOSH_TRY_CUDA(cudaMemcpyAsync(d_n, n.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, s));
+        launch_dep(input_nnz, grid_1d(G), 256, 0, s, static_cast<const SlotIn *>(tab.as<SlotIn>()),
+                   static_cast<const int64_t *>(d_n), G, d_n + G);
+        GOSH_TRY_CUDA(cudaMemcpyAsync(nnz.data(), d_n + G, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, s));
+        GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+        for (int g = 0; g < G; ++g) {
+            out[g]->n.push_back(n[g]);
+            out[g]->nnz.push_back(nnz[g]);
+            out[g]->rowptr.push_back(const_cast<int64_t *>(graphs[g].rowptr));
+            out[g]->col.push_back(const_cast<int32_t *>(graphs[g].col));
+        }
+    }
+    if (max_levels < 2) max_levels = 2;
+    std::vector<int> active(G);
+    for (int g = 0; g < G; ++g) active[g] = g;
+    while (!active.empty()) {
+        // unions within the limits of 32-bit ids and 32-bit sort keys
+        std::vector<std::vector<int>> groups(1);
+        int64_t sum_n = 0, nmax = 0;
+        for (int g : active) {
+            const int64_t ng = out[g]->n.back();
+            const int64_t nm = std::max(nmax, ng);
+            const size_t cnt = groups.back().size() + 1;
+            const bool fits = sum_n + ng < (int64_t(1) << 31) - 1 &&
+                              bits_for((uint64_t)(nm - 1)) + bits_for((uint64_t)(cnt - 1)) <= 32;
+            if (!groups.back().empty() && !fits) {
+                groups.emplace_back();
+                sum_n = 0;
+                nmax = 0;
+            }
+            groups.back().push_back(g);
+            sum_n += ng;
+            nmax = std::max(nmax, ng);
+        }
+        for (auto &grp : groups) GOSH_TRY(union_level(grp, out, s));
+        std::vector<int> next;
+        for (int g : active) {
+            const gosh_hierarchy *h = out[g];
+            const int64_t nc = h->n.back(), nf = h->n[h->n.size() - 2];
+            const bool more = nc > threshold && (double)nc <= std::floor(shrink * (double)nf);
+            if (more && (int)h->n.size() < max_levels) next.push_back(g);
+        }
+        active.swap(next);
+    }
+    GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    fail.armed = false;
     return GOSH_OK;
 }
 

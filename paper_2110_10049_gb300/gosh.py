@@ -83,6 +83,7 @@ def lib() -> C.CDLL:
             "gosh_params_default": [P(gosh_params)],
             "gosh_validate_csr": [P(gosh_csr), vp],
             "gosh_coarsen": [P(gosh_csr), i32, f64, i32, vp, P(vp)],
+            "gosh_coarsen_batch": [vp, i32, i32, f64, i32, vp, vp],
             "gosh_hierarchy_level": [vp, i32, P(gosh_csr), P(vp)],
             "gosh_hierarchy_sizes": [vp, i32, P(C.c_int64), P(C.c_int64)],
             "gosh_hierarchy_copy_level": [vp, i32, vp, vp, vp, vp],
@@ -251,6 +252,16 @@ def gosh_coarsen(g: Csr, threshold=100, shrink=0.8, max_levels=MAX_LEVELS, strea
     _check("gosh_coarsen", lib().gosh_coarsen(C.byref(cg), threshold, shrink, max_levels, _stream(stream),
                                               C.byref(h)))
     return Hierarchy(h.value, g)
+
+
+def gosh_coarsen_batch(graphs, threshold=100, shrink=0.8, max_levels=MAX_LEVELS, stream=None):
+    """Coarsens a list of device CSRs (Csr) together; one Hierarchy per graph."""
+    G = len(graphs)
+    arr = (gosh_csr * G)(*[g.c() for g in graphs])
+    hs = (C.c_void_p * G)()
+    _check("gosh_coarsen_batch", lib().gosh_coarsen_batch(C.cast(arr, C.c_void_p), G, threshold, shrink, max_levels,
+                                                          _stream(stream), C.cast(hs, C.c_void_p)))
+    return [Hierarchy(hs[i], graphs[i]) for i in range(G)]
 
 
 def gosh_init_embedding(M, level=0, seed=0, graph_id=0, stream=None):
