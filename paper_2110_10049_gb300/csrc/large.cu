@@ -138,7 +138,7 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
                                 ? 0u
                                 : sr_source_seed(a.seed, a.graph ^ a.tag, a.level, (uint32_t)a.round, (sideA ? a.start_a : a.start_b) + u);
         float r[E];
-        if (active) load_row<T, E>(Mown + u * D + gl * E, r);
+        if (active) load_row<T, E, L>(Mown + u * D, gl, r);
         else {
 #pragma unroll
             for (int e = 0; e < E; ++e) r[e] = 0.0f;
@@ -162,7 +162,7 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
             }
 #pragma unroll
             for (int x = 0; x < P; ++x) {
-                if (us[x] >= 0) load_row<T, E>(Mopp + (int64_t)us[x] * D + gl * E, row[x]);
+                if (us[x] >= 0) load_row<T, E, L>(Mopp + (int64_t)us[x] * D, gl, row[x]);
                 else {
 #pragma unroll
                     for (int e = 0; e < E; ++e) row[x][e] = 0.0f;
@@ -191,14 +191,14 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
                 for (int e = 0; e < E; ++e) row[x][e] = fmaf(r[e], score, row[x][e]);
                 if (ok) {
                     if constexpr (RED16) {
-                        red_row16<T, D, E>(Mopp + (int64_t)us[x] * D + gl * E, row[x], old16, sr, t, gl * E);
+                        red_row16<T, D, E, L>(Mopp + (int64_t)us[x] * D, row[x], old16, sr, t, gl);
                     } else if (RED) {
                         float c[E];
 #pragma unroll
                         for (int e = 0; e < E; ++e) c[e] = r[e] * score;
-                        red_row<E>(reinterpret_cast<float *>(Mopp) + (int64_t)us[x] * D + gl * E, c);
+                        red_row<E, L>(reinterpret_cast<float *>(Mopp) + (int64_t)us[x] * D, c, gl);
                     } else {
-                        store_row<T, D, E>(Mopp + (int64_t)us[x] * D + gl * E, row[x], sr, t, gl * E);
+                        store_row<T, D, E, L>(Mopp + (int64_t)us[x] * D, row[x], sr, t, gl);
                     }
                     if (gl == 0) ++applied;
                 }
@@ -212,14 +212,14 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
         }
         if (active) {
             if constexpr (RED16) {
-                red_row16<T, D, E>(Mown + u * D + gl * E, r, r0, sr, ns, gl * E);
+                red_row16<T, D, E, L>(Mown + u * D, r, r0, sr, ns, gl);
             } else if (RED) {
                 float dr[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) dr[e] = r[e] - r0[RED ? e : 0];
-                red_row<E>(reinterpret_cast<float *>(Mown) + u * D + gl * E, dr);
+                red_row<E, L>(reinterpret_cast<float *>(Mown) + u * D, dr, gl);
             } else {
-                store_row<T, D, E>(Mown + u * D + gl * E, r, sr, ns, gl * E);
+                store_row<T, D, E, L>(Mown + u * D, r, sr, ns, gl);
             }
         }
     }

@@ -22,40 +22,75 @@ __device__ __forceinline__ float softplus_f(float z) {
     return fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)));
 }
 
-template <typename T, int E>
-__device__ __forceinline__ void load_row(const T *__restrict__ p, float *f) {
-    constexpr int PV = Store<T>::kPerVec;
-    const uint4 *q = reinterpret_cast<const uint4 *>(p);
-#pragma unroll
-    for (int v = 0; v < E / PV; ++v) Store<T>::unpack(__ldcg(q + v), f + v * PV);
+// A lane holds E values of a row as E/PV 16-byte vectors (PV values each):
+// its vector v is the row's vector v*L + gl (gl = lane within the L lanes of a
+// source), so consecutive lanes take consecutive vectors and one load of the
+// L lanes covers L * 16 contiguous bytes: whole 32-byte sectors.
+template <typename T, int L>
+__device__ __forceinline__ int lane_col(int gl, int v) {
+    return (v * L + gl) * Store<T>::kPerVec;
 }
 
-template <typename T, int E>
-__device__ __forceinline__ void load_row_snapshot(const T *__restrict__ p, float *f) {
+template <typename T, int E, int L>
+__device__ __forceinline__ void load_row(const T *__restrict__ row, int gl, float *f) {
     constexpr int PV = Store<T>::kPerVec;
-    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    const uint4 *q = reinterpret_cast<const uint4 *>(row) + gl;
 #pragma unroll
-    for (int v = 0; v < E / PV; ++v) Store<T>::unpack(__ldg(q + v), f + v * PV);
+    for (int v = 0; v < E / PV; ++v) Store<T>::unpack(__ldcg(q + v * L), f + v * PV);
 }
 
-// Stores E elements starting at element `elem0` of row-slot `slot`; f is
-// replaced by the stored (rounded) values.
-template <typename T, int D, int E>
-__device__ __forceinline__ void store_row(T *__restrict__ p, float *f, uint32_t sr, int slot, int elem0) {
+template <typename T, int E, int L>
+__device__ __forceinline__ void load_row_snapshot(const T *__restrict__ row, int gl, float *f) {
     constexpr int PV = Store<T>::kPerVec;
-    uint4 *q = reinterpret_cast<uint4 *>(p);
+    const uint4 *q = reinterpret_cast<const uint4 *>(row) + gl;
+#pragma unroll
+    for (int v = 0; v < E / PV; ++v) Store<T>::unpack(__ldg(q + v * L), f + v * PV);
+}
+
+// Stores the lane's E values of row-slot `slot` (columns lane_col); f is
+// replaced by the stored (rounded) values.  The rounding bits of a pair of
+// values depend on (slot, column) only.
+template <typename T, int D, int E, int L>
+__device__ __forceinline__ void store_row(T *__restrict__ row, float *f, uint32_t sr, int slot, int gl) {
+    constexpr int PV = Store<T>::kPerVec;
+    uint4 *q = reinterpret_cast<uint4 *>(row) + gl;
 #pragma unroll
     for (int v = 0; v < E / PV; ++v) {
-        const uint32_t base = (uint32_t)((slot * D + elem0 + v * PV) >> 1);
-        q[v] = Store<T>::pack(f + v * PV, sr, base);
+        const uint32_t base = (uint32_t)((slot * D + lane_col<T, L>(gl, v)) >> 1);
+        q[v * L] = Store<T>::pack(f + v * PV, sr, base);
     }
 }
 
-template <int E>
-__device__ __forceinline__ void store_f32(float *__restrict__ p, const float *f) {
-    float4 *q = reinterpret_cast<float4 *>(p);
+// FP32 copies of the lane's values (vectors of PV values at columns lane_col
+// of storage type T) into a row of an FP32 buffer.
+template <typename T, int E, int L>
+__device__ __forceinline__ void store_f32(float *__restrict__ row, const float *f, int gl) {
+    constexpr int PV = Store<T>::kPerVec;
 #pragma unroll
-    for (int v = 0; v < E / 4; ++v) q[v] = make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+    for (int v = 0; v < E / PV; ++v) {
+        float4 *q = reinterpret_cast<float4 *>(row + lane_col<T, L>(gl, v));
+#pragma unroll
+        for (int k = 0; k < PV / 4; ++k)
+            q[k] = make_float4(f[v * PV + 4 * k], f[v * PV + 4 * k + 1], f[v * PV + 4 * k + 2], f[v * PV + 4 * k + 3]);
+    }
+}
+
+// ... and back: FP32 buffer row -> the lane's values
+template <typename T, int E, int L>
+__device__ __forceinline__ void load_f32(const float *__restrict__ row, float *f, int gl) {
+    constexpr int PV = Store<T>::kPerVec;
+#pragma unroll
+    for (int v = 0; v < E / PV; ++v) {
+        const float4 *q = reinterpret_cast<const float4 *>(row + lane_col<T, L>(gl, v));
+#pragma unroll
+        for (int k = 0; k < PV / 4; ++k) {
+            const float4 x = __ldg(q + k);
+            f[v * PV + 4 * k] = x.x;
+            f[v * PV + 4 * k + 1] = x.y;
+            f[v * PV + 4 * k + 2] = x.z;
+            f[v * PV + 4 * k + 3] = x.w;
+        }
+    }
 }
 
 // Atomic vector addition at L2 (fire-and-forget): M[p..p+3] += f[0..3].
@@ -71,22 +106,26 @@ __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, 
 // change is below 256 ulps of the value, which covers the small updates that
 // stochastic rounding exists for), else within one ulp of it; with a
 // concurrent writer both changes are kept instead of one overwriting the other.
-template <typename T, int D, int E>
-__device__ __forceinline__ void red_row16(T *__restrict__ p, float *f, const float *old, uint32_t sr, int slot,
-                                          int elem0) {
+template <typename T, int D, int E, int L>
+__device__ __forceinline__ void red_row16(T *__restrict__ row, float *f, const float *old, uint32_t sr, int slot,
+                                          int gl) {
     constexpr int PV = Store<T>::kPerVec;
 #pragma unroll
     for (int v = 0; v < E / PV; ++v) {
-        const uint32_t base = (uint32_t)((slot * D + elem0 + v * PV) >> 1);
+        const int col = lane_col<T, L>(gl, v);
+        const uint32_t base = (uint32_t)((slot * D + col) >> 1);
         const uint4 nw = Store<T>::pack(f + v * PV, sr, base);
-        Store<T>::red_add(p + v * PV, Store<T>::change(nw, old + v * PV));
+        Store<T>::red_add(row + col, Store<T>::change(nw, old + v * PV));
     }
 }
 
-template <int E>
-__device__ __forceinline__ void red_row(float *p, const float *f) {
+template <int E, int L>
+__device__ __forceinline__ void red_row(float *row, const float *f, int gl) {
 #pragma unroll
-    for (int v = 0; v < E / 4; ++v) red_add_v4(p + 4 * v, f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+    for (int v = 0; v < E / 4; ++v) {
+        float *p = row + lane_col<float, L>(gl, v);
+        red_add_v4(p, f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+    }
 }
 
 // d = a * b + c on two FP32 lanes at once (fma.rn.f32x2, sm_100 and later).
@@ -198,8 +237,8 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
             const uint32_t sr = std::is_same<T, float>::value ? 0u : s_sr_w[j];
             float r[E];
             if (active) {
-                if (DET) load_row_snapshot<T, E>(M + v * D + gl * E, r);
-                else load_row<T, E>(M + v * D + gl * E, r);
+                if (DET) load_row_snapshot<T, E, L>(M + v * D, gl, r);
+                else load_row<T, E, L>(M + v * D, gl, r);
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[e] = 0.0f;
@@ -221,8 +260,8 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
 #pragma unroll
                 for (int s = 0; s < P; ++s) {
                     if (us[s] >= 0) {
-                        if (DET) load_row_snapshot<T, E>(M + (int64_t)us[s] * D + gl * E, row[s]);
-                        else load_row<T, E>(M + (int64_t)us[s] * D + gl * E, row[s]);
+                        if (DET) load_row_snapshot<T, E, L>(M + (int64_t)us[s] * D, gl, row[s]);
+                        else load_row<T, E, L>(M + (int64_t)us[s] * D, gl, row[s]);
                     } else {
 #pragma unroll
                         for (int e = 0; e < E; ++e) row[s][e] = 0.0f;
@@ -246,21 +285,21 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
                     axpy2<E>(row[s], r, score);
                     if (ok) {
                         if constexpr (RED16) {
-                            red_row16<T, D, E>(M + (int64_t)us[s] * D + gl * E, row[s], old16, sr, t, gl * E);
+                            red_row16<T, D, E, L>(M + (int64_t)us[s] * D, row[s], old16, sr, t, gl);
                         } else if (DET) {
                             const int64_t slot = (v - a.src_begin) * ns + t;
                             float c[E];
 #pragma unroll
                             for (int e = 0; e < E; ++e) c[e] = r[e] * score;
-                            store_f32<E>(a.C + slot * D + gl * E, c);
+                            store_f32<T, E, L>(a.C + slot * D, c, gl);
                             if (gl == 0) a.keys[slot] = (uint32_t)us[s];
                         } else if (RED) {
                             float c[E];
 #pragma unroll
                             for (int e = 0; e < E; ++e) c[e] = r[e] * score;
-                            red_row<E>(reinterpret_cast<float *>(M) + (int64_t)us[s] * D + gl * E, c);
+                            red_row<E, L>(reinterpret_cast<float *>(M) + (int64_t)us[s] * D, c, gl);
                         } else {
-                            store_row<T, D, E>(M + (int64_t)us[s] * D + gl * E, row[s], sr, t, gl * E);
+                            store_row<T, D, E, L>(M + (int64_t)us[s] * D, row[s], sr, t, gl);
                         }
                         if (gl == 0) {
                             ++applied;
@@ -281,16 +320,16 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
             }
             if (active) {
                 if constexpr (RED16) {
-                    red_row16<T, D, E>(M + v * D + gl * E, r, r0, sr, ns, gl * E);
+                    red_row16<T, D, E, L>(M + v * D, r, r0, sr, ns, gl);
                 } else if (DET) {
-                    store_f32<E>(a.R + (v - a.src_begin) * D + gl * E, r);
+                    store_f32<T, E, L>(a.R + (v - a.src_begin) * D, r, gl);
                 } else if (RED) {
                     float dr[E];
 #pragma unroll
                     for (int e = 0; e < E; ++e) dr[e] = r[e] - r0[RED ? e : 0];
-                    red_row<E>(reinterpret_cast<float *>(M) + v * D + gl * E, dr);
+                    red_row<E, L>(reinterpret_cast<float *>(M) + v * D, dr, gl);
                 } else {
-                    store_row<T, D, E>(M + v * D + gl * E, r, sr, ns, gl * E);
+                    store_row<T, D, E, L>(M + v * D, r, sr, ns, gl);
                 }
             }
         }
@@ -488,25 +527,18 @@ __global__ void __launch_bounds__(256) det_apply_segments(const uint32_t *__rest
         const int64_t x = key;
         float acc[E];
         if (x >= b0 && x < b1) {
-            const float4 *q = reinterpret_cast<const float4 *>(R + (x - b0) * D + gl * E);
-#pragma unroll
-            for (int v = 0; v < E / 4; ++v) {
-                const float4 f = q[v];
-                acc[4 * v] = f.x; acc[4 * v + 1] = f.y; acc[4 * v + 2] = f.z; acc[4 * v + 3] = f.w;
-            }
+            load_f32<T, E, L>(R + (x - b0) * D, acc, gl);
             if (gl == 0) src_done[x - b0] = 1;
         } else {
-            load_row_snapshot<T, E>(M + x * D + gl * E, acc);
+            load_row_snapshot<T, E, L>(M + x * D, gl, acc);
         }
         for (int64_t jj = i; jj < nslots && skeys[jj] == key; ++jj) {
-            const float4 *q = reinterpret_cast<const float4 *>(C + (int64_t)sidx[jj] * D + gl * E);
+            float c[E];
+            load_f32<T, E, L>(C + (int64_t)sidx[jj] * D, c, gl);
 #pragma unroll
-            for (int v = 0; v < E / 4; ++v) {
-                const float4 f = q[v];
-                acc[4 * v] += f.x; acc[4 * v + 1] += f.y; acc[4 * v + 2] += f.z; acc[4 * v + 3] += f.w;
-            }
+            for (int e = 0; e < E; ++e) acc[e] += c[e];
         }
-        store_row<T, D, E>(M + x * D + gl * E, acc, mix32(sr_seed ^ (uint32_t)x), 0, gl * E);
+        store_row<T, D, E, L>(M + x * D, acc, mix32(sr_seed ^ (uint32_t)x), 0, gl);
     }
 }
 
@@ -522,13 +554,8 @@ __global__ void __launch_bounds__(256) det_apply_sources(const float *__restrict
     for (int64_t i = gid; i < b1 - b0; i += gstride) {
         if (src_done[i]) continue;
         float acc[E];
-        const float4 *q = reinterpret_cast<const float4 *>(R + i * D + gl * E);
-#pragma unroll
-        for (int v = 0; v < E / 4; ++v) {
-            const float4 f = q[v];
-            acc[4 * v] = f.x; acc[4 * v + 1] = f.y; acc[4 * v + 2] = f.z; acc[4 * v + 3] = f.w;
-        }
-        store_row<T, D, E>(M + (b0 + i) * D + gl * E, acc, mix32(sr_seed ^ (uint32_t)(b0 + i)), 0, gl * E);
+        load_f32<T, E, L>(R + i * D, acc, gl);
+        store_row<T, D, E, L>(M + (b0 + i) * D, acc, mix32(sr_seed ^ (uint32_t)(b0 + i)), 0, gl);
     }
 }
 

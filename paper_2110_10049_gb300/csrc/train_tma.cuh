@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
             uint8_t *sb = stage_base + st * STAGE + grp * SLOTS * R;  // this source's rows
             float r[E], r0[RED ? E : 1];
             if (active) {
-                const uint4 *q4 = reinterpret_cast<const uint4 *>(sb) + gl * (E / PV);
+                const uint4 *q4 = reinterpret_cast<const uint4 *>(sb) + gl;
 #pragma unroll
-                for (int x = 0; x < E / PV; ++x) Store<T>::unpack(q4[x], r + x * PV);
+                for (int x = 0; x < E / PV; ++x) Store<T>::unpack(q4[x * L], r + x * PV);
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[e] = 0.0f;
@@ -206,10 +206,10 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
                 const int32_t uid = active ? s_u[warp][j * kSlotStride + t] : -1;
                 const bool ok = uid >= 0;
                 float row[E];
-                uint4 *rs = reinterpret_cast<uint4 *>(sb + (1 + t) * R) + gl * (E / PV);
+                uint4 *rs = reinterpret_cast<uint4 *>(sb + (1 + t) * R) + gl;
                 if (ok) {
 #pragma unroll
-                    for (int x = 0; x < E / PV; ++x) Store<T>::unpack(rs[x], row + x * PV);
+                    for (int x = 0; x < E / PV; ++x) Store<T>::unpack(rs[x * L], row + x * PV);
                 } else {
 #pragma unroll
                     for (int e = 0; e < E; ++e) row[e] = 0.0f;
@@ -227,25 +227,25 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
                 axpy2<E>(row, r, score);
                 if (ok) {
                     if constexpr (RED16) {
-                        red_row16<T, D, E>(M + (int64_t)uid * D + gl * E, row, old16, sr, t, gl * E);
+                        red_row16<T, D, E, L>(M + (int64_t)uid * D, row, old16, sr, t, gl);
                     } else if (RED) {
                         float c[E];
 #pragma unroll
                         for (int e = 0; e < E; ++e) c[e] = r[e] * score;
-                        red_row<E>(reinterpret_cast<float *>(M) + (int64_t)uid * D + gl * E, c);
+                        red_row<E, L>(reinterpret_cast<float *>(M) + (int64_t)uid * D, c, gl);
                     } else {
-                        store_row<T, D, E>(M + (int64_t)uid * D + gl * E, row, sr, t, gl * E);
+                        store_row<T, D, E, L>(M + (int64_t)uid * D, row, sr, t, gl);
                     }
                     // a later draw of the same row by this source continues from here
                     for (int t2 = t + 1; t2 < ns; ++t2)
                         if (s_u[warp][j * kSlotStride + t2] == uid) {
-                            uint4 *d4 = reinterpret_cast<uint4 *>(sb + (1 + t2) * R) + gl * (E / PV);
+                            uint4 *d4 = reinterpret_cast<uint4 *>(sb + (1 + t2) * R) + gl;
 #pragma unroll
                             for (int xx = 0; xx < E / PV; ++xx) {
                                 float tmp[PV];
 #pragma unroll
                                 for (int e = 0; e < PV; ++e) tmp[e] = row[xx * PV + e];
-                                d4[xx] = Store<T>::pack(tmp, 0u, 0u);  // values already rounded by the store
+                                d4[xx * L] = Store<T>::pack(tmp, 0u, 0u);  // values already rounded by the store
                             }
                         }
                     if (gl == 0) {
@@ -256,14 +256,14 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
             }
             if (active) {
                 if constexpr (RED16) {
-                    red_row16<T, D, E>(M + v * D + gl * E, r, r0, sr, ns, gl * E);
+                    red_row16<T, D, E, L>(M + v * D, r, r0, sr, ns, gl);
                 } else if (RED) {
                     float dr[E];
 #pragma unroll
                     for (int e = 0; e < E; ++e) dr[e] = r[e] - r0[RED ? e : 0];
-                    red_row<E>(reinterpret_cast<float *>(M) + v * D + gl * E, dr);
+                    red_row<E, L>(reinterpret_cast<float *>(M) + v * D, dr, gl);
                 } else {
-                    store_row<T, D, E>(M + v * D + gl * E, r, sr, ns, gl * E);
+                    store_row<T, D, E, L>(M + v * D, r, sr, ns, gl);
                 }
             }
             __syncwarp();
