@@ -108,7 +108,8 @@ int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) /
 // Sources per warp tile.  A warp walks its tile in tile / (32/L) dependent
 // rounds, so small levels (few tiles, far fewer than the GPU's warps) take
 // short tiles (4 below 2^16 rows; below 2^19, 8 for 16-bit tables with plain
-// stores, 16 in the deterministic mode, 32 otherwise);
+// stores, 16 for 16-bit tables with atomic changes and in the deterministic
+// mode, 32 for FP32 lock-free);
 // large levels take 32 to amortise the draws.  A multiple of 32/L in
 // [32/L, 32]; params->vertices_per_warp overrides.
 int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass) {
@@ -121,7 +122,7 @@ int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass) {
     }
     const bool red16 = p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC && !p->plain_stores;
     const bool f32_lockfree = p->dtype == GOSH_F32 && p->mode != GOSH_DETERMINISTIC;
-    const int mid = (red16 || f32_lockfree) ? 32 : (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC ? 8 : 16);
+    const int mid = red16 ? 16 : f32_lockfree ? 32 : (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC ? 8 : 16);
     if (t <= 0) t = n >= (int64_t(1) << 19) ? 32 : (n >= (int64_t(1) << 16) ? mid : 4);
     t = t < G ? G : (t > 32 ? 32 : t);
     return t / G * G;
@@ -146,13 +147,11 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
     //  - FP32 lock-free: above 2^19 rows TMA-staged with L0 lanes; from 2^14
     //    rows registers, L0 lanes, P = 4; below, TMA-staged with L0/2 lanes
     //    (a latency-bound level: every row of a round in flight at once);
-    //  - 16-bit tables (atomic changes): above 2^19 rows registers, L0/2
-    //    lanes (two vectors per lane, more sources in flight), P = 2; from
-    //    2^16 rows L0 lanes (one vector per lane: 80 registers, 24 warps per
-    //    SM), P = 2; from 2^14 rows L0/2 lanes, P = 2; below, BF16 tables
-    //    TMA-staged with L0/2 lanes (FP16 has no staged variant: L0 lanes,
-    //    P = 4); with plain stores, L0/2 lanes and P = 4 except L0 lanes from
-    //    2^16 to 2^19 rows.
+    //  - 16-bit tables (atomic changes): from 2^14 rows registers, L0/2
+    //    lanes (two vectors per lane, more sources in flight), P = 2; below,
+    //    BF16 tables TMA-staged with L0/2 lanes (FP16 has no staged variant:
+    //    L0 lanes, P = 4); with plain stores, L0/2 lanes and P = 4 except L0
+    //    lanes from 2^16 to 2^19 rows.
     if (!det && lanes <= 0 && pass == 0) {
         const int staged = ns <= 4 ? -4 : -6;
         const int half = nat >= 4 ? nat / 2 : nat;
@@ -168,13 +167,7 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
                 pass = ns <= 6 ? staged : 4;
             }
         } else if (dtype != GOSH_F32 && mode == kModeRed) {
-            if (n >= (int64_t(1) << 19)) {
-                lanes = half;
-                pass = 2;
-            } else if (n >= (int64_t(1) << 16)) {
-                lanes = nat;
-                pass = 2;
-            } else if (n >= (int64_t(1) << 14)) {
+            if (n >= (int64_t(1) << 14)) {
                 lanes = half;
                 pass = 2;
             } else if (dtype == GOSH_BF16 && ns <= 6) {
