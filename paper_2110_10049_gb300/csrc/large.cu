@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <cmath>
 #include <deque>
@@ -422,10 +423,13 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
 
     // ---- edge blocks (pinned, built on host threads) ----
     // A block side (u in V^a, entries in V^b) is built in row chunks spread
-    // over every host thread: per row the sub-range of its sorted row that
-    // falls in V^b (two binary searches), a prefix sum of the counts, then the
-    // entries with local ids.  All blocks share one pinned region, kept across
-    // calls (grow-only: pinning host memory costs far more than building).
+    // over every host thread.  Up front only the entries of each chunk are
+    // counted (two binary searches per row for the sub-range of its sorted
+    // row that falls in V^b); the chunks' offsets then place every block in
+    // one pinned region (kept across calls, grow-only: pinning host memory
+    // costs far more than building), and the row pointers and entries (local
+    // ids) are written straight into it by the threads that overlap the
+    // stream loop below.
     std::vector<std::pair<int, int>> order;
     large_pair_order(K, order);
     std::vector<Block> blocks(order.size());
@@ -434,54 +438,83 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     struct Side {
         int blk;
         bool ab;
+        int pa, pb;  // parts of the rows and of the entries
         int64_t a0, a1, b0, b1;
-        std::vector<int64_t> lo, rp;  // per row: first entry in V^b; prefix of the counts
+        int64_t entries;
     };
     std::vector<Side> sides;
     for (size_t i = 0; i < order.size(); ++i) {
         const int a = order[i].first, b = order[i].second;
-        sides.push_back({(int)i, true, start[a], start[a + 1], start[b], start[b + 1], {}, {}});
-        if (a != b) sides.push_back({(int)i, false, start[b], start[b + 1], start[a], start[a + 1], {}, {}});
+        sides.push_back({(int)i, true, a, b, start[a], start[a + 1], start[b], start[b + 1], 0});
+        if (a != b) sides.push_back({(int)i, false, b, a, start[b], start[b + 1], start[a], start[a + 1], 0});
     }
     constexpr int64_t kChunkRows = 32768;
-    std::vector<std::pair<int, int64_t>> items;  // (side, first row offset)
-    for (size_t j = 0; j < sides.size(); ++j) {
-        Side &sd = sides[j];
-        sd.lo.resize((size_t)(sd.a1 - sd.a0));
-        sd.rp.assign((size_t)(sd.a1 - sd.a0 + 1), 0);
-        for (int64_t r = 0; r < sd.a1 - sd.a0; r += kChunkRows) items.push_back({(int)j, r});
-    }
+    struct Item {
+        int side;
+        int64_t r0;   // first row offset in the side
+        int64_t off;  // entries of the side before this chunk
+    };
+    std::vector<Item> items;
+    for (size_t j = 0; j < sides.size(); ++j)
+        for (int64_t r = 0; r < sides[j].a1 - sides[j].a0; r += kChunkRows) items.push_back({(int)j, r, 0});
     const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    auto parallel_items = [&](auto &&body) {
+    auto row_range = [&](const Side &sd, int64_t r, const int32_t **lo, const int32_t **hi) {
+        const int64_t u = sd.a0 + r;
+        const int32_t *row = g->col + g->rowptr[u], *end = g->col + g->rowptr[u + 1];
+        *lo = std::lower_bound(row, end, (int32_t)sd.b0);
+        *hi = std::lower_bound(*lo, end, (int32_t)sd.b1);
+    };
+    // counts of every (row part, entry part) pair from one walk of each row
+    // chunk: K - 1 binary searches per row split it at every part boundary
+    std::vector<int64_t> part_chunk(K + 1, 0);  // first row chunk of each part
+    for (int a = 0; a < K; ++a) part_chunk[a + 1] = part_chunk[a] + ceil_div(start[a + 1] - start[a], kChunkRows);
+    std::vector<int64_t> pcount((size_t)part_chunk[K] * K, 0);  // [row chunk][entry part]
+    {
+        std::vector<std::pair<int, int64_t>> rchunks;  // (part, first row offset)
+        for (int a = 0; a < K; ++a)
+            for (int64_t r = 0; r < start[a + 1] - start[a]; r += kChunkRows) rchunks.push_back({a, r});
         std::atomic<size_t> next{0};
         std::vector<std::thread> th;
         for (int t = 0; t < nt; ++t)
             th.emplace_back([&]() {
-                for (size_t it = next.fetch_add(1); it < items.size(); it = next.fetch_add(1)) body(items[it]);
+                std::vector<int64_t> c(K);
+                for (size_t k = next.fetch_add(1); k < rchunks.size(); k = next.fetch_add(1)) {
+                    const int a = rchunks[k].first;
+                    const int64_t r0 = rchunks[k].second, r1 = std::min(r0 + kChunkRows, start[a + 1] - start[a]);
+                    std::fill(c.begin(), c.end(), 0);
+                    for (int64_t r = r0; r < r1; ++r) {
+                        const int64_t u = start[a] + r;
+                        const int32_t *row = g->col + g->rowptr[u], *end = g->col + g->rowptr[u + 1];
+                        const int32_t *prev = row;
+                        for (int b = 0; b < K; ++b) {
+                            const int32_t *nx = b + 1 < K ? std::lower_bound(prev, end, (int32_t)start[b + 1]) : end;
+                            c[b] += nx - prev;
+                            prev = nx;
+                        }
+                    }
+                    for (int b = 0; b < K; ++b) pcount[(size_t)k * K + b] = c[b];
+                }
             });
         for (auto &x : th) x.join();
-    };
-    parallel_items([&](const std::pair<int, int64_t> &it) {
-        Side &sd = sides[it.first];
-        const int64_t r1 = std::min(it.second + kChunkRows, sd.a1 - sd.a0);
-        for (int64_t r = it.second; r < r1; ++r) {
-            const int64_t u = sd.a0 + r;
-            const int32_t *row = g->col + g->rowptr[u], *end = g->col + g->rowptr[u + 1];
-            const int32_t *lo = std::lower_bound(row, end, (int32_t)sd.b0);
-            const int32_t *hi = std::lower_bound(lo, end, (int32_t)sd.b1);
-            sd.lo[(size_t)r] = lo - g->col;
-            sd.rp[(size_t)r + 1] = hi - lo;
-        }
-    });
-    for (Side &sd : sides)
-        for (size_t r = 1; r < sd.rp.size(); ++r) sd.rp[r] += sd.rp[r - 1];
+    }
+    std::vector<int64_t> chunk_count(items.size(), 0);
+    for (size_t k = 0; k < items.size(); ++k) {
+        const Side &sd = sides[items[k].side];
+        const int64_t rc = part_chunk[sd.pa] + items[k].r0 / kChunkRows;
+        chunk_count[k] = pcount[(size_t)rc * K + sd.pb];
+    }
+    for (size_t k = 0; k < items.size(); ++k) {  // items are grouped by side, in row order
+        Side &sd = sides[items[k].side];
+        items[k].off = sd.entries;
+        sd.entries += chunk_count[k];
+    }
     size_t total_bytes = 0;
     for (size_t i = 0; i < blocks.size(); ++i) {
         Block &B = blocks[i];
         const int a = order[i].first, b = order[i].second;
         const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
         for (const Side &sd : sides)
-            if (sd.blk == (int)i) (sd.ab ? B.m_ab : B.m_ba) = sd.rp.back();
+            if (sd.blk == (int)i) (sd.ab ? B.m_ab : B.m_ba) = sd.entries;
         B.bytes = al(sizeof(int64_t) * (na + 1)) + al(sizeof(int32_t) * B.m_ab) +
                   al(a != b ? sizeof(int64_t) * (nb + 1) : 0) + al(sizeof(int32_t) * B.m_ba);
         max_block = std::max(max_block, B.bytes);
@@ -503,24 +536,7 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
             B.col_ba = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(B.rp_ba) +
                                                    al(a != b ? sizeof(int64_t) * (nb + 1) : 0));
         }
-        for (const Side &sd : sides) {
-            Block &B = blocks[sd.blk];
-            std::memcpy(sd.ab ? B.rp_ab : B.rp_ba, sd.rp.data(), sizeof(int64_t) * sd.rp.size());
-        }
     }
-    parallel_items([&](const std::pair<int, int64_t> &it) {
-        const Side &sd = sides[it.first];
-        Block &B = blocks[sd.blk];
-        int32_t *out = sd.ab ? B.col_ab : B.col_ba;
-        const int64_t r1 = std::min(it.second + kChunkRows, sd.a1 - sd.a0);
-        const int32_t b0 = (int32_t)sd.b0;
-        for (int64_t r = it.second; r < r1; ++r) {
-            const int32_t *src = g->col + sd.lo[(size_t)r];
-            int32_t *dst = out + sd.rp[(size_t)r];
-            const int64_t cnt = sd.rp[(size_t)r + 1] - sd.rp[(size_t)r];
-            for (int64_t q = 0; q < cnt; ++q) dst[q] = src[q] - b0;
-        }
-    });
     int64_t part_rows = 0;
     for (int i = 0; i < K; ++i) part_rows = std::max(part_rows, start[i + 1] - start[i]);
     const size_t bin_bytes = row * part_rows;
@@ -530,6 +546,54 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
                   (long long)budget);
         return GOSH_ERR_BUDGET;
     }
+
+    // The entries of the blocks are copied by host threads in block order
+    // while the stream loop below already sends the finished blocks: block i's
+    // first copy to the device waits only for block i (the items are ordered
+    // by block, so the first blocks finish first).
+    std::vector<int> items_left(blocks.size(), 0);
+    for (const auto &it : items) ++items_left[sides[it.side].blk];
+    struct BlockGate {
+        std::mutex mu;
+        std::condition_variable cv;
+        std::vector<int> left;
+        std::atomic<size_t> next{0};
+        std::vector<std::thread> th;
+        void wait(int b) {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&] { return left[b] == 0; });
+        }
+        ~BlockGate() {
+            for (auto &x : th) x.join();
+        }
+    } gate;
+    gate.left = items_left;
+    for (int t = 0; t < nt; ++t)
+        gate.th.emplace_back([&]() {
+            for (size_t k = gate.next.fetch_add(1); k < items.size(); k = gate.next.fetch_add(1)) {
+                const Item &it = items[k];
+                const Side &sd = sides[it.side];
+                Block &B = blocks[sd.blk];
+                int32_t *out = sd.ab ? B.col_ab : B.col_ba;
+                int64_t *rp = sd.ab ? B.rp_ab : B.rp_ba;
+                const int64_t r1 = std::min(it.r0 + kChunkRows, sd.a1 - sd.a0);
+                const int32_t b0 = (int32_t)sd.b0;
+                int64_t at = it.off;
+                for (int64_t r = it.r0; r < r1; ++r) {
+                    const int32_t *lo, *hi;
+                    row_range(sd, r, &lo, &hi);
+                    rp[r] = at;
+                    for (const int32_t *q = lo; q < hi; ++q) out[at++] = *q - b0;
+                }
+                if (r1 == sd.a1 - sd.a0) rp[r1] = at;  // the side's last chunk closes its row pointer
+                bool done;
+                {
+                    std::lock_guard<std::mutex> lk(gate.mu);
+                    done = --gate.left[sd.blk] == 0;
+                }
+                if (done) gate.cv.notify_all();
+            }
+        });
 
     // host M pinned for async copies (registered in place if the caller's is pageable)
     bool registered = false;
@@ -646,6 +710,7 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
         // SCT: edge block into the next edge bin
         const int eb = (int)(i % p->s_gpu);
         const Block &blk = blocks[i % order.size()];
+        if (i < order.size()) gate.wait((int)i);
         if (ebin_free[eb]) cudaStreamWaitEvent(estr[eb], ebin_free[eb], 0);
         cudaMemcpyAsync(ebin[eb].ptr, blk.base, blk.bytes, cudaMemcpyHostToDevice, estr[eb]);
         block_bytes += blk.bytes;
