@@ -8,8 +8,11 @@
  *    neighbour ids int32[nnz], strictly ascending inside each row, no
  *    self-loops, symmetric (undirected graph stored in both directions).
  *  - Embedding matrices are row-major n x d, element type given by gosh_dtype,
- *    row stride d elements, base address 16-byte aligned.  d is 32, 64 or 128
- *    (96 for FP32 only).
+ *    row stride d elements, base address 16-byte aligned.  d is 16, 32, 64 or
+ *    128 for the resident entry points (initialisation, training, copy
+ *    projection, gosh_embed with the copy projection, scores); 32, 64 or 128
+ *    for LargeGraphGPU, the batched entry and the learned projection.  At
+ *    d = 16 a warp updates 8 (FP32) or 16 (16-bit tables) sources at once.
  *  - Every pointer is a device pointer unless its comment says otherwise.  The
  *    caller owns every buffer it passes; the library owns hierarchy handles.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default

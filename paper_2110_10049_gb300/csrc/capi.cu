@@ -80,7 +80,7 @@ int grid_for(int64_t work, int threads = 256) {
     return (int)(g < cap ? g : cap);
 }
 
-bool dim_ok(int d, gosh_dtype t) { return d == 32 || d == 64 || d == 128; }
+bool dim_ok(int d, gosh_dtype t) { return d == 16 || d == 32 || d == 64 || d == 128; }
 bool dtype_ok(gosh_dtype t) { return t == GOSH_F32 || t == GOSH_BF16 || t == GOSH_F16; }
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -274,7 +274,7 @@ __global__ void sum_partials(const double *__restrict__ parts, int n, double *__
 gosh_status check_params(const gosh_params *p) {
     GOSH_CHECK_ARG(p != nullptr, "params is NULL");
     GOSH_CHECK_ARG(dtype_ok(p->dtype), "unknown dtype %d", (int)p->dtype);
-    GOSH_CHECK_ARG(dim_ok(p->d, p->dtype), "d must be 32, 64 or 128 (got %d)", p->d);
+    GOSH_CHECK_ARG(dim_ok(p->d, p->dtype), "d must be 16, 32, 64 or 128 (got %d)", p->d);
     GOSH_CHECK_ARG(p->k >= 0 && p->k <= 15, "k must be in 0..15 (got %d)", p->k);
     GOSH_CHECK_ARG(p->lr > 0 && std::isfinite(p->lr), "lr must be positive");
     GOSH_CHECK_ARG(p->lr_floor >= 0 && p->lr_floor <= 1, "lr_floor must be in [0, 1]");

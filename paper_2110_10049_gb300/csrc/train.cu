@@ -152,7 +152,8 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
     //    BF16 tables TMA-staged with L0/2 lanes (FP16 has no staged variant:
     //    L0 lanes, P = 4); with plain stores, L0/2 lanes and P = 4 except L0
     //    lanes from 2^16 to 2^19 rows.
-    if (!det && lanes <= 0 && pass == 0) {
+    const bool defaulted = lanes <= 0 && pass == 0;
+    if (!det && defaulted) {
         const int staged = ns <= 4 ? -4 : -6;
         const int half = nat >= 4 ? nat / 2 : nat;
         if (dtype == GOSH_F32 && mode == kModeRed) {
@@ -195,6 +196,11 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
         return GOSH_ERR_UNSUPPORTED;
     }
     const TrainKernel *kern = find_train_kernel(dtype, d, lanes, pass, mode);
+    if (!kern && defaulted && pass < 0) {
+        // no TMA-staged variant for this width (d = 16): registers, 4 samples per pass
+        pass = 4;
+        kern = find_train_kernel(dtype, d, lanes, pass, mode);
+    }
     if (!kern) {
         set_error("no training kernel for dtype %d, d %d, lanes_per_row %d, samples_per_pass %d, mode %d",
                   (int)dtype, d, lanes, pass, mode);

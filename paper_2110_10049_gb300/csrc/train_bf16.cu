@@ -4,6 +4,7 @@
 namespace gosh {
 namespace {
 using T = __nv_bfloat16;
+constexpr int L16 = 16 * (int)sizeof(T) / 16;
 constexpr int L32 = 32 * (int)sizeof(T) / 16;
 constexpr int L64 = 64 * (int)sizeof(T) / 16;
 constexpr int L128 = 128 * (int)sizeof(T) / 16;
@@ -16,7 +17,7 @@ constexpr gosh_dtype kType = GOSH_BF16;
         GOSH_V(D, L0 / 2, 2, kModeStore), GOSH_V(D, L0 / 2, 4, kModeStore), GOSH_V(D, L0, 4, kModeDet), \
         GOSH_V(D, L0, 8, kModeDet)
 
-const TrainEntry kEntries[] = {GOSH_VD(32, L32), GOSH_VD(64, L64), GOSH_VD(128, L128)};
+const TrainEntry kEntries[] = {GOSH_VD(16, L16), GOSH_VD(32, L32), GOSH_VD(64, L64), GOSH_VD(128, L128)};
 #undef GOSH_VD
 #undef GOSH_V
 }  // namespace
@@ -30,6 +31,7 @@ void det_apply_bf16(int d, const uint32_t *skeys, const uint32_t *sidx, int64_t 
                   const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
                   uint32_t sr_seed, cudaStream_t s) {
     switch (d) {
+    case 16: launch_det_apply_t<T, 16>(skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s); break;
     case 32: launch_det_apply_t<T, 32>(skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s); break;
     case 64: launch_det_apply_t<T, 64>(skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s); break;
     case 128: launch_det_apply_t<T, 128>(skeys, sidx, nslots, C, R, M, n, b0, b1, src_done, sr_seed, s); break;
