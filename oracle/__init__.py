@@ -63,6 +63,12 @@ def lib():
             "orc_project_copy": (None, [i64, vp, vp, vp, i32]),
             "orc_pair_scores": (None, [vp, i32, i64, vp, vp]),
             "orc_auc": (f64, [i64, vp, i64, vp]),
+            "orc_walk_pairs_per_walk": (i64, [i32, i32]),
+            "orc_walk_pairs": (None, [i64, vp, vp, i32, i32, i32, i32, u64, u64, vp]),
+            "orc_walk_perm_key": (C.c_uint32, [u64, u64, i32, i32]),
+            "orc_walk_perm": (u64, [u64, u64, C.c_uint32]),
+            "orc_train_walks": (None, [i64, vp, vp, vp, i32, i32, i32, i32, f64, f64, u64, u64, i32, i32,
+                                       vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -134,6 +140,39 @@ def train_sequential(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, graph
     nup = np.zeros(1, dtype=np.int64)
     lib().orc_train_sequential(len(rowptr) - 1, _p(rowptr), _p(col), _p(M), M.shape[1], k,
                                level, epochs, lr, lr_floor, seed, graph, _p(loss), _p(nup))
+    return loss[:epochs], int(nup[0])
+
+
+def walk_pairs_per_walk(l: int, g: int) -> int:
+    """Pairs (w_i, w_j), 0 < j - i <= g, of a walk of l vertices (Sec. 3.3)."""
+    return int(lib().orc_walk_pairs_per_walk(l, g))
+
+
+def walk_pairs(rowptr, col, l, g, level, epoch, seed, graph=0) -> np.ndarray:
+    """The epoch's walk positions (Sec. 3.3): int32 [n * W, 2] of (source,
+    positive), -1 for holes; the walk from v fills rows v*W .. v*W+W-1."""
+    rowptr, col = _csr(rowptr, col)
+    n = len(rowptr) - 1
+    out = np.zeros((n * walk_pairs_per_walk(l, g), 2), dtype=np.int32)
+    lib().orc_walk_pairs(n, _p(rowptr), _p(col), l, g, level, epoch, seed, graph, _p(out))
+    return out
+
+
+def walk_perm(P: int, seed, graph, level, epoch) -> np.ndarray:
+    """Visiting order of an epoch's P walk positions (the shuffle)."""
+    key = lib().orc_walk_perm_key(seed, graph, level, epoch)
+    return np.array([lib().orc_walk_perm(i, P, key) for i in range(P)], dtype=np.int64)
+
+
+def train_walks(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, l, g, graph=0):
+    """Sequential epochs of walk-based positives (Sec. 3.3) on M (float64, in
+    place). Returns (loss[epochs], n_updates)."""
+    rowptr, col = _csr(rowptr, col)
+    assert M.dtype == np.float64 and M.flags.c_contiguous
+    loss = np.zeros(max(epochs, 1), dtype=np.float64)
+    nup = np.zeros(1, dtype=np.int64)
+    lib().orc_train_walks(len(rowptr) - 1, _p(rowptr), _p(col), _p(M), M.shape[1], k, level, epochs, lr,
+                          lr_floor, seed, graph, l, g, _p(loss), _p(nup))
     return loss[:epochs], int(nup[0])
 
 

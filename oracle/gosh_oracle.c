@@ -398,3 +398,156 @@ double orc_auc(int64_t npos, const double *pos, int64_t nneg, const double *neg)
     free(a);
     return U / ((double)npos * (double)nneg);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Random-walk sampling (Sec. 3.3, GOSHW): positive pairs from walks.        */
+/* The paper gives neither the walk length l nor the distance g, nor how the */
+/* walks are drawn and shuffled.  Readings:                                  */
+/*  - each epoch starts one walk of l vertices at every vertex v; step t      */
+/*    moves to a uniform neighbour of w_t (Philox block (v, t/4, level<<32 |  */
+/*    epoch, TAG_WALK), word t%4); a vertex without neighbours ends the walk; */
+/*  - every pair (w_i, w_j) with 0 < j - i <= g is a positive (source w_i);  */
+/*    the pairs of a full walk are ranked i ascending, then j ascending, and */
+/*    pair rank r of the walk from v sits at position v*W + r (W = pairs of a */
+/*    full walk); positions past the end of a shorter walk, and pairs whose   */
+/*    two ends are the same vertex, are holes (no update);                   */
+/*  - "shuffled": the epoch visits the positions in the order of a pseudo-    */
+/*    random permutation (a 4-round Feistel network on 2h-bit words,          */
+/*    2^(2h) >= P, round function lowbias32(x ^ key_r) & (2^h - 1), applied   */
+/*    again until the value is below P);                                     */
+/*  - each positive comes with k negatives uniform over V (Philox block      */
+/*    (position, blk, level<<32 | epoch, TAG_WALK_NEG), words 1..k; word 0   */
+/*    unused); a negative equal to the source is skipped.                    */
+/* ------------------------------------------------------------------------ */
+enum { TAG_WALK = 4, TAG_WALK_NEG = 5 };
+
+/* lowbias32 (C. Wellons, hash-prospector): xorshift-multiply integer hash. */
+static uint32_t lowbias32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+/* pairs of a walk of l vertices with window g */
+int64_t orc_walk_pairs_per_walk(int l, int g) {
+    int64_t w = 0;
+    for (int i = 0; i + 1 < l; ++i) w += (l - 1 - i) < g ? (l - 1 - i) : g;
+    return w;
+}
+
+/* Walk of up to l vertices from v; returns its length. */
+static int walk_from(const int64_t *rowptr, const int32_t *col, int64_t v, int l, int level, int epoch,
+                     uint64_t seed, uint64_t graph, int32_t *w) {
+    uint64_t key[2] = {seed, graph};
+    uint64_t words[4];
+    w[0] = (int32_t)v;
+    int len = 1;
+    for (int t = 0; t + 1 < l; ++t) {
+        if (t % 4 == 0) {
+            uint64_t ctr[4] = {(uint64_t)v, (uint64_t)(t / 4),
+                               ((uint64_t)(uint32_t)level << 32) | (uint32_t)epoch, TAG_WALK};
+            orc_philox4x64(ctr, key, words);
+        }
+        int64_t cur = w[t];
+        int64_t deg = rowptr[cur + 1] - rowptr[cur];
+        if (deg == 0) break;
+        w[t + 1] = col[rowptr[cur] + (int64_t)uniform_below(words[t % 4], (uint64_t)deg)];
+        ++len;
+    }
+    return len;
+}
+
+/* The epoch's position table: pairs[2*pos] = source (or -1 for a hole),
+ * pairs[2*pos+1] = positive.  n*W positions. */
+void orc_walk_pairs(int64_t n, const int64_t *rowptr, const int32_t *col, int l, int g, int level, int epoch,
+                    uint64_t seed, uint64_t graph, int32_t *pairs) {
+    const int64_t W = orc_walk_pairs_per_walk(l, g);
+    int32_t *w = (int32_t *)malloc(sizeof(int32_t) * (size_t)l);
+    for (int64_t v = 0; v < n; ++v) {
+        int len = walk_from(rowptr, col, v, l, level, epoch, seed, graph, w);
+        int64_t r = 0;
+        for (int i = 0; i + 1 < l; ++i)
+            for (int j = i + 1; j < l && j - i <= g; ++j, ++r) {
+                int32_t *pp = pairs + 2 * (v * W + r);
+                if (j < len && w[i] != w[j]) {
+                    pp[0] = w[i];
+                    pp[1] = w[j];
+                } else {
+                    pp[0] = -1;
+                    pp[1] = -1;
+                }
+            }
+    }
+    free(w);
+}
+
+/* Permutation key of an epoch, and the permutation itself. */
+uint32_t orc_walk_perm_key(uint64_t seed, uint64_t graph, int level, int epoch) {
+    uint32_t k = lowbias32((uint32_t)seed ^ ((uint32_t)level << 24));
+    k = lowbias32(k ^ (uint32_t)(seed >> 32) ^ (uint32_t)epoch);
+    return lowbias32(k ^ lowbias32((uint32_t)graph ^ (uint32_t)(graph >> 32)));
+}
+
+uint64_t orc_walk_perm(uint64_t i, uint64_t P, uint32_t key) {
+    int h = 1;
+    while (((uint64_t)1 << (2 * h)) < P) ++h;
+    const uint32_t mask = h >= 32 ? 0xffffffffU : (((uint32_t)1 << h) - 1);
+    uint64_t x = i;
+    do {
+        uint32_t lo = (uint32_t)(x & mask), hi = (uint32_t)(x >> h);
+        for (uint32_t r = 0; r < 4; ++r) {
+            uint32_t f = lowbias32(lo ^ lowbias32(key + r)) & mask;
+            uint32_t t = hi ^ f;
+            hi = lo;
+            lo = t;
+        }
+        x = ((uint64_t)hi << h) | lo;
+    } while (x >= P);
+    return x;
+}
+
+/* Sequential epochs of walk-based positives (Alg. 1 per sample, the epoch
+ * visiting the positions in permuted order). */
+void orc_train_walks(int64_t n, const int64_t *rowptr, const int32_t *col, double *M, int d, int k, int level,
+                     int epochs, double lr, double lr_floor, uint64_t seed, uint64_t graph, int l, int g,
+                     double *loss_per_epoch, int64_t *n_updates) {
+    const int64_t W = orc_walk_pairs_per_walk(l, g);
+    const uint64_t P = (uint64_t)(n * W);
+    int32_t *pairs = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(P > 0 ? P : 1));
+    uint64_t key[2] = {seed, graph};
+    int64_t applied = 0;
+    for (int j = 0; j < epochs; ++j) {
+        double lrj = orc_epoch_lr(lr, lr_floor, j, epochs);
+        double loss = 0.0;
+        orc_walk_pairs(n, rowptr, col, l, g, level, j, seed, graph, pairs);
+        const uint32_t pk = orc_walk_perm_key(seed, graph, level, j);
+        for (uint64_t i = 0; i < P; ++i) {
+            const uint64_t q = orc_walk_perm(i, P, pk);
+            const int32_t src = pairs[2 * q], pos = pairs[2 * q + 1];
+            if (src < 0) continue;
+            uint64_t w[64];
+            for (int blk = 0; blk * 4 < k + 1; ++blk) {
+                uint64_t ctr[4] = {q, (uint64_t)blk, ((uint64_t)(uint32_t)level << 32) | (uint32_t)j, TAG_WALK_NEG};
+                orc_philox4x64(ctr, key, w + 4 * blk);
+            }
+            for (int t = 0; t <= k; ++t) {
+                int64_t u;
+                if (t == 0) {
+                    u = pos;
+                } else {
+                    u = (int64_t)uniform_below(w[t], (uint64_t)n);
+                    if (u == src) continue;
+                }
+                double x = orc_update_embed(M + (int64_t)src * d, M + u * d, d, t == 0, lrj);
+                loss += orc_sample_loss(x, t == 0);
+                ++applied;
+            }
+        }
+        if (loss_per_epoch) loss_per_epoch[j] = loss;
+    }
+    free(pairs);
+    if (n_updates) *n_updates = applied;
+}
