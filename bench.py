@@ -282,9 +282,79 @@ def run_large_workload(args):
     }), flush=True)
 
 
+WALKS = dict(d=128, k=3, epochs=5, l=8, g=3, lr=0.045)
+
+
+def run_walks_workload(args):
+    """Random-walk positives (Sec. 3.3): level 0 of R-MAT scale 20 (the bench
+    graph), d=128 BF16, k=3, walks of 8 vertices from every vertex, pairs
+    within distance 3, 5 epochs.  One step = one gosh_train_level_walks call
+    (wall time: host walks overlapped with the copies and the device epochs);
+    the vertex-sampled step on the same level is timed beside it."""
+    import torch
+    import synth
+    from paper_2110_10049_gb300 import build as gbuild
+    gbuild.build()
+    from paper_2110_10049_gb300 import gosh
+    gr = synth.workload("rmat20").train
+    params = gosh.default_params(d=WALKS["d"], k=WALKS["k"], lr=WALKS["lr"], dtype=gosh.GOSH_BF16, seed=5,
+                                 walk_length=WALKS["l"], walk_window=WALKS["g"])
+    M = torch.empty((gr.n, WALKS["d"]), dtype=torch.bfloat16, device="cuda")
+    gosh.gosh_init_embedding(M, level=0, seed=5)
+    for _ in range(args.warmup):
+        gosh.gosh_train_level_walks(gr.rowptr, gr.col, M, 0, WALKS["epochs"], params)
+    torch.cuda.synchronize()
+    l0 = gosh.lib().gosh_kernel_launches()
+    nup = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tot_ms, host_ms, st = 0.0, 0.0, None
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            st = gosh.gosh_train_level_walks(gr.rowptr, gr.col, M, 0, WALKS["epochs"], params, n_updates=nup)
+            tot_ms += st["total_ms"]
+            host_ms += st["host_ms"]
+    launches = gosh.lib().gosh_kernel_launches() - l0
+    upd = int(nup.item())
+    value = upd / (tot_ms / 1000.0)
+    # algorithmic bytes of the pair kernels: per applied update of a pair with
+    # k+1 samples, the source row read and written once per pair, each sample
+    # row read and written, and the 8-byte pair (an upper bound on positions)
+    row = WALKS["d"] * 2
+    pairs_applied = upd / (WALKS["k"] + 1)
+    alg = pairs_applied * (2 * row * (WALKS["k"] + 2)) + 8 * st["positions"] * WALKS["epochs"] * args.steps
+    achieved = alg / (tot_ms / 1000.0) / 1e9
+    peak, peak_kind = peaks()
+    # the vertex-sampled step on the same level, for comparison
+    csr = gosh.to_device_csr(gr.rowptr, gr.col)
+    rp = gosh.default_params(d=WALKS["d"], k=WALKS["k"], lr=WALKS["lr"], dtype=gosh.GOSH_BF16, seed=5)
+    nup2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gosh.gosh_train_level(csr, M, 0, 2, rp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gosh.gosh_train_level(csr, M, 0, WALKS["epochs"], rp, n_updates=nup2)
+    e1.record()
+    torch.cuda.synchronize()
+    vs_ms = e0.elapsed_time(e1)
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "random-walk positives: R-MAT scale 20, ef 16, level 0, d=128 BF16, k=3, walks of "
+                               "8 vertices, window 3, 5 epochs",
+                   "vertices": gr.n, "positions_per_epoch": st["positions"]},
+        "host_walks_ms_per_step": host_ms / args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "train_pairs_kernel (whole call: copies and host overlap included)",
+                     "peak_kind": peak_kind},
+        "h2d_bytes_per_step": st["h2d_bytes"],
+        "vertex_sampled": {"value": int(nup2.item()) / (vs_ms / 1000.0), "ms": vs_ms},
+        "clocks": clocks.summary(), "gpu_launches": int(launches),
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "batch512", "large"])
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "batch512", "large", "walks"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -305,6 +375,10 @@ def main():
         return
     if args.workload == "batch512":
         run_batch_workload(args)
+        return
+    if args.workload == "walks":
+        if rank == 0 and args.impl == "gosh":
+            run_walks_workload(args)
         return
     if args.workload == "large":
         run_large_workload(args)

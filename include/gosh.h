@@ -105,7 +105,17 @@ typedef struct gosh_params {
                                launches every epoch separately */
     int vertices_per_warp;  /* sources a warp takes per tile (<= 32, rounded to a multiple
                                of 32/lanes_per_row); 0 = by level size (8 / 16 / 32) */
+    int walk_length;        /* gosh_train_level_walks: vertices per random walk, l (default 8) */
+    int walk_window;        /* gosh_train_level_walks: pairs within distance g (default 3) */
 } gosh_params;
+
+typedef struct gosh_walk_stats {
+    int64_t positions;      /* pair positions per epoch: |V| * W, W = pairs of a full walk */
+    int epochs;
+    double host_ms;         /* walks drawn on host threads (overlapped with the device) */
+    double total_ms;        /* wall time of the call */
+    int64_t h2d_bytes;      /* pair tables copied to the device */
+} gosh_walk_stats;
 
 typedef struct gosh_large_stats {
     int parts;              /* K */
@@ -290,6 +300,30 @@ gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int level, int 
  */
 gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int epochs,
                                    const gosh_params *params, void *stream, gosh_large_stats *stats);
+
+/*
+ * Random-walk positives (Sec. 3.3, the paper's GOSHW): each epoch draws one
+ * walk of l = params->walk_length vertices from every vertex on host threads
+ * (step t of the walk from v: a uniform neighbour from Philox block
+ * (v, t/4, level<<32 | epoch, 4), word t%4; a vertex without neighbours ends
+ * the walk) and takes every pair (w_i, w_j) with 0 < j - i <= g =
+ * params->walk_window as a positive with source w_i.  The walk from v fills
+ * positions v*W .. v*W+W-1 (W = pairs of a full walk, i ascending then j);
+ * positions past a shorter walk and pairs with equal ends are skipped.  The
+ * GPU visits the positions in a pseudo-random order (the shuffle: a 4-round
+ * Feistel permutation of [0, |V| W) keyed by seed, graph, level and epoch)
+ * and applies Alg. 1 to the positive and to k <= 3 negatives drawn uniformly
+ * over V_i from Philox block (position, blk, level<<32 | epoch, 5), words
+ * 1..k (a negative equal to the source is skipped); lr decays per epoch as in
+ * gosh_train_level.  The host fills the pair table of epoch j+1 while the
+ * device copies and trains epoch j.
+ * g: CSR (host, or device: copied back once); M: device |V| x d, FP32 or
+ * BF16, d in {32, 64, 128}, updated in place.  Lock-free mode only.
+ * n_updates: device counter or NULL (incremented).  stats: host or NULL.
+ * Synchronous on `stream`.
+ */
+gosh_status gosh_train_level_walks(const gosh_csr *g, void *M, int level, int epochs, const gosh_params *params,
+                                   void *stream, unsigned long long *n_updates, gosh_walk_stats *stats);
 
 /* Host-only simulation of the LargeGraphGPU part-bin schedule (no GPU use):
  * for `rounds` rounds over K parts and p_gpu bins, writes for every kernel i

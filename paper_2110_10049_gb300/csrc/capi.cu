@@ -410,6 +410,8 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->large_parts = 0;
     p->persistent_small_levels = 0;
     p->vertices_per_warp = 0;
+    p->walk_length = 8;
+    p->walk_window = 3;
     return GOSH_OK;
 }
 

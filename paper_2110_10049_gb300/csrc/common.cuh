@@ -132,14 +132,25 @@ struct Philox4 {
     uint64_t w[4];
 };
 
-__device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
-                                                 uint64_t c3, uint64_t k0, uint64_t k1) {
+// High 64 bits of a 64 x 64-bit product (device: one instruction; host: the
+// compiler's 128-bit integer), so the host threads that draw random walks
+// produce the same words as the kernels.
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                                          uint64_t c3, uint64_t k0, uint64_t k1) {
     const uint64_t kMul0 = 0xD2E7470EE14C6C93ull, kMul1 = 0xCA5A826395121157ull;
     const uint64_t kWeyl0 = 0x9E3779B97F4A7C15ull, kWeyl1 = 0xBB67AE8584CAA73Bull;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint64_t p0hi = __umul64hi(kMul0, c0), p0lo = kMul0 * c0;
-        const uint64_t p1hi = __umul64hi(kMul1, c2), p1lo = kMul1 * c2;
+        const uint64_t p0hi = mulhi64(kMul0, c0), p0lo = kMul0 * c0;
+        const uint64_t p1hi = mulhi64(kMul1, c2), p1lo = kMul1 * c2;
         const uint64_t n0 = p1hi ^ c1 ^ k0;
         const uint64_t n2 = p0hi ^ c3 ^ k1;
         c0 = n0;
@@ -158,9 +169,9 @@ __device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint6
 }
 
 // Uniform integer in [0, n): floor(w * n / 2^64).
-__device__ __forceinline__ uint64_t uniform_index(uint64_t w, uint64_t n) { return __umul64hi(w, n); }
+__host__ __device__ __forceinline__ uint64_t uniform_index(uint64_t w, uint64_t n) { return mulhi64(w, n); }
 
-enum : uint64_t { kTagSample = 0, kTagInit = 1 };
+enum : uint64_t { kTagSample = 0, kTagInit = 1, kTagWalk = 4, kTagWalkNeg = 5 };
 
 // 32-bit integer finaliser "lowbias32" (C. Wellons, hash-prospector, public
 // domain): used as a counter-based source of stochastic-rounding bits.

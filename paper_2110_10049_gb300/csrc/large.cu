@@ -31,6 +31,7 @@
 #include <thread>
 #include <vector>
 
+#include "pinned.cuh"
 #include "train_kernels.cuh"
 
 namespace gosh {
@@ -265,61 +266,10 @@ PairLaunch pick_pair_kernel(gosh_dtype dt, int d) {
     return nullptr;
 }
 
-// Edge block (a, b) of one pair, built once on the host in pinned memory.
-// Pinned host memory for edge blocks, kept across calls (grow-only).  A call
-// that finds it in use by another call takes a private region instead.
-struct PinnedArena {
-    std::mutex mu;
-    char *ptr = nullptr;
-    size_t cap = 0;
-    bool busy = false;
-};
+// Pinned host memory for edge blocks, kept across calls.
 PinnedArena g_pinned;
 
-struct PinnedLease {
-    char *ptr = nullptr;
-    bool shared = false;
-    gosh_status acquire(size_t bytes) {
-        if (bytes == 0) bytes = 256;
-        {
-            std::lock_guard<std::mutex> lock(g_pinned.mu);
-            if (!g_pinned.busy) {
-                if (g_pinned.cap < bytes) {
-                    if (g_pinned.ptr) cudaFreeHost(g_pinned.ptr);
-                    g_pinned.ptr = nullptr;
-                    g_pinned.cap = 0;
-                    if (cudaMallocHost(&g_pinned.ptr, bytes) != cudaSuccess) {
-                        g_pinned.ptr = nullptr;
-                        cudaGetLastError();
-                        set_error("pinned allocation of %zu bytes of edge blocks failed", bytes);
-                        return GOSH_ERR_OOM;
-                    }
-                    g_pinned.cap = bytes;
-                }
-                g_pinned.busy = true;
-                shared = true;
-                ptr = g_pinned.ptr;
-                return GOSH_OK;
-            }
-        }
-        if (cudaMallocHost(&ptr, bytes) != cudaSuccess) {
-            ptr = nullptr;
-            cudaGetLastError();
-            set_error("pinned allocation of %zu bytes of edge blocks failed", bytes);
-            return GOSH_ERR_OOM;
-        }
-        return GOSH_OK;
-    }
-    ~PinnedLease() {
-        if (shared) {
-            std::lock_guard<std::mutex> lock(g_pinned.mu);
-            g_pinned.busy = false;
-        } else if (ptr) {
-            cudaFreeHost(ptr);
-        }
-    }
-};
-
+// Edge block (a, b) of one pair, built once on the host in pinned memory.
 struct Block {
     int64_t *rp_ab = nullptr, *rp_ba = nullptr;
     int32_t *col_ab = nullptr, *col_ba = nullptr;
@@ -520,8 +470,8 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
         max_block = std::max(max_block, B.bytes);
         total_bytes += B.bytes;
     }
-    PinnedLease lease;
-    GOSH_TRY(lease.acquire(total_bytes));
+    PinnedLease lease(g_pinned);
+    GOSH_TRY(lease.acquire(total_bytes, "edge blocks"));
     {
         size_t off = 0;
         for (size_t i = 0; i < blocks.size(); ++i) {

@@ -178,9 +178,30 @@ constexpr int kTileDraws = 1, kTileRounds = 2;
  *               kept, only read stale;
  *   kModeDet    snapshot batch, changes written to R/C/keys (needs P >= k+1).
  */
-template <typename T, int D, int L, int P, int MODE, int PHASES = kTileDraws | kTileRounds>
+// Position i of an epoch's walk pairs visited i-th (Sec. 3.3, "shuffled"):
+// a 4-round Feistel network on 2h-bit words (2^(2h) >= P) with round
+// function mix32(x ^ k_r) & (2^h - 1), k_r = mix32(key + r), repeated until the
+// value falls below P (cycle walking keeps it a bijection of [0, P)).
+__device__ __forceinline__ uint64_t walk_position(uint64_t i, uint64_t P, uint32_t key, int h) {
+    const uint32_t mask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
+    uint64_t x = i;
+    do {
+        uint32_t lo = (uint32_t)(x & mask), hi = (uint32_t)(x >> h);
+#pragma unroll
+        for (uint32_t r = 0; r < 4; ++r) {
+            const uint32_t t = hi ^ (mix32(lo ^ mix32(key + r)) & mask);
+            hi = lo;
+            lo = t;
+        }
+        x = ((uint64_t)hi << h) | lo;
+    } while (x >= P);
+    return x;
+}
+
+template <typename T, int D, int L, int P, int MODE, int PHASES = kTileDraws | kTileRounds, bool PAIRS = false>
 __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0, int32_t *s_u_w, uint32_t *s_sr_w,
-                                           double &loss_acc, unsigned long long &applied) {
+                                           double &loss_acc, unsigned long long &applied,
+                                           int32_t *s_src_w = nullptr) {
     constexpr bool DET = MODE == kModeDet;
     constexpr bool RED = MODE == kModeRed;
     constexpr bool RED16 = RED && !std::is_same<T, float>::value;
@@ -190,6 +211,7 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
     static_assert(E % PV == 0, "lane slice must be whole 16-byte vectors");
     static_assert(32 % L == 0, "L must divide the warp");
     static_assert(!DET || E % 4 == 0, "float4 stores of the change buffers");
+    static_assert(!(DET && PAIRS), "walk pairs are trained lock-free");
 
     const int lane = threadIdx.x & 31;
     const int grp = lane / L, gl = lane % L;
@@ -199,7 +221,38 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
     const bool want_loss = a.loss_partials != nullptr;
     {
         // ---- draws: lane j -> source v0 + j ----
-        if constexpr ((PHASES & kTileDraws) != 0) {
+        if constexpr ((PHASES & kTileDraws) != 0 && PAIRS) {
+            // walk pairs: slot v0 + lane visits position q; its source and
+            // positive come from the pair table, the negatives from the
+            // position's own Philox block (word 0 unused)
+            const int64_t i = v0 + lane;
+            if (lane < a.tile && i < a.src_end) {
+                const uint64_t q = walk_position((uint64_t)i, (uint64_t)a.src_end, a.walk_key, a.walk_h);
+                const int2 pr = __ldg(reinterpret_cast<const int2 *>(a.pairs) + q);
+                s_src_w[lane] = pr.x;
+                for (int blk = 0; blk * 4 < ns; ++blk) {
+                    const Philox4 w = philox4x64_10(q, (uint64_t)blk, ctr2, kTagWalkNeg, a.seed, a.graph);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int t = blk * 4 + j;
+                        if (t < ns) {
+                            int32_t u;
+                            if (pr.x < 0) {
+                                u = -1;
+                            } else if (t == 0) {
+                                u = pr.y;
+                            } else {
+                                const int64_t x = (int64_t)uniform_index(w.w[j], (uint64_t)a.n);
+                                u = x == pr.x ? -1 : (int32_t)x;
+                            }
+                            s_u_w[lane * kSlotStride + t] = u;
+                        }
+                    }
+                }
+                if (!std::is_same<T, float>::value)
+                    s_sr_w[lane] = sr_source_seed(a.seed, a.graph, a.level, a.epoch, (int64_t)q);
+            }
+        } else if constexpr ((PHASES & kTileDraws) != 0) {
             const int64_t v = v0 + lane;
             if (lane < a.tile && v < a.src_end) {
                 const int64_t off = a.rowptr[v];
@@ -232,8 +285,12 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
 #pragma unroll 1
         for (int q = 0; q < rounds; ++q) {
             const int j = q * G + grp;
-            const int64_t v = v0 + j;
-            const bool active = v < a.src_end;
+            int64_t v = v0 + j;
+            bool active = v < a.src_end;
+            if constexpr (PAIRS) {
+                v = active ? s_src_w[j] : -1;  // the pair's source row (-1: a hole)
+                active = v >= 0;
+            }
             const uint32_t sr = std::is_same<T, float>::value ? 0u : s_sr_w[j];
             float r[E];
             if (active) {

@@ -42,7 +42,13 @@ class gosh_params(C.Structure):
                 ("plain_stores", C.c_int), ("projection", C.c_int), ("mlp_hidden", C.c_int),
                 ("mlp_epochs", C.c_int), ("mlp_lr", C.c_double), ("mlp_batch", C.c_int),
                 ("mlp_max_rows", C.c_int64), ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int),
-                ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int)]
+                ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int),
+                ("walk_length", C.c_int), ("walk_window", C.c_int)]
+
+
+class gosh_walk_stats(C.Structure):
+    _fields_ = [("positions", C.c_int64), ("epochs", C.c_int), ("host_ms", C.c_double), ("total_ms", C.c_double),
+                ("h2d_bytes", C.c_int64)]
 
 
 class gosh_large_stats(C.Structure):
@@ -98,6 +104,7 @@ def lib() -> C.CDLL:
             "gosh_embed_batch": [i32, vp, P(gosh_params), vp, vp, P(gosh_batch_stats)],
             "gosh_device_check": [vp],
             "gosh_train_level_large": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, P(gosh_large_stats)],
+            "gosh_train_level_walks": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, vp, P(gosh_walk_stats)],
             "gosh_large_plan": [i64, i32, i32, i32, vp, vp, i32],
             "gosh_mlp_create": [i32, i32, u64, P(vp)],
             "gosh_mlp_get_weights": [vp, vp, vp, vp, vp],
@@ -356,6 +363,21 @@ def gosh_train_level_large(rowptr, col, M, level, epochs, params: gosh_params, s
     _check("gosh_train_level_large", lib().gosh_train_level_large(C.byref(cg), C.c_void_p(ptr), level, epochs,
                                                                   C.byref(params), _stream(stream), C.byref(st)))
     return {f: getattr(st, f) for f, _ in gosh_large_stats._fields_}
+
+
+def gosh_train_level_walks(rowptr, col, M, level, epochs, params: gosh_params, n_updates=None, stream=None):
+    """Random-walk positives (Sec. 3.3) on a host CSR (numpy) and a device M
+    (torch, updated in place).  Returns the stats dict."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    cg = gosh_csr(len(rowptr) - 1, rowptr.ctypes.data, col.ctypes.data, 0)
+    st = gosh_walk_stats()
+    _check("gosh_train_level_walks", lib().gosh_train_level_walks(C.byref(cg), _ptr(M), level, epochs,
+                                                                  C.byref(params), _stream(stream),
+                                                                  _ptr(n_updates), C.byref(st)))
+    return {f: getattr(st, f) for f, _ in gosh_walk_stats._fields_}
 
 
 def gosh_large_plan(n, K, p_gpu, rounds):
