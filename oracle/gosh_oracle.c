@@ -13,6 +13,7 @@
  *   Alg. 3  TRAININGPU epoch loop      (Sec. 3.1)
  *   Alg. 4  MULTIEDGECOLLAPSE          (Sec. 4)
  *   Sec. 3  EXPANDEMBEDDING (copy projection), epoch split, lr decay
+ *   Sec. 3.3 random-walk positive sampling (GOSHW)
  *   Sec. 6.1 link-prediction AUC protocol
  * Where the paper is silent the reading used is written beside the code.
  *
