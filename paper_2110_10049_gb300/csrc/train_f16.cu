@@ -1,31 +1,35 @@
-// Training-step kernel instantiations for f16 storage.
+// Training-step kernel instantiations for f16 storage: one translation
+// unit per embedding width (train_f16_d<d>.cu, compiled in parallel), and
+// here the list of all of them and the deterministic-mode apply kernels.
+#include <vector>
+
 #include "train_kernels.cuh"
 
 namespace gosh {
-namespace {
-using T = __half;
-constexpr int L16 = 16 * (int)sizeof(T) / 16;
-constexpr int L32 = 32 * (int)sizeof(T) / 16;
-constexpr int L64 = 64 * (int)sizeof(T) / 16;
-constexpr int L128 = 128 * (int)sizeof(T) / 16;
-constexpr gosh_dtype kType = GOSH_F16;
 
-#define GOSH_V(D, L, P, MODE) {kType, D, L, P, MODE, &make_train_kernel<T, D, L, P, MODE>}
-#define GOSH_VD(D, L0)                                                                               \
-    GOSH_V(D, L0, 2, kModeRed), GOSH_V(D, L0, 4, kModeRed), GOSH_V(D, L0 / 2, 2, kModeRed),          \
-        GOSH_V(D, L0 / 2, 4, kModeRed), GOSH_V(D, L0, 2, kModeStore), GOSH_V(D, L0, 4, kModeStore),   \
-        GOSH_V(D, L0 / 2, 2, kModeStore), GOSH_V(D, L0 / 2, 4, kModeStore), GOSH_V(D, L0, 4, kModeDet), \
-        GOSH_V(D, L0, 8, kModeDet)
-
-const TrainEntry kEntries[] = {GOSH_VD(16, L16), GOSH_VD(32, L32), GOSH_VD(64, L64), GOSH_VD(128, L128)};
-#undef GOSH_VD
-#undef GOSH_V
-}  // namespace
+const TrainEntry *train_entries_f16_d16(int *count);
+const TrainEntry *train_entries_f16_d32(int *count);
+const TrainEntry *train_entries_f16_d64(int *count);
+const TrainEntry *train_entries_f16_d128(int *count);
 
 const TrainEntry *train_entries_f16(int *count) {
-    *count = (int)(sizeof(kEntries) / sizeof(kEntries[0]));
-    return kEntries;
+    static std::vector<TrainEntry> all = [] {
+        std::vector<TrainEntry> v;
+        for (auto f : {train_entries_f16_d16, train_entries_f16_d32, train_entries_f16_d64,
+                       train_entries_f16_d128}) {
+            int c = 0;
+            const TrainEntry *e = f(&c);
+            v.insert(v.end(), e, e + c);
+        }
+        return v;
+    }();
+    *count = (int)all.size();
+    return all.data();
 }
+
+namespace {
+using T = __half;
+}  // namespace
 
 void det_apply_f16(int d, const uint32_t *skeys, const uint32_t *sidx, int64_t nslots, const float *C,
                   const float *R, void *M, int64_t n, int64_t b0, int64_t b1, uint8_t *src_done,
