@@ -325,6 +325,18 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
 gosh_status gosh_train_level_walks(const gosh_csr *g, void *M, int level, int epochs, const gosh_params *params,
                                    void *stream, unsigned long long *n_updates, gosh_walk_stats *stats);
 
+/* The pair table gosh_train_level_walks uses for one epoch, drawn on the
+ * calling thread (no device involved): pairs = host int32[|V| * W * 2] of
+ * (source, positive) per position, -1 for holes, W = pairs of a full walk
+ * (sum over i < l-1 of min(g, l-1-i)).  g: host CSR. */
+gosh_status gosh_walk_pairs(const gosh_csr *g, int walk_length, int walk_window, int level, int epoch,
+                            uint64_t seed, uint64_t graph_id, int32_t *pairs);
+
+/* The order in which the device visits an epoch's positions (the shuffle):
+ * order = host int64[positions], order[i] = position visited i-th.  Host only. */
+gosh_status gosh_walk_order(int64_t positions, int level, int epoch, uint64_t seed, uint64_t graph_id,
+                            int64_t *order);
+
 /* Host-only simulation of the LargeGraphGPU part-bin schedule (no GPU use):
  * for `rounds` rounds over K parts and p_gpu bins, writes for every kernel i
  * its pair (pairs_out[2i], pairs_out[2i+1]) = (a, b) and the loads done

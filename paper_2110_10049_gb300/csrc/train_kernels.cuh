@@ -182,7 +182,7 @@ constexpr int kTileDraws = 1, kTileRounds = 2;
 // a 4-round Feistel network on 2h-bit words (2^(2h) >= P) with round
 // function mix32(x ^ k_r) & (2^h - 1), k_r = mix32(key + r), repeated until the
 // value falls below P (cycle walking keeps it a bijection of [0, P)).
-__device__ __forceinline__ uint64_t walk_position(uint64_t i, uint64_t P, uint32_t key, int h) {
+__host__ __device__ __forceinline__ uint64_t walk_position(uint64_t i, uint64_t P, uint32_t key, int h) {
     const uint32_t mask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
     uint64_t x = i;
     do {

@@ -114,6 +114,54 @@ int walk_bits(uint64_t P) {
     return h;
 }
 
+// The pair positions of the walks from v0 .. v1-1 of one epoch into out
+// (2 int32 per position, rows v*W ..).  kGroup walks advance in lockstep:
+// their neighbour reads are independent, so the host cores overlap the cache
+// misses of a step.
+void walk_fill(const int64_t *rowptr, const int32_t *col, int64_t v0, int64_t v1, int l, int gw, int64_t W,
+               int level, int epoch, uint64_t seed, uint64_t graph, int32_t *out) {
+    constexpr int kGroup = 32;
+    std::vector<int32_t> w((size_t)kGroup * l);
+    int len[kGroup];
+    Philox4 words[kGroup];
+    const uint64_t ctr2 = ((uint64_t)(uint32_t)level << 32) | (uint32_t)epoch;
+    for (int64_t gs = v0; gs < v1; gs += kGroup) {
+        const int cnt = (int)std::min<int64_t>(kGroup, v1 - gs);
+        for (int b = 0; b < cnt; ++b) {
+            w[(size_t)b * l] = (int32_t)(gs + b);
+            len[b] = 1;
+        }
+        for (int t = 0; t + 1 < l; ++t) {
+            for (int b = 0; b < cnt; ++b) {
+                if (len[b] != t + 1) continue;  // this walk has ended
+                const int64_t v = gs + b;
+                if ((t & 3) == 0) words[b] = philox4x64_10((uint64_t)v, (uint64_t)(t >> 2), ctr2, kTagWalk, seed, graph);
+                const int64_t cur = w[(size_t)b * l + t];
+                const int64_t off = rowptr[cur], deg = rowptr[cur + 1] - off;
+                if (deg == 0) continue;
+                w[(size_t)b * l + t + 1] = col[off + (int64_t)uniform_index(words[b].w[t & 3], (uint64_t)deg)];
+                len[b] = t + 2;
+            }
+        }
+        for (int b = 0; b < cnt; ++b) {
+            const int32_t *wb = w.data() + (size_t)b * l;
+            int32_t *pp = out + 2 * (gs + b) * W;
+            for (int i = 0; i + 1 < l; ++i)
+                for (int j = i + 1; j < l && j - i <= gw; ++j, pp += 2) {
+                    const bool ok = j < len[b] && wb[i] != wb[j];
+                    pp[0] = ok ? wb[i] : -1;
+                    pp[1] = ok ? wb[j] : -1;
+                }
+        }
+    }
+}
+
+int64_t walk_positions_per_walk(int l, int gw) {
+    int64_t W = 0;
+    for (int i = 0; i + 1 < l; ++i) W += std::min(gw, l - 1 - i);
+    return W;
+}
+
 PinnedArena g_walk_pinned;
 
 }  // namespace
@@ -159,8 +207,7 @@ gosh_status gosh_train_level_walks(const gosh_csr *g, void *M, int level, int ep
         col = hcol.data();
     }
 
-    int64_t W = 0;
-    for (int i = 0; i + 1 < l; ++i) W += std::min(gw, l - 1 - i);
+    const int64_t W = walk_positions_per_walk(l, gw);
     const int64_t P = n * W;  // positions per epoch
     const size_t bytes = sizeof(int32_t) * 2 * (size_t)P;
     PinnedLease lease(g_walk_pinned);
@@ -177,47 +224,9 @@ gosh_status gosh_train_level_walks(const gosh_csr *g, void *M, int level, int ep
         constexpr int64_t kWalksPerItem = 4096;
         std::atomic<int64_t> next{0};
         auto work = [&]() {
-            // kGroup walks advance in lockstep: their neighbour reads are
-            // independent, so the host cores overlap the cache misses of a step
-            constexpr int kGroup = 32;
-            std::vector<int32_t> w((size_t)kGroup * l);
-            int len[kGroup];
-            Philox4 words[kGroup];
-            const uint64_t ctr2 = ((uint64_t)(uint32_t)level << 32) | (uint32_t)epoch;
-            for (int64_t v0 = next.fetch_add(kWalksPerItem); v0 < n; v0 = next.fetch_add(kWalksPerItem)) {
-                const int64_t v1 = std::min(v0 + kWalksPerItem, n);
-                for (int64_t gs = v0; gs < v1; gs += kGroup) {
-                    const int cnt = (int)std::min<int64_t>(kGroup, v1 - gs);
-                    for (int b = 0; b < cnt; ++b) {
-                        w[(size_t)b * l] = (int32_t)(gs + b);
-                        len[b] = 1;
-                    }
-                    for (int t = 0; t + 1 < l; ++t) {
-                        for (int b = 0; b < cnt; ++b) {
-                            if (len[b] != t + 1) continue;  // this walk has ended
-                            const int64_t v = gs + b;
-                            if ((t & 3) == 0)
-                                words[b] = philox4x64_10((uint64_t)v, (uint64_t)(t >> 2), ctr2, kTagWalk, p->seed,
-                                                         p->graph_id);
-                            const int64_t cur = w[(size_t)b * l + t];
-                            const int64_t off = rowptr[cur], deg = rowptr[cur + 1] - off;
-                            if (deg == 0) continue;
-                            w[(size_t)b * l + t + 1] = col[off + (int64_t)uniform_index(words[b].w[t & 3], (uint64_t)deg)];
-                            len[b] = t + 2;
-                        }
-                    }
-                    for (int b = 0; b < cnt; ++b) {
-                        const int32_t *wb = w.data() + (size_t)b * l;
-                        int32_t *pp = out + 2 * (gs + b) * W;
-                        for (int i = 0; i + 1 < l; ++i)
-                            for (int j = i + 1; j < l && j - i <= gw; ++j, pp += 2) {
-                                const bool ok = j < len[b] && wb[i] != wb[j];
-                                pp[0] = ok ? wb[i] : -1;
-                                pp[1] = ok ? wb[j] : -1;
-                            }
-                    }
-                }
-            }
+            for (int64_t v0 = next.fetch_add(kWalksPerItem); v0 < n; v0 = next.fetch_add(kWalksPerItem))
+                walk_fill(rowptr, col, v0, std::min(v0 + kWalksPerItem, n), l, gw, W, level, epoch, p->seed,
+                          p->graph_id, out);
         };
         std::vector<std::thread> th;
         for (int t = 1; t < nt; ++t) th.emplace_back(work);
@@ -304,6 +313,28 @@ gosh_status gosh_train_level_walks(const gosh_csr *g, void *M, int level, int ep
         stats->h2d_bytes = (int64_t)bytes * epochs;
     }
     (void)wait_ms;
+    return GOSH_OK;
+}
+
+gosh_status gosh_walk_pairs(const gosh_csr *g, int walk_length, int walk_window, int level, int epoch,
+                            uint64_t seed, uint64_t graph_id, int32_t *pairs) {
+    clear_error();
+    GOSH_CHECK_ARG(g && pairs && !g->on_device, "needs a host CSR and a host output");
+    GOSH_CHECK_ARG(g->n >= 1 && g->n < (int64_t(1) << 31), "bad n");
+    GOSH_CHECK_ARG(walk_length >= 2 && walk_length <= 256 && walk_window >= 1,
+                   "need 2 <= walk_length <= 256 and walk_window >= 1");
+    walk_fill(g->rowptr, g->col, 0, g->n, walk_length, walk_window, walk_positions_per_walk(walk_length, walk_window),
+              level, epoch, seed, graph_id, pairs);
+    return GOSH_OK;
+}
+
+gosh_status gosh_walk_order(int64_t positions, int level, int epoch, uint64_t seed, uint64_t graph_id,
+                            int64_t *order) {
+    clear_error();
+    GOSH_CHECK_ARG(order && positions >= 1, "bad positions / order");
+    const uint32_t key = walk_key(seed, graph_id, level, epoch);
+    const int h = walk_bits((uint64_t)positions);
+    for (int64_t i = 0; i < positions; ++i) order[i] = (int64_t)walk_position((uint64_t)i, (uint64_t)positions, key, h);
     return GOSH_OK;
 }
 

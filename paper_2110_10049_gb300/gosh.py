@@ -105,6 +105,8 @@ def lib() -> C.CDLL:
             "gosh_device_check": [vp],
             "gosh_train_level_large": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, P(gosh_large_stats)],
             "gosh_train_level_walks": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, vp, P(gosh_walk_stats)],
+            "gosh_walk_pairs": [P(gosh_csr), i32, i32, i32, i32, u64, u64, vp],
+            "gosh_walk_order": [i64, i32, i32, u64, u64, vp],
             "gosh_large_plan": [i64, i32, i32, i32, vp, vp, i32],
             "gosh_mlp_create": [i32, i32, u64, P(vp)],
             "gosh_mlp_get_weights": [vp, vp, vp, vp, vp],
@@ -378,6 +380,28 @@ def gosh_train_level_walks(rowptr, col, M, level, epochs, params: gosh_params, n
                                                                   C.byref(params), _stream(stream),
                                                                   _ptr(n_updates), C.byref(st)))
     return {f: getattr(st, f) for f, _ in gosh_walk_stats._fields_}
+
+
+def gosh_walk_pairs(rowptr, col, walk_length, walk_window, level, epoch, seed, graph_id=0):
+    """An epoch's walk pair table (host only): int32 [n * W, 2], -1 for holes."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    n = len(rowptr) - 1
+    W = sum(min(walk_window, walk_length - 1 - i) for i in range(walk_length - 1))
+    out = np.zeros((n * W, 2), dtype=np.int32)
+    cg = gosh_csr(n, rowptr.ctypes.data, col.ctypes.data, 0)
+    _check("gosh_walk_pairs", lib().gosh_walk_pairs(C.byref(cg), walk_length, walk_window, level, epoch, seed,
+                                                    graph_id, out.ctypes.data))
+    return out
+
+
+def gosh_walk_order(positions, level, epoch, seed, graph_id=0):
+    """The order of an epoch's walk positions on the device (host only)."""
+    out = np.zeros(positions, dtype=np.int64)
+    _check("gosh_walk_order", lib().gosh_walk_order(positions, level, epoch, seed, graph_id, out.ctypes.data))
+    return out
 
 
 def gosh_large_plan(n, K, p_gpu, rounds):
