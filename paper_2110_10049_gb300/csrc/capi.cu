@@ -158,12 +158,6 @@ __global__ void project_copy_kernel(const uint4 *__restrict__ Mc, const int32_t 
     }
 }
 
-__global__ void map_range_check(const int32_t *__restrict__ map, int64_t n, int64_t nc, unsigned *__restrict__ bad) {
-    GOSH_DEP_WAIT();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        if (map[i] < 0 || map[i] >= nc) atomicOr(bad, 1u);
-}
-
 // ---------------------------------------------------------------- scores / AUC
 template <typename T, int L>
 __global__ void pair_scores_kernel(const T *__restrict__ M, int d, const int32_t *__restrict__ pairs, int64_t np,

@@ -97,9 +97,4 @@ const TrainKernel *find_train_kernel(gosh_dtype dtype, int d, int lanes, int pas
 // Lists the lanes-per-row and samples-per-pass variants compiled for (dtype, d, mode).
 int list_train_variants(gosh_dtype dtype, int d, int mode, int *lanes, int *pass, int cap);
 
-// Deterministic-mode end-of-batch kernels.
-void launch_det_apply(gosh_dtype dtype, int d, const uint32_t *skeys, const uint32_t *sidx,
-                      int64_t nslots, const float *C, const float *R, void *M, int64_t n,
-                      int64_t b0, int64_t b1, uint8_t *src_done, uint32_t sr_seed, cudaStream_t s);
-
 }  // namespace gosh
