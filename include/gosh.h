@@ -39,7 +39,7 @@ typedef enum gosh_status {
     GOSH_ERR_BUDGET = 3,       /* the work does not fit the device budget */
     GOSH_ERR_CUDA = 4,         /* a CUDA call failed */
     GOSH_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
-    GOSH_ERR_UNSUPPORTED = 6   /* valid request this build does not serve */
+    GOSH_ERR_UNSUPPORTED = 6   /* valid request the library does not serve */
 } gosh_status;
 
 typedef enum gosh_dtype { GOSH_F32 = 0, GOSH_BF16 = 1, GOSH_F16 = 2 } gosh_dtype;
@@ -346,7 +346,7 @@ int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int
 
 /* Stochastic rounding of FP32 values to a 16-bit table type (dtype GOSH_BF16
  * or GOSH_F16), exactly as the training kernels round every value they write
- * (the benchmark spec's 16-bit tables; the paper trains in FP32): value i is rounded
+ * (16-bit tables with FP32 arithmetic; the paper trains in FP32): value i is rounded
  * away from zero with probability equal to its distance from the value toward
  * zero divided by the gap between the two, using 16 random bits from a 32-bit
  * hash of (seed, i / 2); infinities and NaNs pass unchanged.
