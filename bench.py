@@ -112,6 +112,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(total_ms, updates, dist, device):
+    """The job's timed milliseconds (the slowest rank's) and its work (the sum
+    over the ranks); without a process group, this rank's own."""
+    import torch
+    t = torch.tensor([total_ms, float(updates)], dtype=torch.float64, device=device)
+    if dist:
+        mx, sm = t[0:1].clone(), t[1:2].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        t = torch.cat([mx, sm])
+    return float(t[0]), float(t[1])
+
+
 def make_inputs(rank):
     import synth
     seed = 20211021 + 1000 * rank
@@ -443,14 +456,7 @@ def main():
             stats.append(sd)
     launches = l0.gosh_kernel_launches() - launches0
     barrier()
-    # max time over ranks, sum of work
-    t = torch.tensor([total_ms, float(updates)], dtype=torch.float64, device="cuda")
-    if dist:
-        tt = t.clone()
-        dist.all_reduce(tt[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:2], op=dist.ReduceOp.SUM)
-        t = tt
-    max_ms, all_updates = float(t[0]), float(t[1])
+    max_ms, all_updates = reduce_over_ranks(total_ms, updates, dist, "cuda")
     value = all_updates / (max_ms / 1000.0)
     ms_per_step = max_ms / args.steps
 
