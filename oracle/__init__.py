@@ -9,6 +9,13 @@ Alg. 4 (level loop, stop condition, epoch split), each written out from the
 paper.
 
 Parity pins for every function are in ``tests/test_oracle_*.py``.
+
+Parity unpinned (what the GPU path is judged by instead): lock-free training
+beyond the single-warp case, whose update order is not reproducible
+(link-prediction AUC against ``train_sequential``); LargeGraphGPU beyond one
+part, which reorders the updates and has no oracle of its own (AUC against
+the resident step); the learned projection's training trajectory (the
+gradients are pinned; the trained network is judged by its AUC gain).
 """
 from __future__ import annotations
 

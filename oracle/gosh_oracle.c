@@ -19,6 +19,11 @@
  *
  * Compiled with -ffp-contract=off so that every a*b+c is two rounded
  * operations, exactly as written.
+ *
+ * Parity unpinned: lock-free (Hogwild) training beyond one warp with one
+ * source per round, whose update order is not reproducible, is compared with
+ * orc_train_sequential only through link-prediction AUC; LargeGraphGPU beyond
+ * one part has no function here and is compared with the resident step.
  */
 #include <stdint.h>
 #include <stdlib.h>
