@@ -237,13 +237,15 @@ __global__ void write_coarse(const uint64_t *__restrict__ keys, const uint8_t *_
 // minus c itself.  The members that have neighbours are grouped by cluster
 // and their CSR rows, laid end to end, are the "virtual entries" of row c,
 // cut into chunks of kChunk entries.  A block takes one chunk and sets bit
-// map[y] of a shared-memory bitmap over the nc coarse ids for each entry
-// (plus one summary bit per nonzero 32-bit word), then reads the set bits
-// back in ascending order: the row comes out sorted and deduplicated without
-// a global sort, and only the words the chunk touched are visited.  Rows of
-// more than one chunk OR their chunk bitmaps into a global bitmap that a
-// second kernel reads back.  The member order inside a cluster (atomics)
-// does not matter: a bitmap is a set.
+// map[y] of a shared-memory bitmap over the coarse ids (of the row's graph,
+// for a union of graphs) for each entry, plus one summary bit per nonzero
+// 32-bit word, then reads the set bits back in ascending order over the
+// front of the row's own entry range: the row comes out sorted and
+// deduplicated without a global sort, and only the words the chunk touched
+// are visited.  Rows of more than one chunk OR their chunk bitmaps into a
+// global bitmap that a second kernel reads back; a compaction then moves
+// every row to its CSR position.  The member order inside a cluster
+// (atomics) does not matter: a bitmap is a set.
 constexpr int kChunk = 4096;
 constexpr int kBatch = 8;                    // loads in flight per thread
 constexpr int kRowThreads = 128;
