@@ -120,9 +120,10 @@ int walk_bits(uint64_t P) {
 // misses of a step.
 void walk_fill(const int64_t *rowptr, const int32_t *col, int64_t v0, int64_t v1, int l, int gw, int64_t W,
                int level, int epoch, uint64_t seed, uint64_t graph, int32_t *out) {
-    constexpr int kGroup = 32;
+    constexpr int kGroup = 128;
     std::vector<int32_t> w((size_t)kGroup * l);
     int len[kGroup];
+    int64_t at[kGroup];
     Philox4 words[kGroup];
     const uint64_t ctr2 = ((uint64_t)(uint32_t)level << 32) | (uint32_t)epoch;
     for (int64_t gs = v0; gs < v1; gs += kGroup) {
@@ -130,17 +131,27 @@ void walk_fill(const int64_t *rowptr, const int32_t *col, int64_t v0, int64_t v1
         for (int b = 0; b < cnt; ++b) {
             w[(size_t)b * l] = (int32_t)(gs + b);
             len[b] = 1;
+            __builtin_prefetch(rowptr + gs + b);
         }
         for (int t = 0; t + 1 < l; ++t) {
+            // pass 1: the entry each live walk moves through (row pointers,
+            // prefetched one step earlier); pass 2: the neighbour reads, all
+            // independent, then a prefetch of the next step's row pointers
             for (int b = 0; b < cnt; ++b) {
+                at[b] = -1;
                 if (len[b] != t + 1) continue;  // this walk has ended
-                const int64_t v = gs + b;
-                if ((t & 3) == 0) words[b] = philox4x64_10((uint64_t)v, (uint64_t)(t >> 2), ctr2, kTagWalk, seed, graph);
+                if ((t & 3) == 0)
+                    words[b] = philox4x64_10((uint64_t)(gs + b), (uint64_t)(t >> 2), ctr2, kTagWalk, seed, graph);
                 const int64_t cur = w[(size_t)b * l + t];
                 const int64_t off = rowptr[cur], deg = rowptr[cur + 1] - off;
-                if (deg == 0) continue;
-                w[(size_t)b * l + t + 1] = col[off + (int64_t)uniform_index(words[b].w[t & 3], (uint64_t)deg)];
+                if (deg > 0) at[b] = off + (int64_t)uniform_index(words[b].w[t & 3], (uint64_t)deg);
+            }
+            for (int b = 0; b < cnt; ++b) {
+                if (at[b] < 0) continue;
+                const int32_t nx = col[at[b]];
+                w[(size_t)b * l + t + 1] = nx;
                 len[b] = t + 2;
+                __builtin_prefetch(rowptr + nx);
             }
         }
         for (int b = 0; b < cnt; ++b) {
