@@ -308,7 +308,7 @@ WALKS = dict(d=128, k=3, epochs=5, l=8, g=3, lr=0.045)
 
 
 def run_walks_workload(args):
-    """Random-walk positives (Sec. 3.3): level 0 of R-MAT scale 20 (the bench
+    """Random-walk positives (Sec. 3.2): level 0 of R-MAT scale 20 (the bench
     graph), d=128 BF16, k=3, walks of 8 vertices from every vertex, pairs
     within distance 3, 5 epochs.  One step = one gosh_train_level_walks call
     (wall time: host walks overlapped with the copies and the device epochs);

@@ -302,7 +302,7 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
                                    const gosh_params *params, void *stream, gosh_large_stats *stats);
 
 /*
- * Random-walk positives (Sec. 3.3, the paper's GOSHW): each epoch draws one
+ * Random-walk positives (Sec. 3.2, the paper's GOSHW): each epoch draws one
  * walk of l = params->walk_length vertices from every vertex on host threads
  * (step t of the walk from v: a uniform neighbour from Philox block
  * (v, t/4, level<<32 | epoch, 4), word t%4; a vertex without neighbours ends

@@ -151,12 +151,12 @@ def train_sequential(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, graph
 
 
 def walk_pairs_per_walk(l: int, g: int) -> int:
-    """Pairs (w_i, w_j), 0 < j - i <= g, of a walk of l vertices (Sec. 3.3)."""
+    """Pairs (w_i, w_j), 0 < j - i <= g, of a walk of l vertices (Sec. 3.2)."""
     return int(lib().orc_walk_pairs_per_walk(l, g))
 
 
 def walk_pairs(rowptr, col, l, g, level, epoch, seed, graph=0) -> np.ndarray:
-    """The epoch's walk positions (Sec. 3.3): int32 [n * W, 2] of (source,
+    """The epoch's walk positions (Sec. 3.2): int32 [n * W, 2] of (source,
     positive), -1 for holes; the walk from v fills rows v*W .. v*W+W-1."""
     rowptr, col = _csr(rowptr, col)
     n = len(rowptr) - 1
@@ -172,7 +172,7 @@ def walk_perm(P: int, seed, graph, level, epoch) -> np.ndarray:
 
 
 def train_walks(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, l, g, graph=0):
-    """Sequential epochs of walk-based positives (Sec. 3.3) on M (float64, in
+    """Sequential epochs of walk-based positives (Sec. 3.2) on M (float64, in
     place). Returns (loss[epochs], n_updates)."""
     rowptr, col = _csr(rowptr, col)
     assert M.dtype == np.float64 and M.flags.c_contiguous

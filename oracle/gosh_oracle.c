@@ -13,7 +13,7 @@
  *   Alg. 3  TRAININGPU epoch loop      (Sec. 3.1)
  *   Alg. 4  MULTIEDGECOLLAPSE          (Sec. 4)
  *   Sec. 3  EXPANDEMBEDDING (copy projection), epoch split, lr decay
- *   Sec. 3.3 random-walk positive sampling (GOSHW)
+ *   Sec. 3.2 random-walk positive sampling (GOSHW)
  *   Sec. 6.1 link-prediction AUC protocol
  * Where the paper is silent the reading used is written beside the code.
  *
@@ -406,7 +406,7 @@ double orc_auc(int64_t npos, const double *pos, int64_t nneg, const double *neg)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Random-walk sampling (Sec. 3.3, GOSHW): positive pairs from walks.        */
+/* Random-walk sampling (Sec. 3.2, GOSHW): positive pairs from walks.        */
 /* The paper gives neither the walk length l nor the distance g, nor how the */
 /* walks are drawn and shuffled.  Readings:                                  */
 /*  - each epoch starts one walk of l vertices at every vertex v; step t      */

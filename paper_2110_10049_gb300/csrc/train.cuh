@@ -42,7 +42,7 @@ struct TrainArgs {
     double *loss_partials;     // [gridDim.x] or null
     unsigned long long *n_updates;  // or null
     int *err;                  // device error word raised by a timed-out wait, or null
-    // walk pairs (Sec. 3.3): int32 (source, positive) per position, source -1
+    // walk pairs (Sec. 3.2): int32 (source, positive) per position, source -1
     // for a hole; src_end = positions; visited in walk_position order
     const int32_t *pairs;
     uint32_t walk_key;

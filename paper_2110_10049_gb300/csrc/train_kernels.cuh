@@ -178,7 +178,7 @@ constexpr int kTileDraws = 1, kTileRounds = 2;
  *               kept, only read stale;
  *   kModeDet    snapshot batch, changes written to R/C/keys (needs P >= k+1).
  */
-// Position i of an epoch's walk pairs visited i-th (Sec. 3.3, "shuffled"):
+// Position i of an epoch's walk pairs visited i-th (Sec. 3.2, "shuffled"):
 // a 4-round Feistel network on 2h-bit words (2^(2h) >= P) with round
 // function mix32(x ^ k_r) & (2^h - 1), k_r = mix32(key + r), repeated until the
 // value falls below P (cycle walking keeps it a bijection of [0, P)).

@@ -1,4 +1,4 @@
-// Random-walk positives (GOSH Sec. 3.3, the variant the paper calls GOSHW):
+// Random-walk positives (GOSH Sec. 3.2, the variant the paper calls GOSHW):
 // the host draws the walks and their pairs, the GPU applies Alg. 1 to each
 // pair with k uniform negatives.
 //

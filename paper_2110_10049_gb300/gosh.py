@@ -368,7 +368,7 @@ def gosh_train_level_large(rowptr, col, M, level, epochs, params: gosh_params, s
 
 
 def gosh_train_level_walks(rowptr, col, M, level, epochs, params: gosh_params, n_updates=None, stream=None):
-    """Random-walk positives (Sec. 3.3) on a host CSR (numpy) and a device M
+    """Random-walk positives (Sec. 3.2) on a host CSR (numpy) and a device M
     (torch, updated in place).  Returns the stats dict."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)

@@ -1,4 +1,4 @@
-"""Random-walk positives (Sec. 3.3) through the C ABI against the oracle.
+"""Random-walk positives (Sec. 3.2) through the C ABI against the oracle.
 
 - Graphs whose epochs have at most 32 pair positions, trained with 32 lanes
   per source (FP32, d = 128), run in one warp one pair at a time in the

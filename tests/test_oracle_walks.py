@@ -1,4 +1,4 @@
-"""Oracle of random-walk sampling (Sec. 3.3), pinned to properties the
+"""Oracle of random-walk sampling (Sec. 3.2), pinned to properties the
 definition fixes independently of the code:
 
 - consecutive walk vertices are graph edges, and every pair lies within graph

@@ -1,4 +1,4 @@
-"""The library's host side of random-walk sampling (Sec. 3.3) against the
+"""The library's host side of random-walk sampling (Sec. 3.2) against the
 oracle, on the CPU (no device involved): the pair table the walk entry point
 sends to the device and the order in which the device visits it are the
 oracle's, bit for bit, for graphs with isolated vertices, dead ends, stars
