@@ -13,8 +13,8 @@ Parity pins for every function are in ``tests/test_oracle_*.py``.
 Parity unpinned (what the GPU path is judged by instead): lock-free training
 beyond the single-warp case, whose update order is not reproducible
 (link-prediction AUC against ``train_sequential``); LargeGraphGPU beyond one
-part, which reorders the updates and has no oracle of its own (AUC against
-the resident step); the learned projection's training trajectory (the
+part on the device, whose part-pair kernels may overlap on two streams
+(AUC against the resident step; ``train_large`` is the sequential schedule); the learned projection's training trajectory (the
 gradients are pinned; the trained network is judged by its AUC gain).
 """
 from __future__ import annotations
@@ -75,6 +75,8 @@ def lib():
             "orc_walk_perm_key": (C.c_uint32, [u64, u64, i32, i32]),
             "orc_walk_perm": (u64, [u64, u64, C.c_uint32]),
             "orc_train_walks": (None, [i64, vp, vp, vp, i32, i32, i32, i32, f64, f64, u64, u64, i32, i32,
+                                       vp, vp]),
+            "orc_train_large": (None, [i64, vp, vp, vp, i32, i32, i32, i32, f64, f64, u64, u64, i32, i32,
                                        vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -181,6 +183,20 @@ def train_walks(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, l, g, grap
     lib().orc_train_walks(len(rowptr) - 1, _p(rowptr), _p(col), _p(M), M.shape[1], k, level, epochs, lr,
                           lr_floor, seed, graph, l, g, _p(loss), _p(nup))
     return loss[:epochs], int(nup[0])
+
+
+def train_large(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, K, B, graph=0):
+    """LargeGraphGPU (Sec. 5) run sequentially on M (float64, in place):
+    rounds of part pairs, B positives per source per pair from the opposite
+    part, tiles of 32 sources claiming a global positive budget of e*|V|.
+    Returns (n_updates, n_positives)."""
+    rowptr, col = _csr(rowptr, col)
+    assert M.dtype == np.float64 and M.flags.c_contiguous
+    nup = np.zeros(1, dtype=np.int64)
+    npos = np.zeros(1, dtype=np.int64)
+    lib().orc_train_large(len(rowptr) - 1, _p(rowptr), _p(col), _p(M), M.shape[1], k, level, epochs, lr, lr_floor,
+                          seed, graph, K, B, _p(nup), _p(npos))
+    return int(nup[0]), int(npos[0])
 
 
 def train_deterministic(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, m, graph=0):

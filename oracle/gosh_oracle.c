@@ -23,7 +23,9 @@
  * Parity unpinned: lock-free (Hogwild) training beyond one warp with one
  * source per round, whose update order is not reproducible, is compared with
  * orc_train_sequential only through link-prediction AUC; LargeGraphGPU beyond
- * one part has no function here and is compared with the resident step.
+ * one part (orc_train_large) is pinned here on the CPU, but the device runs
+ * the kernels of part pairs on two streams that may overlap, so the GPU path
+ * is compared with the resident step through AUC.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -556,4 +558,121 @@ void orc_train_walks(int64_t n, const int64_t *rowptr, const int32_t *col, doubl
     }
     free(pairs);
     if (n_updates) *n_updates = applied;
+}
+
+/* ------------------------------------------------------------------------ */
+/* LargeGraphGPU (Sec. 5), run sequentially.  Readings (the section gives    */
+/* the pair schedule and the sampling rule, not the streams):                */
+/*  - V is cut into K contiguous parts, part i = [floor(n i/K), floor(n(i+1)/K));*/
+/*  - rounds r = 0 .. ceil(e/B)-1; each round visits the part pairs (a, b),   */
+/*    a >= b, in row-major lower-triangle order (Sec. 5.1);                  */
+/*  - in pair (a, b) the sources are the vertices of V^a, then (a != b) those */
+/*    of V^b; a source u draws B positives uniformly from its neighbours in  */
+/*    the opposite part, each followed by k negatives uniform over the        */
+/*    opposite part (a negative equal to u is skipped when a == b); positive */
+/*    j of round r uses Philox block (u, blk, level<<32 | (r*B+j), tag) with */
+/*    tag = TAG_SAMPLE for K = 1, else 3 | ((a*K+b) << 8), word 0 for the     */
+/*    positive and words 1..k for the negatives, and the rate                 */
+/*    lr * max(1 - (r*B+j)/e, lr_floor);                                      */
+/*  - a global count of positives stops at e*|V|: sources are taken in tiles */
+/*    of 32; a tile's sources claim their positives in order, and a slot     */
+/*    group j of a source is dropped (positive and negatives) once the       */
+/*    source's claimed positives before it plus j reach what the tile may    */
+/*    still take.  A source without a neighbour in the opposite part claims  */
+/*    none (its negatives still count against the tile's limit).             */
+/* ------------------------------------------------------------------------ */
+enum { TAG_LARGE = 3 };
+
+void orc_train_large(int64_t n, const int64_t *rowptr, const int32_t *col, double *M, int d, int k, int level,
+                     int epochs, double lr, double lr_floor, uint64_t seed, uint64_t graph, int K, int B,
+                     int64_t *n_updates, int64_t *n_positives) {
+    uint64_t key[2] = {seed, graph};
+    const int rounds = (epochs + B - 1) / B;
+    const int ns = B * (k + 1);
+    const uint64_t cap = (uint64_t)epochs * (uint64_t)n;
+    uint64_t counter = 0;
+    int64_t applied = 0;
+    int64_t *start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K + 1));
+    for (int i = 0; i <= K; ++i) start[i] = n * i / K;
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * 32 * (size_t)ns);
+    double *lrs = (double *)malloc(sizeof(double) * 32 * (size_t)B);
+    int *npos = (int *)malloc(sizeof(int) * 32);
+    for (int r = 0; r < rounds; ++r) {
+        for (int a = 0; a < K; ++a) {
+            for (int b = 0; b <= a; ++b) {
+                const int same = a == b;
+                const uint64_t tag = K == 1 ? (uint64_t)TAG_SAMPLE : ((uint64_t)TAG_LARGE | ((uint64_t)(a * K + b) << 8));
+                const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
+                const int64_t nsrc = na + (same ? 0 : nb);
+                for (int64_t s0 = 0; s0 < nsrc; s0 += 32) {
+                    const int cnt_t = (int)(nsrc - s0 < 32 ? nsrc - s0 : 32);
+                    int tile_pos = 0;
+                    /* draws of the tile's sources */
+                    for (int q = 0; q < cnt_t; ++q) {
+                        const int64_t s = s0 + q;
+                        const int sideA = s < na;
+                        const int64_t u = sideA ? s : s - na;
+                        const int64_t own0 = sideA ? start[a] : start[b];
+                        const int64_t opp0 = sideA ? start[b] : start[a], opp1 = sideA ? start[b + 1] : start[a + 1];
+                        const int64_t ug = own0 + u;
+                        /* neighbours of ug inside the opposite part: a sorted sub-range of its row */
+                        int64_t lo = rowptr[ug], hi = rowptr[ug + 1];
+                        while (lo < hi && col[lo] < opp0) ++lo;
+                        int64_t e = lo;
+                        while (e < hi && col[e] < opp1) ++e;
+                        const int64_t cnt = e - lo;
+                        for (int j = 0; j < B; ++j) {
+                            const uint32_t t = (uint32_t)(r * B + j);
+                            uint64_t w[64];
+                            for (int blk = 0; blk * 4 < k + 1; ++blk) {
+                                uint64_t ctr[4] = {(uint64_t)ug, (uint64_t)blk, ((uint64_t)(uint32_t)level << 32) | t, tag};
+                                orc_philox4x64(ctr, key, w + 4 * blk);
+                            }
+                            for (int m = 0; m <= k; ++m) {
+                                int32_t id;
+                                if (m == 0) {
+                                    id = cnt > 0 ? (int32_t)(col[lo + (int64_t)uniform_below(w[0], (uint64_t)cnt)] - opp0) : -1;
+                                } else {
+                                    const int64_t x = (int64_t)uniform_below(w[m], (uint64_t)(opp1 - opp0));
+                                    id = (same && x == u) ? -1 : (int32_t)x;
+                                }
+                                ids[q * ns + j * (k + 1) + m] = id;
+                            }
+                            lrs[q * B + j] = orc_epoch_lr(lr, lr_floor, (int)t, epochs);
+                        }
+                        npos[q] = cnt > 0 ? B : 0;
+                        tile_pos += npos[q];
+                    }
+                    /* the tile's share of the global positive count */
+                    const uint64_t old = counter;
+                    counter += (uint64_t)tile_pos;
+                    const int64_t allowed = old >= cap ? 0 : (int64_t)(cap - old < (uint64_t)tile_pos ? cap - old : (uint64_t)tile_pos);
+                    /* updates, source by source */
+                    int first = 0;
+                    for (int q = 0; q < cnt_t; ++q) {
+                        const int64_t s = s0 + q;
+                        const int sideA = s < na;
+                        const int64_t u = sideA ? s : s - na;
+                        const int64_t ug = (sideA ? start[a] : start[b]) + u;
+                        const int64_t opp0 = sideA ? start[b] : start[a];
+                        for (int slot = 0; slot < ns; ++slot) {
+                            const int jj = slot / (k + 1);
+                            const int32_t id = ids[q * ns + slot];
+                            if (id < 0 || first + jj >= allowed) continue;
+                            const int bpos = slot % (k + 1) == 0;
+                            orc_update_embed(M + ug * d, M + (opp0 + id) * d, d, bpos, lrs[q * B + jj]);
+                            ++applied;
+                        }
+                        first += npos[q];
+                    }
+                }
+            }
+        }
+    }
+    free(start);
+    free(ids);
+    free(lrs);
+    free(npos);
+    if (n_updates) *n_updates = applied;
+    if (n_positives) *n_positives = (int64_t)(counter < cap ? counter : cap);
 }
