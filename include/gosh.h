@@ -107,6 +107,11 @@ typedef struct gosh_params {
                                of 32/lanes_per_row); 0 = by level size (8 / 16 / 32) */
     int walk_length;        /* gosh_train_level_walks: vertices per random walk, l (default 8) */
     int walk_window;        /* gosh_train_level_walks: pairs within distance g (default 3) */
+    int large_serial;       /* LargeGraphGPU: 1 runs the part-pair kernels one after another on
+                               one stream (a reproducible kernel order: a pair with at most 32
+                               sources and one source per round then follows the sequential
+                               schedule exactly); 0 (default) alternates two streams so that
+                               kernels of independent pairs overlap */
 } gosh_params;
 
 typedef struct gosh_walk_stats {
@@ -293,7 +298,8 @@ gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int level, int 
  * params->p_gpu device bins (farthest-next-use eviction), edge blocks
  * (built once on host threads) through params->s_gpu bins, all
  * asynchronously on per-bin streams with cudaEvent dependencies; kernels
- * alternate over two streams and may overlap (lock-free, as in the paper).
+ * alternate over two streams and may overlap (lock-free, as in the paper),
+ * or run one after another on one stream when params->large_serial is 1.
  * g: HOST CSR; M: HOST n x d (FP32 or BF16; pinned in place if pageable),
  * updated in place.  Lock-free mode only.  stats: host pointer or NULL.
  * GOSH_ERR_BUDGET if K parts do not fit the budget.  Synchronous.

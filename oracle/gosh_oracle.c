@@ -24,8 +24,9 @@
  * source per round, whose update order is not reproducible, is compared with
  * orc_train_sequential only through link-prediction AUC; LargeGraphGPU beyond
  * one part (orc_train_large) is pinned here on the CPU, but the device runs
- * the kernels of part pairs on two streams that may overlap, so the GPU path
- * is compared with the resident step through AUC.
+ * the kernels of part pairs on two streams that may overlap (one stream only
+ * on request), so the GPU path is compared with the resident step through
+ * AUC.
  */
 #include <stdint.h>
 #include <stdlib.h>

@@ -406,6 +406,7 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->vertices_per_warp = 0;
     p->walk_length = 8;
     p->walk_window = 3;
+    p->large_serial = 0;
     return GOSH_OK;
 }
 

@@ -666,7 +666,7 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
         block_bytes += blk.bytes;
         cudaEvent_t e_ready = new_event(estr[eb]);
         // KT
-        cudaStream_t ks = kstr[i % 2];
+        cudaStream_t ks = kstr[p->large_serial ? 0 : i % 2];
         cudaStreamWaitEvent(ks, bin_ready[ba], 0);
         cudaStreamWaitEvent(ks, bin_ready[bb], 0);
         cudaStreamWaitEvent(ks, e_ready, 0);

@@ -43,7 +43,7 @@ class gosh_params(C.Structure):
                 ("mlp_epochs", C.c_int), ("mlp_lr", C.c_double), ("mlp_batch", C.c_int),
                 ("mlp_max_rows", C.c_int64), ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int),
                 ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int),
-                ("walk_length", C.c_int), ("walk_window", C.c_int)]
+                ("walk_length", C.c_int), ("walk_window", C.c_int), ("large_serial", C.c_int)]
 
 
 class gosh_walk_stats(C.Structure):
