@@ -108,10 +108,11 @@ typedef struct gosh_params {
     int walk_length;        /* gosh_train_level_walks: vertices per random walk, l (default 8) */
     int walk_window;        /* gosh_train_level_walks: pairs within distance g (default 3) */
     int large_serial;       /* LargeGraphGPU: 1 runs the part-pair kernels one after another on
-                               one stream (a reproducible kernel order: a pair with at most 32
-                               sources and one source per round then follows the sequential
-                               schedule exactly); 0 (default) alternates two streams so that
-                               kernels of independent pairs overlap */
+                               one stream (a reproducible kernel order: with FP32 d = 128, whose
+                               kernel gives each source a whole warp, a part pair of at most 32
+                               sources is then trained exactly in the sequential order); 0
+                               (default) alternates two streams so that kernels of independent
+                               pairs overlap */
 } gosh_params;
 
 typedef struct gosh_walk_stats {

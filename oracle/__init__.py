@@ -12,10 +12,12 @@ Parity pins for every function are in ``tests/test_oracle_*.py``.
 
 Parity unpinned (what the GPU path is judged by instead): lock-free training
 beyond the single-warp case, whose update order is not reproducible
-(link-prediction AUC against ``train_sequential``); LargeGraphGPU beyond one
-part on the device, whose part-pair kernels may overlap on two streams
-(AUC against the resident step; ``train_large`` is the sequential schedule); the learned projection's training trajectory (the
-gradients are pinned; the trained network is judged by its AUC gain).
+(link-prediction AUC against ``train_sequential``); LargeGraphGPU on the
+device with its default schedule, whose part-pair kernels may overlap on two
+streams (AUC against the resident step; with the kernels on one stream,
+graphs whose part pairs fit one tile are compared with ``train_large``, the
+sequential schedule, to 1e-5); the learned projection's training trajectory
+(the gradients are pinned; the trained network is judged by its AUC gain).
 """
 from __future__ import annotations
 

@@ -23,10 +23,11 @@
  * Parity unpinned: lock-free (Hogwild) training beyond one warp with one
  * source per round, whose update order is not reproducible, is compared with
  * orc_train_sequential only through link-prediction AUC; LargeGraphGPU beyond
- * one part (orc_train_large) is pinned here on the CPU, but the device runs
- * the kernels of part pairs on two streams that may overlap (one stream only
- * on request), so the GPU path is compared with the resident step through
- * AUC.
+ * one part (orc_train_large) is pinned here on the CPU; the device runs the
+ * kernels of part pairs on two streams that may overlap, so its default
+ * schedule is compared with the resident step through AUC (with the kernels
+ * on one stream, graphs whose part pairs fit one tile are compared with
+ * orc_train_large itself).
  */
 #include <stdint.h>
 #include <stdlib.h>
