@@ -347,8 +347,10 @@ gosh_status gosh_walk_order(int64_t positions, int level, int epoch, uint64_t se
 /* Host-only simulation of the LargeGraphGPU part-bin schedule (no GPU use):
  * for `rounds` rounds over K parts and p_gpu bins, writes for every kernel i
  * its pair (pairs_out[2i], pairs_out[2i+1]) = (a, b) and the loads done
- * before it (loads_out[2i], loads_out[2i+1]: part * 1000 + bin, or -1).
- * Returns the kernel count, or -1 if it exceeds cap_tasks. */
+ * before it (loads_out[2i], loads_out[2i+1]: part * 1000 + bin, or -1),
+ * choosing bins exactly as gosh_train_level_large does.  Returns the kernel
+ * count, -1 if it exceeds cap_tasks, or -2 for invalid arguments (K < 1,
+ * p_gpu outside [2, 999], rounds < 0, NULL outputs). */
 int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int *loads_out, int cap_tasks);
 
 /* Stochastic rounding of FP32 values to a 16-bit table type (dtype GOSH_BF16

@@ -278,12 +278,6 @@ struct Block {
     char *base = nullptr;  // inside the pinned region: rp_ab | col_ab | rp_ba | col_ba
 };
 
-struct Sched {
-    int K, PB, SB;
-    std::vector<int64_t> start;                 // K+1
-    std::vector<std::pair<int, int>> order;     // one round
-};
-
 }  // namespace
 
 // Inside-out order of one round: (0,0),(1,0),(1,1),(2,0),(2,1),(2,2),...
@@ -291,6 +285,38 @@ void large_pair_order(int K, std::vector<std::pair<int, int>> &order) {
     order.clear();
     for (int a = 0; a < K; ++a)
         for (int b = 0; b <= a; ++b) order.push_back({a, b});
+}
+
+// The bin that holds part x for kernel i of seq: the bin already holding it
+// (*load = false), else (*load = true) an empty bin, else the bin whose part
+// is next used farthest ahead in seq.  A bin holding keep0 or keep1 (the
+// parts of kernel i) is never chosen, so two bins always suffice.
+int large_bin_for(const std::vector<int> &bin_part, const std::vector<std::pair<int, int>> &seq, size_t i, int x,
+                  int keep0, int keep1, bool *load) {
+    const int nb = (int)bin_part.size();
+    for (int bi = 0; bi < nb; ++bi)
+        if (bin_part[bi] == x) {
+            *load = false;
+            return bi;
+        }
+    *load = true;
+    int victim = -1;
+    size_t far = 0;
+    for (int bi = 0; bi < nb; ++bi) {
+        if (bin_part[bi] == keep0 || bin_part[bi] == keep1) continue;
+        if (bin_part[bi] < 0) return bi;
+        size_t nxt = seq.size() + 1;
+        for (size_t j = i + 1; j < seq.size(); ++j)
+            if (seq[j].first == bin_part[bi] || seq[j].second == bin_part[bi]) {
+                nxt = j;
+                break;
+            }
+        if (victim < 0 || nxt > far) {
+            victim = bi;
+            far = nxt;
+        }
+    }
+    return victim;
 }
 
 }  // namespace gosh
@@ -303,33 +329,26 @@ extern "C" {
 int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int *loads_out, int cap_tasks) {
     // Host-only simulation of the submatrix-bin schedule: for each kernel of
     // `rounds` rounds, the pair (a, b) and the part loaded into a bin before
-    // it (or -1 entries); returns the number of kernels (or -1 if cap_tasks is
-    // too small).  Eviction: farthest next use.
+    // it (or -1 entries), with the bin choice of gosh_train_level_large
+    // (large_bin_for: farthest next use).
+    if (K < 1 || p_gpu < 2 || p_gpu > 999 || rounds < 0 || cap_tasks < 0 || (cap_tasks > 0 && (!pairs_out || !loads_out)))
+        return -2;
+    if ((int64_t)rounds * K * (K + 1) / 2 > cap_tasks) return -1;
     std::vector<std::pair<int, int>> order;
     large_pair_order(K, order);
     std::vector<std::pair<int, int>> seq;
     for (int r = 0; r < rounds; ++r)
         for (auto &pr : order) seq.push_back(pr);
-    if ((int)seq.size() > cap_tasks) return -1;
     std::vector<int> bin(p_gpu, -1);
     for (size_t i = 0; i < seq.size(); ++i) {
         const int need[2] = {seq[i].first, seq[i].second};
         int loads[2] = {-1, -1};
         for (int q = 0; q < 2; ++q) {
-            const int x = need[q];
-            if (std::find(bin.begin(), bin.end(), x) != bin.end()) continue;
-            int victim = -1;
-            size_t far = 0;
-            for (int bi = 0; bi < p_gpu; ++bi) {
-                if (bin[bi] == need[0] || bin[bi] == need[1]) continue;
-                if (bin[bi] < 0) { victim = bi; break; }
-                size_t nxt = seq.size() + 1;
-                for (size_t j = i + 1; j < seq.size(); ++j)
-                    if (seq[j].first == bin[bi] || seq[j].second == bin[bi]) { nxt = j; break; }
-                if (victim < 0 || nxt > far) { victim = bi; far = nxt; }
-            }
-            bin[victim] = x;
-            loads[q] = x * 1000 + victim;  // part * 1000 + bin
+            bool load = false;
+            const int victim = large_bin_for(bin, seq, i, need[q], need[0], need[1], &load);
+            if (!load) continue;
+            bin[victim] = need[q];
+            loads[q] = need[q] * 1000 + victim;  // part * 1000 + bin
         }
         pairs_out[2 * i] = seq[i].first;
         pairs_out[2 * i + 1] = seq[i].second;
@@ -611,27 +630,9 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     char *hM = static_cast<char *>(M);
 
     auto ensure = [&](int x, int keep0, int keep1, size_t i) -> int {
-        for (int bi = 0; bi < p->p_gpu; ++bi)
-            if (bin_part[bi] == x) return bi;
-        int victim = -1;
-        size_t far = 0;
-        for (int bi = 0; bi < p->p_gpu; ++bi) {
-            if (bin_part[bi] == keep0 || bin_part[bi] == keep1) continue;
-            if (bin_part[bi] < 0) {
-                victim = bi;
-                break;
-            }
-            size_t nxt = seq.size() + 1;
-            for (size_t j = i + 1; j < seq.size(); ++j)
-                if (seq[j].first == bin_part[bi] || seq[j].second == bin_part[bi]) {
-                    nxt = j;
-                    break;
-                }
-            if (victim < 0 || nxt > far) {
-                victim = bi;
-                far = nxt;
-            }
-        }
+        bool load = false;
+        const int victim = large_bin_for(bin_part, seq, i, x, keep0, keep1, &load);
+        if (!load) return victim;
         cudaStream_t st = pstr[victim];
         for (cudaEvent_t e : bin_users[victim]) cudaStreamWaitEvent(st, e, 0);
         bin_users[victim].clear();

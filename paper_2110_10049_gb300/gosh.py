@@ -410,6 +410,8 @@ def gosh_large_plan(n, K, p_gpu, rounds):
     pairs = np.zeros((max(cap, 1), 2), dtype=np.int32)
     loads = np.zeros((max(cap, 1), 2), dtype=np.int32)
     cnt = lib().gosh_large_plan(n, K, p_gpu, rounds, pairs.ctypes.data, loads.ctypes.data, cap)
+    if cnt == -2:
+        raise GoshError("gosh_large_plan", 1, "need K >= 1, 2 <= p_gpu <= 999, rounds >= 0")
     if cnt < 0:
         raise GoshError("gosh_large_plan", 1, "capacity")
     return pairs[:cnt], loads[:cnt]

@@ -36,3 +36,20 @@ def test_schedule_invariants(g, K, bins, rounds):
                 resident[bin_] = part
         assert a in resident.values() and b in resident.values()
         assert len(resident) <= bins
+
+
+@pytest.mark.parametrize("K,bins,rounds", [(0, 3, 1), (4, 1, 1), (4, 0, 1), (3, 1000, 1), (3, 3, -1)])
+def test_invalid_arguments_rejected(g, K, bins, rounds):
+    # one bin cannot hold both parts of a pair: rejected, not simulated
+    with pytest.raises(g.GoshError):
+        g.gosh_large_plan(1000, K, bins, rounds)
+    cnt = g.lib().gosh_large_plan(1000, K, bins, rounds, None, None, 0)
+    assert cnt == -2
+
+
+def test_capacity_checked_before_writing(g):
+    import numpy as np
+    pairs = np.full((3, 2), -7, dtype=np.int32)
+    loads = np.full((3, 2), -7, dtype=np.int32)
+    assert g.lib().gosh_large_plan(1000, 3, 2, 1, pairs.ctypes.data, loads.ctypes.data, 3) == -1
+    assert (pairs == -7).all() and (loads == -7).all()
