@@ -77,7 +77,8 @@ typedef struct gosh_params {
     int lanes_per_row;      /* lanes that share one source row; 0 = automatic */
     int samples_per_pass;   /* sample rows gathered at once per source; 0 = automatic */
     int64_t device_budget_bytes; /* 0 = unlimited */
-    int validate;           /* 1: check the CSR before use (costs one pass) */
+    int validate;           /* 1: check the CSR before use (costs one pass; host CSRs of
+                               gosh_train_level_large and _walks are checked on the host) */
     int plain_stores;       /* GOSH_HOGWILD: 0 (default) applies every row change as an atomic
                                vector addition at L2 (16-bit tables: the stochastically
                                rounded new row minus the row read, rounded to nearest; without
@@ -335,7 +336,9 @@ gosh_status gosh_train_level_walks(const gosh_csr *g, void *M, int level, int ep
 /* The pair table gosh_train_level_walks uses for one epoch, drawn on the
  * calling thread (no device involved): pairs = host int32[|V| * W * 2] of
  * (source, positive) per position, -1 for holes, W = pairs of a full walk
- * (sum over i < l-1 of min(g, l-1-i)).  g: host CSR. */
+ * (sum over i < l-1 of min(g, l-1-i)).  g: host CSR, checked first (rowptr
+ * from 0 and non-decreasing, columns in range, rows strictly ascending, no
+ * self-loops; GOSH_ERR_INVALID_ARG otherwise). */
 gosh_status gosh_walk_pairs(const gosh_csr *g, int walk_length, int walk_window, int level, int epoch,
                             uint64_t seed, uint64_t graph_id, int32_t *pairs);
 

@@ -1,6 +1,7 @@
 // The C ABI of libgosh (include/gosh.h): argument checks, the small kernels
 // around the training step (initialisation, copy projection, CSR validation,
 // pair scores and AUC) and the end-to-end driver of Alg. 2.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <mutex>
@@ -369,6 +370,27 @@ bool is_device_ptr(const void *p) {
 }
 
 }  // namespace
+
+gosh_status check_host_csr(const int64_t *rowptr, const int32_t *col, int64_t n, bool symmetric) {
+    GOSH_CHECK_ARG(rowptr != nullptr && col != nullptr && n >= 1, "csr pointers are NULL or n < 1");
+    GOSH_CHECK_ARG(rowptr[0] == 0, "rowptr[0] must be 0");
+    for (int64_t v = 0; v < n; ++v)
+        GOSH_CHECK_ARG(rowptr[v + 1] >= rowptr[v], "rowptr decreases at row %lld", (long long)v);
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        for (int64_t q = b; q < e; ++q) {
+            const int32_t u = col[q];
+            GOSH_CHECK_ARG(u >= 0 && u < n, "row %lld: column %d out of range", (long long)v, (int)u);
+            GOSH_CHECK_ARG(u != v, "row %lld: self-loop", (long long)v);
+            GOSH_CHECK_ARG(q == b || col[q - 1] < u, "row %lld: columns not strictly ascending", (long long)v);
+            if (symmetric)
+                GOSH_CHECK_ARG(std::binary_search(col + rowptr[u], col + rowptr[u + 1], (int32_t)v),
+                               "row %lld: entry %d has no reverse entry", (long long)v, (int)u);
+        }
+    }
+    return GOSH_OK;
+}
+
 }  // namespace gosh
 
 using namespace gosh;

@@ -339,6 +339,13 @@ template <> struct Store<__half> {
 // Device word raised by bounded waits that gave up (capi.cu); read by gosh_device_check.
 int *device_error_word();
 
+// Content check of a HOST CSR, the host counterpart of gosh_validate_csr:
+// rowptr starts at 0 and never decreases, every column lies in [0, n), rows
+// are strictly ascending and hold no self-loop, and (if `symmetric`) every
+// (v, u) has its (u, v).  Sets the error line and returns
+// GOSH_ERR_INVALID_ARG naming the first bad row.
+gosh_status check_host_csr(const int64_t *rowptr, const int32_t *col, int64_t n, bool symmetric);
+
 // ---------------------------------------------------------------------------
 // Device primitives (primitives.cu).
 // ---------------------------------------------------------------------------

@@ -368,9 +368,12 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     GOSH_CHECK_ARG(p->mode == GOSH_HOGWILD, "LargeGraphGPU is lock-free (GOSH_HOGWILD)");
     GOSH_CHECK_ARG(p->B >= 1 && p->B * (p->k + 1) <= kMaxSlots && p->B <= 8, "need 1 <= B <= 8 and B*(k+1) <= %d",
                    kMaxSlots);
+    GOSH_CHECK_ARG(p->k >= 0, "k must be >= 0");
     GOSH_CHECK_ARG(p->p_gpu >= 2 && p->s_gpu >= 1, "need P_GPU >= 2 and S_GPU >= 1");
     const PairLaunch launch = pick_pair_kernel(p->dtype, p->d);
     GOSH_CHECK_ARG(launch != nullptr, "LargeGraphGPU serves FP32 / BF16 with d in {32, 64, 128}");
+    GOSH_CHECK_ARG(g->rowptr && g->col, "csr pointers are NULL");
+    if (p->validate) GOSH_TRY(check_host_csr(g->rowptr, g->col, g->n, false));
     const auto t_start = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;

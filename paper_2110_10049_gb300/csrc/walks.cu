@@ -217,6 +217,7 @@ gosh_status gosh_train_level_walks(const gosh_csr *g, void *M, int level, int ep
         rowptr = hrp.data();
         col = hcol.data();
     }
+    if (p->validate) GOSH_TRY(check_host_csr(rowptr, col, n, false));
 
     const int64_t W = walk_positions_per_walk(l, gw);
     const int64_t P = n * W;  // positions per epoch
@@ -334,6 +335,7 @@ gosh_status gosh_walk_pairs(const gosh_csr *g, int walk_length, int walk_window,
     GOSH_CHECK_ARG(g->n >= 1 && g->n < (int64_t(1) << 31), "bad n");
     GOSH_CHECK_ARG(walk_length >= 2 && walk_length <= 256 && walk_window >= 1,
                    "need 2 <= walk_length <= 256 and walk_window >= 1");
+    GOSH_TRY(check_host_csr(g->rowptr, g->col, g->n, false));
     walk_fill(g->rowptr, g->col, 0, g->n, walk_length, walk_window, walk_positions_per_walk(walk_length, walk_window),
               level, epoch, seed, graph_id, pairs);
     return GOSH_OK;

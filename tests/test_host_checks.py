@@ -1,0 +1,68 @@
+"""Host-side argument checks of the entry points that take a HOST CSR, run on
+the CPU (each call returns before any device work): gosh_walk_pairs always
+checks the CSR's content, gosh_train_level_large and gosh_train_level_walks
+when params.validate is set; every kind of bad CSR is rejected with
+GOSH_ERR_INVALID_ARG and a message naming the fault."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2110_10049_gb300 import build, gosh as g
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+
+
+def bad_csrs():
+    gr = synth.random_graph(12, 0.4, 3)
+    rp, col = gr.rowptr.copy(), gr.col.copy()
+    v = int(np.argmax(np.diff(rp)))  # a row with at least two entries
+    assert rp[v + 1] - rp[v] >= 2
+    out = []
+    r = rp.copy(); r[0] = 1; out.append(("rowptr[0]", r, col))
+    r = rp.copy(); r[v + 1] = r[v] - 1; out.append(("decreases", r, col))
+    c = col.copy(); c[rp[v]] = 12; out.append(("out of range", rp, c))
+    c = col.copy(); c[rp[v]] = -3; out.append(("out of range", rp, c))
+    c = col.copy(); c[rp[v]] = v; c[rp[v]:rp[v + 1]].sort(); out.append(("self-loop", rp, c))
+    c = col.copy(); c[rp[v]], c[rp[v] + 1] = c[rp[v] + 1], c[rp[v]]; out.append(("ascending", rp, c))
+    c = col.copy(); c[rp[v] + 1] = c[rp[v]]; out.append(("ascending", rp, c))
+    return gr, out
+
+
+def test_walk_pairs_rejects_bad_csrs():
+    gr, cases = bad_csrs()
+    g.gosh_walk_pairs(gr.rowptr, gr.col, 4, 2, 0, 0, 1)  # the good graph passes
+    for what, rp, col in cases:
+        with pytest.raises(g.GoshError) as e:
+            g.gosh_walk_pairs(rp, col, 4, 2, 0, 0, 1)
+        assert e.value.status == 1 and what in str(e.value), (what, str(e.value))
+
+
+def _csr(rp, col):
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    return g.gosh_csr(len(rp) - 1, rp.ctypes.data, col.ctypes.data, 0), (rp, col)
+
+
+@pytest.mark.parametrize("entry", ["large", "walks"])
+def test_validate_rejects_bad_host_csrs_before_device_work(entry):
+    gr, cases = bad_csrs()
+    L = g.lib()
+    M = np.zeros((gr.n, 32), dtype=np.float32)
+    p = g.default_params(d=32, k=3, validate=1, large_parts=2, p_gpu=2, s_gpu=1, B=1)
+    for what, rp, col in cases:
+        cg, keep = _csr(rp, col)
+        if entry == "large":
+            st = g.gosh_large_stats()
+            rc = L.gosh_train_level_large(C.byref(cg), C.c_void_p(M.ctypes.data), 0, 3, C.byref(p), None,
+                                          C.byref(st))
+        else:
+            st = g.gosh_walk_stats()
+            rc = L.gosh_train_level_walks(C.byref(cg), C.c_void_p(M.ctypes.data), 0, 3, C.byref(p), None, None,
+                                          C.byref(st))
+        assert rc == 1, (what, rc)
+        assert what in L.gosh_last_error().decode(), (what, L.gosh_last_error())
