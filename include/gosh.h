@@ -172,6 +172,12 @@ gosh_status gosh_device_check(void *stream);
  * (all threads, all devices).  A diagnostic for profiling and benchmarking. */
 unsigned long long gosh_kernel_launches(void);
 
+/* LargeGraphGPU and walk training keep their pinned host buffers (edge
+ * blocks, walk pair tables) across calls, since pinning costs far more than
+ * filling.  This frees those not held by a running call and returns the
+ * bytes freed; later calls pin again.  No device work. */
+unsigned long long gosh_release_host_buffers(void);
+
 /* Checks a device CSR against the layout above (row pointer monotone,
  * neighbour ids in range, ascending, no self-loop, symmetric).  Synchronous.
  * Returns GOSH_ERR_INVALID_ARG with a message naming the first violation. */

@@ -436,6 +436,10 @@ const char *gosh_last_error(void) { return g_error; }
 
 unsigned long long gosh_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+unsigned long long gosh_release_host_buffers(void) {
+    return (unsigned long long)(large_release_pinned() + walks_release_pinned());
+}
+
 gosh_status gosh_device_check(void *stream) {
     clear_error();
     cudaStream_t s = (cudaStream_t)stream;

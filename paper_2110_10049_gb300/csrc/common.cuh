@@ -346,6 +346,11 @@ int *device_error_word();
 // GOSH_ERR_INVALID_ARG naming the first bad row.
 gosh_status check_host_csr(const int64_t *rowptr, const int32_t *col, int64_t n, bool symmetric);
 
+// Free the idle pinned regions kept across calls by LargeGraphGPU (edge
+// blocks) and walk training (pair tables); each returns the bytes freed.
+size_t large_release_pinned();
+size_t walks_release_pinned();
+
 // ---------------------------------------------------------------------------
 // Device primitives (primitives.cu).
 // ---------------------------------------------------------------------------

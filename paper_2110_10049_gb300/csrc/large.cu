@@ -280,6 +280,8 @@ struct Block {
 
 }  // namespace
 
+size_t large_release_pinned() { return g_pinned.release(); }
+
 // Inside-out order of one round: (0,0),(1,0),(1,1),(2,0),(2,1),(2,2),...
 void large_pair_order(int K, std::vector<std::pair<int, int>> &order) {
     order.clear();

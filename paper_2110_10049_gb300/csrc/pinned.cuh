@@ -14,6 +14,16 @@ struct PinnedArena {
     char *ptr = nullptr;
     size_t cap = 0;
     bool busy = false;
+    // Frees the region unless a call holds it; returns the bytes freed.
+    size_t release() {
+        std::lock_guard<std::mutex> lock(mu);
+        if (busy || !ptr) return 0;
+        cudaFreeHost(ptr);
+        const size_t freed = cap;
+        ptr = nullptr;
+        cap = 0;
+        return freed;
+    }
 };
 
 struct PinnedLease {

@@ -176,6 +176,8 @@ int64_t walk_positions_per_walk(int l, int gw) {
 PinnedArena g_walk_pinned;
 
 }  // namespace
+
+size_t walks_release_pinned() { return g_walk_pinned.release(); }
 }  // namespace gosh
 
 using namespace gosh;

@@ -123,6 +123,8 @@ def lib() -> C.CDLL:
         L.gosh_mlp_feature_stride.argtypes = [C.c_int]
         L.gosh_kernel_launches.restype = C.c_ulonglong
         L.gosh_kernel_launches.argtypes = []
+        L.gosh_release_host_buffers.restype = C.c_ulonglong
+        L.gosh_release_host_buffers.argtypes = []
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
@@ -380,6 +382,12 @@ def gosh_train_level_walks(rowptr, col, M, level, epochs, params: gosh_params, n
                                                                   C.byref(params), _stream(stream),
                                                                   _ptr(n_updates), C.byref(st)))
     return {f: getattr(st, f) for f, _ in gosh_walk_stats._fields_}
+
+
+def gosh_release_host_buffers() -> int:
+    """Free the pinned host buffers kept across LargeGraphGPU and walk calls
+    (those no running call holds); returns the bytes freed."""
+    return int(lib().gosh_release_host_buffers())
 
 
 def gosh_walk_pairs(rowptr, col, walk_length, walk_window, level, epoch, seed, graph_id=0):

@@ -66,3 +66,9 @@ def test_validate_rejects_bad_host_csrs_before_device_work(entry):
                                           C.byref(st))
         assert rc == 1, (what, rc)
         assert what in L.gosh_last_error().decode(), (what, L.gosh_last_error())
+
+
+def test_release_host_buffers_without_any_held():
+    # nothing pinned in this process: nothing to free, no device involved
+    assert g.gosh_release_host_buffers() == 0
+    assert g.gosh_release_host_buffers() == 0
