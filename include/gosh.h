@@ -114,6 +114,11 @@ typedef struct gosh_params {
                                sources is then trained exactly in the sequential order); 0
                                (default) alternates two streams so that kernels of independent
                                pairs overlap */
+    int large_evict;        /* LargeGraphGPU part-bin choice when a part must come in: 0
+                               (default) the part next used farthest ahead (fewest copies); 1
+                               the same, but sparing the parts of the previous kernel while
+                               another bin is eligible, so that the copy overlaps that kernel
+                               (Sec. 5.2's example), at the cost of more copies */
 } gosh_params;
 
 typedef struct gosh_walk_stats {
@@ -354,13 +359,15 @@ gosh_status gosh_walk_order(int64_t positions, int level, int epoch, uint64_t se
                             int64_t *order);
 
 /* Host-only simulation of the LargeGraphGPU part-bin schedule (no GPU use):
- * for `rounds` rounds over K parts and p_gpu bins, writes for every kernel i
+ * for `rounds` rounds over K parts and p_gpu bins, with the bin choice
+ * `evict` (params->large_evict), writes for every kernel i
  * its pair (pairs_out[2i], pairs_out[2i+1]) = (a, b) and the loads done
  * before it (loads_out[2i], loads_out[2i+1]: part * 1000 + bin, or -1),
  * choosing bins exactly as gosh_train_level_large does.  Returns the kernel
  * count, -1 if it exceeds cap_tasks, or -2 for invalid arguments (K < 1,
- * p_gpu outside [2, 999], rounds < 0, NULL outputs). */
-int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int *loads_out, int cap_tasks);
+ * p_gpu outside [2, 999], rounds < 0, evict not 0 or 1, NULL outputs). */
+int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int evict, int *pairs_out, int *loads_out,
+                    int cap_tasks);
 
 /* Stochastic rounding of FP32 values to a 16-bit table type (dtype GOSH_BF16
  * or GOSH_F16), exactly as the training kernels round every value they write

@@ -429,6 +429,7 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->walk_length = 8;
     p->walk_window = 3;
     p->large_serial = 0;
+    p->large_evict = 0;
     return GOSH_OK;
 }
 

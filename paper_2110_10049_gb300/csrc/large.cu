@@ -291,10 +291,14 @@ void large_pair_order(int K, std::vector<std::pair<int, int>> &order) {
 
 // The bin that holds part x for kernel i of seq: the bin already holding it
 // (*load = false), else (*load = true) an empty bin, else the bin whose part
-// is next used farthest ahead in seq.  A bin holding keep0 or keep1 (the
-// parts of kernel i) is never chosen, so two bins always suffice.
+// is next used farthest ahead in seq.  A bin holding a part of kernel i is
+// never chosen, so two bins always suffice.  With spare_prev, bins holding a
+// part of kernel i-1 are passed over while another candidate exists: the
+// copy then need not wait for that kernel, which may still run (the overlap
+// Sec. 5.2 describes: with M^0, M^1, M^5 resident, M^2 replaces M^0 while
+// K_{5,1} runs), at the cost of more copies than the farthest-next-use rule.
 int large_bin_for(const std::vector<int> &bin_part, const std::vector<std::pair<int, int>> &seq, size_t i, int x,
-                  int keep0, int keep1, bool *load) {
+                  bool spare_prev, bool *load) {
     const int nb = (int)bin_part.size();
     for (int bi = 0; bi < nb; ++bi)
         if (bin_part[bi] == x) {
@@ -302,23 +306,30 @@ int large_bin_for(const std::vector<int> &bin_part, const std::vector<std::pair<
             return bi;
         }
     *load = true;
-    int victim = -1;
-    size_t far = 0;
-    for (int bi = 0; bi < nb; ++bi) {
-        if (bin_part[bi] == keep0 || bin_part[bi] == keep1) continue;
-        if (bin_part[bi] < 0) return bi;
-        size_t nxt = seq.size() + 1;
-        for (size_t j = i + 1; j < seq.size(); ++j)
-            if (seq[j].first == bin_part[bi] || seq[j].second == bin_part[bi]) {
-                nxt = j;
-                break;
+    const int keep0 = seq[i].first, keep1 = seq[i].second;
+    const int prev0 = i > 0 ? seq[i - 1].first : -1, prev1 = i > 0 ? seq[i - 1].second : -1;
+    for (int pass = spare_prev ? 0 : 1; pass < 2; ++pass) {
+        int victim = -1;
+        size_t far = 0;
+        for (int bi = 0; bi < nb; ++bi) {
+            const int part = bin_part[bi];
+            if (part == keep0 || part == keep1) continue;
+            if (part < 0) return bi;
+            if (pass == 0 && (part == prev0 || part == prev1)) continue;
+            size_t nxt = seq.size() + 1;
+            for (size_t j = i + 1; j < seq.size(); ++j)
+                if (seq[j].first == part || seq[j].second == part) {
+                    nxt = j;
+                    break;
+                }
+            if (victim < 0 || nxt > far) {
+                victim = bi;
+                far = nxt;
             }
-        if (victim < 0 || nxt > far) {
-            victim = bi;
-            far = nxt;
         }
+        if (victim >= 0) return victim;
     }
-    return victim;
+    return -1;
 }
 
 }  // namespace gosh
@@ -328,12 +339,14 @@ using namespace gosh;
 extern "C" {
 
 /* See include/gosh.h. */
-int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int *loads_out, int cap_tasks) {
+int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int evict, int *pairs_out, int *loads_out,
+                    int cap_tasks) {
     // Host-only simulation of the submatrix-bin schedule: for each kernel of
     // `rounds` rounds, the pair (a, b) and the part loaded into a bin before
     // it (or -1 entries), with the bin choice of gosh_train_level_large
     // (large_bin_for: farthest next use).
-    if (K < 1 || p_gpu < 2 || p_gpu > 999 || rounds < 0 || cap_tasks < 0 || (cap_tasks > 0 && (!pairs_out || !loads_out)))
+    if (K < 1 || p_gpu < 2 || p_gpu > 999 || rounds < 0 || (evict != 0 && evict != 1) || cap_tasks < 0 ||
+        (cap_tasks > 0 && (!pairs_out || !loads_out)))
         return -2;
     if ((int64_t)rounds * K * (K + 1) / 2 > cap_tasks) return -1;
     std::vector<std::pair<int, int>> order;
@@ -347,7 +360,7 @@ int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int *pairs_out, int
         int loads[2] = {-1, -1};
         for (int q = 0; q < 2; ++q) {
             bool load = false;
-            const int victim = large_bin_for(bin, seq, i, need[q], need[0], need[1], &load);
+            const int victim = large_bin_for(bin, seq, i, need[q], evict == 1, &load);
             if (!load) continue;
             bin[victim] = need[q];
             loads[q] = need[q] * 1000 + victim;  // part * 1000 + bin
@@ -372,6 +385,7 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
                    kMaxSlots);
     GOSH_CHECK_ARG(p->k >= 0, "k must be >= 0");
     GOSH_CHECK_ARG(p->p_gpu >= 2 && p->s_gpu >= 1, "need P_GPU >= 2 and S_GPU >= 1");
+    GOSH_CHECK_ARG(p->large_evict == 0 || p->large_evict == 1, "large_evict must be 0 or 1");
     const PairLaunch launch = pick_pair_kernel(p->dtype, p->d);
     GOSH_CHECK_ARG(launch != nullptr, "LargeGraphGPU serves FP32 / BF16 with d in {32, 64, 128}");
     GOSH_CHECK_ARG(g->rowptr && g->col, "csr pointers are NULL");
@@ -634,9 +648,9 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     const int grid = num_sms() * 2;
     char *hM = static_cast<char *>(M);
 
-    auto ensure = [&](int x, int keep0, int keep1, size_t i) -> int {
+    auto ensure = [&](int x, size_t i) -> int {
         bool load = false;
-        const int victim = large_bin_for(bin_part, seq, i, x, keep0, keep1, &load);
+        const int victim = large_bin_for(bin_part, seq, i, x, p->large_evict == 1, &load);
         if (!load) return victim;
         cudaStream_t st = pstr[victim];
         for (cudaEvent_t e : bin_users[victim]) cudaStreamWaitEvent(st, e, 0);
@@ -661,8 +675,8 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     for (size_t i = 0; i < seq.size(); ++i) {
         const int a = seq[i].first, b = seq[i].second;
         const int r = (int)(i / order.size());
-        const int ba = ensure(a, a, b, i);
-        const int bb = ensure(b, a, b, i);
+        const int ba = ensure(a, i);
+        const int bb = ensure(b, i);
         // SCT: edge block into the next edge bin
         const int eb = (int)(i % p->s_gpu);
         const Block &blk = blocks[i % order.size()];

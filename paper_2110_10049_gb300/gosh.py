@@ -43,7 +43,8 @@ class gosh_params(C.Structure):
                 ("mlp_epochs", C.c_int), ("mlp_lr", C.c_double), ("mlp_batch", C.c_int),
                 ("mlp_max_rows", C.c_int64), ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int),
                 ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int),
-                ("walk_length", C.c_int), ("walk_window", C.c_int), ("large_serial", C.c_int)]
+                ("walk_length", C.c_int), ("walk_window", C.c_int), ("large_serial", C.c_int),
+                ("large_evict", C.c_int)]
 
 
 class gosh_walk_stats(C.Structure):
@@ -107,7 +108,7 @@ def lib() -> C.CDLL:
             "gosh_train_level_walks": [P(gosh_csr), vp, i32, i32, P(gosh_params), vp, vp, P(gosh_walk_stats)],
             "gosh_walk_pairs": [P(gosh_csr), i32, i32, i32, i32, u64, u64, vp],
             "gosh_walk_order": [i64, i32, i32, u64, u64, vp],
-            "gosh_large_plan": [i64, i32, i32, i32, vp, vp, i32],
+            "gosh_large_plan": [i64, i32, i32, i32, i32, vp, vp, i32],
             "gosh_mlp_create": [i32, i32, u64, P(vp)],
             "gosh_mlp_get_weights": [vp, vp, vp, vp, vp],
             "gosh_mlp_set_weights": [vp, vp, vp, vp, vp],
@@ -412,14 +413,14 @@ def gosh_walk_order(positions, level, epoch, seed, graph_id=0):
     return out
 
 
-def gosh_large_plan(n, K, p_gpu, rounds):
+def gosh_large_plan(n, K, p_gpu, rounds, evict=0):
     """Host-only schedule simulation: (pairs [kernels x 2], loads [kernels x 2])."""
-    cap = rounds * K * (K + 1) // 2
+    cap = max(rounds * K * (K + 1) // 2, 0)
     pairs = np.zeros((max(cap, 1), 2), dtype=np.int32)
     loads = np.zeros((max(cap, 1), 2), dtype=np.int32)
-    cnt = lib().gosh_large_plan(n, K, p_gpu, rounds, pairs.ctypes.data, loads.ctypes.data, cap)
+    cnt = lib().gosh_large_plan(n, K, p_gpu, rounds, evict, pairs.ctypes.data, loads.ctypes.data, cap)
     if cnt == -2:
-        raise GoshError("gosh_large_plan", 1, "need K >= 1, 2 <= p_gpu <= 999, rounds >= 0")
+        raise GoshError("gosh_large_plan", 1, "need K >= 1, 2 <= p_gpu <= 999, rounds >= 0, evict 0 or 1")
     if cnt < 0:
         raise GoshError("gosh_large_plan", 1, "capacity")
     return pairs[:cnt], loads[:cnt]

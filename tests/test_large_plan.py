@@ -1,8 +1,15 @@
 """LargeGraphGPU scheduler invariants (host only, no GPU): the inside-out order
 (Sec. 5.1), every part pair once per round, never more parts resident than
 bins, both parts of a kernel resident when it runs, and loads only when a part
-is missing."""
+is missing, under both bin choices; the paper's worked example of Sec. 5.2
+(tests/golden/large_bins_example.txt) under the choice that spares the
+previous kernel's parts, which then never makes a copy wait for the previous
+kernel when three or more bins are available."""
+import os
+
 import pytest
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -18,9 +25,10 @@ def test_inside_out_order(g):
                                         (3, 0), (3, 1), (3, 2), (3, 3)]
 
 
+@pytest.mark.parametrize("evict", [0, 1])
 @pytest.mark.parametrize("K,bins,rounds", [(1, 2, 3), (2, 2, 2), (5, 3, 3), (8, 2, 2), (9, 4, 3), (16, 3, 2)])
-def test_schedule_invariants(g, K, bins, rounds):
-    pairs, loads = g.gosh_large_plan(10 ** 6, K, bins, rounds)
+def test_schedule_invariants(g, K, bins, rounds, evict):
+    pairs, loads = g.gosh_large_plan(10 ** 6, K, bins, rounds, evict)
     per_round = K * (K + 1) // 2
     assert len(pairs) == rounds * per_round
     for r in range(rounds):
@@ -38,12 +46,13 @@ def test_schedule_invariants(g, K, bins, rounds):
         assert len(resident) <= bins
 
 
-@pytest.mark.parametrize("K,bins,rounds", [(0, 3, 1), (4, 1, 1), (4, 0, 1), (3, 1000, 1), (3, 3, -1)])
-def test_invalid_arguments_rejected(g, K, bins, rounds):
+@pytest.mark.parametrize("K,bins,rounds,evict", [(0, 3, 1, 0), (4, 1, 1, 0), (4, 0, 1, 0), (3, 1000, 1, 0),
+                                                 (3, 3, -1, 0), (3, 3, 1, 2), (3, 3, 1, -1)])
+def test_invalid_arguments_rejected(g, K, bins, rounds, evict):
     # one bin cannot hold both parts of a pair: rejected, not simulated
     with pytest.raises(g.GoshError):
-        g.gosh_large_plan(1000, K, bins, rounds)
-    cnt = g.lib().gosh_large_plan(1000, K, bins, rounds, None, None, 0)
+        g.gosh_large_plan(1000, K, bins, rounds, evict)
+    cnt = g.lib().gosh_large_plan(1000, K, bins, rounds, evict, None, None, 0)
     assert cnt == -2
 
 
@@ -51,5 +60,59 @@ def test_capacity_checked_before_writing(g):
     import numpy as np
     pairs = np.full((3, 2), -7, dtype=np.int32)
     loads = np.full((3, 2), -7, dtype=np.int32)
-    assert g.lib().gosh_large_plan(1000, 3, 2, 1, pairs.ctypes.data, loads.ctypes.data, 3) == -1
+    assert g.lib().gosh_large_plan(1000, 3, 2, 1, 0, pairs.ctypes.data, loads.ctypes.data, 3) == -1
     assert (pairs == -7).all() and (loads == -7).all()
+
+
+def replay(pairs, loads, bins):
+    """Resident part per bin before each kernel, and the (part, bin, evicted)
+    loads made for it."""
+    held = [-1] * bins
+    for (a, b), (l0, l1) in zip(pairs, loads):
+        before = list(held)
+        made = []
+        for ld in (l0, l1):
+            if ld >= 0:
+                part, bin_ = divmod(int(ld), 1000)
+                made.append((part, bin_, held[bin_]))
+                held[bin_] = part
+        yield (int(a), int(b)), before, made
+
+
+def test_paper_bin_example():
+    from paper_2110_10049_gb300 import gosh as g
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "large_bins_example.txt")) if ln.strip()[:1] not in ("#", "")]
+    for K, bins, resident, ka, kb, loaded, evicted in rows:
+        K, bins, ka, kb, loaded, evicted = int(K), int(bins), int(ka), int(kb), int(loaded), int(evicted)
+        resident = sorted(int(x) for x in resident.split(","))
+        pairs, loads = g.gosh_large_plan(1000, K, bins, 1, 1)
+        seen = False
+        for pair, before, made in replay(pairs, loads, bins):
+            if pair != (ka, kb):
+                continue
+            # the example's situation arises in the simulated round ...
+            assert sorted(before) == resident
+            # ... and the incoming part replaces the one the paper names
+            assert [(p, e) for p, _, e in made] == [(loaded, evicted)]
+            seen = True
+        assert seen
+        # the farthest-next-use choice makes that copy wait for the running
+        # kernel instead (it evicts the other part)
+        pairs, loads = g.gosh_large_plan(1000, K, bins, 2, 0)
+        for pair, before, made in replay(pairs, loads, bins):
+            if pair == (ka, kb) and sorted(before) == resident:
+                assert [(p, e) for p, _, e in made] != [(loaded, evicted)]
+
+
+@pytest.mark.parametrize("K,bins", [(4, 3), (6, 3), (9, 3), (16, 3), (7, 4), (12, 5)])
+def test_sparing_previous_kernel_never_waits_on_it(g, K, bins):
+    for evict in (0, 1):
+        pairs, loads = g.gosh_large_plan(1000, K, bins, 3, evict)
+        waits, prev = 0, None
+        for pair, before, made in replay(pairs, loads, bins):
+            waits += sum(1 for _, _, e in made if prev is not None and e in prev)
+            prev = pair
+        if evict == 1:
+            assert waits == 0
+        elif K > bins:
+            assert waits > 0  # the rule that minimises copies does wait
