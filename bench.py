@@ -258,7 +258,7 @@ def run_large_workload(args):
     gr = sp.train
     params = gosh.default_params(d=LARGE["d"], k=LARGE["k"], lr=LARGE["lr"], dtype=gosh.GOSH_BF16, seed=5,
                                  B=LARGE["B"], p_gpu=LARGE["p_gpu"], s_gpu=LARGE["s_gpu"],
-                                 device_budget_bytes=LARGE["budget"])
+                                 device_budget_bytes=LARGE["budget"], large_evict=args.large_evict)
     M = torch.zeros((gr.n, LARGE["d"]), dtype=torch.bfloat16).pin_memory()
     Md = torch.empty((gr.n, LARGE["d"]), dtype=torch.bfloat16, device="cuda")
     gosh.gosh_init_embedding(Md, level=0, seed=5)
@@ -294,7 +294,8 @@ def run_large_workload(args):
         "config": {"workload": "LargeGraphGPU: R-MAT scale 22, ef 16, level 0 out of core, d=32 BF16, k=3, e=20, "
                                "B=5, P_GPU=3, S_GPU=2, device budget 512 MB",
                    "vertices": gr.n, "csr_entries": gr.nnz, "parts": st["parts"], "rounds": st["rounds"],
-                   "kernels": st["kernels"], "swaps": st["swaps"], "device_bytes": st["device_bytes"]},
+                   "kernels": st["kernels"], "swaps": st["swaps"], "device_bytes": st["device_bytes"],
+                   "bin_choice": "spare previous kernel" if args.large_evict else "farthest next use"},
         "setup_ms_per_step": st["setup_ms"], "streaming_ms_per_step": st["total_ms"] - st["setup_ms"],
         "host_link": {"h2d_bytes_per_step": st["h2d_bytes"], "d2h_bytes_per_step": st["d2h_bytes"],
                       "GBps": (st["h2d_bytes"] + st["d2h_bytes"]) / (tot_ms / args.steps / 1000.0) / 1e9},
@@ -387,6 +388,9 @@ def main():
     ap.add_argument("--projection", default="copy", choices=["copy", "learned"],
                     help="projection between levels in the timed embed")
     ap.add_argument("--epochs", type=int, default=None, help="epochs of the timed embed (default 200)")
+    ap.add_argument("--large-evict", type=int, default=0, choices=[0, 1],
+                    help="LargeGraphGPU bin choice (--workload large): 0 farthest next use, 1 spare the "
+                         "previous kernel's parts")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
