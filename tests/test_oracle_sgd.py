@@ -130,3 +130,34 @@ def test_auc_brute_force_and_ties(orc):
     pos, neg = rng.normal(1, 1, 500), rng.normal(0, 1, 700)
     y = np.r_[np.ones(500), np.zeros(700)]
     assert orc.auc(pos, neg) == pytest.approx(skm.roc_auc_score(y, np.r_[pos, neg]), abs=1e-12)
+
+
+def test_embed_single_level_trains_level_zero(orc):
+    # without coarsening (the paper's NoCoarse configuration, D = 1) Alg. 2
+    # must still train M_0 (reading: level 0 is trained) with every epoch,
+    # from the init of level D-1 = 0 rounded to the storage precision
+    g = synth.random_graph(60, 0.1, 2)
+    M, info = orc.embed(g.rowptr, g.col, 16, 3, 0.05, 30, 0.3, seed=6, coarsening=False)
+    assert info["levels"] == 1 and info["epochs"] == [30]
+    R = orc.init_uniform(g.n, 16, 0, 6).astype(np.float32).astype(np.float64)
+    orc.train_sequential(g.rowptr, g.col, R, 3, 0, 30, 0.05, 1e-4, 6)
+    np.testing.assert_array_equal(M, R)
+    assert not np.array_equal(M, orc.init_uniform(g.n, 16, 0, 6).astype(np.float32).astype(np.float64))
+
+
+def test_embed_two_levels_follows_alg2(orc):
+    # D = 2 (Alg. 4 coarsens once, then stops below the threshold): Alg. 2
+    # trains the coarse level first with its share of the epochs, expands it
+    # through the map, then trains level 0 with the rest
+    g = synth.random_graph(60, 0.1, 2)
+    M, info = orc.embed(g.rowptr, g.col, 16, 3, 0.05, 30, 0.3, seed=6, threshold=100)
+    graphs, maps = orc.mec_hierarchy(g.rowptr, g.col, 100, 0.8)
+    assert info["levels"] == len(graphs) == 2
+    e0, e1 = orc.epoch_split(30, 0.3, 2)
+    assert info["epochs"] == [e0, e1] and e1 > 0 and e0 > 0
+    (rp0, co0), (rp1, co1) = graphs
+    R1 = orc.init_uniform(len(rp1) - 1, 16, 1, 6).astype(np.float32).astype(np.float64)
+    orc.train_sequential(rp1, co1, R1, 3, 1, e1, 0.05, 1e-4, 6)
+    R0 = R1[maps[0]].copy()
+    orc.train_sequential(rp0, co0, R0, 3, 0, e0, 0.05, 1e-4, 6)
+    np.testing.assert_array_equal(M, R0)
