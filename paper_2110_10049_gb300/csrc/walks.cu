@@ -135,8 +135,9 @@ void walk_fill(const int64_t *rowptr, const int32_t *col, int64_t v0, int64_t v1
         }
         for (int t = 0; t + 1 < l; ++t) {
             // pass 1: the entry each live walk moves through (row pointers,
-            // prefetched one step earlier); pass 2: the neighbour reads, all
-            // independent, then a prefetch of the next step's row pointers
+            // prefetched one step earlier), and a prefetch of that entry;
+            // pass 2: the neighbour reads, all independent, then a prefetch
+            // of the next step's row pointers
             for (int b = 0; b < cnt; ++b) {
                 at[b] = -1;
                 if (len[b] != t + 1) continue;  // this walk has ended
@@ -144,7 +145,10 @@ void walk_fill(const int64_t *rowptr, const int32_t *col, int64_t v0, int64_t v1
                     words[b] = philox4x64_10((uint64_t)(gs + b), (uint64_t)(t >> 2), ctr2, kTagWalk, seed, graph);
                 const int64_t cur = w[(size_t)b * l + t];
                 const int64_t off = rowptr[cur], deg = rowptr[cur + 1] - off;
-                if (deg > 0) at[b] = off + (int64_t)uniform_index(words[b].w[t & 3], (uint64_t)deg);
+                if (deg > 0) {
+                    at[b] = off + (int64_t)uniform_index(words[b].w[t & 3], (uint64_t)deg);
+                    __builtin_prefetch(col + at[b]);
+                }
             }
             for (int b = 0; b < cnt; ++b) {
                 if (at[b] < 0) continue;
