@@ -60,8 +60,10 @@ typedef struct gosh_csr {
 } gosh_csr;
 
 typedef struct gosh_params {
-    int d;                  /* embedding dimension */
-    int k;                  /* negatives per positive, n_s (1..15) */
+    int d;                  /* embedding dimension: 16, 32, 64 or 128 (LargeGraphGPU, walks, the
+                               batched entry and the learned projection: 32, 64 or 128) */
+    int k;                  /* negatives per positive, n_s (0..15; deterministic mode <= 7,
+                               walks <= 3, LargeGraphGPU B * (k+1) <= 32) */
     double lr;              /* initial learning rate of every level */
     double lr_floor;        /* lr' = lr * max(1 - j/e_i, lr_floor); paper: 1e-4 */
     int epochs;             /* e: total epochs over all levels (one epoch = one pass over V_i) */

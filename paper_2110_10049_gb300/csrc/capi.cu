@@ -81,7 +81,7 @@ int grid_for(int64_t work, int threads = 256) {
     return (int)(g < cap ? g : cap);
 }
 
-bool dim_ok(int d, gosh_dtype t) { return d == 16 || d == 32 || d == 64 || d == 128; }
+bool dim_ok(int d) { return d == 16 || d == 32 || d == 64 || d == 128; }
 bool dtype_ok(gosh_dtype t) { return t == GOSH_F32 || t == GOSH_BF16 || t == GOSH_F16; }
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -266,20 +266,6 @@ __global__ void sum_partials(const double *__restrict__ parts, int n, double *__
     if (threadIdx.x == 0) *out = s[0];
 }
 
-gosh_status check_params(const gosh_params *p) {
-    GOSH_CHECK_ARG(p != nullptr, "params is NULL");
-    GOSH_CHECK_ARG(dtype_ok(p->dtype), "unknown dtype %d", (int)p->dtype);
-    GOSH_CHECK_ARG(dim_ok(p->d, p->dtype), "d must be 16, 32, 64 or 128 (got %d)", p->d);
-    GOSH_CHECK_ARG(p->k >= 0 && p->k <= 15, "k must be in 0..15 (got %d)", p->k);
-    GOSH_CHECK_ARG(p->lr > 0 && std::isfinite(p->lr), "lr must be positive");
-    GOSH_CHECK_ARG(p->lr_floor >= 0 && p->lr_floor <= 1, "lr_floor must be in [0, 1]");
-    GOSH_CHECK_ARG(p->mode == GOSH_HOGWILD || p->mode == GOSH_DETERMINISTIC, "unknown mode %d", (int)p->mode);
-    GOSH_CHECK_ARG(p->epochs >= 0, "epochs must be >= 0");
-    GOSH_CHECK_ARG(p->p >= 0 && p->p <= 1, "p must be in [0, 1]");
-    GOSH_CHECK_ARG(p->shrink > 0 && p->shrink <= 1, "shrink must be in (0, 1]");
-    return GOSH_OK;
-}
-
 gosh_status check_csr(const gosh_csr *g) {
     GOSH_CHECK_ARG(g != nullptr, "csr is NULL");
     GOSH_CHECK_ARG(g->n >= 1 && g->n < (int64_t(1) << 31), "n must be in [1, 2^31) (got %lld)", (long long)g->n);
@@ -370,6 +356,20 @@ bool is_device_ptr(const void *p) {
 }
 
 }  // namespace
+
+gosh_status check_params(const gosh_params *p) {
+    GOSH_CHECK_ARG(p != nullptr, "params is NULL");
+    GOSH_CHECK_ARG(dtype_ok(p->dtype), "unknown dtype %d", (int)p->dtype);
+    GOSH_CHECK_ARG(dim_ok(p->d), "d must be 16, 32, 64 or 128 (got %d)", p->d);
+    GOSH_CHECK_ARG(p->k >= 0 && p->k <= 15, "k must be in 0..15 (got %d)", p->k);
+    GOSH_CHECK_ARG(p->lr > 0 && std::isfinite(p->lr), "lr must be positive");
+    GOSH_CHECK_ARG(p->lr_floor >= 0 && p->lr_floor <= 1, "lr_floor must be in [0, 1]");
+    GOSH_CHECK_ARG(p->mode == GOSH_HOGWILD || p->mode == GOSH_DETERMINISTIC, "unknown mode %d", (int)p->mode);
+    GOSH_CHECK_ARG(p->epochs >= 0, "epochs must be >= 0");
+    GOSH_CHECK_ARG(p->p >= 0 && p->p <= 1, "p must be in [0, 1]");
+    GOSH_CHECK_ARG(p->shrink > 0 && p->shrink <= 1, "shrink must be in (0, 1]");
+    return GOSH_OK;
+}
 
 gosh_status check_host_csr(const int64_t *rowptr, const int32_t *col, int64_t n, bool symmetric) {
     GOSH_CHECK_ARG(rowptr != nullptr && col != nullptr && n >= 1, "csr pointers are NULL or n < 1");
@@ -553,7 +553,7 @@ gosh_status gosh_init_embedding(void *M, int64_t n, int d, gosh_dtype dtype, int
                                 uint64_t graph_id, void *stream) {
     clear_error();
     GOSH_CHECK_ARG(M != nullptr && n >= 0, "bad M / n");
-    GOSH_CHECK_ARG(dtype_ok(dtype) && dim_ok(d, dtype), "bad d / dtype");
+    GOSH_CHECK_ARG(dtype_ok(dtype) && dim_ok(d), "bad d / dtype");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t work = n * ((d + 3) / 4);
     GOSH_TRY(by_dtype(dtype, [&](auto *tp) {
@@ -614,7 +614,7 @@ gosh_status gosh_project(const void *M_coarse, int64_t n_coarse, const int32_t *
     GOSH_CHECK_ARG(M_coarse && M_fine && map, "NULL pointer");
     GOSH_CHECK_ARG(aligned16(M_coarse) && aligned16(M_fine), "M must be 16-byte aligned");
     GOSH_CHECK_ARG(n_coarse >= 1 && n_fine >= 0, "bad sizes");
-    GOSH_CHECK_ARG(dtype_ok(dtype) && dim_ok(d, dtype), "bad d / dtype");
+    GOSH_CHECK_ARG(dtype_ok(dtype) && dim_ok(d), "bad d / dtype");
     cudaStream_t s = (cudaStream_t)stream;
     const int vecs = (int)(d * dtype_size(dtype) / 16);
     launch_dep(project_copy_kernel, grid_for(n_fine * vecs), 256, 0, s, static_cast<const uint4 *>(M_coarse), map,
@@ -627,7 +627,7 @@ gosh_status gosh_pair_scores(const void *M, int d, gosh_dtype dtype, const int32
                              void *stream) {
     clear_error();
     GOSH_CHECK_ARG(M && pairs && out && npairs >= 0, "bad arguments");
-    GOSH_CHECK_ARG(dtype_ok(dtype) && dim_ok(d, dtype), "bad d / dtype");
+    GOSH_CHECK_ARG(dtype_ok(dtype) && dim_ok(d), "bad d / dtype");
     cudaStream_t s = (cudaStream_t)stream;
     if (npairs == 0) return GOSH_OK;
     GOSH_TRY(by_dtype(dtype, [&](auto *tp) {

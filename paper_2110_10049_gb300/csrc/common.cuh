@@ -339,6 +339,11 @@ template <> struct Store<__half> {
 // Device word raised by bounded waits that gave up (capi.cu); read by gosh_device_check.
 int *device_error_word();
 
+// The parameter checks every training entry point makes: dtype, d in
+// {16, 32, 64, 128}, 0 <= k <= 15, a positive finite lr, lr_floor in [0, 1],
+// mode, epochs >= 0, p in [0, 1], shrink in (0, 1].
+gosh_status check_params(const gosh_params *p);
+
 // Content check of a HOST CSR, the host counterpart of gosh_validate_csr:
 // rowptr starts at 0 and never decreases, every column lies in [0, n), rows
 // are strictly ascending and hold no self-loop, and (if `symmetric`) every

@@ -378,12 +378,12 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
                                    void *stream, gosh_large_stats *stats) {
     clear_error();
     GOSH_CHECK_ARG(g && p && M, "NULL argument");
+    GOSH_TRY(check_params(p));
     GOSH_CHECK_ARG(!g->on_device, "gosh_train_level_large takes a host CSR (it streams it)");
     GOSH_CHECK_ARG(g->n >= 1 && g->n < (int64_t(1) << 31), "bad n");
     GOSH_CHECK_ARG(p->mode == GOSH_HOGWILD, "LargeGraphGPU is lock-free (GOSH_HOGWILD)");
     GOSH_CHECK_ARG(p->B >= 1 && p->B * (p->k + 1) <= kMaxSlots && p->B <= 8, "need 1 <= B <= 8 and B*(k+1) <= %d",
                    kMaxSlots);
-    GOSH_CHECK_ARG(p->k >= 0, "k must be >= 0");
     GOSH_CHECK_ARG(p->p_gpu >= 2 && p->s_gpu >= 1, "need P_GPU >= 2 and S_GPU >= 1");
     GOSH_CHECK_ARG(p->large_evict == 0 || p->large_evict == 1, "large_evict must be 0 or 1");
     const PairLaunch launch = pick_pair_kernel(p->dtype, p->d);

@@ -192,6 +192,7 @@ gosh_status gosh_train_level_walks(const gosh_csr *g, void *M, int level, int ep
                                    void *stream, unsigned long long *n_updates, gosh_walk_stats *stats) {
     clear_error();
     GOSH_CHECK_ARG(g && p && M, "NULL argument");
+    GOSH_TRY(check_params(p));
     GOSH_CHECK_ARG(g->n >= 1 && g->n < (int64_t(1) << 31), "bad n");
     GOSH_CHECK_ARG(((uintptr_t)M & 15) == 0, "M must be a 16-byte aligned device pointer");
     GOSH_CHECK_ARG(p->mode == GOSH_HOGWILD, "walk sampling is lock-free (GOSH_HOGWILD)");

@@ -72,3 +72,23 @@ def test_release_host_buffers_without_any_held():
     # nothing pinned in this process: nothing to free, no device involved
     assert g.gosh_release_host_buffers() == 0
     assert g.gosh_release_host_buffers() == 0
+
+
+@pytest.mark.parametrize("entry", ["large", "walks"])
+@pytest.mark.parametrize("bad", [dict(lr=0.0), dict(lr=float("nan")), dict(d=48), dict(k=-1), dict(lr_floor=2.0),
+                                 dict(dtype=7)])
+def test_bad_params_rejected_before_device_work(entry, bad):
+    gr = synth.random_graph(12, 0.4, 3)
+    L = g.lib()
+    M = np.zeros((gr.n, 32), dtype=np.float32)
+    p = g.default_params(d=32, k=3, large_parts=2, p_gpu=2, s_gpu=1, B=1)
+    for key, val in bad.items():
+        setattr(p, key, val)
+    cg, keep = _csr(gr.rowptr, gr.col)
+    if entry == "large":
+        rc = L.gosh_train_level_large(C.byref(cg), C.c_void_p(M.ctypes.data), 0, 3, C.byref(p), None,
+                                      C.byref(g.gosh_large_stats()))
+    else:
+        rc = L.gosh_train_level_walks(C.byref(cg), C.c_void_p(M.ctypes.data), 0, 3, C.byref(p), None, None,
+                                      C.byref(g.gosh_walk_stats()))
+    assert rc == 1, (bad, rc, L.gosh_last_error())
