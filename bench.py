@@ -34,10 +34,13 @@ UNIT = "sample-updates/s"
 WL = dict(name="rmat20", scale=20, edge_factor=16, d=128, k=3, epochs=200, p=0.3, lr=0.045)
 
 
-def workload_name(tables, epochs=None, projection="copy"):
+def workload_name(tables, epochs=None, projection="copy", mode="hogwild", det_batch=4096):
     e = WL["epochs"] if epochs is None else epochs
-    return "R-MAT scale 20, ef 16, 80/20 split, d=128, k=3, e=%d, p=0.3, %s tables, %s projection" % (e, tables,
+    name = "R-MAT scale 20, ef 16, 80/20 split, d=128, k=3, e=%d, p=0.3, %s tables, %s projection" % (e, tables,
                                                                                                   projection)
+    if mode == "deterministic":
+        name += ", deterministic mode (snapshot batches of %d sources)" % det_batch
+    return name
 
 
 def peaks():
@@ -159,21 +162,30 @@ def run_reference(args, rank, world):
     sp = make_inputs(0)
     gr = sp.train
     M = oracle.init_uniform(gr.n, WL["d"], 0, 1) * 30
+    det = args.mode == "deterministic"
+
+    def epoch(seed):
+        if det:
+            return oracle.train_deterministic(gr.rowptr, gr.col, M, WL["k"], 0, 1, WL["lr"], 1e-4, seed,
+                                              args.det_batch)[1]
+        return oracle.train_sequential(gr.rowptr, gr.col, M, WL["k"], 0, 1, WL["lr"], 1e-4, seed)[1]
+
     for w in range(args.warmup):
-        oracle.train_sequential(gr.rowptr, gr.col, M, WL["k"], 0, 1, WL["lr"], 1e-4, 100 + w)
+        epoch(100 + w)
     t0 = time.perf_counter()
     upd = 0
     for s in range(args.steps):
-        _, nu = oracle.train_sequential(gr.rowptr, gr.col, M, WL["k"], 0, 1, WL["lr"], 1e-4, 200 + s)
-        upd += nu
+        upd += epoch(200 + s)
     dt = time.perf_counter() - t0
     val = upd / dt
-    sample = "one level-0 epoch per step (%d sources, FP64 sequential Alg. 3)" % gr.n
+    sample = "one level-0 epoch per step (%d sources, FP64 %s)" % (
+        gr.n, "deterministic mode, batches of %d" % args.det_batch if det else "sequential Alg. 3")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(args.tables, args.epochs, args.projection),
+        "data": "synthetic", "config": {"workload": workload_name(args.tables, args.epochs, args.projection,
+                                                                  args.mode, args.det_batch),
                                         "oracle_tables": "f64"},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -388,6 +400,9 @@ def main():
     ap.add_argument("--projection", default="copy", choices=["copy", "learned"],
                     help="projection between levels in the timed embed")
     ap.add_argument("--epochs", type=int, default=None, help="epochs of the timed embed (default 200)")
+    ap.add_argument("--mode", default="hogwild", choices=["hogwild", "deterministic"],
+                    help="training mode of the timed embed (the default workload)")
+    ap.add_argument("--det-batch", type=int, default=4096, help="sources per snapshot batch (--mode deterministic)")
     ap.add_argument("--large-evict", type=int, default=0, choices=[0, 1],
                     help="LargeGraphGPU bin choice (--workload large): 0 farthest next use, 1 spare the "
                          "previous kernel's parts")
@@ -426,8 +441,10 @@ def main():
     co = torch.from_numpy(gr.col).cuda()
     dt_code = gosh.GOSH_BF16 if args.tables == "bf16" else gosh.GOSH_F32
     epochs = WL["epochs"] if args.epochs is None else args.epochs
+    det = args.mode == "deterministic"
     params = gosh.default_params(d=WL["d"], k=WL["k"], lr=WL["lr"], epochs=epochs, p=WL["p"],
-                                 dtype=dt_code, seed=11 + rank, projection=1 if args.projection == "learned" else 0)
+                                 dtype=dt_code, seed=11 + rank, projection=1 if args.projection == "learned" else 0,
+                                 mode=args.mode, det_batch=args.det_batch)
     out = torch.empty((gr.n, WL["d"]), dtype=gosh.torch_dtype(dt_code), device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -487,7 +504,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(args.tables, epochs, args.projection), "vertices": gr.n,
+        "config": {"workload": workload_name(args.tables, epochs, args.projection, args.mode, args.det_batch),
+                   "vertices": gr.n,
                    "csr_entries": gr.nnz,
                    "levels": last["levels"], "level_sizes": last["n"], "epochs_per_level": last["epochs"],
                    "tables": args.tables, "l2": "flushed between steps (512 MB write)",
@@ -496,8 +514,10 @@ def main():
         "breakdown_ms": {"coarsen": last["coarsen_ms"], "train": sum(last["train_ms"]),
                          "project": last["project_ms"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "train_kernel (level 0, one launch per epoch)",
+                     "frac": achieved / peak, "traffic": None if det else traffic,
+                     "kernel": ("level-0 deterministic epoch (training launches, sorts and applies of every "
+                                "batch; achieved counts the training bytes only)") if det else
+                               "train_kernel (level 0, one launch per epoch)",
                      "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": l0_ms,
                      "peak_kind": peak_kind + " copy bandwidth"},
         "clocks": clocks.summary(),
@@ -525,7 +545,7 @@ def main():
                          "h2d_bytes_per_step": int(gr.rowptr.nbytes + gr.col.nbytes),
                          "d2h_bytes_per_step": int(hout.numel() * hout.element_size())}
 
-    if not args.no_compare and rank == 0:
+    if not args.no_compare and not det and rank == 0:
         pos = torch.from_numpy(sp.test_pos).cuda()
         neg = torch.from_numpy(sp.test_neg).cuda()
         def timed_embed(code, epochs, proj):
