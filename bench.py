@@ -403,6 +403,8 @@ def main():
     ap.add_argument("--mode", default="hogwild", choices=["hogwild", "deterministic"],
                     help="training mode of the timed embed (the default workload)")
     ap.add_argument("--det-batch", type=int, default=4096, help="sources per snapshot batch (--mode deterministic)")
+    ap.add_argument("--epoch-overlap", type=int, default=1,
+                    help="epochs of a large level allowed to run at once (1 = serialised, as the paper)")
     ap.add_argument("--large-evict", type=int, default=0, choices=[0, 1],
                     help="LargeGraphGPU bin choice (--workload large): 0 farthest next use, 1 spare the "
                          "previous kernel's parts")
@@ -444,7 +446,7 @@ def main():
     det = args.mode == "deterministic"
     params = gosh.default_params(d=WL["d"], k=WL["k"], lr=WL["lr"], epochs=epochs, p=WL["p"],
                                  dtype=dt_code, seed=11 + rank, projection=1 if args.projection == "learned" else 0,
-                                 mode=args.mode, det_batch=args.det_batch)
+                                 mode=args.mode, det_batch=args.det_batch, epoch_overlap=args.epoch_overlap)
     out = torch.empty((gr.n, WL["d"]), dtype=gosh.torch_dtype(dt_code), device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -509,6 +511,7 @@ def main():
                    "csr_entries": gr.nnz,
                    "levels": last["levels"], "level_sizes": last["n"], "epochs_per_level": last["epochs"],
                    "tables": args.tables, "l2": "flushed between steps (512 MB write)",
+                   "epoch_overlap": args.epoch_overlap,
                    "parallelism": "replicas x%d" % world},
         "time_to_embed_ms": ms_per_step,
         "breakdown_ms": {"coarsen": last["coarsen_ms"], "train": sum(last["train_ms"]),

@@ -121,6 +121,14 @@ typedef struct gosh_params {
                                the same, but sparing the parts of the previous kernel while
                                another bin is eligible, so that the copy overlaps that kernel
                                (Sec. 5.2's example), at the cost of more copies */
+    int64_t overlap_min_vertices; /* epoch_overlap applies to levels with at least this many
+                               vertices (default 65536); smaller levels stay serialised */
+    int epoch_overlap;      /* lock-free per-epoch launches: c in 1..8 consecutive epochs of a
+                               large level may run at once (epoch j waits only for epoch j-c:
+                               the concurrency that Sec. 6.3 leaves as future work); 1
+                               (default) serialises every epoch as the paper does.  Levels
+                               trained in one cooperative launch, and calls that request
+                               per-epoch losses, stay serialised. */
 } gosh_params;
 
 typedef struct gosh_walk_stats {

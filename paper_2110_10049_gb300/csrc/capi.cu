@@ -368,6 +368,9 @@ gosh_status check_params(const gosh_params *p) {
     GOSH_CHECK_ARG(p->epochs >= 0, "epochs must be >= 0");
     GOSH_CHECK_ARG(p->p >= 0 && p->p <= 1, "p must be in [0, 1]");
     GOSH_CHECK_ARG(p->shrink > 0 && p->shrink <= 1, "shrink must be in (0, 1]");
+    GOSH_CHECK_ARG(p->epoch_overlap >= 0 && p->epoch_overlap <= 8, "epoch_overlap must be in 0..8 (got %d)",
+                   p->epoch_overlap);
+    GOSH_CHECK_ARG(p->overlap_min_vertices >= 0, "overlap_min_vertices must be >= 0");
     return GOSH_OK;
 }
 
@@ -430,6 +433,8 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->walk_window = 3;
     p->large_serial = 0;
     p->large_evict = 0;
+    p->overlap_min_vertices = 65536;
+    p->epoch_overlap = 1;
     return GOSH_OK;
 }
 

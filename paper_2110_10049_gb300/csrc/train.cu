@@ -266,13 +266,45 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
             if (e == cudaSuccess) return GOSH_OK;
             cudaGetLastError();  // not co-resident here: fall back to one launch per epoch
         }
+        // Epoch overlap (off by default; Sec. 6.3 leaves concurrent epochs on
+        // large levels as future work): on a level of at least
+        // overlap_min_vertices, epoch j runs on stream j mod c and so waits
+        // only for epoch j - c; the streams fork from s and join it again.
+        const int c = (!loss_per_epoch && p->epoch_overlap > 1 && n >= p->overlap_min_vertices && epochs > 1)
+                          ? std::min(p->epoch_overlap, epochs)
+                          : 1;
+        cudaStream_t side[8] = {};
+        cudaEvent_t ev[8] = {};
+        struct SideCleanup {
+            cudaStream_t *side;
+            cudaEvent_t *ev;
+            ~SideCleanup() {
+                for (int i = 0; i < 8; ++i) {
+                    if (side[i]) cudaStreamDestroy(side[i]);  // released once its work is done
+                    if (ev[i]) cudaEventDestroy(ev[i]);
+                }
+            }
+        } side_cleanup{side, ev};
+        for (int i = 1; i < c; ++i) {
+            GOSH_TRY_CUDA(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking));
+            GOSH_TRY_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+        }
+        if (c > 1) {
+            GOSH_TRY_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+            GOSH_TRY_CUDA(cudaEventRecord(ev[0], s));
+            for (int i = 1; i < c; ++i) GOSH_TRY_CUDA(cudaStreamWaitEvent(side[i], ev[0], 0));
+        }
         for (int j = 0; j < epochs; ++j) {
             const double f = 1.0 - (double)j / (double)epochs;
             a.lr = (float)(p->lr * (f > p->lr_floor ? f : p->lr_floor));
             a.epoch = (uint32_t)j;
-            kern->launch(a, grid, s);
+            kern->launch(a, grid, j % c == 0 ? s : side[j % c]);
             if (loss_per_epoch)
                 launch_dep(loss_finalize, 1, 256, 0, s, parts.as<double>(), grid, loss_per_epoch + j, 0);
+        }
+        for (int i = 1; i < c; ++i) {
+            GOSH_TRY_CUDA(cudaEventRecord(ev[i], side[i]));
+            GOSH_TRY_CUDA(cudaStreamWaitEvent(s, ev[i], 0));
         }
         GOSH_TRY_CUDA(cudaGetLastError());
         return GOSH_OK;

@@ -44,7 +44,7 @@ class gosh_params(C.Structure):
                 ("mlp_max_rows", C.c_int64), ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int),
                 ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int),
                 ("walk_length", C.c_int), ("walk_window", C.c_int), ("large_serial", C.c_int),
-                ("large_evict", C.c_int)]
+                ("large_evict", C.c_int), ("overlap_min_vertices", C.c_int64), ("epoch_overlap", C.c_int)]
 
 
 class gosh_walk_stats(C.Structure):

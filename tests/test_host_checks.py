@@ -92,3 +92,17 @@ def test_bad_params_rejected_before_device_work(entry, bad):
         rc = L.gosh_train_level_walks(C.byref(cg), C.c_void_p(M.ctypes.data), 0, 3, C.byref(p), None, None,
                                       C.byref(g.gosh_walk_stats()))
     assert rc == 1, (bad, rc, L.gosh_last_error())
+
+
+@pytest.mark.parametrize("bad", [dict(epoch_overlap=9), dict(epoch_overlap=-1), dict(overlap_min_vertices=-5)])
+def test_epoch_overlap_limits_checked_first(bad):
+    # the parameter check precedes any device work, so placeholder device
+    # pointers are never touched
+    L = g.lib()
+    p = g.default_params(d=32)
+    assert p.epoch_overlap == 1 and p.overlap_min_vertices == 65536
+    for key, val in bad.items():
+        setattr(p, key, val)
+    cg = g.gosh_csr(10, 256, 512, 1)
+    rc = L.gosh_train_level(C.byref(cg), C.c_void_p(1024), 0, 3, C.byref(p), None, None, None)
+    assert rc == 1 and "overlap" in L.gosh_last_error().decode()
