@@ -49,6 +49,11 @@ def test_params_default_on_host():
     p = gosh.default_params()
     assert (p.d, p.k, p.threshold) == (128, 3, 100)
     assert abs(p.shrink - 0.8) < 1e-12 and abs(p.lr_floor - 1e-4) < 1e-18
+    # the paper's LargeGraphGPU settings and the defaults that keep its
+    # serialised epochs and overlapping part-pair kernels
+    assert (p.p_gpu, p.s_gpu, p.B) == (3, 2, 5)
+    assert (p.large_serial, p.large_evict, p.epoch_overlap, p.overlap_min_vertices) == (0, 0, 1, 65536)
+    assert (p.walk_length, p.walk_window) == (8, 3)
 
 
 def test_struct_layouts_match_binding(tmp_path):
