@@ -368,6 +368,16 @@ gosh_status gosh_walk_pairs(const gosh_csr *g, int walk_length, int walk_window,
 gosh_status gosh_walk_order(int64_t positions, int level, int epoch, uint64_t seed, uint64_t graph_id,
                             int64_t *order);
 
+/* The edge block of part pair (a, b), 0 <= b <= a < K, exactly as
+ * gosh_train_level_large builds it on host threads and streams it (no GPU
+ * use): V is split into K contiguous parts (part i = [n*i/K, n*(i+1)/K));
+ * rp_ab [n_a+1] / col_ab [m_ab] hold, for every u in V^a, its neighbours in
+ * V^b as ids local to V^b (rows from 0); rp_ba / col_ba the same for V^b
+ * against V^a (left untouched when a == b).  Call with rp_ab = NULL to get
+ * m_ab and m_ba only.  g: host CSR, checked as by gosh_walk_pairs. */
+gosh_status gosh_large_block(const gosh_csr *g, int K, int a, int b, int64_t *m_ab, int64_t *m_ba, int64_t *rp_ab,
+                             int32_t *col_ab, int64_t *rp_ba, int32_t *col_ba);
+
 /* Host-only simulation of the LargeGraphGPU part-bin schedule (no GPU use):
  * for `rounds` rounds over K parts and p_gpu bins, with the bin choice
  * `evict` (params->large_evict), writes for every kernel i

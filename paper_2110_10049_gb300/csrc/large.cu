@@ -289,6 +289,153 @@ void large_pair_order(int K, std::vector<std::pair<int, int>> &order) {
         for (int b = 0; b <= a; ++b) order.push_back({a, b});
 }
 
+// The edge blocks of one LargeGraphGPU call, all in one host region: block i
+// holds pair (a, b) = order[i] as rp_ab | col_ab | rp_ba | col_ba (row
+// pointers from 0, entries as local ids of the opposite part; no ba side
+// when a == b), each array 256-byte aligned.  A block side (u in V^a,
+// entries in V^b) is built in row chunks (items) spread over host threads.
+// plan() only counts the entries of each chunk (one walk per row splits it
+// at every part boundary by binary searches of its sorted row) and lays the
+// blocks out; place() puts them in a region; fill(k) writes item k.
+struct EdgeBlocks {
+    struct Side {
+        int blk;
+        bool ab;
+        int pa, pb;  // parts of the rows and of the entries
+        int64_t a0, a1, b0, b1;
+        int64_t entries;
+    };
+    struct Item {
+        int side;
+        int64_t r0;   // first row offset in the side
+        int64_t off;  // entries of the side before this chunk
+    };
+    static constexpr int64_t kChunkRows = 32768;
+    const int64_t *rowptr = nullptr;
+    const int32_t *col = nullptr;
+    int K = 0;
+    std::vector<int64_t> start;
+    std::vector<std::pair<int, int>> order;
+    std::vector<Block> blocks;
+    std::vector<Side> sides;
+    std::vector<Item> items;
+    size_t total_bytes = 0, max_block = 0;
+
+    static size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+    void row_range(const Side &sd, int64_t r, const int32_t **lo, const int32_t **hi) const {
+        const int64_t u = sd.a0 + r;
+        const int32_t *row = col + rowptr[u], *end = col + rowptr[u + 1];
+        *lo = std::lower_bound(row, end, (int32_t)sd.b0);
+        *hi = std::lower_bound(*lo, end, (int32_t)sd.b1);
+    }
+
+    void plan(const int64_t *rp, const int32_t *cl, int parts, const std::vector<int64_t> &st, int nt) {
+        rowptr = rp;
+        col = cl;
+        K = parts;
+        start = st;
+        large_pair_order(K, order);
+        blocks.assign(order.size(), Block{});
+        sides.clear();
+        items.clear();
+        for (size_t i = 0; i < order.size(); ++i) {
+            const int a = order[i].first, b = order[i].second;
+            sides.push_back({(int)i, true, a, b, start[a], start[a + 1], start[b], start[b + 1], 0});
+            if (a != b) sides.push_back({(int)i, false, b, a, start[b], start[b + 1], start[a], start[a + 1], 0});
+        }
+        for (size_t j = 0; j < sides.size(); ++j)
+            for (int64_t r = 0; r < sides[j].a1 - sides[j].a0; r += kChunkRows) items.push_back({(int)j, r, 0});
+        // counts of every (row part, entry part) pair from one walk of each row
+        // chunk: K - 1 binary searches per row split it at every part boundary
+        std::vector<int64_t> part_chunk(K + 1, 0);  // first row chunk of each part
+        for (int a = 0; a < K; ++a) part_chunk[a + 1] = part_chunk[a] + ceil_div(start[a + 1] - start[a], kChunkRows);
+        std::vector<int64_t> pcount((size_t)part_chunk[K] * K, 0);  // [row chunk][entry part]
+        {
+            std::vector<std::pair<int, int64_t>> rchunks;  // (part, first row offset)
+            for (int a = 0; a < K; ++a)
+                for (int64_t r = 0; r < start[a + 1] - start[a]; r += kChunkRows) rchunks.push_back({a, r});
+            std::atomic<size_t> next{0};
+            auto work = [&]() {
+                std::vector<int64_t> c(K);
+                for (size_t k = next.fetch_add(1); k < rchunks.size(); k = next.fetch_add(1)) {
+                    const int a = rchunks[k].first;
+                    const int64_t r0 = rchunks[k].second, r1 = std::min(r0 + kChunkRows, start[a + 1] - start[a]);
+                    std::fill(c.begin(), c.end(), 0);
+                    for (int64_t r = r0; r < r1; ++r) {
+                        const int64_t u = start[a] + r;
+                        const int32_t *row = col + rowptr[u], *end = col + rowptr[u + 1];
+                        const int32_t *prev = row;
+                        for (int b = 0; b < K; ++b) {
+                            const int32_t *nx = b + 1 < K ? std::lower_bound(prev, end, (int32_t)start[b + 1]) : end;
+                            c[b] += nx - prev;
+                            prev = nx;
+                        }
+                    }
+                    for (int b = 0; b < K; ++b) pcount[(size_t)k * K + b] = c[b];
+                }
+            };
+            std::vector<std::thread> th;
+            for (int t = 1; t < nt; ++t) th.emplace_back(work);
+            work();
+            for (auto &x : th) x.join();
+        }
+        for (size_t k = 0; k < items.size(); ++k) {  // items are grouped by side, in row order
+            Side &sd = sides[items[k].side];
+            const int64_t rc = part_chunk[sd.pa] + items[k].r0 / kChunkRows;
+            items[k].off = sd.entries;
+            sd.entries += pcount[(size_t)rc * K + sd.pb];
+        }
+        total_bytes = 0;
+        max_block = 0;
+        for (size_t i = 0; i < blocks.size(); ++i) {
+            Block &B = blocks[i];
+            const int a = order[i].first, b = order[i].second;
+            const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
+            for (const Side &sd : sides)
+                if (sd.blk == (int)i) (sd.ab ? B.m_ab : B.m_ba) = sd.entries;
+            B.bytes = al(sizeof(int64_t) * (na + 1)) + al(sizeof(int32_t) * B.m_ab) +
+                      al(a != b ? sizeof(int64_t) * (nb + 1) : 0) + al(sizeof(int32_t) * B.m_ba);
+            max_block = std::max(max_block, B.bytes);
+            total_bytes += B.bytes;
+        }
+    }
+
+    void place(char *base) {
+        size_t off = 0;
+        for (size_t i = 0; i < blocks.size(); ++i) {
+            Block &B = blocks[i];
+            const int a = order[i].first, b = order[i].second;
+            const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
+            B.base = base + off;
+            off += B.bytes;
+            B.rp_ab = reinterpret_cast<int64_t *>(B.base);
+            B.col_ab = reinterpret_cast<int32_t *>(B.base + al(sizeof(int64_t) * (na + 1)));
+            B.rp_ba = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(B.col_ab) + al(sizeof(int32_t) * B.m_ab));
+            B.col_ba = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(B.rp_ba) +
+                                                   al(a != b ? sizeof(int64_t) * (nb + 1) : 0));
+        }
+    }
+
+    void fill(size_t k) const {
+        const Item &it = items[k];
+        const Side &sd = sides[it.side];
+        const Block &B = blocks[sd.blk];
+        int32_t *out = sd.ab ? B.col_ab : B.col_ba;
+        int64_t *rp = sd.ab ? B.rp_ab : B.rp_ba;
+        const int64_t r1 = std::min(it.r0 + kChunkRows, sd.a1 - sd.a0);
+        const int32_t b0 = (int32_t)sd.b0;
+        int64_t at = it.off;
+        for (int64_t r = it.r0; r < r1; ++r) {
+            const int32_t *lo, *hi;
+            row_range(sd, r, &lo, &hi);
+            rp[r] = at;
+            for (const int32_t *q = lo; q < hi; ++q) out[at++] = *q - b0;
+        }
+        if (r1 == sd.a1 - sd.a0) rp[r1] = at;  // the side's last chunk closes its row pointer
+    }
+};
+
 // The bin that holds part x for kernel i of seq: the bin already holding it
 // (*load = false), else (*load = true) an empty bin, else the bin whose part
 // is next used farthest ahead in seq.  A bin holding a part of kernel i is
@@ -374,6 +521,40 @@ int gosh_large_plan(int64_t n, int K, int p_gpu, int rounds, int evict, int *pai
     return (int)seq.size();
 }
 
+gosh_status gosh_large_block(const gosh_csr *g, int K, int a, int b, int64_t *m_ab, int64_t *m_ba, int64_t *rp_ab,
+                             int32_t *col_ab, int64_t *rp_ba, int32_t *col_ba) {
+    clear_error();
+    GOSH_CHECK_ARG(g && !g->on_device && g->rowptr && g->col, "needs a host CSR");
+    GOSH_CHECK_ARG(g->n >= 1 && g->n < (int64_t(1) << 31), "bad n");
+    GOSH_CHECK_ARG(K >= 1 && K <= g->n, "need 1 <= K <= n");
+    GOSH_CHECK_ARG(0 <= b && b <= a && a < K, "need 0 <= b <= a < K");
+    GOSH_CHECK_ARG(m_ab && m_ba, "m_ab and m_ba are required");
+    GOSH_TRY(check_host_csr(g->rowptr, g->col, g->n, false));
+    std::vector<int64_t> start(K + 1);
+    for (int i = 0; i <= K; ++i) start[i] = g->n * i / K;
+    EdgeBlocks eb;
+    eb.plan(g->rowptr, g->col, K, start, 1);
+    const size_t i = (size_t)a * (a + 1) / 2 + b;  // position of (a, b) in the inside-out order
+    GOSH_CHECK_ARG(eb.order[i] == std::make_pair(a, b), "pair order mismatch");
+    *m_ab = eb.blocks[i].m_ab;
+    *m_ba = eb.blocks[i].m_ba;
+    if (!rp_ab) return GOSH_OK;  // sizes only
+    GOSH_CHECK_ARG(col_ab && (a == b || (rp_ba && col_ba)), "NULL output");
+    std::vector<char> region(eb.total_bytes);
+    eb.place(region.data());
+    for (size_t k = 0; k < eb.items.size(); ++k)
+        if (eb.sides[eb.items[k].side].blk == (int)i) eb.fill(k);
+    const Block &B = eb.blocks[i];
+    const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
+    std::memcpy(rp_ab, B.rp_ab, sizeof(int64_t) * (na + 1));
+    std::memcpy(col_ab, B.col_ab, sizeof(int32_t) * B.m_ab);
+    if (a != b) {
+        std::memcpy(rp_ba, B.rp_ba, sizeof(int64_t) * (nb + 1));
+        std::memcpy(col_ba, B.col_ba, sizeof(int32_t) * B.m_ba);
+    }
+    return GOSH_OK;
+}
+
 gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int epochs, const gosh_params *p,
                                    void *stream, gosh_large_stats *stats) {
     clear_error();
@@ -418,113 +599,15 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     // costs far more than building), and the row pointers and entries (local
     // ids) are written straight into it by the threads that overlap the
     // stream loop below.
-    std::vector<std::pair<int, int>> order;
-    large_pair_order(K, order);
-    std::vector<Block> blocks(order.size());
-    size_t max_block = 0;
-    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    struct Side {
-        int blk;
-        bool ab;
-        int pa, pb;  // parts of the rows and of the entries
-        int64_t a0, a1, b0, b1;
-        int64_t entries;
-    };
-    std::vector<Side> sides;
-    for (size_t i = 0; i < order.size(); ++i) {
-        const int a = order[i].first, b = order[i].second;
-        sides.push_back({(int)i, true, a, b, start[a], start[a + 1], start[b], start[b + 1], 0});
-        if (a != b) sides.push_back({(int)i, false, b, a, start[b], start[b + 1], start[a], start[a + 1], 0});
-    }
-    constexpr int64_t kChunkRows = 32768;
-    struct Item {
-        int side;
-        int64_t r0;   // first row offset in the side
-        int64_t off;  // entries of the side before this chunk
-    };
-    std::vector<Item> items;
-    for (size_t j = 0; j < sides.size(); ++j)
-        for (int64_t r = 0; r < sides[j].a1 - sides[j].a0; r += kChunkRows) items.push_back({(int)j, r, 0});
     const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    auto row_range = [&](const Side &sd, int64_t r, const int32_t **lo, const int32_t **hi) {
-        const int64_t u = sd.a0 + r;
-        const int32_t *row = g->col + g->rowptr[u], *end = g->col + g->rowptr[u + 1];
-        *lo = std::lower_bound(row, end, (int32_t)sd.b0);
-        *hi = std::lower_bound(*lo, end, (int32_t)sd.b1);
-    };
-    // counts of every (row part, entry part) pair from one walk of each row
-    // chunk: K - 1 binary searches per row split it at every part boundary
-    std::vector<int64_t> part_chunk(K + 1, 0);  // first row chunk of each part
-    for (int a = 0; a < K; ++a) part_chunk[a + 1] = part_chunk[a] + ceil_div(start[a + 1] - start[a], kChunkRows);
-    std::vector<int64_t> pcount((size_t)part_chunk[K] * K, 0);  // [row chunk][entry part]
-    {
-        std::vector<std::pair<int, int64_t>> rchunks;  // (part, first row offset)
-        for (int a = 0; a < K; ++a)
-            for (int64_t r = 0; r < start[a + 1] - start[a]; r += kChunkRows) rchunks.push_back({a, r});
-        std::atomic<size_t> next{0};
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t)
-            th.emplace_back([&]() {
-                std::vector<int64_t> c(K);
-                for (size_t k = next.fetch_add(1); k < rchunks.size(); k = next.fetch_add(1)) {
-                    const int a = rchunks[k].first;
-                    const int64_t r0 = rchunks[k].second, r1 = std::min(r0 + kChunkRows, start[a + 1] - start[a]);
-                    std::fill(c.begin(), c.end(), 0);
-                    for (int64_t r = r0; r < r1; ++r) {
-                        const int64_t u = start[a] + r;
-                        const int32_t *row = g->col + g->rowptr[u], *end = g->col + g->rowptr[u + 1];
-                        const int32_t *prev = row;
-                        for (int b = 0; b < K; ++b) {
-                            const int32_t *nx = b + 1 < K ? std::lower_bound(prev, end, (int32_t)start[b + 1]) : end;
-                            c[b] += nx - prev;
-                            prev = nx;
-                        }
-                    }
-                    for (int b = 0; b < K; ++b) pcount[(size_t)k * K + b] = c[b];
-                }
-            });
-        for (auto &x : th) x.join();
-    }
-    std::vector<int64_t> chunk_count(items.size(), 0);
-    for (size_t k = 0; k < items.size(); ++k) {
-        const Side &sd = sides[items[k].side];
-        const int64_t rc = part_chunk[sd.pa] + items[k].r0 / kChunkRows;
-        chunk_count[k] = pcount[(size_t)rc * K + sd.pb];
-    }
-    for (size_t k = 0; k < items.size(); ++k) {  // items are grouped by side, in row order
-        Side &sd = sides[items[k].side];
-        items[k].off = sd.entries;
-        sd.entries += chunk_count[k];
-    }
-    size_t total_bytes = 0;
-    for (size_t i = 0; i < blocks.size(); ++i) {
-        Block &B = blocks[i];
-        const int a = order[i].first, b = order[i].second;
-        const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
-        for (const Side &sd : sides)
-            if (sd.blk == (int)i) (sd.ab ? B.m_ab : B.m_ba) = sd.entries;
-        B.bytes = al(sizeof(int64_t) * (na + 1)) + al(sizeof(int32_t) * B.m_ab) +
-                  al(a != b ? sizeof(int64_t) * (nb + 1) : 0) + al(sizeof(int32_t) * B.m_ba);
-        max_block = std::max(max_block, B.bytes);
-        total_bytes += B.bytes;
-    }
+    EdgeBlocks eb;
+    eb.plan(g->rowptr, g->col, K, start, nt);
+    const std::vector<std::pair<int, int>> &order = eb.order;
+    const std::vector<Block> &blocks = eb.blocks;
+    const size_t max_block = eb.max_block;
     PinnedLease lease(g_pinned);
-    GOSH_TRY(lease.acquire(total_bytes, "edge blocks"));
-    {
-        size_t off = 0;
-        for (size_t i = 0; i < blocks.size(); ++i) {
-            Block &B = blocks[i];
-            const int a = order[i].first, b = order[i].second;
-            const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
-            B.base = lease.ptr + off;
-            off += B.bytes;
-            B.rp_ab = reinterpret_cast<int64_t *>(B.base);
-            B.col_ab = reinterpret_cast<int32_t *>(B.base + al(sizeof(int64_t) * (na + 1)));
-            B.rp_ba = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(B.col_ab) + al(sizeof(int32_t) * B.m_ab));
-            B.col_ba = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(B.rp_ba) +
-                                                   al(a != b ? sizeof(int64_t) * (nb + 1) : 0));
-        }
-    }
+    GOSH_TRY(lease.acquire(eb.total_bytes, "edge blocks"));
+    eb.place(lease.ptr);
     int64_t part_rows = 0;
     for (int i = 0; i < K; ++i) part_rows = std::max(part_rows, start[i + 1] - start[i]);
     const size_t bin_bytes = row * part_rows;
@@ -540,7 +623,7 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     // first copy to the device waits only for block i (the items are ordered
     // by block, so the first blocks finish first).
     std::vector<int> items_left(blocks.size(), 0);
-    for (const auto &it : items) ++items_left[sides[it.side].blk];
+    for (const auto &it : eb.items) ++items_left[eb.sides[it.side].blk];
     struct BlockGate {
         std::mutex mu;
         std::condition_variable cv;
@@ -558,26 +641,13 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     gate.left = items_left;
     for (int t = 0; t < nt; ++t)
         gate.th.emplace_back([&]() {
-            for (size_t k = gate.next.fetch_add(1); k < items.size(); k = gate.next.fetch_add(1)) {
-                const Item &it = items[k];
-                const Side &sd = sides[it.side];
-                Block &B = blocks[sd.blk];
-                int32_t *out = sd.ab ? B.col_ab : B.col_ba;
-                int64_t *rp = sd.ab ? B.rp_ab : B.rp_ba;
-                const int64_t r1 = std::min(it.r0 + kChunkRows, sd.a1 - sd.a0);
-                const int32_t b0 = (int32_t)sd.b0;
-                int64_t at = it.off;
-                for (int64_t r = it.r0; r < r1; ++r) {
-                    const int32_t *lo, *hi;
-                    row_range(sd, r, &lo, &hi);
-                    rp[r] = at;
-                    for (const int32_t *q = lo; q < hi; ++q) out[at++] = *q - b0;
-                }
-                if (r1 == sd.a1 - sd.a0) rp[r1] = at;  // the side's last chunk closes its row pointer
+            for (size_t k = gate.next.fetch_add(1); k < eb.items.size(); k = gate.next.fetch_add(1)) {
+                eb.fill(k);
+                const int blk = eb.sides[eb.items[k].side].blk;
                 bool done;
                 {
                     std::lock_guard<std::mutex> lk(gate.mu);
-                    done = --gate.left[sd.blk] == 0;
+                    done = --gate.left[blk] == 0;
                 }
                 if (done) gate.cv.notify_all();
             }

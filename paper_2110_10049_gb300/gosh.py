@@ -109,6 +109,7 @@ def lib() -> C.CDLL:
             "gosh_walk_pairs": [P(gosh_csr), i32, i32, i32, i32, u64, u64, vp],
             "gosh_walk_order": [i64, i32, i32, u64, u64, vp],
             "gosh_large_plan": [i64, i32, i32, i32, i32, vp, vp, i32],
+            "gosh_large_block": [P(gosh_csr), i32, i32, i32, vp, vp, vp, vp, vp, vp],
             "gosh_mlp_create": [i32, i32, u64, P(vp)],
             "gosh_mlp_get_weights": [vp, vp, vp, vp, vp],
             "gosh_mlp_set_weights": [vp, vp, vp, vp, vp],
@@ -383,6 +384,33 @@ def gosh_train_level_walks(rowptr, col, M, level, epochs, params: gosh_params, n
                                                                   C.byref(params), _stream(stream),
                                                                   _ptr(n_updates), C.byref(st)))
     return {f: getattr(st, f) for f, _ in gosh_walk_stats._fields_}
+
+
+def gosh_large_block(rowptr, col, K, a, b):
+    """The LargeGraphGPU edge block of part pair (a, b) as the library builds
+    it (host only): (rp_ab, col_ab, rp_ba, col_ba), the ba side None when
+    a == b."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    n = len(rowptr) - 1
+    cg = gosh_csr(n, rowptr.ctypes.data, col.ctypes.data, 0)
+    m_ab, m_ba = C.c_int64(0), C.c_int64(0)
+    _check("gosh_large_block", lib().gosh_large_block(C.byref(cg), K, a, b, C.byref(m_ab), C.byref(m_ba),
+                                                      None, None, None, None))
+    na = n * (a + 1) // K - n * a // K
+    nb = n * (b + 1) // K - n * b // K
+    rp_ab = np.zeros(na + 1, np.int64)
+    col_ab = np.zeros(max(m_ab.value, 1), np.int32)
+    rp_ba = np.zeros(nb + 1, np.int64)
+    col_ba = np.zeros(max(m_ba.value, 1), np.int32)
+    _check("gosh_large_block", lib().gosh_large_block(C.byref(cg), K, a, b, C.byref(m_ab), C.byref(m_ba),
+                                                      rp_ab.ctypes.data, col_ab.ctypes.data, rp_ba.ctypes.data,
+                                                      col_ba.ctypes.data))
+    if a == b:
+        return rp_ab, col_ab[:m_ab.value], None, None
+    return rp_ab, col_ab[:m_ab.value], rp_ba, col_ba[:m_ba.value]
 
 
 def gosh_release_host_buffers() -> int:
