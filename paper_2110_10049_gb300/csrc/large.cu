@@ -591,14 +591,11 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     for (int i = 0; i <= K; ++i) start[i] = n * i / K;
 
     // ---- edge blocks (pinned, built on host threads) ----
-    // A block side (u in V^a, entries in V^b) is built in row chunks spread
-    // over every host thread.  Up front only the entries of each chunk are
-    // counted (two binary searches per row for the sub-range of its sorted
-    // row that falls in V^b); the chunks' offsets then place every block in
-    // one pinned region (kept across calls, grow-only: pinning host memory
-    // costs far more than building), and the row pointers and entries (local
-    // ids) are written straight into it by the threads that overlap the
-    // stream loop below.
+    // Only the count pass and the layout run up front (EdgeBlocks::plan);
+    // the blocks then sit in one pinned region (kept across calls,
+    // grow-only: pinning host memory costs far more than building), and
+    // their row chunks are filled by the threads that overlap the stream
+    // loop below.
     const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     EdgeBlocks eb;
     eb.plan(g->rowptr, g->col, K, start, nt);
