@@ -94,6 +94,9 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+            self.t.join(timeout=1.0)
+            if self.proc.stdout:
+                self.proc.stdout.close()
 
     def summary(self):
         sm, mx, reasons = [], None, set()
