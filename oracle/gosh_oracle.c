@@ -198,56 +198,70 @@ void orc_train_sequential(int64_t n, const int64_t *rowptr, const int32_t *col,
  *     base(x) + c_1 + c_2 + ...     (summed left to right)
  * with base(x) = r_x if x is a source of the batch, else S[x], and the
  * contributions to x taken in order of (source ascending, sample ascending).
+ *
+ * orc_det_batch applies one batch [b0, b1) whose samples are given:
+ * samples[(v-b0)*(k+1) + t] is sample t of source v (t = 0 the positive,
+ * b = 1; t >= 1 negatives, b = 0; -1 = skipped).  The NLL of every applied
+ * update is added to *loss (nullable) in update order; *n_applied
+ * (nullable) is incremented.
  */
+void orc_det_batch(double *M, int d, int64_t b0, int64_t b1, int k, const int32_t *samples, double lrj,
+                   double *loss, int64_t *n_applied) {
+    const int64_t m = b1 - b0;
+    int64_t applied = 0;
+    /* M itself is the snapshot S: nothing writes M until the batch ends. */
+    double *R = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * d);            /* r of each source */
+    double *C = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * (k + 1) * d);  /* contributions */
+    double *rows = (double *)malloc(sizeof(double) * (size_t)(k + 1) * d);                  /* private sample rows */
+    for (int64_t v = b0; v < b1; ++v) {
+        double *r = R + (v - b0) * d;
+        memcpy(r, M + v * d, sizeof(double) * d);
+        const int32_t *u = samples + (v - b0) * (k + 1);
+        for (int t = 0; t <= k; ++t) {
+            if (u[t] < 0) continue;
+            double *row = rows + t * d;
+            int prev = -1;
+            for (int s = 0; s < t; ++s) if (u[s] == u[t]) prev = s;
+            memcpy(row, prev >= 0 ? rows + prev * d : M + (int64_t)u[t] * d, sizeof(double) * d);
+            double x = orc_update_embed(r, row, d, t == 0, lrj);
+            /* the sample row received row + r_new * score: record r_new * score */
+            double score = ((double)(t == 0) - sigmoid(x)) * lrj;
+            double *c = C + ((v - b0) * (k + 1) + t) * d;
+            for (int q = 0; q < d; ++q) c[q] = r[q] * score;
+            if (loss) *loss += orc_sample_loss(x, t == 0);
+            ++applied;
+        }
+    }
+    /* write back: bases of the sources first, then contributions in order */
+    for (int64_t v = b0; v < b1; ++v) memcpy(M + v * d, R + (v - b0) * d, sizeof(double) * d);
+    for (int64_t i = 0; i < m * (k + 1); ++i) {
+        int32_t x = samples[i];
+        if (x < 0) continue;
+        const double *c = C + i * d;
+        for (int q = 0; q < d; ++q) M[(int64_t)x * d + q] = M[(int64_t)x * d + q] + c[q];
+    }
+    free(R); free(C); free(rows);
+    if (n_applied) *n_applied += applied;
+}
+
 void orc_train_deterministic(int64_t n, const int64_t *rowptr, const int32_t *col,
                              double *M, int d, int k, int level, int epochs,
                              double lr, double lr_floor, uint64_t seed, uint64_t graph,
                              int64_t m, double *loss_per_epoch, int64_t *n_updates) {
-    int32_t u[64];
     int64_t applied = 0;
-    /* M itself is the snapshot S: nothing writes M until the batch ends. */
-    double *R = (double *)malloc(sizeof(double) * (size_t)m * d);            /* r of each source */
-    double *C = (double *)malloc(sizeof(double) * (size_t)m * (k + 1) * d);  /* contributions */
     int32_t *tgt = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * (k + 1));
-    double *rows = (double *)malloc(sizeof(double) * (size_t)(k + 1) * d);   /* private sample rows */
     for (int j = 0; j < epochs; ++j) {
         double lrj = orc_epoch_lr(lr, lr_floor, j, epochs);
         double loss = 0.0;
         for (int64_t b0 = 0; b0 < n; b0 += m) {
             int64_t b1 = b0 + m < n ? b0 + m : n;
-            for (int64_t v = b0; v < b1; ++v) {
-                double *r = R + (v - b0) * d;
-                memcpy(r, M + v * d, sizeof(double) * d);
-                orc_draw_samples(n, rowptr, col, k, level, j, seed, graph, v, u);
-                for (int t = 0; t <= k; ++t) {
-                    int64_t slot = (v - b0) * (k + 1) + t;
-                    tgt[slot] = u[t];
-                    if (u[t] < 0) continue;
-                    double *row = rows + t * d;
-                    int prev = -1;
-                    for (int s = 0; s < t; ++s) if (u[s] == u[t]) prev = s;
-                    memcpy(row, prev >= 0 ? rows + prev * d : M + (int64_t)u[t] * d, sizeof(double) * d);
-                    double x = orc_update_embed(r, row, d, t == 0, lrj);
-                    /* the sample row received row + r_new * score: record r_new * score */
-                    double score = ((double)(t == 0) - sigmoid(x)) * lrj;
-                    double *c = C + slot * d;
-                    for (int q = 0; q < d; ++q) c[q] = r[q] * score;
-                    loss += orc_sample_loss(x, t == 0);
-                    ++applied;
-                }
-            }
-            /* write back: bases of the sources first, then contributions in order */
-            for (int64_t v = b0; v < b1; ++v) memcpy(M + v * d, R + (v - b0) * d, sizeof(double) * d);
-            for (int64_t i = 0; i < (b1 - b0) * (k + 1); ++i) {
-                int32_t x = tgt[i];
-                if (x < 0) continue;
-                const double *c = C + i * d;
-                for (int q = 0; q < d; ++q) M[(int64_t)x * d + q] = M[(int64_t)x * d + q] + c[q];
-            }
+            for (int64_t v = b0; v < b1; ++v)
+                orc_draw_samples(n, rowptr, col, k, level, j, seed, graph, v, tgt + (v - b0) * (k + 1));
+            orc_det_batch(M, d, b0, b1, k, tgt, lrj, &loss, &applied);
         }
         if (loss_per_epoch) loss_per_epoch[j] = loss;
     }
-    free(R); free(C); free(tgt); free(rows);
+    free(tgt);
     if (n_updates) *n_updates = applied;
 }
 
@@ -569,19 +583,18 @@ void orc_train_walks(int64_t n, const int64_t *rowptr, const int32_t *col, doubl
 /*  - rounds r = 0 .. ceil(e/B)-1; each round visits the part pairs (a, b),   */
 /*    a >= b, in row-major lower-triangle order (Sec. 5.1);                  */
 /*  - in pair (a, b) the sources are the vertices of V^a, then (a != b) those */
-/*    of V^b; a source u draws B positives uniformly from its neighbours in  */
-/*    the opposite part, each followed by k negatives uniform over the        */
-/*    opposite part (a negative equal to u is skipped when a == b); positive */
-/*    j of round r uses Philox block (u, blk, level<<32 | (r*B+j), tag) with */
-/*    tag = TAG_SAMPLE for K = 1, else 3 | ((a*K+b) << 8), word 0 for the     */
-/*    positive and words 1..k for the negatives, and the rate                 */
+/*    of V^b, in id order; a source u draws B positives uniformly from its    */
+/*    neighbours in the opposite part, each followed by k negatives uniform   */
+/*    over the opposite part (a negative equal to u is skipped when a == b);  */
+/*    positive j of round r uses Philox block (u, blk, level<<32 | (r*B+j),   */
+/*    tag) with tag = TAG_SAMPLE for K = 1, else 3 | ((a*K+b) << 8), word 0   */
+/*    for the positive and words 1..k for the negatives, and the rate         */
 /*    lr * max(1 - (r*B+j)/e, lr_floor);                                      */
-/*  - a global count of positives stops at e*|V|: sources are taken in tiles */
-/*    of 32; a tile's sources claim their positives in order, and a slot     */
-/*    group j of a source is dropped (positive and negatives) once the       */
-/*    source's claimed positives before it plus j reach what the tile may    */
-/*    still take.  A source without a neighbour in the opposite part claims  */
-/*    none (its negatives still count against the tile's limit).             */
+/*  - "a global counter" of positive updates bounds the work at e*|V|: the   */
+/*    count rises by one with every positive applied, and once it has        */
+/*    reached e*|V| every later slot group (a positive with its negatives)   */
+/*    is dropped.  A source without a neighbour in the opposite part has no  */
+/*    positive; its negatives are applied while the count is below the cap. */
 /* ------------------------------------------------------------------------ */
 enum { TAG_LARGE = 3 };
 
@@ -590,33 +603,22 @@ void orc_train_large(int64_t n, const int64_t *rowptr, const int32_t *col, doubl
                      int64_t *n_updates, int64_t *n_positives) {
     uint64_t key[2] = {seed, graph};
     const int rounds = (epochs + B - 1) / B;
-    const int ns = B * (k + 1);
     const uint64_t cap = (uint64_t)epochs * (uint64_t)n;
-    uint64_t counter = 0;
+    uint64_t count = 0;  /* positives applied */
     int64_t applied = 0;
     int64_t *start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(K + 1));
     for (int i = 0; i <= K; ++i) start[i] = n * i / K;
-    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * 32 * (size_t)ns);
-    double *lrs = (double *)malloc(sizeof(double) * 32 * (size_t)B);
-    int *npos = (int *)malloc(sizeof(int) * 32);
     for (int r = 0; r < rounds; ++r) {
         for (int a = 0; a < K; ++a) {
             for (int b = 0; b <= a; ++b) {
                 const int same = a == b;
                 const uint64_t tag = K == 1 ? (uint64_t)TAG_SAMPLE : ((uint64_t)TAG_LARGE | ((uint64_t)(a * K + b) << 8));
-                const int64_t na = start[a + 1] - start[a], nb = start[b + 1] - start[b];
-                const int64_t nsrc = na + (same ? 0 : nb);
-                for (int64_t s0 = 0; s0 < nsrc; s0 += 32) {
-                    const int cnt_t = (int)(nsrc - s0 < 32 ? nsrc - s0 : 32);
-                    int tile_pos = 0;
-                    /* draws of the tile's sources */
-                    for (int q = 0; q < cnt_t; ++q) {
-                        const int64_t s = s0 + q;
-                        const int sideA = s < na;
-                        const int64_t u = sideA ? s : s - na;
-                        const int64_t own0 = sideA ? start[a] : start[b];
-                        const int64_t opp0 = sideA ? start[b] : start[a], opp1 = sideA ? start[b + 1] : start[a + 1];
-                        const int64_t ug = own0 + u;
+                for (int side = 0; side < (same ? 1 : 2); ++side) {
+                    /* side 0: sources in V^a against V^b; side 1: V^b against V^a */
+                    const int64_t own0 = side == 0 ? start[a] : start[b], own1 = side == 0 ? start[a + 1] : start[b + 1];
+                    const int64_t opp0 = side == 0 ? start[b] : start[a], opp1 = side == 0 ? start[b + 1] : start[a + 1];
+                    for (int64_t ug = own0; ug < own1; ++ug) {
+                        const int64_t u = ug - own0;
                         /* neighbours of ug inside the opposite part: a sorted sub-range of its row */
                         int64_t lo = rowptr[ug], hi = rowptr[ug + 1];
                         while (lo < hi && col[lo] < opp0) ++lo;
@@ -624,57 +626,33 @@ void orc_train_large(int64_t n, const int64_t *rowptr, const int32_t *col, doubl
                         while (e < hi && col[e] < opp1) ++e;
                         const int64_t cnt = e - lo;
                         for (int j = 0; j < B; ++j) {
+                            if (count >= cap) continue;  /* budget spent: the group is dropped */
                             const uint32_t t = (uint32_t)(r * B + j);
+                            const double lrt = orc_epoch_lr(lr, lr_floor, (int)t, epochs);
                             uint64_t w[64];
                             for (int blk = 0; blk * 4 < k + 1; ++blk) {
                                 uint64_t ctr[4] = {(uint64_t)ug, (uint64_t)blk, ((uint64_t)(uint32_t)level << 32) | t, tag};
                                 orc_philox4x64(ctr, key, w + 4 * blk);
                             }
-                            for (int m = 0; m <= k; ++m) {
-                                int32_t id;
-                                if (m == 0) {
-                                    id = cnt > 0 ? (int32_t)(col[lo + (int64_t)uniform_below(w[0], (uint64_t)cnt)] - opp0) : -1;
-                                } else {
-                                    const int64_t x = (int64_t)uniform_below(w[m], (uint64_t)(opp1 - opp0));
-                                    id = (same && x == u) ? -1 : (int32_t)x;
-                                }
-                                ids[q * ns + j * (k + 1) + m] = id;
+                            if (cnt > 0) {
+                                const int64_t v = col[lo + (int64_t)uniform_below(w[0], (uint64_t)cnt)];
+                                orc_update_embed(M + ug * d, M + v * d, d, 1, lrt);
+                                ++applied;
+                                ++count;
                             }
-                            lrs[q * B + j] = orc_epoch_lr(lr, lr_floor, (int)t, epochs);
+                            for (int m = 1; m <= k; ++m) {
+                                const int64_t x = (int64_t)uniform_below(w[m], (uint64_t)(opp1 - opp0));
+                                if (same && x == u) continue;
+                                orc_update_embed(M + ug * d, M + (opp0 + x) * d, d, 0, lrt);
+                                ++applied;
+                            }
                         }
-                        npos[q] = cnt > 0 ? B : 0;
-                        tile_pos += npos[q];
-                    }
-                    /* the tile's share of the global positive count */
-                    const uint64_t old = counter;
-                    counter += (uint64_t)tile_pos;
-                    const int64_t allowed = old >= cap ? 0 : (int64_t)(cap - old < (uint64_t)tile_pos ? cap - old : (uint64_t)tile_pos);
-                    /* updates, source by source */
-                    int first = 0;
-                    for (int q = 0; q < cnt_t; ++q) {
-                        const int64_t s = s0 + q;
-                        const int sideA = s < na;
-                        const int64_t u = sideA ? s : s - na;
-                        const int64_t ug = (sideA ? start[a] : start[b]) + u;
-                        const int64_t opp0 = sideA ? start[b] : start[a];
-                        for (int slot = 0; slot < ns; ++slot) {
-                            const int jj = slot / (k + 1);
-                            const int32_t id = ids[q * ns + slot];
-                            if (id < 0 || first + jj >= allowed) continue;
-                            const int bpos = slot % (k + 1) == 0;
-                            orc_update_embed(M + ug * d, M + (opp0 + id) * d, d, bpos, lrs[q * B + jj]);
-                            ++applied;
-                        }
-                        first += npos[q];
                     }
                 }
             }
         }
     }
     free(start);
-    free(ids);
-    free(lrs);
-    free(npos);
     if (n_updates) *n_updates = applied;
-    if (n_positives) *n_positives = (int64_t)(counter < cap ? counter : cap);
+    if (n_positives) *n_positives = (int64_t)count;
 }

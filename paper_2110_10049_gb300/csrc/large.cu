@@ -118,11 +118,17 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
         const int y = __shfl_up_sync(0xffffffffu, before, o);
         if (lane >= o) before += y;
     }
+    // The tile takes its positives from the global count in one addition; in
+    // source order, slot group jj of a source is dropped once the count before
+    // it (old + positives of earlier sources + jj if the source has positives)
+    // reaches the cap: exactly the sequential per-positive count when tiles
+    // claim in order.  A tile without positives still reads the count (adds 0),
+    // since its sources' negatives stop with the budget as well.
     const int tile_pos = __shfl_sync(0xffffffffu, before, 31);
     unsigned long long old = 0;
-    if (lane == 0 && tile_pos > 0) old = atomicAdd(a.positives, (unsigned long long)tile_pos);
+    if (lane == 0) old = atomicAdd(a.positives, (unsigned long long)tile_pos);
     old = __shfl_sync(0xffffffffu, old, 0);
-    const long long allowed = old >= a.cap ? 0 : (long long)std::min<unsigned long long>(a.cap - old, tile_pos);
+    const long long allowed = old >= a.cap ? 0 : (long long)(a.cap - old);
     const int my_first = before - npos;  // positives of this lane's source start here
     __syncwarp();
     // ---- updates ----
@@ -136,6 +142,7 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
         T *Mown = static_cast<T *>(sideA ? a.Ma : a.Mb);
         T *Mopp = static_cast<T *>(sideA ? a.Mb : a.Ma);
         const int first = __shfl_sync(0xffffffffu, my_first, j);
+        const bool has_pos = __shfl_sync(0xffffffffu, npos, j) > 0;
         const uint32_t sr = std::is_same<T, float>::value
                                 ? 0u
                                 : sr_source_seed(a.seed, a.graph ^ a.tag, a.level, (uint32_t)a.round, (sideA ? a.start_a : a.start_b) + u);
@@ -159,7 +166,7 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
                 const int t = p0 + x;
                 int32_t id = (active && t < ns) ? su[j * kMaxSlots + t] : -1;
                 const int jj = t / (a.k + 1);  // positive group of this slot
-                if (id >= 0 && first + jj >= allowed) id = -1;  // over the global cap
+                if (id >= 0 && first + (has_pos ? jj : 0) >= allowed) id = -1;  // over the global cap
                 us[x] = id;
             }
 #pragma unroll

@@ -9,8 +9,14 @@ method fixes independently of the code:
   of one, so the update count lies between the positives and (k+1) times
   them, and is (k+1) times them when no negative can hit its own source;
 - the library's host schedule (gosh_large_plan) visits the same
-  lower-triangle pair order as the oracle's reading of Sec. 5.1.
+  lower-triangle pair order as the oracle's reading of Sec. 5.1;
+- the global positive budget on stars cut into one-vertex parts, where every
+  draw is forced, equals the hand count of tests/golden/large_budget_hand.txt
+  (positives and updates, including the negatives of sources without a
+  positive while the budget lasts).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -56,3 +62,28 @@ def test_pair_order_matches_library_schedule(K):
     pairs, _ = g.gosh_large_plan(100, K, max(2, K), 1)
     expect = [(a, b) for a in range(K) for b in range(a + 1)]
     assert [tuple(p) for p in pairs.tolist()] == expect
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large_budget_hand.txt")
+
+
+def star(n):
+    return synth.csr_from_edges(n, np.zeros(n - 1, np.int64), np.arange(1, n), compact=False)
+
+
+def budget_cases():
+    out = []
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, K, B, k, e, npos, nup = line.split()
+        out.append((int(name[4:]), int(K), int(B), int(k), int(e), int(npos), int(nup)))
+    return out
+
+
+@pytest.mark.parametrize("n,K,B,k,e,npos,nup", budget_cases())
+def test_budget_hand_count(n, K, B, k, e, npos, nup):
+    gr = star(n)
+    M = oracle.init_uniform(n, 16, 0, 3)
+    got_u, got_p = oracle.train_large(gr.rowptr, gr.col, M, k, 0, e, 0.05, 1e-4, 7, K, B)
+    assert (got_p, got_u) == (npos, nup)
