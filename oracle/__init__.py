@@ -65,6 +65,7 @@ def lib():
                                             u64, u64, vp, vp]),
             "orc_train_deterministic": (None, [i64, vp, vp, vp, i32, i32, i32, i32, f64, f64,
                                                u64, u64, i64, vp, vp]),
+            "orc_det_batch": (None, [vp, i32, i64, i64, i32, vp, f64, vp, vp]),
             "orc_init_uniform": (None, [i64, i32, i32, u64, u64, vp]),
             "orc_degree_order": (None, [i64, vp, vp]),
             "orc_mec_map": (i64, [i64, vp, vp, vp]),
@@ -212,6 +213,18 @@ def train_deterministic(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, m,
     return loss[:epochs], int(nup[0])
 
 
+def det_batch(M, b0, b1, samples, lr):
+    """One snapshot batch of the deterministic mode on M (float64, in place)
+    with given samples: int32 [(b1-b0), k+1], column 0 the positive, -1 =
+    skipped.  Returns (summed loss, applied updates)."""
+    assert M.dtype == np.float64 and M.flags.c_contiguous
+    smp = np.ascontiguousarray(samples, dtype=np.int32)
+    nap = np.zeros(1, dtype=np.int64)
+    loss = np.zeros(1, dtype=np.float64)
+    lib().orc_det_batch(_p(M), M.shape[1], int(b0), int(b1), smp.shape[1] - 1, _p(smp), float(lr), _p(loss), _p(nap))
+    return float(loss[0]), int(nap[0])
+
+
 def init_uniform(n, d, level, seed, graph=0) -> np.ndarray:
     M = np.zeros((n, d), dtype=np.float64)
     lib().orc_init_uniform(n, d, level, seed, graph, _p(M))
@@ -289,6 +302,30 @@ def epoch_split(e: int, p: float, D: int) -> list[int]:
     return out
 
 
+def epoch_passes(e_i: int, n_i: int, nnz_i: int) -> int:
+    """Passes over V_i for e_i epochs of |E_i| updates each (Sec. 6's setup
+    defines one epoch as |E| updates; one Alg. 3 pass over V_i makes |V_i|
+    positive draws).  Reading: |E_i| counts CSR entries (both directions, the
+    count the density delta = |E_i|/|V_i| of Alg. 4 uses), the quotient
+    e_i*|E_i|/|V_i| is rounded half up, and a level given any epoch keeps at
+    least one pass."""
+    if e_i == 0:
+        return 0
+    from fractions import Fraction
+    q = Fraction(e_i * nnz_i, n_i)
+    return max(1, math.floor(q + Fraction(1, 2)))
+
+
+def level_epochs(e: int, p: float, sizes, nnzs, epoch_unit: str = "V") -> list[int]:
+    """Passes per level: the Sec. 3 split in epochs, then, for the |E| unit,
+    each level's epochs converted by epoch_passes."""
+    ep = epoch_split(e, p, len(sizes))
+    if epoch_unit == "V":
+        return ep
+    assert epoch_unit == "E"
+    return [epoch_passes(ep[i], sizes[i], nnzs[i]) for i in range(len(sizes))]
+
+
 def project_copy(mp, Mc) -> np.ndarray:
     mp = np.ascontiguousarray(mp, dtype=np.int32)
     Mc = np.ascontiguousarray(Mc, dtype=np.float64)
@@ -322,17 +359,18 @@ def link_auc(M, pos_pairs, neg_pairs) -> float:
 # Alg. 2 GOSH end to end (copy projection)
 # --------------------------------------------------------------------------
 def embed(rowptr, col, d, k, lr, e, p, seed, threshold=100, shrink=0.8, lr_floor=1e-4,
-          mode="sequential", det_batch=1, storage=np.float32, graph=0, coarsening=True):
+          mode="sequential", det_batch=1, storage=np.float32, graph=0, coarsening=True, epoch_unit="V"):
     """GOSH (Alg. 2) with every level D-1..0 trained (level 0 included: the
     algorithm returns M_0, and the single-level configuration must train).
     M_{D-1} starts from the init rounded to the storage precision; training
-    runs in FP64.  Returns (M_0, info)."""
+    runs in FP64.  epoch_unit "V": an epoch is one Alg. 3 pass over V_i; "E":
+    an epoch is |E_i| updates (Sec. 6), see epoch_passes.  Returns (M_0, info)."""
     if coarsening:
         graphs, maps = mec_hierarchy(rowptr, col, threshold, shrink)
     else:
         graphs, maps = [(np.asarray(rowptr, np.int64), np.asarray(col, np.int32))], []
     D = len(graphs)
-    ep = epoch_split(e, p, D)
+    ep = level_epochs(e, p, [len(g[0]) - 1 for g in graphs], [int(g[0][-1]) for g in graphs], epoch_unit)
     n_top = len(graphs[-1][0]) - 1
     M = init_uniform(n_top, d, D - 1, seed, graph).astype(storage).astype(np.float64)
     losses, updates = [], 0

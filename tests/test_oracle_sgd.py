@@ -2,17 +2,24 @@
 epoch split, projection and AUC.
 
 - deterministic mode with batch m = 1 is exactly the sequential epoch
-  (including repeated samples within a source);
+  (including repeated samples within a source); a batch of three sources
+  in which a source is another's sample and a row receives three changes
+  equals its hand-worked value (tests/golden/det_batch_hand.txt);
 - training lowers the per-epoch loss and fits the training edges; on a
   planted-partition graph it predicts held-out edges;
 - epoch split closed forms (Sec. 3);
 - copy projection preserves every coarse dot product on the fine pairs;
 - AUC equals the O(n+ n-) pair count and sklearn's roc_auc_score.
 """
+import math
+import os
+
 import numpy as np
 import pytest
 
 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def small_graph():
@@ -38,6 +45,21 @@ def test_det_repeated_samples_within_a_source(orc):
     orc.train_sequential(g.rowptr, g.col, A, 7, 0, 4, 0.3, 1e-4, 1)
     orc.train_deterministic(g.rowptr, g.col, B, 7, 0, 4, 0.3, 1e-4, 1, 1)
     np.testing.assert_array_equal(A, B)
+
+
+def test_det_batch_hand_worked(orc):
+    rows = {"S": [], "U": [], "M": []}
+    for line in open(os.path.join(GOLDEN, "det_batch_hand.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        tag, *vals = line.split()
+        rows[tag].append([float(x) for x in vals])
+    M = np.array(rows["S"], dtype=np.float64)
+    samples = np.array(rows["U"], dtype=np.int32)
+    loss, nap = orc.det_batch(M, 0, 3, samples, 0.5)
+    np.testing.assert_array_equal(M, np.array(rows["M"]))
+    assert nap == 5
+    assert abs(loss - 5 * math.log(2.0)) < 1e-15
 
 
 def test_det_large_batch_differs_but_converges_similarly(orc):
@@ -161,3 +183,79 @@ def test_embed_two_levels_follows_alg2(orc):
     R0 = R1[maps[0]].copy()
     orc.train_sequential(rp0, co0, R0, 3, 0, e0, 0.05, 1e-4, 6)
     np.testing.assert_array_equal(M, R0)
+
+
+# ----------------------------------------------------------------- |E| epochs
+@pytest.mark.parametrize("e,n,nnz,want", [
+    (0, 10, 50, 0),          # no epoch, no pass
+    (26, 2863, 42660, 387),  # 26 * 14.9 = 387.4 -> 387
+    (3, 4, 2, 2),            # 1.5 rounds half up -> 2
+    (1, 4, 1, 1),            # 0.25 -> 0, but a level given an epoch keeps one pass
+    (5, 7, 7, 5),            # density 1: passes = epochs
+    (2, 3, 5, 3),            # 10/3 = 3.33 -> 3
+    (7, 6, 15, 18),          # 17.5 -> 18 (half up)
+])
+def test_epoch_passes_hand_values(orc, e, n, nnz, want):
+    assert orc.epoch_passes(e, n, nnz) == want
+
+
+def test_epoch_passes_update_count(orc):
+    # e_i epochs of |E_i| positive draws: the passes make e_i*|E_i| draws to
+    # within half a pass
+    rng = np.random.default_rng(4)
+    for _ in range(500):
+        e, n = int(rng.integers(1, 2000)), int(rng.integers(1, 10 ** 6))
+        nnz = int(rng.integers(0, 60 * n))
+        q = orc.epoch_passes(e, n, nnz)
+        if e * nnz >= n / 2:
+            assert abs(q * n - e * nnz) <= n / 2
+        else:
+            assert q == 1
+
+
+def test_level_epochs_library_equals_oracle(orc):
+    # two independent statements of the schedule (the library's host entry
+    # gosh_level_epochs and the oracle's) agree on random hierarchies
+    from paper_2110_10049_gb300 import build, gosh as g
+    build.build()
+    rng = np.random.default_rng(9)
+    for _ in range(300):
+        D = int(rng.integers(1, 12))
+        n = np.sort(rng.integers(1, 10 ** 7, D))[::-1].copy()
+        nnz = (n * rng.uniform(0, 80, D)).astype(np.int64)
+        e, p = int(rng.integers(0, 3000)), float(rng.choice([0.0, 0.1, 0.3, 0.5, 1.0]))
+        for unit, name in ((0, "V"), (1, "E")):
+            want = orc.level_epochs(e, p, n.tolist(), nnz.tolist(), name)
+            assert g.gosh_level_epochs(e, p, D, unit, n, nnz) == want
+    with pytest.raises(g.GoshError):
+        g.gosh_level_epochs(10, 0.3, 2, 2, [5, 3], [10, 4])
+
+
+def train_edge_auc(orc, M, gr, seed=5):
+    src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
+    keep = src < gr.col
+    pos = np.stack([src[keep], gr.col[keep]], 1)
+    rng = np.random.default_rng(seed)
+    neg = rng.integers(0, gr.n, size=(len(pos), 2))
+    neg = neg[neg[:, 0] != neg[:, 1]]
+    return orc.link_auc(M, pos, neg)
+
+
+def test_oracle_learns_at_the_small_workload_schedule(orc):
+    """The schedule of the small workload (d=32, k=3, lr 0.045, e=200,
+    p=0.3) with epochs of |E_i| updates (Sec. 6): the FP64 oracle fits the
+    R-MAT scale-12 training edges (AUC >= 0.9) and, on the planted-partition
+    graph of the same size, predicts held-out edges (AUC >= 0.8); with
+    one-pass epochs (Alg. 3's unit) the same e leaves R-MAT near chance,
+    which is why the quality bars use the |E| unit."""
+    r = synth.workload("rmat12")
+    M, info = orc.embed(r.train.rowptr, r.train.col, 32, 3, 0.045, 200, 0.3, seed=1, epoch_unit="E")
+    assert info["epochs"][0] == orc.epoch_passes(orc.epoch_split(200, 0.3, info["levels"])[0],
+                                                 r.train.n, r.train.nnz)
+    assert train_edge_auc(orc, M, r.train) >= 0.9
+    Mv, _ = orc.embed(r.train.rowptr, r.train.col, 32, 3, 0.045, 200, 0.3, seed=1, epoch_unit="V")
+    assert train_edge_auc(orc, Mv, r.train) < 0.7
+    s = synth.workload("sbm12")
+    Ms, _ = orc.embed(s.train.rowptr, s.train.col, 32, 3, 0.045, 200, 0.3, seed=1, epoch_unit="E")
+    assert orc.link_auc(Ms, s.test_pos, s.test_neg) >= 0.8
+    assert train_edge_auc(orc, Ms, s.train) >= 0.9
