@@ -66,7 +66,7 @@ typedef struct gosh_params {
                                walks <= 3, LargeGraphGPU B * (k+1) <= 32) */
     double lr;              /* initial learning rate of every level */
     double lr_floor;        /* lr' = lr * max(1 - j/e_i, lr_floor); paper: 1e-4 */
-    int epochs;             /* e: total epochs over all levels (one epoch = one pass over V_i) */
+    int epochs;             /* e: total epochs over all levels (unit: epoch_unit) */
     double p;               /* smoothing ratio of the epoch split */
     int threshold;          /* coarsening stops once |V_i| <= threshold (paper: 100) */
     double shrink;          /* ... or once |V_{i+1}| > shrink * |V_i| (paper: 0.8) */
@@ -129,6 +129,11 @@ typedef struct gosh_params {
                                (default) serialises every epoch as the paper does.  Levels
                                trained in one cooperative launch, and calls that request
                                per-epoch losses, stay serialised. */
+    int epoch_unit;         /* unit of `epochs` in gosh_embed and gosh_embed_batch: 0 (default)
+                               one pass over V_i (Alg. 3); 1 |E_i| positive draws, the unit of
+                               the paper's experiments (Sec. 6 setup), so level i's e_i epochs
+                               run round(e_i * nnz_i / |V_i|) passes (gosh_level_epochs).
+                               gosh_train_level always counts passes. */
 } gosh_params;
 
 typedef struct gosh_walk_stats {
@@ -173,6 +178,20 @@ typedef struct gosh_hierarchy gosh_hierarchy;
  * e 200, p 0.3 (the "normal" row of the configuration table, Sec. 7),
  * threshold 100 and shrink 0.8 (Sec. 4), FP32 Hogwild, det_batch 4096. */
 gosh_status gosh_params_default(gosh_params *p);
+
+/* The epoch schedule of gosh_embed (Alg. 2, Sec. 3) for D graphs, host only:
+ * a fraction p of `epochs` spread uniformly over the levels and the rest
+ * geometrically (each level twice its finer neighbour),
+ *   e_i = floor(p*e/D + (1-p)*e*2^i/(2^D-1)) for i >= 1,  e_0 = e - sum of the others,
+ * then, with epoch_unit = 1 (|E_i| positive draws per epoch, the paper's
+ * experimental unit, Sec. 6), each e_i becomes floor((2 e_i nnz_i + n_i) /
+ * (2 n_i)) passes over V_i (nnz_i / n_i rounded half up), at least 1 when
+ * e_i >= 1.  n, nnz: host int64[D] (|V_i| >= 1 and CSR entries of G_i; read
+ * only with epoch_unit = 1, may be NULL otherwise); out: host int[D] passes.
+ * GOSH_ERR_INVALID_ARG for D < 1, epochs < 0, p outside [0, 1], an unknown
+ * unit, or a pass count beyond INT_MAX. */
+gosh_status gosh_level_epochs(int epochs, double p, int D, int epoch_unit, const int64_t *n, const int64_t *nnz,
+                              int *out);
 
 /* Thread-local message of the last failed call ("" if none). */
 const char *gosh_last_error(void);

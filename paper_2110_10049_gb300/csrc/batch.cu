@@ -272,20 +272,6 @@ const BatchKernel *find_batch(gosh_dtype dtype, int d, int lanes, int pass) {
     return nullptr;
 }
 
-void epoch_split(int e, double p, int D, int *out) {
-    if (D == 1) {
-        out[0] = e;
-        return;
-    }
-    const double denom = std::pow(2.0, D) - 1.0;
-    int rest = 0;
-    for (int i = 1; i < D; ++i) {
-        out[i] = (int)std::floor(p * e / D + (1.0 - p) * e * std::pow(2.0, i) / denom);
-        rest += out[i];
-    }
-    out[0] = e - rest;
-}
-
 // Device-resident schedule of the whole batch.
 struct Plan {
     std::vector<Phase> phases;
@@ -304,7 +290,7 @@ gosh_status build_plan(const std::vector<gosh_hierarchy *> &hs, const std::vecto
         const gosh_hierarchy *h = hs[gi];
         const int D = (int)h->n.size();
         std::vector<int> ep(D);
-        epoch_split(epochs, p.p, D, ep.data());
+        GOSH_TRY(level_epochs(epochs, p.p, D, p.epoch_unit, h->n.data(), h->nnz.data(), ep.data()));
         plan.first.push_back((int)plan.phases.size());
         auto items = [&](int64_t n) { return (n + rows_per_item - 1) / rows_per_item; };
         Phase init{};

@@ -284,22 +284,6 @@ gosh_status by_dtype(gosh_dtype t, F &&f) {
     return GOSH_ERR_INVALID_ARG;
 }
 
-// Epoch split of Sec. 3: fraction p uniform over the D levels, the rest
-// geometric (level i gets twice level i-1); levels >= 1 floor, level 0 the rest.
-void epoch_split(int e, double p, int D, int *out) {
-    if (D == 1) {
-        out[0] = e;
-        return;
-    }
-    const double denom = std::pow(2.0, D) - 1.0;
-    int rest = 0;
-    for (int i = 1; i < D; ++i) {
-        out[i] = (int)std::floor(p * e / D + (1.0 - p) * e * std::pow(2.0, i) / denom);
-        rest += out[i];
-    }
-    out[0] = e - rest;
-}
-
 struct EventTimer {
     cudaEvent_t a = nullptr, b = nullptr;
     cudaStream_t s;
@@ -357,6 +341,40 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 
+// Epoch schedule of Sec. 3 (see gosh_level_epochs): fraction p uniform over
+// the D levels, the rest geometric (level i gets twice level i-1), levels >= 1
+// floored and level 0 the remainder; with the |E| unit of Sec. 6 each level's
+// count is scaled by its density nnz_i / n_i, rounded half up in integers.
+gosh_status level_epochs(int e, double p, int D, int unit, const int64_t *n, const int64_t *nnz, int *out) {
+    GOSH_CHECK_ARG(D >= 1 && out != nullptr, "need D >= 1 and an output array");
+    GOSH_CHECK_ARG(e >= 0 && p >= 0 && p <= 1, "epochs must be >= 0 and p in [0, 1]");
+    GOSH_CHECK_ARG(unit == 0 || unit == 1, "epoch_unit must be 0 (passes over V) or 1 (|E| draws)");
+    if (D == 1) {
+        out[0] = e;
+    } else {
+        const double denom = std::pow(2.0, D) - 1.0;
+        int rest = 0;
+        for (int i = 1; i < D; ++i) {
+            out[i] = (int)std::floor(p * e / D + (1.0 - p) * e * std::pow(2.0, i) / denom);
+            rest += out[i];
+        }
+        out[0] = e - rest;
+    }
+    if (unit == 1) {
+        GOSH_CHECK_ARG(n != nullptr && nnz != nullptr, "epoch_unit 1 needs the level sizes");
+        for (int i = 0; i < D; ++i) {
+            GOSH_CHECK_ARG(n[i] >= 1 && nnz[i] >= 0, "level %d: bad size", i);
+            if (out[i] == 0) continue;
+            // floor((2 e nnz + n) / (2 n)) without overflow: e < 2^31, nnz < 2^62
+            const unsigned __int128 num = (unsigned __int128)2 * (unsigned)out[i] * (uint64_t)nnz[i] + (uint64_t)n[i];
+            const unsigned __int128 q = num / ((unsigned __int128)2 * (uint64_t)n[i]);
+            GOSH_CHECK_ARG(q <= (unsigned __int128)INT32_MAX, "level %d: pass count overflows", i);
+            out[i] = q < 1 ? 1 : (int)q;
+        }
+    }
+    return GOSH_OK;
+}
+
 gosh_status check_params(const gosh_params *p) {
     GOSH_CHECK_ARG(p != nullptr, "params is NULL");
     GOSH_CHECK_ARG(dtype_ok(p->dtype), "unknown dtype %d", (int)p->dtype);
@@ -371,6 +389,7 @@ gosh_status check_params(const gosh_params *p) {
     GOSH_CHECK_ARG(p->epoch_overlap >= 0 && p->epoch_overlap <= 8, "epoch_overlap must be in 0..8 (got %d)",
                    p->epoch_overlap);
     GOSH_CHECK_ARG(p->overlap_min_vertices >= 0, "overlap_min_vertices must be >= 0");
+    GOSH_CHECK_ARG(p->epoch_unit == 0 || p->epoch_unit == 1, "epoch_unit must be 0 or 1 (got %d)", p->epoch_unit);
     return GOSH_OK;
 }
 
@@ -399,6 +418,12 @@ gosh_status check_host_csr(const int64_t *rowptr, const int32_t *col, int64_t n,
 using namespace gosh;
 
 extern "C" {
+
+gosh_status gosh_level_epochs(int epochs, double p, int D, int epoch_unit, const int64_t *n, const int64_t *nnz,
+                              int *out) {
+    clear_error();
+    return level_epochs(epochs, p, D, epoch_unit, n, nnz, out);
+}
 
 gosh_status gosh_params_default(gosh_params *p) {
     if (!p) return GOSH_ERR_INVALID_ARG;
@@ -726,7 +751,7 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
     } guard{h};
     const int D = (int)h->n.size();
     std::vector<int> ep(D);
-    epoch_split(p.epochs, p.p, D, ep.data());
+    GOSH_TRY(level_epochs(p.epochs, p.p, D, p.epoch_unit, h->n.data(), h->nnz.data(), ep.data()));
 
     // embedding buffers: even levels in the output (or a device copy of it), odd levels in tmp
     const bool out_dev = is_device_ptr(M0_out);

@@ -344,6 +344,10 @@ int *device_error_word();
 // mode, epochs >= 0, p in [0, 1], shrink in (0, 1].
 gosh_status check_params(const gosh_params *p);
 
+// Per-level epoch counts of Alg. 2 (Sec. 3 split; with unit 1 scaled to the
+// |E_i| draws of Sec. 6's epoch); the body of gosh_level_epochs.
+gosh_status level_epochs(int e, double p, int D, int unit, const int64_t *n, const int64_t *nnz, int *out);
+
 // Content check of a HOST CSR, the host counterpart of gosh_validate_csr:
 // rowptr starts at 0 and never decreases, every column lies in [0, n), rows
 // are strictly ascending and hold no self-loop, and (if `symmetric`) every

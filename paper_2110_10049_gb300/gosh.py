@@ -44,7 +44,8 @@ class gosh_params(C.Structure):
                 ("mlp_max_rows", C.c_int64), ("p_gpu", C.c_int), ("s_gpu", C.c_int), ("B", C.c_int), ("large_parts", C.c_int),
                 ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int),
                 ("walk_length", C.c_int), ("walk_window", C.c_int), ("large_serial", C.c_int),
-                ("large_evict", C.c_int), ("overlap_min_vertices", C.c_int64), ("epoch_overlap", C.c_int)]
+                ("large_evict", C.c_int), ("overlap_min_vertices", C.c_int64), ("epoch_overlap", C.c_int),
+                ("epoch_unit", C.c_int)]
 
 
 class gosh_walk_stats(C.Structure):
@@ -118,6 +119,7 @@ def lib() -> C.CDLL:
             "gosh_mlp_train": [vp, P(gosh_csr), vp, vp, vp, i32, i32, i32, f64, i32, i64, vp, P(C.c_double)],
             "gosh_project_learned": [vp, vp, vp, P(gosh_csr), vp, i32, i32, vp],
             "gosh_round_stochastic": [vp, vp, i64, i32, u64, vp],
+            "gosh_level_epochs": [i32, f64, i32, i32, vp, vp, vp],
         }
         L.gosh_mlp_free.restype = None
         L.gosh_mlp_free.argtypes = [vp]
@@ -439,6 +441,17 @@ def gosh_walk_order(positions, level, epoch, seed, graph_id=0):
     out = np.zeros(positions, dtype=np.int64)
     _check("gosh_walk_order", lib().gosh_walk_order(positions, level, epoch, seed, graph_id, out.ctypes.data))
     return out
+
+
+def gosh_level_epochs(epochs, p, D, epoch_unit=0, n=None, nnz=None) -> list:
+    """Per-level passes of gosh_embed's schedule (host only)."""
+    out = np.zeros(max(D, 1), dtype=np.int32)
+    nv = None if n is None else np.ascontiguousarray(n, dtype=np.int64)
+    ne = None if nnz is None else np.ascontiguousarray(nnz, dtype=np.int64)
+    _check("gosh_level_epochs", lib().gosh_level_epochs(
+        int(epochs), float(p), int(D), int(epoch_unit), None if nv is None else nv.ctypes.data,
+        None if ne is None else ne.ctypes.data, out.ctypes.data))
+    return [int(x) for x in out[:D]]
 
 
 def gosh_large_plan(n, K, p_gpu, rounds, evict=0):

@@ -158,16 +158,24 @@ def link_split(g: Graph, seed: int, test_frac: float = 0.2) -> LinkSplit:
     return LinkSplit(Graph(trp, tco[:m2]), pos[:nte.value], neg[:nte.value])
 
 
-# Named workloads: R-MAT parameters of the benchmark configurations.
+# Named workloads: R-MAT parameters of the benchmark configurations, and the
+# degree-corrected planted partitions of the same sizes on which held-out
+# link prediction is informative (synth/sbm.py).
 _WORKLOADS = {
     "rmat12": dict(scale=12, edge_factor=8, seed=20211020),
     "rmat20": dict(scale=20, edge_factor=16, seed=20211021),
     "rmat22": dict(scale=22, edge_factor=16, seed=20211022),
+    "sbm12": dict(scale=12, edge_factor=8, seed=20211030, communities=32, mu=0.8),
+    "sbm20": dict(scale=20, edge_factor=16, seed=20211031, communities=1024, mu=0.8),
 }
 
 
 def workload(name: str, split: bool = True):
     """The graph of a named workload (and its link split unless split=False)."""
     cfg = _WORKLOADS[name]
-    g = rmat_graph(cfg["scale"], cfg["edge_factor"], cfg["seed"])
+    if "communities" in cfg:
+        from .sbm import sbm_graph
+        g = sbm_graph(1 << cfg["scale"], cfg["communities"], cfg["edge_factor"], cfg["mu"], cfg["seed"])
+    else:
+        g = rmat_graph(cfg["scale"], cfg["edge_factor"], cfg["seed"])
     return link_split(g, cfg["seed"]) if split else g

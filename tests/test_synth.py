@@ -64,3 +64,30 @@ def test_link_split(seed):
     assert len(sp.test_neg) == m_test
     for u, v in sp.test_neg.tolist():
         assert u != v and (u, v) not in train and (u, v) not in pos and (v, u) not in pos
+
+
+def test_planted_partition_graph():
+    """Degree-corrected planted partition (synth/sbm.py): reproducible from
+    its seed, a valid symmetric CSR, skewed degrees, and about mu + (1 - mu)
+    * sum_c share_c^2 of the draws inside a community (share_c: community c's
+    fraction of the degree propensity)."""
+    n, C, ef, mu, seed = 4096, 32, 8, 0.8, 11
+    s1, d1, comm = synth.sbm_edges(n, C, ef, mu, seed)
+    s2, d2, _ = synth.sbm_edges(n, C, ef, mu, seed)
+    np.testing.assert_array_equal(s1, s2)
+    np.testing.assert_array_equal(d1, d2)
+    s3, _, _ = synth.sbm_edges(n, C, ef, mu, seed + 1)
+    assert not np.array_equal(s1, s3)
+    inside = (comm[s1] == comm[d1]).mean()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rng.integers(0, C, n)
+    theta = 1.0 / np.sqrt(1.0 - rng.random(n))
+    share = np.bincount(comm, weights=theta, minlength=C) / theta.sum()
+    expect = mu + (1 - mu) * float((share ** 2).sum())
+    assert abs(inside - expect) < 0.01, (inside, expect)
+    g = synth.sbm_graph(n, C, ef, mu, seed)
+    check_csr(g)
+    deg = np.diff(g.rowptr)
+    assert deg.max() > 8 * deg.mean()
+    lk = synth.workload("sbm12")
+    assert 0.15 < len(lk.test_pos) / (lk.train.nnz / 2 + len(lk.test_pos)) < 0.25
