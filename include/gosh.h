@@ -310,8 +310,14 @@ gosh_status gosh_train_level(const gosh_csr *g, void *M, int level, int epochs,
  *  - The per-block loss partial sums live in one static device array of 4096
  *    FP64 values (32 KB), held by every GPU that loads the library until the
  *    process exits.  A launch needing more blocks than that returns
- *    GOSH_ERR_INVALID_ARG before any kernel runs (a GB300 launch uses at most
- *    152 SMs x 8 blocks = 1216).
+ *    GOSH_ERR_INVALID_ARG before any kernel runs (a launch uses at most SMs x
+ *    resident blocks of the chosen kernel: on a GB300 152 x 8 = 1216 for the
+ *    256-thread register kernels, at most 152 x 16 = 2432 for the 128-thread
+ *    staged ones).
+ *  - A bounded device-side wait that gives up (the staged kernels' copy
+ *    completion) raises a second static device word, not the library's
+ *    allocated one; gosh_device_check reads and clears it, returning
+ *    GOSH_ERR_TIMEOUT, exactly as for the other entry points.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture starts.

@@ -475,6 +475,12 @@ gosh_status gosh_device_check(void *stream) {
     clear_error();
     cudaStream_t s = (cudaStream_t)stream;
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
+    int raised = 0;
+    GOSH_TRY(noalloc_take_error(&raised));
+    if (raised) {
+        set_error("a bounded device-side wait timed out in an earlier gosh_train_level_noalloc call");
+        return GOSH_ERR_TIMEOUT;
+    }
     int *w = device_error_word();
     if (!w) return GOSH_OK;
     int h = 0;

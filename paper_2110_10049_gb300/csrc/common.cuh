@@ -338,6 +338,9 @@ template <> struct Store<__half> {
 
 // Device word raised by bounded waits that gave up (capi.cu); read by gosh_device_check.
 int *device_error_word();
+// The same for gosh_train_level_noalloc's static word (noalloc.cu): *raised = 1
+// if it was set since the last read (then cleared).
+gosh_status noalloc_take_error(int *raised);
 
 // The parameter checks every training entry point makes: dtype, d in
 // {16, 32, 64, 128}, 0 <= k <= 15, a positive finite lr, lr_floor in [0, 1],

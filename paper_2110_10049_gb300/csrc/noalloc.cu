@@ -23,24 +23,32 @@ int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass);
 namespace {
 
 // At most this many thread blocks may contribute a partial loss sum (32 KB).
-// The launcher never uses more blocks than (SMs x resident blocks per SM),
-// 152 x 8 = 1216 on a GB300.
+// A launch uses at most (SMs x resident blocks per SM) of the chosen kernel:
+// 152 x 8 = 1216 for the 256-thread register kernels on a GB300, and at most
+// 152 x 16 = 2432 for the 128-thread TMA-staged ones (2048 threads per SM);
+// the entry point checks the grid against this size before any launch.
 constexpr int kNoAllocMaxPartials = 4096;
+static_assert(kNoAllocMaxPartials >= 152 * (2048 / 128), "static scratch below the GB300 worst case");
 
 // Shared by every call on a device and never cleared: each launch writes the
 // slots [0, grid) before the finalising kernel reads them.
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
 
+// Raised (set to 1) by a training kernel whose bounded wait gave up; read and
+// cleared by gosh_device_check through noalloc_take_error.
+static __device__ __align__(256) int g_noalloc_err;
+
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_partials_ptr[kMaxDevices] = {nullptr};
+int *g_err_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_noalloc_partials on the current device.  In host code
-// the symbol name is only a host-side stand-in, so the address is looked up
-// once per device with cudaGetSymbolAddress (this first lookup may load the
-// library's device code, so make the first call on a device before any
-// stream capture begins).
-gosh_status partials_on_current_device(double **out) {
+// Device addresses of g_noalloc_partials and g_noalloc_err on the current
+// device.  In host code the symbol names are only host-side stand-ins, so the
+// addresses are looked up once per device with cudaGetSymbolAddress (this
+// first lookup may load the library's device code, so make the first call on
+// a device before any stream capture begins).
+gosh_status scratch_on_current_device(double **partials, int **err) {
     int dev = 0;
     GOSH_TRY_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) {
@@ -49,15 +57,18 @@ gosh_status partials_on_current_device(double **out) {
     }
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_partials_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess || p == nullptr) {
-            set_error("cudaGetSymbolAddress(static loss scratch) on device %d: %s", dev, cudaGetErrorString(e));
+        void *p = nullptr, *q = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_noalloc_err);
+        if (e != cudaSuccess || p == nullptr || q == nullptr) {
+            set_error("cudaGetSymbolAddress(static scratch) on device %d: %s", dev, cudaGetErrorString(e));
             return GOSH_ERR_CUDA;
         }
+        g_err_ptr[dev] = static_cast<int *>(q);
         g_partials_ptr[dev] = static_cast<double *>(p);
     }
-    *out = g_partials_ptr[dev];
+    *partials = g_partials_ptr[dev];
+    *err = g_err_ptr[dev];
     return GOSH_OK;
 }
 
@@ -77,6 +88,30 @@ __global__ void noalloc_loss_finalize(const double *__restrict__ parts, int npar
 }
 
 }  // namespace
+
+// Reads and clears the static error word of the current device (only if an
+// allocation-free call has run there; no allocation either way).  *raised is
+// set to 1 if a bounded wait of such a call gave up since the last read.
+gosh_status noalloc_take_error(int *raised) {
+    *raised = 0;
+    int dev = 0;
+    GOSH_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return GOSH_OK;
+    int *w = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        w = g_err_ptr[dev];
+    }
+    if (!w) return GOSH_OK;
+    int h = 0;
+    GOSH_TRY_CUDA(cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        GOSH_TRY_CUDA(cudaMemset(w, 0, sizeof(int)));
+        *raised = 1;
+    }
+    return GOSH_OK;
+}
+
 }  // namespace gosh
 
 using namespace gosh;
@@ -106,15 +141,15 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
     const int cap_blocks = num_sms() * kern->blocks_per_sm;
     const int64_t want = ceil_div(ceil_div(n, tile_vertices(p, n, kern->lanes, kern->pass)), kern->warps);
     const int grid = (int)(want < cap_blocks ? (want > 0 ? want : 1) : cap_blocks);
-    double *partials = nullptr;
-    if (loss_per_epoch) {
-        if (grid > kNoAllocMaxPartials) {
-            set_error("gosh_train_level_noalloc: %d thread blocks exceed the static scratch of %d partial loss sums",
-                      grid, kNoAllocMaxPartials);
-            return GOSH_ERR_INVALID_ARG;
-        }
-        GOSH_TRY(partials_on_current_device(&partials));
+    if (loss_per_epoch && grid > kNoAllocMaxPartials) {
+        set_error("gosh_train_level_noalloc: %d thread blocks exceed the static scratch of %d partial loss sums",
+                  grid, kNoAllocMaxPartials);
+        return GOSH_ERR_INVALID_ARG;
     }
+    double *partials = nullptr;
+    int *err = nullptr;
+    GOSH_TRY(scratch_on_current_device(&partials, &err));
+    if (!loss_per_epoch) partials = nullptr;
     TrainArgs a{};
     a.rowptr = g->rowptr;
     a.col = g->col;
@@ -126,6 +161,7 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
     a.level = (uint32_t)level;
     a.n_updates = n_updates;
     a.loss_partials = partials;
+    a.err = err;
     a.src_begin = 0;
     a.src_end = n;
     a.tile = tile_vertices(p, n, kern->lanes, kern->pass);

@@ -301,6 +301,12 @@ def gosh_train_level_noalloc(g, M, level, epochs, params: gosh_params, loss=None
         C.byref(cg), _ptr(M), level, epochs, C.byref(params), _stream(stream), _ptr(loss), _ptr(n_updates)))
 
 
+def gosh_device_check(stream=None):
+    """Synchronises the stream and raises GoshError (GOSH_ERR_TIMEOUT) if a
+    bounded device-side wait gave up since the last check."""
+    _check("gosh_device_check", lib().gosh_device_check(_stream(stream)))
+
+
 def gosh_round_stochastic(x, dtype, seed=0, stream=None):
     """x: torch.float32 device tensor; dtype: torch.bfloat16 / torch.float16 or
     a GOSH_* code.  Returns the stochastically rounded tensor."""

@@ -62,6 +62,36 @@ def test_serial_parts_equal_sequential_oracle(K, B, seed):
     assert rel_fro(Mh.astype(np.float64), Mo) <= 1e-5
 
 
+def golden_budget_cases():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large_budget_hand.txt")
+    out = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, K, B, k, e, npos, nup = line.split()
+        out.append((int(name[4:]), int(K), int(B), int(k), int(e), int(npos), int(nup)))
+    return out
+
+
+@pytest.mark.parametrize("n,K,B,k,e,npos,nup", golden_budget_cases())
+def test_budget_hand_count_on_device(n, K, B, k, e, npos, nup):
+    """The global positive budget as counted by hand (stars cut into
+    one-vertex parts: every draw is forced), run on the device in stream
+    order; the embeddings equal the sequential oracle's."""
+    g = gosh()
+    gr = synth.csr_from_edges(n, np.zeros(n - 1, np.int64), np.arange(1, n), compact=False)
+    M0 = (oracle.init_uniform(n, 128, 0, 5) * 60).astype(np.float32).astype(np.float64)
+    Mo = M0.copy()
+    nup_o, npos_o = oracle.train_large(gr.rowptr, gr.col, Mo, k, 0, e, 0.05, 1e-4, 7, K, B)
+    assert (npos_o, nup_o) == (npos, nup)
+    Mh = M0.astype(np.float32)
+    p = g.default_params(d=128, k=k, lr=0.05, seed=7, B=B, large_parts=K, p_gpu=2, s_gpu=1, large_serial=1)
+    st = g.gosh_train_level_large(gr.rowptr, gr.col, Mh, 0, e, p)
+    assert (st["positives"], st["updates"]) == (npos, nup)
+    assert rel_fro(Mh.astype(np.float64), Mo) <= 1e-5
+
+
 def fit_auc(M, gr, seed=0):
     src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
     rng = np.random.default_rng(seed)
