@@ -130,9 +130,9 @@ typedef struct gosh_params {
                                trained in one cooperative launch, and calls that request
                                per-epoch losses, stay serialised. */
     int epoch_unit;         /* unit of `epochs` in gosh_embed and gosh_embed_batch: 0 (default)
-                               one pass over V_i (Alg. 3); 1 |E_i| positive draws, the unit of
-                               the paper's experiments (Sec. 6 setup), so level i's e_i epochs
-                               run round(e_i * nnz_i / |V_i|) passes (gosh_level_epochs).
+                               one pass over V_i (Alg. 3); 1 |E| positive draws, the unit of the
+                               paper's experiments (Sec. 6 setup): e becomes round(e * nnz_0 /
+                               |V_0|) passes, split over the levels as usual (gosh_level_epochs).
                                gosh_train_level always counts passes. */
 } gosh_params;
 
@@ -179,15 +179,16 @@ typedef struct gosh_hierarchy gosh_hierarchy;
  * threshold 100 and shrink 0.8 (Sec. 4), FP32 Hogwild, det_batch 4096. */
 gosh_status gosh_params_default(gosh_params *p);
 
-/* The epoch schedule of gosh_embed (Alg. 2, Sec. 3) for D graphs, host only:
- * a fraction p of `epochs` spread uniformly over the levels and the rest
- * geometrically (each level twice its finer neighbour),
- *   e_i = floor(p*e/D + (1-p)*e*2^i/(2^D-1)) for i >= 1,  e_0 = e - sum of the others,
- * then, with epoch_unit = 1 (|E_i| positive draws per epoch, the paper's
- * experimental unit, Sec. 6), each e_i becomes floor((2 e_i nnz_i + n_i) /
- * (2 n_i)) passes over V_i (nnz_i / n_i rounded half up), at least 1 when
- * e_i >= 1.  n, nnz: host int64[D] (|V_i| >= 1 and CSR entries of G_i; read
- * only with epoch_unit = 1, may be NULL otherwise); out: host int[D] passes.
+/* The epoch schedule of gosh_embed (Alg. 2, Sec. 3) for D graphs, host only.
+ * With epoch_unit = 1 (an epoch is |E| positive draws, the paper's
+ * experimental unit, Sec. 6; one Alg. 3 pass makes |V| of them) the total e
+ * first becomes floor((2 e nnz_0 + n_0) / (2 n_0)) passes (e * nnz_0 / n_0
+ * rounded half up, at least 1 when e >= 1; nnz_0 = CSR entries of G_0).
+ * Then a fraction p of the total goes uniformly to the levels and the rest
+ * geometrically (each level twice its finer neighbour):
+ *   e_i = floor(p*e/D + (1-p)*e*2^i/(2^D-1)) for i >= 1,  e_0 = e - sum of the others.
+ * n, nnz: host int64[D] sizes of the graphs (only G_0's are read, and only
+ * with epoch_unit = 1; may be NULL otherwise); out: host int[D] passes.
  * GOSH_ERR_INVALID_ARG for D < 1, epochs < 0, p outside [0, 1], an unknown
  * unit, or a pass count beyond INT_MAX. */
 gosh_status gosh_level_epochs(int epochs, double p, int D, int epoch_unit, const int64_t *n, const int64_t *nnz,

@@ -341,37 +341,35 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 
-// Epoch schedule of Sec. 3 (see gosh_level_epochs): fraction p uniform over
-// the D levels, the rest geometric (level i gets twice level i-1), levels >= 1
-// floored and level 0 the remainder; with the |E| unit of Sec. 6 each level's
-// count is scaled by its density nnz_i / n_i, rounded half up in integers.
+// Epoch schedule of Sec. 3 (see gosh_level_epochs): with the |E| unit of
+// Sec. 6 the total e is first converted to passes over V by the input
+// graph's density nnz_0 / n_0 (rounded half up in integers); then a fraction
+// p of it goes uniformly to the D levels and the rest geometrically (level i
+// twice level i-1), levels >= 1 floored and level 0 the remainder.
 gosh_status level_epochs(int e, double p, int D, int unit, const int64_t *n, const int64_t *nnz, int *out) {
     GOSH_CHECK_ARG(D >= 1 && out != nullptr, "need D >= 1 and an output array");
     GOSH_CHECK_ARG(e >= 0 && p >= 0 && p <= 1, "epochs must be >= 0 and p in [0, 1]");
     GOSH_CHECK_ARG(unit == 0 || unit == 1, "epoch_unit must be 0 (passes over V) or 1 (|E| draws)");
+    if (unit == 1 && e > 0) {
+        GOSH_CHECK_ARG(n != nullptr && nnz != nullptr, "epoch_unit 1 needs the size of G_0");
+        GOSH_CHECK_ARG(n[0] >= 1 && nnz[0] >= 0, "bad size of G_0");
+        // floor((2 e nnz + n) / (2 n)) without overflow: e < 2^31, nnz < 2^62
+        const unsigned __int128 num = (unsigned __int128)2 * (unsigned)e * (uint64_t)nnz[0] + (uint64_t)n[0];
+        const unsigned __int128 q = num / ((unsigned __int128)2 * (uint64_t)n[0]);
+        GOSH_CHECK_ARG(q <= (unsigned __int128)INT32_MAX, "the pass count overflows");
+        e = q < 1 ? 1 : (int)q;
+    }
     if (D == 1) {
         out[0] = e;
-    } else {
-        const double denom = std::pow(2.0, D) - 1.0;
-        int rest = 0;
-        for (int i = 1; i < D; ++i) {
-            out[i] = (int)std::floor(p * e / D + (1.0 - p) * e * std::pow(2.0, i) / denom);
-            rest += out[i];
-        }
-        out[0] = e - rest;
+        return GOSH_OK;
     }
-    if (unit == 1) {
-        GOSH_CHECK_ARG(n != nullptr && nnz != nullptr, "epoch_unit 1 needs the level sizes");
-        for (int i = 0; i < D; ++i) {
-            GOSH_CHECK_ARG(n[i] >= 1 && nnz[i] >= 0, "level %d: bad size", i);
-            if (out[i] == 0) continue;
-            // floor((2 e nnz + n) / (2 n)) without overflow: e < 2^31, nnz < 2^62
-            const unsigned __int128 num = (unsigned __int128)2 * (unsigned)out[i] * (uint64_t)nnz[i] + (uint64_t)n[i];
-            const unsigned __int128 q = num / ((unsigned __int128)2 * (uint64_t)n[i]);
-            GOSH_CHECK_ARG(q <= (unsigned __int128)INT32_MAX, "level %d: pass count overflows", i);
-            out[i] = q < 1 ? 1 : (int)q;
-        }
+    const double denom = std::pow(2.0, D) - 1.0;
+    int rest = 0;
+    for (int i = 1; i < D; ++i) {
+        out[i] = (int)std::floor(p * e / D + (1.0 - p) * e * std::pow(2.0, i) / denom);
+        rest += out[i];
     }
+    out[0] = e - rest;
     return GOSH_OK;
 }
 

@@ -268,6 +268,19 @@ template <> struct Store<__nv_bfloat16> {
         }
         return make_uint4(w[0], w[1], w[2], w[3]);
     }
+    // The same difference with `old` still packed (its 8 values are exact
+    // BF16): the identical packed subtraction, without unpacking.
+    __device__ __forceinline__ static uint4 change_packed(const uint4 &nw, const uint4 &old) {
+        const uint32_t n4[4] = {nw.x, nw.y, nw.z, nw.w}, o4[4] = {old.x, old.y, old.z, old.w};
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 d = __hsub2(*reinterpret_cast<const __nv_bfloat162 *>(&n4[i]),
+                                             *reinterpret_cast<const __nv_bfloat162 *>(&o4[i]));
+            w[i] = *reinterpret_cast<const uint32_t *>(&d);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
     // Atomic addition of 8 packed values at L2 (no flush to zero).
     __device__ __forceinline__ static void red_add(__nv_bfloat16 *p, const uint4 &d) {
         asm volatile("red.global.add.noftz.v4.bf16x2 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(d.x), "r"(d.y),
@@ -329,6 +342,18 @@ template <> struct Store<__half> {
         }
         return make_uint4(w[0], w[1], w[2], w[3]);
     }
+    // The same difference with `old` still packed (exact FP16 values).
+    __device__ __forceinline__ static uint4 change_packed(const uint4 &nw, const uint4 &old) {
+        const uint32_t n4[4] = {nw.x, nw.y, nw.z, nw.w}, o4[4] = {old.x, old.y, old.z, old.w};
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 d = __hsub2(*reinterpret_cast<const __half2 *>(&n4[i]),
+                                      *reinterpret_cast<const __half2 *>(&o4[i]));
+            w[i] = *reinterpret_cast<const uint32_t *>(&d);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
     __device__ __forceinline__ static void red_add(__half *p, const uint4 &d) {
         asm volatile("red.global.add.noftz.v4.f16x2 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(d.x), "r"(d.y),
                      "r"(d.z), "r"(d.w)
@@ -347,8 +372,8 @@ gosh_status noalloc_take_error(int *raised);
 // mode, epochs >= 0, p in [0, 1], shrink in (0, 1].
 gosh_status check_params(const gosh_params *p);
 
-// Per-level epoch counts of Alg. 2 (Sec. 3 split; with unit 1 scaled to the
-// |E_i| draws of Sec. 6's epoch); the body of gosh_level_epochs.
+// Per-level epoch counts of Alg. 2 (Sec. 3 split; with unit 1 the total first
+// converted from Sec. 6's |E|-draw epochs to passes); the body of gosh_level_epochs.
 gosh_status level_epochs(int e, double p, int D, int unit, const int64_t *n, const int64_t *nnz, int *out);
 
 // Content check of a HOST CSR, the host counterpart of gosh_validate_csr:

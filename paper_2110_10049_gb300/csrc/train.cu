@@ -108,10 +108,11 @@ int natural_lanes(gosh_dtype dtype, int d) { return d * (int)dtype_size(dtype) /
 // Sources per warp tile.  A warp walks its tile in tile / (32/L) dependent
 // rounds, so small levels (few tiles, far fewer than the GPU's warps) take
 // short tiles (4 below 2^16 rows; below 2^19, 8 for 16-bit tables with plain
-// stores, 16 for 16-bit tables with atomic changes and in the deterministic
-// mode, 32 for FP32 lock-free);
-// large levels take 32 to amortise the draws.  A multiple of 32/L in
-// [32/L, 32]; params->vertices_per_warp overrides.
+// stores, 16 in the deterministic mode, 32 lock-free with atomic changes);
+// from 2^19 rows 16 for the lock-free modes with atomic changes (one more
+// wave of tiles than 32 evens out the tail; measured on R-MAT 20 level 0:
+// BF16 231 vs 234 us, FP32 362 vs 373 us), else 32 to amortise the draws.
+// A multiple of 32/L in [32/L, 32]; params->vertices_per_warp overrides.
 int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass) {
     const int G = 32 / lanes;
     int t = p->vertices_per_warp;
@@ -122,8 +123,10 @@ int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass) {
     }
     const bool red16 = p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC && !p->plain_stores;
     const bool f32_lockfree = p->dtype == GOSH_F32 && p->mode != GOSH_DETERMINISTIC;
-    const int mid = red16 ? 16 : f32_lockfree ? 32 : (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC ? 8 : 16);
-    if (t <= 0) t = n >= (int64_t(1) << 19) ? 32 : (n >= (int64_t(1) << 16) ? mid : 4);
+    const bool atomic_lockfree = (red16 || f32_lockfree) && !p->plain_stores;
+    const int mid = atomic_lockfree ? 32 : (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC ? 8 : 16);
+    const int large = atomic_lockfree ? 16 : 32;
+    if (t <= 0) t = n >= (int64_t(1) << 19) ? large : (n >= (int64_t(1) << 16) ? mid : 4);
     t = t < G ? G : (t > 32 ? 32 : t);
     return t / G * G;
 }
@@ -144,9 +147,11 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
     // Defaults by level size, from per-level sweeps of lanes per row L,
     // samples per pass P and tile on the R-MAT 20 hierarchy (d = 128, k = 3;
     // L0 = one 16-byte vector per lane; P < 0: rows staged by TMA):
-    //  - FP32 lock-free: above 2^19 rows TMA-staged with L0 lanes; from 2^14
-    //    rows registers, L0 lanes, P = 4; below, TMA-staged with L0/2 lanes
-    //    (a latency-bound level: every row of a round in flight at once);
+    //  - FP32 lock-free: from 2^19 rows registers, L0/2 lanes, P = 4 (362 us
+    //    per level-0 epoch against 444 TMA-staged); from 2^16 registers, L0
+    //    lanes, P = 4; from 2^14 registers, L0/2 lanes, P = 4; below,
+    //    TMA-staged with L0/2 lanes (a latency-bound level: every row of a
+    //    round in flight at once);
     //  - 16-bit tables (atomic changes): from 2^14 rows registers, L0/2
     //    lanes (two vectors per lane, more sources in flight), P = 2; below,
     //    BF16 tables TMA-staged with L0/2 lanes (FP16 has no staged variant:
@@ -157,9 +162,9 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
         const int staged = ns <= 4 ? -4 : -6;
         const int half = nat >= 4 ? nat / 2 : nat;
         if (dtype == GOSH_F32 && mode == kModeRed) {
-            if (n >= (int64_t(1) << 19) && ns <= 6) {
-                lanes = nat;
-                pass = staged;
+            if (n >= (int64_t(1) << 19) || (n >= (int64_t(1) << 14) && n < (int64_t(1) << 16))) {
+                lanes = half;
+                pass = 4;
             } else if (n >= (int64_t(1) << 14)) {
                 lanes = nat;
                 pass = 4;

@@ -292,6 +292,104 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
                 active = v >= 0;
             }
             const uint32_t sr = std::is_same<T, float>::value ? 0u : s_sr_w[j];
+            if constexpr (RED16) {
+                // 16-bit tables, atomic changes: the rows as read stay packed
+                // (their values are exact in T) and are unpacked where used,
+                // so a lane holds E/2 words per row instead of E floats; same
+                // operations in the same order as the unpacked form below
+                constexpr int NV = E / PV;
+                const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+                uint4 r0p[NV];
+                float r[E];
+                if (active) {
+                    const uint4 *q4 = reinterpret_cast<const uint4 *>(M + v * D) + gl;
+#pragma unroll
+                    for (int x = 0; x < NV; ++x) {
+                        r0p[x] = __ldcg(q4 + x * L);
+                        Store<T>::unpack(r0p[x], r + x * PV);
+                    }
+                } else {
+#pragma unroll
+                    for (int x = 0; x < NV; ++x) r0p[x] = z4;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) r[e] = 0.0f;
+                }
+#pragma unroll 1
+                for (int p0 = 0; p0 < ns; p0 += P) {
+                    int32_t us[P];
+                    uint4 rowp[P][NV];
+#pragma unroll
+                    for (int s = 0; s < P; ++s) {
+                        const int t = p0 + s;
+                        us[s] = (active && t < ns) ? s_u_w[j * kSlotStride + t] : -1;
+                    }
+#pragma unroll
+                    for (int s = 0; s < P; ++s) {
+                        const uint4 *q4 = reinterpret_cast<const uint4 *>(M + (int64_t)(us[s] >= 0 ? us[s] : 0) * D) + gl;
+#pragma unroll
+                        for (int x = 0; x < NV; ++x) rowp[s][x] = us[s] >= 0 ? __ldcg(q4 + x * L) : z4;
+                    }
+#pragma unroll
+                    for (int s = 0; s < P; ++s) {
+                        const int t = p0 + s;
+                        const bool ok = us[s] >= 0;
+                        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+                        for (int x = 0; x < NV; ++x) {
+                            float tmp[PV];
+                            Store<T>::unpack(rowp[s][x], tmp);
+#pragma unroll
+                            for (int e = 0; e < PV; e += 2)
+                                ffma2(s0, s1, r[x * PV + e], r[x * PV + e + 1], tmp[e], tmp[e + 1], s0, s1);
+                        }
+                        const float xd = group_sum<L>(s0 + s1);
+                        const float b = t == 0 ? 1.0f : 0.0f;
+                        const float sig = __frcp_rn(1.0f + __expf(-xd));
+                        const float score = ok ? (b - sig) * a.lr : 0.0f;
+#pragma unroll
+                        for (int x = 0; x < NV; ++x) {
+                            float tmp[PV];
+                            Store<T>::unpack(rowp[s][x], tmp);
+#pragma unroll
+                            for (int e = 0; e < PV; e += 2)
+                                ffma2(r[x * PV + e], r[x * PV + e + 1], tmp[e], tmp[e + 1], score, score,
+                                      r[x * PV + e], r[x * PV + e + 1]);
+                        }
+                        if (ok) {
+                            T *row = M + (int64_t)us[s] * D;
+#pragma unroll
+                            for (int x = 0; x < NV; ++x) {
+                                float tmp[PV];
+                                Store<T>::unpack(rowp[s][x], tmp);
+#pragma unroll
+                                for (int e = 0; e < PV; e += 2)
+                                    ffma2(tmp[e], tmp[e + 1], r[x * PV + e], r[x * PV + e + 1], score, score, tmp[e],
+                                          tmp[e + 1]);
+                                const int col = lane_col<T, L>(gl, x);
+                                const uint4 nw = Store<T>::pack(tmp, sr, (uint32_t)((t * D + col) >> 1));
+                                Store<T>::red_add(row + col, Store<T>::change_packed(nw, rowp[s][x]));
+                                // a later sample of this pass with the same id continues from this row
+#pragma unroll
+                                for (int s2 = s + 1; s2 < P; ++s2)
+                                    if (us[s2] == us[s]) rowp[s2][x] = nw;
+                            }
+                            if (gl == 0) {
+                                ++applied;
+                                if (want_loss) loss_acc += (double)softplus_f(t == 0 ? -xd : xd);
+                            }
+                        }
+                    }
+                }
+                if (active) {
+#pragma unroll
+                    for (int x = 0; x < NV; ++x) {
+                        const int col = lane_col<T, L>(gl, x);
+                        const uint4 nw = Store<T>::pack(r + x * PV, sr, (uint32_t)((ns * D + col) >> 1));
+                        Store<T>::red_add(M + v * D + col, Store<T>::change_packed(nw, r0p[x]));
+                    }
+                }
+                continue;
+            }
             float r[E];
             if (active) {
                 if (DET) load_row_snapshot<T, E, L>(M + v * D, gl, r);
@@ -396,10 +494,15 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
 
 // Resident blocks the register allocation must allow: three (80 registers,
 // 24 warps per SM) for lock-free variants whose lanes hold at most 8 values of
-// a row, two (128 registers) otherwise: longer slices and the deterministic
-// mode's larger passes would spill under three.
+// a row, and for 16-bit tables with atomic changes (rows kept packed) up to 16;
+// two (128 registers) otherwise: longer slices and the deterministic mode's
+// larger passes would spill under three.
+template <typename T>
 constexpr int train_min_blocks(int values_per_lane, int mode) {
-    return (mode != kModeDet && values_per_lane <= 8) ? 3 : 2;
+    return (mode != kModeDet && (values_per_lane <= 8 ||
+                                 (mode == kModeRed && !std::is_same<T, float>::value && values_per_lane <= 16)))
+               ? 3
+               : 2;
 }
 
 /*
@@ -407,7 +510,7 @@ constexpr int train_min_blocks(int values_per_lane, int mode) {
  * grid take tiles of consecutive sources of [src_begin, src_end) in turn.
  */
 template <typename T, int D, int L, int P, int MODE>
-__global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, MODE)) train_kernel(TrainArgs a) {
+__global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks<T>(D / L, MODE)) train_kernel(TrainArgs a) {
     __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
     __shared__ uint32_t s_sr[kTrainWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -471,7 +574,7 @@ constexpr uint32_t kEpochBarrierPolls = 1u << 22;
  * and goes on.
  */
 template <typename T, int D, int L, int P, int MODE>
-__global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, MODE))
+__global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks<T>(D / L, MODE))
     train_epochs_kernel(TrainArgs a, int epochs, double lr, double lr_floor, unsigned int *barrier) {
     GOSH_DEP_WAIT();
     __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];

@@ -28,7 +28,7 @@ namespace gosh {
 namespace {
 
 template <typename T, int D, int L, int P>
-__global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks(D / L, kModeRed)) train_pairs_kernel(TrainArgs a) {
+__global__ void __launch_bounds__(kTrainWarps * 32, train_min_blocks<T>(D / L, kModeRed)) train_pairs_kernel(TrainArgs a) {
     __shared__ int32_t s_u[kTrainWarps][32 * kSlotStride];
     __shared__ uint32_t s_sr[kTrainWarps][32];
     __shared__ int32_t s_src[kTrainWarps][32];
