@@ -158,6 +158,21 @@ def link_split(g: Graph, seed: int, test_frac: float = 0.2) -> LinkSplit:
     return LinkSplit(Graph(trp, tco[:m2]), pos[:nte.value], neg[:nte.value])
 
 
+def fit_pairs(g: Graph, count: int = 400000, seed: int = 5):
+    """Pairs of a training-edge AUC: training edges (u < v; a seeded sample of
+    `count` of them, drawn with replacement, when there are more) and as many
+    uniform vertex pairs (u != v).  Returns (pos, neg), int32 [m, 2] each."""
+    src = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    keep = src < g.col
+    pos = np.stack([src[keep], g.col[keep]], 1)
+    rng = np.random.default_rng(seed)
+    if len(pos) > count:
+        pos = pos[rng.integers(0, len(pos), count)]
+    neg = rng.integers(0, g.n, size=(len(pos), 2))
+    neg = neg[neg[:, 0] != neg[:, 1]]
+    return pos.astype(np.int32), neg.astype(np.int32)
+
+
 # Named workloads: R-MAT parameters of the benchmark configurations, and the
 # degree-corrected planted partitions of the same sizes on which held-out
 # link prediction is informative (synth/sbm.py).

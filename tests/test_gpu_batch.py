@@ -2,11 +2,13 @@
 
 - graphs small enough that every level is a single work item of one warp
   with one source per round (FP32, d = 128, 32 lanes per source) are trained
-  sequentially both in the batch and standalone: the batch must reproduce the
-  standalone gosh_embed of each graph (same Philox stream: graph_id + g) to
-  the deterministic-mode tolerance 1e-5;
-- a batch of R-MAT graphs reaches the standalone training-edge AUC (within
-  0.01, mean over the batch; lock-free runs are not bit-reproducible);
+  sequentially in the batch: each graph's result equals the sequential FP64
+  oracle's Alg. 2 on that graph (same Philox stream: graph_id + g) to the
+  deterministic-mode tolerance 1e-5;
+- a batch of R-MAT graphs trained with epochs of |E| updates, where the
+  oracle fits the training edges (mean AUC >= 0.85), reaches the oracle's
+  mean training-edge AUC within 0.005 (lock-free runs are not
+  bit-reproducible; the mean is over the 12 graphs);
 - the autotuner runs once per (dtype, d, k) and its choice is reused.
 """
 import numpy as np
@@ -23,7 +25,7 @@ def dev_csr(g, gr):
     return g.to_device_csr(gr.rowptr, gr.col)
 
 
-def test_batch_equals_standalone_on_single_warp_graphs():
+def test_batch_equals_oracle_on_single_warp_graphs():
     g = gosh()
     graphs = [synth.random_graph(int(n), 0.25, int(s)) for n, s in zip(range(18, 32, 2), range(7))]
     csrs = [dev_csr(g, gr) for gr in graphs]
@@ -32,10 +34,8 @@ def test_batch_equals_standalone_on_single_warp_graphs():
     outs, st = g.gosh_embed_batch(csrs, p)
     assert st["graphs"] == len(graphs)
     for i, gr in enumerate(graphs):
-        q = g.default_params(d=128, k=3, lr=0.05, epochs=30, p=0.3, seed=5, graph_id=100 + i,
-                             lanes_per_row=32, samples_per_pass=2, threshold=4, vertices_per_warp=32)
-        M, _ = g.gosh_embed(csrs[i].rowptr, csrs[i].col, q)
-        assert rel_fro(outs[i].double().cpu().numpy(), M.double().cpu().numpy()) <= 1e-5
+        Mo, info = oracle.embed(gr.rowptr, gr.col, 128, 3, 0.05, 30, 0.3, seed=5, threshold=4, graph=100 + i)
+        assert rel_fro(outs[i].double().cpu().numpy(), Mo) <= 1e-5, i
 
 
 def fit_auc(M, gr, seed=0):
@@ -45,21 +45,25 @@ def fit_auc(M, gr, seed=0):
     return oracle.link_auc(M, np.stack([src, gr.col], 1), rnd)
 
 
+_oracle_fit = {}
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_batch_matches_standalone_quality(dtype):
+def test_batch_reaches_oracle_quality(dtype):
     g = gosh()
     rng = np.random.default_rng(3)
     graphs = [synth.rmat_graph(int(rng.integers(8, 12)), int(rng.integers(4, 17)), 50 + i) for i in range(12)]
     csrs = [dev_csr(g, gr) for gr in graphs]
-    p = g.default_params(d=64, k=5, lr=0.045, epochs=200, p=0.3, seed=9, dtype=dtype)
+    p = g.default_params(d=64, k=5, lr=0.045, epochs=200, p=0.3, seed=9, dtype=dtype, epoch_unit=1)
     outs, st = g.gosh_embed_batch(csrs, p)
     a_batch = [fit_auc(o.double().cpu().numpy(), gr) for o, gr in zip(outs, graphs)]
-    a_alone = []
-    for i, gr in enumerate(graphs):
-        q = g.default_params(d=64, k=5, lr=0.045, epochs=200, p=0.3, seed=9, graph_id=i, dtype=dtype)
-        M, _ = g.gosh_embed(csrs[i].rowptr, csrs[i].col, q)
-        a_alone.append(fit_auc(M.double().cpu().numpy(), gr))
-    assert abs(np.mean(a_batch) - np.mean(a_alone)) <= 0.01, (np.mean(a_batch), np.mean(a_alone))
+    if not _oracle_fit:
+        for i, gr in enumerate(graphs):
+            Mo, _ = oracle.embed(gr.rowptr, gr.col, 64, 5, 0.045, 200, 0.3, seed=9, graph=i, epoch_unit="E")
+            _oracle_fit[i] = fit_auc(Mo, gr)
+    a_orc = [_oracle_fit[i] for i in range(len(graphs))]
+    assert np.mean(a_orc) >= 0.85, a_orc
+    assert abs(np.mean(a_batch) - np.mean(a_orc)) <= 0.005, (np.round(a_batch, 4), np.round(a_orc, 4))
     assert st["updates"] > 0
 
 

@@ -4,10 +4,16 @@ training split (614,524 vertices, 25.1 M CSR entries), d = 128, k = 3.
 - coarsening: every level's map and CSR bit-exact against the oracle;
 - one deterministic epoch of level 0 (FP32, snapshot batches of 4096) within
   the deterministic-mode bar, 1e-5 relative, against the FP64 oracle;
-- the lock-free step as bench.py runs it (e = 200 over the hierarchy): the
-  FP32 held-out and training-edge AUC within 0.005 of the sequential oracle's
-  and sane update counts for the BF16 tables.
+- the lock-free embed as bench.py runs it (lr 0.01, e = 400 epochs of |E|
+  updates over the hierarchy): FP32 training-edge and held-out AUC within
+  0.005 of the sequential FP64 oracle's (means over seeds 1-3; the oracle's
+  values, with training-edge AUC >= 0.9, are stored in
+  tests/golden/c2_oracle_auc.txt by a script that runs only the oracle), BF16
+  tables within 0.005 of FP32, the oracle's per-level schedule, and sane
+  update counts.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -54,35 +60,34 @@ def test_fullsize_deterministic_epoch(c2):
     assert abs(float(loss.item()) - lo[0]) <= 1e-5 * lo[0]
 
 
-def fit_auc(M, gr, seed=0):
-    src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
-    rng = np.random.default_rng(seed)
-    rnd = np.stack([rng.integers(0, gr.n, 200000), rng.integers(0, gr.n, 200000)], 1)
-    pick = rng.integers(0, len(src), 200000)
-    return oracle.link_auc(M, np.stack([src[pick], gr.col[pick]], 1), rnd)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_oracle_auc.txt")
+C2 = dict(d=128, k=3, lr=0.01, epochs=400, p=0.3, epoch_unit=1)
 
 
 def test_fullsize_lockfree_matches_oracle_auc(c2):
     g = gosh()
     gr = c2.train
-    Mo, info = oracle.embed(gr.rowptr, gr.col, 128, 3, 0.045, 200, 0.3, seed=11)
+    ref = np.array([[float(x) for x in line.split()[1:]] for line in open(GOLDEN)
+                    if line.strip() and not line.startswith("#")])
+    assert len(ref) == 3 and ref[:, 0].mean() >= 0.9, ref
     rp, co = torch.from_numpy(gr.rowptr).cuda(), torch.from_numpy(gr.col).cuda()
-    p = g.default_params(d=128, k=3, lr=0.045, epochs=200, p=0.3, seed=11)
-    Mg, st = g.gosh_embed(rp, co, p)
-    s = g.stats_dict(st)
-    assert s["epochs"] == info["epochs"]
-    Mgn = Mg.double().cpu().numpy()
-    ho = oracle.link_auc(Mo, c2.test_pos, c2.test_neg)
-    hg = oracle.link_auc(Mgn, c2.test_pos, c2.test_neg)
-    fo, fg = fit_auc(Mo, gr), fit_auc(Mgn, gr)
-    assert abs(ho - hg) <= 0.005, (ho, hg)
-    assert abs(fo - fg) <= 0.005, (fo, fg)
-    # BF16 tables as bench.py times them: finite, and the applied-update count
-    # within the draws' skip rate (a source without neighbours skips its
-    # positive; a negative equal to the source is skipped)
-    pb = g.default_params(d=128, k=3, lr=0.045, epochs=200, p=0.3, seed=11, dtype=torch.bfloat16)
-    Mb, stb = g.gosh_embed(rp, co, pb)
-    sb = g.stats_dict(stb)
-    assert torch.isfinite(Mb.float()).all()
-    full = sum(e * n * 4 for e, n in zip(sb["epochs"], sb["n"]))
-    assert 0.99 * full <= sb["updates"] <= full
+    fp, fn = synth.fit_pairs(gr)
+    fp, fn = torch.from_numpy(fp).cuda(), torch.from_numpy(fn).cuda()
+    pos, neg = torch.from_numpy(c2.test_pos).cuda(), torch.from_numpy(c2.test_neg).cuda()
+    got = {}
+    for dt in (torch.float32, torch.bfloat16):
+        rows = []
+        for seed in (1, 2, 3):
+            M, st = g.gosh_embed(rp, co, g.default_params(seed=seed, dtype=dt, **C2))
+            s = g.stats_dict(st)
+            assert torch.isfinite(M.float()).all()
+            assert s["epochs"] == oracle.level_epochs(400, 0.3, s["n"], s["nnz"], "E")
+            full = sum(e * n * 4 for e, n in zip(s["epochs"], s["n"]))
+            assert 0.99 * full <= s["updates"] <= full
+            rows.append((g.gosh_link_auc(M, fp, fn), g.gosh_link_auc(M, pos, neg)))
+        got[dt] = np.array(rows)
+    f32, b16 = got[torch.float32], got[torch.bfloat16]
+    msg = "oracle %s, FP32 %s, BF16 %s" % (np.round(ref, 4).tolist(), np.round(f32, 4).tolist(),
+                                          np.round(b16, 4).tolist())
+    assert (np.abs(f32.mean(0) - ref.mean(0)) <= 0.005).all(), msg
+    assert (b16.mean(0) >= f32.mean(0) - 0.005).all(), msg

@@ -7,7 +7,8 @@ Bars (see the tolerance derivation next to each test):
     same snapshot batches: relative Frobenius error <= 1e-5;
   - Hogwild on a graph small enough to occupy one warp with one source per
     round is sequential, so it meets the same 1e-5 bar against the sequential
-    oracle; larger graphs are judged by link-prediction AUC within 0.005.
+    oracle; larger graphs are judged by link-prediction AUC within 0.005 of
+    the oracle's (means over 3 seeds) at a schedule where the oracle learns.
 """
 import numpy as np
 import pytest
@@ -203,61 +204,95 @@ def test_hogwild_single_warp_all_epochs_in_one_launch(g, k):
         assert rel_fro(M.double().cpu().numpy(), Mo) <= DET_TOL
 
 
-def heldout_and_fit_auc(M, sp, seed=0):
-    gr = sp.train
+# Quality bars of the lock-free path (held-out and training-edge AUC) are
+# applied where the oracle learns: the small workload's schedule (d = 32, k = 3,
+# lr 0.045, e = 200 epochs of |E| updates, p = 0.3) fits the R-MAT scale-12
+# training edges (oracle AUC >= 0.9) and predicts held-out edges of the
+# planted partition of the same size (oracle AUC >= 0.8); each bar is a mean
+# over seeds 1-3, and the seed spread is reported with it.
+SEEDS = (1, 2, 3)
+C1 = dict(k=3, lr=0.045, p=0.3)
+E1 = 200
+
+
+@pytest.fixture(scope="module")
+def s1():
+    return synth.workload("sbm12")
+
+
+def fit_auc(M, gr, seed=5):
+    """Training-edge AUC: every training edge (u < v) against as many uniform
+    vertex pairs."""
     src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
+    keep = src < gr.col
+    pos = np.stack([src[keep], gr.col[keep]], 1)
     rng = np.random.default_rng(seed)
-    rnd = np.stack([rng.integers(0, gr.n, 20000), rng.integers(0, gr.n, 20000)], 1)
-    fit = oracle.link_auc(M, np.stack([src, gr.col], 1), rnd)
-    return oracle.link_auc(M, sp.test_pos, sp.test_neg), fit
+    neg = rng.integers(0, gr.n, size=(len(pos), 2))
+    return oracle.link_auc(M, pos, neg[neg[:, 0] != neg[:, 1]])
 
 
-def test_hogwild_auc_matches_oracle(g, c1):
-    """FP32 Hogwild on R-MAT scale 12, d=32, k=3, 200 epochs over the full
-    hierarchy: held-out and training-edge AUC within 0.005 of the sequential
-    oracle, each averaged over 3 seeds."""
-    sp = c1
-    res_o, res_g = [], []
-    for seed in (1, 2, 3):
-        Mo, _ = oracle.embed(sp.train.rowptr, sp.train.col, 32, 3, 0.045, 200, 0.3, seed=seed)
-        p = g.default_params(d=32, k=3, lr=0.045, epochs=200, p=0.3, seed=seed)
-        Mg, st = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
-        res_o.append(heldout_and_fit_auc(Mo, sp))
-        res_g.append(heldout_and_fit_auc(Mg.double().cpu().numpy(), sp))
-    o, gg = np.mean(res_o, 0), np.mean(res_g, 0)
-    assert abs(o[0] - gg[0]) <= 0.005, (o, gg)
-    assert abs(o[1] - gg[1]) <= 0.005, (o, gg)
+_oracle_cache = {}
+
+
+def oracle_quality(r, s, d):
+    """Oracle (FP64, sequential) AUCs per seed: (R-MAT fit, planted held-out, planted fit)."""
+    key = d
+    if key not in _oracle_cache:
+        out = []
+        for seed in SEEDS:
+            Mr, _ = oracle.embed(r.train.rowptr, r.train.col, d, e=E1, seed=seed, epoch_unit="E", **C1)
+            Ms, _ = oracle.embed(s.train.rowptr, s.train.col, d, e=E1, seed=seed, epoch_unit="E", **C1)
+            out.append((fit_auc(Mr, r.train), oracle.link_auc(Ms, s.test_pos, s.test_neg), fit_auc(Ms, s.train)))
+        _oracle_cache[key] = np.array(out)
+    return _oracle_cache[key]
+
+
+def gpu_quality(g, r, s, d, dtype=torch.float32, **kw):
+    out = []
+    for seed in SEEDS:
+        row = []
+        for sp in (r, s):
+            p = g.default_params(d=d, epochs=E1, seed=seed, dtype=dtype, epoch_unit=1, **C1, **kw)
+            M, _ = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
+            row.append(M.double().cpu().numpy())
+        out.append((fit_auc(row[0], r.train), oracle.link_auc(row[1], s.test_pos, s.test_neg),
+                    fit_auc(row[1], s.train)))
+    return np.array(out)
+
+
+def check_quality(got, ref, bar=0.005, floors=(0.9, 0.8, 0.9)):
+    names = ("R-MAT training-edge", "planted held-out", "planted training-edge")
+    for j, name in enumerate(names):
+        msg = "%s AUC: GPU %s (spread %.4f) vs oracle %s (spread %.4f)" % (
+            name, np.round(got[:, j], 4), np.ptp(got[:, j]), np.round(ref[:, j], 4), np.ptp(ref[:, j]))
+        assert ref[:, j].mean() >= floors[j], msg
+        assert abs(got[:, j].mean() - ref[:, j].mean()) <= bar, msg
+
+
+def test_hogwild_auc_matches_oracle(g, c1, s1):
+    """FP32 lock-free embed over the full hierarchy against the sequential FP64
+    oracle: R-MAT training-edge AUC and planted-partition held-out and
+    training-edge AUC within 0.005 (means over 3 seeds), where the oracle
+    learns."""
+    check_quality(gpu_quality(g, c1, s1, 32), oracle_quality(c1, s1, 32))
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_small_d_embed_auc_matches_oracle(g, c1, dtype):
+def test_small_d_embed_auc_matches_oracle(g, c1, s1, dtype):
     """d = 16 (a warp updates 8 or 16 sources at once; the small levels fall
-    back from the staged kernel to registers): held-out and training-edge
-    AUC within 0.01 of the sequential oracle on R-MAT scale 12, 2 seeds."""
-    sp = c1
-    res_o, res_g = [], []
-    for seed in (1, 2):
-        Mo, _ = oracle.embed(sp.train.rowptr, sp.train.col, 16, 3, 0.045, 200, 0.3, seed=seed)
-        p = g.default_params(d=16, k=3, lr=0.045, epochs=200, p=0.3, seed=seed, dtype=dtype)
-        Mg, _ = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
-        res_o.append(heldout_and_fit_auc(Mo, sp))
-        res_g.append(heldout_and_fit_auc(Mg.double().cpu().numpy(), sp))
-    o, gg = np.mean(res_o, 0), np.mean(res_g, 0)
-    assert abs(o[0] - gg[0]) <= 0.01, (o, gg)
-    assert abs(o[1] - gg[1]) <= 0.01, (o, gg)
+    back from the staged kernel to registers): the same 0.005 bars as d = 32;
+    the oracle's R-MAT training-edge AUC is lower at this width (0.889 over
+    the three seeds), so its floor is 0.85."""
+    check_quality(gpu_quality(g, c1, s1, 16, dtype), oracle_quality(c1, s1, 16), floors=(0.85, 0.8, 0.9))
 
 
-def test_bf16_tables_reach_fp32_auc(g, c1):
-    """BF16 tables (FP32 arithmetic, stochastic rounding) reach the held-out
-    AUC of the FP32 tables within 0.005 (mean of 3 seeds)."""
-    sp = c1
-    res = {torch.float32: [], torch.bfloat16: []}
-    for seed in (1, 2, 3):
-        for dt in res:
-            p = g.default_params(d=32, k=3, lr=0.045, epochs=200, p=0.3, seed=seed, dtype=dt)
-            Mg, _ = g.gosh_embed(dev(sp.train.rowptr), dev(sp.train.col), p)
-            res[dt].append(heldout_and_fit_auc(Mg.double().cpu().numpy(), sp)[0])
-    assert np.mean(res[torch.bfloat16]) >= np.mean(res[torch.float32]) - 0.005, res
+def test_bf16_tables_reach_fp32_auc(g, c1, s1):
+    """BF16 tables (FP32 arithmetic, stochastic rounding) reach the FP32
+    tables' AUCs within 0.005 (means over 3 seeds), and the oracle's."""
+    f32 = gpu_quality(g, c1, s1, 32, torch.float32)
+    b16 = gpu_quality(g, c1, s1, 32, torch.bfloat16)
+    assert (b16.mean(0) >= f32.mean(0) - 0.005).all(), (b16, f32)
+    check_quality(b16, oracle_quality(c1, s1, 32))
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])

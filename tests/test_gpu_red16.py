@@ -9,9 +9,9 @@ is the stochastically rounded new row minus the row read, added at L2.
   (i, i+16), k = 0, one L-lane group per source) therefore leaves tables
   bit-identical to the plain stochastic-rounding stores of the paper's
   scheme (same rounding bits), for BF16 and FP16 and both lane widths;
-- with many warps racing on R-MAT rows, the atomic mode reaches the
-  sequential oracle's training-edge AUC within 0.01 (plain stores lose
-  updates on hub rows).
+- with many warps racing on the rows of the planted partition, the atomic
+  mode reaches the sequential oracle's held-out AUC within 0.005 (means over
+  3 seeds; plain stores lose updates on hub rows).
 """
 import numpy as np
 import pytest
@@ -45,22 +45,24 @@ def test_uncontended_atomic_equals_rounded_store(dtype, lanes, spp):
     assert torch.equal(out[0], out[1])
 
 
-def fit_auc(M, gr, seed=0):
-    src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
-    rng = np.random.default_rng(seed)
-    rnd = np.stack([rng.integers(0, gr.n, 20000), rng.integers(0, gr.n, 20000)], 1)
-    return oracle.link_auc(M, np.stack([src, gr.col], 1), rnd)
-
-
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 def test_atomic_16bit_reaches_oracle_auc(dtype):
+    """300 level-0 epochs on the planted partition of the small workload
+    (d = 128, k = 3, lr 0.045, default kernels): held-out AUC within 0.005 of
+    the sequential FP64 oracle's (means over 3 seeds; the oracle reaches
+    >= 0.8)."""
     g = gosh()
-    gr = synth.rmat_graph(12, 8, 41)
-    M0 = oracle.init_uniform(gr.n, 128, 0, 4).astype(np.float32) * 20
-    Mo = M0.astype(np.float64)
-    oracle.train_sequential(gr.rowptr, gr.col, Mo, 3, 0, 60, 0.045, 1e-4, 6)
+    s = synth.workload("sbm12")
+    gr = s.train
     csr = g.to_device_csr(gr.rowptr, gr.col)
-    M = torch.from_numpy(M0).to(dtype).cuda()
-    g.gosh_train_level(csr, M, 0, 60, g.default_params(d=128, k=3, lr=0.045, seed=6, dtype=dtype))
-    a_o, a_g = fit_auc(Mo, gr), fit_auc(M.double().cpu().numpy(), gr)
-    assert abs(a_o - a_g) <= 0.01, (a_o, a_g)
+    got, ref = [], []
+    for seed in (1, 2, 3):
+        M0 = oracle.init_uniform(gr.n, 128, 0, seed).astype(np.float32)
+        Mo = M0.astype(np.float64)
+        oracle.train_sequential(gr.rowptr, gr.col, Mo, 3, 0, 300, 0.045, 1e-4, seed)
+        ref.append(oracle.link_auc(Mo, s.test_pos, s.test_neg))
+        M = torch.from_numpy(M0).to(dtype).cuda()
+        g.gosh_train_level(csr, M, 0, 300, g.default_params(d=128, k=3, lr=0.045, seed=seed, dtype=dtype))
+        got.append(oracle.link_auc(M.double().cpu().numpy(), s.test_pos, s.test_neg))
+    assert np.mean(ref) >= 0.8, ref
+    assert abs(np.mean(got) - np.mean(ref)) <= 0.005, (np.round(got, 4), np.round(ref, 4))

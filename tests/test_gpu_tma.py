@@ -7,9 +7,10 @@ shared-memory ring) against the oracle.
   consecutive sources touch disjoint rows (edges (i, i+16), negatives
   excluded by k = 0) the result is still the sequential epoch: within 1e-5
   of the oracle;
-- on R-MAT scale 12 the staged kernel reaches the oracle's training-edge AUC
-  within 0.01 (FP32 and BF16, both with atomic row changes), and draws
-  exactly the oracle's update count.
+- on the planted partition of the small workload (300 level-0 epochs,
+  d = 128) the staged kernel reaches the oracle's held-out AUC within 0.005
+  (means over 3 seeds; FP32 and BF16, both with atomic row changes), and
+  draws exactly the oracle's update count.
 """
 import numpy as np
 import pytest
@@ -39,31 +40,42 @@ def test_staged_single_warp_matches_sequential():
     assert rel_fro(M.double().cpu().numpy(), Mo) <= 1e-5
 
 
-def fit_auc(M, gr, seed=0):
-    src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
-    rng = np.random.default_rng(seed)
-    rnd = np.stack([rng.integers(0, gr.n, 20000), rng.integers(0, gr.n, 20000)], 1)
-    return oracle.link_auc(M, np.stack([src, gr.col], 1), rnd)
+_oracle_held = {}
+
+
+def oracle_held(s, k, seed):
+    """Held-out AUC of the sequential oracle: 300 epochs of level-0 training
+    on the planted partition of the small workload (d = 128, lr 0.045) from
+    the init; returns (AUC, update count)."""
+    if (k, seed) not in _oracle_held:
+        Mo = oracle.init_uniform(s.train.n, 128, 0, seed).astype(np.float32).astype(np.float64)
+        _, no = oracle.train_sequential(s.train.rowptr, s.train.col, Mo, k, 0, 300, 0.045, 1e-4, seed)
+        _oracle_held[(k, seed)] = (oracle.link_auc(Mo, s.test_pos, s.test_neg), no)
+    return _oracle_held[(k, seed)]
 
 
 @pytest.mark.parametrize("dtype,lanes,ks", [(torch.float32, 32, 4), (torch.float32, 16, 6),
                                             (torch.bfloat16, 8, 4), (torch.bfloat16, 4, 6)])
 def test_staged_kernel_quality_and_counts(dtype, lanes, ks):
     g = gosh()
-    gr = synth.rmat_graph(12, 8, 41)
+    s = synth.workload("sbm12")
+    gr = s.train
     k = ks - 1
-    M0 = oracle.init_uniform(gr.n, 128, 0, 4).astype(np.float32) * 20
-    Mo = M0.astype(np.float64)
-    _, no = oracle.train_sequential(gr.rowptr, gr.col, Mo, k, 0, 60, 0.045, 1e-4, 6)
     csr = g.to_device_csr(gr.rowptr, gr.col)
-    M = torch.from_numpy(M0).to(dtype).cuda()
-    nup = torch.zeros(1, dtype=torch.int64, device="cuda")
-    p = g.default_params(d=128, k=k, lr=0.045, seed=6, dtype=dtype, lanes_per_row=lanes, samples_per_pass=-ks)
-    g.gosh_train_level(csr, M, 0, 60, p, n_updates=nup)
-    assert g.lib().gosh_device_check(None) == 0
-    assert int(nup.item()) == no
-    a_o, a_g = fit_auc(Mo, gr), fit_auc(M.double().cpu().numpy(), gr)
+    got, ref = [], []
+    for seed in (1, 2, 3):
+        a_o, no = oracle_held(s, k, seed)
+        M0 = oracle.init_uniform(gr.n, 128, 0, seed).astype(np.float32)
+        M = torch.from_numpy(M0).to(dtype).cuda()
+        nup = torch.zeros(1, dtype=torch.int64, device="cuda")
+        p = g.default_params(d=128, k=k, lr=0.045, seed=seed, dtype=dtype, lanes_per_row=lanes, samples_per_pass=-ks)
+        g.gosh_train_level(csr, M, 0, 300, p, n_updates=nup)
+        assert g.lib().gosh_device_check(None) == 0
+        assert int(nup.item()) == no
+        got.append(oracle.link_auc(M.double().cpu().numpy(), s.test_pos, s.test_neg))
+        ref.append(a_o)
     # FP32 and 16-bit rows both change by atomic additions at L2 (16-bit: the
     # stochastically rounded change), so rows staged a round ahead are read
     # stale but no update is overwritten
-    assert abs(a_o - a_g) <= 0.01, (a_o, a_g)
+    assert np.mean(ref) >= 0.8, ref
+    assert abs(np.mean(got) - np.mean(ref)) <= 0.005, (np.round(got, 4), np.round(ref, 4))

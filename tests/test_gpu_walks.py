@@ -5,8 +5,9 @@
   permuted order: the epochs are the oracle's sequential ones (walks drawn on
   host threads, permutation and negatives on the device), to 1e-5, with the
   same number of updates; a device CSR gives the same result as a host one.
-- On R-MAT scale 12 the training-edge AUC of lock-free walk training (FP32 and
-  BF16 tables) is within 0.02 of the sequential oracle's.
+- On the planted partition of the small workload the held-out AUC of
+  lock-free walk training (FP32 and BF16 tables) is within 0.005 of the
+  sequential oracle's (means over 3 seeds).
 """
 import numpy as np
 import pytest
@@ -50,22 +51,30 @@ def test_walks_single_warp_is_sequential(k):
             assert rel_fro(M.double().cpu().numpy(), Mo) <= 1e-5
 
 
+_oracle_held = {}
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_walks_auc_matches_oracle(dtype):
+    """Lock-free walk training (walks of 6, window 2, k = 3, 20 epochs, lr
+    0.1) on the planted partition of the small workload: held-out AUC within
+    0.005 of the sequential oracle's (means over 3 seeds; the oracle reaches
+    >= 0.8)."""
     g = gosh()
-    sp = synth.workload("rmat12")
-    gr = sp.train
-    src = np.repeat(np.arange(gr.n), np.diff(gr.rowptr))
-    rng = np.random.default_rng(1)
-    rnd = np.stack([rng.integers(0, gr.n, 20000), rng.integers(0, gr.n, 20000)], 1)
-    M0 = oracle.init_uniform(gr.n, 32, 0, 8)
-    Mo = M0.copy()
-    oracle.train_walks(gr.rowptr, gr.col, Mo, 3, 0, 20, 0.1, 1e-4, 8, 6, 2)
-    ao = oracle.link_auc(Mo, np.stack([src, gr.col], 1), rnd)
-    p = g.default_params(d=32, k=3, lr=0.1, seed=8, dtype=dtype, walk_length=6, walk_window=2)
-    M = torch.tensor(M0, dtype=torch.float32).to(dtype).cuda()
-    st = g.gosh_train_level_walks(gr.rowptr, gr.col, M, 0, 20, p)
-    assert st["positions"] == gr.n * oracle.walk_pairs_per_walk(6, 2)
-    ag = oracle.link_auc(M.double().cpu().numpy(), np.stack([src, gr.col], 1), rnd)
-    assert abs(ag - ao) <= 0.02, (ag, ao)
-    assert ag > 0.8
+    s = synth.workload("sbm12")
+    gr = s.train
+    got, ref = [], []
+    for seed in (1, 2, 3):
+        M0 = oracle.init_uniform(gr.n, 32, 0, seed)
+        if seed not in _oracle_held:
+            Mo = M0.copy()
+            oracle.train_walks(gr.rowptr, gr.col, Mo, 3, 0, 20, 0.1, 1e-4, seed, 6, 2)
+            _oracle_held[seed] = oracle.link_auc(Mo, s.test_pos, s.test_neg)
+        ref.append(_oracle_held[seed])
+        p = g.default_params(d=32, k=3, lr=0.1, seed=seed, dtype=dtype, walk_length=6, walk_window=2)
+        M = torch.tensor(M0, dtype=torch.float32).to(dtype).cuda()
+        st = g.gosh_train_level_walks(gr.rowptr, gr.col, M, 0, 20, p)
+        assert st["positions"] == gr.n * oracle.walk_pairs_per_walk(6, 2)
+        got.append(oracle.link_auc(M.double().cpu().numpy(), s.test_pos, s.test_neg))
+    assert np.mean(ref) >= 0.8, ref
+    assert abs(np.mean(got) - np.mean(ref)) <= 0.005, (np.round(got, 4), np.round(ref, 4))

@@ -188,6 +188,7 @@ def test_embed_two_levels_follows_alg2(orc):
 # ----------------------------------------------------------------- |E| epochs
 @pytest.mark.parametrize("e,n,nnz,want", [
     (0, 10, 50, 0),          # no epoch, no pass
+    (200, 2863, 42660, 2980),  # 200 * 14.9 = 2980.1 -> 2980
     (26, 2863, 42660, 387),  # 26 * 14.9 = 387.4 -> 387
     (3, 4, 2, 2),            # 1.5 rounds half up -> 2
     (1, 4, 1, 1),            # 0.25 -> 0, but a level given an epoch keeps one pass
@@ -200,8 +201,8 @@ def test_epoch_passes_hand_values(orc, e, n, nnz, want):
 
 
 def test_epoch_passes_update_count(orc):
-    # e_i epochs of |E_i| positive draws: the passes make e_i*|E_i| draws to
-    # within half a pass
+    # e epochs of |E| positive draws: the passes make e*|E| draws to within
+    # half a pass
     rng = np.random.default_rng(4)
     for _ in range(500):
         e, n = int(rng.integers(1, 2000)), int(rng.integers(1, 10 ** 6))
@@ -227,6 +228,10 @@ def test_level_epochs_library_equals_oracle(orc):
         for unit, name in ((0, "V"), (1, "E")):
             want = orc.level_epochs(e, p, n.tolist(), nnz.tolist(), name)
             assert g.gosh_level_epochs(e, p, D, unit, n, nnz) == want
+        # the |E| unit scales the total before the split: Sec. 3's closed
+        # forms then hold for the converted total
+        ep = orc.level_epochs(e, p, n.tolist(), nnz.tolist(), "E")
+        assert sum(ep) == orc.epoch_passes(e, int(n[0]), int(nnz[0]))
     with pytest.raises(g.GoshError):
         g.gosh_level_epochs(10, 0.3, 2, 2, [5, 3], [10, 4])
 
@@ -243,15 +248,14 @@ def train_edge_auc(orc, M, gr, seed=5):
 
 def test_oracle_learns_at_the_small_workload_schedule(orc):
     """The schedule of the small workload (d=32, k=3, lr 0.045, e=200,
-    p=0.3) with epochs of |E_i| updates (Sec. 6): the FP64 oracle fits the
+    p=0.3) with epochs of |E| updates (Sec. 6): the FP64 oracle fits the
     R-MAT scale-12 training edges (AUC >= 0.9) and, on the planted-partition
     graph of the same size, predicts held-out edges (AUC >= 0.8); with
     one-pass epochs (Alg. 3's unit) the same e leaves R-MAT near chance,
     which is why the quality bars use the |E| unit."""
     r = synth.workload("rmat12")
     M, info = orc.embed(r.train.rowptr, r.train.col, 32, 3, 0.045, 200, 0.3, seed=1, epoch_unit="E")
-    assert info["epochs"][0] == orc.epoch_passes(orc.epoch_split(200, 0.3, info["levels"])[0],
-                                                 r.train.n, r.train.nnz)
+    assert info["epochs"] == orc.epoch_split(orc.epoch_passes(200, r.train.n, r.train.nnz), 0.3, info["levels"])
     assert train_edge_auc(orc, M, r.train) >= 0.9
     Mv, _ = orc.embed(r.train.rowptr, r.train.col, 32, 3, 0.045, 200, 0.3, seed=1, epoch_unit="V")
     assert train_edge_auc(orc, Mv, r.train) < 0.7
