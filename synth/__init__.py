@@ -7,8 +7,8 @@ partitions, Karrer-Newman 2011), their CSR form, and the
 WebDataCommons) are not available; these graphs stand in for them.
 """
 from .rmat import (Graph, LinkSplit, rmat_edges, to_csr, rmat_graph, link_split,
-                   random_graph, csr_from_edges, workload, fit_pairs)
+                   random_graph, csr_from_edges, workload, fit_pairs, rmat_graph_large)
 from .sbm import sbm_edges, sbm_graph
 
 __all__ = ["Graph", "LinkSplit", "rmat_edges", "to_csr", "rmat_graph", "link_split",
-           "random_graph", "csr_from_edges", "workload", "fit_pairs", "sbm_edges", "sbm_graph"]
+           "random_graph", "csr_from_edges", "workload", "fit_pairs", "rmat_graph_large", "sbm_edges", "sbm_graph"]

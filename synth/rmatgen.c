@@ -226,3 +226,91 @@ int64_t link_split(int64_t n, const int64_t *rowptr, const int32_t *col, uint64_
     free(oldid);
     return w;
 }
+
+/*
+ * The same CSR as csr_build (symmetrised, self-loops dropped, deduplicated,
+ * isolated vertices dropped when `compact`, rows ascending) for graphs of
+ * billions of entries, in about a third of csr_build's memory and on all
+ * threads: entries are bucketed by row with a counting sort (atomic row
+ * cursors), then every row is sorted and deduplicated on its own.
+ * csr_large_count: builds the rows in a handle, returns the CSR size and the
+ * vertex count (*n_out); csr_large_fill copies them out and frees the handle.
+ */
+typedef struct {
+    int64_t n, nn, nnz;
+    int64_t *start;   /* [n+1] bucket starts */
+    int64_t *uniq;    /* [n] unique entries per row */
+    int32_t *ent;     /* [start[n]] bucketed entries, each row sorted and unique in front */
+    int32_t *newid;   /* [n] */
+} CsrLarge;
+
+static int cmp_i32(const void *a, const void *b) {
+    const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+void *csr_large_count(int64_t n, int64_t m, const uint32_t *src, const uint32_t *dst, int compact,
+                      int64_t *n_out, int64_t *nnz_out) {
+    CsrLarge *h = (CsrLarge *)calloc(1, sizeof(CsrLarge));
+    h->n = n;
+    h->start = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+    h->uniq = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    h->newid = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        if (src[i] == dst[i]) continue;
+        __atomic_fetch_add(&h->start[src[i] + 1], 1, __ATOMIC_RELAXED);
+        __atomic_fetch_add(&h->start[dst[i] + 1], 1, __ATOMIC_RELAXED);
+    }
+    for (int64_t v = 0; v < n; ++v) h->start[v + 1] += h->start[v];
+    h->ent = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->start[n] > 0 ? h->start[n] : 1));
+    int64_t *cur = h->uniq; /* cursors (reused as unique counts below) */
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < n; ++v) cur[v] = h->start[v];
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        if (src[i] == dst[i]) continue;
+        h->ent[__atomic_fetch_add(&cur[src[i]], 1, __ATOMIC_RELAXED)] = (int32_t)dst[i];
+        h->ent[__atomic_fetch_add(&cur[dst[i]], 1, __ATOMIC_RELAXED)] = (int32_t)src[i];
+    }
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t *row = h->ent + h->start[v];
+        const int64_t len = h->start[v + 1] - h->start[v];
+        qsort(row, (size_t)len, sizeof(int32_t), cmp_i32);
+        int64_t w = 0;
+        for (int64_t i = 0; i < len; ++i)
+            if (i == 0 || row[i] != row[i - 1]) row[w++] = row[i];
+        h->uniq[v] = w;
+    }
+    int64_t nn = 0, nnz = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        h->newid[v] = (!compact || h->uniq[v] > 0) ? (int32_t)nn++ : -1;
+        nnz += h->uniq[v];
+    }
+    h->nn = nn;
+    h->nnz = nnz;
+    *n_out = nn;
+    *nnz_out = nnz;
+    return h;
+}
+
+void csr_large_fill(void *handle, int64_t *rowptr, int32_t *col) {
+    CsrLarge *h = (CsrLarge *)handle;
+    rowptr[0] = 0;
+    int64_t r = 0;
+    for (int64_t v = 0; v < h->n; ++v)
+        if (h->newid[v] >= 0) { rowptr[r + 1] = rowptr[r] + h->uniq[v]; ++r; }
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t v = 0; v < h->n; ++v) {
+        if (h->newid[v] < 0) continue;
+        const int32_t *row = h->ent + h->start[v];
+        int32_t *out = col + rowptr[h->newid[v]];
+        for (int64_t i = 0; i < h->uniq[v]; ++i) out[i] = h->newid[row[i]];
+    }
+    free(h->start);
+    free(h->uniq);
+    free(h->ent);
+    free(h->newid);
+    free(h);
+}

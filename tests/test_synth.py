@@ -91,3 +91,13 @@ def test_planted_partition_graph():
     assert deg.max() > 8 * deg.mean()
     lk = synth.workload("sbm12")
     assert 0.15 < len(lk.test_pos) / (lk.train.nnz / 2 + len(lk.test_pos)) < 0.25
+
+
+@pytest.mark.parametrize("scale,ef,seed", [(8, 4, 1), (11, 16, 20211020), (13, 8, 5)])
+def test_large_builder_equals_small_builder(scale, ef, seed):
+    """The many-threaded, lower-memory CSR builder for very large graphs gives
+    exactly the CSR of the default builder."""
+    a = synth.rmat_graph(scale, ef, seed)
+    b = synth.rmat_graph_large(scale, ef, seed)
+    np.testing.assert_array_equal(a.rowptr, b.rowptr)
+    np.testing.assert_array_equal(a.col, b.col)
