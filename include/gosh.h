@@ -8,17 +8,19 @@
  *    neighbour ids int32[nnz], strictly ascending inside each row, no
  *    self-loops, symmetric (undirected graph stored in both directions).
  *  - Embedding matrices are row-major n x d, element type given by gosh_dtype,
- *    row stride d elements, base address 16-byte aligned.  d is 16, 32, 64 or
- *    128 for the resident entry points (initialisation, training, copy
+ *    row stride d elements, base address 16-byte aligned.  d is 8, 16, 32, 64
+ *    or 128 for the resident entry points (initialisation, training, copy
  *    projection, gosh_embed with the copy projection, scores); 32, 64 or 128
  *    for LargeGraphGPU, the batched entry and the learned projection.  At
- *    d = 16 a warp updates 8 (FP32) or 16 (16-bit tables) sources at once.
+ *    d = 16 a warp updates 8 (FP32) or 16 (16-bit tables) sources at once, at
+ *    d = 8 16 or 32 (Sec. 3.1.1's small-d mapping).
  *  - Every pointer is a device pointer unless its comment says otherwise.  The
  *    caller owns every buffer it passes; the library owns hierarchy handles.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Entry points are asynchronous on that stream unless marked
  *    "synchronous".  Temporary device memory is taken with cudaMallocAsync on
- *    the same stream and released before return.
+ *    the same stream (or from the caller's allocator, gosh_set_allocator)
+ *    and released before return.
  *  - No exception crosses the ABI.  Each call returns a gosh_status; on error
  *    gosh_last_error() (thread-local) holds a one-line message.  Argument
  *    errors are detected before any kernel is launched.
@@ -26,6 +28,7 @@
 #ifndef GOSH_H
 #define GOSH_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -60,7 +63,7 @@ typedef struct gosh_csr {
 } gosh_csr;
 
 typedef struct gosh_params {
-    int d;                  /* embedding dimension: 16, 32, 64 or 128 (LargeGraphGPU, walks, the
+    int d;                  /* embedding dimension: 8, 16, 32, 64 or 128 (LargeGraphGPU, walks, the
                                batched entry and the learned projection: 32, 64 or 128) */
     int k;                  /* negatives per positive, n_s (0..15; deterministic mode <= 7,
                                walks <= 3, LargeGraphGPU B * (k+1) <= 32) */
@@ -129,6 +132,10 @@ typedef struct gosh_params {
                                (default) serialises every epoch as the paper does.  Levels
                                trained in one cooperative launch, and calls that request
                                per-epoch losses, stay serialised. */
+    int large_pools;        /* LargeGraphGPU positives: 0 (default) drawn on the device from edge
+                               blocks streamed from the host; 1 drawn on host threads into sample
+                               pools (B per source per kernel, Sec. 5's scheme) streamed instead;
+                               the same samples either way */
     int epoch_unit;         /* unit of `epochs` in gosh_embed and gosh_embed_batch: 0 (default)
                                one pass over V_i (Alg. 3); 1 |E| positive draws, the unit of the
                                paper's experiments (Sec. 6 setup): e becomes round(e * nnz_0 /
@@ -193,6 +200,24 @@ gosh_status gosh_params_default(gosh_params *p);
  * unit, or a pass count beyond INT_MAX. */
 gosh_status gosh_level_epochs(int epochs, double p, int D, int epoch_unit, const int64_t *n, const int64_t *nnz,
                               int *out);
+
+/* Caller-provided device memory.  alloc(bytes, stream, ctx) returns device
+ * memory of at least `bytes` bytes, 256-byte aligned, usable in stream order on
+ * `stream` (a cudaStream_t, NULL = legacy default stream), or NULL when it
+ * cannot; free(ptr, bytes, stream, ctx) takes it back in stream order.  A
+ * framework that owns device memory through its own caching allocator (e.g.
+ * PyTorch's) installs it here so that the library's working buffers come from
+ * it: every call's workspaces (deterministic-mode batches, LargeGraphGPU
+ * bins, gosh_embed's level tables, coarsening temporaries) and the coarse
+ * levels a hierarchy handle holds.  Not routed: the learned projection's
+ * weights (created with the network), the prefix sum's cached per-stream
+ * status words (a few KB) and the 4-byte device error word.  Process-wide;
+ * both functions, or neither (NULL, NULL: back to the stream-ordered pool).
+ * Each block is returned to the allocator that provided it, so the allocator
+ * may change between calls, but not while a call runs. */
+typedef void *(*gosh_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*gosh_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+gosh_status gosh_set_allocator(gosh_alloc_fn alloc, gosh_free_fn free, void *ctx);
 
 /* Thread-local message of the last failed call ("" if none). */
 const char *gosh_last_error(void);
@@ -345,7 +370,9 @@ gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int level, int 
  * (so K = 1, B = 1 draws exactly the samples of gosh_train_level) and
  * 3 | (a*K+b) << 8 otherwise.  Parts move between pinned host memory and
  * params->p_gpu device bins (farthest-next-use eviction), edge blocks
- * (built once on host threads) through params->s_gpu bins, all
+ * (built once on host threads) or, with params->large_pools = 1, each
+ * kernel's sample pool (its positives drawn on host threads, the same
+ * samples; gosh_large_pool) through params->s_gpu bins, all
  * asynchronously on per-bin streams with cudaEvent dependencies; kernels
  * alternate over two streams and may overlap (lock-free, as in the paper),
  * or run one after another on one stream when params->large_serial is 1.
@@ -403,6 +430,19 @@ gosh_status gosh_walk_order(int64_t positions, int level, int epoch, uint64_t se
  * m_ab and m_ba only.  g: host CSR, checked as by gosh_walk_pairs. */
 gosh_status gosh_large_block(const gosh_csr *g, int K, int a, int b, int64_t *m_ab, int64_t *m_ba, int64_t *rp_ab,
                              int32_t *col_ab, int64_t *rp_ba, int32_t *col_ba);
+
+/* The sample pool of part pair (a, b), 0 <= b <= a < K, in round `round`,
+ * exactly as gosh_train_level_large with large_pools = 1 draws it on host
+ * threads (no GPU use): V is split into K contiguous parts; for every source
+ * u of the pair (V^a, then V^b when a != b) and j < B, out[s * B + j] is the
+ * local id (in the opposite part) of a neighbour of u drawn uniformly from
+ * its neighbours in the opposite part with Philox word 0 of block
+ * (u, 0, level << 32 | round*B + j, tag), tag 0 when K = 1 and
+ * 3 | (a*K + b) << 8 otherwise; -1 when u has no neighbour there.
+ * out: host int32[(|V^a| + (a != b ? |V^b| : 0)) * B].  g: host CSR, checked
+ * as by gosh_walk_pairs. */
+gosh_status gosh_large_pool(const gosh_csr *g, int K, int a, int b, int round, int B, int level, uint64_t seed,
+                            uint64_t graph_id, int32_t *out);
 
 /* Host-only simulation of the LargeGraphGPU part-bin schedule (no GPU use):
  * for `rounds` rounds over K parts and p_gpu bins, with the bin choice

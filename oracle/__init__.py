@@ -81,6 +81,7 @@ def lib():
                                        vp, vp]),
             "orc_train_large": (None, [i64, vp, vp, vp, i32, i32, i32, i32, f64, f64, u64, u64, i32, i32,
                                        vp, vp]),
+            "orc_large_pool": (None, [i64, vp, vp, i32, i32, i32, i32, i32, i32, u64, u64, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -202,6 +203,18 @@ def train_large(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, K, B, grap
     return int(nup[0]), int(npos[0])
 
 
+def large_pool(rowptr, col, K, a, b, r, B, level, seed, graph=0) -> np.ndarray:
+    """Positives of pair (a, b) in round r for each of its sources (Sec. 5's
+    host sample pool): int32 [sources, B] of local ids, -1 = no neighbour."""
+    rowptr, col = _csr(rowptr, col)
+    n = len(rowptr) - 1
+    st = [n * i // K for i in range(K + 1)]
+    ns = (st[a + 1] - st[a]) + ((st[b + 1] - st[b]) if a != b else 0)
+    out = np.zeros((max(ns, 1), B), dtype=np.int32)
+    lib().orc_large_pool(n, _p(rowptr), _p(col), K, a, b, r, B, level, seed, graph, _p(out))
+    return out[:ns]
+
+
 def train_deterministic(rowptr, col, M, k, level, epochs, lr, lr_floor, seed, m, graph=0):
     rowptr, col = _csr(rowptr, col)
     assert M.dtype == np.float64 and M.flags.c_contiguous
@@ -302,28 +315,29 @@ def epoch_split(e: int, p: float, D: int) -> list[int]:
     return out
 
 
-def epoch_passes(e_i: int, n_i: int, nnz_i: int) -> int:
-    """Passes over V_i for e_i epochs of |E_i| updates each (Sec. 6's setup
-    defines one epoch as |E| updates; one Alg. 3 pass over V_i makes |V_i|
-    positive draws).  Reading: |E_i| counts CSR entries (both directions, the
-    count the density delta = |E_i|/|V_i| of Alg. 4 uses), the quotient
-    e_i*|E_i|/|V_i| is rounded half up, and a level given any epoch keeps at
-    least one pass."""
-    if e_i == 0:
+def epoch_passes(e: int, n0: int, nnz0: int) -> int:
+    """Alg. 3 passes for e epochs of |E| updates (Sec. 6's setup defines one
+    epoch as |E| updates and adjusts the epoch count accordingly; one Alg. 3
+    pass makes |V| positive draws).  Reading: the conversion applies to the
+    total e of Alg. 2, by the input graph's |E|/|V|; |E| counts CSR entries
+    (both directions, the count in Alg. 4's density delta = |E_i|/|V_i|);
+    the quotient is rounded half up, and any e >= 1 keeps at least one
+    pass."""
+    if e == 0:
         return 0
     from fractions import Fraction
-    q = Fraction(e_i * nnz_i, n_i)
+    q = Fraction(e * nnz0, n0)
     return max(1, math.floor(q + Fraction(1, 2)))
 
 
 def level_epochs(e: int, p: float, sizes, nnzs, epoch_unit: str = "V") -> list[int]:
-    """Passes per level: the Sec. 3 split in epochs, then, for the |E| unit,
-    each level's epochs converted by epoch_passes."""
-    ep = epoch_split(e, p, len(sizes))
-    if epoch_unit == "V":
-        return ep
-    assert epoch_unit == "E"
-    return [epoch_passes(ep[i], sizes[i], nnzs[i]) for i in range(len(sizes))]
+    """Passes per level: for the |E| unit the total converted by
+    epoch_passes on G_0, then the Sec. 3 split over the levels."""
+    if epoch_unit == "E":
+        e = epoch_passes(e, sizes[0], nnzs[0])
+    else:
+        assert epoch_unit == "V"
+    return epoch_split(e, p, len(sizes))
 
 
 def project_copy(mp, Mc) -> np.ndarray:
@@ -364,7 +378,7 @@ def embed(rowptr, col, d, k, lr, e, p, seed, threshold=100, shrink=0.8, lr_floor
     algorithm returns M_0, and the single-level configuration must train).
     M_{D-1} starts from the init rounded to the storage precision; training
     runs in FP64.  epoch_unit "V": an epoch is one Alg. 3 pass over V_i; "E":
-    an epoch is |E_i| updates (Sec. 6), see epoch_passes.  Returns (M_0, info)."""
+    an epoch is |E| updates (Sec. 6), see epoch_passes.  Returns (M_0, info)."""
     if coarsening:
         graphs, maps = mec_hierarchy(rowptr, col, threshold, shrink)
     else:

@@ -598,6 +598,39 @@ void orc_train_walks(int64_t n, const int64_t *rowptr, const int32_t *col, doubl
 /* ------------------------------------------------------------------------ */
 enum { TAG_LARGE = 3 };
 
+/* The positives that pair (a, b) of round r draws for each of its sources
+ * (V^a, then V^b when a != b): out[s*B + j] = the local id (in the opposite
+ * part) of the positive of slot group j, drawn as orc_train_large draws it,
+ * or -1 when the source has no neighbour in the opposite part.  (Sec. 5
+ * draws these on the host and sends them as sample pools.) */
+void orc_large_pool(int64_t n, const int64_t *rowptr, const int32_t *col, int K, int a, int b, int r, int B,
+                    int level, uint64_t seed, uint64_t graph, int32_t *out) {
+    uint64_t key[2] = {seed, graph};
+    const uint64_t tag = K == 1 ? (uint64_t)TAG_SAMPLE : ((uint64_t)TAG_LARGE | ((uint64_t)(a * K + b) << 8));
+    const int64_t a0 = n * a / K, a1 = n * (a + 1) / K, b0 = n * b / K, b1 = n * (b + 1) / K;
+    int64_t s = 0;
+    for (int side = 0; side < (a == b ? 1 : 2); ++side) {
+        const int64_t own0 = side == 0 ? a0 : b0, own1 = side == 0 ? a1 : b1;
+        const int64_t opp0 = side == 0 ? b0 : a0, opp1 = side == 0 ? b1 : a1;
+        for (int64_t ug = own0; ug < own1; ++ug, ++s) {
+            int64_t lo = rowptr[ug], hi = rowptr[ug + 1];
+            while (lo < hi && col[lo] < opp0) ++lo;
+            int64_t e = lo;
+            while (e < hi && col[e] < opp1) ++e;
+            for (int j = 0; j < B; ++j) {
+                if (e == lo) {
+                    out[s * B + j] = -1;
+                    continue;
+                }
+                uint64_t w[4];
+                uint64_t ctr[4] = {(uint64_t)ug, 0, ((uint64_t)(uint32_t)level << 32) | (uint32_t)(r * B + j), tag};
+                orc_philox4x64(ctr, key, w);
+                out[s * B + j] = (int32_t)(col[lo + (int64_t)uniform_below(w[0], (uint64_t)(e - lo))] - opp0);
+            }
+        }
+    }
+}
+
 void orc_train_large(int64_t n, const int64_t *rowptr, const int32_t *col, double *M, int d, int k, int level,
                      int epochs, double lr, double lr_floor, uint64_t seed, uint64_t graph, int K, int B,
                      int64_t *n_updates, int64_t *n_positives) {

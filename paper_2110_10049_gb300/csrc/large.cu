@@ -48,6 +48,8 @@ struct PairArgs {
     const int32_t *col_ab;
     const int64_t *rp_ba;             // [nb+1] block (b,a) (a != b)
     const int32_t *col_ba;
+    const int32_t *pool;              // host sample pool (or null: positives from the edge block):
+                                      // B positives per source (V^a, then V^b), local ids, -1 = none
     int same;                         // a == b
     int B, k;
     int epochs_total;                 // e of this level
@@ -83,7 +85,9 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
             const int32_t *cl = sideA ? a.col_ab : a.col_ba;
             const int64_t nopp = sideA ? a.nb : a.na;
             const int64_t ug = (sideA ? a.start_a : a.start_b) + u;
-            const int64_t lo = rp[u], cnt = rp[u + 1] - lo;
+            const int32_t *pp = a.pool ? a.pool + s * a.B : nullptr;
+            const int64_t lo = pp ? 0 : rp[u];
+            const int64_t cnt = pp ? (__ldg(pp) >= 0 ? 1 : 0) : rp[u + 1] - lo;
             for (int j = 0; j < a.B; ++j) {
                 const uint32_t t = (uint32_t)(a.round * a.B + j);
                 const int ks = j * (a.k + 1);
@@ -96,7 +100,8 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
                         if (m <= a.k) {
                             int32_t id;
                             if (m == 0) {
-                                id = cnt > 0 ? __ldg(cl + lo + (int64_t)uniform_index(w.w[0], (uint64_t)cnt)) : -1;
+                                if (pp) id = __ldg(pp + j);
+                                else id = cnt > 0 ? __ldg(cl + lo + (int64_t)uniform_index(w.w[0], (uint64_t)cnt)) : -1;
                             } else {
                                 const int64_t x = (int64_t)uniform_index(w.w[q], (uint64_t)nopp);
                                 id = (a.same && x == u) ? -1 : (int32_t)x;
@@ -273,8 +278,8 @@ PairLaunch pick_pair_kernel(gosh_dtype dt, int d) {
     return nullptr;
 }
 
-// Pinned host memory for edge blocks, kept across calls.
-PinnedArena g_pinned;
+// Pinned host memory for edge blocks and for the sample-pool ring, kept across calls.
+PinnedArena g_pinned, g_pinned_pools;
 
 // Edge block (a, b) of one pair, built once on the host in pinned memory.
 struct Block {
@@ -287,7 +292,7 @@ struct Block {
 
 }  // namespace
 
-size_t large_release_pinned() { return g_pinned.release(); }
+size_t large_release_pinned() { return g_pinned.release() + g_pinned_pools.release(); }
 
 // Inside-out order of one round: (0,0),(1,0),(1,1),(2,0),(2,1),(2,2),...
 void large_pair_order(int K, std::vector<std::pair<int, int>> &order) {
@@ -443,6 +448,51 @@ struct EdgeBlocks {
     }
 };
 
+// Host sample pools (Sec. 5: the positive samples are generated on the host
+// in parallel and sent to the GPU as they are needed; the negatives are drawn
+// on the GPU).  The pool of kernel K_{a,b} in round r holds, for every source
+// of the pair (V^a, then V^b when a != b), its B positives as local ids of
+// the opposite part, or -1 when it has no neighbour there.  A positive is
+// drawn exactly as the device draws it from an edge block (Philox word 0 of
+// block (u, 0, level << 32 | r*B + j, tag), a uniform neighbour in the
+// opposite part's id range), so both streaming forms train on the same samples.
+struct PoolDraw {
+    const int64_t *rowptr = nullptr;
+    const int32_t *col = nullptr;
+    std::vector<int64_t> start;
+    int K = 1, B = 1;
+    uint32_t level = 0;
+    uint64_t seed = 0, graph = 0;
+
+    int64_t sources(int a, int b) const {
+        return (start[a + 1] - start[a]) + (a != b ? start[b + 1] - start[b] : 0);
+    }
+    // sources [s0, s1) of pair (a, b) in round r -> out[(s - s0) * B + j]
+    void fill(int a, int b, int r, int64_t s0, int64_t s1, int32_t *out) const {
+        const int64_t na = start[a + 1] - start[a];
+        const uint64_t tag = K == 1 ? kTagSample : (kTagLarge | ((uint64_t)(a * K + b) << 8));
+        for (int64_t s = s0; s < s1; ++s) {
+            const bool sideA = s < na;
+            const int own = sideA ? a : b, opp = sideA ? b : a;
+            const int64_t ug = start[own] + (sideA ? s : s - na);
+            const int32_t *row = col + rowptr[ug], *end = col + rowptr[ug + 1];
+            const int32_t *lo = std::lower_bound(row, end, (int32_t)start[opp]);
+            const int32_t *hi = std::lower_bound(lo, end, (int32_t)start[opp + 1]);
+            const uint64_t cnt = (uint64_t)(hi - lo);
+            int32_t *o = out + (s - s0) * B;
+            for (int j = 0; j < B; ++j) {
+                if (cnt == 0) {
+                    o[j] = -1;
+                    continue;
+                }
+                const uint32_t t = (uint32_t)(r * B + j);
+                const Philox4 w = philox4x64_10((uint64_t)ug, 0, ((uint64_t)level << 32) | t, tag, seed, graph);
+                o[j] = lo[uniform_index(w.w[0], cnt)] - (int32_t)start[opp];
+            }
+        }
+    }
+};
+
 // The bin that holds part x for kernel i of seq: the bin already holding it
 // (*load = false), else (*load = true) an empty bin, else the bin whose part
 // is next used farthest ahead in seq.  A bin holding a part of kernel i is
@@ -562,6 +612,29 @@ gosh_status gosh_large_block(const gosh_csr *g, int K, int a, int b, int64_t *m_
     return GOSH_OK;
 }
 
+gosh_status gosh_large_pool(const gosh_csr *g, int K, int a, int b, int round, int B, int level, uint64_t seed,
+                            uint64_t graph_id, int32_t *out) {
+    clear_error();
+    GOSH_CHECK_ARG(g && !g->on_device && g->rowptr && g->col && out, "needs a host CSR and an output");
+    GOSH_CHECK_ARG(g->n >= 1 && g->n < (int64_t(1) << 31), "bad n");
+    GOSH_CHECK_ARG(K >= 1 && K <= g->n, "need 1 <= K <= n");
+    GOSH_CHECK_ARG(0 <= b && b <= a && a < K, "need 0 <= b <= a < K");
+    GOSH_CHECK_ARG(B >= 1 && round >= 0 && level >= 0, "bad B / round / level");
+    GOSH_TRY(check_host_csr(g->rowptr, g->col, g->n, false));
+    PoolDraw pd;
+    pd.rowptr = g->rowptr;
+    pd.col = g->col;
+    pd.start.resize(K + 1);
+    for (int i = 0; i <= K; ++i) pd.start[i] = g->n * i / K;
+    pd.K = K;
+    pd.B = B;
+    pd.level = (uint32_t)level;
+    pd.seed = seed;
+    pd.graph = graph_id;
+    pd.fill(a, b, round, 0, pd.sources(a, b), out);
+    return GOSH_OK;
+}
+
 gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int epochs, const gosh_params *p,
                                    void *stream, gosh_large_stats *stats) {
     clear_error();
@@ -597,21 +670,41 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     std::vector<int64_t> start(K + 1);
     for (int i = 0; i <= K; ++i) start[i] = n * i / K;
 
-    // ---- edge blocks (pinned, built on host threads) ----
-    // Only the count pass and the layout run up front (EdgeBlocks::plan);
-    // the blocks then sit in one pinned region (kept across calls,
-    // grow-only: pinning host memory costs far more than building), and
-    // their row chunks are filled by the threads that overlap the stream
-    // loop below.
+    // ---- positive samples: edge blocks or host sample pools ----
+    // Edge blocks (default): only the count pass and the layout run up front
+    // (EdgeBlocks::plan); the blocks then sit in one pinned region (kept
+    // across calls, grow-only: pinning host memory costs far more than
+    // building), and their row chunks are filled by the threads that overlap
+    // the stream loop below.  Sample pools (large_pools = 1): host threads
+    // draw every kernel's positives, in kernel order, into a ring of pinned
+    // slots, running ahead of the stream loop by up to the ring's length.
+    const bool use_pools = p->large_pools != 0;
     const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::pair<int, int>> order;
+    large_pair_order(K, order);
     EdgeBlocks eb;
-    eb.plan(g->rowptr, g->col, K, start, nt);
-    const std::vector<std::pair<int, int>> &order = eb.order;
-    const std::vector<Block> &blocks = eb.blocks;
-    const size_t max_block = eb.max_block;
     PinnedLease lease(g_pinned);
-    GOSH_TRY(lease.acquire(eb.total_bytes, "edge blocks"));
-    eb.place(lease.ptr);
+    PoolDraw pd;
+    size_t max_pool = 0;
+    if (!use_pools) {
+        eb.plan(g->rowptr, g->col, K, start, nt);
+        GOSH_TRY(lease.acquire(eb.total_bytes, "edge blocks"));
+        eb.place(lease.ptr);
+    } else {
+        pd.rowptr = g->rowptr;
+        pd.col = g->col;
+        pd.start = start;
+        pd.K = K;
+        pd.B = p->B;
+        pd.level = (uint32_t)level;
+        pd.seed = p->seed;
+        pd.graph = p->graph_id;
+        for (auto &pr : order)
+            max_pool = std::max(max_pool, (size_t)pd.sources(pr.first, pr.second) * p->B * sizeof(int32_t));
+        max_pool = (max_pool + 255) / 256 * 256;
+    }
+    const std::vector<Block> &blocks = eb.blocks;
+    const size_t max_block = use_pools ? max_pool : eb.max_block;
     int64_t part_rows = 0;
     for (int i = 0; i < K; ++i) part_rows = std::max(part_rows, start[i + 1] - start[i]);
     const size_t bin_bytes = row * part_rows;
@@ -626,8 +719,6 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     // while the stream loop below already sends the finished blocks: block i's
     // first copy to the device waits only for block i (the items are ordered
     // by block, so the first blocks finish first).
-    std::vector<int> items_left(blocks.size(), 0);
-    for (const auto &it : eb.items) ++items_left[eb.sides[it.side].blk];
     struct BlockGate {
         std::mutex mu;
         std::condition_variable cv;
@@ -642,20 +733,24 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
             for (auto &x : th) x.join();
         }
     } gate;
-    gate.left = items_left;
-    for (int t = 0; t < nt; ++t)
-        gate.th.emplace_back([&]() {
-            for (size_t k = gate.next.fetch_add(1); k < eb.items.size(); k = gate.next.fetch_add(1)) {
-                eb.fill(k);
-                const int blk = eb.sides[eb.items[k].side].blk;
-                bool done;
-                {
-                    std::lock_guard<std::mutex> lk(gate.mu);
-                    done = --gate.left[blk] == 0;
+    if (!use_pools) {
+        std::vector<int> items_left(blocks.size(), 0);
+        for (const auto &it : eb.items) ++items_left[eb.sides[it.side].blk];
+        gate.left = items_left;
+        for (int t = 0; t < nt; ++t)
+            gate.th.emplace_back([&]() {
+                for (size_t k = gate.next.fetch_add(1); k < eb.items.size(); k = gate.next.fetch_add(1)) {
+                    eb.fill(k);
+                    const int blk = eb.sides[eb.items[k].side].blk;
+                    bool done;
+                    {
+                        std::lock_guard<std::mutex> lk(gate.mu);
+                        done = --gate.left[blk] == 0;
+                    }
+                    if (done) gate.cv.notify_all();
                 }
-                if (done) gate.cv.notify_all();
-            }
-        });
+            });
+    }
 
     // host M pinned for async copies (registered in place if the caller's is pageable)
     bool registered = false;
@@ -712,6 +807,74 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
     std::vector<std::pair<int, int>> seq;
     for (int r = 0; r < rounds; ++r)
         for (auto &pr : order) seq.push_back(pr);
+
+    // Sample pools: items of kPoolChunk sources of kernel i, taken by host
+    // threads in kernel order; kernel i's pool goes into ring slot i % R once
+    // the copy of the pool that used the slot before (kernel i - R) has
+    // completed; the stream loop sends pool i when all its items are done.
+    constexpr int64_t kPoolChunk = 16384;
+    const int R = std::max(2, p->s_gpu + 2);
+    PinnedLease pool_lease(g_pinned_pools);
+    struct PoolGate {
+        std::mutex mu;
+        std::condition_variable cv;
+        std::vector<int> left;
+        std::vector<cudaEvent_t> copied;  // H2D copy of pool i (recorded by the stream loop)
+        std::atomic<size_t> next{0};
+        bool stop = false;
+        std::vector<std::thread> th;
+        ~PoolGate() {
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                stop = true;
+            }
+            cv.notify_all();
+            for (auto &x : th) x.join();
+        }
+    } pgate;
+    struct PoolItem {
+        size_t kernel;
+        int64_t s0, s1;
+    };
+    std::vector<PoolItem> pitems;
+    if (use_pools) {
+        GOSH_TRY(pool_lease.acquire(max_pool * R, "sample pools"));
+        pgate.left.assign(seq.size(), 0);
+        pgate.copied.assign(seq.size(), nullptr);
+        for (size_t i = 0; i < seq.size(); ++i) {
+            const int64_t ns = pd.sources(seq[i].first, seq[i].second);
+            for (int64_t s0 = 0; s0 < ns; s0 += kPoolChunk) {
+                pitems.push_back({i, s0, std::min(ns, s0 + kPoolChunk)});
+                ++pgate.left[i];
+            }
+        }
+        const size_t per_round = order.size();
+        for (int t = 0; t < nt; ++t)
+            pgate.th.emplace_back([&, per_round]() {
+                for (size_t k = pgate.next.fetch_add(1); k < pitems.size(); k = pgate.next.fetch_add(1)) {
+                    const PoolItem &it = pitems[k];
+                    const size_t i = it.kernel;
+                    if (i >= (size_t)R) {  // the slot's previous pool must be on the device
+                        cudaEvent_t ev = nullptr;
+                        {
+                            std::unique_lock<std::mutex> lk(pgate.mu);
+                            pgate.cv.wait(lk, [&] { return pgate.stop || pgate.copied[i - R] != nullptr; });
+                            if (pgate.stop) return;
+                            ev = pgate.copied[i - R];
+                        }
+                        cudaEventSynchronize(ev);
+                    }
+                    int32_t *slot = reinterpret_cast<int32_t *>(pool_lease.ptr + (i % R) * max_pool);
+                    pd.fill(seq[i].first, seq[i].second, (int)(i / per_round), it.s0, it.s1, slot + it.s0 * p->B);
+                    bool done;
+                    {
+                        std::lock_guard<std::mutex> lk(pgate.mu);
+                        done = --pgate.left[i] == 0;
+                    }
+                    if (done) pgate.cv.notify_all();
+                }
+            });
+    }
     std::vector<int> bin_part(p->p_gpu, -1);
     std::vector<std::vector<cudaEvent_t>> bin_users(p->p_gpu);     // kernels using the bin since its load
     std::vector<cudaEvent_t> bin_ready(p->p_gpu, nullptr);
@@ -751,14 +914,32 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
         const int r = (int)(i / order.size());
         const int ba = ensure(a, i);
         const int bb = ensure(b, i);
-        // SCT: edge block into the next edge bin
+        // SCT: the edge block, or the kernel's sample pool, into the next bin
         const int eb = (int)(i % p->s_gpu);
-        const Block &blk = blocks[i % order.size()];
-        if (i < order.size()) gate.wait((int)i);
+        const Block *blk = use_pools ? nullptr : &blocks[i % order.size()];
         if (ebin_free[eb]) cudaStreamWaitEvent(estr[eb], ebin_free[eb], 0);
-        cudaMemcpyAsync(ebin[eb].ptr, blk.base, blk.bytes, cudaMemcpyHostToDevice, estr[eb]);
-        block_bytes += blk.bytes;
-        cudaEvent_t e_ready = new_event(estr[eb]);
+        cudaEvent_t e_ready;
+        if (!use_pools) {
+            if (i < order.size()) gate.wait((int)i);
+            cudaMemcpyAsync(ebin[eb].ptr, blk->base, blk->bytes, cudaMemcpyHostToDevice, estr[eb]);
+            block_bytes += blk->bytes;
+            e_ready = new_event(estr[eb]);
+        } else {
+            {
+                std::unique_lock<std::mutex> lk(pgate.mu);
+                pgate.cv.wait(lk, [&] { return pgate.left[i] == 0; });
+            }
+            const size_t bytes = (size_t)pd.sources(a, b) * p->B * sizeof(int32_t);
+            cudaMemcpyAsync(ebin[eb].ptr, pool_lease.ptr + (i % R) * max_pool, bytes, cudaMemcpyHostToDevice,
+                            estr[eb]);
+            block_bytes += bytes;
+            e_ready = new_event(estr[eb]);
+            {
+                std::lock_guard<std::mutex> lk(pgate.mu);
+                pgate.copied[i] = e_ready;
+            }
+            pgate.cv.notify_all();
+        }
         // KT
         cudaStream_t ks = kstr[p->large_serial ? 0 : i % 2];
         cudaStreamWaitEvent(ks, bin_ready[ba], 0);
@@ -772,10 +953,14 @@ gosh_status gosh_train_level_large(const gosh_csr *g, void *M, int level, int ep
         pa.nb = start[b + 1] - start[b];
         pa.start_a = start[a];
         pa.start_b = start[b];
-        pa.rp_ab = reinterpret_cast<const int64_t *>(eb0 + ((char *)blk.rp_ab - blk.base));
-        pa.col_ab = reinterpret_cast<const int32_t *>(eb0 + ((char *)blk.col_ab - blk.base));
-        pa.rp_ba = reinterpret_cast<const int64_t *>(eb0 + ((char *)blk.rp_ba - blk.base));
-        pa.col_ba = reinterpret_cast<const int32_t *>(eb0 + ((char *)blk.col_ba - blk.base));
+        if (!use_pools) {
+            pa.rp_ab = reinterpret_cast<const int64_t *>(eb0 + ((char *)blk->rp_ab - blk->base));
+            pa.col_ab = reinterpret_cast<const int32_t *>(eb0 + ((char *)blk->col_ab - blk->base));
+            pa.rp_ba = reinterpret_cast<const int64_t *>(eb0 + ((char *)blk->rp_ba - blk->base));
+            pa.col_ba = reinterpret_cast<const int32_t *>(eb0 + ((char *)blk->col_ba - blk->base));
+        } else {
+            pa.pool = reinterpret_cast<const int32_t *>(eb0);
+        }
         pa.same = a == b;
         pa.B = p->B;
         pa.k = p->k;

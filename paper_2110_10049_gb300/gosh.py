@@ -45,7 +45,7 @@ class gosh_params(C.Structure):
                 ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int),
                 ("walk_length", C.c_int), ("walk_window", C.c_int), ("large_serial", C.c_int),
                 ("large_evict", C.c_int), ("overlap_min_vertices", C.c_int64), ("epoch_overlap", C.c_int),
-                ("epoch_unit", C.c_int)]
+                ("large_pools", C.c_int), ("epoch_unit", C.c_int)]
 
 
 class gosh_walk_stats(C.Structure):
@@ -120,6 +120,7 @@ def lib() -> C.CDLL:
             "gosh_project_learned": [vp, vp, vp, P(gosh_csr), vp, i32, i32, vp],
             "gosh_round_stochastic": [vp, vp, i64, i32, u64, vp],
             "gosh_level_epochs": [i32, f64, i32, i32, vp, vp, vp],
+            "gosh_large_pool": [P(gosh_csr), i32, i32, i32, i32, i32, i32, u64, u64, vp],
         }
         L.gosh_mlp_free.restype = None
         L.gosh_mlp_free.argtypes = [vp]
@@ -139,6 +140,8 @@ def lib() -> C.CDLL:
         L.gosh_hierarchy_levels.argtypes = [vp]
         L.gosh_hierarchy_free.restype = None
         L.gosh_hierarchy_free.argtypes = [vp]
+        L.gosh_set_allocator.restype = C.c_int
+        L.gosh_set_allocator.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
 
@@ -419,6 +422,52 @@ def gosh_large_block(rowptr, col, K, a, b):
     if a == b:
         return rp_ab, col_ab[:m_ab.value], None, None
     return rp_ab, col_ab[:m_ab.value], rp_ba, col_ba[:m_ba.value]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_allocator_refs = None  # keeps the installed callbacks alive
+
+
+def gosh_set_allocator(alloc=None, free=None):
+    """Installs Python callables as the library's device allocator:
+    alloc(bytes, stream) -> int device pointer (0 on failure) and
+    free(ptr, bytes, stream); both None restores the stream-ordered pool."""
+    global _allocator_refs
+    if alloc is None and free is None:
+        _check("gosh_set_allocator", lib().gosh_set_allocator(None, None, None))
+        _allocator_refs = None
+        return
+    a = ALLOC_FN(lambda nbytes, stream, ctx: alloc(int(nbytes), stream or 0) or None)
+    f = FREE_FN(lambda ptr, nbytes, stream, ctx: free(int(ptr), int(nbytes), stream or 0))
+    _check("gosh_set_allocator", lib().gosh_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), None))
+    _allocator_refs = (a, f)
+
+
+def use_torch_allocator(device=None):
+    """Serves the library's device memory from PyTorch's caching allocator
+    (the memory then shows in torch.cuda.memory_allocated)."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    gosh_set_allocator(lambda n, stream: torch.cuda.caching_allocator_alloc(n, dev, stream),
+                       lambda ptr, n, stream: torch.cuda.caching_allocator_delete(ptr))
+
+
+def gosh_large_pool(rowptr, col, K, a, b, rnd, B, level, seed, graph_id=0) -> np.ndarray:
+    """The host sample pool of pair (a, b) in round rnd (no GPU use): int32
+    [sources, B] of local ids in the opposite part, -1 = no neighbour there."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    co = np.ascontiguousarray(col, dtype=np.int32)
+    if co.size == 0:
+        co = np.zeros(1, dtype=np.int32)
+    n = len(rp) - 1
+    start = [n * i // K for i in range(K + 1)]
+    ns = (start[a + 1] - start[a]) + ((start[b + 1] - start[b]) if a != b else 0)
+    out = np.empty((max(ns, 1), B), dtype=np.int32)
+    cg = gosh_csr(n, rp.ctypes.data, co.ctypes.data, 0)
+    _check("gosh_large_pool", lib().gosh_large_pool(C.byref(cg), K, a, b, rnd, B, level, seed, graph_id,
+                                                    out.ctypes.data))
+    return out[:ns]
 
 
 def gosh_release_host_buffers() -> int:

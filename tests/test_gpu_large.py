@@ -15,7 +15,10 @@
   AUC of the sequential oracle within 0.005 on the planted partition,
   launches rounds * K(K+1)/2 kernels, and the global counter caps positives
   at e * |V|;
-- BF16 tables run through the same path.
+- BF16 tables run through the same path;
+- every case above also runs with host sample pools (large_pools = 1: the
+  positives drawn on host threads and streamed, Sec. 5's scheme), which
+  draw the same samples as the edge blocks.
 """
 import numpy as np
 import pytest
@@ -45,8 +48,9 @@ def test_single_part_equals_resident_step():
     assert rel_fro(Mh, Md.cpu().numpy()) <= 1e-5
 
 
+@pytest.mark.parametrize("pools", [0, 1])
 @pytest.mark.parametrize("K,B,seed", [(2, 2, 3), (3, 1, 5), (2, 3, 9)])
-def test_serial_parts_equal_sequential_oracle(K, B, seed):
+def test_serial_parts_equal_sequential_oracle(K, B, seed, pools):
     # every part pair has at most 32 sources: one tile, one warp, one source
     # at a time; with the kernels in stream order the device run is the
     # oracle's sequential LargeGraphGPU
@@ -57,7 +61,8 @@ def test_serial_parts_equal_sequential_oracle(K, B, seed):
     Mo = M0.copy()
     nup_o, npos_o = oracle.train_large(gr.rowptr, gr.col, Mo, 3, 0, e, 0.05, 1e-4, seed, K, B)
     Mh = M0.astype(np.float32)
-    p = g.default_params(d=128, k=3, lr=0.05, seed=seed, B=B, large_parts=K, p_gpu=2, s_gpu=1, large_serial=1)
+    p = g.default_params(d=128, k=3, lr=0.05, seed=seed, B=B, large_parts=K, p_gpu=2, s_gpu=1, large_serial=1,
+                         large_pools=pools)
     st = g.gosh_train_level_large(gr.rowptr, gr.col, Mh, 0, e, p)
     assert st["positives"] == npos_o
     assert st["updates"] == nup_o
@@ -76,8 +81,9 @@ def golden_budget_cases():
     return out
 
 
+@pytest.mark.parametrize("pools", [0, 1])
 @pytest.mark.parametrize("n,K,B,k,e,npos,nup", golden_budget_cases())
-def test_budget_hand_count_on_device(n, K, B, k, e, npos, nup):
+def test_budget_hand_count_on_device(n, K, B, k, e, npos, nup, pools):
     """The global positive budget as counted by hand (stars cut into
     one-vertex parts: every draw is forced), run on the device in stream
     order; the embeddings equal the sequential oracle's."""
@@ -88,7 +94,8 @@ def test_budget_hand_count_on_device(n, K, B, k, e, npos, nup):
     nup_o, npos_o = oracle.train_large(gr.rowptr, gr.col, Mo, k, 0, e, 0.05, 1e-4, 7, K, B)
     assert (npos_o, nup_o) == (npos, nup)
     Mh = M0.astype(np.float32)
-    p = g.default_params(d=128, k=k, lr=0.05, seed=7, B=B, large_parts=K, p_gpu=2, s_gpu=1, large_serial=1)
+    p = g.default_params(d=128, k=k, lr=0.05, seed=7, B=B, large_parts=K, p_gpu=2, s_gpu=1, large_serial=1,
+                         large_pools=pools)
     st = g.gosh_train_level_large(gr.rowptr, gr.col, Mh, 0, e, p)
     assert (st["positives"], st["updates"]) == (npos, nup)
     assert rel_fro(Mh.astype(np.float64), Mo) <= 1e-5
@@ -97,8 +104,9 @@ def test_budget_hand_count_on_device(n, K, B, k, e, npos, nup):
 _oracle_held = {}
 
 
+@pytest.mark.parametrize("pools", [0, 1])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_parts_reach_oracle_quality(dtype):
+def test_parts_reach_oracle_quality(dtype, pools):
     """The default (overlapping) schedule on the planted partition of the
     small workload, K = 4 parts, 3 bins, B = 5, e = 300 from the random init:
     held-out AUC within 0.005 of the sequential LargeGraphGPU oracle's (means
@@ -117,7 +125,8 @@ def test_parts_reach_oracle_quality(dtype):
             _oracle_held[seed] = oracle.link_auc(Mo, s.test_pos, s.test_neg)
         ref.append(_oracle_held[seed])
         Mh = torch.from_numpy(M0).to(dtype).contiguous()
-        p = g.default_params(d=32, k=3, lr=0.045, seed=seed, dtype=dtype, B=B, large_parts=K, p_gpu=3, s_gpu=2)
+        p = g.default_params(d=32, k=3, lr=0.045, seed=seed, dtype=dtype, B=B, large_parts=K, p_gpu=3, s_gpu=2,
+                             large_pools=pools)
         st = g.gosh_train_level_large(gr.rowptr, gr.col, Mh, 0, e, p)
         assert st["parts"] == K and st["rounds"] == e // B and st["kernels"] == (e // B) * K * (K + 1) // 2
         assert st["positives"] == e * gr.n

@@ -3,7 +3,8 @@ to the device for its kernel) as the library builds them on host threads,
 on the CPU: for every part pair (a, b) of K contiguous parts, block (a, b)
 lists for every u in V^a exactly its neighbours in V^b, ascending, as ids
 local to V^b (and the same for V^b against V^a), for graphs with isolated
-vertices, hubs, parts of one vertex and rows longer than one build chunk."""
+vertices, hubs, parts of one vertex and rows longer than one build chunk;
+and the host sample pools (large_pools = 1) against the oracle's draws."""
 import numpy as np
 import pytest
 
@@ -76,3 +77,31 @@ def test_invalid_pairs_rejected():
     for K, a, b in ((3, 1, 2), (3, 3, 0), (0, 0, 0), (21, 0, 0)):
         with pytest.raises(g.GoshError):
             g.gosh_large_block(gr.rowptr, gr.col, K, a, b)
+
+
+@pytest.mark.parametrize("K,B,seed", [(1, 1, 3), (3, 5, 4), (4, 2, 5)])
+def test_sample_pools_equal_oracle_draws(K, B, seed):
+    """Host sample pools (Sec. 5: positives drawn on the host, sent as pools)
+    equal, entry for entry, the oracle's draws of the same pairs and rounds;
+    every entry is a neighbour in the opposite part (local id), and -1
+    exactly where the source has no neighbour there."""
+    import oracle
+    gr = synth.rmat_graph(9, 8, seed)
+    n = gr.n
+    st = [n * i // K for i in range(K + 1)]
+    for a in range(K):
+        for b in range(a + 1):
+            for r in (0, 2):
+                got = g.gosh_large_pool(gr.rowptr, gr.col, K, a, b, r, B, 1, 77 + seed, 5)
+                want = oracle.large_pool(gr.rowptr, gr.col, K, a, b, r, B, 1, 77 + seed, 5)
+                np.testing.assert_array_equal(got, want)
+                srcs = list(range(st[a], st[a + 1])) + (list(range(st[b], st[b + 1])) if a != b else [])
+                for s, u in enumerate(srcs):
+                    own_a = s < st[a + 1] - st[a]
+                    o0, o1 = (st[b], st[b + 1]) if own_a else (st[a], st[a + 1])
+                    nb = gr.col[gr.rowptr[u]:gr.rowptr[u + 1]]
+                    inside = nb[(nb >= o0) & (nb < o1)]
+                    if len(inside) == 0:
+                        assert (got[s] == -1).all()
+                    else:
+                        assert np.isin(got[s] + o0, inside).all()
