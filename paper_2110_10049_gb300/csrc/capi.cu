@@ -5,6 +5,7 @@
 #include <atomic>
 #include <chrono>
 #include <mutex>
+#include <unordered_map>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -28,6 +29,66 @@ void clear_error() { g_error[0] = 0; }
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+std::mutex g_alloc_mu;
+gosh_alloc_fn g_alloc = nullptr;
+gosh_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+struct CallerBlock {
+    size_t bytes;
+    gosh_free_fn free;
+    void *ctx;
+};
+std::unordered_map<void *, CallerBlock> g_caller_blocks;  // blocks lent by a caller's allocator
+}  // namespace
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    gosh_alloc_fn fa;
+    gosh_free_fn ff;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        fa = g_alloc;
+        ff = g_free;
+        ctx = g_alloc_ctx;
+    }
+    if (!fa) {
+        keep_pool_memory();
+        return cudaMallocAsync(p, bytes, s);
+    }
+    void *q = fa(bytes, (void *)s, ctx);
+    if (!q) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    if (((uintptr_t)q & 255u) != 0) {  // not the promised alignment: give it back
+        ff(q, bytes, (void *)s, ctx);
+        *p = nullptr;
+        return cudaErrorInvalidValue;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        g_caller_blocks[q] = {bytes, ff, ctx};
+    }
+    *p = q;
+    return cudaSuccess;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (!p) return;
+    CallerBlock b{0, nullptr, nullptr};
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        auto it = g_caller_blocks.find(p);
+        if (it != g_caller_blocks.end()) {
+            b = it->second;
+            g_caller_blocks.erase(it);
+        }
+    }
+    if (b.free) b.free(p, b.bytes, (void *)s, b.ctx);
+    else cudaFreeAsync(p, s);
+}
 
 void keep_pool_memory() {
     static std::atomic<unsigned long long> done_mask{0};
@@ -81,7 +142,7 @@ int grid_for(int64_t work, int threads = 256) {
     return (int)(g < cap ? g : cap);
 }
 
-bool dim_ok(int d) { return d == 16 || d == 32 || d == 64 || d == 128; }
+bool dim_ok(int d) { return d == 8 || d == 16 || d == 32 || d == 64 || d == 128; }
 bool dtype_ok(gosh_dtype t) { return t == GOSH_F32 || t == GOSH_BF16 || t == GOSH_F16; }
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -376,7 +437,7 @@ gosh_status level_epochs(int e, double p, int D, int unit, const int64_t *n, con
 gosh_status check_params(const gosh_params *p) {
     GOSH_CHECK_ARG(p != nullptr, "params is NULL");
     GOSH_CHECK_ARG(dtype_ok(p->dtype), "unknown dtype %d", (int)p->dtype);
-    GOSH_CHECK_ARG(dim_ok(p->d), "d must be 16, 32, 64 or 128 (got %d)", p->d);
+    GOSH_CHECK_ARG(dim_ok(p->d), "d must be 8, 16, 32, 64 or 128 (got %d)", p->d);
     GOSH_CHECK_ARG(p->k >= 0 && p->k <= 15, "k must be in 0..15 (got %d)", p->k);
     GOSH_CHECK_ARG(p->lr > 0 && std::isfinite(p->lr), "lr must be positive");
     GOSH_CHECK_ARG(p->lr_floor >= 0 && p->lr_floor <= 1, "lr_floor must be in [0, 1]");
@@ -416,6 +477,16 @@ gosh_status check_host_csr(const int64_t *rowptr, const int32_t *col, int64_t n,
 using namespace gosh;
 
 extern "C" {
+
+gosh_status gosh_set_allocator(gosh_alloc_fn alloc, gosh_free_fn free, void *ctx) {
+    clear_error();
+    GOSH_CHECK_ARG((alloc == nullptr) == (free == nullptr), "give both allocator functions or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = free;
+    g_alloc_ctx = alloc ? ctx : nullptr;
+    return GOSH_OK;
+}
 
 gosh_status gosh_level_epochs(int epochs, double p, int D, int epoch_unit, const int64_t *n, const int64_t *nnz,
                               int *out) {

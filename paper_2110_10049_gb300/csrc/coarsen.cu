@@ -745,7 +745,7 @@ gosh_status coarse_graph_sorted(int64_t n, const int64_t *rowptr, const int32_t 
     int64_t m = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&m, pos.as<int64_t>() + nnz, sizeof(m), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
-    GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
+    GOSH_TRY_CUDA(dev_alloc((void **)co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
     GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
     launch_dep(write_coarse, grid_1d(nnz), 256, 0, s, ek.as<uint64_t>(), fl.as<uint8_t>(), pos.as<int64_t>(), nnz, sentinel, nc, *co_out, rp);
     *m_out = m;
@@ -840,7 +840,7 @@ gosh_status coarse_graph_bitmap(int64_t n, const int64_t *rowptr, const int32_t 
     int64_t m = 0;
     GOSH_TRY_CUDA(cudaMemcpyAsync(&m, rp + nc, sizeof(m), cudaMemcpyDeviceToHost, s));
     GOSH_TRY_CUDA(cudaStreamSynchronize(s));
-    GOSH_TRY_CUDA(cudaMallocAsync(co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
+    GOSH_TRY_CUDA(dev_alloc((void **)co_out, sizeof(int32_t) * (m > 0 ? m : 1), s));
     if (m > 0)
         launch_dep(compact_rows, grid_warps(nchunks), 256, 0, s, vb.as<int32_t>(), chunk_info.as<ChunkInfo>(),
                    nchunks, rp, *co_out);
@@ -1086,7 +1086,7 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     int64_t *rp = nullptr;
     int32_t *co = nullptr;
     // hierarchy buffers come from the stream-ordered pool (no device-wide sync)
-    GOSH_TRY_CUDA(cudaMallocAsync(&rp, sizeof(int64_t) * (nc + 1), s));
+    GOSH_TRY_CUDA(dev_alloc((void **)&rp, sizeof(int64_t) * (nc + 1), s));
     int64_t m = 0;
     if (nnz > 0 && width <= bitmap_limit()) {
         GOSH_TRY(coarse_graph_bitmap(n, rowptr, col, map, nc, nnz, width, u ? cbase.as<int32_t>() : nullptr, rp, &co,
@@ -1094,7 +1094,7 @@ gosh_status mec_level(int64_t n, const int64_t *rowptr, const int32_t *col, int6
     } else if (nnz > 0) {
         GOSH_TRY(coarse_graph_sorted(n, rowptr, col, map, nc, nnz, rp, &co, &m, s));
     } else {
-        GOSH_TRY_CUDA(cudaMallocAsync(&co, sizeof(int32_t), s));
+        GOSH_TRY_CUDA(dev_alloc((void **)&co, sizeof(int32_t), s));
         GOSH_TRY_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t) * (nc + 1), s));
     }
     *nc_out = nc;
@@ -1125,7 +1125,7 @@ gosh_status coarsen_impl(const gosh_csr *g0, int threshold, double shrink, int m
         const size_t i = h->n.size() - 1;
         const int64_t n = h->n[i];
         int32_t *map = nullptr;
-        if (cudaMallocAsync(&map, sizeof(int32_t) * (n > 0 ? n : 1), s) != cudaSuccess) {
+        if (dev_alloc((void **)&map, sizeof(int32_t) * (n > 0 ? n : 1), s) != cudaSuccess) {
             delete h;
             set_error("allocation of map_%zu failed", i);
             return GOSH_ERR_OOM;
@@ -1244,11 +1244,11 @@ gosh_status union_level(const std::vector<int> &slots, std::vector<gosh_hierarch
     // entries, shared by the hierarchies
     int32_t *maps = nullptr, *cols = nullptr;
     int64_t *rps = nullptr;
-    GOSH_TRY_CUDA(cudaMallocAsync(&maps, sizeof(int32_t) * N, s));
+    GOSH_TRY_CUDA(dev_alloc((void **)&maps, sizeof(int32_t) * N, s));
     std::shared_ptr<void> maps_own = device_owner(maps);
-    GOSH_TRY_CUDA(cudaMallocAsync(&rps, sizeof(int64_t) * (NC + A), s));
+    GOSH_TRY_CUDA(dev_alloc((void **)&rps, sizeof(int64_t) * (NC + A), s));
     std::shared_ptr<void> rps_own = device_owner(rps);
-    GOSH_TRY_CUDA(cudaMallocAsync(&cols, sizeof(int32_t) * (M > 0 ? M : 1), s));
+    GOSH_TRY_CUDA(dev_alloc((void **)&cols, sizeof(int32_t) * (M > 0 ? M : 1), s));
     std::shared_ptr<void> cols_own = device_owner(cols);
     std::vector<SlotOut> out(A);
     for (int j = 0; j < A; ++j)

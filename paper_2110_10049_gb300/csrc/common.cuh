@@ -52,6 +52,12 @@ void note_launch();
 // pages for their scratch; done once per device.
 void keep_pool_memory();
 
+// Device memory of the library: from the caller's allocator when one is set
+// (gosh_set_allocator), else cudaMallocAsync on the stream-ordered pool.
+// dev_free returns a block to whichever allocator provided it.
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
 // Stream-ordered device scratch, released on the same stream when it leaves scope.
 struct Scratch {
     void *ptr = nullptr;
@@ -64,17 +70,16 @@ struct Scratch {
         release();
         stream = s;
         if (bytes == 0) bytes = 16;
-        keep_pool_memory();
-        cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
+        cudaError_t e = dev_alloc(&ptr, bytes, s);
         if (e != cudaSuccess) {
             ptr = nullptr;
-            set_error("cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+            set_error("device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
             return GOSH_ERR_OOM;
         }
         return GOSH_OK;
     }
     void release() {
-        if (ptr) cudaFreeAsync(ptr, stream);
+        if (ptr) dev_free(ptr, stream);
         ptr = nullptr;
     }
     template <typename T> T *as() const { return static_cast<T *>(ptr); }

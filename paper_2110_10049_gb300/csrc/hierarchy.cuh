@@ -22,10 +22,10 @@ struct gosh_hierarchy {
     }
 };
 
-// A device buffer from cudaMallocAsync as a shared owner (freed with
-// cudaFreeAsync on the legacy stream when the last owner goes).
+// A device buffer from dev_alloc as a shared owner (returned to its
+// allocator on the legacy stream when the last owner goes).
 inline std::shared_ptr<void> device_owner(void *p) {
     return std::shared_ptr<void>(p, [](void *q) {
-        if (q) cudaFreeAsync(q, 0);
+        if (q) gosh::dev_free(q, 0);
     });
 }

@@ -124,7 +124,8 @@ extern "C" gosh_status gosh_train_level_noalloc(const gosh_csr *g, void *M, int 
     GOSH_CHECK_ARG(g->on_device && g->n >= 1 && g->rowptr && g->col, "needs a device CSR with n >= 1");
     GOSH_CHECK_ARG(M != nullptr && ((uintptr_t)M & 15u) == 0, "M must be a 16-byte aligned device pointer");
     GOSH_CHECK_ARG(epochs >= 0 && level >= 0, "bad epochs / level");
-    GOSH_CHECK_ARG(p->d == 16 || p->d == 32 || p->d == 64 || p->d == 128, "d must be 16, 32, 64 or 128 (got %d)", p->d);
+    GOSH_CHECK_ARG(p->d == 8 || p->d == 16 || p->d == 32 || p->d == 64 || p->d == 128,
+                   "d must be 8, 16, 32, 64 or 128 (got %d)", p->d);
     GOSH_CHECK_ARG(p->k >= 0 && p->k <= kMaxK, "k must be in 0..%d (got %d)", kMaxK, p->k);
     GOSH_CHECK_ARG(p->dtype == GOSH_F32 || p->dtype == GOSH_BF16 || p->dtype == GOSH_F16, "unknown dtype");
     if (p->mode != GOSH_HOGWILD) {

@@ -146,7 +146,7 @@ def train_gpu(g, gr, M0, k, level, epochs, lr, seed, mode, m=1, dtype=torch.floa
     return M.double().cpu().numpy(), loss.cpu().numpy()[:epochs], int(nup.item())
 
 
-@pytest.mark.parametrize("d", [16, 32, 64, 128])
+@pytest.mark.parametrize("d", [8, 16, 32, 64, 128])
 @pytest.mark.parametrize("k,m", [(3, 64), (3, 1), (5, 257), (1, 10 ** 6)])
 def test_deterministic_matches_oracle(g, c1, d, k, m):
     gr = c1.train
@@ -277,13 +277,15 @@ def test_hogwild_auc_matches_oracle(g, c1, s1):
     check_quality(gpu_quality(g, c1, s1, 32), oracle_quality(c1, s1, 32))
 
 
+@pytest.mark.parametrize("d,floor", [(16, 0.85), (8, 0.75)])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_small_d_embed_auc_matches_oracle(g, c1, s1, dtype):
-    """d = 16 (a warp updates 8 or 16 sources at once; the small levels fall
-    back from the staged kernel to registers): the same 0.005 bars as d = 32;
-    the oracle's R-MAT training-edge AUC is lower at this width (0.889 over
-    the three seeds), so its floor is 0.85."""
-    check_quality(gpu_quality(g, c1, s1, 16, dtype), oracle_quality(c1, s1, 16), floors=(0.85, 0.8, 0.9))
+def test_small_d_embed_auc_matches_oracle(g, c1, s1, dtype, d, floor):
+    """Small d (Sec. 3.1.1): at d = 16 a warp updates 8 (FP32) or 16 (16-bit)
+    sources at once, at d = 8 16 or 32; the small levels fall back from the
+    staged kernel to registers.  The same 0.005 bars as d = 32; the oracle's
+    R-MAT training-edge AUC is lower at these widths (0.889 at d = 16, 0.789
+    at d = 8, over the three seeds), so its floor is 0.85 / 0.75."""
+    check_quality(gpu_quality(g, c1, s1, d, dtype), oracle_quality(c1, s1, d), floors=(floor, 0.8, 0.9))
 
 
 def test_bf16_tables_reach_fp32_auc(g, c1, s1):

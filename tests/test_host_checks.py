@@ -106,3 +106,13 @@ def test_epoch_overlap_limits_checked_first(bad):
     cg = g.gosh_csr(10, 256, 512, 1)
     rc = L.gosh_train_level(C.byref(cg), C.c_void_p(1024), 0, 3, C.byref(p), None, None, None)
     assert rc == 1 and "overlap" in L.gosh_last_error().decode()
+
+
+def test_allocator_needs_both_functions():
+    """gosh_set_allocator takes both callbacks or neither (no device use)."""
+    L = g.lib()
+    noop_alloc = g.ALLOC_FN(lambda n, s, c: None)
+    with pytest.raises(g.GoshError) as e:
+        g._check("gosh_set_allocator", L.gosh_set_allocator(C.cast(noop_alloc, C.c_void_p), None, None))
+    assert e.value.status == 1
+    g.gosh_set_allocator(None, None)
