@@ -38,10 +38,15 @@ UNIT = "sample-updates/s"
 WL = dict(name="rmat20", scale=20, edge_factor=16, d=128, k=3, epochs=400, p=0.3, lr=0.01, epoch_unit=1)
 
 
+# The learned-projection workload (--workload rmat22): the same schedule on
+# R-MAT scale 22.
+WL22 = dict(WL, name="rmat22", scale=22, seed=20211022)
+
+
 def workload_name(tables, epochs=None, projection="copy", mode="hogwild", det_batch=4096):
     e = WL["epochs"] if epochs is None else epochs
-    name = ("R-MAT scale 20, ef 16, 80/20 split, d=128, k=3, e=%d epochs of |E| updates, p=0.3, lr=%g, "
-            "%s tables, %s projection" % (e, WL["lr"], tables, projection))
+    name = ("R-MAT scale %d, ef 16, 80/20 split, d=128, k=3, e=%d epochs of |E| updates, p=0.3, lr=%g, "
+            "%s tables, %s projection" % (WL["scale"], e, WL["lr"], tables, projection))
     if mode == "deterministic":
         name += ", deterministic mode (snapshot batches of %d sources)" % det_batch
     return name
@@ -137,7 +142,7 @@ def reduce_over_ranks(total_ms, updates, dist, device):
 
 def make_inputs(rank):
     import synth
-    seed = 20211021 + 1000 * rank
+    seed = WL.get("seed", 20211021) + 1000 * rank
     g = synth.rmat_graph(WL["scale"], WL["edge_factor"], seed)
     return synth.link_split(g, seed)
 
@@ -373,7 +378,8 @@ LARGE = dict(scale=22, edge_factor=16, d=32, k=3, epochs=20, B=5, p_gpu=3, s_gpu
 def run_large_workload(args):
     """LargeGraphGPU (Sec. 5): level 0 of R-MAT scale 22 trained out of core
     under a 512 MB device budget (the embedding and the CSR live in pinned
-    host memory; parts and edge blocks stream through device bins), d=32 BF16,
+    host memory; parts and edge blocks, or host-drawn sample pools, stream
+    through device bins), d=32 BF16,
     k=3, e=20, B=5, P_GPU=3, S_GPU=2.  One step = one gosh_train_level_large
     call (wall time, copies included); the resident step on the same graph is
     timed beside it."""
@@ -382,11 +388,20 @@ def run_large_workload(args):
     from paper_2110_10049_gb300 import build as gbuild
     gbuild.build()
     from paper_2110_10049_gb300 import gosh
-    sp = synth.workload("rmat22")
-    gr = sp.train
+    if args.large_scale == 26:
+        # the paper-scale configuration: R-MAT 26, edge factor 27 (1.8 G draws),
+        # the whole graph trained (no held-out split) under a 16 GB budget
+        t_gen = time.perf_counter()
+        gr = synth.rmat_graph_large(26, 27, 20211026)
+        gen_s = time.perf_counter() - t_gen
+        budget, ef, scale = 16 << 30, 27, 26
+    else:
+        gr = synth.workload("rmat22").train
+        gen_s, budget, ef, scale = None, LARGE["budget"], 16, 22
     params = gosh.default_params(d=LARGE["d"], k=LARGE["k"], lr=LARGE["lr"], dtype=gosh.GOSH_BF16, seed=5,
                                  B=LARGE["B"], p_gpu=LARGE["p_gpu"], s_gpu=LARGE["s_gpu"],
-                                 device_budget_bytes=LARGE["budget"], large_evict=args.large_evict)
+                                 device_budget_bytes=budget, large_evict=args.large_evict,
+                                 large_pools=args.large_pools)
     M = torch.zeros((gr.n, LARGE["d"]), dtype=torch.bfloat16).pin_memory()
     Md = torch.empty((gr.n, LARGE["d"]), dtype=torch.bfloat16, device="cuda")
     gosh.gosh_init_embedding(Md, level=0, seed=5)
@@ -419,11 +434,14 @@ def run_large_workload(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 math, bf16 tables", "data": "synthetic",
-        "config": {"workload": "LargeGraphGPU: R-MAT scale 22, ef 16, level 0 out of core, d=32 BF16, k=3, e=20, "
-                               "B=5, P_GPU=3, S_GPU=2, device budget 512 MB",
+        "config": {"workload": "LargeGraphGPU: R-MAT scale %d, ef %d, level 0 out of core, d=32 BF16, k=3, e=20, "
+                               "B=5, P_GPU=3, S_GPU=2, device budget %d MB" % (scale, ef, budget >> 20),
+                   "graph_generation_s": gen_s,
                    "vertices": gr.n, "csr_entries": gr.nnz, "parts": st["parts"], "rounds": st["rounds"],
                    "kernels": st["kernels"], "swaps": st["swaps"], "device_bytes": st["device_bytes"],
-                   "bin_choice": "spare previous kernel" if args.large_evict else "farthest next use"},
+                   "bin_choice": "spare previous kernel" if args.large_evict else "farthest next use",
+                   "positives": ("host sample pools (drawn on host threads, streamed per kernel)" if args.large_pools
+                                 else "edge blocks (built once on host threads, streamed; drawn on the device)")},
         "setup_ms_per_step": st["setup_ms"], "streaming_ms_per_step": st["total_ms"] - st["setup_ms"],
         "host_link": {"h2d_bytes_per_step": st["h2d_bytes"], "d2h_bytes_per_step": st["d2h_bytes"],
                       "GBps": (st["h2d_bytes"] + st["d2h_bytes"]) / (tot_ms / args.steps / 1000.0) / 1e9},
@@ -505,7 +523,8 @@ def run_walks_workload(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "batch512", "large", "walks"])
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "rmat22", "batch512", "large", "walks"],
+                    help="rmat20: the headline; rmat22: the learned-projection workload (same line, R-MAT 22)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -521,6 +540,11 @@ def main():
     ap.add_argument("--det-batch", type=int, default=4096, help="sources per snapshot batch (--mode deterministic)")
     ap.add_argument("--epoch-overlap", type=int, default=1,
                     help="epochs of a large level allowed to run at once (1 = serialised, as the paper)")
+    ap.add_argument("--large-scale", type=int, default=22, choices=[22, 26],
+                    help="--workload large: R-MAT 22 under 512 MB, or R-MAT 26 (ef 27) under 16 GB")
+    ap.add_argument("--large-pools", type=int, default=0, choices=[0, 1],
+                    help="LargeGraphGPU positives (--workload large): 0 edge blocks drawn on the device, 1 host "
+                         "sample pools")
     ap.add_argument("--large-evict", type=int, default=0, choices=[0, 1],
                     help="LargeGraphGPU bin choice (--workload large): 0 farthest next use, 1 spare the "
                          "previous kernel's parts")
@@ -542,6 +566,8 @@ def main():
     if args.workload == "large":
         run_large_workload(args)
         return
+    if args.workload == "rmat22":
+        WL.update(WL22)
 
     import torch
     dist = None
@@ -596,6 +622,12 @@ def main():
             stats.append(sd)
     launches = l0.gosh_kernel_launches() - launches0
     barrier()
+    # quality of the last timed embed: training-edge and held-out AUC
+    import synth
+    fpos, fneg = synth.fit_pairs(gr)
+    quality = {"fit_auc": gosh.gosh_link_auc(out, torch.from_numpy(fpos).cuda(), torch.from_numpy(fneg).cuda()),
+               "heldout_auc": gosh.gosh_link_auc(out, torch.from_numpy(sp.test_pos).cuda(),
+                                                 torch.from_numpy(sp.test_neg).cuda())}
     max_ms, all_updates = reduce_over_ranks(total_ms, updates, dist, "cuda")
     value = all_updates / (max_ms / 1000.0)
     ms_per_step = max_ms / args.steps
@@ -615,7 +647,7 @@ def main():
         try:
             with open(tr_path) as f:
                 tr = json.load(f)
-            traffic = tr.get("%s_level0_bytes_per_launch" % args.tables)
+            traffic = tr.get("%s_level0_bytes_per_launch" % args.tables) if WL["name"] == "rmat20" else None
         except Exception:
             traffic = None
 
@@ -631,6 +663,7 @@ def main():
                    "epoch_overlap": args.epoch_overlap,
                    "parallelism": "replicas x%d" % world},
         "time_to_embed_ms": ms_per_step,
+        "quality": quality,
         "breakdown_ms": {"coarsen": last["coarsen_ms"], "train": sum(last["train_ms"]),
                          "project": last["project_ms"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
