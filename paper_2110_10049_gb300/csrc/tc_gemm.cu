@@ -5,10 +5,10 @@
 // embedding table.
 //
 // One CTA (4 warps) computes a 128 x NT tile.  Operands arrive by TMA: each
-// stage holds 64 K-columns of the A and B tiles, loaded as eight 2-D boxes
-// of {8 columns, rows} placed side by side, which is the tensor cores'
-// canonical K-major layout without swizzle (8-row x 16-byte core matrices;
-// K-adjacent ones rows * 16 bytes apart, row groups 128 bytes apart).  Thread
+// stage holds 64 K-columns of the A and B tiles, one 2-D box of {64 columns,
+// rows} per operand written with the 128-byte swizzle (rows of 128 bytes,
+// 8-row atoms of 1024 bytes), the tensor cores' K-major swizzled layout: one
+// copy per operand and stage instead of eight 16-byte-wide boxes.  Thread
 // 0 of warp 0 runs the TMA producer over a ring of S stages (full/empty
 // mbarriers), thread 0 of warp 1 issues the MMAs (one elected thread) and
 // frees each stage with tcgen05.commit; after the last commit all four warps
@@ -76,7 +76,8 @@ struct GemmShape {
     static constexpr int kStageBytes = (128 + NT) * kGemmKStage * 2;
     static constexpr int kFit = 98304 / kStageBytes;
     static constexpr int kStages = kFit < 2 ? 2 : (kFit > 4 ? 4 : kFit);
-    static constexpr size_t kSmem = (size_t)kStages * kStageBytes;
+    // + 1024: the stages start at the first 1024-byte boundary (swizzle atoms)
+    static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 1024;
 };
 
 template <int NT, int EPI, typename T>
@@ -89,7 +90,9 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
     constexpr int S = GemmShape<NT>::kStages;
     constexpr uint32_t kCols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
     constexpr int A_BYTES = 128 * kGemmKStage * 2, B_BYTES = NT * kGemmKStage * 2;
-    extern __shared__ __align__(128) uint8_t smem[];
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // the 128-byte swizzle needs 1024-byte aligned atoms: round the base up
+    uint8_t *smem = smem_raw + ((1024u - (tc::smem_addr(smem_raw) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[S], empty[S], done;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
@@ -125,14 +128,13 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
                 break;
             }
             const int k0 = kb + k * kGemmKStage;
-            const int nc = min(kGemmKStage, ke - k0) / 8;  // 8-column boxes inside this split
-            mbar_arrive_expect_tx(&full[st], (uint32_t)nc * (128 + NT) * 16);
+            // whole boxes arrive (columns past K read as zero); the MMA
+            // steps below stop at this split's end
+            mbar_arrive_expect_tx(&full[st], (uint32_t)(A_BYTES + B_BYTES));
             const uint32_t sa = tc::smem_addr(smem + (size_t)st * (A_BYTES + B_BYTES));
             const uint32_t sb = sa + A_BYTES;
-            for (int c = 0; c < nc; ++c) {
-                tma_load_2d(sa + c * 128 * 16, &tmA, k0 + 8 * c, m0, tc::smem_addr(&full[st]));
-                tma_load_2d(sb + c * NT * 16, &tmB, k0 + 8 * c, n0, tc::smem_addr(&full[st]));
-            }
+            tma_load_2d(sa, &tmA, k0, m0, tc::smem_addr(&full[st]));
+            tma_load_2d(sb, &tmB, k0, n0, tc::smem_addr(&full[st]));
             ++issued[st];
         }
     } else if (warp == 1 && lane == 0) {
@@ -152,8 +154,8 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
             const uint32_t sa = tc::smem_addr(smem + (size_t)st * (A_BYTES + B_BYTES));
             const uint32_t sb = sa + A_BYTES;
             for (int j = 0; j < steps; ++j) {
-                const uint64_t ad = tc::make_desc(sa + 2 * j * 128 * 16, 128 * 16, 128);
-                const uint64_t bd = tc::make_desc(sb + 2 * j * NT * 16, NT * 16, 128);
+                const uint64_t ad = tc::make_desc_sw128(sa + 32 * j);
+                const uint64_t bd = tc::make_desc_sw128(sb + 32 * j);
                 tc::mma_bf16(tmem, ad, bd, idesc, (k > 0 || j > 0) ? 1u : 0u);
             }
             tc::mma_commit(&empty[st]);
@@ -267,16 +269,17 @@ gosh_status encoder(EncodeTiled *out) {
 }
 
 // Row-major BF16 matrix (rows x cols, row stride ld elements) read in boxes of
-// {8 columns, box_rows rows}; out-of-range rows and columns read as zero.
+// {64 columns, box_rows rows} with the 128-byte swizzle; out-of-range rows
+// and columns read as zero.
 gosh_status make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
     EncodeTiled enc = nullptr;
     GOSH_TRY(encoder(&enc));
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)kGemmKStage, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld operand, stride %lld", (int)r, (long long)rows,

@@ -28,6 +28,22 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
+// Shared-memory matrix descriptor for a K-major operand stored with the
+// 128-byte swizzle: rows of 128 bytes (64 BF16 of K), 8-row atoms of 1024
+// bytes stacked along M/N (SBO = 1024), the 16-byte chunks of row r permuted
+// by r mod 8 (as TMA writes them with CU_TENSOR_MAP_SWIZZLE_128B).  The atom
+// must be 1024-byte aligned; the K offset inside it is added to the start
+// address (32 bytes per 16-element MMA step).
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3fffu);
+    d |= (uint64_t)1 << 16;                      // LBO (unused for a K-major swizzled operand)
+    d |= (uint64_t)((1024u >> 4) & 0x3fffu) << 32;  // SBO: 8-row atoms 1024 bytes apart
+    d |= (uint64_t)1 << 46;                      // descriptor version for sm_100-class tensor cores
+    d |= (uint64_t)2 << 61;                      // layout: 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor for kind::f16: D = FP32, A = B = BF16, both K-major.
 __host__ __device__ __forceinline__ uint32_t make_idesc_bf16(int M, int N) {
     uint32_t d = 0;
