@@ -28,6 +28,10 @@ gosh_status tc_gemm_bias_relu(const __nv_bfloat16 *A, int64_t lda, const __nv_bf
 gosh_status tc_gemm_residual(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B, int64_t ldb,
                              const float *bias, const int32_t *map, const void *Mc, void *Mf, int64_t v0, int d,
                              gosh_dtype dt, int M, int K, int *err, cudaStream_t s);
+bool tc_mlp_fused_ok(int d, int hid, int kp);
+gosh_status tc_mlp_project(const __nv_bfloat16 *X, const __nv_bfloat16 *W1b, const __nv_bfloat16 *W2b,
+                           const float *b1, const float *b2, const int32_t *map, const void *Mc, void *Mf, int64_t v0,
+                           int d, int hid, int kp, gosh_dtype dt, int M, int *err, cudaStream_t s);
 }
 
 struct gosh_mlp {
@@ -675,15 +679,23 @@ gosh_status mlp_project(gosh_mlp *m, const void *Mc, const int32_t *map, const g
         GOSH_TRY_CUDA(cudaMalloc(&m->Xc, sizeof(__nv_bfloat16) * nkeep * kp));
         m->Xc_cap = nkeep;
     }
+    // both layers in one persistent kernel where the accumulators fit one
+    // SM's tensor memory; else two GEMMs with the hidden layer in memory
+    const bool fused = tc_mlp_fused_ok(d, hid, kp);
     Scratch X, H;
     GOSH_TRY(X.alloc(sizeof(__nv_bfloat16) * chunk * kp, s));
-    GOSH_TRY(H.alloc(sizeof(__nv_bfloat16) * chunk * hid, s));
+    if (!fused) GOSH_TRY(H.alloc(sizeof(__nv_bfloat16) * chunk * hid, s));
     for (int64_t v0 = 0; v0 < n; v0 += chunk) {
         const int rows = (int)std::min<int64_t>(chunk, n - v0);
         GOSH_TRY(features(g, map, Mc, d, dt, kp, v0, rows, X.as<__nv_bfloat16>(), s));
         if (keep_rows_of != 0)
             launch_dep(keep_rows, grid_for(ceil_div(rows, stride) * (kp / 8)), 256, 0, s, X.as<__nv_bfloat16>(), kp, v0, rows,
                                                                                   stride, m->Xc);
+        if (fused) {
+            GOSH_TRY(tc_mlp_project(X.as<__nv_bfloat16>(), m->W1b, m->W2b, m->b1, m->b2, map, Mc, Mf, v0, d, hid, kp, dt,
+                                    rows, m->err, s));
+            continue;
+        }
         GOSH_TRY(gemm_bias_relu(X.as<__nv_bfloat16>(), kp, m->W1b, kp, m->b1, H.as<__nv_bfloat16>(), hid, rows, hid, kp,
                                 m->err, s));
         // Mf[v] = Mc[map v] + H W2^T + b2, written by the second GEMM's epilogue

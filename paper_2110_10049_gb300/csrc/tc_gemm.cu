@@ -18,6 +18,8 @@
 // output unwritten.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -246,6 +248,287 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
     if (warp == 0) tc::tmem_dealloc(tmem, kCols);
 }
 
+// ---------------------------------------------------------------------------
+// The learned projection of one chunk of fine vertices in one persistent
+// kernel (both layers of the MLP, the hidden layer never leaves the SM):
+//
+//   acc1 = X W1^T                 tensor memory columns [0, HID)
+//   H    = relu(acc1 + b1)        BF16, written to shared memory
+//   acc2 = H W2^T                 tensor memory columns [HID, HID + D)
+//   Mf[v0 + m] = Mc[map[v0 + m]] + acc2 + b2
+//
+// One CTA per SM walks the chunk's 128-row tiles (tile = blockIdx.x + i *
+// gridDim.x).  Roles: warps 0-7 run the epilogues (warps w and w + 4 read
+// the same 32 tensor-memory lanes, each half of the columns), warp 8 loads
+// the X tiles (two tile buffers, the next tile's rows arrive while this
+// one is computed), warp 9 streams the weights through a two-slot ring in
+// 64-column blocks (W1 blocks for layer 1, W2 blocks for layer 2, in the
+// order the MMAs consume them) and warp 10 issues the MMAs.  H of tile t is
+// written over X of tile t (layer 1 has consumed it), in the same 128-byte
+// swizzled K-major layout the TMA writes, so layer 2 reads it in place.
+// Every operand and tile buffer starts on a 1024-byte boundary.
+//
+// Barriers: x_full / x_empty per tile buffer, w_full / w_empty per ring
+// slot, acc1_full (layer 1 done), acc1_empty (acc1 read out), h_full (H
+// written and fenced for the tensor cores), acc2_full (layer 2 done: H and
+// its buffer free), acc2_empty (acc2 read out).  Every wait is bounded; on
+// time-out the CTA raises *err, every role stops, the producers wait
+// (bounded) for their copies in flight and the tensor memory is freed.
+constexpr int kMlpEpiWarps = 8;
+constexpr int kMlpThreads = (kMlpEpiWarps + 3) * 32;
+constexpr int kMlpTileBytes = 128 * kGemmKStage * 2;  // one 64-column block of a 128-row tile
+
+struct MlpDims {
+    int hid, kp, nkb1, nkb2, xbytes, slot;
+    __host__ __device__ MlpDims(int D, int hid_, int kp_)
+        : hid(hid_), kp(kp_), nkb1((kp_ + kGemmKStage - 1) / kGemmKStage), nkb2(hid_ / kGemmKStage),
+          xbytes((nkb1 > nkb2 ? nkb1 : nkb2) * kMlpTileBytes), slot((hid_ > D ? hid_ : D) * kGemmKStage * 2) {}
+    __host__ __device__ size_t smem() const { return (size_t)2 * xbytes + (size_t)2 * slot + 1024; }
+};
+
+// The MMA issue order: layer 1 of tile i then layer 2 of tile i.  The
+// weight producer loads the ring in the same order.
+template <typename T, int D>
+__global__ void __launch_bounds__(kMlpThreads, 1)
+    mlp_project_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
+                       const __grid_constant__ CUtensorMap tmW2, const float *__restrict__ b1,
+                       const float *__restrict__ b2, const int32_t *__restrict__ map, const T *__restrict__ Mc,
+                       T *__restrict__ Mf, int64_t v0, int M, int hid, int kp, uint32_t tmem_cols,
+                       int *__restrict__ err) {
+    GOSH_DEP_WAIT();
+    static_assert(D == 32 || D == 64 || D == 128, "D in {32, 64, 128}");
+    const MlpDims dm(D, hid, kp);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((1024u - (tc::smem_addr(smem_raw) & 1023u)) & 1023u);
+    const uint32_t xbuf0 = tc::smem_addr(smem);
+    const uint32_t ring0 = xbuf0 + 2u * (uint32_t)dm.xbytes;
+    __shared__ __align__(8) uint64_t x_full[2], x_empty[2], w_full[2], w_empty[2];
+    __shared__ __align__(8) uint64_t acc1_full, acc1_empty, h_full, acc2_full, acc2_empty, fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = (M + 127) / 128;
+    const int T_n = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (warp == kMlpEpiWarps) tc::tmem_alloc(&tmem_base, tmem_cols);
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&x_full[i], 1);
+            tc::mbar_init(&x_empty[i], 1);
+            tc::mbar_init(&w_full[i], 1);
+            tc::mbar_init(&w_empty[i], 1);
+        }
+        tc::mbar_init(&acc1_full, 1);
+        tc::mbar_init(&acc1_empty, kMlpEpiWarps);
+        tc::mbar_init(&h_full, kMlpEpiWarps);
+        tc::mbar_init(&acc2_full, 1);
+        tc::mbar_init(&acc2_empty, kMlpEpiWarps);
+        tc::mbar_init(&fin, 1);
+        s_fail = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    volatile int *vfail = &s_fail;
+
+    if (warp == kMlpEpiWarps) {
+        // ---- X tiles: buffer t & 1, reused once layer 2 of tile t - 2 is done ----
+        if (lane == 0) {
+            int issued[2] = {0, 0};
+            for (int t = 0; t < T_n; ++t) {
+                const int b = t & 1;
+                if (*vfail) break;
+                if (t >= 2 && !tc::mbar_wait(&x_empty[b], ((t >> 1) - 1) & 1, kGemmWaitPolls)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * 128;
+                mbar_arrive_expect_tx(&x_full[b], (uint32_t)(dm.nkb1 * kMlpTileBytes));
+                for (int kb = 0; kb < dm.nkb1; ++kb)
+                    tma_load_2d(xbuf0 + (uint32_t)(b * dm.xbytes + kb * kMlpTileBytes), &tmX, kb * kGemmKStage, m0,
+                                tc::smem_addr(&x_full[b]));
+                ++issued[b];
+            }
+            // every copy has landed before shared memory goes away (at once
+            // when the MMAs consumed them)
+            for (int b = 0; b < 2; ++b)
+                if (issued[b] > 0) tc::mbar_wait(&x_full[b], (uint32_t)(issued[b] - 1) & 1u, kGemmWaitPolls);
+        }
+    } else if (warp == kMlpEpiWarps + 1) {
+        // ---- weight ring: per tile nkb1 W1 blocks, then nkb2 W2 blocks ----
+        if (lane == 0) {
+            int issued[2] = {0, 0};
+            int it = 0;
+            bool ok = true;
+            for (int t = 0; t < T_n && ok; ++t) {
+                for (int layer = 0; layer < 2 && ok; ++layer) {
+                    const int nb = layer == 0 ? dm.nkb1 : dm.nkb2;
+                    const uint32_t bytes = (uint32_t)((layer == 0 ? hid : D) * kGemmKStage * 2);
+                    for (int kb = 0; kb < nb; ++kb, ++it) {
+                        const int sl = it & 1;
+                        if (*vfail || (it >= 2 && !tc::mbar_wait(&w_empty[sl], ((it >> 1) - 1) & 1, kGemmWaitPolls))) {
+                            atomicExch(&s_fail, 1);
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&w_full[sl], bytes);
+                        tma_load_2d(ring0 + (uint32_t)(sl * dm.slot), layer == 0 ? &tmW1 : &tmW2, kb * kGemmKStage, 0,
+                                    tc::smem_addr(&w_full[sl]));
+                        ++issued[sl];
+                    }
+                }
+            }
+            for (int sl = 0; sl < 2; ++sl)
+                if (issued[sl] > 0) tc::mbar_wait(&w_full[sl], (uint32_t)(issued[sl] - 1) & 1u, kGemmWaitPolls);
+        }
+    } else if (warp == kMlpEpiWarps + 2) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            const uint32_t idesc1 = tc::make_idesc_bf16(128, hid);
+            const uint32_t idesc2 = tc::make_idesc_bf16(128, D);
+            int it = 0;
+            bool ok = true;
+            for (int t = 0; t < T_n && ok; ++t) {
+                const int b = t & 1;
+                const uint32_t xb = xbuf0 + (uint32_t)(b * dm.xbytes);
+                // layer 1: X(t) and acc1 free (read out for tile t - 1)
+                ok = tc::mbar_wait(&x_full[b], (t >> 1) & 1, kGemmWaitPolls) &&
+                     (t == 0 || tc::mbar_wait(&acc1_empty, (t - 1) & 1, kGemmWaitPolls));
+                for (int kb = 0; kb < dm.nkb1 && ok; ++kb, ++it) {
+                    const int sl = it & 1;
+                    if (*vfail || !tc::mbar_wait(&w_full[sl], (it >> 1) & 1, kGemmWaitPolls)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const int k0 = kb * kGemmKStage;
+                    const int steps = min(kGemmKStage, kp - k0) / 16;
+                    const uint32_t wb = ring0 + (uint32_t)(sl * dm.slot);
+                    for (int j = 0; j < steps; ++j)
+                        tc::mma_bf16(tmem, tc::make_desc_sw128(xb + (uint32_t)(kb * kMlpTileBytes + 32 * j)),
+                                     tc::make_desc_sw128(wb + (uint32_t)(32 * j)), idesc1, (kb > 0 || j > 0) ? 1u : 0u);
+                    tc::mma_commit(&w_empty[sl]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&acc1_full);
+                // layer 2: H(t) written, acc2 free (read out for tile t - 1)
+                ok = tc::mbar_wait(&h_full, t & 1, kGemmWaitPolls) &&
+                     (t == 0 || tc::mbar_wait(&acc2_empty, (t - 1) & 1, kGemmWaitPolls));
+                for (int kb = 0; kb < dm.nkb2 && ok; ++kb, ++it) {
+                    const int sl = it & 1;
+                    if (*vfail || !tc::mbar_wait(&w_full[sl], (it >> 1) & 1, kGemmWaitPolls)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t wb = ring0 + (uint32_t)(sl * dm.slot);
+                    for (int j = 0; j < kGemmKStage / 16; ++j)
+                        tc::mma_bf16(tmem + (uint32_t)hid, tc::make_desc_sw128(xb + (uint32_t)(kb * kMlpTileBytes + 32 * j)),
+                                     tc::make_desc_sw128(wb + (uint32_t)(32 * j)), idesc2, (kb > 0 || j > 0) ? 1u : 0u);
+                    tc::mma_commit(&w_empty[sl]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&acc2_full);
+                tc::mma_commit(&x_empty[b]);
+            }
+            if (!ok) atomicExch(&s_fail, 1);
+            tc::mma_commit(&fin);  // every MMA issued above has completed when this arrives
+            tc::mbar_wait(&fin, 0, kGemmWaitPolls);
+        }
+    } else {
+        // ---- epilogues: warp w reads lanes 32 (w % 4) .. + 31, column half w / 4 ----
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        const int r = quarter * 32 + lane;  // row of the tile
+        const int hc0 = half * (hid / 2), hc1 = hc0 + hid / 2;
+        constexpr int DH = D / 2;                       // acc2 columns of this warp
+        constexpr int PV = 16 / (int)sizeof(T);         // table values per 16-byte vector
+        constexpr int NV = DH / PV;                     // 16-byte vectors of this warp's part of a row
+        const int dc0 = half * DH;
+        for (int t = 0; t < T_n; ++t) {
+            const int b = t & 1;
+            const uint32_t xb = xbuf0 + (uint32_t)(b * dm.xbytes);
+            const int row = ((int)blockIdx.x + t * (int)gridDim.x) * 128 + r;
+            // the coarse rows of the residual do not depend on the MMAs: fetch them first
+            uint4 own[NV];
+            const int64_t vv = v0 + row;
+            if (row < M) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(Mc + (int64_t)__ldg(map + vv) * D + dc0);
+#pragma unroll
+                for (int x = 0; x < NV; ++x) own[x] = __ldg(src + x);
+            }
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc1_full, t & 1, kGemmWaitPolls) && !*vfail)) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            tc::fence_after_sync();
+            // H = relu(acc1 + b1) -> BF16, 128-byte swizzle: 16-byte chunk c of
+            // row r of a 64-column block sits at chunk c ^ (r mod 8)
+            for (int c0 = hc0; c0 < hc1; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tmem + lane_addr + (uint32_t)c0, v);
+                uint32_t w[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float2 bb = __ldg(reinterpret_cast<const float2 *>(b1 + c0) + j);
+                    const __nv_bfloat162 h =
+                        __floats2bfloat162_rn(fmaxf(v[2 * j] + bb.x, 0.0f), fmaxf(v[2 * j + 1] + bb.y, 0.0f));
+                    w[j] = *reinterpret_cast<const uint32_t *>(&h);
+                }
+                const uint32_t base = xb + (uint32_t)((c0 / kGemmKStage) * kMlpTileBytes + r * 128);
+                const int cc = (c0 % kGemmKStage) / 8;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t a = base + (uint32_t)((((cc + q) ^ (r & 7)) & 7) << 4);
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[4 * q]), "r"(w[4 * q + 1]),
+                                 "r"(w[4 * q + 2]), "r"(w[4 * q + 3])
+                                 : "memory");
+                }
+            }
+            tc::fence_before_sync();
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(&acc1_empty);
+                tc::mbar_arrive(&h_full);
+            }
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc2_full, t & 1, kGemmWaitPolls) && !*vfail)) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            tc::fence_after_sync();
+            float y[DH];
+#pragma unroll
+            for (int c = 0; c < DH; c += 16) tc::tmem_ld16(tmem + lane_addr + (uint32_t)(hid + dc0 + c), y + c);
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc2_empty);
+            if (row < M) {
+                uint4 *dst = reinterpret_cast<uint4 *>(Mf + vv * D + dc0);
+#pragma unroll
+                for (int x = 0; x < NV; ++x) {
+                    union {
+                        uint4 u;
+                        T t[PV];
+                    } pk;
+                    pk.u = own[x];
+#pragma unroll
+                    for (int q = 0; q < PV; ++q)
+                        pk.t[q] = from_f<T>(to_f<T>(pk.t[q]) + y[x * PV + q] + __ldg(b2 + dc0 + x * PV + q));
+                    dst[x] = pk.u;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (s_fail && tid == 0) atomicExch(err, 1);
+    if (warp == kMlpEpiWarps) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
 namespace {
 
 typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -329,7 +612,68 @@ gosh_status check_operands(const void *A, int64_t lda, const void *B, int64_t ld
     return GOSH_OK;
 }
 
+template <typename T, int D>
+gosh_status launch_mlp(const CUtensorMap &mx, const CUtensorMap &m1, const CUtensorMap &m2, const float *b1,
+                       const float *b2, const int32_t *map, const void *Mc, void *Mf, int64_t v0, int M, int hid, int kp,
+                       int *err, cudaStream_t s) {
+    const MlpDims dm(D, hid, kp);
+    const size_t smem = dm.smem();
+    static size_t attr = 0;
+    if (attr < smem) {
+        GOSH_TRY_CUDA(
+            cudaFuncSetAttribute(mlp_project_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = smem;
+    }
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(hid + D)) cols <<= 1;
+    const int ntiles = (int)ceil_div(M, 128);
+    const int grid = ntiles < num_sms() ? ntiles : num_sms();
+    launch_dep(mlp_project_kernel<T, D>, grid, kMlpThreads, smem, s, mx, m1, m2, b1, b2, map, static_cast<const T *>(Mc),
+               static_cast<T *>(Mf), v0, M, hid, kp, cols, err);
+    GOSH_TRY_CUDA(cudaGetLastError());
+    return GOSH_OK;
+}
+
 }  // namespace
+
+// Whether tc_mlp_project takes these shapes: d in {32, 64, 128}, hidden a
+// multiple of 64 up to 256 (both accumulators in one SM's tensor memory).
+bool tc_mlp_fused_ok(int d, int hid, int kp) {
+    if (!(d == 32 || d == 64 || d == 128) || hid % 64 != 0 || hid < 64 || hid > 256 || kp % 16 != 0 || kp <= 0)
+        return false;
+    return MlpDims(d, hid, kp).smem() <= 232448 - 1024;
+}
+
+// Mf[v0 + m] = Mc[map[v0 + m]] + relu(X[m] W1^T + b1) W2^T + b2 for m < M:
+// X (M x kp, BF16, row stride kp), W1b (hid x kp), W2b (d x hid), both BF16
+// row-major; the hidden layer is rounded to BF16 as the two-GEMM path does.
+gosh_status tc_mlp_project(const __nv_bfloat16 *X, const __nv_bfloat16 *W1b, const __nv_bfloat16 *W2b,
+                           const float *b1, const float *b2, const int32_t *map, const void *Mc, void *Mf, int64_t v0,
+                           int d, int hid, int kp, gosh_dtype dt, int M, int *err, cudaStream_t s) {
+    GOSH_CHECK_ARG(M > 0 && tc_mlp_fused_ok(d, hid, kp), "fused projection: unsupported shape");
+    GOSH_CHECK_ARG(((uintptr_t)X & 15) == 0 && ((uintptr_t)W1b & 15) == 0 && ((uintptr_t)W2b & 15) == 0 &&
+                       ((uintptr_t)Mc & 15) == 0 && ((uintptr_t)Mf & 15) == 0 && ((uintptr_t)b1 & 7) == 0,
+                   "fused projection: operands must be 16-byte aligned");
+    CUtensorMap mx, m1, m2;
+    GOSH_TRY(make_map(&mx, X, M, kp, kp, 128));
+    GOSH_TRY(make_map(&m1, W1b, hid, kp, kp, hid));
+    GOSH_TRY(make_map(&m2, W2b, d, hid, hid, d));
+    auto go = [&](auto *tp) -> gosh_status {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        switch (d) {
+        case 32: return launch_mlp<T, 32>(mx, m1, m2, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
+        case 64: return launch_mlp<T, 64>(mx, m1, m2, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
+        default: return launch_mlp<T, 128>(mx, m1, m2, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
+        }
+    };
+    switch (dt) {
+    case GOSH_F32: return go((float *)nullptr);
+    case GOSH_BF16: return go((__nv_bfloat16 *)nullptr);
+    case GOSH_F16: return go((__half *)nullptr);
+    }
+    set_error("unknown dtype");
+    return GOSH_ERR_INVALID_ARG;
+}
 
 // C (M x N, FP32, row stride ldc) = A (M x K) . B (N x K)^T, or += when splits > 1
 // (split-K over `splits` CTAs per tile, C must then hold the addend).  N <= 256.

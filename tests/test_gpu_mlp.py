@@ -175,3 +175,49 @@ def test_projection_matches_oracle_forward(d, hidden):
     Y, _ = omlp.forward(W1, b1.astype(np.float64), W2, b2.astype(np.float64), X)
     got = Mf.double().cpu().numpy() - Mc[mp]
     assert rel(got, Y) < TOL, rel(got, Y)
+
+
+def _bf16_forward_ref(W1, b1, W2, b2, X):
+    """The forward pass with the GPU's roundings: BF16 features and weights
+    (given), FP64 sums, the hidden layer rounded to BF16."""
+    H = bf16_round_np(np.maximum(X @ W1.T + b1, 0.0))
+    return H @ W2.T + b2
+
+
+@pytest.mark.parametrize("d,hidden,dt,scale", [(128, 256, "f32", 16), (128, 256, "bf16", 15), (64, 256, "f16", 15),
+                                                (32, 64, "bf16", 15), (64, 128, "f32", 15)])
+def test_projection_tiles_tables_ragged(d, hidden, dt, scale):
+    """gosh_project_learned over more 128-row tiles than SMs (so CTAs of the
+    persistent kernel reuse both tile buffers), a ragged last tile, and every
+    table type: Mf - copy against the oracle's forward pass with the GPU's
+    BF16 roundings (features, weights, hidden layer), norm-wise and row by
+    row (a row from the wrong tile or a mis-swizzled hidden block is off by
+    O(1))."""
+    g = gosh()
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dt]
+    gr = synth.rmat_graph(scale, 8, 9)
+    assert gr.n > 152 * 128 and gr.n % 128 != 0
+    rng = np.random.default_rng(d + hidden + scale)
+    nc = 3000
+    din = 2 * d + 1
+    mp = rng.integers(0, nc, gr.n).astype(np.int32)
+    Mc_t = torch.from_numpy((rng.normal(size=(nc, d)) * 0.5).astype(np.float32)).to(tdt)
+    Mc = Mc_t.double().numpy()
+    W1 = bf16_round_np(rng.normal(size=(hidden, din)) * 0.1)
+    b1 = rng.normal(size=hidden).astype(np.float32) * 0.1
+    W2 = bf16_round_np(rng.normal(size=(d, hidden)) * 0.1)
+    b2 = rng.normal(size=d).astype(np.float32) * 0.1
+    m = g.Mlp(d, hidden, seed=1)
+    m.set_weights(W1, b1, W2, b2)
+    csr = g.to_device_csr(gr.rowptr, gr.col)
+    Mf = torch.empty((gr.n, d), device="cuda", dtype=tdt)
+    m.project(Mc_t.cuda(), torch.from_numpy(mp).cuda(), csr, Mf)
+    X = bf16_round_np(omlp.features(gr.rowptr, gr.col, mp, Mc)).astype(np.float64)
+    Y = _bf16_forward_ref(W1, b1.astype(np.float64), W2, b2.astype(np.float64), X)
+    got = Mf.double().cpu().numpy() - Mc[mp]
+    # FP32 tables: FP32 accumulation and hidden-layer rounding flips only;
+    # 16-bit tables add the rounding of Mf itself (2^-9 / 2^-12 of |Mf|)
+    tol = {"f32": 4e-3, "f16": 6e-3, "bf16": 2.5e-2}[dt]
+    assert rel(got, Y) < tol, rel(got, Y)
+    row_err = np.linalg.norm(got - Y, axis=1) / np.maximum(np.linalg.norm(Y, axis=1), 1e-3)
+    assert row_err.max() < 8 * tol, (int(row_err.argmax()), float(row_err.max()))
