@@ -53,9 +53,30 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// The box at {x, y} into L2 only (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(mbar)), "r"(bytes)
                  : "memory");
+}
+
+// relu(a + b) for two pairs, rounded to BF16 and packed (a0 + b0 in the low
+// half): one paired FP32 add and one converting ReLU.
+__device__ __forceinline__ uint32_t bias_relu_bf16x2(float a0, float a1, float b0, float b1) {
+    uint64_t x, y, z;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b0), "f"(b1));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+    float s0, s1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(s0), "=f"(s1) : "l"(z));
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(s1), "f"(s0));
+    return r;
 }
 
 template <typename T>
@@ -250,213 +271,256 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
 
 // ---------------------------------------------------------------------------
 // The learned projection of one chunk of fine vertices in one persistent
-// kernel (both layers of the MLP, the hidden layer never leaves the SM):
+// kernel (both layers of the MLP; the hidden layer never leaves the SM):
 //
-//   acc1 = X W1^T                 tensor memory columns [0, HID)
-//   H    = relu(acc1 + b1)        BF16, written to shared memory
-//   acc2 = H W2^T                 tensor memory columns [HID, HID + D)
-//   Mf[v0 + m] = Mc[map[v0 + m]] + acc2 + b2
+//   acc1   = X W1^T                    tensor memory, lanes = tile rows, columns [0, hid)
+//   H      = relu(acc1 + b1)           BF16, shared memory
+//   acc2^T = W2 H^T                    tensor memory, lanes = output dimensions, columns = tile rows
+//   Mf[v0 + m][o] = Mc[map[v0 + m]][o] + acc2^T[o][m] + b2[o]
+//
+// Layer 2 runs transposed so that W2 stays resident in tensor memory as the
+// A operand (lanes = its rows, zero rows up to 128, the K = hid values of a
+// row packed two per 32-bit column) and H, the B operand, is read in place
+// from shared memory; the weights streamed per tile are then W1's alone.
+// Its epilogue gives lane o of a warp output dimension o of a row, so the
+// coarse-row loads and the fine-row stores of a warp are contiguous.
 //
 // One CTA per SM walks the chunk's 128-row tiles (tile = blockIdx.x + i *
-// gridDim.x).  Roles: warps 0-7 run the epilogues (warps w and w + 4 read
-// the same 32 tensor-memory lanes, each half of the columns), warp 8 loads
-// the X tiles (two tile buffers, the next tile's rows arrive while this
-// one is computed), warp 9 streams the weights through a two-slot ring in
-// 64-column blocks (W1 blocks for layer 1, W2 blocks for layer 2, in the
-// order the MMAs consume them) and warp 10 issues the MMAs.  H of tile t is
-// written over X of tile t (layer 1 has consumed it), in the same 128-byte
-// swizzled K-major layout the TMA writes, so layer 2 reads it in place.
-// Every operand and tile buffer starts on a 1024-byte boundary.
+// gridDim.x).  Roles: warps 0-7 run the epilogues (warps 0-3 first write
+// W2 into tensor memory, while layer 1 of the first tile runs), warp 8
+// loads the ring of S stages (each: one 64-column block of the X tile and
+// the matching block of W1, both as one 128-byte-swizzled TMA box; the
+// 16-column tail of K as two 8-column boxes per operand without swizzle)
+// and prefetches the next tile's X rows into L2, warp 9 issues the MMAs.
+// The epilogue warps bring the residual's coarse rows into L2 at the start
+// of a tile, so their latency hides behind layer 1.
 //
-// Barriers: x_full / x_empty per tile buffer, w_full / w_empty per ring
-// slot, acc1_full (layer 1 done), acc1_empty (acc1 read out), h_full (H
-// written and fenced for the tensor cores), acc2_full (layer 2 done: H and
-// its buffer free), acc2_empty (acc2 read out).  Every wait is bounded; on
-// time-out the CTA raises *err, every role stops, the producers wait
-// (bounded) for their copies in flight and the tensor memory is freed.
+// Barriers: full / empty per stage, acc1_full (layer 1 done), h_full (acc1
+// read out and H written and fenced for the tensor cores), w2_ready (W2 in
+// tensor memory), acc2_full (layer 2 done: H free), acc2_empty (acc2 read
+// out).  Every wait is bounded; on time-out the CTA raises *err, every role
+// stops, the producer waits (bounded) for its copies in flight and the
+// tensor memory is freed.
 constexpr int kMlpEpiWarps = 8;
-constexpr int kMlpThreads = (kMlpEpiWarps + 3) * 32;
-constexpr int kMlpTileBytes = 128 * kGemmKStage * 2;  // one 64-column block of a 128-row tile
+constexpr int kMlpThreads = (kMlpEpiWarps + 2) * 32;
+constexpr int kMlpXBlock = 128 * kGemmKStage * 2;  // one 64-column block of a 128-row tile
+constexpr int kMlpKS = kGemmKStage;                 // K columns per ring stage (128-byte swizzled rows)
+constexpr int kMlpXPart = kMlpXBlock;               // the X part of a stage
+constexpr int kMlpMaxHid = 256;
+constexpr int kMlpMaxStages = 8;
+constexpr size_t kMlpSmemLimit = 232448 - 4096;    // dynamic shared memory left beside the static part
 
 struct MlpDims {
-    int hid, kp, nkb1, nkb2, xbytes, slot;
-    __host__ __device__ MlpDims(int D, int hid_, int kp_)
-        : hid(hid_), kp(kp_), nkb1((kp_ + kGemmKStage - 1) / kGemmKStage), nkb2(hid_ / kGemmKStage),
-          xbytes((nkb1 > nkb2 ? nkb1 : nkb2) * kMlpTileBytes), slot((hid_ > D ? hid_ : D) * kGemmKStage * 2) {}
-    __host__ __device__ size_t smem() const { return (size_t)2 * xbytes + (size_t)2 * slot + 1024; }
+    int hid, kp, nkb1, hbytes, stage, S;
+    uint32_t c_w2, c_acc2, cols;
+    __host__ __device__ MlpDims(int hid_, int kp_)
+        : hid(hid_), kp(kp_), nkb1((kp_ + kMlpKS - 1) / kMlpKS), hbytes(128 * hid_ * 2),
+          stage(kMlpXPart + hid_ * kMlpKS * 2), S(0), c_w2((uint32_t)hid_), c_acc2((uint32_t)(hid_ + hid_ / 2)),
+          cols(32) {
+        const long room = (long)kMlpSmemLimit - 1024 - hbytes;
+        S = (int)(room / stage);
+        if (S > kMlpMaxStages) S = kMlpMaxStages;
+        while (cols < c_acc2 + 128u) cols <<= 1;
+    }
+    __host__ __device__ size_t smem() const { return (size_t)hbytes + (size_t)S * stage + 1024; }
 };
 
-// The MMA issue order: layer 1 of tile i then layer 2 of tile i.  The
-// weight producer loads the ring in the same order.
 template <typename T, int D>
 __global__ void __launch_bounds__(kMlpThreads, 1)
     mlp_project_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
-                       const __grid_constant__ CUtensorMap tmW2, const float *__restrict__ b1,
+                       const __grid_constant__ CUtensorMap tmXt, const __grid_constant__ CUtensorMap tmW1t,
+                       const __nv_bfloat16 *__restrict__ W2b, const float *__restrict__ b1,
                        const float *__restrict__ b2, const int32_t *__restrict__ map, const T *__restrict__ Mc,
-                       T *__restrict__ Mf, int64_t v0, int M, int hid, int kp, uint32_t tmem_cols,
-                       int *__restrict__ err) {
+                       T *__restrict__ Mf, int64_t v0, int M, int hid, int kp, int *__restrict__ err) {
     GOSH_DEP_WAIT();
     static_assert(D == 32 || D == 64 || D == 128, "D in {32, 64, 128}");
-    const MlpDims dm(D, hid, kp);
+    const MlpDims dm(hid, kp);
+    const int S = dm.S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (tc::smem_addr(smem_raw) & 1023u)) & 1023u);
-    const uint32_t xbuf0 = tc::smem_addr(smem);
-    const uint32_t ring0 = xbuf0 + 2u * (uint32_t)dm.xbytes;
-    __shared__ __align__(8) uint64_t x_full[2], x_empty[2], w_full[2], w_empty[2];
-    __shared__ __align__(8) uint64_t acc1_full, acc1_empty, h_full, acc2_full, acc2_empty, fin;
+    const uint32_t hbuf = tc::smem_addr(smem);
+    const uint32_t ring0 = hbuf + (uint32_t)dm.hbytes;
+    __shared__ __align__(8) uint64_t full[kMlpMaxStages], empty[kMlpMaxStages];
+    __shared__ __align__(8) uint64_t acc1_full, h_full, acc2_full, acc2_empty, w2_ready, fin;
+    __shared__ __align__(16) float sb1[kMlpMaxHid];
+    __shared__ float sb2[128];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = (M + 127) / 128;
     const int T_n = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+#define MLP_TILE_ROW0(t) (((int)blockIdx.x + (t) * (int)gridDim.x) * 128)
 
-    if (warp == kMlpEpiWarps) tc::tmem_alloc(&tmem_base, tmem_cols);
+    if (warp == kMlpEpiWarps) tc::tmem_alloc(&tmem_base, dm.cols);
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&x_full[i], 1);
-            tc::mbar_init(&x_empty[i], 1);
-            tc::mbar_init(&w_full[i], 1);
-            tc::mbar_init(&w_empty[i], 1);
+        for (int i = 0; i < S; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
         }
         tc::mbar_init(&acc1_full, 1);
-        tc::mbar_init(&acc1_empty, kMlpEpiWarps);
         tc::mbar_init(&h_full, kMlpEpiWarps);
         tc::mbar_init(&acc2_full, 1);
         tc::mbar_init(&acc2_empty, kMlpEpiWarps);
+        tc::mbar_init(&w2_ready, 4);
         tc::mbar_init(&fin, 1);
         s_fail = 0;
     }
+    for (int i = tid; i < hid; i += kMlpThreads) sb1[i] = b1[i];
+    for (int i = tid; i < 128; i += kMlpThreads) sb2[i] = i < D ? b2[i] : 0.0f;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
     volatile int *vfail = &s_fail;
 
+    // W2 into tensor memory (warps 0-3, while layer 1 of the first tile
+    // runs): warp w writes lanes 32 w .. 32 w + 31, row o of W2 (zero past
+    // D) packed two BF16 per column; layer 2 waits for w2_ready
+    if (warp < 4) {
+        const int o = warp * 32 + lane;
+        const uint4 *src = reinterpret_cast<const uint4 *>(W2b + (int64_t)(o < D ? o : 0) * hid);
+        for (int c = 0; c < hid / 2; c += 32) {
+            uint32_t r[32];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint4 q = o < D ? __ldg(src + c / 4 + i) : make_uint4(0, 0, 0, 0);
+                r[4 * i] = q.x;
+                r[4 * i + 1] = q.y;
+                r[4 * i + 2] = q.z;
+                r[4 * i + 3] = q.w;
+            }
+            tc::tmem_st32(tmem + ((uint32_t)(warp * 32) << 16) + dm.c_w2 + (uint32_t)c, r);
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&w2_ready);
+    }
+
     if (warp == kMlpEpiWarps) {
-        // ---- X tiles: buffer t & 1, reused once layer 2 of tile t - 2 is done ----
+        // ---- producer: per tile nkb1 stages of (X block, W1 block) ----
         if (lane == 0) {
-            int issued[2] = {0, 0};
-            for (int t = 0; t < T_n; ++t) {
-                const int b = t & 1;
-                if (*vfail) break;
-                if (t >= 2 && !tc::mbar_wait(&x_empty[b], ((t >> 1) - 1) & 1, kGemmWaitPolls)) {
-                    atomicExch(&s_fail, 1);
-                    break;
+            int issued[kMlpMaxStages];
+            for (int i = 0; i < kMlpMaxStages; ++i) issued[i] = 0;
+            int st = 0, round = 0;  // ring position: stage st, pass `round` over the ring
+            bool ok = true;
+            for (int t = 0; t < T_n && ok; ++t) {
+                const int m0 = MLP_TILE_ROW0(t);
+                if (t + 1 < T_n) {  // the next tile's rows into L2 while this one is computed
+                    const int m1 = MLP_TILE_ROW0(t + 1);
+                    for (int kb = 0; kb < dm.nkb1; ++kb) tma_prefetch_2d(&tmX, kb * kMlpKS, m1);
                 }
-                const int m0 = ((int)blockIdx.x + t * (int)gridDim.x) * 128;
-                mbar_arrive_expect_tx(&x_full[b], (uint32_t)(dm.nkb1 * kMlpTileBytes));
-                for (int kb = 0; kb < dm.nkb1; ++kb)
-                    tma_load_2d(xbuf0 + (uint32_t)(b * dm.xbytes + kb * kMlpTileBytes), &tmX, kb * kGemmKStage, m0,
-                                tc::smem_addr(&x_full[b]));
-                ++issued[b];
+                for (int kb = 0; kb < dm.nkb1; ++kb) {
+                    if (*vfail || (round > 0 && !tc::mbar_wait(&empty[st], (round - 1) & 1, kGemmWaitPolls))) {
+                        atomicExch(&s_fail, 1);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sx = ring0 + (uint32_t)(st * dm.stage);
+                    const uint32_t fb = tc::smem_addr(&full[st]);
+                    const int k0 = kb * kMlpKS;
+                    if (kp - k0 >= kMlpKS) {
+                        mbar_arrive_expect_tx(&full[st], (uint32_t)dm.stage);
+                        tma_load_2d(sx, &tmX, k0, m0, fb);
+                        tma_load_2d(sx + kMlpXPart, &tmW1, k0, 0, fb);
+                    } else {
+                        // the last 16 columns: two 8-column boxes per operand (no swizzle)
+                        mbar_arrive_expect_tx(&full[st], (uint32_t)(2 * 128 * 16 + 2 * hid * 16));
+                        tma_load_2d(sx, &tmXt, k0, m0, fb);
+                        tma_load_2d(sx + 128 * 16, &tmXt, k0 + 8, m0, fb);
+                        tma_load_2d(sx + kMlpXPart, &tmW1t, k0, 0, fb);
+                        tma_load_2d(sx + kMlpXPart + (uint32_t)(hid * 16), &tmW1t, k0 + 8, 0, fb);
+                    }
+                    ++issued[st];
+                    if (++st == S) {
+                        st = 0;
+                        ++round;
+                    }
+                }
             }
             // every copy has landed before shared memory goes away (at once
             // when the MMAs consumed them)
-            for (int b = 0; b < 2; ++b)
-                if (issued[b] > 0) tc::mbar_wait(&x_full[b], (uint32_t)(issued[b] - 1) & 1u, kGemmWaitPolls);
+            for (int st = 0; st < S; ++st)
+                if (issued[st] > 0) tc::mbar_wait(&full[st], (uint32_t)(issued[st] - 1) & 1u, kGemmWaitPolls);
         }
     } else if (warp == kMlpEpiWarps + 1) {
-        // ---- weight ring: per tile nkb1 W1 blocks, then nkb2 W2 blocks ----
-        if (lane == 0) {
-            int issued[2] = {0, 0};
-            int it = 0;
-            bool ok = true;
-            for (int t = 0; t < T_n && ok; ++t) {
-                for (int layer = 0; layer < 2 && ok; ++layer) {
-                    const int nb = layer == 0 ? dm.nkb1 : dm.nkb2;
-                    const uint32_t bytes = (uint32_t)((layer == 0 ? hid : D) * kGemmKStage * 2);
-                    for (int kb = 0; kb < nb; ++kb, ++it) {
-                        const int sl = it & 1;
-                        if (*vfail || (it >= 2 && !tc::mbar_wait(&w_empty[sl], ((it >> 1) - 1) & 1, kGemmWaitPolls))) {
-                            atomicExch(&s_fail, 1);
-                            ok = false;
-                            break;
-                        }
-                        mbar_arrive_expect_tx(&w_full[sl], bytes);
-                        tma_load_2d(ring0 + (uint32_t)(sl * dm.slot), layer == 0 ? &tmW1 : &tmW2, kb * kGemmKStage, 0,
-                                    tc::smem_addr(&w_full[sl]));
-                        ++issued[sl];
-                    }
-                }
-            }
-            for (int sl = 0; sl < 2; ++sl)
-                if (issued[sl] > 0) tc::mbar_wait(&w_full[sl], (uint32_t)(issued[sl] - 1) & 1u, kGemmWaitPolls);
-        }
-    } else if (warp == kMlpEpiWarps + 2) {
         // ---- MMA issuer ----
         if (lane == 0) {
             const uint32_t idesc1 = tc::make_idesc_bf16(128, hid);
-            const uint32_t idesc2 = tc::make_idesc_bf16(128, D);
-            int it = 0;
+            const uint32_t idesc2 = tc::make_idesc_bf16(128, 128);
+            int st = 0, round = 0;
             bool ok = true;
             for (int t = 0; t < T_n && ok; ++t) {
-                const int b = t & 1;
-                const uint32_t xb = xbuf0 + (uint32_t)(b * dm.xbytes);
-                // layer 1: X(t) and acc1 free (read out for tile t - 1)
-                ok = tc::mbar_wait(&x_full[b], (t >> 1) & 1, kGemmWaitPolls) &&
-                     (t == 0 || tc::mbar_wait(&acc1_empty, (t - 1) & 1, kGemmWaitPolls));
-                for (int kb = 0; kb < dm.nkb1 && ok; ++kb, ++it) {
-                    const int sl = it & 1;
-                    if (*vfail || !tc::mbar_wait(&w_full[sl], (it >> 1) & 1, kGemmWaitPolls)) {
+                // layer 1 (acc1 was read out before h_full of tile t - 1)
+                for (int kb = 0; kb < dm.nkb1; ++kb) {
+                    if (*vfail || !tc::mbar_wait(&full[st], round & 1, kGemmWaitPolls)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    const int k0 = kb * kGemmKStage;
-                    const int steps = min(kGemmKStage, kp - k0) / 16;
-                    const uint32_t wb = ring0 + (uint32_t)(sl * dm.slot);
-                    for (int j = 0; j < steps; ++j)
-                        tc::mma_bf16(tmem, tc::make_desc_sw128(xb + (uint32_t)(kb * kMlpTileBytes + 32 * j)),
-                                     tc::make_desc_sw128(wb + (uint32_t)(32 * j)), idesc1, (kb > 0 || j > 0) ? 1u : 0u);
-                    tc::mma_commit(&w_empty[sl]);
+                    const uint32_t sx = ring0 + (uint32_t)(st * dm.stage);
+                    if (kp - kb * kMlpKS >= kMlpKS) {
+#pragma unroll
+                        for (int j = 0; j < kMlpKS / 16; ++j)
+                            tc::mma_bf16(tmem, tc::make_desc_sw128(sx + (uint32_t)(32 * j)),
+                                         tc::make_desc_sw128(sx + (uint32_t)(kMlpXPart + 32 * j)), idesc1,
+                                         (kb > 0 || j > 0) ? 1u : 0u);
+                    } else {  // 16-column tail: K-major core matrices, the two 8-column halves LBO apart
+                        tc::mma_bf16(tmem, tc::make_desc(sx, 128 * 16, 128),
+                                     tc::make_desc(sx + kMlpXPart, (uint32_t)(hid * 16), 128), idesc1,
+                                     kb > 0 ? 1u : 0u);
+                    }
+                    tc::mma_commit(&empty[st]);
+                    if (++st == S) {
+                        st = 0;
+                        ++round;
+                    }
                 }
                 if (!ok) break;
                 tc::mma_commit(&acc1_full);
-                // layer 2: H(t) written, acc2 free (read out for tile t - 1)
+                // layer 2: H(t) written, acc2 read out for tile t - 1
                 ok = tc::mbar_wait(&h_full, t & 1, kGemmWaitPolls) &&
-                     (t == 0 || tc::mbar_wait(&acc2_empty, (t - 1) & 1, kGemmWaitPolls));
-                for (int kb = 0; kb < dm.nkb2 && ok; ++kb, ++it) {
-                    const int sl = it & 1;
-                    if (*vfail || !tc::mbar_wait(&w_full[sl], (it >> 1) & 1, kGemmWaitPolls)) {
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
-                    const uint32_t wb = ring0 + (uint32_t)(sl * dm.slot);
-                    for (int j = 0; j < kGemmKStage / 16; ++j)
-                        tc::mma_bf16(tmem + (uint32_t)hid, tc::make_desc_sw128(xb + (uint32_t)(kb * kMlpTileBytes + 32 * j)),
-                                     tc::make_desc_sw128(wb + (uint32_t)(32 * j)), idesc2, (kb > 0 || j > 0) ? 1u : 0u);
-                    tc::mma_commit(&w_empty[sl]);
-                }
+                     (t > 0 || tc::mbar_wait(&w2_ready, 0, kGemmWaitPolls)) &&
+                     (t == 0 || tc::mbar_wait(&acc2_empty, (t - 1) & 1, kGemmWaitPolls)) && !*vfail;
                 if (!ok) break;
+                tc::fence_after_sync();
+                for (int j = 0; j < hid / 16; ++j)
+                    tc::mma_bf16_tmem_a(tmem + dm.c_acc2, tmem + dm.c_w2 + (uint32_t)(8 * j),
+                                        tc::make_desc_sw128(hbuf + (uint32_t)((j / 4) * kMlpXBlock + 32 * (j % 4))),
+                                        idesc2, j > 0 ? 1u : 0u);
                 tc::mma_commit(&acc2_full);
-                tc::mma_commit(&x_empty[b]);
             }
             if (!ok) atomicExch(&s_fail, 1);
             tc::mma_commit(&fin);  // every MMA issued above has completed when this arrives
             tc::mbar_wait(&fin, 0, kGemmWaitPolls);
         }
     } else {
-        // ---- epilogues: warp w reads lanes 32 (w % 4) .. + 31, column half w / 4 ----
+        // ---- epilogues ----
+        // layer 1: warp w reads tile rows 32 (w % 4) .. + 31, hidden half w / 4
+        // layer 2: warp w reads output dimensions 32 (w % 4) .. + 31, tile rows 64 (w / 4) .. + 63
         const int quarter = warp & 3, half = warp >> 2;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        const int r = quarter * 32 + lane;  // row of the tile
+        const int r = quarter * 32 + lane;
         const int hc0 = half * (hid / 2), hc1 = hc0 + hid / 2;
-        constexpr int DH = D / 2;                       // acc2 columns of this warp
-        constexpr int PV = 16 / (int)sizeof(T);         // table values per 16-byte vector
-        constexpr int NV = DH / PV;                     // 16-byte vectors of this warp's part of a row
-        const int dc0 = half * DH;
+        const int o = quarter * 32 + lane;  // output dimension in layer 2
+        const bool dim_ok = o < D;
+        const bool warp_dims = quarter * 32 < D;
+        const float bo = sb2[o];
         for (int t = 0; t < T_n; ++t) {
-            const int b = t & 1;
-            const uint32_t xb = xbuf0 + (uint32_t)(b * dm.xbytes);
-            const int row = ((int)blockIdx.x + t * (int)gridDim.x) * 128 + r;
-            // the coarse rows of the residual do not depend on the MMAs: fetch them first
-            uint4 own[NV];
-            const int64_t vv = v0 + row;
-            if (row < M) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(Mc + (int64_t)__ldg(map + vv) * D + dc0);
+            const int m0 = MLP_TILE_ROW0(t);
+            // the residual's coarse rows do not depend on the MMAs: bring
+            // this warp's 64-byte piece of each into L2 now (lane l: rows
+            // rb0 + l and rb0 + 32 + l), its latency hides behind layer 1
+            const int rb0 = m0 + 64 * half;
+            int32_t mv[2] = {0, 0};
+            if (warp_dims) {
 #pragma unroll
-                for (int x = 0; x < NV; ++x) own[x] = __ldg(src + x);
+                for (int c = 0; c < 2; ++c) {
+                    const int rl = rb0 + 32 * c + lane;
+                    if (rl < M) {
+                        mv[c] = __ldg(map + v0 + rl);
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(Mc + (int64_t)mv[c] * D + quarter * 32));
+                    }
+                }
             }
             if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc1_full, t & 1, kGemmWaitPolls) && !*vfail)) {
                 atomicExch(&s_fail, 1);
@@ -470,13 +534,12 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                 tc::tmem_ld32(tmem + lane_addr + (uint32_t)c0, v);
                 uint32_t w[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float2 bb = __ldg(reinterpret_cast<const float2 *>(b1 + c0) + j);
-                    const __nv_bfloat162 h =
-                        __floats2bfloat162_rn(fmaxf(v[2 * j] + bb.x, 0.0f), fmaxf(v[2 * j + 1] + bb.y, 0.0f));
-                    w[j] = *reinterpret_cast<const uint32_t *>(&h);
+                for (int j = 0; j < 8; ++j) {
+                    const float4 bb = reinterpret_cast<const float4 *>(sb1 + c0)[j];
+                    w[2 * j] = bias_relu_bf16x2(v[4 * j], v[4 * j + 1], bb.x, bb.y);
+                    w[2 * j + 1] = bias_relu_bf16x2(v[4 * j + 2], v[4 * j + 3], bb.z, bb.w);
                 }
-                const uint32_t base = xb + (uint32_t)((c0 / kGemmKStage) * kMlpTileBytes + r * 128);
+                const uint32_t base = hbuf + (uint32_t)((c0 / kGemmKStage) * kMlpXBlock + r * 128);
                 const int cc = (c0 % kGemmKStage) / 8;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -489,34 +552,36 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             tc::fence_before_sync();
             tc::fence_proxy_async();
             __syncwarp();
-            if (lane == 0) {
-                tc::mbar_arrive(&acc1_empty);
-                tc::mbar_arrive(&h_full);
-            }
+            if (lane == 0) tc::mbar_arrive(&h_full);
             if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc2_full, t & 1, kGemmWaitPolls) && !*vfail)) {
                 atomicExch(&s_fail, 1);
                 break;
             }
             tc::fence_after_sync();
-            float y[DH];
+            // residual: row rb0 + i, lane o = output dimension (contiguous per warp);
+            // 32 rows per tensor-memory load
+            const int nrow = M - rb0;
+            T *dst = Mf + (v0 + rb0) * D + o;
 #pragma unroll
-            for (int c = 0; c < DH; c += 16) tc::tmem_ld16(tmem + lane_addr + (uint32_t)(hid + dc0 + c), y + c);
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&acc2_empty);
-            if (row < M) {
-                uint4 *dst = reinterpret_cast<uint4 *>(Mf + vv * D + dc0);
+            for (int c = 0; c < 2; ++c) {
+                float y[32];
+                if (warp_dims) tc::tmem_ld32(tmem + lane_addr + dm.c_acc2 + (uint32_t)(64 * half + 32 * c), y);
+                if (c == 1) {
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&acc2_empty);
+                }
+                if (!warp_dims || !dim_ok) continue;
+                T own[32];
 #pragma unroll
-                for (int x = 0; x < NV; ++x) {
-                    union {
-                        uint4 u;
-                        T t[PV];
-                    } pk;
-                    pk.u = own[x];
+                for (int i = 0; i < 32; ++i) {
+                    const int32_t mi = __shfl_sync(0xffffffffu, mv[c], i);
+                    own[i] = 32 * c + i < nrow ? __ldg(Mc + (int64_t)mi * D + o) : from_f<T>(0.0f);
+                }
 #pragma unroll
-                    for (int q = 0; q < PV; ++q)
-                        pk.t[q] = from_f<T>(to_f<T>(pk.t[q]) + y[x * PV + q] + __ldg(b2 + dc0 + x * PV + q));
-                    dst[x] = pk.u;
+                for (int i = 0; i < 32; ++i) {
+                    if (32 * c + i >= nrow) break;
+                    dst[(int64_t)(32 * c + i) * D] = from_f<T>(to_f<T>(own[i]) + y[i] + bo);
                 }
             }
         }
@@ -526,7 +591,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     __syncthreads();
     tc::fence_after_sync();
     if (s_fail && tid == 0) atomicExch(err, 1);
-    if (warp == kMlpEpiWarps) tc::tmem_dealloc(tmem, tmem_cols);
+    if (warp == kMlpEpiWarps) tc::tmem_dealloc(tmem, dm.cols);
+#undef MLP_TILE_ROW0
 }
 
 namespace {
@@ -552,17 +618,20 @@ gosh_status encoder(EncodeTiled *out) {
 }
 
 // Row-major BF16 matrix (rows x cols, row stride ld elements) read in boxes of
-// {64 columns, box_rows rows} with the 128-byte swizzle; out-of-range rows
-// and columns read as zero.
-gosh_status make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// {box_cols columns, box_rows rows}: 64 columns written with the 128-byte
+// swizzle, or 8 columns (one 16-byte core-matrix column, no swizzle);
+// out-of-range rows and columns read as zero.
+gosh_status make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                     int box_cols = kGemmKStage) {
     EncodeTiled enc = nullptr;
     GOSH_TRY(encoder(&enc));
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kGemmKStage, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           box_cols == kGemmKStage ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d) for a %lld x %lld operand, stride %lld", (int)r, (long long)rows,
@@ -613,10 +682,10 @@ gosh_status check_operands(const void *A, int64_t lda, const void *B, int64_t ld
 }
 
 template <typename T, int D>
-gosh_status launch_mlp(const CUtensorMap &mx, const CUtensorMap &m1, const CUtensorMap &m2, const float *b1,
-                       const float *b2, const int32_t *map, const void *Mc, void *Mf, int64_t v0, int M, int hid, int kp,
-                       int *err, cudaStream_t s) {
-    const MlpDims dm(D, hid, kp);
+gosh_status launch_mlp(const CUtensorMap &mx, const CUtensorMap &m1, const CUtensorMap &mxt, const CUtensorMap &m1t,
+                       const __nv_bfloat16 *W2b, const float *b1, const float *b2, const int32_t *map, const void *Mc,
+                       void *Mf, int64_t v0, int M, int hid, int kp, int *err, cudaStream_t s) {
+    const MlpDims dm(hid, kp);
     const size_t smem = dm.smem();
     static size_t attr = 0;
     if (attr < smem) {
@@ -624,24 +693,24 @@ gosh_status launch_mlp(const CUtensorMap &mx, const CUtensorMap &m1, const CUten
             cudaFuncSetAttribute(mlp_project_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = smem;
     }
-    uint32_t cols = 32;
-    while (cols < (uint32_t)(hid + D)) cols <<= 1;
     const int ntiles = (int)ceil_div(M, 128);
     const int grid = ntiles < num_sms() ? ntiles : num_sms();
-    launch_dep(mlp_project_kernel<T, D>, grid, kMlpThreads, smem, s, mx, m1, m2, b1, b2, map, static_cast<const T *>(Mc),
-               static_cast<T *>(Mf), v0, M, hid, kp, cols, err);
+    launch_dep(mlp_project_kernel<T, D>, grid, kMlpThreads, smem, s, mx, m1, mxt, m1t, W2b, b1, b2, map,
+               static_cast<const T *>(Mc), static_cast<T *>(Mf), v0, M, hid, kp, err);
     GOSH_TRY_CUDA(cudaGetLastError());
     return GOSH_OK;
 }
 
 }  // namespace
 
-// Whether tc_mlp_project takes these shapes: d in {32, 64, 128}, hidden a
-// multiple of 64 up to 256 (both accumulators in one SM's tensor memory).
+// Whether tc_mlp_project takes these shapes: d in {32, 64, 128}, hidden 64,
+// 128 or 256 (acc1, W2 and acc2 in one SM's tensor memory), at least two
+// ring stages beside the hidden tile in shared memory.
 bool tc_mlp_fused_ok(int d, int hid, int kp) {
-    if (!(d == 32 || d == 64 || d == 128) || hid % 64 != 0 || hid < 64 || hid > 256 || kp % 16 != 0 || kp <= 0)
+    if (!(d == 32 || d == 64 || d == 128) || !(hid == 64 || hid == 128 || hid == 256) || kp % 16 != 0 || kp <= 0)
         return false;
-    return MlpDims(d, hid, kp).smem() <= 232448 - 1024;
+    const MlpDims dm(hid, kp);
+    return kp % kMlpKS == 16 && dm.S >= 2 && dm.cols <= 512;
 }
 
 // Mf[v0 + m] = Mc[map[v0 + m]] + relu(X[m] W1^T + b1) W2^T + b2 for m < M:
@@ -651,19 +720,19 @@ gosh_status tc_mlp_project(const __nv_bfloat16 *X, const __nv_bfloat16 *W1b, con
                            const float *b1, const float *b2, const int32_t *map, const void *Mc, void *Mf, int64_t v0,
                            int d, int hid, int kp, gosh_dtype dt, int M, int *err, cudaStream_t s) {
     GOSH_CHECK_ARG(M > 0 && tc_mlp_fused_ok(d, hid, kp), "fused projection: unsupported shape");
-    GOSH_CHECK_ARG(((uintptr_t)X & 15) == 0 && ((uintptr_t)W1b & 15) == 0 && ((uintptr_t)W2b & 15) == 0 &&
-                       ((uintptr_t)Mc & 15) == 0 && ((uintptr_t)Mf & 15) == 0 && ((uintptr_t)b1 & 7) == 0,
+    GOSH_CHECK_ARG(((uintptr_t)X & 15) == 0 && ((uintptr_t)W1b & 15) == 0 && ((uintptr_t)W2b & 3) == 0,
                    "fused projection: operands must be 16-byte aligned");
-    CUtensorMap mx, m1, m2;
-    GOSH_TRY(make_map(&mx, X, M, kp, kp, 128));
-    GOSH_TRY(make_map(&m1, W1b, hid, kp, kp, hid));
-    GOSH_TRY(make_map(&m2, W2b, d, hid, hid, d));
+    CUtensorMap mx, m1, mxt, m1t;
+    GOSH_TRY(make_map(&mx, X, M, kp, kp, 128, kMlpKS));
+    GOSH_TRY(make_map(&m1, W1b, hid, kp, kp, hid, kMlpKS));
+    GOSH_TRY(make_map(&mxt, X, M, kp, kp, 128, 8));
+    GOSH_TRY(make_map(&m1t, W1b, hid, kp, kp, hid, 8));
     auto go = [&](auto *tp) -> gosh_status {
         using T = std::remove_pointer_t<decltype(tp)>;
         switch (d) {
-        case 32: return launch_mlp<T, 32>(mx, m1, m2, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
-        case 64: return launch_mlp<T, 64>(mx, m1, m2, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
-        default: return launch_mlp<T, 128>(mx, m1, m2, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
+        case 32: return launch_mlp<T, 32>(mx, m1, mxt, m1t, W2b, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
+        case 64: return launch_mlp<T, 64>(mx, m1, mxt, m1t, W2b, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
+        default: return launch_mlp<T, 128>(mx, m1, mxt, m1t, W2b, b1, b2, map, Mc, Mf, v0, M, hid, kp, err, s);
         }
     };
     switch (dt) {
