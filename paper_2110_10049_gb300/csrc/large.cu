@@ -193,7 +193,7 @@ __device__ void pair_tile(const PairArgs &a, int64_t s0, int64_t nsrc, int32_t *
                 const int jj = t / (a.k + 1);
                 const float b = (t % (a.k + 1)) == 0 ? 1.0f : 0.0f;
                 const float lr = (active && t < ns) ? slr[j * 8 + jj] : 0.0f;
-                const float score = ok ? (b - __frcp_rn(1.0f + __expf(-xx))) * lr : 0.0f;
+                const float score = ok ? (b - sigmoid_f(xx)) * lr : 0.0f;
 #pragma unroll
                 for (int e = 0; e < E; ++e) r[e] = fmaf(row[x][e], score, r[e]);
                 float old16[RED16 ? E : 1];

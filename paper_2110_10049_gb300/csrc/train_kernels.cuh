@@ -18,6 +18,12 @@ __device__ __forceinline__ uint32_t sr_source_seed(uint64_t seed, uint64_t graph
     return h;
 }
 
+// sigma(x) = 1 / (1 + e^-x) with the fast exponential and the fast
+// reciprocal (MUFU rcp: within 2 ulps, 0 for an infinite denominator); the
+// correctly rounded reciprocal costs a slow path that made it a tenth of
+// the level-0 step.
+__device__ __forceinline__ float sigmoid_f(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
+
 __device__ __forceinline__ float softplus_f(float z) {
     return fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)));
 }
@@ -344,7 +350,7 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
                         }
                         const float xd = group_sum<L>(s0 + s1);
                         const float b = t == 0 ? 1.0f : 0.0f;
-                        const float sig = __frcp_rn(1.0f + __expf(-xd));
+                        const float sig = sigmoid_f(xd);
                         const float score = ok ? (b - sig) * a.lr : 0.0f;
 #pragma unroll
                         for (int x = 0; x < NV; ++x) {
@@ -429,7 +435,7 @@ __device__ __forceinline__ void train_tile(const TrainArgs &a, const int64_t v0,
                     const float part = dot2<E>(r, row[s]);
                     const float x = group_sum<L>(part);
                     const float b = t == 0 ? 1.0f : 0.0f;
-                    const float sig = __frcp_rn(1.0f + __expf(-x));
+                    const float sig = sigmoid_f(x);
                     const float score = ok ? (b - sig) * a.lr : 0.0f;
                     axpy2<E>(r, row[s], score);
                     float old16[RED16 ? E : 1];

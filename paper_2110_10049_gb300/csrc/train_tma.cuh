@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) train_tma_kernel(TrainArgs a) 
                 const float part = dot2<E>(r, row);
                 const float x = group_sum<L>(part);
                 const float b = t == 0 ? 1.0f : 0.0f;
-                const float score = ok ? (b - __frcp_rn(1.0f + __expf(-x))) * a.lr : 0.0f;
+                const float score = ok ? (b - sigmoid_f(x)) * a.lr : 0.0f;
                 axpy2<E>(r, row, score);
                 float old16[RED16 ? E : 1];
                 if (RED16) {
