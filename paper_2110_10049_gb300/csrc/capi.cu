@@ -449,6 +449,8 @@ gosh_status check_params(const gosh_params *p) {
                    p->epoch_overlap);
     GOSH_CHECK_ARG(p->overlap_min_vertices >= 0, "overlap_min_vertices must be >= 0");
     GOSH_CHECK_ARG(p->epoch_unit == 0 || p->epoch_unit == 1, "epoch_unit must be 0 or 1 (got %d)", p->epoch_unit);
+    GOSH_CHECK_ARG(p->cooperative_epochs == 0 || p->cooperative_epochs == 1, "cooperative_epochs must be 0 or 1 (got %d)",
+                   p->cooperative_epochs);
     return GOSH_OK;
 }
 
@@ -529,6 +531,7 @@ gosh_status gosh_params_default(gosh_params *p) {
     p->large_evict = 0;
     p->overlap_min_vertices = 65536;
     p->epoch_overlap = 1;
+    p->cooperative_epochs = 0;
     return GOSH_OK;
 }
 

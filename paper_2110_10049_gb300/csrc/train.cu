@@ -256,12 +256,14 @@ gosh_status train_level_impl(const gosh_csr *g, void *M, int level, int epochs, 
     if (!det) {
         a.src_begin = 0;
         a.src_end = n;
-        // Small levels: every epoch in one cooperative launch (per-epoch
-        // launches cost about as much as the epochs' work).
-        // Only where one wave holds every tile (more would make warps loop).
+        // On request (cooperative_epochs), every epoch in one cooperative
+        // launch, where one wave holds every tile (more would make warps
+        // loop); by default one launch per epoch, whose programmatic
+        // overlap measured faster than a grid barrier per epoch.
         const int coop_cap = num_sms() * kern->epochs_blocks_per_sm;
         const int grid = grid_for(n);
-        if (kern->launch_epochs && !loss_per_epoch && epochs > 1 && kern->epochs_blocks_per_sm > 0 &&
+        if (p->cooperative_epochs && kern->launch_epochs && !loss_per_epoch && epochs > 1 &&
+            kern->epochs_blocks_per_sm > 0 &&
             ceil_div(ceil_div(n, a.tile), kern->warps) <= coop_cap) {
             const int g = grid;
             Scratch bar;

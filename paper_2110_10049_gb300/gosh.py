@@ -45,7 +45,8 @@ class gosh_params(C.Structure):
                 ("persistent_small_levels", C.c_int), ("vertices_per_warp", C.c_int),
                 ("walk_length", C.c_int), ("walk_window", C.c_int), ("large_serial", C.c_int),
                 ("large_evict", C.c_int), ("overlap_min_vertices", C.c_int64), ("epoch_overlap", C.c_int),
-                ("large_pools", C.c_int), ("epoch_unit", C.c_int)]
+                ("large_pools", C.c_int), ("epoch_unit", C.c_int),
+                ("cooperative_epochs", C.c_int)]
 
 
 class gosh_walk_stats(C.Structure):

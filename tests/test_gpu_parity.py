@@ -185,23 +185,25 @@ def test_hogwild_single_warp_is_sequential(g, k):
 
 @pytest.mark.parametrize("k", [3, 5, 7])
 def test_hogwild_single_warp_all_epochs_in_one_launch(g, k):
-    # Without a loss request a small level runs every epoch in one cooperative
-    # launch, each epoch's samples drawn before the barrier that closes the
-    # previous one: the single-warp epochs must still be the sequential ones.
+    # With cooperative_epochs and no loss request a small level runs every
+    # epoch in one cooperative launch, each epoch's samples drawn before the
+    # barrier that closes the previous one: the single-warp epochs must still
+    # be the sequential ones.
     gr = synth.random_graph(30, 0.2, 17)
     M0 = oracle.init_uniform(gr.n, 128, 0, 3).astype(np.float32).astype(np.float64) * 60
     Mo = M0.copy()
     _, no = oracle.train_sequential(gr.rowptr, gr.col, Mo, k, 0, 20, 0.05, 1e-4, 8)
     csr = g.to_device_csr(gr.rowptr, gr.col)
-    for pas in (2, 4):
-        M = dev(M0, torch.float32)
-        p = g.default_params(d=128, k=k, lr=0.05, seed=8, lanes_per_row=32, samples_per_pass=pas,
-                             vertices_per_warp=32)
-        nup = torch.zeros(1, dtype=torch.int64, device="cuda")
-        g.gosh_train_level(csr, M, 0, 20, p, n_updates=nup)
-        torch.cuda.synchronize()
-        assert int(nup.item()) == no
-        assert rel_fro(M.double().cpu().numpy(), Mo) <= DET_TOL
+    for coop in (1, 0):
+        for pas in (2, 4):
+            M = dev(M0, torch.float32)
+            p = g.default_params(d=128, k=k, lr=0.05, seed=8, lanes_per_row=32, samples_per_pass=pas,
+                                 vertices_per_warp=32, cooperative_epochs=coop)
+            nup = torch.zeros(1, dtype=torch.int64, device="cuda")
+            g.gosh_train_level(csr, M, 0, 20, p, n_updates=nup)
+            torch.cuda.synchronize()
+            assert int(nup.item()) == no
+            assert rel_fro(M.double().cpu().numpy(), Mo) <= DET_TOL
 
 
 # Quality bars of the lock-free path (held-out and training-edge AUC) are
