@@ -126,7 +126,10 @@ int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass) {
     const bool atomic_lockfree = (red16 || f32_lockfree) && !p->plain_stores;
     const int mid = atomic_lockfree ? 32 : (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC ? 8 : 16);
     const int large = atomic_lockfree ? 16 : 32;
-    if (t <= 0) t = n >= (int64_t(1) << 19) ? large : (n >= (int64_t(1) << 16) ? mid : 4);
+    // atomic lock-free levels of 2^14 to 2^16 rows: 8 (level 2 of R-MAT 20,
+    // 22k rows: 10.4 us per BF16 epoch against 12.6 at 4)
+    const int small = atomic_lockfree && n >= (int64_t(1) << 14) ? 8 : 4;
+    if (t <= 0) t = n >= (int64_t(1) << 19) ? large : (n >= (int64_t(1) << 16) ? mid : small);
     t = t < G ? G : (t > 32 ? 32 : t);
     return t / G * G;
 }
@@ -147,38 +150,41 @@ gosh_status pick_train_kernel(gosh_dtype dtype, int d, int k, int mode, int lane
     // Defaults by level size, from per-level sweeps of lanes per row L,
     // samples per pass P and tile on the R-MAT 20 hierarchy (d = 128, k = 3;
     // L0 = one 16-byte vector per lane; P < 0: rows staged by TMA):
-    //  - FP32 lock-free: from 2^19 rows registers, L0/2 lanes, P = 4 (362 us
+    //  - FP32 lock-free: from 2^19 rows registers, L0/2 lanes, P = 4 (361 us
     //    per level-0 epoch against 444 TMA-staged); from 2^16 registers, L0
-    //    lanes, P = 4; from 2^14 registers, L0/2 lanes, P = 4; below,
-    //    TMA-staged with L0/2 lanes (a latency-bound level: every row of a
-    //    round in flight at once);
-    //  - 16-bit tables (atomic changes): from 2^14 rows registers, L0/2
-    //    lanes (two vectors per lane, more sources in flight), P = 2; below,
-    //    BF16 tables TMA-staged with L0/2 lanes (FP16 has no staged variant:
-    //    L0 lanes, P = 4); with plain stores, L0/2 lanes and P = 4 except L0
-    //    lanes from 2^16 to 2^19 rows.
+    //    lanes, P = 4; from 2^12 registers, L0/2 lanes, P = 2 (level 2, 22k
+    //    rows: 14.9 us against 16.3 with P = 4; level 3, 6.4k rows: 6.5 us
+    //    against 7.7 TMA-staged); below, TMA-staged with L0 lanes (a
+    //    latency-bound level: every row of a round in flight at once; 3.7 us
+    //    against 3.9 with L0/2 lanes);
+    //  - BF16 tables (atomic changes): registers, L0/2 lanes (two vectors per
+    //    lane, more sources in flight), P = 2 at every size (levels of 6.4k,
+    //    1.6k and 1.3k rows: 5.1, 4.0 and 3.9 us against 5.7, 4.2 and 4.1
+    //    TMA-staged); FP16 tables the same from 2^14 rows, below L0 lanes,
+    //    P = 4; with plain stores, L0/2 lanes and P = 4 except L0 lanes from
+    //    2^16 to 2^19 rows.
     const bool defaulted = lanes <= 0 && pass == 0;
     if (!det && defaulted) {
         const int staged = ns <= 4 ? -4 : -6;
         const int half = nat >= 4 ? nat / 2 : nat;
         if (dtype == GOSH_F32 && mode == kModeRed) {
-            if (n >= (int64_t(1) << 19) || (n >= (int64_t(1) << 14) && n < (int64_t(1) << 16))) {
+            if (n >= (int64_t(1) << 19)) {
                 lanes = half;
                 pass = 4;
-            } else if (n >= (int64_t(1) << 14)) {
+            } else if (n >= (int64_t(1) << 16)) {
                 lanes = nat;
                 pass = 4;
-            } else {
+            } else if (n >= (int64_t(1) << 12)) {
                 lanes = half;
+                pass = 2;
+            } else {
+                lanes = nat;
                 pass = ns <= 6 ? staged : 4;
             }
         } else if (dtype != GOSH_F32 && mode == kModeRed) {
-            if (n >= (int64_t(1) << 14)) {
+            if (n >= (int64_t(1) << 14) || dtype == GOSH_BF16) {
                 lanes = half;
                 pass = 2;
-            } else if (dtype == GOSH_BF16 && ns <= 6) {
-                lanes = half;
-                pass = staged;
             } else {
                 lanes = nat;
                 pass = 4;
