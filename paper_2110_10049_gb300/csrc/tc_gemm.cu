@@ -286,12 +286,13 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
 // coarse-row loads and the fine-row stores of a warp are contiguous.
 //
 // One CTA per SM walks the chunk's 128-row tiles (tile = blockIdx.x + i *
-// gridDim.x).  Roles: warps 0-7 run the epilogues (warps 0-3 first write
-// W2 into tensor memory, while layer 1 of the first tile runs), warp 8
+// gridDim.x).  Roles: warps 0-15 run the epilogues (four warps per 32
+// tensor-memory lanes, each a quarter of the columns; warps 0-3 first write
+// W2 into tensor memory, while layer 1 of the first tile runs), warp 16
 // loads the ring of S stages (each: one 64-column block of the X tile and
 // the matching block of W1, both as one 128-byte-swizzled TMA box; the
 // 16-column tail of K as two 8-column boxes per operand without swizzle)
-// and prefetches the next tile's X rows into L2, warp 9 issues the MMAs.
+// and prefetches the next tile's X rows into L2, warp 17 issues the MMAs.
 // The epilogue warps bring the residual's coarse rows into L2 at the start
 // of a tile, so their latency hides behind layer 1.
 //
@@ -301,7 +302,8 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
 // out).  Every wait is bounded; on time-out the CTA raises *err, every role
 // stops, the producer waits (bounded) for its copies in flight and the
 // tensor memory is freed.
-constexpr int kMlpEpiWarps = 8;
+constexpr int kMlpEpiWarps = 16;
+constexpr int kMlpParts = kMlpEpiWarps / 4;  // epilogue warps sharing each 32 tensor-memory lanes
 constexpr int kMlpThreads = (kMlpEpiWarps + 2) * 32;
 constexpr int kMlpXBlock = 128 * kGemmKStage * 2;  // one 64-column block of a 128-row tile
 constexpr int kMlpKS = kGemmKStage;                 // K columns per ring stage (128-byte swizzled rows)
@@ -495,12 +497,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         }
     } else {
         // ---- epilogues ----
-        // layer 1: warp w reads tile rows 32 (w % 4) .. + 31, hidden half w / 4
-        // layer 2: warp w reads output dimensions 32 (w % 4) .. + 31, tile rows 64 (w / 4) .. + 63
-        const int quarter = warp & 3, half = warp >> 2;
+        // layer 1: warp w reads tile rows 32 (w % 4) .. + 31, part w / 4 of the hidden columns
+        // layer 2: warp w reads output dimensions 32 (w % 4) .. + 31, part w / 4 of the tile rows
+        constexpr int RW = 128 / kMlpParts;  // tile rows per warp in layer 2
+        const int quarter = warp & 3, part = warp >> 2;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         const int r = quarter * 32 + lane;
-        const int hc0 = half * (hid / 2), hc1 = hc0 + hid / 2;
+        const int hc0 = part * (hid / kMlpParts), hc1 = hc0 + hid / kMlpParts;
         const int o = quarter * 32 + lane;  // output dimension in layer 2
         const bool dim_ok = o < D;
         const bool warp_dims = quarter * 32 < D;
@@ -508,13 +511,15 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         for (int t = 0; t < T_n; ++t) {
             const int m0 = MLP_TILE_ROW0(t);
             // the residual's coarse rows do not depend on the MMAs: bring
-            // this warp's 64-byte piece of each into L2 now (lane l: rows
-            // rb0 + l and rb0 + 32 + l), its latency hides behind layer 1
-            const int rb0 = m0 + 64 * half;
-            int32_t mv[2] = {0, 0};
+            // this warp's piece of each into L2 now (lane l: rows rb0 + l,
+            // rb0 + 32 + l, ...), its latency hides behind layer 1
+            const int rb0 = m0 + RW * part;
+            int32_t mv[RW / 32];
+#pragma unroll
+            for (int c = 0; c < RW / 32; ++c) mv[c] = 0;
             if (warp_dims) {
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
+                for (int c = 0; c < RW / 32; ++c) {
                     const int rl = rb0 + 32 * c + lane;
                     if (rl < M) {
                         mv[c] = __ldg(map + v0 + rl);
@@ -563,10 +568,10 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             const int nrow = M - rb0;
             T *dst = Mf + (v0 + rb0) * D + o;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
+            for (int c = 0; c < RW / 32; ++c) {
                 float y[32];
-                if (warp_dims) tc::tmem_ld32(tmem + lane_addr + dm.c_acc2 + (uint32_t)(64 * half + 32 * c), y);
-                if (c == 1) {
+                if (warp_dims) tc::tmem_ld32(tmem + lane_addr + dm.c_acc2 + (uint32_t)(RW * part + 32 * c), y);
+                if (c == RW / 32 - 1) {
                     tc::fence_before_sync();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&acc2_empty);
@@ -703,14 +708,15 @@ gosh_status launch_mlp(const CUtensorMap &mx, const CUtensorMap &m1, const CUten
 
 }  // namespace
 
-// Whether tc_mlp_project takes these shapes: d in {32, 64, 128}, hidden 64,
-// 128 or 256 (acc1, W2 and acc2 in one SM's tensor memory), at least two
-// ring stages beside the hidden tile in shared memory.
+// Whether tc_mlp_project takes these shapes: d in {32, 64, 128}, hidden 128
+// or 256 (acc1, W2 and acc2 in one SM's tensor memory; whole 32-column
+// loads for each epilogue warp), at least two ring stages beside the hidden
+// tile in shared memory.
 bool tc_mlp_fused_ok(int d, int hid, int kp) {
     if (!(d == 32 || d == 64 || d == 128) || !(hid == 64 || hid == 128 || hid == 256) || kp % 16 != 0 || kp <= 0)
         return false;
     const MlpDims dm(hid, kp);
-    return kp % kMlpKS == 16 && dm.S >= 2 && dm.cols <= 512;
+    return kp % kMlpKS == 16 && hid / kMlpParts % 32 == 0 && dm.S >= 2 && dm.cols <= 512;
 }
 
 // Mf[v0 + m] = Mc[map[v0 + m]] + relu(X[m] W1^T + b1) W2^T + b2 for m < M:
