@@ -187,12 +187,13 @@ def _bf16_forward_ref(W1, b1, W2, b2, X):
 @pytest.mark.parametrize("d,hidden,dt,scale", [(128, 256, "f32", 16), (128, 256, "bf16", 15), (64, 256, "f16", 15),
                                                 (32, 64, "bf16", 15), (64, 128, "f32", 15)])
 def test_projection_tiles_tables_ragged(d, hidden, dt, scale):
-    """gosh_project_learned over more 128-row tiles than SMs (so CTAs of the
-    persistent kernel reuse both tile buffers), a ragged last tile, and every
-    table type: Mf - copy against the oracle's forward pass with the GPU's
-    BF16 roundings (features, weights, hidden layer), norm-wise and row by
-    row (a row from the wrong tile or a mis-swizzled hidden block is off by
-    O(1))."""
+    """gosh_project_learned over more 128-row tiles than SMs (so each CTA of
+    the fused persistent kernel walks several tiles, its stage ring and
+    barrier phases wrapping), a ragged last tile, and every table type: Mf -
+    copy against the oracle's forward pass with the GPU's BF16 roundings
+    (features, weights, hidden layer), norm-wise and row by row (a row from
+    the wrong tile or a mis-swizzled hidden block is off by O(1)).  Hidden
+    width 64 takes the two-GEMM form (the fused kernel takes 128 and 256)."""
     g = gosh()
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dt]
     gr = synth.rmat_graph(scale, 8, 9)
