@@ -108,6 +108,21 @@ def test_epoch_overlap_limits_checked_first(bad):
     assert rc == 1 and "overlap" in L.gosh_last_error().decode()
 
 
+@pytest.mark.parametrize("bad", [dict(cooperative_epochs=2), dict(cooperative_epochs=-1), dict(epoch_unit=2)])
+def test_launch_and_unit_flags_checked_first(bad):
+    # both flags take 0 or 1; checked before any device work (placeholder
+    # device pointers are never touched); the defaults are 0
+    L = g.lib()
+    p = g.default_params(d=32)
+    assert p.cooperative_epochs == 0 and p.epoch_unit == 0
+    for key, val in bad.items():
+        setattr(p, key, val)
+    cg = g.gosh_csr(10, 256, 512, 1)
+    rc = L.gosh_train_level(C.byref(cg), C.c_void_p(1024), 0, 3, C.byref(p), None, None, None)
+    name = next(iter(bad))
+    assert rc == 1 and name in L.gosh_last_error().decode()
+
+
 def test_allocator_needs_both_functions():
     """gosh_set_allocator takes both callbacks or neither (no device use)."""
     L = g.lib()
