@@ -107,8 +107,9 @@ typedef struct gosh_params {
     int large_parts;        /* LargeGraphGPU: K; 0 = derive from device_budget_bytes */
     int persistent_small_levels; /* gosh_embed, lock-free with copy projection and automatic
                                kernels: 1 trains every level with |V_i| <= 2^17 in one
-                               persistent launch (as gosh_embed_batch does); 0 (default)
-                               launches every epoch separately */
+                               persistent launch (as gosh_embed_batch does; built for many
+                               graphs at once, it is slower for one: R-MAT 20, 835 against
+                               347 ms per embed); 0 (default) launches every epoch separately */
     int vertices_per_warp;  /* sources a warp takes per tile (<= 32, rounded to a multiple
                                of 32/lanes_per_row); 0 = by level size (8 / 16 / 32) */
     int walk_length;        /* gosh_train_level_walks: vertices per random walk, l (default 8) */
@@ -523,7 +524,11 @@ gosh_status gosh_mlp_train(gosh_mlp *m, const gosh_csr *g_fine, const int32_t *m
                            int64_t max_rows, void *stream, double *final_loss);
 
 /* M_fine[v] = M_coarse[map v] + MLP(f(v)) for every vertex of g_fine,
- * rounded to nearest in the storage type.  Synchronous. */
+ * rounded to nearest in the storage type.  The hidden layer is rounded to
+ * BF16.  For d in {32, 64, 128} and hidden width 128 or 256 both layers run
+ * in one persistent tensor-core kernel per chunk of 2^18 vertices (the
+ * hidden layer never leaves the SM); other shapes take two GEMMs.
+ * Synchronous. */
 gosh_status gosh_project_learned(gosh_mlp *m, const void *M_coarse, const int32_t *map,
                                  const gosh_csr *g_fine, void *M_fine, int d, gosh_dtype dtype,
                                  void *stream);

@@ -848,8 +848,8 @@ gosh_status gosh_embed(const gosh_csr *g0, const gosh_params *params, void *M0_o
 
     // per-level events, read once at the end so that no level waits for the host
     EventList ev(stats ? 2 * D + 1 : 0);
-    // The small levels (|V_i| <= 2^17) of a lock-free, copy-projection run go
-    // through one persistent launch (epochs would otherwise be launch-bound);
+    // On request (persistent_small_levels), the small levels (|V_i| <= 2^17)
+    // of a lock-free, copy-projection run go through one persistent launch;
     // the large levels keep one launch per epoch with the best kernel.
     int top = D - 1;  // highest level still to train below
     const bool persist = p.persistent_small_levels && p.mode == GOSH_HOGWILD && p.projection == 0 && D > 1 &&
