@@ -448,9 +448,8 @@ struct EdgeBlocks {
     }
 };
 
-// Host sample pools (Sec. 5: the positive samples are generated on the host
-// in parallel and sent to the GPU as they are needed; the negatives are drawn
-// on the GPU).  The pool of kernel K_{a,b} in round r holds, for every source
+// Host sample pools (Sec. 5: host threads draw each kernel's positives and
+// ship them to the device just in time; negatives stay device-drawn).  The pool of kernel K_{a,b} in round r holds, for every source
 // of the pair (V^a, then V^b when a != b), its B positives as local ids of
 // the opposite part, or -1 when it has no neighbour there.  A positive is
 // drawn exactly as the device draws it from an edge block (Philox word 0 of
