@@ -296,10 +296,11 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
 // The epilogue warps bring the residual's coarse rows into L2 at the start
 // of a tile, so their latency hides behind layer 1.
 //
-// Barriers: full / empty per stage, acc1_full (layer 1 done), h_full (acc1
-// read out and H written and fenced for the tensor cores), w2_ready (W2 in
-// tensor memory), acc2_full (layer 2 done: H free), acc2_empty (acc2 read
-// out).  Every wait is bounded; on time-out the CTA raises *err, every role
+// Barriers: full / empty per stage, hs_full (the K block staged in H's
+// buffer arrived), acc1_full (layer 1 done), h_full (acc1 read out and H
+// written and fenced for the tensor cores), w2_ready (W2 in tensor memory),
+// acc2_full (layer 2 done: H's buffer free for the next tile's staged
+// block), acc2_empty (acc2 read out).  Every wait is bounded; on time-out the CTA raises *err, every role
 // stops, the producer waits (bounded) for its copies in flight and the
 // tensor memory is freed.
 constexpr int kMlpEpiWarps = 16;
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     const uint32_t hbuf = tc::smem_addr(smem);
     const uint32_t ring0 = hbuf + (uint32_t)dm.hbytes;
     __shared__ __align__(8) uint64_t full[kMlpMaxStages], empty[kMlpMaxStages];
-    __shared__ __align__(8) uint64_t acc1_full, h_full, acc2_full, acc2_empty, w2_ready, fin;
+    __shared__ __align__(8) uint64_t acc1_full, h_full, acc2_full, acc2_empty, w2_ready, hs_full, fin;
     __shared__ __align__(16) float sb1[kMlpMaxHid];
     __shared__ float sb2[128];
     __shared__ uint32_t tmem_base;
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
         tc::mbar_init(&acc2_full, 1);
         tc::mbar_init(&acc2_empty, kMlpEpiWarps);
         tc::mbar_init(&w2_ready, 4);
+        tc::mbar_init(&hs_full, 1);
         tc::mbar_init(&fin, 1);
         s_fail = 0;
     }
@@ -374,6 +376,12 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
     volatile int *vfail = &s_fail;
+    // K block kh of every tile is staged in the hidden tile's buffer, idle
+    // from the end of layer 2 of one tile to the hidden-layer epilogue of the
+    // next: one more stage in flight during layer 1 (the last full block, so
+    // that its load, which waits for the previous tile's layer 2, starts a
+    // few stages before it is needed); none when a tile has fewer than three
+    const int kh = dm.nkb1 >= 3 ? dm.nkb1 - 2 : -1;
 
     // W2 into tensor memory (warps 0-3, while layer 1 of the first tile
     // runs): warp w writes lanes 32 w .. 32 w + 31, row o of W2 (zero past
@@ -404,6 +412,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             int issued[kMlpMaxStages];
             for (int i = 0; i < kMlpMaxStages; ++i) issued[i] = 0;
             int st = 0, round = 0;  // ring position: stage st, pass `round` over the ring
+            int h_issued = 0;       // loads into the hidden tile's buffer
             bool ok = true;
             for (int t = 0; t < T_n && ok; ++t) {
                 const int m0 = MLP_TILE_ROW0(t);
@@ -412,6 +421,20 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                     for (int kb = 0; kb < dm.nkb1; ++kb) tma_prefetch_2d(&tmX, kb * kMlpKS, m1);
                 }
                 for (int kb = 0; kb < dm.nkb1; ++kb) {
+                    if (kb == kh) {
+                        // the hidden tile's buffer is free once layer 2 of tile t - 1 is done
+                        if (*vfail || (t > 0 && !tc::mbar_wait(&acc2_full, (t - 1) & 1, kGemmWaitPolls))) {
+                            atomicExch(&s_fail, 1);
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t hb = tc::smem_addr(&hs_full);
+                        mbar_arrive_expect_tx(&hs_full, (uint32_t)dm.stage);
+                        tma_load_2d(hbuf, &tmX, kb * kMlpKS, m0, hb);
+                        tma_load_2d(hbuf + kMlpXPart, &tmW1, kb * kMlpKS, 0, hb);
+                        ++h_issued;
+                        continue;
+                    }
                     if (*vfail || (round > 0 && !tc::mbar_wait(&empty[st], (round - 1) & 1, kGemmWaitPolls))) {
                         atomicExch(&s_fail, 1);
                         ok = false;
@@ -443,6 +466,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             // when the MMAs consumed them)
             for (int st = 0; st < S; ++st)
                 if (issued[st] > 0) tc::mbar_wait(&full[st], (uint32_t)(issued[st] - 1) & 1u, kGemmWaitPolls);
+            if (h_issued > 0) tc::mbar_wait(&hs_full, (uint32_t)(h_issued - 1) & 1u, kGemmWaitPolls);
         }
     } else if (warp == kMlpEpiWarps + 1) {
         // ---- MMA issuer ----
@@ -454,12 +478,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
             for (int t = 0; t < T_n && ok; ++t) {
                 // layer 1 (acc1 was read out before h_full of tile t - 1)
                 for (int kb = 0; kb < dm.nkb1; ++kb) {
-                    if (*vfail || !tc::mbar_wait(&full[st], round & 1, kGemmWaitPolls)) {
+                    const bool in_h = kb == kh;  // staged in the hidden tile's buffer
+                    if (*vfail || !tc::mbar_wait(in_h ? &hs_full : &full[st], (uint32_t)(in_h ? t : round) & 1u,
+                                                 kGemmWaitPolls)) {
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t sx = ring0 + (uint32_t)(st * dm.stage);
+                    const uint32_t sx = in_h ? hbuf : ring0 + (uint32_t)(st * dm.stage);
                     if (kp - kb * kMlpKS >= kMlpKS) {
 #pragma unroll
                         for (int j = 0; j < kMlpKS / 16; ++j)
@@ -471,6 +497,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                                      tc::make_desc(sx + kMlpXPart, (uint32_t)(hid * 16), 128), idesc1,
                                      kb > 0 ? 1u : 0u);
                     }
+                    if (in_h) continue;  // freed by acc2_full of this tile instead
                     tc::mma_commit(&empty[st]);
                     if (++st == S) {
                         st = 0;
