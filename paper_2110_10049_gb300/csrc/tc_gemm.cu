@@ -743,7 +743,8 @@ bool tc_mlp_fused_ok(int d, int hid, int kp) {
     if (!(d == 32 || d == 64 || d == 128) || !(hid == 64 || hid == 128 || hid == 256) || kp % 16 != 0 || kp <= 0)
         return false;
     const MlpDims dm(hid, kp);
-    return kp % kMlpKS == 16 && hid / kMlpParts % 32 == 0 && dm.S >= 2 && dm.cols <= 512;
+    // (the hidden tile's buffer also holds one ring stage: hbytes >= stage)
+    return kp % kMlpKS == 16 && hid / kMlpParts % 32 == 0 && dm.S >= 2 && dm.cols <= 512 && dm.hbytes >= dm.stage;
 }
 
 // Mf[v0 + m] = Mc[map[v0 + m]] + relu(X[m] W1^T + b1) W2^T + b2 for m < M:
