@@ -251,7 +251,8 @@ def tables_compare(gosh, sp, rp, co, flush, stream, seeds=(1, 2, 3)):
                         "as many non-edges" % (len(fp), len(sp.test_pos))}
     best = None
     for proj, key in ((0, "bf16_copy"), (1, "bf16_learned")):
-        for e in (WL["epochs"], WL["epochs"] * 3 // 4, WL["epochs"] // 2, WL["epochs"] * 3 // 8, WL["epochs"] // 4):
+        for e in (WL["epochs"], WL["epochs"] * 3 // 4, WL["epochs"] * 5 // 8, WL["epochs"] // 2, WL["epochs"] * 3 // 8,
+                  WL["epochs"] // 4):
             r = arm(gosh.GOSH_BF16, e, proj)
             cmp[key].append(r)
             if (r["fit_auc"] >= ref["fit_auc"] - 0.005 and r["heldout_auc"] >= ref["heldout_auc"] - 0.005 and
