@@ -648,7 +648,7 @@ def main():
         try:
             with open(tr_path) as f:
                 tr = json.load(f)
-            traffic = tr.get("%s_level0_bytes_per_launch" % args.tables) if WL["name"] == "rmat20" else None
+            traffic = tr.get("%s_%s_level0_bytes_per_launch" % (WL["name"], args.tables))
         except Exception:
             traffic = None
 
