@@ -304,7 +304,9 @@ __device__ __forceinline__ uint32_t f16_sr_bits(float x, uint32_t r16) {
     const float lo = __half2float(t);
     const __half u = __ushort_as_half((uint16_t)(tb + 1));
     const float hi = __half2float(u);
-    const float frac = (fabsf(x) - fabsf(lo)) / (fabsf(hi) - fabsf(lo));
+    // fast division (within 2 ulps; 0 past the largest finite value, where hi
+    // is infinite): the IEEE division's slow path is not worth a 2^-16 decision
+    const float frac = __fdividef(fabsf(x) - fabsf(lo), fabsf(hi) - fabsf(lo));
     return ((float)(r16 & 0xffffu) * (1.0f / 65536.0f) < frac) ? (uint32_t)(tb + 1) : (uint32_t)tb;
 }
 
