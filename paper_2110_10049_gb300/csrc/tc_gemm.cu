@@ -291,18 +291,19 @@ __global__ void __launch_bounds__(kGemmThreads) tma_gemm_kernel(const __grid_con
 // W2 into tensor memory, while layer 1 of the first tile runs), warp 16
 // loads the ring of S stages (each: one 64-column block of the X tile and
 // the matching block of W1, both as one 128-byte-swizzled TMA box; the
-// 16-column tail of K as two 8-column boxes per operand without swizzle)
-// and prefetches the next tile's X rows into L2, warp 17 issues the MMAs.
-// The epilogue warps bring the residual's coarse rows into L2 at the start
-// of a tile, so their latency hides behind layer 1.
+// 16-column tail of K as two 8-column boxes per operand without swizzle),
+// stages one more block per tile in H's buffer (idle during layer 1) and
+// prefetches the next tile's X rows into L2, warp 17 issues the MMAs.  The
+// epilogue warps bring the residual's coarse rows into L2 at the start of a
+// tile, so their latency hides behind layer 1.
 //
 // Barriers: full / empty per stage, hs_full (the K block staged in H's
 // buffer arrived), acc1_full (layer 1 done), h_full (acc1 read out and H
 // written and fenced for the tensor cores), w2_ready (W2 in tensor memory),
 // acc2_full (layer 2 done: H's buffer free for the next tile's staged
-// block), acc2_empty (acc2 read out).  Every wait is bounded; on time-out the CTA raises *err, every role
-// stops, the producer waits (bounded) for its copies in flight and the
-// tensor memory is freed.
+// block), acc2_empty (acc2 read out).  Every wait is bounded; on time-out
+// the CTA raises *err, every role stops, the producer waits (bounded) for
+// its copies in flight and the tensor memory is freed.
 constexpr int kMlpEpiWarps = 16;
 constexpr int kMlpParts = kMlpEpiWarps / 4;  // epilogue warps sharing each 32 tensor-memory lanes
 constexpr int kMlpThreads = (kMlpEpiWarps + 2) * 32;
