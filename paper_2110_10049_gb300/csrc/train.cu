@@ -125,10 +125,12 @@ int tile_vertices(const gosh_params *p, int64_t n, int lanes, int pass) {
     const bool f32_lockfree = p->dtype == GOSH_F32 && p->mode != GOSH_DETERMINISTIC;
     const bool atomic_lockfree = (red16 || f32_lockfree) && !p->plain_stores;
     const int mid = atomic_lockfree ? 32 : (p->dtype != GOSH_F32 && p->mode != GOSH_DETERMINISTIC ? 8 : 16);
-    // 16-bit atomic levels from 2^21 rows: 32 (R-MAT 22 level 0, 2.27 M rows:
-    // 882 us per BF16 epoch against 912 at 16; at 614 k rows the two are
-    // within 0.6%)
-    const int large = atomic_lockfree ? (red16 && n >= (int64_t(1) << 21) ? 32 : 16) : 32;
+    // 16-bit atomic levels: 28 from 2^19 rows, 32 from 2^21 (per-epoch BF16
+    // sweep of tiles 12-32, two repeats: R-MAT 20 level 0, 614 k rows, 204.3
+    // us at 28 against 207.5 at 16 and 32; R-MAT 22 level 0, 2.27 M rows,
+    // 880 us at 32 against 885 at 28 and 911 at 16)
+    const int large =
+        atomic_lockfree ? (red16 ? (n >= (int64_t(1) << 21) ? 32 : 28) : 16) : 32;
     // atomic lock-free levels of 2^14 to 2^16 rows: 8 (level 2 of R-MAT 20,
     // 22k rows: 10.4 us per BF16 epoch against 12.6 at 4)
     const int small = atomic_lockfree && n >= (int64_t(1) << 14) ? 8 : 4;
